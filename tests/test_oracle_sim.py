@@ -1,0 +1,148 @@
+"""Pins of the oracle's full step (DM + gas + subgrid) and of its spectra and gradients.
+
+* Uniform universe: nothing moves and the specific internal energy falls exactly as a^-2
+  (adiabatic expansion at gamma = 5/3: the energy-equation source vanishes, Eq. ev).
+* Exact conservation over a run: gas mass, and total (DM + gas) momentum.
+* A single small mode grows like D(a) in DM and gas alike (linear theory, Sec. 2.2).
+* Subgrid trend (Sec. 2.4.1): a higher density threshold gives fewer star-formation events.
+* Power spectrum: Parseval, a single mode lands in one bin with its amplitude, r_c = +-1.
+* Gradients: reverse mode through whole runs equals central finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import cosmology as C
+from oracle import pm, sim, spectra
+from oracle.subgrid import t_per_e
+
+DT = torch.float64
+
+
+def test_uniform_universe_adiabatic_cooling():
+    prm = sim.Params(n=8, box=8.0, n_steps=6, a_start=0.1, a_end=0.7).as_dict()
+    st = sim.run(torch.zeros(8, 8, 8, dtype=DT), prm)
+    U = st["U"]
+    assert st["s"].abs().max() == 0 and st["p"].abs().max() == 0
+    a = prm["a_end"]
+    e = (U[4] - (U[1:4] ** 2).sum(0) / (2 * U[0])) / (a * a * U[0])
+    e0 = prm["T_init"] / t_per_e(prm["gamma"], prm["mu"])
+    assert torch.allclose(e * a * a, torch.full_like(e, e0 * prm["a_start"] ** 2), rtol=1e-12)
+
+
+def test_run_conserves_gas_mass_and_total_momentum():
+    prm = sim.Params(n=16, box=16.0, n_steps=8, a_start=0.1, a_end=0.6, rms_ref=0.2,
+                     subgrid_on=1, T0_uv=1e4).as_dict()
+    noise = sim.noise_field(prm)
+    st0 = sim.init_state(noise, prm)
+    st = sim.run(noise, prm)
+    fb = sim.f_baryon(prm)
+    mom = lambda s: (1 - fb) * s["p"].sum(1) + s["U"][1:4].sum((1, 2, 3))
+    assert abs(st["U"][0].sum() - st0["U"][0].sum()) < 1e-12 * st0["U"][0].sum()
+    scale = (1 - fb) * st["p"].abs().sum() + st["U"][1:4].abs().sum()
+    assert (mom(st) - mom(st0)).abs().max() < 1e-12 * scale
+
+
+@pytest.mark.slow
+def test_single_mode_linear_growth():
+    n, box = 32, 32.0
+    prm = sim.Params(n=n, box=box, n_steps=16, a_start=0.1, a_end=0.5, T_init=100.0).as_dict()
+    z, y, x = torch.meshgrid(*(torch.arange(n, dtype=DT),) * 3, indexing="ij")
+    # white noise whose shaped field is one Fourier mode along x (k = 2 pi / L)
+    noise = 0.011 * torch.cos(2 * math.pi * x / n)   # delta ~ 0.01 at a_start, ~0.05 at a_end
+    st0 = sim.init_state(noise, prm)
+    st = sim.run(noise, prm)
+
+    def amp(field):
+        return torch.fft.rfftn(field)[0, 0, 1].abs().item()
+
+    fb = sim.f_baryon(prm)
+    g0 = amp(st0["U"][0] / fb - 1)
+    g1 = amp(st["U"][0] / fb - 1)
+    dm1 = amp(pm.deposit(st["s"], torch.ones(n ** 3, dtype=DT), n, box) - 1)
+    growth = (C.growth_D(prm["a_end"], 0.3) / C.growth_D(prm["a_start"], 0.3)).item()
+    assert abs(g1 / g0 / growth - 1) < 0.02
+    assert abs(g1 / dm1 - 1) < 0.03
+
+
+def test_higher_threshold_fewer_events():
+    base = dict(n=16, box=16.0, n_steps=6, a_start=0.2, a_end=0.8, rms_ref=0.3,
+                subgrid_on=1, Pi0=0.3, T_c=1e6, w_T=5e4)
+    counts = []
+    for dc in (0.0, 0.5, 2.0):
+        prm = sim.Params(**base, delta_c=dc, w_delta=0.05 * max(dc, 0.2)).as_dict()
+        st = sim.run(sim.noise_field(prm), prm)
+        counts.append(sum(int(e.sum()) for e in st["events"]))
+    assert counts[0] > counts[1] > counts[2]
+
+
+def test_power_spectrum_parseval_and_single_mode():
+    n, box = 16, 10.0
+    f = torch.randn(n, n, n, dtype=DT, generator=torch.Generator().manual_seed(0))
+    f -= f.mean()
+    k, P, nm = spectra.power_spectrum(f, box, nbins=n)
+    # sum_k |f_k|^2 = N^3 sum_x f^2 ; P = L^3 |f_k|^2 / N^6
+    total = (P * nm).sum().item() * n ** 6 / box ** 3
+    assert abs(total / (n ** 3 * (f ** 2).sum().item()) - 1) < 1e-12
+    z, y, x = torch.meshgrid(*(torch.arange(n, dtype=DT),) * 3, indexing="ij")
+    g = 0.7 * torch.cos(2 * math.pi * (2 * x + y) / n)
+    k, P, nm = spectra.power_spectrum(g, box, nbins=n)
+    b = round(math.sqrt(5))  # |k| / k_f = sqrt(2^2 + 1^2)
+    nz = torch.nonzero(P > 1e-20).flatten().tolist()
+    assert nz == [b - 1]
+    # two modes (+-k) of |g_k| = 0.35 N^3 each among nm[b-1] modes in the bin
+    expect = 2 * (0.35 * n ** 3) ** 2 * box ** 3 / n ** 6 / nm[b - 1].item()
+    assert abs(P[b - 1].item() / expect - 1) < 1e-12
+    r = spectra.cross_correlation(f, f, box)
+    assert torch.allclose(r[nm > 0], torch.ones_like(r[nm > 0]), atol=1e-12)
+    r = spectra.cross_correlation(f, -f, box)
+    assert torch.allclose(r[nm > 0], -torch.ones_like(r[nm > 0]), atol=1e-12)
+
+
+def _fd_check(fun, x, direction, h):
+    """Reverse-mode derivative along `direction` and the central difference closest to it
+    over steps h, h/10, h/100. The scheme has kinks (limiter gate, CIC cell edges, |v|,
+    the UV-floor max) and a large step can straddle one; a small step cannot, in practice."""
+    x = x.detach().clone().requires_grad_(True)
+    val = fun(x)
+    (g,) = torch.autograd.grad(val, x)
+    ad = (g * direction).sum().item()
+    best = None
+    for hh in (h, h / 10, h / 100):
+        fd = (fun(x.detach() + hh * direction) - fun(x.detach() - hh * direction)).item() / (2 * hh)
+        if best is None or abs(fd - ad) < abs(best - ad):
+            best = fd
+    return ad, best
+
+
+def test_gradient_wrt_initial_noise_matches_finite_differences():
+    prm = sim.Params(n=8, box=8.0, n_steps=4, a_start=0.1, a_end=0.5, rms_ref=0.3,
+                     subgrid_on=1, delta_c=0.2, w_delta=0.1, T_c=1e6, w_T=1e5, Pi0=0.2,
+                     T0_uv=5e3).as_dict()
+    noise = sim.noise_field(prm)
+    target = sim.run(sim.noise_field(dict(prm, seed=2)), prm)["U"][0].detach()
+    fun = lambda w: sim.mse_density(sim.run(w, prm)["U"], target)
+    d = torch.randn(noise.shape, dtype=DT, generator=torch.Generator().manual_seed(3))
+    ad, fd = _fd_check(fun, noise, d, 1e-5)
+    assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-14
+
+
+@pytest.mark.parametrize("name", ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"])
+def test_gradient_wrt_parameters_matches_finite_differences(name):
+    base = dict(n=8, box=8.0, n_steps=4, a_start=0.1, a_end=0.5, rms_ref=0.3, subgrid_on=1,
+                delta_c=0.2, w_delta=0.1, T_c=1e6, w_T=1e5, Pi0=0.2, T0_uv=5e3)
+    prm = sim.Params(**base).as_dict()
+    noise = sim.noise_field(prm)
+    target = sim.run(sim.noise_field(dict(prm, seed=2)), prm)["U"][0].detach()
+
+    def fun(v):
+        q = dict(prm)
+        q[name] = v
+        st = sim.run(noise, q)
+        return sim.mse_density(st["U"], target) + 1e-3 * st["U"][4].mean()
+
+    x0 = torch.tensor(float(prm[name]), dtype=DT)
+    ad, fd = _fd_check(fun, x0, torch.tensor(1.0, dtype=DT), 1e-6 * max(abs(x0.item()), 1e-2))
+    assert abs(ad - fd) <= 1e-5 * abs(fd) + 1e-12
