@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable hydro step on GB300: cell-steps/s forward + adjoint.
+
+One bench step is one pass of the whole hot path on a 128^3 grid with 128^3 dark-matter
+particles: initial conditions from device-resident white noise, 100 steps a = 0.05 -> 1.0
+(FastPM kick-drift-kick, three relaxing-TVD sweeps, subgrid with Gumbel-softmax, CIC +
+spectral Poisson), the density loss against a mock field, and the checkpointed adjoint
+(checkpoint every 10 steps) back to the white noise and the parameters.
+
+value     cell-steps/s of that pass = 128^3 * 100 / time, summed over ranks (replicas).
+e2e       the same through the C ABI with the noise copied from pinned host memory and
+          the noise gradient plus the loss copied back inside the timed region.
+roofline  the dominant kernel (hydro sweeps), timed with CUDA events on its stream.
+cpu_baseline  the FP64 oracle on the host cores on a bounded sample of the same workload.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: launched by torchrun, each rank runs an independent replica (no collective on
+the data path); timing is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s fwd & fwd+adjoint at 128^3 FP32; HBM GB/s vs peak; err vs FP64"
+WORKLOAD = dict(n=128, box=128.0, n_steps=100, a_start=0.05, a_end=1.0, ckpt_every=10,
+                subgrid_on=1, delta_c=100.0, Pi0=0.05, E0=0.03, T_c=3.0e4, w_delta=5.0,
+                w_T=1500.0, T0_uv=1.0e4, gamma_uv=1.4, seed=1)
+WORKLOAD_NAME = ("128^3 cells + 128^3 DM particles, box 128 Mpc/h, 100 steps a=0.05->1.0, "
+                 "subgrid on, ICs + forward + density-MSE loss + checkpointed adjoint "
+                 "(every 10 steps) to the 2,097,152 white-noise amplitudes and 7 parameters")
+SWEEP_BYTES_PER_CELL = 40  # 5 float32 fields read + 5 written
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline_sample(steps: int = 1):
+    """The oracle (FP64, torch CPU, autograd) on `steps` full steps of the 128^3 workload,
+    forward + reverse; returns (cell-steps/s, seconds, threads)."""
+    import torch
+    from oracle import sim as osim
+
+    prm = dict(osim.Params().as_dict(), **WORKLOAD)
+    n = prm["n"]
+    noise = torch.randn(n, n, n, dtype=torch.float64, generator=torch.Generator().manual_seed(1))
+    st = osim.init_state(noise, prm)
+    sched = osim.schedule(prm)
+    U = st["U"].detach().clone().requires_grad_(True)
+    st["U"] = U
+    t0 = time.perf_counter()
+    cur = st
+    for _ in range(steps):
+        cur = osim.step(cur, prm, sched)
+    L = (cur["U"][0] ** 2).sum()
+    L.backward()
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt, dt, torch.get_num_threads()
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same metric and unit."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline_sample(1)
+    times = []
+    for _ in range(args.steps):
+        v, dt, threads = cpu_baseline_sample(1)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    n3 = WORKLOAD["n"] ** 3
+    value = n3 / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "one full step (forward + reverse) of the 128^3 workload "
+                                   "per bench step: " + WORKLOAD_NAME},
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": "1 step fwd+reverse at 128^3 per bench step"},
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    import paper_2502_02294_gb300 as dh
+    import synth
+
+    dev = torch.device("cuda", local)
+    p = dh.default_params(**WORKLOAD)
+    p.seed = WORKLOAD["seed"] + rank
+    n = p.n
+    n3 = n ** 3
+    noise = torch.from_numpy(synth.white_noise(n, 100 + rank).astype("float32")).to(dev)
+    target = torch.from_numpy((0.163 * (1 + 0.3 * synth.field(n, 7))).astype("float32")).to(dev)
+    sim = dh.Simulation(p, noise)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    c = 1.0 / n3
+
+    def hot_path(noise_dev):
+        sim.reinit(noise_dev)
+        sim.run()
+        dL, loss = sim.loss_density(target, c)
+        dnoise, dpar = sim.run_adjoint(dL, None)
+        return dnoise, dpar, loss
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        hot_path(noise)
+    # ---- device-resident timing (value)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    launches0 = dh.lib.sim_kernel_launches()
+    times = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hot_path(noise)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    launches = dh.lib.sim_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    # ---- forward-only timing
+    fwd_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.reinit(noise)
+        sim.run()
+        e1.record(stream)
+        e1.synchronize()
+        fwd_times.append(e0.elapsed_time(e1))
+    fwd_ms = statistics.mean(fwd_times)
+    # ---- end to end through host buffers
+    host_noise = noise.cpu().pin_memory()
+    host_grad = torch.empty(n3, dtype=torch.float32).pin_memory()
+    host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    dev_noise = torch.empty_like(noise)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dev_noise.copy_(host_noise, non_blocking=True)
+        dnoise, dpar, loss = hot_path(dev_noise)
+        host_grad.copy_(dnoise.view(-1), non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e2e_times)
+    # ---- dominant kernel: the three hydro sweeps, timed on the launching stream
+    gas = sim.state()["gas"]
+    out = torch.empty_like(gas)
+    nu = sim.schedule(50)["dtau"] * n / p.box
+    reps = 20
+    for axis in range(3):
+        dh.sweep(gas, axis, nu)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in range(reps):
+        for axis in range(3):
+            dh.lib.sim_sweep(dh.api._ptr(gas if r % 2 == 0 else out),
+                             dh.api._ptr(out if r % 2 == 0 else gas), n, axis, nu, p.gamma,
+                             p.limiter_eps, dh.api._stream())
+    e1.record(stream)
+    e1.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / (3 * reps)
+    sweep_gbs = SWEEP_BYTES_PER_CELL * n3 / (sweep_ms * 1e-3) / 1e9
+
+    # ---- max over ranks
+    vals = torch.tensor([ms, fwd_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+    ms, fwd_ms, e2e_ms = vals.tolist()
+    cell_steps = n3 * p.n_steps * ws
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks = _peaks()
+    peak_bw = peaks["hbm_gbs"] if peaks else 6800.0
+    line = {
+        "metric": METRIC,
+        "value": cell_steps / (ms / 1e3),
+        "unit": "cell-steps/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "n": n, "n_steps": p.n_steps,
+                   "ckpt_every": p.ckpt_every, "parallelism": f"replicas x{ws}",
+                   "l2": "512 MB buffer written between timed iterations"},
+        "fwd_value": cell_steps / (fwd_ms / 1e3),
+        "fwd_ms_per_step": fwd_ms,
+        "e2e": {"value": cell_steps / (e2e_ms / 1e3), "unit": "cell-steps/s",
+                "h2d_bytes_per_step": n3 * 4, "d2h_bytes_per_step": n3 * 4 + 8},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": peak_bw, "unit": "GB/s",
+                     "frac": sweep_gbs / peak_bw, "traffic": None,
+                     "kernel": "sweep_fwd_kernel (x, y, z average)",
+                     "algorithmic_bytes_per_launch": SWEEP_BYTES_PER_CELL * n3,
+                     "launch_ms": sweep_ms,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
+                     else "fallback 6.8 TB/s (of fallback)"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        v, dt, threads = cpu_baseline_sample(1)
+        line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"1 full step fwd+reverse at 128^3 ({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

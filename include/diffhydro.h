@@ -1,0 +1,259 @@
+/*
+ * diffhydro.h -- C ABI of the GB300 (sm_103a) differentiable cosmological hydro step.
+ *
+ * Method: arXiv 2502.02294 (Horowitz & Lukic, "Differentiable Cosmological Hydrodynamics",
+ * diffHydro). One time step couples
+ *   - the comoving Euler equations (Sec. 2.3, Eqs. cont / momentum / ev / conservation)
+ *     solved with the relaxing TVD scheme (Sec. 2.3.1-2.3.2, Eqs. TVD_halfstep and
+ *     TVD_fullstep, van Leer limiter, Strang-split sweeps),
+ *   - dark matter particles under particle-mesh gravity with FastPM kick-drift-kick factors
+ *     (Sec. 2.2, Eq. dm_hamil),
+ *   - a stochastic subgrid star-formation step differentiated with Gumbel-softmax
+ *     (Sec. 2.4, Eqs. reparam / gumbelsoftmax and pi_0(rho, T)),
+ * and its reverse-mode derivative (Sec. 2.3.5), with checkpoints every few steps.
+ *
+ * Conventions for every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller unless a comment says "host".
+ *     The library never frees them and never keeps them past the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Work is
+ *     enqueued on it and the call returns without synchronising, except where stated.
+ *   - Grids are n^3 float32 in C order [z][y][x] (x fastest). The gas state is 5 such
+ *     fields back to back: rho, m_x, m_y, m_z, eps (structure of arrays, 5 n^3 floats).
+ *     Particle arrays are [3][n^3] (x, y, z components) in Lagrangian order, particle
+ *     index (qz n + qy) n + qx for lattice site q = (qx, qy, qz) dx; positions are stored
+ *     as displacements s from the lattice site (x = q + s, periodic), momenta as p = a^2 dx/dt.
+ *   - Units: length Mpc/h (comoving), velocity 100 km/s, time 1/H0 (so H0 = 1). Densities
+ *     in units of the mean total matter density; the mean gas density is f_b = Omega_b/Omega_m.
+ *     Gas variables: m = a rho U (U peculiar velocity), eps = a^2 rho (e + U^2/2).
+ *   - Errors are returned as sim_status codes; nothing aborts or traps. sim_last_error()
+ *     gives a message. Invalid arguments are rejected before any work is enqueued.
+ *   - The library is not thread safe for one handle; distinct handles may be used from
+ *     distinct threads.
+ */
+#ifndef DIFFHYDRO_H
+#define DIFFHYDRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SIM_OK = 0,
+  SIM_EINVAL = 1,   /* invalid argument or state                          */
+  SIM_ENOMEM = 2,   /* device allocation failed                           */
+  SIM_ECUDA = 3,    /* a CUDA runtime or cuFFT call failed                */
+  SIM_ECFL = 4,     /* CFL number above the configured limit (sim_run)   */
+  SIM_ENAN = 5,     /* non-finite value detected in the state            */
+  SIM_ETIMEOUT = 6, /* a bounded device wait gave up                      */
+  SIM_ENOTIMPL = 7  /* option not implemented                             */
+} sim_status;
+
+/* Parameter block. sim_params_default() fills the values quoted beside each field. */
+typedef struct {
+  int32_t n;            /* grid cells per side = particles per side (32)                 */
+  int32_t n_steps;      /* steps from a_start to a_end, uniform in a (20)  Sec. 2.3.3   */
+  int32_t ckpt_every;   /* checkpoint interval of sim_run, steps (6)       Sec. 2.3.5   */
+  int32_t subgrid_on;   /* 1: star formation + UV floor each step (0)      Sec. 2.4     */
+  int32_t gravity_on;   /* 1: PM gravity and kicks (1)                                   */
+  int32_t hydro_on;     /* 1: gas sweeps (1)                                             */
+  int32_t kdk_mode;     /* 0: FastPM factors, 1: plain int dt factors (0)  Sec. 2.2     */
+  int32_t instance;     /* Philox counter word 2 (0)                                     */
+  uint64_t seed;        /* Philox key (1)                                                */
+  double box;           /* box side, Mpc/h (32)                                          */
+  double omega_m;       /* (0.3) */
+  double omega_b;       /* (0.049): f_b = omega_b / omega_m                              */
+  double h;             /* (0.7), does not enter in these units                          */
+  double sigma8;        /* (0.8): scales the initial amplitude linearly                  */
+  double gamma;         /* adiabatic index (5/3)                                         */
+  double mu;            /* mean molecular weight (0.6)                                   */
+  double T_init;        /* initial gas temperature, K (1e4)                              */
+  double a_start;       /* (0.1) */
+  double a_end;         /* (0.5) */
+  double delta_c;       /* star-formation overdensity threshold (100)      Sec. 2.4.2  */
+  double Pi0;           /* star-formation probability scale (0.05)                      */
+  double E0;            /* injected specific energy, (100 km/s)^2 (0.03)                */
+  double T_c;           /* star-formation temperature threshold, K (3e4)                */
+  double w_delta;       /* sigmoid width in delta (5)                                    */
+  double w_T;           /* sigmoid width in T, K (1500)                                  */
+  double tau;           /* Gumbel-softmax temperature (0.1)                Sec. 2.4.2  */
+  double T0_uv;         /* UV-background floor temperature at mean density, K; 0 = off (0) */
+  double gamma_uv;      /* floor slope: T_floor = T0 (rho/f_b)^(gamma_uv - 1) (1.4)      */
+  double rms_ref;       /* rms of the linear contrast at a_ref for sigma8_ref (0.05)     */
+  double a_ref;         /* (0.1) */
+  double sigma8_ref;    /* (0.8) */
+  double omega_m_ref;   /* (0.3) */
+  double kc_frac;       /* spectrum cutoff k_c as a fraction of Nyquist (0.5)            */
+  double limiter_eps;   /* van Leer epsilon (1e-30)                                      */
+  double cfl_max;       /* sim_run returns SIM_ECFL above this CFL number; 0 = no check (0) */
+} sim_params;
+
+/* Order of the parameter-gradient vector of sim_run_adjoint / sim_step_adjoint. */
+enum {
+  SIM_P_OMEGA_M = 0,
+  SIM_P_SIGMA8 = 1,
+  SIM_P_DELTA_C = 2,
+  SIM_P_PI0 = 3,
+  SIM_P_E0 = 4,
+  SIM_P_T0_UV = 5,
+  SIM_P_GAMMA_UV = 6,
+  SIM_NPARAMS = 7
+};
+
+typedef struct sim_s sim_t;
+
+/* Fill *p with the defaults above. Host pointer. */
+sim_status sim_params_default(sim_params* p);
+
+/* Last error message of this handle, or of the calling thread when h is NULL. */
+const char* sim_last_error(const sim_t* h);
+
+/* Number of CUDA kernels this library has launched in this process so far (all devices,
+ * all threads; cuFFT's own kernels are not counted). Host-only, never fails. */
+int64_t sim_kernel_launches(void);
+
+/* ------------------------------------------------------------------ whole path */
+
+/* Create a simulation and set up its initial conditions (Sec. 2.1): white noise w
+ * (noise: device n^3 floats, or NULL to draw it from Philox with tag 0), shaped by the
+ * synthetic spectrum P(k) = A k^-2 exp(-(k/k_c)^2) normalised to rms_ref (sigma8/sigma8_ref)
+ * D(a_start)/D(a_ref), displaced with the Zel'dovich approximation for DM and gas, then
+ * the initial force. Allocates all working memory on the current device (the handle owns
+ * it). The noise buffer is read before the call returns to the stream order only; the
+ * caller may reuse it after the stream reaches this point. */
+sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t** out);
+
+/* Free the handle and its device memory (synchronises its stream). NULL is ignored. */
+void sim_destroy(sim_t* h);
+
+/* Advance one step a_n -> a_{n+1}: half kick (DM + gas), DM drift, three Strang-ordered
+ * hydro sweeps (order XYZ, ZYX, ZXY, YXZ, YZX, XZY by n mod 6, Sec. 2.3.2), subgrid,
+ * CIC deposit + Poisson (Sec. 2.2), half kick. Keeps a copy of the step's input state
+ * so that sim_step_adjoint can back-propagate through it. */
+sim_status sim_step(sim_t* h);
+
+/* Reverse-mode derivative of the most recent sim_step. On entry adj_gas (5 n^3) and
+ * adj_part (6 n^3: d/ds then d/dp) hold dL/d(state after the step); on return they hold
+ * dL/d(state before the step). adj_params (device, SIM_NPARAMS doubles) is ACCUMULATED
+ * with the step's direct dependence on the parameters. The step's gravity at its start is
+ * a function of the state before it, and is differentiated as such. */
+sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* adj_params);
+
+/* Advance n_steps steps from the initial state (the handle must be fresh from sim_init or
+ * sim_reset), storing a checkpoint of the state every ckpt_every steps for
+ * sim_run_adjoint (Sec. 2.3.5: checkpoints every 6 steps in the paper). */
+sim_status sim_run(sim_t* h, int32_t n_steps);
+
+/* Gradient of a scalar loss through the whole run made by sim_run and through the
+ * initial conditions. dL_dgas (5 n^3) and dL_dpart (6 n^3: d/ds then d/dp) are the
+ * loss derivatives at the final state (either may be NULL = 0). Outputs: dL_dnoise
+ * (n^3, may be NULL) and dL_dparams (device, SIM_NPARAMS doubles, overwritten). Each
+ * segment between checkpoints is recomputed forward once. */
+sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart,
+                           float* dL_dnoise, double* dL_dparams);
+
+/* Rewind the handle to its initial state (keeps allocations; clears checkpoints). */
+sim_status sim_reset(sim_t* h);
+
+/* Recompute the initial conditions from new white noise (device n^3; NULL = Philox draw
+ * of the handle's seed) and rewind to step 0, keeping all allocations. This is the
+ * per-iteration entry of field-level inference (Sec. 3.2): the noise is the variable. */
+sim_status sim_reinit(sim_t* h, const float* noise);
+
+/* Density loss of the current state (Sec. 3.1-3.2): L = c sum_cells (rho - target)^2,
+ * c = 1/n^3 gives the mean squared error, c = 1/(2 sigma^2) the Gaussian pixel likelihood
+ * of field-level inference. Writes dL/d(gas) (5 n^3: 2 c (rho - target) in the density
+ * field, 0 elsewhere) and stores L in *loss (device double, overwritten). */
+sim_status sim_loss_density(sim_t* h, const float* target, double c, float* dL_dgas,
+                            double* loss);
+
+/* Copy the current state out (device pointers; any may be NULL):
+ * gas 5 n^3, part 6 n^3 (s then p), star n^3 (accumulated relaxed star field),
+ * aux n^3 (per-particle star readout, Sec. 2.4.1), events n^3/32 uint32 words (bit i of
+ * word j: cell 32 j + i formed a star in the last step's hard Gumbel-max draw),
+ * gravity 3 n^3 (current force field on the mesh). Also returns the step index. */
+sim_status sim_get_state(sim_t* h, float* gas, float* part, float* star, float* aux,
+                         uint32_t* events, float* gravity, int32_t* step);
+
+/* Overwrite the state (gas 5 n^3, part 6 n^3) at step index `step` and recompute the
+ * force field. Star, aux and checkpoints are cleared. */
+sim_status sim_set_state(sim_t* h, const float* gas, const float* part, int32_t step);
+
+/* Host FP64 step factors of step i: out[0..5] = a_i, a_{i+1}, K1, dtau, K2,
+ * 3 Omega_m / (2 a_{i+1}) (FastPM or plain, Sec. 2.2). Host pointer. */
+sim_status sim_schedule(const sim_t* h, int32_t i, double* out6);
+
+/* Largest CFL number max(|v_d| + c_s) dtau / dx over cells and directions for the
+ * current state and the next step's dtau (Eq. dt). Synchronises the stream. */
+sim_status sim_cfl(sim_t* h, double* cfl_out);
+
+/* ------------------------------------------------------------------ single kernels */
+
+/* One relaxing-TVD sweep along axis (0 = x, 1 = y, 2 = z) with nu = dtau/dx:
+ * half step with first-order upwind relaxed fluxes (Eq. TVD_halfstep), full step with
+ * limited second-order fluxes on the half-step state (Eq. TVD_fullstep). u_in, u_out:
+ * 5 n^3 each, must not alias. */
+sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int32_t axis, double nu,
+                     double gamma, double limiter_eps, void* stream);
+
+/* Adjoint of sim_sweep at u_in: lam_in = (d u_out / d u_in)^T lam_out (5 n^3 each, no
+ * aliasing). If dnu (device double) is not NULL, adds lam_out . d u_out / d nu to it. */
+sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out, float* lam_in,
+                             int32_t n, int32_t axis, double nu, double gamma,
+                             double limiter_eps, double* dnu, void* stream);
+
+/* Cloud-in-cell deposit (Sec. 2.2): grid[node] += sum_p value_p W(x_p - node) with
+ * W the CIC weights, cell decision floor(s/dx) taken in float32. values may be NULL (=1).
+ * Particles: np = n^3 in Lagrangian order of an n^3 lattice, s: 3 n^3. grid: n^3,
+ * ACCUMULATED. Deterministic (64-bit fixed-point accumulation). */
+sim_status sim_deposit_cic(const float* s, const float* values, int32_t n, double box,
+                           float* grid, void* stream);
+
+/* CIC readout of `nf` fields (grid: nf n^3) at the particles: out[f][p] (nf n^3). */
+sim_status sim_interp_cic(const float* grid, int32_t nf, int32_t n, double box,
+                          const float* s, float* out, void* stream);
+
+/* Spectral Poisson force g = -grad(phi), del^2 phi = pref * delta (Sec. 2.2):
+ * g_k = i k pref delta_k / k^2, k = 0 removed, Nyquist gradient factor zeroed.
+ * delta: n^3, g: 3 n^3 (x, y, z). Uses cuFFT. */
+sim_status sim_gravity(const float* delta, int32_t n, double box, double pref, float* g,
+                       void* stream);
+
+/* Adjoint of sim_gravity: lam_delta = (d g / d delta)^T lam_g (lam_g 3 n^3, lam_delta n^3). */
+sim_status sim_gravity_adjoint(const float* lam_g, int32_t n, double box, double pref,
+                               float* lam_delta, void* stream);
+
+/* Subgrid update of a gas state in place at scale factor a with Philox draws of
+ * (seed, step, instance): pi_0(rho, T), Gumbel-softmax zhat (Eq. gumbelsoftmax), energy
+ * injection E0 zhat, UV floor. zhat (n^3) and events (n^3/32 words) may be NULL.
+ * `gas` 5 n^3. Parameters from *p (gamma, mu, omega_b/omega_m, subgrid fields). */
+sim_status sim_subgrid(float* gas, int32_t n, double a, const sim_params* p, int32_t step,
+                       float* zhat, uint32_t* events, void* stream);
+
+/* Adjoint of sim_subgrid at gas_in (the state before the update): lam (5 n^3) is
+ * overwritten with the adjoint of the input; dparams (device doubles, SIM_NPARAMS) is
+ * accumulated for delta_c, Pi0, E0, T0_uv, gamma_uv; dfb (device double, may be NULL)
+ * accumulates the derivative with respect to f_b. */
+sim_status sim_subgrid_adjoint(const float* gas_in, float* lam, int32_t n, double a,
+                               const sim_params* p, int32_t step, double* dparams,
+                               double* dfb, void* stream);
+
+/* Philox4x32-10 words for counters (i, step, instance, tag), i = 0..count-1, key from
+ * seed: out[4*i + j] = word j. */
+sim_status sim_philox(uint64_t seed, uint32_t step, uint32_t instance, uint32_t tag,
+                      int64_t count, uint32_t* out, void* stream);
+
+/* Binned power spectrum (Sec. 3.1; cross spectrum if b != NULL) of n^3 fields a, b with
+ * bins of width k_f = 2 pi / box, bin index round(|k|/k_f), bins 1..nbins reported:
+ * k (mode-weighted mean |k|), pk = box^3 <Re(a_k conj(b_k))> / n^6, nmodes. Outputs are
+ * device doubles of length nbins (1 <= nbins <= 2048). Uses cuFFT. */
+sim_status sim_power_spectrum(const float* a, const float* b, int32_t n, double box,
+                              int32_t nbins, double* k, double* pk, double* nmodes,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFHYDRO_H */

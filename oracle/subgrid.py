@@ -22,7 +22,8 @@ f_b; T = (gamma - 1) mu m_p e / k_B from the specific internal energy
 e = (eps - |m|^2/(2 rho)) / (a^2 rho); E_0 is a specific energy in (100 km/s)^2 added to
 the cell's own e times zhat (the forward pass injects the relaxed zhat); w_delta, w_T are
 fixed hyper-parameters. The UV-background temperature floor T_0 (rho / rho_gas_mean)^(gamma_T
-- 1) is applied after the injection, e <- max(e, e_floor) (d/de at a tie goes to e).
+- 1) is applied after the injection, e <- max(e, e_floor) (d/de at a tie goes to e), and
+only when T_0 > 0 (T_0 = 0: no UV background, as in the paper, which has no heating term).
 """
 from __future__ import annotations
 
@@ -64,8 +65,11 @@ def subgrid(U, a, prm, g0, g1):
     zhat = torch.sigmoid(logit / prm["tau"])
     events = logit.detach() > 0
     e1 = e + prm["E0"] * zhat
-    e_floor = (prm["T0_uv"] / tpe) * (rho / prm["f_b"]) ** (prm["gamma_uv"] - 1.0)
-    e2 = torch.where(e1 >= e_floor, e1, e_floor)
+    if float(prm["T0_uv"]) > 0:
+        e_floor = (prm["T0_uv"] / tpe) * (rho / prm["f_b"]) ** (prm["gamma_uv"] - 1.0)
+        e2 = torch.where(e1 >= e_floor, e1, e_floor)
+    else:
+        e2 = e1
     eps_new = ke + a * a * rho * e2
     return torch.cat([U[:4], eps_new[None]]), zhat, events
 

@@ -1,0 +1,268 @@
+"""Torch-facing wrappers of the C ABI (same names as the C entry points, minus ``sim_``).
+
+PyTorch provides device memory and the current CUDA stream; every computation is a call
+into libdiffhydro.so. Inputs must be contiguous CUDA tensors of the stated dtype.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import (NPARAMS, SimParams, check, default_params, lib)
+
+F32, F64, U32 = torch.float32, torch.float64, torch.int32
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _chk(t, dtype, numel, name):
+    if t.dtype != dtype or t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements of {dtype}, got {t.numel()} of {t.dtype}")
+
+
+# ------------------------------------------------------------------ single kernels
+def _side(cells: int) -> int:
+    n = round(cells ** (1.0 / 3.0))
+    if n ** 3 != cells:
+        raise ValueError(f"{cells} cells is not a cube")
+    return n
+
+
+def sweep(u_in, axis: int, nu: float, gamma: float = 5.0 / 3.0, limiter_eps: float = 1e-30):
+    n = _side(u_in.numel() // 5)
+    _chk(u_in, F32, 5 * n ** 3, "u_in")
+    out = torch.empty_like(u_in)
+    check(lib.sim_sweep(_ptr(u_in), _ptr(out), n, axis, nu, gamma, limiter_eps, _stream()), "sim_sweep")
+    return out
+
+
+def sweep_adjoint(u_in, lam_out, axis: int, nu: float, gamma: float = 5.0 / 3.0,
+                  limiter_eps: float = 1e-30):
+    n = _side(u_in.numel() // 5)
+    _chk(u_in, F32, 5 * n ** 3, "u_in")
+    _chk(lam_out, F32, 5 * n ** 3, "lam_out")
+    lam_in = torch.empty_like(u_in)
+    dnu = torch.zeros(1, dtype=F64, device=u_in.device)
+    check(lib.sim_sweep_adjoint(_ptr(u_in), _ptr(lam_out), _ptr(lam_in), n, axis, nu, gamma,
+                                limiter_eps, _ptr(dnu), _stream()), "sim_sweep_adjoint")
+    return lam_in, dnu
+
+
+def deposit_cic(s, n: int, box: float, values=None, grid=None):
+    _chk(s, F32, 3 * n ** 3, "s")
+    if grid is None:
+        grid = torch.zeros(n, n, n, dtype=F32, device=s.device)
+    check(lib.sim_deposit_cic(_ptr(s), _ptr(values), n, box, _ptr(grid), _stream()), "sim_deposit_cic")
+    return grid
+
+
+def interp_cic(grid, s, n: int, box: float):
+    nf = grid.numel() // n ** 3
+    _chk(s, F32, 3 * n ** 3, "s")
+    out = torch.empty(nf, n ** 3, dtype=F32, device=s.device)
+    check(lib.sim_interp_cic(_ptr(grid), nf, n, box, _ptr(s), _ptr(out), _stream()), "sim_interp_cic")
+    return out
+
+
+def gravity(delta, box: float, pref: float):
+    n = delta.shape[-1]
+    _chk(delta, F32, n ** 3, "delta")
+    g = torch.empty(3, n, n, n, dtype=F32, device=delta.device)
+    check(lib.sim_gravity(_ptr(delta), n, box, pref, _ptr(g), _stream()), "sim_gravity")
+    return g
+
+
+def gravity_adjoint(lam_g, box: float, pref: float):
+    n = lam_g.shape[-1]
+    _chk(lam_g, F32, 3 * n ** 3, "lam_g")
+    out = torch.empty(n, n, n, dtype=F32, device=lam_g.device)
+    check(lib.sim_gravity_adjoint(_ptr(lam_g), n, box, pref, _ptr(out), _stream()), "sim_gravity_adjoint")
+    return out
+
+
+def subgrid(gas, a: float, params: SimParams, step: int, with_outputs: bool = True):
+    """In-place subgrid update of gas [5, n, n, n]; returns (zhat, events)."""
+    n = gas.shape[-1]
+    _chk(gas, F32, 5 * n ** 3, "gas")
+    zhat = torch.empty(n, n, n, dtype=F32, device=gas.device) if with_outputs else None
+    events = torch.zeros((n ** 3 + 31) // 32, dtype=U32, device=gas.device) if with_outputs else None
+    check(lib.sim_subgrid(_ptr(gas), n, a, ctypes.byref(params), step, _ptr(zhat), _ptr(events),
+                          _stream()), "sim_subgrid")
+    return zhat, events
+
+
+def subgrid_adjoint(gas_in, lam, a: float, params: SimParams, step: int):
+    """lam [5, n, n, n] is overwritten; returns (dparams[NPARAMS], dfb[1])."""
+    n = gas_in.shape[-1]
+    dpar = torch.zeros(NPARAMS, dtype=F64, device=gas_in.device)
+    dfb = torch.zeros(1, dtype=F64, device=gas_in.device)
+    check(lib.sim_subgrid_adjoint(_ptr(gas_in), _ptr(lam), n, a, ctypes.byref(params), step,
+                                  _ptr(dpar), _ptr(dfb), _stream()), "sim_subgrid_adjoint")
+    return dpar, dfb
+
+
+def philox(seed: int, step: int, instance: int, tag: int, count: int, device="cuda"):
+    out = torch.empty(count, 4, dtype=U32, device=device)
+    check(lib.sim_philox(seed, step, instance, tag, count, _ptr(out), _stream()), "sim_philox")
+    return out
+
+
+def power_spectrum(a, box: float, nbins: int, b=None):
+    n = a.shape[-1]
+    k = torch.empty(nbins, dtype=F64, device=a.device)
+    pk = torch.empty_like(k)
+    nm = torch.empty_like(k)
+    check(lib.sim_power_spectrum(_ptr(a), _ptr(b), n, box, nbins, _ptr(k), _ptr(pk), _ptr(nm),
+                                 _stream()), "sim_power_spectrum")
+    return k, pk, nm
+
+
+# ------------------------------------------------------------------ whole path
+class Simulation:
+    """Owns a sim_t handle. All methods enqueue on torch's current stream at creation."""
+
+    def __init__(self, params: SimParams | None = None, noise=None, **overrides):
+        self.params = params if params is not None else default_params(**overrides)
+        if params is not None:
+            for k, v in overrides.items():
+                setattr(self.params, k, v)
+        n = self.params.n
+        self.n = n
+        if noise is not None:
+            _chk(noise, F32, n ** 3, "noise")
+        self._stream = torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib.sim_init(ctypes.byref(self.params), _ptr(noise),
+                           ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h)), "sim_init")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, where):
+        check(st, where, self.h)
+
+    def step(self):
+        self._check(lib.sim_step(self.h), "sim_step")
+
+    def step_adjoint(self, adj_gas, adj_part, adj_params=None):
+        n = self.n
+        _chk(adj_gas, F32, 5 * n ** 3, "adj_gas")
+        _chk(adj_part, F32, 6 * n ** 3, "adj_part")
+        self._check(lib.sim_step_adjoint(self.h, _ptr(adj_gas), _ptr(adj_part), _ptr(adj_params)),
+                    "sim_step_adjoint")
+
+    def run(self, n_steps: int | None = None):
+        self._check(lib.sim_run(self.h, self.params.n_steps if n_steps is None else n_steps), "sim_run")
+
+    def run_adjoint(self, dL_dgas=None, dL_dpart=None, want_noise: bool = True):
+        n = self.n
+        dev = torch.device("cuda", torch.cuda.current_device())
+        dnoise = torch.empty(n, n, n, dtype=F32, device=dev) if want_noise else None
+        dpar = torch.zeros(NPARAMS, dtype=F64, device=dev)
+        self._check(lib.sim_run_adjoint(self.h, _ptr(dL_dgas), _ptr(dL_dpart), _ptr(dnoise), _ptr(dpar)),
+                    "sim_run_adjoint")
+        return dnoise, dpar
+
+    def reset(self):
+        self._check(lib.sim_reset(self.h), "sim_reset")
+
+    def reinit(self, noise=None):
+        if noise is not None:
+            _chk(noise, F32, self.n ** 3, "noise")
+        self._check(lib.sim_reinit(self.h, _ptr(noise)), "sim_reinit")
+
+    def loss_density(self, target, c: float, out=None, loss=None):
+        """(dL/dgas [5, n, n, n], loss [1] float64) of L = c sum (rho - target)^2."""
+        n = self.n
+        _chk(target, F32, n ** 3, "target")
+        dev = target.device
+        out = torch.empty(5, n, n, n, dtype=F32, device=dev) if out is None else out
+        loss = torch.empty(1, dtype=F64, device=dev) if loss is None else loss
+        self._check(lib.sim_loss_density(self.h, _ptr(target), c, _ptr(out), _ptr(loss)),
+                    "sim_loss_density")
+        return out, loss
+
+    def state(self, gravity: bool = False):
+        n = self.n
+        dev = torch.device("cuda", torch.cuda.current_device())
+        gas = torch.empty(5, n, n, n, dtype=F32, device=dev)
+        part = torch.empty(6, n ** 3, dtype=F32, device=dev)
+        star = torch.empty(n, n, n, dtype=F32, device=dev)
+        aux = torch.empty(n ** 3, dtype=F32, device=dev)
+        events = torch.empty((n ** 3 + 31) // 32, dtype=U32, device=dev)
+        g = torch.empty(3, n, n, n, dtype=F32, device=dev) if gravity else None
+        step = ctypes.c_int32()
+        self._check(lib.sim_get_state(self.h, _ptr(gas), _ptr(part), _ptr(star), _ptr(aux),
+                                      _ptr(events), _ptr(g), ctypes.byref(step)), "sim_get_state")
+        out = {"gas": gas, "s": part[:3], "p": part[3:], "star": star, "aux": aux,
+               "events": events, "step": step.value}
+        if gravity:
+            out["g"] = g
+        return out
+
+    def set_state(self, gas, part, step: int):
+        n = self.n
+        _chk(gas, F32, 5 * n ** 3, "gas")
+        _chk(part, F32, 6 * n ** 3, "part")
+        self._check(lib.sim_set_state(self.h, _ptr(gas), _ptr(part), step), "sim_set_state")
+
+    def schedule(self, i: int):
+        out = (ctypes.c_double * 6)()
+        check(lib.sim_schedule(self.h, i, out), "sim_schedule", self.h)
+        return dict(zip(("a0", "a1", "K1", "dtau", "K2", "pref1"), list(out)))
+
+    def cfl(self) -> float:
+        c = ctypes.c_double()
+        self._check(lib.sim_cfl(self.h, ctypes.byref(c)), "sim_cfl")
+        return c.value
+
+
+class SimRunFunction(torch.autograd.Function):
+    """Final gas state [5, n, n, n] of a full run as a differentiable function of the white
+    noise [n, n, n] and the parameter vector [NPARAMS] (omega_m, sigma8, delta_c, Pi0, E0,
+    T0_uv, gamma_uv). Backward calls sim_run_adjoint (checkpointed recomputation)."""
+
+    @staticmethod
+    def forward(ctx, noise, pvec, params: SimParams):
+        p = SimParams.from_buffer_copy(params)
+        vals = pvec.detach().double().cpu().tolist()
+        for name, v in zip(("omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"), vals):
+            setattr(p, name, v)
+        sim = Simulation(p, noise.detach().float().contiguous())
+        sim.run()
+        st = sim.state()
+        ctx.sim = sim
+        return st["gas"]
+
+    @staticmethod
+    def backward(ctx, g_gas):
+        sim = ctx.sim
+        dnoise, dpar = sim.run_adjoint(g_gas.detach().float().contiguous(), None,
+                                       want_noise=ctx.needs_input_grad[0])
+        sim.close()
+        ctx.sim = None
+        return dnoise, dpar.to(torch.float64), None
+
+
+def simulate(noise, pvec, params: SimParams):
+    return SimRunFunction.apply(noise, pvec, params)

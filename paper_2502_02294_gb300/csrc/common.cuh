@@ -1,0 +1,200 @@
+// Shared device helpers for the diffHydro GB300 library: error plumbing, the Philox
+// counter-based generator, and the per-cell relaxing-TVD flux split and its adjoint.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "diffhydro.h"
+
+namespace dh {
+
+// ------------------------------------------------------------------ error plumbing
+// The last error message of the calling host thread (calls without a handle) is kept in a
+// thread-local buffer; handle calls also copy it into the handle.
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+#define DH_CUDA_TRY(expr)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (expr);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      ::dh::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, \
+                      __LINE__);                                                       \
+      return SIM_ECUDA;                                                                \
+    }                                                                                  \
+  } while (0)
+
+// Every kernel launch of the library is followed by DH_LAUNCH_CHECK, which also counts it
+// (sim_kernel_launches() reports the process-wide total).
+void count_launch();
+#define DH_LAUNCH_CHECK()            \
+  do {                               \
+    ::dh::count_launch();            \
+    DH_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+#define DH_TRY(expr)                    \
+  do {                                  \
+    sim_status _s = (expr);             \
+    if (_s != SIM_OK) return _s;        \
+  } while (0)
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon et al. (SC'11): 10 rounds of two 32x32->64 multiplies whose halves are mixed
+// with the other counter words and the key; Weyl key bumps between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// u = ((x >> 9) + 0.5) * 2^-23: an odd multiple of 2^-24 in (0,1), exact in float.
+__device__ __forceinline__ float uniform_from_word(uint32_t x) {
+  return (__uint2float_rn(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+enum { TAG_IC_NOISE = 0, TAG_SUBGRID = 1 };
+
+// ------------------------------------------------------------------ relaxing TVD cell
+// Flux split of one cell for a sweep whose momentum component is u[f] (f = 1 + axis):
+//   v = m_f / rho, P = (gamma-1)(eps - |m|^2/(2 rho)), c = |v| + sqrt(max(gamma P/rho, 0))
+//   F = (m_f, m_x v, m_y v, m_z v, (eps+P) v) + P e_f,  F^R = (cU + F)/2, F^L = (cU - F)/2.
+__device__ __forceinline__ void split_flux(const float u[5], int f, float gam, float FR[5],
+                                           float FL[5]) {
+  const float inv = 1.0f / u[0];
+  const float md = u[f];
+  const float v = md * inv;
+  const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  const float P = (gam - 1.0f) * (u[4] - 0.5f * m2 * inv);
+  const float cs2 = gam * P * inv;
+  const float c = fabsf(v) + (cs2 > 0.0f ? sqrtf(cs2) : 0.0f);
+  float F[5];
+  F[0] = md;
+  F[1] = u[1] * v;
+  F[2] = u[2] * v;
+  F[3] = u[3] * v;
+  F[f] += P;
+  F[4] = (u[4] + P) * v;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float cu = c * u[k];
+    FR[k] = 0.5f * (cu + F[k]);
+    FL[k] = 0.5f * (cu - F[k]);
+  }
+}
+
+// Vector-Jacobian product of split_flux: lu += (dF^R/dU)^T lR + (dF^L/dU)^T lL.
+// Conventions at kinks match the oracle: d|v|/dv = 0 at v = 0, dc_s = 0 where c_s = 0.
+__device__ __forceinline__ void split_flux_vjp(const float u[5], int f, float gam,
+                                               const float lR[5], const float lL[5],
+                                               float lu[5]) {
+  const float rho = u[0];
+  const float inv = 1.0f / rho;
+  const float md = u[f];
+  const float v = md * inv;
+  const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  const float P = (gam - 1.0f) * (u[4] - 0.5f * m2 * inv);
+  const float cs2 = gam * P * inv;
+  const float cs = cs2 > 0.0f ? sqrtf(cs2) : 0.0f;
+  const float c = fabsf(v) + cs;
+  float sig[5], del[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    sig[k] = 0.5f * (lR[k] + lL[k]);
+    del[k] = 0.5f * (lR[k] - lL[k]);
+  }
+  // c U term
+  float lc = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    lu[k] += c * sig[k];
+    lc += sig[k] * u[k];
+  }
+  // flux term with del
+  float lv = 0.0f, lP = del[f], lrho = 0.0f;
+  lu[f] += del[0];  // F0 = m_f
+#pragma unroll
+  for (int k = 1; k <= 3; ++k) {  // F_k = m_k v (+P)
+    lu[k] += del[k] * v;
+    lv += del[k] * u[k];
+  }
+  lu[4] += del[4] * v;  // F4 = (eps + P) v
+  lP += del[4] * v;
+  lv += del[4] * (u[4] + P);
+  // c = |v| + cs
+  lv += lc * (float)((v > 0.0f) - (v < 0.0f));
+  if (cs > 0.0f) {
+    lP += lc * gam / (2.0f * cs * rho);
+    lrho -= lc * cs / (2.0f * rho);
+  }
+  // P = (gam-1)(eps - m2/(2 rho))
+  const float gP = (gam - 1.0f) * lP;
+  lu[4] += gP;
+#pragma unroll
+  for (int k = 1; k <= 3; ++k) lu[k] -= gP * u[k] * inv;
+  lrho += gP * 0.5f * m2 * inv * inv;
+  // v = m_f / rho
+  lu[f] += lv * inv;
+  lrho -= lv * v * inv;
+  lu[0] += lrho;
+}
+
+// Gated harmonic-mean (van Leer) limiter 2 max(ab,0) / (a + b + copysign(eps, a+b)).
+__device__ __forceinline__ float vanleer(float a, float b, float eps) {
+  const float ab = a * b;
+  const float s = a + b;
+  return ab > 0.0f ? 2.0f * ab / (s + copysignf(eps, s)) : 0.0f;
+}
+
+__device__ __forceinline__ void vanleer_grad(float a, float b, float eps, float& da,
+                                             float& db) {
+  const float ab = a * b;
+  if (ab > 0.0f) {
+    const float s = a + b;
+    const float D = s + copysignf(eps, s);
+    const float i2 = 1.0f / (D * D);
+    da = 2.0f * b * (D - a) * i2;
+    db = 2.0f * a * (D - b) * i2;
+  } else {
+    da = 0.0f;
+    db = 0.0f;
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one double per thread, added atomically to *out by thread 0.
+// Requires blockDim.x * blockDim.y a multiple of 32 and <= 1024.
+__device__ __forceinline__ void block_sum_atomic(double v, double* out) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nt = blockDim.x * blockDim.y;
+  v = warp_sum(v);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    double w = (tid < (nt >> 5)) ? red[tid] : 0.0;
+    w = warp_sum(w);
+    if (tid == 0 && w != 0.0) atomicAdd(out, w);
+  }
+}
+
+}  // namespace dh

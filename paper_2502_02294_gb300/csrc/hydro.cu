@@ -1,0 +1,380 @@
+// Relaxing TVD sweep (Sec. 2.3.1-2.3.2 of arXiv 2502.02294) and its adjoint.
+//
+// One CTA owns a tile of S output cells along the sweep axis times W lines. It stages the
+// tile plus a halo (3 cells per side forward, 5 adjoint) of the 5 gas fields in shared
+// memory, and computes both RK2 stages there, so each global cell is read once per tile
+// and written once. For the y and z sweeps the W lines are W consecutive x cells (128-byte
+// coalesced rows); for the x sweep the lines are W consecutive y rows, each read as a
+// contiguous segment.
+//
+//   half step  (Eq. TVD_halfstep):  Uh_i = U_i - nu/2 (F_{i+1/2} - F_{i-1/2}),
+//              F_{i+1/2} = F^R_i - F^L_{i+1}  (first-order upwind of the relaxed fluxes)
+//   full step  (Eq. TVD_fullstep):  U'_i = U_i - nu (F2_{i+1/2} - F2_{i-1/2}),
+//              F2_{i+1/2} = [Fh^R_i + phi(dL, dR)] - [Fh^L_{i+1} - phi(dL', dR')]
+//              with the gated van Leer limiter phi and half differences of Fh^R / Fh^L.
+#include "common.cuh"
+
+namespace dh {
+
+// global offset of (sweep coordinate sg, line coordinate wg, third coordinate t)
+template <int AXIS>
+__device__ __forceinline__ long long goff(int sg, int wg, int t, int n) {
+  if (AXIS == 0) return ((long long)t * n + wg) * n + sg;  // x sweep: lines are y rows
+  if (AXIS == 1) return ((long long)t * n + sg) * n + wg;  // y sweep: lines are x cells
+  return ((long long)sg * n + t) * n + wg;                 // z sweep: lines are x cells
+}
+
+template <int AXIS, int S, int W, int H>
+struct TileGeom {
+  static constexpr int SP = S + 2 * H;  // cells along the sweep including the halo
+  static constexpr int NC = SP * W;
+  static constexpr int DS = (AXIS == 0) ? 1 : W;  // shared-memory stride along the sweep
+  __device__ static __forceinline__ int s_of(int c) { return AXIS == 0 ? c % SP : c / W; }
+  __device__ static __forceinline__ int w_of(int c) { return AXIS == 0 ? c / SP : c % W; }
+};
+
+// tile shapes: x sweep 64 x 4 lines, y/z sweeps 16 x 32 lines
+template <int AXIS> struct SweepCfg;
+template <> struct SweepCfg<0> { static constexpr int S = 64, W = 4, NT = 128; };
+template <> struct SweepCfg<1> { static constexpr int S = 16, W = 32, NT = 256; };
+template <> struct SweepCfg<2> { static constexpr int S = 16, W = 32, NT = 256; };
+
+template <int AXIS>
+__global__ void __launch_bounds__(SweepCfg<AXIS>::NT)
+sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, float nu,
+                 float gam, float eps) {
+  constexpr int S = SweepCfg<AXIS>::S, W = SweepCfg<AXIS>::W, NT = SweepCfg<AXIS>::NT;
+  using G = TileGeom<AXIS, S, W, 3>;
+  constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
+  constexpr int F = 1 + AXIS;
+  extern __shared__ float sf[];  // 10 NC: F^R, F^L of U, then of Uh (U stays in registers)
+  const long long N3 = (long long)n * n * n;
+  const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z;
+
+  float ureg[CPT][5];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    if (c < NC) {
+      const int s = G::s_of(c), w = G::w_of(c), wg = w0 + w;
+      int sg = (s0 + s - 3) % n;
+      if (sg < 0) sg += n;
+      float u[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
+      if (wg < n) {
+        const long long o = goff<AXIS>(sg, wg, t, n);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) u[k] = __ldg(uin + k * N3 + o);
+      }
+      float FR[5], FL[5];
+      split_flux(u, F, gam, FR, FL);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        ureg[i][k] = u[k];
+        sf[k * NC + c] = FR[k];
+        sf[(5 + k) * NC + c] = FL[k];
+      }
+    }
+  }
+  __syncthreads();
+  float uh[CPT][5];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c);
+    if (c < NC && s >= 1 && s < SP - 1) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const float fp = sf[k * NC + c] - sf[(5 + k) * NC + c + DS];
+        const float fm = sf[k * NC + c - DS] - sf[(5 + k) * NC + c];
+        uh[i][k] = ureg[i][k] - 0.5f * nu * (fp - fm);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c);
+    if (c < NC && s >= 1 && s < SP - 1) {
+      float FR[5], FL[5];
+      split_flux(uh[i], F, gam, FR, FL);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        sf[k * NC + c] = FR[k];
+        sf[(5 + k) * NC + c] = FL[k];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c), w = G::w_of(c);
+    const int sg = s0 + s - 3, wg = w0 + w;
+    if (c < NC && s >= 3 && s < S + 3 && sg < n && wg < n) {
+      const long long o = goff<AXIS>(sg, wg, t, n);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const float* R = sf + k * NC + c;
+        const float* L = sf + (5 + k) * NC + c;
+        const float Rm2 = R[-2 * DS], Rm1 = R[-DS], R0 = R[0], Rp1 = R[DS];
+        const float Lm1 = L[-DS], L0 = L[0], Lp1 = L[DS], Lp2 = L[2 * DS];
+        const float frp = R0 + vanleer(0.5f * (R0 - Rm1), 0.5f * (Rp1 - R0), eps);
+        const float flp = Lp1 - vanleer(0.5f * (Lp1 - L0), 0.5f * (Lp2 - Lp1), eps);
+        const float frm = Rm1 + vanleer(0.5f * (Rm1 - Rm2), 0.5f * (R0 - Rm1), eps);
+        const float flm = L0 - vanleer(0.5f * (L0 - Lm1), 0.5f * (Lp1 - L0), eps);
+        uout[k * N3 + o] = ureg[i][k] - nu * ((frp - flp) - (frm - flm));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------- adjoint
+// lam_in_k = lam_out_k + lamUh_k + VJP_{F^R,F^L}(U_k; lamF^R_k, lamF^L_k), with
+// lamF^R_k = nu/2 (lamUh_{k+1} - lamUh_k), lamF^L_k = -nu/2 (lamUh_k - lamUh_{k-1}), and
+// lamUh_j = VJP_{F^R,F^L}(Uh_j; lamFh^R_j, lamFh^L_j) gathered from the limited faces
+// t+1/2 (t = j-2 .. j+1) whose adjoint is nu (lam_out_{t+1} - lam_out_t). Output cells need
+// U on a 5-cell halo and lam_out on a 3-cell halo; the forward stages are recomputed.
+template <int AXIS>
+__global__ void __launch_bounds__(SweepCfg<AXIS>::NT)
+sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
+                 float* __restrict__ lin, int n, float nu, float gam, float eps,
+                 double* __restrict__ dnu) {
+  constexpr int S = SweepCfg<AXIS>::S, W = SweepCfg<AXIS>::W, NT = SweepCfg<AXIS>::NT;
+  using G = TileGeom<AXIS, S, W, 5>;
+  constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
+  constexpr int F = 1 + AXIS;
+  extern __shared__ float sm[];
+  float* su = sm;            // 5 NC: Uh, then lamUh
+  float* sf = sm + 5 * NC;   // 10 NC: F^R,F^L of U, then of Uh
+  float* sl = sm + 15 * NC;  // 5 NC: lam_out
+  const long long N3 = (long long)n * n * n;
+  const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z;
+
+  float ureg[CPT][5];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    if (c < NC) {
+      const int s = G::s_of(c), w = G::w_of(c), wg = w0 + w;
+      int sg = (s0 + s - 5) % n;
+      if (sg < 0) sg += n;
+      float u[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
+      float l[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      if (wg < n) {
+        const long long o = goff<AXIS>(sg, wg, t, n);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) u[k] = __ldg(uin + k * N3 + o);
+        if (s >= 2 && s < SP - 2) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) l[k] = __ldg(lout + k * N3 + o);
+        }
+      }
+      float FR[5], FL[5];
+      split_flux(u, F, gam, FR, FL);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        ureg[i][k] = u[k];
+        sf[k * NC + c] = FR[k];
+        sf[(5 + k) * NC + c] = FL[k];
+        sl[k * NC + c] = l[k];
+      }
+    }
+  }
+  __syncthreads();
+  float uh[CPT][5], df1[CPT][5];
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c);
+    if (c < NC && s >= 1 && s < SP - 1) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const float fp = sf[k * NC + c] - sf[(5 + k) * NC + c + DS];
+        const float fm = sf[k * NC + c - DS] - sf[(5 + k) * NC + c];
+        df1[i][k] = fp - fm;
+        uh[i][k] = ureg[i][k] - 0.5f * nu * df1[i][k];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c);
+    if (c < NC && s >= 1 && s < SP - 1) {
+      float FR[5], FL[5];
+      split_flux(uh[i], F, gam, FR, FL);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        su[k * NC + c] = uh[i][k];
+        sf[k * NC + c] = FR[k];
+        sf[(5 + k) * NC + c] = FL[k];
+      }
+    }
+  }
+  __syncthreads();
+  double dnu_acc = 0.0;
+  // stage E: lamUh_j for j in [4, S+6)
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c), w = G::w_of(c);
+    if (c < NC && s >= 4 && s < S + 6) {
+      float lR[5], lL[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const float* R = sf + k * NC + c;
+        const float* L = sf + (5 + k) * NC + c;
+        const float* lo = sl + k * NC + c;
+        // face adjoints lam_f(t) = nu (lam_out_{t+1} - lam_out_t), t = j-2 .. j+1
+        const float lf_m2 = nu * (lo[-DS] - lo[-2 * DS]);
+        const float lf_m1 = nu * (lo[0] - lo[-DS]);
+        const float lf_0 = nu * (lo[DS] - lo[0]);
+        const float lf_p1 = nu * (lo[2 * DS] - lo[DS]);
+        float da, db;
+        // right-moving: faces t = j-1, j, j+1
+        float acc;
+        vanleer_grad(0.5f * (R[0] - R[-DS]), 0.5f * (R[DS] - R[0]), eps, da, db);
+        acc = lf_0 * (1.0f + 0.5f * da - 0.5f * db);
+        vanleer_grad(0.5f * (R[DS] - R[0]), 0.5f * (R[2 * DS] - R[DS]), eps, da, db);
+        acc -= 0.5f * da * lf_p1;
+        vanleer_grad(0.5f * (R[-DS] - R[-2 * DS]), 0.5f * (R[0] - R[-DS]), eps, da, db);
+        acc += 0.5f * db * lf_m1;
+        lR[k] = acc;
+        // left-moving: F^L face t = L_{t+1} - phi(0.5(L_{t+1}-L_t), 0.5(L_{t+2}-L_{t+1}))
+        vanleer_grad(0.5f * (L[0] - L[-DS]), 0.5f * (L[DS] - L[0]), eps, da, db);  // t=j-1
+        acc = -lf_m1 * (1.0f - 0.5f * da + 0.5f * db);
+        vanleer_grad(0.5f * (L[DS] - L[0]), 0.5f * (L[2 * DS] - L[DS]), eps, da, db);  // t=j
+        acc -= lf_0 * 0.5f * da;
+        vanleer_grad(0.5f * (L[-DS] - L[-2 * DS]), 0.5f * (L[0] - L[-DS]), eps, da, db);  // t=j-2
+        acc += 0.5f * db * lf_m2;
+        lL[k] = acc;
+      }
+      float luh[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      split_flux_vjp(uh[i], F, gam, lR, lL, luh);
+      const int sg = s0 + s - 5, wg = w0 + w;
+      if (s >= 5 && s < S + 5 && sg < n && wg < n) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dnu_acc -= 0.5 * (double)luh[k] * (double)df1[i][k];
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) su[k * NC + c] = luh[k];
+    }
+  }
+  __syncthreads();
+  // stage F: outputs s in [5, S+5)
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c), w = G::w_of(c);
+    const int sg = s0 + s - 5, wg = w0 + w;
+    if (c < NC && s >= 5 && s < S + 5 && sg < n && wg < n) {
+      float lR[5], lL[5], lu[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const float* lh = su + k * NC + c;
+        lR[k] = 0.5f * nu * (lh[DS] - lh[0]);
+        lL[k] = -0.5f * nu * (lh[0] - lh[-DS]);
+        lu[k] = sl[k * NC + c] + lh[0];
+        // d u_out / d nu = -(F2_{+} - F2_{-})
+        const float* R = sf + k * NC + c;
+        const float* L = sf + (5 + k) * NC + c;
+        const float Rm2 = R[-2 * DS], Rm1 = R[-DS], R0 = R[0], Rp1 = R[DS];
+        const float Lm1 = L[-DS], L0 = L[0], Lp1 = L[DS], Lp2 = L[2 * DS];
+        const float frp = R0 + vanleer(0.5f * (R0 - Rm1), 0.5f * (Rp1 - R0), eps);
+        const float flp = Lp1 - vanleer(0.5f * (Lp1 - L0), 0.5f * (Lp2 - Lp1), eps);
+        const float frm = Rm1 + vanleer(0.5f * (Rm1 - Rm2), 0.5f * (R0 - Rm1), eps);
+        const float flm = L0 - vanleer(0.5f * (L0 - Lm1), 0.5f * (Lp1 - L0), eps);
+        dnu_acc -= (double)sl[k * NC + c] * (double)((frp - flp) - (frm - flm));
+      }
+      split_flux_vjp(ureg[i], F, gam, lR, lL, lu);
+      const long long o = goff<AXIS>(sg, wg, t, n);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) lin[k * N3 + o] = lu[k];
+    }
+  }
+  if (dnu) block_sum_atomic(dnu_acc, dnu);
+}
+
+template <int AXIS>
+static sim_status launch_sweep_t(const float* uin, float* uout, int n, float nu, float gam,
+                                 float eps, cudaStream_t st) {
+  using C = SweepCfg<AXIS>;
+  constexpr int NC = (C::S + 6) * C::W;
+  const size_t smem = 10 * NC * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(sweep_fwd_kernel<AXIS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n);
+  sweep_fwd_kernel<AXIS><<<grid, C::NT, smem, st>>>(uin, uout, n, nu, gam, eps);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+template <int AXIS>
+static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float* lin, int n,
+                                     float nu, float gam, float eps, double* dnu,
+                                     cudaStream_t st) {
+  using C = SweepCfg<AXIS>;
+  constexpr int NC = (C::S + 10) * C::W;
+  const size_t smem = 20 * NC * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(sweep_adj_kernel<AXIS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n);
+  sweep_adj_kernel<AXIS><<<grid, C::NT, smem, st>>>(uin, lout, lin, n, nu, gam, eps, dnu);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double nu,
+                        double gam, double eps, cudaStream_t st) {
+  switch (axis) {
+    case 0: return launch_sweep_t<0>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
+    case 1: return launch_sweep_t<1>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
+    case 2: return launch_sweep_t<2>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
+  }
+  set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
+  return SIM_EINVAL;
+}
+
+sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
+                                int n, double nu, double gam, double eps, double* dnu,
+                                cudaStream_t st) {
+  switch (axis) {
+    case 0: return launch_sweep_adj_t<0>(uin, lout, lin, n, (float)nu, (float)gam, (float)eps, dnu, st);
+    case 1: return launch_sweep_adj_t<1>(uin, lout, lin, n, (float)nu, (float)gam, (float)eps, dnu, st);
+    case 2: return launch_sweep_adj_t<2>(uin, lout, lin, n, (float)nu, (float)gam, (float)eps, dnu, st);
+  }
+  set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
+  return SIM_EINVAL;
+}
+
+}  // namespace dh
+
+extern "C" sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int32_t axis,
+                                double nu, double gamma, double limiter_eps, void* stream) {
+  if (!u_in || !u_out || n < 1 || u_in == u_out) {
+    dh::set_error("sim_sweep: null/aliased buffers or n < 1");
+    return SIM_EINVAL;
+  }
+  return dh::launch_sweep(axis, u_in, u_out, n, nu, gamma, limiter_eps, (cudaStream_t)stream);
+}
+
+extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out, float* lam_in,
+                                        int32_t n, int32_t axis, double nu, double gamma,
+                                        double limiter_eps, double* dnu, void* stream) {
+  if (!u_in || !lam_out || !lam_in || n < 1 || lam_in == lam_out || lam_in == u_in) {
+    dh::set_error("sim_sweep_adjoint: null/aliased buffers or n < 1");
+    return SIM_EINVAL;
+  }
+  return dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, nu, gamma, limiter_eps, dnu,
+                                  (cudaStream_t)stream);
+}

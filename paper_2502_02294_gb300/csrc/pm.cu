@@ -1,0 +1,646 @@
+// Particle-mesh gravity (Sec. 2.2 of arXiv 2502.02294): CIC deposit with deterministic
+// 64-bit fixed-point accumulation, spectral Poisson solve (cuFFT + a fused Green's
+// function / gradient kernel), CIC readout with kick and drift, and the adjoints.
+//
+// Cell decision: t = s * (n / box) in float32 with a single rounded multiply; the base node
+// is q + floor(t) (mod n) and the weight fraction f = t - floor(t) is exact in float32.
+#include <map>
+#include <mutex>
+
+#include "pm.cuh"
+
+namespace dh {
+
+// ------------------------------------------------------------------ FFT plans
+static sim_status make_plan(cufftHandle* h, int n, cufftType type, int batch) {
+  int dims[3] = {n, n, n};
+  int real_emb[3] = {n, n, n};
+  int cplx_emb[3] = {n, n, n / 2 + 1};
+  const long long nr = (long long)n * n * n, nc = (long long)n * n * (n / 2 + 1);
+  cufftResult r;
+  if (type == CUFFT_R2C)
+    r = cufftPlanMany(h, 3, dims, real_emb, 1, (int)nr, cplx_emb, 1, (int)nc, type, batch);
+  else
+    r = cufftPlanMany(h, 3, dims, cplx_emb, 1, (int)nc, real_emb, 1, (int)nr, type, batch);
+  if (r != CUFFT_SUCCESS) {
+    set_error("cufftPlanMany(n=%d, batch=%d) failed with code %d", n, batch, (int)r);
+    return r == CUFFT_ALLOC_FAILED ? SIM_ENOMEM : SIM_ECUDA;
+  }
+  return SIM_OK;
+}
+
+sim_status FFTPlans::create(int n_) {
+  n = n_;
+  DH_TRY(make_plan(&r2c1, n, CUFFT_R2C, 1));
+  DH_TRY(make_plan(&r2c3, n, CUFFT_R2C, 3));
+  DH_TRY(make_plan(&r2c4, n, CUFFT_R2C, 4));
+  DH_TRY(make_plan(&c2r1, n, CUFFT_C2R, 1));
+  DH_TRY(make_plan(&c2r3, n, CUFFT_C2R, 3));
+  DH_TRY(make_plan(&c2r4, n, CUFFT_C2R, 4));
+  return SIM_OK;
+}
+
+void FFTPlans::destroy() {
+  for (cufftHandle* h : {&r2c1, &r2c3, &r2c4, &c2r1, &c2r3, &c2r4})
+    if (*h) {
+      cufftDestroy(*h);
+      *h = 0;
+    }
+}
+
+sim_status FFTPlans::set_stream(cudaStream_t st) {
+  for (cufftHandle h : {r2c1, r2c3, r2c4, c2r1, c2r3, c2r4})
+    if (cufftSetStream(h, st) != CUFFT_SUCCESS) {
+      set_error("cufftSetStream failed");
+      return SIM_ECUDA;
+    }
+  return SIM_OK;
+}
+
+FFTPlans* shared_plans(int n) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, FFTPlans*> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, n});
+  if (it != cache.end()) return it->second;
+  FFTPlans* p = new FFTPlans();
+  if (p->create(n) != SIM_OK) {
+    p->destroy();
+    delete p;
+    return nullptr;
+  }
+  cache[{dev, n}] = p;
+  return p;
+}
+
+static sim_status fft_exec_r2c(cufftHandle h, const float* in, cufftComplex* out) {
+  cufftResult r = cufftExecR2C(h, const_cast<float*>(in), out);
+  if (r != CUFFT_SUCCESS) {
+    set_error("cufftExecR2C failed with code %d", (int)r);
+    return SIM_ECUDA;
+  }
+  return SIM_OK;
+}
+
+static sim_status fft_exec_c2r(cufftHandle h, cufftComplex* in, float* out) {
+  cufftResult r = cufftExecC2R(h, in, out);
+  if (r != CUFFT_SUCCESS) {
+    set_error("cufftExecC2R failed with code %d", (int)r);
+    return SIM_ECUDA;
+  }
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ CIC geometry
+struct Cic {
+  int ix[2], iy[2], iz[2];
+  float wx[2], wy[2], wz[2];
+};
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ void cic_axis(float s, int q, int n, float inv_dx, int* idx,
+                                         float* w) {
+  const float t = __fmul_rn(s, inv_dx);
+  const float fl = floorf(t);
+  const float f = t - fl;
+  const int b = wrap(q + (int)fl, n);
+  idx[0] = b;
+  idx[1] = (b + 1 == n) ? 0 : b + 1;
+  w[0] = 1.0f - f;
+  w[1] = f;
+}
+
+__device__ __forceinline__ void cic_setup(const float* s, long long p, long long N3, int n,
+                                          float inv_dx, Cic& c) {
+  const int qx = (int)(p % n), qy = (int)((p / n) % n), qz = (int)(p / ((long long)n * n));
+  cic_axis(s[p], qx, n, inv_dx, c.ix, c.wx);
+  cic_axis(s[N3 + p], qy, n, inv_dx, c.iy, c.wy);
+  cic_axis(s[2 * N3 + p], qz, n, inv_dx, c.iz, c.wz);
+}
+
+__device__ __forceinline__ long long node(const Cic& c, int oz, int oy, int ox, int n) {
+  return ((long long)c.iz[oz] * n + c.iy[oy]) * n + c.ix[ox];
+}
+
+// ------------------------------------------------------------------ deposit
+__global__ void deposit_kernel(const float* __restrict__ s, const float* __restrict__ vals,
+                               int n, float inv_dx, unsigned long long* __restrict__ acc) {
+  const long long N3 = (long long)n * n * n;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N3) return;
+  Cic c;
+  cic_setup(s, p, N3, n, inv_dx, c);
+  const float v = vals ? vals[p] : 1.0f;
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox) {
+        const float w = c.wz[oz] * c.wy[oy] * c.wx[ox] * v;
+        const long long fx = __float2ll_rn(w * kFix);
+        if (fx) atomicAdd(acc + node(c, oz, oy, ox, n), (unsigned long long)fx);
+      }
+}
+
+__global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, float scale,
+                                    const float* __restrict__ add, float offset,
+                                    float* __restrict__ out, long long N3) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N3) return;
+  const float cnt = __ll2float_rn((long long)acc[i]) * kInvFix;
+  acc[i] = 0ull;
+  out[i] = scale * cnt + (add ? add[i] : 0.0f) + offset;
+}
+
+sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
+                          unsigned long long* acc, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  deposit_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s, values, n, inv_dx, acc);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+sim_status launch_fix_to_float(unsigned long long* acc, float scale, const float* add,
+                               float offset, float* out, int n, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  fix_to_float_kernel<<<cdiv(N3, 256), 256, 0, st>>>(acc, scale, add, offset, out, N3);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ Green's function
+// half-complex index -> signed integer wavenumbers and Nyquist flags
+__device__ __forceinline__ void kindex(long long i, int n, int nh, int& kx, int& ky, int& kz,
+                                       bool& nx, bool& ny, bool& nz) {
+  kx = (int)(i % nh);
+  const long long r = i / nh;
+  ky = (int)(r % n);
+  kz = (int)(r / n);
+  const bool even = (n % 2 == 0);
+  nx = even && kx == n / 2;
+  ny = even && ky == n / 2;
+  nz = even && kz == n / 2;
+  if (ky > n / 2) ky -= n;
+  if (kz > n / 2) kz -= n;
+}
+
+// gk[j] = i kgrad_j (pref / k^2) dk / n^3   (j = x, y, z)
+__global__ void green_kernel(const cufftComplex* __restrict__ dk, cufftComplex* __restrict__ gk,
+                             int n, float kf, float pref_norm) {
+  const int nh = n / 2 + 1;
+  const long long NC = (long long)n * n * nh;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NC) return;
+  int kx, ky, kz;
+  bool nx, ny, nz;
+  kindex(i, n, nh, kx, ky, kz, nx, ny, nz);
+  const float fx = kf * kx, fy = kf * ky, fz = kf * kz;
+  const float k2 = fx * fx + fy * fy + fz * fz;
+  const float G = (k2 > 0.0f) ? pref_norm / k2 : 0.0f;
+  const cufftComplex d = dk[i];
+  const float gxs = nx ? 0.0f : fx * G, gys = ny ? 0.0f : fy * G, gzs = nz ? 0.0f : fz * G;
+  // i * c * (a + ib) = -c b + i c a
+  gk[i] = make_cuFloatComplex(-gxs * d.y, gxs * d.x);
+  gk[NC + i] = make_cuFloatComplex(-gys * d.y, gys * d.x);
+  gk[2 * NC + i] = make_cuFloatComplex(-gzs * d.y, gzs * d.x);
+}
+
+// Adjoint: Y = sum_j (-i kgrad_j)(pref / k^2) L_j / n^3 (the operator with the sign of the
+// gradient flipped; the Hermitian weights of the half spectrum cancel, see sim_gravity_adjoint)
+__global__ void green_adj_kernel(const cufftComplex* __restrict__ lk, cufftComplex* __restrict__ yk,
+                                 int n, float kf, float pref_norm) {
+  const int nh = n / 2 + 1;
+  const long long NC = (long long)n * n * nh;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NC) return;
+  int kx, ky, kz;
+  bool nx, ny, nz;
+  kindex(i, n, nh, kx, ky, kz, nx, ny, nz);
+  const float fx = kf * kx, fy = kf * ky, fz = kf * kz;
+  const float k2 = fx * fx + fy * fy + fz * fz;
+  const float G = (k2 > 0.0f) ? pref_norm / k2 : 0.0f;
+  const float cx = nx ? 0.0f : fx * G, cy = ny ? 0.0f : fy * G, cz = nz ? 0.0f : fz * G;
+  const cufftComplex a = lk[i], b = lk[NC + i], c = lk[2 * NC + i];
+  // -i c (re + i im) = c im - i c re
+  const float re = cx * a.y + cy * b.y + cz * c.y;
+  const float im = -(cx * a.x + cy * b.x + cz * c.x);
+  yk[i] = make_cuFloatComplex(re, im);
+}
+
+sim_status launch_gravity(const float* delta, float* g, cufftComplex* dk, cufftComplex* gk,
+                          int n, double box, double pref, FFTPlans& plans, cudaStream_t st) {
+  const long long NC = (long long)n * n * (n / 2 + 1);
+  DH_TRY(plans.set_stream(st));
+  DH_TRY(fft_exec_r2c(plans.r2c1, delta, dk));
+  const float kf = (float)(2.0 * M_PI / box);
+  const float pn = (float)(pref / ((double)n * n * n));
+  green_kernel<<<cdiv(NC, 256), 256, 0, st>>>(dk, gk, n, kf, pn);
+  DH_LAUNCH_CHECK();
+  DH_TRY(fft_exec_c2r(plans.c2r3, gk, g));
+  return SIM_OK;
+}
+
+sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftComplex* gk,
+                                  cufftComplex* dk, int n, double box, double pref,
+                                  FFTPlans& plans, cudaStream_t st) {
+  const long long NC = (long long)n * n * (n / 2 + 1);
+  DH_TRY(plans.set_stream(st));
+  DH_TRY(fft_exec_r2c(plans.r2c3, lam_g, gk));
+  const float kf = (float)(2.0 * M_PI / box);
+  const float pn = (float)(pref / ((double)n * n * n));
+  green_adj_kernel<<<cdiv(NC, 256), 256, 0, st>>>(gk, dk, n, kf, pn);
+  DH_LAUNCH_CHECK();
+  DH_TRY(fft_exec_c2r(plans.c2r1, dk, lam_delta));
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ readout, kick, drift
+__global__ void interp_kernel(const float* __restrict__ grid, int nf, int n, float inv_dx,
+                              const float* __restrict__ s, float* __restrict__ out) {
+  const long long N3 = (long long)n * n * n;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N3) return;
+  Cic c;
+  cic_setup(s, p, N3, n, inv_dx, c);
+  for (int f = 0; f < nf; ++f) {
+    const float* gf = grid + f * N3;
+    float acc = 0.0f;
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox)
+          acc += c.wz[oz] * c.wy[oy] * c.wx[ox] * __ldg(gf + node(c, oz, oy, ox, n));
+    out[f * N3 + p] = acc;
+  }
+}
+
+sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
+                         float* out, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  interp_kernel<<<cdiv(N3, 256), 256, 0, st>>>(grid, nf, n, inv_dx, s, out);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+__device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& c, int n,
+                                        long long N3, float out[3]) {
+  out[0] = out[1] = out[2] = 0.0f;
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox) {
+        const float w = c.wz[oz] * c.wy[oy] * c.wx[ox];
+        const long long o = node(c, oz, oy, ox, n);
+        out[0] += w * __ldg(g + o);
+        out[1] += w * __ldg(g + N3 + o);
+        out[2] += w * __ldg(g + 2 * N3 + o);
+      }
+}
+
+__global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
+                                  const float* __restrict__ g, float K, float dtau,
+                                  const float* __restrict__ zhat, float* __restrict__ aux,
+                                  int n, float inv_dx) {
+  const long long N3 = (long long)n * n * n;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N3) return;
+  Cic c;
+  cic_setup(s, i, N3, n, inv_dx, c);
+  float gi[3];
+  interp3(g, c, n, N3, gi);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float pj = p[j * N3 + i] + K * gi[j];
+    p[j * N3 + i] = pj;
+    if (dtau != 0.0f) s[j * N3 + i] += dtau * pj;
+  }
+  if (zhat) {
+    cic_setup(s, i, N3, n, inv_dx, c);
+    float acc = 0.0f;
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox)
+          acc += c.wz[oz] * c.wy[oy] * c.wx[ox] * __ldg(zhat + node(c, oz, oy, ox, n));
+    aux[i] += acc;
+  }
+}
+
+sim_status launch_kick_drift(float* s, float* p, const float* g, float K, float dtau,
+                             const float* zhat, float* aux, int n, float inv_dx,
+                             cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  kick_drift_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s, p, g, K, dtau, zhat, aux, n, inv_dx);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+__global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__ g, float K,
+                                long long N3) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N3) return;
+  const float rho = u[i];
+  float mg = 0.0f, g2 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float gj = g[j * N3 + i];
+    const float mj = u[(1 + j) * N3 + i];
+    mg += mj * gj;
+    g2 += gj * gj;
+    u[(1 + j) * N3 + i] = mj + rho * gj * K;
+  }
+  u[4 * N3 + i] += K * mg + 0.5f * K * K * rho * g2;
+}
+
+sim_status launch_gas_kick(float* gas, const float* g, float K, int n, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  gas_kick_kernel<<<cdiv(N3, 256), 256, 0, st>>>(gas, g, K, N3);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ adjoints
+__global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __restrict__ g,
+                                    float K, float* __restrict__ lam, float* __restrict__ lam_g,
+                                    double* __restrict__ dK, long long N3) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double dk = 0.0;
+  if (i < N3) {
+    const float rho = u[i];
+    const float le = lam[4 * N3 + i];
+    float lrho = lam[i];
+    float mg = 0.0f, g2 = 0.0f;
+    float m[3], gg[3], lm[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      gg[j] = g[j * N3 + i];
+      m[j] = u[(1 + j) * N3 + i];
+      lm[j] = lam[(1 + j) * N3 + i];
+      mg += m[j] * gg[j];
+      g2 += gg[j] * gg[j];
+    }
+    float dkf = le * (mg + K * rho * g2);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lrho += K * lm[j] * gg[j];
+      dkf += lm[j] * rho * gg[j];
+      lam_g[j * N3 + i] += lm[j] * rho * K + le * (K * m[j] + K * K * rho * gg[j]);
+      lam[(1 + j) * N3 + i] = lm[j] + le * K * gg[j];
+    }
+    lrho += 0.5f * K * K * g2 * le;
+    lam[i] = lrho;
+    dk = (double)dkf;
+  }
+  if (dK) block_sum_atomic(dk, dK);
+}
+
+sim_status launch_gas_kick_adjoint(const float* gas, const float* g, float K, float* lam,
+                                   float* lam_g, double* dK, int n, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  gas_kick_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(gas, g, K, lam, lam_g, dK, N3);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+__global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0,
+                                      const float* __restrict__ g, float K, float dtau,
+                                      float* __restrict__ lam_s, float* __restrict__ lam_p,
+                                      float* __restrict__ lam_g, double* __restrict__ dK,
+                                      double* __restrict__ ddtau, int n, float inv_dx) {
+  const long long N3 = (long long)n * n * n;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double dk = 0.0, dd = 0.0;
+  if (i < N3) {
+    Cic c;
+    cic_setup(s0, i, N3, n, inv_dx, c);
+    float gi[3];
+    interp3(g, c, n, N3, gi);
+    float lp[3], ls[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      ls[j] = lam_s[j * N3 + i];
+      if (p0) {
+        const float p1 = p0[j * N3 + i] + K * gi[j];
+        dd += (double)ls[j] * (double)p1;
+      }
+      lp[j] = lam_p[j * N3 + i] + dtau * ls[j];
+      dk += (double)lp[j] * (double)gi[j];
+    }
+    // lam_s0 += K d/ds (sum_j lp_j interp(g_j)) ; lam_g += interp^T(K lp)
+    float gs[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+          const long long o = node(c, oz, oy, ox, n);
+          const float w = c.wz[oz] * c.wy[oy] * c.wx[ox];
+          const float dwx = (ox ? inv_dx : -inv_dx) * c.wy[oy] * c.wz[oz];
+          const float dwy = (oy ? inv_dx : -inv_dx) * c.wx[ox] * c.wz[oz];
+          const float dwz = (oz ? inv_dx : -inv_dx) * c.wx[ox] * c.wy[oy];
+          float lg = 0.0f;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const float gv = __ldg(g + j * N3 + o);
+            lg += lp[j] * gv;
+            atomicAdd(lam_g + j * N3 + o, K * lp[j] * w);
+          }
+          gs[0] += dwx * lg;
+          gs[1] += dwy * lg;
+          gs[2] += dwz * lg;
+        }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lam_s[j * N3 + i] = ls[j] + K * gs[j];
+      lam_p[j * N3 + i] = lp[j];
+    }
+  }
+  if (dK) block_sum_atomic(dk, dK);
+  if (ddtau) block_sum_atomic(dd, ddtau);
+}
+
+sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, float K,
+                                     float dtau, float* lam_s, float* lam_p, float* lam_g,
+                                     double* dK, double* ddtau, int n, float inv_dx,
+                                     cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  kick_drift_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s0, p0, g, K, dtau, lam_s, lam_p, lam_g,
+                                                        dK, ddtau, n, inv_dx);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+__global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __restrict__ ld,
+                                   float cm, float* __restrict__ lam_s, double* __restrict__ dcm,
+                                   int n, float inv_dx) {
+  const long long N3 = (long long)n * n * n;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (i < N3) {
+    Cic c;
+    cic_setup(s, i, N3, n, inv_dx, c);
+    float gs[3] = {0.0f, 0.0f, 0.0f};
+    float itp = 0.0f;
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox) {
+          const float v = __ldg(ld + node(c, oz, oy, ox, n));
+          itp += c.wz[oz] * c.wy[oy] * c.wx[ox] * v;
+          gs[0] += (ox ? inv_dx : -inv_dx) * c.wy[oy] * c.wz[oz] * v;
+          gs[1] += (oy ? inv_dx : -inv_dx) * c.wx[ox] * c.wz[oz] * v;
+          gs[2] += (oz ? inv_dx : -inv_dx) * c.wx[ox] * c.wy[oy] * v;
+        }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lam_s[j * N3 + i] += cm * gs[j];
+    acc = (double)itp;
+  }
+  if (dcm) block_sum_atomic(acc, dcm);
+}
+
+sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, float cm,
+                                  float* lam_s, double* dcm, int n, float inv_dx,
+                                  cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  deposit_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s, lam_delta, cm, lam_s, dcm, n, inv_dx);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+__global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                           long long count, double* __restrict__ out) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    acc += (double)a[i] * (double)b[i];
+  block_sum_atomic(acc, out);
+}
+
+sim_status launch_dot(const float* a, const float* b, long long count, double* out,
+                      cudaStream_t st) {
+  int blocks = cdiv(count, 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  dot_kernel<<<blocks, 256, 0, st>>>(a, b, count, out);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+__global__ void axpy_kernel(float alpha, const float* __restrict__ x, float* __restrict__ y,
+                            long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) y[i] += alpha * x[i];
+}
+
+sim_status launch_axpy(float alpha, const float* x, float* y, long long count, cudaStream_t st) {
+  axpy_kernel<<<cdiv(count, 256), 256, 0, st>>>(alpha, x, y, count);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+__global__ void density_loss_kernel(const float* __restrict__ rho, const float* __restrict__ t,
+                                    float c, float* __restrict__ grad, double* __restrict__ loss,
+                                    long long N3) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float d = rho[i] - t[i];
+    grad[i] = 2.0f * c * d;
+    acc += (double)c * (double)d * (double)d;
+  }
+  block_sum_atomic(acc, loss);
+}
+
+sim_status launch_density_loss(const float* rho, const float* target, float c, float* grad,
+                               double* loss, long long N3, cudaStream_t st) {
+  int blocks = cdiv(N3, 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  density_loss_kernel<<<blocks, 256, 0, st>>>(rho, target, c, grad, loss, N3);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+}  // namespace dh
+
+// ------------------------------------------------------------------ C ABI
+using namespace dh;
+
+extern "C" sim_status sim_deposit_cic(const float* s, const float* values, int32_t n, double box,
+                                      float* grid, void* stream) {
+  if (!s || !grid || n < 1 || !(box > 0)) {
+    set_error("sim_deposit_cic: invalid arguments");
+    return SIM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long N3 = (long long)n * n * n;
+  unsigned long long* acc = nullptr;
+  DH_CUDA_TRY(cudaMallocAsync((void**)&acc, N3 * sizeof(unsigned long long), st));
+  sim_status r = SIM_OK;
+  if (cudaMemsetAsync(acc, 0, N3 * sizeof(unsigned long long), st) != cudaSuccess) {
+    set_error("cudaMemsetAsync failed");
+    r = SIM_ECUDA;
+  }
+  if (r == SIM_OK) r = launch_deposit(s, values, n, (float)(n / box), acc, st);
+  if (r == SIM_OK) r = launch_fix_to_float(acc, 1.0f, grid, 0.0f, grid, n, st);
+  cudaFreeAsync(acc, st);
+  return r;
+}
+
+extern "C" sim_status sim_interp_cic(const float* grid, int32_t nf, int32_t n, double box,
+                                     const float* s, float* out, void* stream) {
+  if (!grid || !s || !out || n < 1 || nf < 1 || !(box > 0)) {
+    set_error("sim_interp_cic: invalid arguments");
+    return SIM_EINVAL;
+  }
+  return launch_interp(grid, nf, n, (float)(n / box), s, out, (cudaStream_t)stream);
+}
+
+extern "C" sim_status sim_gravity(const float* delta, int32_t n, double box, double pref,
+                                  float* g, void* stream) {
+  if (!delta || !g || n < 2 || !(box > 0)) {
+    set_error("sim_gravity: invalid arguments");
+    return SIM_EINVAL;
+  }
+  FFTPlans* plans = shared_plans(n);
+  if (!plans) return SIM_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long NC = (long long)n * n * (n / 2 + 1);
+  cufftComplex* buf = nullptr;
+  DH_CUDA_TRY(cudaMallocAsync((void**)&buf, 4 * NC * sizeof(cufftComplex), st));
+  sim_status r = launch_gravity(delta, g, buf, buf + NC, n, box, pref, *plans, st);
+  cudaFreeAsync(buf, st);
+  return r;
+}
+
+extern "C" sim_status sim_gravity_adjoint(const float* lam_g, int32_t n, double box, double pref,
+                                          float* lam_delta, void* stream) {
+  if (!lam_g || !lam_delta || n < 2 || !(box > 0)) {
+    set_error("sim_gravity_adjoint: invalid arguments");
+    return SIM_EINVAL;
+  }
+  FFTPlans* plans = shared_plans(n);
+  if (!plans) return SIM_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long NC = (long long)n * n * (n / 2 + 1);
+  cufftComplex* buf = nullptr;
+  DH_CUDA_TRY(cudaMallocAsync((void**)&buf, 4 * NC * sizeof(cufftComplex), st));
+  sim_status r = launch_gravity_adjoint(lam_g, lam_delta, buf, buf + 3 * NC, n, box, pref,
+                                        *plans, st);
+  cudaFreeAsync(buf, st);
+  return r;
+}

@@ -1,0 +1,80 @@
+// Particle-mesh gravity kernels (Sec. 2.2 of arXiv 2502.02294) and their adjoints.
+#pragma once
+
+#include <cufft.h>
+
+#include "common.cuh"
+
+namespace dh {
+
+// Fixed-point scale of the deterministic CIC accumulation: weights * 2^32 in int64.
+constexpr float kFix = 4294967296.0f;
+constexpr float kInvFix = 2.3283064365386963e-10f;
+
+// cuFFT plans for one grid size: r2c batch 1/3/4, c2r batch 1/3/4 (n^3 real <-> n^2(n/2+1)).
+struct FFTPlans {
+  int n = 0;
+  cufftHandle r2c1 = 0, r2c3 = 0, r2c4 = 0, c2r1 = 0, c2r3 = 0, c2r4 = 0;
+  sim_status create(int n);
+  void destroy();
+  sim_status set_stream(cudaStream_t st);
+};
+
+// Plans shared by the standalone entry points, keyed by n (created on first use).
+FFTPlans* shared_plans(int n);
+
+// ------------------------------------------------------------------ launchers
+// grid (int64 fixed point, n^3) += sum_p value_p W(x_p - node); values may be NULL (= 1)
+sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
+                          unsigned long long* acc, cudaStream_t st);
+// out = scale * fixed_to_float(acc) + add (add may be NULL) + offset; acc is zeroed
+sim_status launch_fix_to_float(unsigned long long* acc, float scale, const float* add,
+                               float offset, float* out, int n, cudaStream_t st);
+// g (3 n^3) from delta (n^3): r2c, Green's function * i k * pref / n^3, c2r x3
+sim_status launch_gravity(const float* delta, float* g, cufftComplex* dk, cufftComplex* gk,
+                          int n, double box, double pref, FFTPlans& plans, cudaStream_t st);
+// lam_delta (n^3) = (d g / d delta)^T lam_g (3 n^3)
+sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftComplex* gk,
+                                  cufftComplex* dk, int n, double box, double pref,
+                                  FFTPlans& plans, cudaStream_t st);
+// out[f][p] = CIC readout of grid f at particle p, nf fields
+sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
+                         float* out, cudaStream_t st);
+// p += K interp(g, s); then, if dtau != 0, s += dtau p. If zhat != NULL also
+// aux += interp(zhat, s) (after the drift).
+sim_status launch_kick_drift(float* s, float* p, const float* g, float K, float dtau,
+                             const float* zhat, float* aux, int n, float inv_dx,
+                             cudaStream_t st);
+// m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2 (gas 5 n^3, g 3 n^3)
+sim_status launch_gas_kick(float* gas, const float* g, float K, int n, cudaStream_t st);
+
+// ---- adjoints
+// Gas kick: lam (5 n^3, in/out) through the kick at the pre-kick gas state `gas`;
+// lam_g (3 n^3) += partial (plain add, cell-owned); dK += lam . d/dK.
+sim_status launch_gas_kick_adjoint(const float* gas, const float* g, float K, float* lam,
+                                   float* lam_g, double* dK, int n, cudaStream_t st);
+// Particle kick (+ preceding drift if dtau != 0), reverse order:
+//   forward: p1 = p0 + K interp(g, s0); s1 = s0 + dtau p1
+//   given lam_s (= lam_s1), lam_p (= lam_p1 from later use), both in/out:
+//   lam_p1 += dtau lam_s1; d_dtau += lam_s1 . p1; lam_p0 = lam_p1;
+//   lam_s0 = lam_s1 + K grad(interp g)(s0) . lam_p1; lam_g += interp^T(K lam_p1) (atomic);
+//   dK += lam_p1 . interp(g)(s0).
+sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, float K,
+                                     float dtau, float* lam_s, float* lam_p, float* lam_g,
+                                     double* dK, double* ddtau, int n, float inv_dx,
+                                     cudaStream_t st);
+// Deposit adjoint for delta = cm * count + rho_gas - 1:
+//   lam_s += cm grad(interp lam_delta)(s) / dx ; d_cm += sum_p interp(lam_delta)(s_p)
+sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, float cm,
+                                  float* lam_s, double* dcm, int n, float inv_dx,
+                                  cudaStream_t st);
+// sum_i a_i b_i over `count` floats into *out (device double, accumulated)
+sim_status launch_dot(const float* a, const float* b, long long count, double* out,
+                      cudaStream_t st);
+// y += alpha x over count floats
+sim_status launch_axpy(float alpha, const float* x, float* y, long long count, cudaStream_t st);
+// grad[i] = 2 c (rho_i - t_i) for the first N3 floats; *loss += c sum (rho - t)^2
+sim_status launch_density_loss(const float* rho, const float* target, float c, float* grad,
+                               double* loss, long long N3, cudaStream_t st);
+
+}  // namespace dh

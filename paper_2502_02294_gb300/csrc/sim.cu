@@ -1,0 +1,908 @@
+// Simulation handle: one time step of the coupled DM + gas + subgrid system, checkpointed
+// runs and their reverse-mode derivative (arXiv 2502.02294, Secs. 2.1-2.4 and 2.3.5).
+//
+// Step i (a_i -> a_{i+1}), the same kick-drift-kick for DM and gas:
+//   1 half kick with g(a_i) (K1) and DM drift (dtau)        [kick_drift, gas_kick]
+//   2 three relaxing-TVD sweeps in the Strang order (i mod 6) [sweep x3]
+//   3 subgrid at a_{i+1} with the Philox draws of step i      [subgrid]
+//   4 CIC deposit + spectral Poisson -> g(a_{i+1})             [deposit, fix, r2c, green, c2r]
+//   5 half kick with g(a_{i+1}) (K2)                           [kick_drift, gas_kick]
+// The reverse pass recomputes each checkpoint segment forward, recording the inputs of
+// every stage (the tape), then applies the hand-written adjoint of each stage in reverse
+// order. The adjoint of g(a_i) seen by the first kick of step i is carried into step i-1,
+// whose force stage produced it, so each force adjoint runs once per step.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ics.cuh"
+#include "pm.cuh"
+#include "schedule.h"
+#include "subgrid.cuh"
+
+namespace dh {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+const char* get_error() { return g_err; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double nu, double gam,
+                        double eps, cudaStream_t st);
+sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
+                                int n, double nu, double gam, double eps, double* dnu,
+                                cudaStream_t st);
+
+static const char* kOrders[6] = {"xyz", "zyx", "zxy", "yxz", "yzx", "xzy"};
+
+// per-step partial sums of the reverse pass (doubles on the device)
+enum { SL_DK1 = 0, SL_DK2, SL_DNU, SL_DDTAU, SL_DPREF, SL_DCM, SL_DFB, SL_N = 8 };
+
+// One recorded step: inputs of every stage (pointers into the tape allocation).
+struct TapeSlot {
+  float *U0, *Uk1, *Us1, *Us2, *Us3, *Usg;  // 5 n^3 each
+  float *s0, *p0, *g0, *s1, *g1;            // 3 n^3 each
+};
+constexpr int kTapeFloatsPerCell = 6 * 5 + 5 * 3;
+
+}  // namespace dh
+
+using namespace dh;
+
+struct sim_s {
+  sim_params prm;
+  int n = 0;
+  long long N3 = 0, NC = 0;
+  cudaStream_t st = 0;
+  double dx = 0, inv_dx = 0, fb = 0, cm = 0;
+  std::vector<StepFactors> sched;
+  double pref0 = 0, dpref0 = 0;
+  // ICs constants
+  double C = 0, dlnC_dom = 0, rp = 0, drp_dom = 0, a2e0 = 0;
+  FFTPlans plans;
+  // state
+  float *gas = nullptr, *gas2 = nullptr, *s = nullptr, *p = nullptr, *g = nullptr;
+  float *star = nullptr, *aux = nullptr, *zhat = nullptr, *delta = nullptr;
+  uint32_t* events = nullptr;
+  unsigned long long* acc = nullptr;
+  cufftComplex* ck = nullptr;  // 5 NC complex scratch
+  float *noise = nullptr, *f4 = nullptr;
+  float *init_gas = nullptr, *init_part = nullptr;
+  float *prev_gas = nullptr, *prev_part = nullptr;
+  int prev_step = -1;
+  bool ics_valid = false;
+  int init_step = 0;
+  int step = 0;
+  // checkpoints
+  std::vector<float*> ckpt;
+  std::vector<int> ckpt_step;
+  // tape and adjoint scratch (allocated on first use)
+  float* tape = nullptr;
+  int tape_cap = 0;
+  float *w_gas = nullptr, *w_gas2 = nullptr, *w_s = nullptr, *w_p = nullptr, *w_g = nullptr;
+  float *lam_gas = nullptr, *lam_tmp = nullptr, *lam_s = nullptr, *lam_p = nullptr;
+  float *lamG0 = nullptr, *lamG1 = nullptr, *lam_delta = nullptr, *lam4 = nullptr;
+  double* dslots = nullptr;
+  int dslots_cap = 0;
+  double* dglob = nullptr;  // SIM_NPARAMS + 4 extras
+  unsigned int* speed_bits = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace dh {
+
+static sim_status fail(sim_t* h, sim_status s) {
+  if (h && s != SIM_OK) h->err = get_error();
+  return s;
+}
+
+static sim_status dalloc(sim_t* h, void** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return SIM_ENOMEM;
+  }
+  h->allocs.push_back(*ptr);
+  return SIM_OK;
+}
+
+template <class T>
+static sim_status dalloc_t(sim_t* h, T** ptr, size_t count) {
+  return dalloc(h, (void**)ptr, count * sizeof(T));
+}
+
+static sim_status dcopy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  DH_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+  return SIM_OK;
+}
+
+static sim_status dzero(void* dst, size_t bytes, cudaStream_t st) {
+  DH_CUDA_TRY(cudaMemsetAsync(dst, 0, bytes, st));
+  return SIM_OK;
+}
+
+static sim_status validate(const sim_params* p) {
+  if (!p) {
+    set_error("null parameter block");
+    return SIM_EINVAL;
+  }
+  if (p->n < 4 || p->n > 1024) {
+    set_error("n must be in [4, 1024] (got %d)", p->n);
+    return SIM_EINVAL;
+  }
+  if (p->n_steps < 1 || p->ckpt_every < 1) {
+    set_error("n_steps and ckpt_every must be >= 1");
+    return SIM_EINVAL;
+  }
+  if (!(p->box > 0) || !(p->omega_m > 0 && p->omega_m <= 1) || !(p->omega_b > 0) ||
+      !(p->omega_b < p->omega_m) || !(p->gamma > 1) || !(p->mu > 0) || !(p->T_init > 0) ||
+      !(p->a_start > 0) || !(p->a_end > p->a_start) || !(p->sigma8 > 0) ||
+      !(p->rms_ref >= 0) || !(p->a_ref > 0) || !(p->sigma8_ref > 0) ||
+      !(p->omega_m_ref > 0 && p->omega_m_ref <= 1) || !(p->kc_frac > 0) ||
+      !(p->limiter_eps > 0)) {
+    set_error("invalid cosmology, gas or IC parameters");
+    return SIM_EINVAL;
+  }
+  if (p->subgrid_on && (!(p->Pi0 > 0 && p->Pi0 < 1) || !(p->tau > 0) || !(p->w_delta > 0) ||
+                        !(p->w_T > 0) || !(p->T0_uv >= 0))) {
+    set_error("invalid subgrid parameters (0 < Pi0 < 1, tau > 0, widths > 0, T0_uv >= 0)");
+    return SIM_EINVAL;
+  }
+  if (p->kdk_mode != 0 && p->kdk_mode != 1) {
+    set_error("kdk_mode must be 0 (FastPM) or 1 (plain)");
+    return SIM_EINVAL;
+  }
+  return SIM_OK;
+}
+
+// total matter contrast from particles and gas, then the force field g (3 n^3)
+static sim_status compute_force(sim_t* h, const float* s, const float* gas, double pref,
+                                float* g) {
+  if (!h->prm.gravity_on) return dzero(g, 3 * h->N3 * sizeof(float), h->st);
+  DH_TRY(launch_deposit(s, nullptr, h->n, (float)h->inv_dx, h->acc, h->st));
+  DH_TRY(launch_fix_to_float(h->acc, (float)h->cm, gas, -1.0f, h->delta, h->n, h->st));
+  return launch_gravity(h->delta, g, h->ck, h->ck + h->NC, h->n, h->prm.box, pref, h->plans,
+                        h->st);
+}
+
+// One forward step in place on (gas/gas_tmp ping-pong, s, p, g). With tape != nullptr the
+// inputs of every stage are recorded; diagnostics (star, aux, events) only without tape.
+static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, float* s, float* p,
+                               float* g, const TapeSlot* T) {
+  const StepFactors& f = h->sched[i];
+  const sim_params& P = h->prm;
+  cudaStream_t st = h->st;
+  const size_t gb = 5 * h->N3 * sizeof(float), vb = 3 * h->N3 * sizeof(float);
+  const float K1 = P.gravity_on ? (float)f.K1 : 0.0f;
+  const float K2 = P.gravity_on ? (float)f.K2 : 0.0f;
+  if (T) {
+    DH_TRY(dcopy(T->U0, *gas, gb, st));
+    DH_TRY(dcopy(T->s0, s, vb, st));
+    DH_TRY(dcopy(T->p0, p, vb, st));
+    DH_TRY(dcopy(T->g0, g, vb, st));
+  }
+  // 1. half kick + drift
+  DH_TRY(launch_kick_drift(s, p, g, K1, (float)f.dtau, nullptr, nullptr, h->n,
+                           (float)h->inv_dx, st));
+  float* cur = *gas;
+  if (T) {
+    DH_TRY(dcopy(T->Uk1, cur, gb, st));
+    cur = T->Uk1;
+  }
+  if (P.gravity_on) DH_TRY(launch_gas_kick(cur, g, K1, h->n, st));
+  // 2. sweeps
+  if (P.hydro_on) {
+    const char* order = kOrders[i % 6];
+    const double nu = f.dtau * h->inv_dx;
+    float* outs_tape[3] = {T ? T->Us1 : nullptr, T ? T->Us2 : nullptr, T ? T->Us3 : nullptr};
+    for (int k = 0; k < 3; ++k) {
+      float* out = T ? outs_tape[k] : (cur == *gas ? *gas_tmp : *gas);
+      DH_TRY(launch_sweep(order[k] - 'x', cur, out, h->n, nu, P.gamma, P.limiter_eps, st));
+      cur = out;
+    }
+  } else if (T) {
+    DH_TRY(dcopy(T->Us3, cur, gb, st));
+    cur = T->Us3;
+  }
+  // 3. subgrid
+  float* zh = nullptr;
+  if (P.subgrid_on) {
+    const SubgridConst c = make_subgrid_const(P, f.a1, i);
+    float* out = T ? T->Usg : cur;
+    zh = T ? nullptr : h->zhat;
+    DH_TRY(launch_subgrid(cur, out, c, zh, T ? nullptr : h->events, h->N3, st));
+    cur = out;
+  } else if (T) {
+    DH_TRY(dcopy(T->Usg, cur, gb, st));
+    cur = T->Usg;
+  }
+  // 4. force at a_{i+1}
+  DH_TRY(compute_force(h, s, cur, f.pref1, g));
+  if (T) {
+    DH_TRY(dcopy(T->s1, s, vb, st));
+    DH_TRY(dcopy(T->g1, g, vb, st));
+    DH_TRY(dcopy(*gas, cur, gb, st));
+    cur = *gas;
+  } else if (cur != *gas) {
+    float* t = *gas;
+    *gas = *gas_tmp;
+    *gas_tmp = t;
+  }
+  // 5. half kick (+ star readout on the particles)
+  DH_TRY(launch_kick_drift(s, p, g, K2, 0.0f, zh, zh ? h->aux : nullptr, h->n,
+                           (float)h->inv_dx, st));
+  if (P.gravity_on) DH_TRY(launch_gas_kick(*gas, g, K2, h->n, st));
+  if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, h->N3, st));
+  return SIM_OK;
+}
+
+static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
+  const long long N3 = h->N3;
+  if (!h->lam_gas) {
+    DH_TRY(dalloc_t(h, &h->w_gas, 5 * N3));
+    DH_TRY(dalloc_t(h, &h->w_gas2, 5 * N3));
+    DH_TRY(dalloc_t(h, &h->w_s, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->w_p, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->w_g, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->lam_gas, 5 * N3));
+    DH_TRY(dalloc_t(h, &h->lam_tmp, 5 * N3));
+    DH_TRY(dalloc_t(h, &h->lam_s, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->lam_p, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->lamG0, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->lamG1, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->lam_delta, N3));
+    DH_TRY(dalloc_t(h, &h->lam4, 4 * N3));
+    DH_TRY(dalloc_t(h, &h->dglob, SIM_NPARAMS + 8));
+  }
+  if (h->tape_cap < tape_steps) {
+    if (h->tape) {
+      DH_CUDA_TRY(cudaStreamSynchronize(h->st));
+      cudaFree(h->tape);
+      for (auto& a : h->allocs)
+        if (a == h->tape) a = nullptr;
+    }
+    h->tape = nullptr;
+    DH_TRY(dalloc_t(h, &h->tape, (size_t)tape_steps * kTapeFloatsPerCell * N3));
+    h->tape_cap = tape_steps;
+  }
+  const int slots = h->prm.n_steps + 2;
+  if (h->dslots_cap < slots) {
+    DH_TRY(dalloc_t(h, &h->dslots, (size_t)slots * SL_N));
+    h->dslots_cap = slots;
+  }
+  return SIM_OK;
+}
+
+static TapeSlot tape_slot(sim_t* h, int k) {
+  const long long N3 = h->N3;
+  float* b = h->tape + (size_t)k * kTapeFloatsPerCell * N3;
+  TapeSlot t;
+  t.U0 = b;
+  t.Uk1 = b + 5 * N3;
+  t.Us1 = b + 10 * N3;
+  t.Us2 = b + 15 * N3;
+  t.Us3 = b + 20 * N3;
+  t.Usg = b + 25 * N3;
+  t.s0 = b + 30 * N3;
+  t.p0 = b + 33 * N3;
+  t.g0 = b + 36 * N3;
+  t.s1 = b + 39 * N3;
+  t.g1 = b + 42 * N3;
+  return t;
+}
+
+// Adjoint of the force field g = G(s, rho) at one state: lam_G (3 n^3, consumed) ->
+// lam_rho += ..., lam_s += ...; slot[SL_DPREF] += lam_G . g, slot[SL_DCM] += d/d(1 - f_b).
+static sim_status force_adjoint(sim_t* h, const float* s, const float* g, double pref,
+                                float* lamG, double* slot) {
+  if (!h->prm.gravity_on) return SIM_OK;
+  cudaStream_t st = h->st;
+  DH_TRY(launch_dot(lamG, g, 3 * h->N3, slot + SL_DPREF, st));
+  DH_TRY(launch_gravity_adjoint(lamG, h->lam_delta, h->ck, h->ck + 3 * h->NC, h->n,
+                                h->prm.box, pref, h->plans, st));
+  DH_TRY(launch_axpy(1.0f, h->lam_delta, h->lam_gas, h->N3, st));
+  return launch_deposit_adjoint(s, h->lam_delta, (float)h->cm, h->lam_s, slot + SL_DCM, h->n,
+                                (float)h->inv_dx, st);
+}
+
+// Reverse of forward_step for step i with tape T. In: lam_gas / lam_s / lam_p of the state
+// after the step, lamG1 = adjoint of g(a_{i+1}) carried from step i+1. Out: the same
+// buffers for the state before the step, lamG0 = adjoint of g(a_i) (to carry).
+static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot) {
+  const StepFactors& f = h->sched[i];
+  const sim_params& P = h->prm;
+  cudaStream_t st = h->st;
+  const float K1 = P.gravity_on ? (float)f.K1 : 0.0f;
+  const float K2 = P.gravity_on ? (float)f.K2 : 0.0f;
+  // 5. second half kick
+  if (P.gravity_on) {
+    DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, h->lamG1, slot + SL_DK2, h->n, st));
+    DH_TRY(launch_kick_drift_adjoint(T.s1, nullptr, T.g1, K2, 0.0f, h->lam_s, h->lam_p, h->lamG1,
+                                     slot + SL_DK2, nullptr, h->n, (float)h->inv_dx, st));
+    // 4. force at a_{i+1}
+    DH_TRY(force_adjoint(h, T.s1, T.g1, f.pref1, h->lamG1, slot));
+  }
+  // 3. subgrid
+  if (P.subgrid_on) {
+    const SubgridConst c = make_subgrid_const(P, f.a1, i);
+    DH_TRY(launch_subgrid_adjoint(T.Us3, h->lam_gas, c, h->dglob, slot + SL_DFB, h->N3, st));
+  }
+  // 2. sweeps in reverse
+  if (P.hydro_on) {
+    const char* order = kOrders[i % 6];
+    const double nu = f.dtau * h->inv_dx;
+    const float* ins[3] = {T.Uk1, T.Us1, T.Us2};
+    for (int k = 2; k >= 0; --k) {
+      DH_TRY(launch_sweep_adjoint(order[k] - 'x', ins[k], h->lam_gas, h->lam_tmp, h->n, nu,
+                                  P.gamma, P.limiter_eps, slot + SL_DNU, st));
+      float* t = h->lam_gas;
+      h->lam_gas = h->lam_tmp;
+      h->lam_tmp = t;
+    }
+  }
+  // 1. first half kick and drift
+  DH_TRY(dzero(h->lamG0, 3 * h->N3 * sizeof(float), st));
+  if (P.gravity_on)
+    DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, h->lamG0, slot + SL_DK1, h->n, st));
+  DH_TRY(launch_kick_drift_adjoint(T.s0, T.p0, T.g0, K1, (float)f.dtau, h->lam_s, h->lam_p,
+                                   h->lamG0, slot + SL_DK1, slot + SL_DDTAU, h->n,
+                                   (float)h->inv_dx, st));
+  float* t = h->lamG0;
+  h->lamG0 = h->lamG1;
+  h->lamG1 = t;  // carry: lamG1 now holds the adjoint of g(a_i)
+  return SIM_OK;
+}
+
+// d/dOmega_m of the per-step partials (host, FP64 chain rule through the schedule)
+static double omega_chain(sim_t* h, const std::vector<double>& slots, int first, int last) {
+  double d = 0.0;
+  const double dfb = -h->fb / h->prm.omega_m;
+  for (int i = first; i < last; ++i) {
+    const StepFactors& f = h->sched[i];
+    const double* sl = slots.data() + (size_t)i * SL_N;
+    d += sl[SL_DK1] * f.dK1 + sl[SL_DK2] * f.dK2;
+    d += (sl[SL_DNU] * h->inv_dx + sl[SL_DDTAU]) * f.ddtau;
+    d += sl[SL_DPREF] / f.pref1 * f.dpref1;
+    d += (-sl[SL_DCM] + sl[SL_DFB]) * dfb;
+  }
+  return d;
+}
+
+static sim_status alloc_state(sim_t* h) {
+  const long long N3 = h->N3, NC = h->NC;
+  DH_TRY(dalloc_t(h, &h->gas, 5 * N3));
+  DH_TRY(dalloc_t(h, &h->gas2, 5 * N3));
+  DH_TRY(dalloc_t(h, &h->s, 3 * N3));
+  DH_TRY(dalloc_t(h, &h->p, 3 * N3));
+  DH_TRY(dalloc_t(h, &h->g, 3 * N3));
+  DH_TRY(dalloc_t(h, &h->star, N3));
+  DH_TRY(dalloc_t(h, &h->aux, N3));
+  DH_TRY(dalloc_t(h, &h->zhat, N3));
+  DH_TRY(dalloc_t(h, &h->delta, N3));
+  DH_TRY(dalloc_t(h, &h->events, (N3 + 31) / 32));
+  DH_TRY(dalloc_t(h, &h->acc, N3));
+  DH_TRY(dalloc_t(h, &h->ck, 5 * NC));
+  DH_TRY(dalloc_t(h, &h->noise, N3));
+  DH_TRY(dalloc_t(h, &h->f4, 4 * N3));
+  DH_TRY(dalloc_t(h, &h->init_gas, 5 * N3));
+  DH_TRY(dalloc_t(h, &h->init_part, 6 * N3));
+  DH_TRY(dalloc_t(h, &h->prev_gas, 5 * N3));
+  DH_TRY(dalloc_t(h, &h->prev_part, 6 * N3));
+  DH_TRY(dalloc_t(h, &h->speed_bits, 1));
+  DH_TRY(dzero(h->acc, N3 * sizeof(unsigned long long), h->st));
+  DH_TRY(dzero(h->events, ((N3 + 31) / 32) * sizeof(uint32_t), h->st));
+  return SIM_OK;
+}
+
+static void clear_checkpoints(sim_t* h) {
+  if (!h->ckpt.empty()) cudaStreamSynchronize(h->st);
+  for (float* c : h->ckpt) {
+    cudaFree(c);
+    for (auto& a : h->allocs)
+      if (a == c) a = nullptr;
+  }
+  h->ckpt.clear();
+  h->ckpt_step.clear();
+}
+
+static sim_status reset_to_init(sim_t* h) {
+  const long long N3 = h->N3;
+  cudaStream_t st = h->st;
+  DH_TRY(dcopy(h->gas, h->init_gas, 5 * N3 * sizeof(float), st));
+  DH_TRY(dcopy(h->s, h->init_part, 3 * N3 * sizeof(float), st));
+  DH_TRY(dcopy(h->p, h->init_part + 3 * N3, 3 * N3 * sizeof(float), st));
+  DH_TRY(dzero(h->star, N3 * sizeof(float), st));
+  DH_TRY(dzero(h->aux, N3 * sizeof(float), st));
+  h->step = h->init_step;
+  const double a = h->init_step == 0 ? h->prm.a_start : h->sched[h->init_step - 1].a1;
+  DH_TRY(compute_force(h, h->s, h->gas, 1.5 * h->prm.omega_m / a, h->g));
+  clear_checkpoints(h);
+  h->prev_step = -1;
+  return SIM_OK;
+}
+
+static sim_status store_checkpoint(sim_t* h) {
+  const long long N3 = h->N3;
+  float* c = nullptr;
+  DH_TRY(dalloc_t(h, &c, 11 * N3));
+  h->ckpt.push_back(c);
+  h->ckpt_step.push_back(h->step);
+  DH_TRY(dcopy(c, h->gas, 5 * N3 * sizeof(float), h->st));
+  DH_TRY(dcopy(c + 5 * N3, h->s, 3 * N3 * sizeof(float), h->st));
+  return dcopy(c + 8 * N3, h->p, 3 * N3 * sizeof(float), h->st);
+}
+
+}  // namespace dh
+
+// ===================================================================== C ABI
+extern "C" {
+
+sim_status sim_params_default(sim_params* p) {
+  if (!p) return SIM_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->n = 32;
+  p->n_steps = 20;
+  p->ckpt_every = 6;
+  p->subgrid_on = 0;
+  p->gravity_on = 1;
+  p->hydro_on = 1;
+  p->kdk_mode = 0;
+  p->instance = 0;
+  p->seed = 1;
+  p->box = 32.0;
+  p->omega_m = 0.3;
+  p->omega_b = 0.049;
+  p->h = 0.7;
+  p->sigma8 = 0.8;
+  p->gamma = 5.0 / 3.0;
+  p->mu = 0.6;
+  p->T_init = 1.0e4;
+  p->a_start = 0.1;
+  p->a_end = 0.5;
+  p->delta_c = 100.0;
+  p->Pi0 = 0.05;
+  p->E0 = 0.03;
+  p->T_c = 3.0e4;
+  p->w_delta = 5.0;
+  p->w_T = 1500.0;
+  p->tau = 0.1;
+  p->T0_uv = 0.0;
+  p->gamma_uv = 1.4;
+  p->rms_ref = 0.05;
+  p->a_ref = 0.1;
+  p->sigma8_ref = 0.8;
+  p->omega_m_ref = 0.3;
+  p->kc_frac = 0.5;
+  p->limiter_eps = 1e-30;
+  p->cfl_max = 0.0;
+  return SIM_OK;
+}
+
+const char* sim_last_error(const sim_t* h) { return h ? h->err.c_str() : get_error(); }
+
+int64_t sim_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t** out) {
+  if (!out) {
+    set_error("sim_init: out is NULL");
+    return SIM_EINVAL;
+  }
+  *out = nullptr;
+  DH_TRY(validate(p));
+  sim_t* h = new sim_t();
+  h->prm = *p;
+  h->n = p->n;
+  h->N3 = (long long)p->n * p->n * p->n;
+  h->NC = (long long)p->n * p->n * (p->n / 2 + 1);
+  h->st = (cudaStream_t)stream;
+  h->dx = p->box / p->n;
+  h->inv_dx = p->n / p->box;
+  h->fb = p->omega_b / p->omega_m;
+  h->cm = 1.0 - h->fb;
+  h->sched = make_schedule(p->a_start, p->a_end, p->n_steps, p->omega_m, p->kdk_mode);
+  h->pref0 = 1.5 * p->omega_m / p->a_start;
+  h->dpref0 = 1.5 / p->a_start;
+  // IC constants (Sec. 2.1): C = rms_target sqrt(n^3 / sum_k P(k))
+  {
+    const int n = p->n;
+    const double kf = 2.0 * M_PI / p->box, kc = p->kc_frac * M_PI * n / p->box;
+    double total = 0.0;
+    for (int z = 0; z < n; ++z)
+      for (int y = 0; y < n; ++y)
+        for (int x = 0; x <= n / 2; ++x) {
+          const int kz = z > n / 2 ? z - n : z, ky = y > n / 2 ? y - n : y;
+          const double k2 = kf * kf * ((double)x * x + (double)ky * ky + (double)kz * kz);
+          if (k2 <= 0) continue;
+          const double w = (x == 0 || (n % 2 == 0 && x == n / 2)) ? 1.0 : 2.0;
+          total += w * std::exp(-k2 / (kc * kc)) / k2;
+        }
+    const double Di = growth_D(p->a_start, p->omega_m);
+    const double rms = p->rms_ref * (p->sigma8 / p->sigma8_ref) * Di /
+                       growth_D(p->a_ref, p->omega_m_ref);
+    h->C = rms * std::sqrt((double)n * n * n / total);
+    const double hh = 1e-5 * p->omega_m;
+    h->dlnC_dom = (growth_D(p->a_start, p->omega_m + hh) - growth_D(p->a_start, p->omega_m - hh)) /
+                  (2 * hh) / Di;
+    auto rpf = [&](double om) { return growth_gp(p->a_start, om) / growth_D(p->a_start, om); };
+    h->rp = rpf(p->omega_m);
+    h->drp_dom = (rpf(p->omega_m + hh) - rpf(p->omega_m - hh)) / (2 * hh);
+    const double e0 = p->T_init / temperature_per_energy(p->gamma, p->mu);
+    h->a2e0 = p->a_start * p->a_start * e0;
+  }
+  sim_status r = h->plans.create(p->n);
+  if (r == SIM_OK) r = alloc_state(h);
+  cudaStream_t st = h->st;
+  if (r == SIM_OK) {
+    if (noise)
+      r = dcopy(h->noise, noise, h->N3 * sizeof(float), st);
+    else
+      r = launch_noise(p->seed, p->instance, h->noise, h->N3, st);
+  }
+  if (r == SIM_OK)
+    r = launch_linear_field(h->noise, h->f4, h->ck, p->n, p->box, p->kc_frac, h->C, h->plans, st);
+  if (r == SIM_OK) r = launch_place(h->f4, h->gas, h->s, h->p, h->rp, h->fb, h->a2e0, h->N3, st);
+  if (r == SIM_OK) r = dcopy(h->init_gas, h->gas, 5 * h->N3 * sizeof(float), st);
+  if (r == SIM_OK) r = dcopy(h->init_part, h->s, 3 * h->N3 * sizeof(float), st);
+  if (r == SIM_OK) r = dcopy(h->init_part + 3 * h->N3, h->p, 3 * h->N3 * sizeof(float), st);
+  if (r == SIM_OK) {
+    h->ics_valid = true;
+    h->init_step = 0;
+    r = reset_to_init(h);
+  }
+  if (r != SIM_OK) {
+    sim_destroy(h);
+    return r;
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+void sim_destroy(sim_t* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  h->plans.destroy();
+  for (void* a : h->allocs)
+    if (a) cudaFree(a);
+  delete h;
+}
+
+sim_status sim_step(sim_t* h) {
+  if (!h) return SIM_EINVAL;
+  if (h->step >= h->prm.n_steps) {
+    set_error("sim_step: already at the last step (%d)", h->prm.n_steps);
+    return fail(h, SIM_EINVAL);
+  }
+  const long long N3 = h->N3;
+  sim_status r = dcopy(h->prev_gas, h->gas, 5 * N3 * sizeof(float), h->st);
+  if (r == SIM_OK) r = dcopy(h->prev_part, h->s, 3 * N3 * sizeof(float), h->st);
+  if (r == SIM_OK) r = dcopy(h->prev_part + 3 * N3, h->p, 3 * N3 * sizeof(float), h->st);
+  if (r == SIM_OK) r = forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr);
+  if (r != SIM_OK) return fail(h, r);
+  h->prev_step = h->step;
+  h->step += 1;
+  clear_checkpoints(h);
+  return SIM_OK;
+}
+
+sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* adj_params) {
+  if (!h || !adj_gas || !adj_part) {
+    set_error("sim_step_adjoint: null arguments");
+    return fail(h, SIM_EINVAL);
+  }
+  if (h->prev_step < 0 || h->prev_step + 1 != h->step) {
+    set_error("sim_step_adjoint: no sim_step to differentiate");
+    return fail(h, SIM_EINVAL);
+  }
+  const long long N3 = h->N3;
+  cudaStream_t st = h->st;
+  const int i = h->prev_step;
+  sim_status r = ensure_adjoint_buffers(h, 1);
+  if (r != SIM_OK) return fail(h, r);
+  const TapeSlot T = tape_slot(h, 0);
+  double* slot = h->dslots;
+  auto run = [&]() -> sim_status {
+    DH_TRY(dzero(h->dslots, 2 * SL_N * sizeof(double), st));
+    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + 8) * sizeof(double), st));
+    // recompute the step from its input with the tape
+    DH_TRY(dcopy(h->w_gas, h->prev_gas, 5 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(h->w_s, h->prev_part, 3 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(h->w_p, h->prev_part + 3 * N3, 3 * N3 * sizeof(float), st));
+    const double a0 = h->sched[i].a0;
+    DH_TRY(compute_force(h, h->w_s, h->w_gas, 1.5 * h->prm.omega_m / a0, h->w_g));
+    DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
+    // reverse
+    DH_TRY(dcopy(h->lam_gas, adj_gas, 5 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(h->lam_s, adj_part, 3 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(h->lam_p, adj_part + 3 * N3, 3 * N3 * sizeof(float), st));
+    DH_TRY(dzero(h->lamG1, 3 * N3 * sizeof(float), st));
+    DH_TRY(reverse_step(h, i, T, slot));
+    // g(a_i) is a function of the input state: flush its adjoint now
+    DH_TRY(force_adjoint(h, T.s0, T.g0, 1.5 * h->prm.omega_m / a0, h->lamG1, slot + SL_N));
+    DH_TRY(dcopy(adj_gas, h->lam_gas, 5 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(adj_part, h->lam_s, 3 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(adj_part + 3 * N3, h->lam_p, 3 * N3 * sizeof(float), st));
+    return SIM_OK;
+  };
+  r = run();
+  if (r != SIM_OK) return fail(h, r);
+  if (adj_params) {
+    std::vector<double> sl(2 * SL_N), gl(SIM_NPARAMS + 8), acc(SIM_NPARAMS);
+    if (cudaMemcpyAsync(sl.data(), h->dslots, sl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(gl.data(), h->dglob, gl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(acc.data(), adj_params, SIM_NPARAMS * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("sim_step_adjoint: reading partial sums failed");
+      return fail(h, SIM_ECUDA);
+    }
+    const StepFactors& f = h->sched[i];
+    const double dfb = -h->fb / h->prm.omega_m;
+    double dom = 0.0;
+    dom += sl[SL_DK1] * f.dK1 + sl[SL_DK2] * f.dK2;
+    dom += (sl[SL_DNU] * h->inv_dx + sl[SL_DDTAU]) * f.ddtau;
+    dom += sl[SL_DPREF] / f.pref1 * f.dpref1;
+    dom += (-sl[SL_DCM] + sl[SL_DFB]) * dfb;
+    const double pa = 1.5 * h->prm.omega_m / f.a0;
+    dom += sl[SL_N + SL_DPREF] / pa * (1.5 / f.a0) + (-sl[SL_N + SL_DCM]) * dfb;
+    acc[SIM_P_OMEGA_M] += dom;
+    for (int k = SIM_P_DELTA_C; k < SIM_NPARAMS; ++k) acc[k] += gl[k];
+    if (cudaMemcpyAsync(adj_params, acc.data(), SIM_NPARAMS * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("sim_step_adjoint: writing parameter gradient failed");
+      return fail(h, SIM_ECUDA);
+    }
+  }
+  return SIM_OK;
+}
+
+sim_status sim_run(sim_t* h, int32_t n_steps) {
+  if (!h) return SIM_EINVAL;
+  if (h->step != h->init_step || !h->ckpt.empty()) {
+    set_error("sim_run: the handle must be at its initial state (sim_init / sim_reset)");
+    return fail(h, SIM_EINVAL);
+  }
+  if (n_steps < 0 || h->step + n_steps > h->prm.n_steps) {
+    set_error("sim_run: n_steps out of range");
+    return fail(h, SIM_EINVAL);
+  }
+  for (int k = 0; k < n_steps; ++k) {
+    sim_status r = SIM_OK;
+    if ((h->step - h->init_step) % h->prm.ckpt_every == 0) r = store_checkpoint(h);
+    if (r == SIM_OK) r = forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr);
+    if (r != SIM_OK) return fail(h, r);
+    h->step += 1;
+    if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
+      double c = 0;
+      r = sim_cfl(h, &c);
+      if (r != SIM_OK) return fail(h, r);
+      if (!(c <= h->prm.cfl_max)) {
+        set_error("sim_run: CFL number %.4g above cfl_max %.4g after step %d", c,
+                  h->prm.cfl_max, h->step);
+        return fail(h, std::isfinite(c) ? SIM_ECFL : SIM_ENAN);
+      }
+    }
+  }
+  h->prev_step = -1;
+  return SIM_OK;
+}
+
+sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart,
+                           float* dL_dnoise, double* dL_dparams) {
+  if (!h || !dL_dparams) {
+    set_error("sim_run_adjoint: null arguments");
+    return fail(h, SIM_EINVAL);
+  }
+  if (h->ckpt.empty()) {
+    set_error("sim_run_adjoint: no sim_run to differentiate");
+    return fail(h, SIM_EINVAL);
+  }
+  if (!h->ics_valid && dL_dnoise) {
+    set_error("sim_run_adjoint: the run did not start from initial conditions");
+    return fail(h, SIM_EINVAL);
+  }
+  const long long N3 = h->N3;
+  cudaStream_t st = h->st;
+  const int K = h->prm.ckpt_every;
+  sim_status r = ensure_adjoint_buffers(h, K);
+  if (r != SIM_OK) return fail(h, r);
+  const int nseg = (int)h->ckpt.size();
+  const int last = h->step;
+  auto body = [&]() -> sim_status {
+    DH_TRY(dzero(h->dslots, (size_t)h->dslots_cap * SL_N * sizeof(double), st));
+    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + 8) * sizeof(double), st));
+    if (dL_dgas)
+      DH_TRY(dcopy(h->lam_gas, dL_dgas, 5 * N3 * sizeof(float), st));
+    else
+      DH_TRY(dzero(h->lam_gas, 5 * N3 * sizeof(float), st));
+    if (dL_dpart) {
+      DH_TRY(dcopy(h->lam_s, dL_dpart, 3 * N3 * sizeof(float), st));
+      DH_TRY(dcopy(h->lam_p, dL_dpart + 3 * N3, 3 * N3 * sizeof(float), st));
+    } else {
+      DH_TRY(dzero(h->lam_s, 3 * N3 * sizeof(float), st));
+      DH_TRY(dzero(h->lam_p, 3 * N3 * sizeof(float), st));
+    }
+    DH_TRY(dzero(h->lamG1, 3 * N3 * sizeof(float), st));
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int first = h->ckpt_step[seg];
+      const int end = seg + 1 < nseg ? h->ckpt_step[seg + 1] : last;
+      const float* c = h->ckpt[seg];
+      DH_TRY(dcopy(h->w_gas, c, 5 * N3 * sizeof(float), st));
+      DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
+      DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
+      const double a0 = first == 0 ? h->prm.a_start : h->sched[first - 1].a1;
+      DH_TRY(compute_force(h, h->w_s, h->w_gas, 1.5 * h->prm.omega_m / a0, h->w_g));
+      for (int i = first; i < end; ++i) {
+        const TapeSlot T = tape_slot(h, i - first);
+        DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
+      }
+      for (int i = end - 1; i >= first; --i)
+        DH_TRY(reverse_step(h, i, tape_slot(h, i - first), h->dslots + (size_t)i * SL_N));
+    }
+    // g at the start of the run is a function of the initial state
+    const TapeSlot T0 = tape_slot(h, 0);
+    const int s0 = h->ckpt_step[0];
+    const double a0 = s0 == 0 ? h->prm.a_start : h->sched[s0 - 1].a1;
+    double* slot0 = h->dslots + (size_t)h->prm.n_steps * SL_N;
+    DH_TRY(force_adjoint(h, T0.s0, T0.g0, 1.5 * h->prm.omega_m / a0, h->lamG1, slot0));
+    // through the initial conditions to the white noise
+    if (h->ics_valid) {
+      DH_TRY(launch_ic_adjoint(h->f4, h->lam_gas, h->lam_s, h->lam_p, h->lam4, dL_dnoise, h->ck,
+                               h->n, h->prm.box, h->prm.kc_frac, h->C, h->rp, h->fb, h->a2e0,
+                               h->dglob + SIM_NPARAMS, h->dglob + SIM_NPARAMS + 1, h->plans, st));
+      DH_TRY(launch_dot(h->lam4, h->f4, 4 * N3, h->dglob + SIM_NPARAMS + 2, st));
+    }
+    return SIM_OK;
+  };
+  r = body();
+  if (r != SIM_OK) return fail(h, r);
+  std::vector<double> sl((size_t)h->dslots_cap * SL_N), gl(SIM_NPARAMS + 8);
+  if (cudaMemcpyAsync(sl.data(), h->dslots, sl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(gl.data(), h->dglob, gl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("sim_run_adjoint: reading partial sums failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(h, SIM_ECUDA);
+  }
+  std::vector<double> out(SIM_NPARAMS, 0.0);
+  const double dfb = -h->fb / h->prm.omega_m;
+  double dom = omega_chain(h, sl, h->ckpt_step[0], last);
+  const double* s0 = sl.data() + (size_t)h->prm.n_steps * SL_N;
+  const int st0 = h->ckpt_step[0];
+  const double a0 = st0 == 0 ? h->prm.a_start : h->sched[st0 - 1].a1;
+  dom += s0[SL_DPREF] / (1.5 * h->prm.omega_m / a0) * (1.5 / a0) + (-s0[SL_DCM]) * dfb;
+  double dsig = 0.0;
+  if (h->ics_valid) {
+    const double drp = gl[SIM_NPARAMS], dfb_ic = gl[SIM_NPARAMS + 1], lamC_C = gl[SIM_NPARAMS + 2];
+    dom += lamC_C * h->dlnC_dom + drp * h->drp_dom + dfb_ic * dfb;
+    dsig = lamC_C / h->prm.sigma8;
+  }
+  out[SIM_P_OMEGA_M] = dom;
+  out[SIM_P_SIGMA8] = dsig;
+  for (int k = SIM_P_DELTA_C; k < SIM_NPARAMS; ++k) out[k] = gl[k];
+  if (cudaMemcpyAsync(dL_dparams, out.data(), SIM_NPARAMS * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("sim_run_adjoint: writing parameter gradient failed");
+    return fail(h, SIM_ECUDA);
+  }
+  return SIM_OK;
+}
+
+sim_status sim_reset(sim_t* h) {
+  if (!h) return SIM_EINVAL;
+  return fail(h, reset_to_init(h));
+}
+
+sim_status sim_reinit(sim_t* h, const float* noise) {
+  if (!h) return SIM_EINVAL;
+  cudaStream_t st = h->st;
+  const long long N3 = h->N3;
+  sim_status r = noise ? dcopy(h->noise, noise, N3 * sizeof(float), st)
+                       : launch_noise(h->prm.seed, h->prm.instance, h->noise, N3, st);
+  if (r == SIM_OK)
+    r = launch_linear_field(h->noise, h->f4, h->ck, h->n, h->prm.box, h->prm.kc_frac, h->C,
+                            h->plans, st);
+  if (r == SIM_OK)
+    r = launch_place(h->f4, h->init_gas, h->init_part, h->init_part + 3 * N3, h->rp, h->fb,
+                     h->a2e0, N3, st);
+  if (r == SIM_OK) {
+    h->ics_valid = true;
+    h->init_step = 0;
+    r = reset_to_init(h);
+  }
+  return fail(h, r);
+}
+
+sim_status sim_loss_density(sim_t* h, const float* target, double c, float* dL_dgas,
+                            double* loss) {
+  if (!h || !target || !dL_dgas || !loss) {
+    set_error("sim_loss_density: null arguments");
+    return fail(h, SIM_EINVAL);
+  }
+  cudaStream_t st = h->st;
+  sim_status r = dzero(dL_dgas + h->N3, 4 * h->N3 * sizeof(float), st);
+  if (r == SIM_OK) r = dzero(loss, sizeof(double), st);
+  if (r == SIM_OK) r = launch_density_loss(h->gas, target, (float)c, dL_dgas, loss, h->N3, st);
+  return fail(h, r);
+}
+
+sim_status sim_get_state(sim_t* h, float* gas, float* part, float* star, float* aux,
+                         uint32_t* events, float* gravity, int32_t* step) {
+  if (!h) return SIM_EINVAL;
+  const long long N3 = h->N3;
+  cudaStream_t st = h->st;
+  sim_status r = SIM_OK;
+  if (gas && r == SIM_OK) r = dcopy(gas, h->gas, 5 * N3 * sizeof(float), st);
+  if (part && r == SIM_OK) r = dcopy(part, h->s, 3 * N3 * sizeof(float), st);
+  if (part && r == SIM_OK) r = dcopy(part + 3 * N3, h->p, 3 * N3 * sizeof(float), st);
+  if (star && r == SIM_OK) r = dcopy(star, h->star, N3 * sizeof(float), st);
+  if (aux && r == SIM_OK) r = dcopy(aux, h->aux, N3 * sizeof(float), st);
+  if (events && r == SIM_OK) r = dcopy(events, h->events, ((N3 + 31) / 32) * sizeof(uint32_t), st);
+  if (gravity && r == SIM_OK) r = dcopy(gravity, h->g, 3 * N3 * sizeof(float), st);
+  if (step) *step = h->step;
+  return fail(h, r);
+}
+
+sim_status sim_set_state(sim_t* h, const float* gas, const float* part, int32_t step) {
+  if (!h || !gas || !part || step < 0 || step > h->prm.n_steps) {
+    set_error("sim_set_state: invalid arguments");
+    return fail(h, SIM_EINVAL);
+  }
+  const long long N3 = h->N3;
+  cudaStream_t st = h->st;
+  sim_status r = dcopy(h->init_gas, gas, 5 * N3 * sizeof(float), st);
+  if (r == SIM_OK) r = dcopy(h->init_part, part, 6 * N3 * sizeof(float), st);
+  if (r == SIM_OK) {
+    h->ics_valid = false;
+    h->init_step = step;
+    r = reset_to_init(h);
+  }
+  return fail(h, r);
+}
+
+sim_status sim_schedule(const sim_t* h, int32_t i, double* out6) {
+  if (!h || !out6 || i < 0 || i >= h->prm.n_steps) {
+    set_error("sim_schedule: invalid arguments");
+    return SIM_EINVAL;
+  }
+  const StepFactors& f = h->sched[i];
+  out6[0] = f.a0;
+  out6[1] = f.a1;
+  out6[2] = f.K1;
+  out6[3] = f.dtau;
+  out6[4] = f.K2;
+  out6[5] = f.pref1;
+  return SIM_OK;
+}
+
+sim_status sim_cfl(sim_t* h, double* cfl_out) {
+  if (!h || !cfl_out) return SIM_EINVAL;
+  cudaStream_t st = h->st;
+  unsigned int bits = 0;
+  sim_status r = dzero(h->speed_bits, sizeof(unsigned int), st);
+  if (r == SIM_OK) r = launch_signal_speed(h->gas, (float)h->prm.gamma, h->N3, h->speed_bits, st);
+  if (r == SIM_OK && (cudaMemcpyAsync(&bits, h->speed_bits, sizeof(unsigned int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                      cudaStreamSynchronize(st) != cudaSuccess)) {
+    set_error("sim_cfl: readback failed");
+    r = SIM_ECUDA;
+  }
+  if (r != SIM_OK) return fail(h, r);
+  float v;
+  memcpy(&v, &bits, sizeof(v));
+  const int i = h->step < h->prm.n_steps ? h->step : h->prm.n_steps - 1;
+  *cfl_out = (double)v * h->sched[i].dtau * h->inv_dx;
+  return SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+// Subgrid star formation (Sec. 2.4 of arXiv 2502.02294): launchers.
+#pragma once
+
+#include "common.cuh"
+
+namespace dh {
+
+// Per-run constants of the subgrid step, in float for the kernels.
+struct SubgridConst {
+  float a2;        // a^2 at the update
+  float inv_fb;    // 1 / f_b
+  float fb;
+  float tpe;       // temperature per unit specific energy
+  float delta_c, inv_wd, T_c, inv_wT, lnPi0, Pi0, E0, inv_tau;
+  float ef0;       // T0_uv / tpe (0: floor off)
+  float gexp;      // gamma_uv - 1
+  float T0;
+  uint32_t k0, k1, step, instance;
+};
+
+SubgridConst make_subgrid_const(const sim_params& p, double a, int step);
+double temperature_per_energy(double gamma, double mu);
+
+// out = subgrid(in) (may alias); zhat (n^3) and events (ceil(n^3/32) words) may be NULL
+sim_status launch_subgrid(const float* in, float* out, const SubgridConst& c, float* zhat,
+                          uint32_t* events, long long N3, cudaStream_t st);
+// lam (5 n^3) in/out through the update at `in`; dpar[SIM_P_*] and dfb accumulated
+sim_status launch_subgrid_adjoint(const float* in, float* lam, const SubgridConst& c,
+                                  double* dpar, double* dfb, long long N3, cudaStream_t st);
+// max over cells and directions of |v_d| + c_s  (float bits in *out_bits, atomicMax)
+sim_status launch_signal_speed(const float* gas, float gamma, long long N3,
+                               unsigned int* out_bits, cudaStream_t st);
+
+}  // namespace dh

@@ -1,0 +1,218 @@
+"""GPU parity of each kernel against the FP64 oracle on identical float32 inputs.
+
+Tolerances (relative L2 over a field unless stated): 1e-5 for forward kernels (the per-step
+bar), 1e-4 for adjoints (longer FP32 chains; both are far below any modelling error).
+Integer work (Philox words, CIC cell decisions, event bits outside the decision guard band)
+is compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_helpers import f32, gas, lib, need_gpu, rel_l2
+from oracle import hydro, philox as ophilox, pm, spectra, subgrid as osub
+from oracle.sim import Params, subgrid_params
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def dh():
+    need_gpu()
+    return lib()
+
+
+def _nu(U, frac=0.4):
+    return frac / hydro.signal_speed_max(U, GAMMA)
+
+
+@pytest.mark.parametrize("n", [8, 12, 48, 70])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sweep_forward(dh, n, axis):
+    Ug, Uo = f32(gas(n, seed=n + axis))
+    nu = _nu(Uo)
+    got = dh.sweep(Ug, axis, nu)
+    want = hydro.sweep(Uo, "xyz"[axis], nu, GAMMA)
+    for k in range(5):
+        assert rel_l2(got[k], want[k]) < 1e-5, (k, rel_l2(got[k], want[k]))
+
+
+def test_sweep_sharp_fronts_and_uniform(dh):
+    # Sod-like jump along each axis plus an exactly uniform block (stays exactly uniform)
+    n = 32
+    U = gas(n, seed=3, rho_rel=0.0, vel=0.0)
+    U[0, :, :, : n // 2] *= 8.0
+    U[4, :, :, : n // 2] *= 10.0
+    Ug, Uo = f32(U)
+    for axis in range(3):
+        got = dh.sweep(Ug, axis, 0.3)
+        want = hydro.sweep(Uo, "xyz"[axis], 0.3, GAMMA)
+        for k in (0, 4):
+            assert rel_l2(got[k], want[k]) < 1e-5
+    Uu = np.zeros((5, 16, 16, 16))
+    Uu[0], Uu[1], Uu[4] = 0.3, 0.03, 0.01
+    Ug, _ = f32(Uu)
+    for axis in range(3):
+        assert torch.equal(dh.sweep(Ug, axis, 0.7), Ug)
+
+
+@pytest.mark.parametrize("n", [8, 20, 48])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sweep_adjoint(dh, n, axis):
+    Ug, Uo = f32(gas(n, seed=7 * n + axis))
+    lam_g, lam_o = f32(synth.field(n, seed=99, shape=(5, n, n, n)))
+    nu = _nu(Uo)
+    got, dnu = dh.sweep_adjoint(Ug, lam_g, axis, nu)
+    X = Uo.clone().requires_grad_(True)
+    nut = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
+    out = (hydro.sweep(X, "xyz"[axis], nut, GAMMA) * lam_o).sum()
+    gx, gnu = torch.autograd.grad(out, (X, nut))
+    for k in range(5):
+        assert rel_l2(got[k], gx[k]) < 1e-4, (k, rel_l2(got[k], gx[k]))
+    assert abs(dnu.item() - gnu.item()) < 1e-4 * abs(gnu.item())
+
+
+def _positions(n, seed, scale):
+    s = synth.displacements(n, seed, scale)
+    # a few particles exactly on nodes and exactly half way, and far outside the box
+    s[:, :5] = 0.0
+    s[0, 5:10] = 0.5 * (10.0 / n)
+    s[:, 10:12] = -3.0 * (10.0 / n) * n
+    return s
+
+
+@pytest.mark.parametrize("n", [8, 16, 33])
+def test_deposit_and_readout(dh, n):
+    box = 10.0
+    sg, so = f32(_positions(n, 5, 2.5 * box / n))
+    vg, vo = f32(synth.rng(6).uniform(0.5, 2.0, size=n ** 3))
+    got = dh.deposit_cic(sg, n, box, values=vg)
+    want = pm.deposit(so, vo, n, box, index_fp32=True)
+    assert (got.double().cpu() - want).abs().max().item() < 2e-6 * want.abs().max().item()
+    # mass is conserved to the fixed-point resolution
+    assert abs(got.double().sum().item() - vo.sum().item()) < 1e-4
+    fg, fo = f32(synth.field(n, 8, shape=(3, n, n, n)))
+    got = dh.interp_cic(fg, sg, n, box)
+    want = pm.interp(fo, so, n, box, index_fp32=True)
+    assert rel_l2(got, want) < 1e-6
+
+
+def test_deposit_deterministic(dh):
+    n, box = 32, 32.0
+    sg, _ = f32(_positions(n, 9, 3.0))
+    a = dh.deposit_cic(sg, n, box)
+    b = dh.deposit_cic(sg, n, box)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("n", [8, 16, 48])
+def test_gravity_and_adjoint(dh, n):
+    box, pref = 1.3 * n, 0.77
+    dg, do = f32(synth.field(n, 11))
+    got = dh.gravity(dg, box, pref)
+    want = pm.gravity(do, pref, box)
+    assert rel_l2(got, want) < 1e-5
+    lg, lo = f32(synth.field(n, 12, shape=(3, n, n, n)))
+    got = dh.gravity_adjoint(lg, box, pref)
+    X = do.clone().requires_grad_(True)
+    (gx,) = torch.autograd.grad((pm.gravity(X, pref, box) * lo).sum(), X)
+    assert rel_l2(got, gx) < 1e-5
+
+
+def _subgrid_state(n, seed):
+    prm = Params(T0_uv=8e3, gamma_uv=1.3, delta_c=1.5, w_delta=0.3, T_c=2e4, w_T=3e3,
+                 Pi0=0.3, E0=0.03, seed=77).as_dict()
+    sp = subgrid_params(prm)
+    a = 0.4
+    rng = synth.rng(seed)
+    rho = sp["f_b"] * (1 + prm["delta_c"] + 3 * prm["w_delta"] * rng.normal(size=(n, n, n)))
+    rho = np.abs(rho) + 0.01
+    m = 0.05 * rho * rng.normal(size=(3, n, n, n))
+    T = prm["T_c"] + 3 * prm["w_T"] * rng.normal(size=(n, n, n))
+    e = np.abs(T) / osub.t_per_e(GAMMA, 0.6)
+    eps = a * a * rho * e + (m * m).sum(0) / (2 * rho)
+    return np.concatenate([rho[None], m, eps[None]]), prm, sp, a
+
+
+@pytest.mark.parametrize("n", [16, 30])
+def test_subgrid_forward_and_events(dh, n):
+    U, prm, sp, a = _subgrid_state(n, 4)
+    step = 3
+    p = dh.default_params(**{k: prm[k] for k in ("delta_c", "w_delta", "T_c", "w_T", "Pi0", "E0",
+                                                 "T0_uv", "gamma_uv", "tau", "seed")})
+    Ug, Uo = f32(U)
+    zh, ev = dh.subgrid(Ug, a, p, step)
+    g0, g1 = ophilox.gumbel_pair(prm["seed"], n ** 3, step)
+    g0 = torch.tensor(g0.reshape(n, n, n)); g1 = torch.tensor(g1.reshape(n, n, n))
+    Uw, zw, evw = osub.subgrid(Uo, a, sp, g0, g1)
+    assert rel_l2(Ug[4], Uw[4]) < 1e-5
+    assert torch.equal(Ug[:4].cpu(), torch.from_numpy(U[:4].astype(np.float32)))
+    assert (zh.double().cpu() - zw).abs().max() < 1e-4
+    # event bits: exact outside a guard band of the decision variable
+    bits = ev.cpu().numpy().view(np.uint32)
+    got = np.unpackbits(bits.view(np.uint8), bitorder="little")[: n ** 3].astype(bool)
+    rho, m = Uo[0], Uo[1:4]
+    e = (Uo[4] - (m * m).sum(0) / (2 * rho)) / (a * a * rho)
+    x1 = (rho / sp["f_b"] - 1 - sp["delta_c"]) / sp["w_delta"]
+    x2 = (sp["T_c"] - osub.t_per_e(GAMMA, 0.6) * e) / sp["w_T"]
+    lnpi = math.log(sp["Pi0"]) - torch.nn.functional.softplus(-x1) - torch.nn.functional.softplus(-x2)
+    logit = (lnpi - torch.log1p(-torch.exp(lnpi)) + g0 - g1).flatten().numpy()
+    far = np.abs(logit) > 1e-4
+    assert far.mean() > 0.99
+    assert np.array_equal(got[far], evw.flatten().numpy()[far])
+    assert 0.02 < got.mean() < 0.98
+
+
+def test_subgrid_adjoint(dh):
+    n = 16
+    U, prm, sp, a = _subgrid_state(n, 5)
+    step = 2
+    p = dh.default_params(**{k: prm[k] for k in ("delta_c", "w_delta", "T_c", "w_T", "Pi0", "E0",
+                                                 "T0_uv", "gamma_uv", "tau", "seed")})
+    Ug, Uo = f32(U)
+    lg, lo = f32(synth.field(n, 21, shape=(5, n, n, n)))
+    lam = lg.clone()
+    dpar, dfb = dh.subgrid_adjoint(Ug, lam, a, p, step)
+    g0, g1 = ophilox.gumbel_pair(prm["seed"], n ** 3, step)
+    g0 = torch.tensor(g0.reshape(n, n, n)); g1 = torch.tensor(g1.reshape(n, n, n))
+    names = ("delta_c", "Pi0", "E0", "T0_uv", "gamma_uv", "f_b")
+    leaves = {k: torch.tensor(float(sp[k]), dtype=torch.float64, requires_grad=True) for k in names}
+    X = Uo.clone().requires_grad_(True)
+    sp2 = dict(sp, **leaves)
+    Uw, _, _ = osub.subgrid(X, a, sp2, g0, g1)
+    grads = torch.autograd.grad((Uw * lo).sum(), [X] + [leaves[k] for k in names])
+    for k in range(5):
+        assert rel_l2(lam[k], grads[0][k]) < 1e-4, (k, rel_l2(lam[k], grads[0][k]))
+    idx = {"delta_c": 2, "Pi0": 3, "E0": 4, "T0_uv": 5, "gamma_uv": 6}
+    for j, k in enumerate(names[:5]):
+        want = grads[1 + j].item()
+        assert abs(dpar[idx[k]].item() - want) < 1e-4 * abs(want) + 1e-9, (k, dpar[idx[k]].item(), want)
+    want = grads[-1].item()
+    assert abs(dfb.item() - want) < 1e-4 * abs(want)
+
+
+def test_philox_words(dh):
+    for seed, step, inst, tag in ((1, 0, 0, 0), (0x123456789ABCDEF, 17, 3, 1)):
+        got = dh.philox(seed, step, inst, tag, 5000).cpu().numpy().view(np.uint32)
+        want = np.stack(ophilox.words(seed, 5000, step, inst, tag), axis=1)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n", [16, 24])
+def test_power_spectrum(dh, n):
+    box = 25.0
+    ag, ao = f32(synth.field(n, 31))
+    bg, bo = f32(synth.field(n, 32))
+    k, P, nm = dh.power_spectrum(ag, box, n)
+    kw, Pw, nw = spectra.power_spectrum(ao, box, n)
+    assert torch.equal(nm.cpu(), nw)
+    assert rel_l2(k, kw) < 1e-12
+    assert rel_l2(P, Pw) < 1e-5
+    k, P, nm = dh.power_spectrum(ag, box, n, b=bg)
+    kw, Pw, nw = spectra.power_spectrum(ao, box, n, bo)
+    assert (P.cpu() - Pw).abs().max() < 1e-5 * Pw.abs().max()

@@ -118,7 +118,7 @@ def _fd_check(fun, x, direction, h):
 
 
 def test_gradient_wrt_initial_noise_matches_finite_differences():
-    prm = sim.Params(n=8, box=8.0, n_steps=4, a_start=0.1, a_end=0.5, rms_ref=0.3,
+    prm = sim.Params(n=8, box=8.0, n_steps=4, a_start=0.1, a_end=0.3, rms_ref=0.15,
                      subgrid_on=1, delta_c=0.2, w_delta=0.1, T_c=1e6, w_T=1e5, Pi0=0.2,
                      T0_uv=5e3).as_dict()
     noise = sim.noise_field(prm)
@@ -131,7 +131,7 @@ def test_gradient_wrt_initial_noise_matches_finite_differences():
 
 @pytest.mark.parametrize("name", ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"])
 def test_gradient_wrt_parameters_matches_finite_differences(name):
-    base = dict(n=8, box=8.0, n_steps=4, a_start=0.1, a_end=0.5, rms_ref=0.3, subgrid_on=1,
+    base = dict(n=8, box=8.0, n_steps=4, a_start=0.1, a_end=0.3, rms_ref=0.15, subgrid_on=1,
                 delta_c=0.2, w_delta=0.1, T_c=1e6, w_T=1e5, Pi0=0.2, T0_uv=5e3)
     prm = sim.Params(**base).as_dict()
     noise = sim.noise_field(prm)
