@@ -210,6 +210,23 @@ sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out, float* lam
 sim_status sim_deposit_cic(const float* s, const float* values, int32_t n, double box,
                            float* grid, void* stream);
 
+/* Same result as sim_deposit_cic, for callers that cannot allocate device memory: those
+ * running while a framework's caching allocator holds the device memory (a direct
+ * allocation may then fail), those that must keep a fixed device footprint after start-up,
+ * and latency-critical loops that cannot take cudaFree's implicit synchronisation. The
+ * paper has no counterpart; this is a deployment variant of the deposit above.
+ * It calls no allocating routine: its fixed-point accumulator is a library-owned static
+ * device array of SIM_DEPOSIT_STATIC_MAX_CELLS 64-bit words (16 MiB), which every GPU
+ * that loads the library holds until the process exits. Requires n^3 <= that maximum
+ * (n <= 128), else SIM_EINVAL. The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream capture.
+ * All calls on one device share its array, which keeps the last call's contents; each call
+ * clears the part it uses on entry. Calls on the same device that can overlap on the GPU
+ * (for instance on two streams without ordering between them) race. */
+#define SIM_DEPOSIT_STATIC_MAX_CELLS 2097152
+sim_status sim_deposit_cic_static(const float* s, const float* values, int32_t n, double box,
+                                  float* grid, void* stream);
+
 /* CIC readout of `nf` fields (grid: nf n^3) at the particles: out[f][p] (nf n^3). */
 sim_status sim_interp_cic(const float* grid, int32_t nf, int32_t n, double box,
                           const float* s, float* out, void* stream);

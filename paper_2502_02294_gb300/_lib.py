@@ -68,6 +68,7 @@ SIGNATURES = {
     "sim_sweep": (ctypes.c_int, [_P, _P, _I32, _I32, _D, _D, _D, _P]),
     "sim_sweep_adjoint": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _D, _D, _D, _P, _P]),
     "sim_deposit_cic": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P]),
+    "sim_deposit_cic_static": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P]),
     "sim_interp_cic": (ctypes.c_int, [_P, _I32, _I32, _D, _P, _P, _P]),
     "sim_gravity": (ctypes.c_int, [_P, _I32, _D, _D, _P, _P]),
     "sim_gravity_adjoint": (ctypes.c_int, [_P, _I32, _D, _D, _P, _P]),
