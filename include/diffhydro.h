@@ -127,6 +127,14 @@ sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t
 /* Free the handle and its device memory (synchronises its stream). NULL is ignored. */
 void sim_destroy(sim_t* h);
 
+/* on != 0: sim_run and sim_run_adjoint are captured into CUDA graphs the first time they
+ * are called with a given argument set from a given handle state, and replayed afterwards
+ * (launch overhead of the ~50 kernels per step removed). Capture happens on a private
+ * stream ordered after the handle's stream; replays run on the handle's stream. Graphs
+ * keep the argument pointers they were captured with. Not used when cfl_max > 0.
+ * on == 0 drops all graphs. Default off. */
+sim_status sim_set_graphs(sim_t* h, int32_t on);
+
 /* Advance one step a_n -> a_{n+1}: half kick (DM + gas), DM drift, three Strang-ordered
  * hydro sweeps (order XYZ, ZYX, ZXY, YXZ, YZX, XZY by n mod 6, Sec. 2.3.2), subgrid,
  * CIC deposit + Poisson (Sec. 2.2), half kick. Keeps a copy of the step's input state

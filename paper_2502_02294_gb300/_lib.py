@@ -54,6 +54,7 @@ SIGNATURES = {
     "sim_kernel_launches": (ctypes.c_int64, []),
     "sim_init": (ctypes.c_int, [_PP, _P, _P, ctypes.POINTER(_P)]),
     "sim_destroy": (None, [_P]),
+    "sim_set_graphs": (ctypes.c_int, [_P, _I32]),
     "sim_step": (ctypes.c_int, [_P]),
     "sim_step_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "sim_run": (ctypes.c_int, [_P, _I32]),

@@ -71,15 +71,19 @@ enum { TAG_IC_NOISE = 0, TAG_SUBGRID = 1 };
 // Flux split of one cell for a sweep whose momentum component is u[f] (f = 1 + axis):
 //   v = m_f / rho, P = (gamma-1)(eps - |m|^2/(2 rho)), c = |v| + sqrt(max(gamma P/rho, 0))
 //   F = (m_f, m_x v, m_y v, m_z v, (eps+P) v) + P e_f,  F^R = (cU + F)/2, F^L = (cU - F)/2.
+// Reciprocal and square root use the SFU approximations (about 1 ulp), far below the
+// float32 round-off that accumulates over a sweep.
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+
 __device__ __forceinline__ void split_flux(const float u[5], int f, float gam, float FR[5],
                                            float FL[5]) {
-  const float inv = 1.0f / u[0];
+  const float inv = fast_rcp(u[0]);
   const float md = u[f];
   const float v = md * inv;
   const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   const float P = (gam - 1.0f) * (u[4] - 0.5f * m2 * inv);
   const float cs2 = gam * P * inv;
-  const float c = fabsf(v) + (cs2 > 0.0f ? sqrtf(cs2) : 0.0f);
+  const float c = fabsf(v) + (cs2 > 0.0f ? cs2 * rsqrtf(cs2) : 0.0f);
   float F[5];
   F[0] = md;
   F[1] = u[1] * v;
@@ -100,14 +104,14 @@ __device__ __forceinline__ void split_flux(const float u[5], int f, float gam, f
 __device__ __forceinline__ void split_flux_vjp(const float u[5], int f, float gam,
                                                const float lR[5], const float lL[5],
                                                float lu[5]) {
-  const float rho = u[0];
-  const float inv = 1.0f / rho;
+  const float inv = fast_rcp(u[0]);
   const float md = u[f];
   const float v = md * inv;
   const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   const float P = (gam - 1.0f) * (u[4] - 0.5f * m2 * inv);
   const float cs2 = gam * P * inv;
-  const float cs = cs2 > 0.0f ? sqrtf(cs2) : 0.0f;
+  const float rcs = cs2 > 0.0f ? rsqrtf(cs2) : 0.0f;
+  const float cs = cs2 * rcs;
   const float c = fabsf(v) + cs;
   float sig[5], del[5];
 #pragma unroll
@@ -133,11 +137,11 @@ __device__ __forceinline__ void split_flux_vjp(const float u[5], int f, float ga
   lu[4] += del[4] * v;  // F4 = (eps + P) v
   lP += del[4] * v;
   lv += del[4] * (u[4] + P);
-  // c = |v| + cs
+  // c = |v| + cs, cs = sqrt(gam P / rho): dcs/dP = gam/(2 cs rho), dcs/drho = -cs/(2 rho)
   lv += lc * (float)((v > 0.0f) - (v < 0.0f));
-  if (cs > 0.0f) {
-    lP += lc * gam / (2.0f * cs * rho);
-    lrho -= lc * cs / (2.0f * rho);
+  if (cs2 > 0.0f) {
+    lP += lc * 0.5f * gam * rcs * inv;
+    lrho -= lc * 0.5f * cs * inv;
   }
   // P = (gam-1)(eps - m2/(2 rho))
   const float gP = (gam - 1.0f) * lP;
@@ -155,7 +159,7 @@ __device__ __forceinline__ void split_flux_vjp(const float u[5], int f, float ga
 __device__ __forceinline__ float vanleer(float a, float b, float eps) {
   const float ab = a * b;
   const float s = a + b;
-  return ab > 0.0f ? 2.0f * ab / (s + copysignf(eps, s)) : 0.0f;
+  return ab > 0.0f ? __fdividef(2.0f * ab, s + copysignf(eps, s)) : 0.0f;
 }
 
 __device__ __forceinline__ void vanleer_grad(float a, float b, float eps, float& da,
@@ -164,7 +168,8 @@ __device__ __forceinline__ void vanleer_grad(float a, float b, float eps, float&
   if (ab > 0.0f) {
     const float s = a + b;
     const float D = s + copysignf(eps, s);
-    const float i2 = 1.0f / (D * D);
+    const float iD = fast_rcp(D);
+    const float i2 = iD * iD;
     da = 2.0f * b * (D - a) * i2;
     db = 2.0f * a * (D - b) * i2;
   } else {
@@ -174,27 +179,36 @@ __device__ __forceinline__ void vanleer_grad(float a, float b, float eps, float&
 }
 
 // ------------------------------------------------------------------ reductions
-__device__ __forceinline__ double warp_sum(double v) {
+// Per-thread partial sums stay in float32 (GB300's FP64 rate is a small fraction of FP32);
+// each block converts its float32 total once and adds it to a double accumulator.
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Block-wide sum of one double per thread, added atomically to *out by thread 0.
-// Requires blockDim.x * blockDim.y a multiple of 32 and <= 1024.
-__device__ __forceinline__ void block_sum_atomic(double v, double* out) {
-  __shared__ double red[32];
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nt = blockDim.x * blockDim.y;
+// Block-wide sum of one float per thread, added atomically (as double) to *out by one
+// thread. All threads of the block must call it; blockDim a multiple of 32, <= 1024.
+__device__ __forceinline__ void block_sum_atomic(float v, double* out) {
+  __shared__ float red[32];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
   v = warp_sum(v);
   __syncthreads();
   if ((tid & 31) == 0) red[tid >> 5] = v;
   __syncthreads();
   if (tid < 32) {
-    double w = (tid < (nt >> 5)) ? red[tid] : 0.0;
+    float w = (tid < (nt >> 5)) ? red[tid] : 0.0f;
     w = warp_sum(w);
-    if (tid == 0 && w != 0.0) atomicAdd(out, w);
+    if (tid == 0 && w != 0.0f) atomicAdd(out, (double)w);
   }
+}
+
+// periodic wrap of an index known to lie within a few periods of [0, n)
+__device__ __forceinline__ int wrap_periodic(int i, int n) {
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
 }
 
 }  // namespace dh

@@ -1,11 +1,11 @@
 // Relaxing TVD sweep (Sec. 2.3.1-2.3.2 of arXiv 2502.02294) and its adjoint.
 //
-// One CTA owns a tile of S output cells along the sweep axis times W lines. It stages the
-// tile plus a halo (3 cells per side forward, 5 adjoint) of the 5 gas fields in shared
-// memory, and computes both RK2 stages there, so each global cell is read once per tile
-// and written once. For the y and z sweeps the W lines are W consecutive x cells (128-byte
-// coalesced rows); for the x sweep the lines are W consecutive y rows, each read as a
-// contiguous segment.
+// One CTA owns a tile of S output cells along the sweep axis times W lines. It reads the
+// tile plus a halo (3 cells per side forward, 5 adjoint) once from global memory into
+// registers, keeps the per-cell flux splits and the per-face fluxes in shared memory, and
+// evaluates every flux split and every limited face flux exactly once per tile cell. For
+// the y and z sweeps the W lines are W consecutive x cells (128-byte rows per warp load);
+// for the x sweep the lines are W consecutive y rows read as contiguous segments.
 //
 //   half step  (Eq. TVD_halfstep):  Uh_i = U_i - nu/2 (F_{i+1/2} - F_{i-1/2}),
 //              F_{i+1/2} = F^R_i - F^L_{i+1}  (first-order upwind of the relaxed fluxes)
@@ -33,21 +33,32 @@ struct TileGeom {
   __device__ static __forceinline__ int w_of(int c) { return AXIS == 0 ? c / SP : c % W; }
 };
 
-// tile shapes: x sweep 64 x 4 lines, y/z sweeps 16 x 32 lines
+// tile shapes (forward / adjoint): x sweep 64 x 4 lines, y/z sweeps 32 x 32 and 16 x 32
 template <int AXIS> struct SweepCfg;
-template <> struct SweepCfg<0> { static constexpr int S = 64, W = 4, NT = 128; };
-template <> struct SweepCfg<1> { static constexpr int S = 16, W = 32, NT = 256; };
-template <> struct SweepCfg<2> { static constexpr int S = 16, W = 32, NT = 256; };
+template <> struct SweepCfg<0> { static constexpr int S = 64, W = 4, NT = 128, SA = 64, WA = 4, NTA = 128; };
+template <> struct SweepCfg<1> { static constexpr int S = 32, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
+template <> struct SweepCfg<2> { static constexpr int S = 32, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
+
+// limited second-order face flux at face c+1/2 from the half-step splits R = Fh^R, L = Fh^L
+__device__ __forceinline__ float face_flux(const float* R, const float* L, int DS, float eps) {
+  const float Rm1 = R[-DS], R0 = R[0], Rp1 = R[DS];
+  const float L0 = L[0], Lp1 = L[DS], Lp2 = L[2 * DS];
+  const float fr = R0 + vanleer(0.5f * (R0 - Rm1), 0.5f * (Rp1 - R0), eps);
+  const float fl = Lp1 - vanleer(0.5f * (Lp1 - L0), 0.5f * (Lp2 - Lp1), eps);
+  return fr - fl;
+}
 
 template <int AXIS>
-__global__ void __launch_bounds__(SweepCfg<AXIS>::NT)
+__global__ void __launch_bounds__(SweepCfg<AXIS>::NT, 2)
 sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, float nu,
                  float gam, float eps) {
   constexpr int S = SweepCfg<AXIS>::S, W = SweepCfg<AXIS>::W, NT = SweepCfg<AXIS>::NT;
   using G = TileGeom<AXIS, S, W, 3>;
   constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
   constexpr int F = 1 + AXIS;
-  extern __shared__ float sf[];  // 10 NC: F^R, F^L of U, then of Uh (U stays in registers)
+  extern __shared__ float sm[];
+  float* sf = sm;            // 10 NC: F^R, F^L of U, then of Uh
+  float* sg = sm + 10 * NC;  // 5 NC: limited face fluxes (face c+1/2 at c)
   const long long N3 = (long long)n * n * n;
   const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z;
 
@@ -57,11 +68,10 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
     const int c = threadIdx.x + i * NT;
     if (c < NC) {
       const int s = G::s_of(c), w = G::w_of(c), wg = w0 + w;
-      int sg = (s0 + s - 3) % n;
-      if (sg < 0) sg += n;
+      const int sgl = wrap_periodic(s0 + s - 3, n);
       float u[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
       if (wg < n) {
-        const long long o = goff<AXIS>(sg, wg, t, n);
+        const long long o = goff<AXIS>(sgl, wg, t, n);
 #pragma unroll
         for (int k = 0; k < 5; ++k) u[k] = __ldg(uin + k * N3 + o);
       }
@@ -106,26 +116,97 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
     }
   }
   __syncthreads();
+  // faces c+1/2 for s in [2, S+3): each computed once
+#pragma unroll
+  for (int i = 0; i < CPT; ++i) {
+    const int c = threadIdx.x + i * NT;
+    const int s = G::s_of(c);
+    if (c < NC && s >= 2 && s < S + 3) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        sg[k * NC + c] = face_flux(sf + k * NC + c, sf + (5 + k) * NC + c, DS, eps);
+    }
+  }
+  __syncthreads();
 #pragma unroll
   for (int i = 0; i < CPT; ++i) {
     const int c = threadIdx.x + i * NT;
     const int s = G::s_of(c), w = G::w_of(c);
-    const int sg = s0 + s - 3, wg = w0 + w;
-    if (c < NC && s >= 3 && s < S + 3 && sg < n && wg < n) {
-      const long long o = goff<AXIS>(sg, wg, t, n);
+    const int sgl = s0 + s - 3, wg = w0 + w;
+    if (c < NC && s >= 3 && s < S + 3 && sgl < n && wg < n) {
+      const long long o = goff<AXIS>(sgl, wg, t, n);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const float* R = sf + k * NC + c;
-        const float* L = sf + (5 + k) * NC + c;
-        const float Rm2 = R[-2 * DS], Rm1 = R[-DS], R0 = R[0], Rp1 = R[DS];
-        const float Lm1 = L[-DS], L0 = L[0], Lp1 = L[DS], Lp2 = L[2 * DS];
-        const float frp = R0 + vanleer(0.5f * (R0 - Rm1), 0.5f * (Rp1 - R0), eps);
-        const float flp = Lp1 - vanleer(0.5f * (Lp1 - L0), 0.5f * (Lp2 - Lp1), eps);
-        const float frm = Rm1 + vanleer(0.5f * (Rm1 - Rm2), 0.5f * (R0 - Rm1), eps);
-        const float flm = L0 - vanleer(0.5f * (L0 - Lm1), 0.5f * (Lp1 - L0), eps);
-        uout[k * N3 + o] = ureg[i][k] - nu * ((frp - flp) - (frm - flm));
-      }
+      for (int k = 0; k < 5; ++k)
+        uout[k * N3 + o] = ureg[i][k] - nu * (sg[k * NC + c] - sg[k * NC + c - DS]);
     }
+  }
+}
+
+// ------------------------------------------------------------- forward, marching form
+// Each thread owns one line and a segment of L output cells along the sweep axis. It loads
+// the segment plus 3 halo cells per side in order and keeps a sliding window in registers:
+// at load j it forms the first-order face j-1/2, the half-step state Uh_{j-1} and its
+// splits, the limited face (j-3)+1/2 and the output U'_{j-3}. No shared memory, no
+// barriers; adjacent threads own adjacent lines (x for the y/z sweeps, y for x).
+template <int AXIS, int L>
+__global__ void __launch_bounds__(128)
+sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, float nu,
+                   float gam, float eps) {
+  constexpr int F = 1 + AXIS;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;  // line coordinate
+  const int t = blockIdx.y;                             // third coordinate
+  const int s0 = blockIdx.z * L;
+  if (w >= n) return;
+  const long long N3 = (long long)n * n * n;
+  const float hnu = 0.5f * nu;
+  float Ua[5], Ub[5], Uc[5];      // U_{j-3}, U_{j-2}, U_{j-1}
+  float FRp[5], f1m[5];           // F^R_{j-1}, first-order face (j-3/2)
+  float R0[5], R1[5], R2[5];      // Fh^R_{j-4..j-2}
+  float L0[5], L1[5];             // Fh^L_{j-3..j-2}
+  float F2m[5];                   // limited face (j-4)+1/2
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float init = (k == 0 || k == 4) ? 1.0f : 0.0f;
+    Ua[k] = Ub[k] = Uc[k] = init;
+    FRp[k] = f1m[k] = R0[k] = R1[k] = R2[k] = L0[k] = L1[k] = F2m[k] = 0.0f;
+  }
+  int j = wrap_periodic(s0 - 3, n);
+#pragma unroll 1
+  for (int it = 0; it < L + 6; ++it) {
+    const long long o = goff<AXIS>(j, w, t, n);
+    float u[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) u[k] = __ldg(uin + k * N3 + o);
+    float FR[5], FL[5];
+    split_flux(u, F, gam, FR, FL);
+    float f1[5], uh[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      f1[k] = FRp[k] - FL[k];                 // face j-1/2
+      uh[k] = Uc[k] - hnu * (f1[k] - f1m[k]);  // Uh_{j-1}
+    }
+    float FRh[5], FLh[5];
+    split_flux(uh, F, gam, FRh, FLh);
+    const int jo = s0 + it - 6;  // output cell j-3 (unwrapped)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float fr = R1[k] + vanleer(0.5f * (R1[k] - R0[k]), 0.5f * (R2[k] - R1[k]), eps);
+      const float fl = L1[k] - vanleer(0.5f * (L1[k] - L0[k]), 0.5f * (FLh[k] - L1[k]), eps);
+      const float F2 = fr - fl;               // face (j-3)+1/2
+      if (it >= 6 && jo < n) uout[k * N3 + goff<AXIS>(jo, w, t, n)] = Ua[k] - nu * (F2 - F2m[k]);
+      F2m[k] = F2;
+      Ua[k] = Ub[k];
+      Ub[k] = Uc[k];
+      Uc[k] = u[k];
+      FRp[k] = FR[k];
+      f1m[k] = f1[k];
+      R0[k] = R1[k];
+      R1[k] = R2[k];
+      R2[k] = FRh[k];
+      L0[k] = L1[k];
+      L1[k] = FLh[k];
+    }
+    j = (j + 1 == n) ? 0 : j + 1;
   }
 }
 
@@ -135,19 +216,20 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
 // lamUh_j = VJP_{F^R,F^L}(Uh_j; lamFh^R_j, lamFh^L_j) gathered from the limited faces
 // t+1/2 (t = j-2 .. j+1) whose adjoint is nu (lam_out_{t+1} - lam_out_t). Output cells need
 // U on a 5-cell halo and lam_out on a 3-cell halo; the forward stages are recomputed.
+// d(out)/d(nu) = -(F2_+ - F2_-) - nu dF2/dUh . (F_{+} - F_{-})/2 is accumulated into *dnu.
 template <int AXIS>
-__global__ void __launch_bounds__(SweepCfg<AXIS>::NT)
+__global__ void __launch_bounds__(SweepCfg<AXIS>::NTA, 2)
 sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                  float* __restrict__ lin, int n, float nu, float gam, float eps,
                  double* __restrict__ dnu) {
-  constexpr int S = SweepCfg<AXIS>::S, W = SweepCfg<AXIS>::W, NT = SweepCfg<AXIS>::NT;
+  constexpr int S = SweepCfg<AXIS>::SA, W = SweepCfg<AXIS>::WA, NT = SweepCfg<AXIS>::NTA;
   using G = TileGeom<AXIS, S, W, 5>;
   constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
   constexpr int F = 1 + AXIS;
   extern __shared__ float sm[];
-  float* su = sm;            // 5 NC: Uh, then lamUh
-  float* sf = sm + 5 * NC;   // 10 NC: F^R,F^L of U, then of Uh
-  float* sl = sm + 15 * NC;  // 5 NC: lam_out
+  float* sf = sm;            // 10 NC: F^R,F^L of U, then of Uh
+  float* sl = sm + 10 * NC;  // 5 NC: lam_out
+  float* sh = sm + 15 * NC;  // 5 NC: lamUh
   const long long N3 = (long long)n * n * n;
   const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z;
 
@@ -157,12 +239,11 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
     const int c = threadIdx.x + i * NT;
     if (c < NC) {
       const int s = G::s_of(c), w = G::w_of(c), wg = w0 + w;
-      int sg = (s0 + s - 5) % n;
-      if (sg < 0) sg += n;
+      const int sgl = wrap_periodic(s0 + s - 5, n);
       float u[5] = {1.f, 0.f, 0.f, 0.f, 1.f};
       float l[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       if (wg < n) {
-        const long long o = goff<AXIS>(sg, wg, t, n);
+        const long long o = goff<AXIS>(sgl, wg, t, n);
 #pragma unroll
         for (int k = 0; k < 5; ++k) u[k] = __ldg(uin + k * N3 + o);
         if (s >= 2 && s < SP - 2) {
@@ -207,15 +288,14 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
       split_flux(uh[i], F, gam, FR, FL);
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
-        su[k * NC + c] = uh[i][k];
         sf[k * NC + c] = FR[k];
         sf[(5 + k) * NC + c] = FL[k];
       }
     }
   }
   __syncthreads();
-  double dnu_acc = 0.0;
-  // stage E: lamUh_j for j in [4, S+6)
+  float dnu_acc = 0.0f;
+  // lamUh_j for j in [4, S+6)
 #pragma unroll
   for (int i = 0; i < CPT; ++i) {
     const int c = threadIdx.x + i * NT;
@@ -232,9 +312,8 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
         const float lf_m1 = nu * (lo[0] - lo[-DS]);
         const float lf_0 = nu * (lo[DS] - lo[0]);
         const float lf_p1 = nu * (lo[2 * DS] - lo[DS]);
-        float da, db;
+        float da, db, acc;
         // right-moving: faces t = j-1, j, j+1
-        float acc;
         vanleer_grad(0.5f * (R[0] - R[-DS]), 0.5f * (R[DS] - R[0]), eps, da, db);
         acc = lf_0 * (1.0f + 0.5f * da - 0.5f * db);
         vanleer_grad(0.5f * (R[DS] - R[0]), 0.5f * (R[2 * DS] - R[DS]), eps, da, db);
@@ -253,43 +332,37 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
       }
       float luh[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       split_flux_vjp(uh[i], F, gam, lR, lL, luh);
-      const int sg = s0 + s - 5, wg = w0 + w;
-      if (s >= 5 && s < S + 5 && sg < n && wg < n) {
+      const int sgl = s0 + s - 5, wg = w0 + w;
+      if (s >= 5 && s < S + 5 && sgl < n && wg < n) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) dnu_acc -= 0.5 * (double)luh[k] * (double)df1[i][k];
+        for (int k = 0; k < 5; ++k) dnu_acc -= 0.5f * luh[k] * df1[i][k];
       }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) su[k * NC + c] = luh[k];
+      for (int k = 0; k < 5; ++k) sh[k * NC + c] = luh[k];
     }
   }
   __syncthreads();
-  // stage F: outputs s in [5, S+5)
+  // outputs s in [5, S+5)
 #pragma unroll
   for (int i = 0; i < CPT; ++i) {
     const int c = threadIdx.x + i * NT;
     const int s = G::s_of(c), w = G::w_of(c);
-    const int sg = s0 + s - 5, wg = w0 + w;
-    if (c < NC && s >= 5 && s < S + 5 && sg < n && wg < n) {
+    const int sgl = s0 + s - 5, wg = w0 + w;
+    if (c < NC && s >= 5 && s < S + 5 && sgl < n && wg < n) {
       float lR[5], lL[5], lu[5];
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
-        const float* lh = su + k * NC + c;
+        const float* lh = sh + k * NC + c;
         lR[k] = 0.5f * nu * (lh[DS] - lh[0]);
         lL[k] = -0.5f * nu * (lh[0] - lh[-DS]);
-        lu[k] = sl[k * NC + c] + lh[0];
-        // d u_out / d nu = -(F2_{+} - F2_{-})
-        const float* R = sf + k * NC + c;
-        const float* L = sf + (5 + k) * NC + c;
-        const float Rm2 = R[-2 * DS], Rm1 = R[-DS], R0 = R[0], Rp1 = R[DS];
-        const float Lm1 = L[-DS], L0 = L[0], Lp1 = L[DS], Lp2 = L[2 * DS];
-        const float frp = R0 + vanleer(0.5f * (R0 - Rm1), 0.5f * (Rp1 - R0), eps);
-        const float flp = Lp1 - vanleer(0.5f * (Lp1 - L0), 0.5f * (Lp2 - Lp1), eps);
-        const float frm = Rm1 + vanleer(0.5f * (Rm1 - Rm2), 0.5f * (R0 - Rm1), eps);
-        const float flm = L0 - vanleer(0.5f * (L0 - Lm1), 0.5f * (Lp1 - L0), eps);
-        dnu_acc -= (double)sl[k * NC + c] * (double)((frp - flp) - (frm - flm));
+        const float lo = sl[k * NC + c];
+        lu[k] = lo + lh[0];
+        const float fp = face_flux(sf + k * NC + c, sf + (5 + k) * NC + c, DS, eps);
+        const float fm = face_flux(sf + k * NC + c - DS, sf + (5 + k) * NC + c - DS, DS, eps);
+        dnu_acc -= lo * (fp - fm);
       }
       split_flux_vjp(ureg[i], F, gam, lR, lL, lu);
-      const long long o = goff<AXIS>(sg, wg, t, n);
+      const long long o = goff<AXIS>(sgl, wg, t, n);
 #pragma unroll
       for (int k = 0; k < 5; ++k) lin[k * N3 + o] = lu[k];
     }
@@ -297,12 +370,26 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
   if (dnu) block_sum_atomic(dnu_acc, dnu);
 }
 
+#ifndef DH_SWEEP_MARCH
+#define DH_SWEEP_MARCH 0
+#endif
+#ifndef DH_MARCH_L
+#define DH_MARCH_L 16
+#endif
+
 template <int AXIS>
 static sim_status launch_sweep_t(const float* uin, float* uout, int n, float nu, float gam,
                                  float eps, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
+  if (DH_SWEEP_MARCH == 2 || (DH_SWEEP_MARCH == 1 && AXIS != 0)) {
+    constexpr int L = DH_MARCH_L;
+    dim3 grid(cdiv(n, 128), n, cdiv(n, L));
+    sweep_march_kernel<AXIS, L><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps);
+    DH_LAUNCH_CHECK();
+    return SIM_OK;
+  }
   constexpr int NC = (C::S + 6) * C::W;
-  const size_t smem = 10 * NC * sizeof(float);
+  const size_t smem = 15 * NC * sizeof(float);
   static bool attr = false;
   if (!attr) {
     DH_CUDA_TRY(cudaFuncSetAttribute(sweep_fwd_kernel<AXIS>,
@@ -320,7 +407,7 @@ static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float*
                                      float nu, float gam, float eps, double* dnu,
                                      cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  constexpr int NC = (C::S + 10) * C::W;
+  constexpr int NC = (C::SA + 10) * C::WA;
   const size_t smem = 20 * NC * sizeof(float);
   static bool attr = false;
   if (!attr) {
@@ -328,10 +415,30 @@ static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float*
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n);
-  sweep_adj_kernel<AXIS><<<grid, C::NT, smem, st>>>(uin, lout, lin, n, nu, gam, eps, dnu);
+  dim3 grid(cdiv(n, C::SA), cdiv(n, C::WA), n);
+  sweep_adj_kernel<AXIS><<<grid, C::NTA, smem, st>>>(uin, lout, lin, n, nu, gam, eps, dnu);
   DH_LAUNCH_CHECK();
   return SIM_OK;
+}
+
+template <int AXIS>
+static sim_status set_sweep_attributes() {
+  using C = SweepCfg<AXIS>;
+  DH_CUDA_TRY(cudaFuncSetAttribute(sweep_fwd_kernel<AXIS>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(15 * (C::S + 6) * C::W * sizeof(float))));
+  DH_CUDA_TRY(cudaFuncSetAttribute(sweep_adj_kernel<AXIS>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(20 * (C::SA + 10) * C::WA * sizeof(float))));
+  return SIM_OK;
+}
+
+// Shared-memory limits of the sweep kernels, set on the current device before any launch
+// (and before any stream capture).
+sim_status prepare_sweep_kernels() {
+  DH_TRY(set_sweep_attributes<0>());
+  DH_TRY(set_sweep_attributes<1>());
+  return set_sweep_attributes<2>();
 }
 
 sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double nu,

@@ -103,7 +103,7 @@ __global__ void unplace_kernel(const float* __restrict__ f4, const float* __rest
                                float* __restrict__ lam4, float rp, float fb, float a2e0,
                                double* __restrict__ drp, double* __restrict__ dfb, long long N3) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double arp = 0.0, afb = 0.0;
+  float arp = 0.0f, afb = 0.0f;
   if (i < N3) {
     const float delta = f4[i];
     const float rho = fb * (1.0f + delta);
@@ -123,10 +123,10 @@ __global__ void unplace_kernel(const float* __restrict__ f4, const float* __rest
       const float lpj = lp ? lp[j * N3 + i] : 0.0f;
       const float lsj = ls ? ls[j * N3 + i] : 0.0f;
       lam4[(1 + j) * N3 + i] = lsj + rp * lpj + lm * rho * rp;
-      arp += (double)lpj * psi[j] + (double)lm * rho * psi[j];
+      arp += lpj * psi[j] + lm * rho * psi[j];
     }
     lam4[i] = fb * lrho;
-    afb = (double)lrho * (1.0 + (double)delta);
+    afb = lrho * (1.0f + delta);
   }
   block_sum_atomic(arp, drp);
   block_sum_atomic(afb, dfb);

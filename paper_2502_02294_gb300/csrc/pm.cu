@@ -94,82 +94,110 @@ static sim_status fft_exec_c2r(cufftHandle h, cufftComplex* in, float* out) {
 }
 
 // ------------------------------------------------------------------ CIC geometry
+// Particle kernels run on a 3-D grid: x = blockIdx.x * blockDim.x + threadIdx.x (lattice
+// q_x), y = blockIdx.y (q_y), z = blockIdx.z (q_z); no integer division is needed to
+// recover the lattice site. Node and particle indices are 32-bit (n <= 1024).
 struct Cic {
   int ix[2], iy[2], iz[2];
   float wx[2], wy[2], wz[2];
 };
-
-__device__ __forceinline__ int wrap(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
-}
 
 __device__ __forceinline__ void cic_axis(float s, int q, int n, float inv_dx, int* idx,
                                          float* w) {
   const float t = __fmul_rn(s, inv_dx);
   const float fl = floorf(t);
   const float f = t - fl;
-  const int b = wrap(q + (int)fl, n);
+  const int b = wrap_periodic(q + (int)fl, n);
   idx[0] = b;
   idx[1] = (b + 1 == n) ? 0 : b + 1;
   w[0] = 1.0f - f;
   w[1] = f;
 }
 
-__device__ __forceinline__ void cic_setup(const float* s, long long p, long long N3, int n,
-                                          float inv_dx, Cic& c) {
-  const int qx = (int)(p % n), qy = (int)((p / n) % n), qz = (int)(p / ((long long)n * n));
-  cic_axis(s[p], qx, n, inv_dx, c.ix, c.wx);
-  cic_axis(s[N3 + p], qy, n, inv_dx, c.iy, c.wy);
-  cic_axis(s[2 * N3 + p], qz, n, inv_dx, c.iz, c.wz);
+struct PIdx {
+  int qx, qy, qz, p;
+  bool ok;
+};
+
+__device__ __forceinline__ PIdx particle_index(int n) {
+  PIdx r;
+  r.qx = blockIdx.x * blockDim.x + threadIdx.x;
+  r.qy = blockIdx.y;
+  r.qz = blockIdx.z;
+  r.ok = r.qx < n;
+  r.p = (r.qz * n + r.qy) * n + r.qx;
+  return r;
 }
 
-__device__ __forceinline__ long long node(const Cic& c, int oz, int oy, int ox, int n) {
-  return ((long long)c.iz[oz] * n + c.iy[oy]) * n + c.ix[ox];
+static inline dim3 particle_grid(int n, int threads) { return dim3(cdiv(n, threads), n, n); }
+constexpr int kPT = 128;  // threads per particle block
+
+__device__ __forceinline__ void cic_setup(const float* s, const PIdx& q, int N3, int n,
+                                          float inv_dx, Cic& c) {
+  cic_axis(s[q.p], q.qx, n, inv_dx, c.ix, c.wx);
+  cic_axis(s[N3 + q.p], q.qy, n, inv_dx, c.iy, c.wy);
+  cic_axis(s[2 * N3 + q.p], q.qz, n, inv_dx, c.iz, c.wz);
+}
+
+__device__ __forceinline__ int node(const Cic& c, int oz, int oy, int ox, int n) {
+  return (c.iz[oz] * n + c.iy[oy]) * n + c.ix[ox];
 }
 
 // ------------------------------------------------------------------ deposit
+// Fixed point: 2^31 units per unit weight, accumulated in 64-bit integers (deterministic).
+// Values below 2^31 units convert through 32-bit integers (the 64-bit conversions run on
+// the FP64 pipe, which is slow on this part).
+__device__ __forceinline__ unsigned long long to_fix(float x) {
+  const float y = x * kFix;
+  if (fabsf(y) < 2147483520.0f) return (unsigned long long)(long long)__float2int_rn(y);
+  return (unsigned long long)__float2ll_rn(y);
+}
+
+__device__ __forceinline__ float from_fix(unsigned long long a) {
+  const int hi = (int)(a >> 32);
+  const unsigned lo = (unsigned)(a & 0xffffffffull);
+  return 2.0f * __int2float_rn(hi) + __uint2float_rn(lo) * kInvFix;
+}
+
 __global__ void deposit_kernel(const float* __restrict__ s, const float* __restrict__ vals,
                                int n, float inv_dx, unsigned long long* __restrict__ acc) {
-  const long long N3 = (long long)n * n * n;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N3) return;
+  const int N3 = n * n * n;
+  const PIdx q = particle_index(n);
+  if (!q.ok) return;
   Cic c;
-  cic_setup(s, p, N3, n, inv_dx, c);
-  const float v = vals ? vals[p] : 1.0f;
+  cic_setup(s, q, N3, n, inv_dx, c);
+  const float v = vals ? vals[q.p] : 1.0f;
 #pragma unroll
   for (int oz = 0; oz < 2; ++oz)
 #pragma unroll
     for (int oy = 0; oy < 2; ++oy)
 #pragma unroll
       for (int ox = 0; ox < 2; ++ox) {
-        const float w = c.wz[oz] * c.wy[oy] * c.wx[ox] * v;
-        const long long fx = __float2ll_rn(w * kFix);
-        if (fx) atomicAdd(acc + node(c, oz, oy, ox, n), (unsigned long long)fx);
+        const unsigned long long fx = to_fix(c.wz[oz] * c.wy[oy] * c.wx[ox] * v);
+        if (fx) atomicAdd(acc + node(c, oz, oy, ox, n), fx);
       }
 }
 
 __global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, float scale,
                                     const float* __restrict__ add, float offset,
-                                    float* __restrict__ out, long long N3) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                    float* __restrict__ out, int N3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N3) return;
-  const float cnt = __ll2float_rn((long long)acc[i]) * kInvFix;
+  const float cnt = from_fix(acc[i]);
   acc[i] = 0ull;
   out[i] = scale * cnt + (add ? add[i] : 0.0f) + offset;
 }
 
 sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
                           unsigned long long* acc, cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
-  deposit_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s, values, n, inv_dx, acc);
+  deposit_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s, values, n, inv_dx, acc);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 sim_status launch_fix_to_float(unsigned long long* acc, float scale, const float* add,
                                float offset, float* out, int n, cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
+  const int N3 = n * n * n;
   fix_to_float_kernel<<<cdiv(N3, 256), 256, 0, st>>>(acc, scale, add, offset, out, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -177,12 +205,12 @@ sim_status launch_fix_to_float(unsigned long long* acc, float scale, const float
 
 // ------------------------------------------------------------------ Green's function
 // half-complex index -> signed integer wavenumbers and Nyquist flags
-__device__ __forceinline__ void kindex(long long i, int n, int nh, int& kx, int& ky, int& kz,
+__device__ __forceinline__ void kindex(int i, int n, int nh, int& kx, int& ky, int& kz,
                                        bool& nx, bool& ny, bool& nz) {
-  kx = (int)(i % nh);
-  const long long r = i / nh;
-  ky = (int)(r % n);
-  kz = (int)(r / n);
+  kx = i % nh;
+  const int r = i / nh;
+  ky = r % n;
+  kz = r / n;
   const bool even = (n % 2 == 0);
   nx = even && kx == n / 2;
   ny = even && ky == n / 2;
@@ -195,8 +223,8 @@ __device__ __forceinline__ void kindex(long long i, int n, int nh, int& kx, int&
 __global__ void green_kernel(const cufftComplex* __restrict__ dk, cufftComplex* __restrict__ gk,
                              int n, float kf, float pref_norm) {
   const int nh = n / 2 + 1;
-  const long long NC = (long long)n * n * nh;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int NC = n * n * nh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NC) return;
   int kx, ky, kz;
   bool nx, ny, nz;
@@ -217,8 +245,8 @@ __global__ void green_kernel(const cufftComplex* __restrict__ dk, cufftComplex* 
 __global__ void green_adj_kernel(const cufftComplex* __restrict__ lk, cufftComplex* __restrict__ yk,
                                  int n, float kf, float pref_norm) {
   const int nh = n / 2 + 1;
-  const long long NC = (long long)n * n * nh;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int NC = n * n * nh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NC) return;
   int kx, ky, kz;
   bool nx, ny, nz;
@@ -236,7 +264,7 @@ __global__ void green_adj_kernel(const cufftComplex* __restrict__ lk, cufftCompl
 
 sim_status launch_gravity(const float* delta, float* g, cufftComplex* dk, cufftComplex* gk,
                           int n, double box, double pref, FFTPlans& plans, cudaStream_t st) {
-  const long long NC = (long long)n * n * (n / 2 + 1);
+  const int NC = n * n * (n / 2 + 1);
   DH_TRY(plans.set_stream(st));
   DH_TRY(fft_exec_r2c(plans.r2c1, delta, dk));
   const float kf = (float)(2.0 * M_PI / box);
@@ -250,7 +278,7 @@ sim_status launch_gravity(const float* delta, float* g, cufftComplex* dk, cufftC
 sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftComplex* gk,
                                   cufftComplex* dk, int n, double box, double pref,
                                   FFTPlans& plans, cudaStream_t st) {
-  const long long NC = (long long)n * n * (n / 2 + 1);
+  const int NC = n * n * (n / 2 + 1);
   DH_TRY(plans.set_stream(st));
   DH_TRY(fft_exec_r2c(plans.r2c3, lam_g, gk));
   const float kf = (float)(2.0 * M_PI / box);
@@ -264,13 +292,13 @@ sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftCom
 // ------------------------------------------------------------------ readout, kick, drift
 __global__ void interp_kernel(const float* __restrict__ grid, int nf, int n, float inv_dx,
                               const float* __restrict__ s, float* __restrict__ out) {
-  const long long N3 = (long long)n * n * n;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N3) return;
+  const int N3 = n * n * n;
+  const PIdx q = particle_index(n);
+  if (!q.ok) return;
   Cic c;
-  cic_setup(s, p, N3, n, inv_dx, c);
+  cic_setup(s, q, N3, n, inv_dx, c);
   for (int f = 0; f < nf; ++f) {
-    const float* gf = grid + f * N3;
+    const float* gf = grid + (size_t)f * N3;
     float acc = 0.0f;
 #pragma unroll
     for (int oz = 0; oz < 2; ++oz)
@@ -279,20 +307,19 @@ __global__ void interp_kernel(const float* __restrict__ grid, int nf, int n, flo
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox)
           acc += c.wz[oz] * c.wy[oy] * c.wx[ox] * __ldg(gf + node(c, oz, oy, ox, n));
-    out[f * N3 + p] = acc;
+    out[(size_t)f * N3 + q.p] = acc;
   }
 }
 
 sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
                          float* out, cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
-  interp_kernel<<<cdiv(N3, 256), 256, 0, st>>>(grid, nf, n, inv_dx, s, out);
+  interp_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(grid, nf, n, inv_dx, s, out);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 __device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& c, int n,
-                                        long long N3, float out[3]) {
+                                        int N3, float out[3]) {
   out[0] = out[1] = out[2] = 0.0f;
 #pragma unroll
   for (int oz = 0; oz < 2; ++oz)
@@ -301,7 +328,7 @@ __device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& 
 #pragma unroll
       for (int ox = 0; ox < 2; ++ox) {
         const float w = c.wz[oz] * c.wy[oy] * c.wx[ox];
-        const long long o = node(c, oz, oy, ox, n);
+        const int o = node(c, oz, oy, ox, n);
         out[0] += w * __ldg(g + o);
         out[1] += w * __ldg(g + N3 + o);
         out[2] += w * __ldg(g + 2 * N3 + o);
@@ -312,11 +339,12 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
                                   const float* __restrict__ g, float K, float dtau,
                                   const float* __restrict__ zhat, float* __restrict__ aux,
                                   int n, float inv_dx) {
-  const long long N3 = (long long)n * n * n;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N3) return;
+  const int N3 = n * n * n;
+  const PIdx q = particle_index(n);
+  if (!q.ok) return;
+  const int i = q.p;
   Cic c;
-  cic_setup(s, i, N3, n, inv_dx, c);
+  cic_setup(s, q, N3, n, inv_dx, c);
   float gi[3];
   interp3(g, c, n, N3, gi);
 #pragma unroll
@@ -326,7 +354,7 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
     if (dtau != 0.0f) s[j * N3 + i] += dtau * pj;
   }
   if (zhat) {
-    cic_setup(s, i, N3, n, inv_dx, c);
+    cic_setup(s, q, N3, n, inv_dx, c);
     float acc = 0.0f;
 #pragma unroll
     for (int oz = 0; oz < 2; ++oz)
@@ -342,15 +370,15 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
 sim_status launch_kick_drift(float* s, float* p, const float* g, float K, float dtau,
                              const float* zhat, float* aux, int n, float inv_dx,
                              cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
-  kick_drift_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s, p, g, K, dtau, zhat, aux, n, inv_dx);
+  kick_drift_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s, p, g, K, dtau, zhat, aux, n,
+                                                            inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 __global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__ g, float K,
-                                long long N3) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                int N3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N3) return;
   const float rho = u[i];
   float mg = 0.0f, g2 = 0.0f;
@@ -366,7 +394,7 @@ __global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__
 }
 
 sim_status launch_gas_kick(float* gas, const float* g, float K, int n, cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
+  const int N3 = n * n * n;
   gas_kick_kernel<<<cdiv(N3, 256), 256, 0, st>>>(gas, g, K, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -375,9 +403,9 @@ sim_status launch_gas_kick(float* gas, const float* g, float K, int n, cudaStrea
 // ------------------------------------------------------------------ adjoints
 __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __restrict__ g,
                                     float K, float* __restrict__ lam, float* __restrict__ lam_g,
-                                    double* __restrict__ dK, long long N3) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double dk = 0.0;
+                                    double* __restrict__ dK, int N3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float dkf = 0.0f;
   if (i < N3) {
     const float rho = u[i];
     const float le = lam[4 * N3 + i];
@@ -392,7 +420,7 @@ __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __
       mg += m[j] * gg[j];
       g2 += gg[j] * gg[j];
     }
-    float dkf = le * (mg + K * rho * g2);
+    dkf = le * (mg + K * rho * g2);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       lrho += K * lm[j] * gg[j];
@@ -402,14 +430,13 @@ __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __
     }
     lrho += 0.5f * K * K * g2 * le;
     lam[i] = lrho;
-    dk = (double)dkf;
   }
-  if (dK) block_sum_atomic(dk, dK);
+  if (dK) block_sum_atomic(dkf, dK);
 }
 
 sim_status launch_gas_kick_adjoint(const float* gas, const float* g, float K, float* lam,
                                    float* lam_g, double* dK, int n, cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
+  const int N3 = n * n * n;
   gas_kick_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(gas, g, K, lam, lam_g, dK, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -420,24 +447,22 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
                                       float* __restrict__ lam_s, float* __restrict__ lam_p,
                                       float* __restrict__ lam_g, double* __restrict__ dK,
                                       double* __restrict__ ddtau, int n, float inv_dx) {
-  const long long N3 = (long long)n * n * n;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double dk = 0.0, dd = 0.0;
-  if (i < N3) {
+  const int N3 = n * n * n;
+  const PIdx q = particle_index(n);
+  float dk = 0.0f, dd = 0.0f;
+  if (q.ok) {
+    const int i = q.p;
     Cic c;
-    cic_setup(s0, i, N3, n, inv_dx, c);
+    cic_setup(s0, q, N3, n, inv_dx, c);
     float gi[3];
     interp3(g, c, n, N3, gi);
     float lp[3], ls[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       ls[j] = lam_s[j * N3 + i];
-      if (p0) {
-        const float p1 = p0[j * N3 + i] + K * gi[j];
-        dd += (double)ls[j] * (double)p1;
-      }
+      if (p0) dd += ls[j] * (p0[j * N3 + i] + K * gi[j]);
       lp[j] = lam_p[j * N3 + i] + dtau * ls[j];
-      dk += (double)lp[j] * (double)gi[j];
+      dk += lp[j] * gi[j];
     }
     // lam_s0 += K d/ds (sum_j lp_j interp(g_j)) ; lam_g += interp^T(K lp)
     float gs[3] = {0.0f, 0.0f, 0.0f};
@@ -447,7 +472,7 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
       for (int oy = 0; oy < 2; ++oy)
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox) {
-          const long long o = node(c, oz, oy, ox, n);
+          const int o = node(c, oz, oy, ox, n);
           const float w = c.wz[oz] * c.wy[oy] * c.wx[ox];
           const float dwx = (ox ? inv_dx : -inv_dx) * c.wy[oy] * c.wz[oz];
           const float dwy = (oy ? inv_dx : -inv_dx) * c.wx[ox] * c.wz[oz];
@@ -477,9 +502,8 @@ sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const flo
                                      float dtau, float* lam_s, float* lam_p, float* lam_g,
                                      double* dK, double* ddtau, int n, float inv_dx,
                                      cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
-  kick_drift_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s0, p0, g, K, dtau, lam_s, lam_p, lam_g,
-                                                        dK, ddtau, n, inv_dx);
+  kick_drift_adj_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s0, p0, g, K, dtau, lam_s, lam_p,
+                                                               lam_g, dK, ddtau, n, inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -487,14 +511,14 @@ sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const flo
 __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __restrict__ ld,
                                    float cm, float* __restrict__ lam_s, double* __restrict__ dcm,
                                    int n, float inv_dx) {
-  const long long N3 = (long long)n * n * n;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc = 0.0;
-  if (i < N3) {
+  const int N3 = n * n * n;
+  const PIdx q = particle_index(n);
+  float itp = 0.0f;
+  if (q.ok) {
+    const int i = q.p;
     Cic c;
-    cic_setup(s, i, N3, n, inv_dx, c);
+    cic_setup(s, q, N3, n, inv_dx, c);
     float gs[3] = {0.0f, 0.0f, 0.0f};
-    float itp = 0.0f;
 #pragma unroll
     for (int oz = 0; oz < 2; ++oz)
 #pragma unroll
@@ -509,33 +533,32 @@ __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __r
         }
 #pragma unroll
     for (int j = 0; j < 3; ++j) lam_s[j * N3 + i] += cm * gs[j];
-    acc = (double)itp;
   }
-  if (dcm) block_sum_atomic(acc, dcm);
+  if (dcm) block_sum_atomic(itp, dcm);
 }
 
 sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, float cm,
                                   float* lam_s, double* dcm, int n, float inv_dx,
                                   cudaStream_t st) {
-  const long long N3 = (long long)n * n * n;
-  deposit_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(s, lam_delta, cm, lam_s, dcm, n, inv_dx);
+  deposit_adj_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s, lam_delta, cm, lam_s, dcm, n,
+                                                            inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b,
                            long long count, double* __restrict__ out) {
-  double acc = 0.0;
+  float acc = 0.0f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
-    acc += (double)a[i] * (double)b[i];
+    acc += a[i] * b[i];
   block_sum_atomic(acc, out);
 }
 
 sim_status launch_dot(const float* a, const float* b, long long count, double* out,
                       cudaStream_t st) {
   int blocks = cdiv(count, 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   dot_kernel<<<blocks, 256, 0, st>>>(a, b, count, out);
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -556,12 +579,12 @@ sim_status launch_axpy(float alpha, const float* x, float* y, long long count, c
 __global__ void density_loss_kernel(const float* __restrict__ rho, const float* __restrict__ t,
                                     float c, float* __restrict__ grad, double* __restrict__ loss,
                                     long long N3) {
-  double acc = 0.0;
+  float acc = 0.0f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N3;
        i += (long long)gridDim.x * blockDim.x) {
     const float d = rho[i] - t[i];
     grad[i] = 2.0f * c * d;
-    acc += (double)c * (double)d * (double)d;
+    acc += c * d * d;
   }
   block_sum_atomic(acc, loss);
 }
@@ -569,7 +592,7 @@ __global__ void density_loss_kernel(const float* __restrict__ rho, const float* 
 sim_status launch_density_loss(const float* rho, const float* target, float c, float* grad,
                                double* loss, long long N3, cudaStream_t st) {
   int blocks = cdiv(N3, 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   density_loss_kernel<<<blocks, 256, 0, st>>>(rho, target, c, grad, loss, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;

@@ -7,9 +7,9 @@
 
 namespace dh {
 
-// Fixed-point scale of the deterministic CIC accumulation: weights * 2^32 in int64.
-constexpr float kFix = 4294967296.0f;
-constexpr float kInvFix = 2.3283064365386963e-10f;
+// Fixed-point scale of the deterministic CIC accumulation: weights * 2^31 in int64.
+constexpr float kFix = 2147483648.0f;
+constexpr float kInvFix = 4.656612873077393e-10f;
 
 // cuFFT plans for one grid size: r2c batch 1/3/4, c2r batch 1/3/4 (n^3 real <-> n^2(n/2+1)).
 struct FFTPlans {

@@ -10,8 +10,16 @@
 // The reverse pass recomputes each checkpoint segment forward, recording the inputs of
 // every stage (the tape), then applies the hand-written adjoint of each stage in reverse
 // order. The adjoint of g(a_i) seen by the first kick of step i is carried into step i-1,
-// whose force stage produced it, so each force adjoint runs once per step.
+// whose force stage produced it, so each force adjoint runs once per step. Scalar
+// parameter partials are reduced per step on the device and chained through the FP64
+// schedule derivatives by a small device kernel, so neither pass synchronises the host.
+//
+// With graphs enabled (sim_set_graphs), sim_run and sim_run_adjoint are captured once per
+// argument set into CUDA graphs on a private stream and replayed on the caller's stream;
+// the handle's host-side bookkeeping (step counter, ping-pong buffers, checkpoint list) is
+// restored to what the captured call produced.
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -45,11 +53,15 @@ sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double n
 sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
                                 int n, double nu, double gam, double eps, double* dnu,
                                 cudaStream_t st);
+sim_status prepare_sweep_kernels();
 
 static const char* kOrders[6] = {"xyz", "zyx", "zxy", "yxz", "yzx", "xzy"};
 
-// per-step partial sums of the reverse pass (doubles on the device)
+// per-step partial sums of the reverse pass (doubles on the device), and the chain-rule
+// coefficient of each with respect to Omega_m
 enum { SL_DK1 = 0, SL_DK2, SL_DNU, SL_DDTAU, SL_DPREF, SL_DCM, SL_DFB, SL_N = 8 };
+// extra global partials after the SIM_NPARAMS subgrid ones
+enum { GX_DRP = 0, GX_DFB_IC = 1, GX_LAMC = 2, GX_N = 8 };
 
 // One recorded step: inputs of every stage (pointers into the tape allocation).
 struct TapeSlot {
@@ -57,6 +69,31 @@ struct TapeSlot {
   float *s0, *p0, *g0, *s1, *g1;            // 3 n^3 each
 };
 constexpr int kTapeFloatsPerCell = 6 * 5 + 5 * 3;
+
+// Host-side state that a call changes; a replayed graph must start from and end in the
+// same values as the captured call.
+struct HostState {
+  int step, init_step, prev_step, ckpt_count;
+  bool ics_valid;
+  float *gas, *gas2, *w_gas, *w_gas2, *lam_gas, *lam_tmp, *lamG0, *lamG1;
+  std::vector<int> ckpt_step;
+  bool operator==(const HostState& o) const {
+    return step == o.step && init_step == o.init_step && prev_step == o.prev_step &&
+           ckpt_count == o.ckpt_count && ics_valid == o.ics_valid && gas == o.gas &&
+           gas2 == o.gas2 && w_gas == o.w_gas && w_gas2 == o.w_gas2 && lam_gas == o.lam_gas &&
+           lam_tmp == o.lam_tmp && lamG0 == o.lamG0 && lamG1 == o.lamG1 &&
+           std::vector<int>(ckpt_step.begin(), ckpt_step.begin() + ckpt_count) ==
+               std::vector<int>(o.ckpt_step.begin(), o.ckpt_step.begin() + o.ckpt_count);
+  }
+};
+
+struct GraphEntry {
+  int kind = 0;
+  std::vector<uintptr_t> key;
+  HostState before, after;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
 
 }  // namespace dh
 
@@ -67,9 +104,8 @@ struct sim_s {
   int n = 0;
   long long N3 = 0, NC = 0;
   cudaStream_t st = 0;
-  double dx = 0, inv_dx = 0, fb = 0, cm = 0;
+  double dx = 0, inv_dx = 0, fb = 0, cm = 0, dfb_dom = 0;
   std::vector<StepFactors> sched;
-  double pref0 = 0, dpref0 = 0;
   // ICs constants
   double C = 0, dlnC_dom = 0, rp = 0, drp_dom = 0, a2e0 = 0;
   FFTPlans plans;
@@ -86,19 +122,24 @@ struct sim_s {
   bool ics_valid = false;
   int init_step = 0;
   int step = 0;
-  // checkpoints
-  std::vector<float*> ckpt;
+  // checkpoints: a pool of buffers (11 n^3 floats each) allocated on first use
+  std::vector<float*> ckpt_pool;
   std::vector<int> ckpt_step;
+  int ckpt_count = 0;
   // tape and adjoint scratch (allocated on first use)
   float* tape = nullptr;
   int tape_cap = 0;
   float *w_gas = nullptr, *w_gas2 = nullptr, *w_s = nullptr, *w_p = nullptr, *w_g = nullptr;
   float *lam_gas = nullptr, *lam_tmp = nullptr, *lam_s = nullptr, *lam_p = nullptr;
   float *lamG0 = nullptr, *lamG1 = nullptr, *lam_delta = nullptr, *lam4 = nullptr;
-  double* dslots = nullptr;
-  int dslots_cap = 0;
-  double* dglob = nullptr;  // SIM_NPARAMS + 4 extras
+  double* dslots = nullptr;  // (n_steps + 2) x SL_N
+  double* dcoef = nullptr;   // (n_steps) x SL_N chain-rule coefficients
+  double* dglob = nullptr;   // SIM_NPARAMS + GX_N
   unsigned int* speed_bits = nullptr;
+  // graphs
+  bool graphs = false;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<GraphEntry> graph_cache;
   std::vector<void*> allocs;
   std::string err;
 };
@@ -135,6 +176,112 @@ static sim_status dzero(void* dst, size_t bytes, cudaStream_t st) {
   return SIM_OK;
 }
 
+static HostState snapshot(const sim_t* h) {
+  HostState s;
+  s.step = h->step;
+  s.init_step = h->init_step;
+  s.prev_step = h->prev_step;
+  s.ckpt_count = h->ckpt_count;
+  s.ics_valid = h->ics_valid;
+  s.gas = h->gas;
+  s.gas2 = h->gas2;
+  s.w_gas = h->w_gas;
+  s.w_gas2 = h->w_gas2;
+  s.lam_gas = h->lam_gas;
+  s.lam_tmp = h->lam_tmp;
+  s.lamG0 = h->lamG0;
+  s.lamG1 = h->lamG1;
+  s.ckpt_step = h->ckpt_step;
+  return s;
+}
+
+static void restore(sim_t* h, const HostState& s) {
+  h->step = s.step;
+  h->init_step = s.init_step;
+  h->prev_step = s.prev_step;
+  h->ckpt_count = s.ckpt_count;
+  h->ics_valid = s.ics_valid;
+  h->gas = s.gas;
+  h->gas2 = s.gas2;
+  h->w_gas = s.w_gas;
+  h->w_gas2 = s.w_gas2;
+  h->lam_gas = s.lam_gas;
+  h->lam_tmp = s.lam_tmp;
+  h->lamG0 = s.lamG0;
+  h->lamG1 = s.lamG1;
+  h->ckpt_step = s.ckpt_step;
+}
+
+// Run `body` directly, or (graphs on) replay the graph captured for (kind, key) from the
+// same host state, capturing it first if there is none.
+template <class Body>
+static sim_status run_maybe_graph(sim_t* h, int kind, const std::vector<uintptr_t>& key,
+                                  Body body) {
+  if (!h->graphs) return body();
+  const HostState before = snapshot(h);
+  for (GraphEntry& e : h->graph_cache) {
+    if (e.kind == kind && e.key == key && e.before == before) {
+      DH_CUDA_TRY(cudaGraphLaunch(e.exec, h->st));
+      restore(h, e.after);
+      g_launches.fetch_add(e.launches, std::memory_order_relaxed);
+      return SIM_OK;
+    }
+  }
+  // capture on the private stream, ordered after the caller's stream
+  cudaEvent_t ev;
+  DH_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaStream_t user = h->st;
+  cudaError_t ce = cudaEventRecord(ev, user);
+  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h->cap_stream, ev, 0);
+  cudaEventDestroy(ev);
+  if (ce != cudaSuccess) {
+    set_error("graph capture setup failed: %s", cudaGetErrorString(ce));
+    return SIM_ECUDA;
+  }
+  DH_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  h->st = h->cap_stream;
+  const long long l0 = g_launches.load();
+  sim_status r = body();
+  h->st = user;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (r != SIM_OK || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    restore(h, before);
+    if (r == SIM_OK) set_error("graph capture failed: %s", cudaGetErrorString(ee));
+    return r != SIM_OK ? r : SIM_ECUDA;
+  }
+  GraphEntry e;
+  e.kind = kind;
+  e.key = key;
+  e.before = before;
+  e.after = snapshot(h);
+  e.launches = g_launches.load() - l0;
+  ce = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    restore(h, before);
+    set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(ce));
+    return SIM_ECUDA;
+  }
+  // the captured call's work has not run yet: run it now
+  ce = cudaGraphLaunch(e.exec, h->st);
+  if (ce != cudaSuccess) {
+    cudaGraphExecDestroy(e.exec);
+    restore(h, before);
+    set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(ce));
+    return SIM_ECUDA;
+  }
+  h->graph_cache.push_back(std::move(e));
+  return SIM_OK;
+}
+
+static void clear_graphs(sim_t* h) {
+  for (GraphEntry& e : h->graph_cache)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  h->graph_cache.clear();
+}
+
 static sim_status validate(const sim_params* p) {
   if (!p) {
     set_error("null parameter block");
@@ -167,6 +314,10 @@ static sim_status validate(const sim_params* p) {
     return SIM_EINVAL;
   }
   return SIM_OK;
+}
+
+static double a_of_step(const sim_t* h, int i) {
+  return i == 0 ? h->prm.a_start : h->sched[i - 1].a1;
 }
 
 // total matter contrast from particles and gas, then the force field g (3 n^3)
@@ -266,11 +417,13 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
     DH_TRY(dalloc_t(h, &h->lamG1, 3 * N3));
     DH_TRY(dalloc_t(h, &h->lam_delta, N3));
     DH_TRY(dalloc_t(h, &h->lam4, 4 * N3));
-    DH_TRY(dalloc_t(h, &h->dglob, SIM_NPARAMS + 8));
+    DH_TRY(dalloc_t(h, &h->dglob, SIM_NPARAMS + GX_N));
+    DH_TRY(dalloc_t(h, &h->dslots, (size_t)(h->prm.n_steps + 2) * SL_N));
   }
   if (h->tape_cap < tape_steps) {
     if (h->tape) {
       DH_CUDA_TRY(cudaStreamSynchronize(h->st));
+      clear_graphs(h);
       cudaFree(h->tape);
       for (auto& a : h->allocs)
         if (a == h->tape) a = nullptr;
@@ -278,11 +431,6 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
     h->tape = nullptr;
     DH_TRY(dalloc_t(h, &h->tape, (size_t)tape_steps * kTapeFloatsPerCell * N3));
     h->tape_cap = tape_steps;
-  }
-  const int slots = h->prm.n_steps + 2;
-  if (h->dslots_cap < slots) {
-    DH_TRY(dalloc_t(h, &h->dslots, (size_t)slots * SL_N));
-    h->dslots_cap = slots;
   }
   return SIM_OK;
 }
@@ -321,7 +469,7 @@ static sim_status force_adjoint(sim_t* h, const float* s, const float* g, double
 
 // Reverse of forward_step for step i with tape T. In: lam_gas / lam_s / lam_p of the state
 // after the step, lamG1 = adjoint of g(a_{i+1}) carried from step i+1. Out: the same
-// buffers for the state before the step, lamG0 = adjoint of g(a_i) (to carry).
+// buffers for the state before the step, lamG1 = adjoint of g(a_i) (to carry).
 static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot) {
   const StepFactors& f = h->sched[i];
   const sim_params& P = h->prm;
@@ -367,19 +515,53 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot)
   return SIM_OK;
 }
 
-// d/dOmega_m of the per-step partials (host, FP64 chain rule through the schedule)
-static double omega_chain(sim_t* h, const std::vector<double>& slots, int first, int last) {
-  double d = 0.0;
-  const double dfb = -h->fb / h->prm.omega_m;
-  for (int i = first; i < last; ++i) {
-    const StepFactors& f = h->sched[i];
-    const double* sl = slots.data() + (size_t)i * SL_N;
-    d += sl[SL_DK1] * f.dK1 + sl[SL_DK2] * f.dK2;
-    d += (sl[SL_DNU] * h->inv_dx + sl[SL_DDTAU]) * f.ddtau;
-    d += sl[SL_DPREF] / f.pref1 * f.dpref1;
-    d += (-sl[SL_DCM] + sl[SL_DFB]) * dfb;
+// dL/dparams from the device partials: d/dOmega_m = sum over step slots of slot * coef
+// (schedule derivatives, host FP64, uploaded once) + the flush slot (force at the start of
+// the differentiated span) + the IC terms; sigma8 from the IC amplitude; the subgrid
+// parameters pass through. out is overwritten, or accumulated when `accumulate`.
+__global__ void param_chain_kernel(const double* __restrict__ slots,
+                                   const double* __restrict__ coef, int nvals,
+                                   const double* __restrict__ flush, double c_pref0,
+                                   double c_cm0, const double* __restrict__ glob,
+                                   double dlnC, double drp, double dfb, double inv_s8, int ics,
+                                   int accumulate, double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) acc += slots[i] * coef[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
   }
-  return d;
+  if (threadIdx.x == 0) {
+    double dom = red[0] + flush[SL_DPREF] * c_pref0 + flush[SL_DCM] * c_cm0;
+    double ds8 = 0.0;
+    if (ics) {
+      const double* gx = glob + SIM_NPARAMS;
+      dom += gx[GX_LAMC] * dlnC + gx[GX_DRP] * drp + gx[GX_DFB_IC] * dfb;
+      ds8 = gx[GX_LAMC] * inv_s8;
+    }
+    double v[SIM_NPARAMS];
+    v[SIM_P_OMEGA_M] = dom;
+    v[SIM_P_SIGMA8] = ds8;
+    for (int k = SIM_P_DELTA_C; k < SIM_NPARAMS; ++k) v[k] = glob[k];
+    for (int k = 0; k < SIM_NPARAMS; ++k) out[k] = accumulate ? out[k] + v[k] : v[k];
+  }
+}
+
+static sim_status launch_param_chain(sim_t* h, int first, int last, const double* flush,
+                                     double a_flush, bool ics, bool accumulate, double* out,
+                                     const double* slots_first) {
+  const int nvals = (last - first) * SL_N;
+  const double pref0 = 1.5 * h->prm.omega_m / a_flush;
+  const double c_pref0 = (1.5 / a_flush) / pref0;
+  param_chain_kernel<<<1, 256, 0, h->st>>>(slots_first, h->dcoef + (size_t)first * SL_N, nvals,
+                                           flush, c_pref0, -h->dfb_dom, h->dglob, h->dlnC_dom,
+                                           h->drp_dom, h->dfb_dom, 1.0 / h->prm.sigma8, ics ? 1 : 0,
+                                           accumulate ? 1 : 0, out);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
 }
 
 static sim_status alloc_state(sim_t* h) {
@@ -403,20 +585,37 @@ static sim_status alloc_state(sim_t* h) {
   DH_TRY(dalloc_t(h, &h->prev_gas, 5 * N3));
   DH_TRY(dalloc_t(h, &h->prev_part, 6 * N3));
   DH_TRY(dalloc_t(h, &h->speed_bits, 1));
+  DH_TRY(dalloc_t(h, &h->dcoef, (size_t)h->prm.n_steps * SL_N));
   DH_TRY(dzero(h->acc, N3 * sizeof(unsigned long long), h->st));
   DH_TRY(dzero(h->events, ((N3 + 31) / 32) * sizeof(uint32_t), h->st));
+  // chain-rule coefficients of the per-step partials with respect to Omega_m
+  std::vector<double> coef((size_t)h->prm.n_steps * SL_N, 0.0);
+  for (int i = 0; i < h->prm.n_steps; ++i) {
+    const StepFactors& f = h->sched[i];
+    double* c = coef.data() + (size_t)i * SL_N;
+    c[SL_DK1] = f.dK1;
+    c[SL_DK2] = f.dK2;
+    c[SL_DNU] = f.ddtau * h->inv_dx;
+    c[SL_DDTAU] = f.ddtau;
+    c[SL_DPREF] = f.dpref1 / f.pref1;
+    c[SL_DCM] = -h->dfb_dom;
+    c[SL_DFB] = h->dfb_dom;
+  }
+  DH_CUDA_TRY(cudaMemcpy(h->dcoef, coef.data(), coef.size() * sizeof(double),
+                         cudaMemcpyHostToDevice));
   return SIM_OK;
 }
 
-static void clear_checkpoints(sim_t* h) {
-  if (!h->ckpt.empty()) cudaStreamSynchronize(h->st);
-  for (float* c : h->ckpt) {
-    cudaFree(c);
-    for (auto& a : h->allocs)
-      if (a == c) a = nullptr;
+static void clear_checkpoints(sim_t* h) { h->ckpt_count = 0; }
+
+static sim_status ensure_ckpt_pool(sim_t* h, int count) {
+  while ((int)h->ckpt_pool.size() < count) {
+    float* c = nullptr;
+    DH_TRY(dalloc_t(h, &c, 11 * h->N3));
+    h->ckpt_pool.push_back(c);
+    h->ckpt_step.push_back(0);
   }
-  h->ckpt.clear();
-  h->ckpt_step.clear();
+  return SIM_OK;
 }
 
 static sim_status reset_to_init(sim_t* h) {
@@ -428,8 +627,7 @@ static sim_status reset_to_init(sim_t* h) {
   DH_TRY(dzero(h->star, N3 * sizeof(float), st));
   DH_TRY(dzero(h->aux, N3 * sizeof(float), st));
   h->step = h->init_step;
-  const double a = h->init_step == 0 ? h->prm.a_start : h->sched[h->init_step - 1].a1;
-  DH_TRY(compute_force(h, h->s, h->gas, 1.5 * h->prm.omega_m / a, h->g));
+  DH_TRY(compute_force(h, h->s, h->gas, 1.5 * h->prm.omega_m / a_of_step(h, h->init_step), h->g));
   clear_checkpoints(h);
   h->prev_step = -1;
   return SIM_OK;
@@ -437,10 +635,13 @@ static sim_status reset_to_init(sim_t* h) {
 
 static sim_status store_checkpoint(sim_t* h) {
   const long long N3 = h->N3;
-  float* c = nullptr;
-  DH_TRY(dalloc_t(h, &c, 11 * N3));
-  h->ckpt.push_back(c);
-  h->ckpt_step.push_back(h->step);
+  if (h->ckpt_count >= (int)h->ckpt_pool.size()) {
+    set_error("internal: checkpoint pool exhausted");
+    return SIM_EINVAL;
+  }
+  float* c = h->ckpt_pool[h->ckpt_count];
+  h->ckpt_step[h->ckpt_count] = h->step;
+  h->ckpt_count += 1;
   DH_TRY(dcopy(c, h->gas, 5 * N3 * sizeof(float), h->st));
   DH_TRY(dcopy(c + 5 * N3, h->s, 3 * N3 * sizeof(float), h->st));
   return dcopy(c + 8 * N3, h->p, 3 * N3 * sizeof(float), h->st);
@@ -450,6 +651,8 @@ static sim_status store_checkpoint(sim_t* h) {
 
 // ===================================================================== C ABI
 extern "C" {
+
+int64_t sim_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 sim_status sim_params_default(sim_params* p) {
   if (!p) return SIM_EINVAL;
@@ -494,8 +697,6 @@ sim_status sim_params_default(sim_params* p) {
 
 const char* sim_last_error(const sim_t* h) { return h ? h->err.c_str() : get_error(); }
 
-int64_t sim_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
-
 sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t** out) {
   if (!out) {
     set_error("sim_init: out is NULL");
@@ -513,9 +714,8 @@ sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t
   h->inv_dx = p->n / p->box;
   h->fb = p->omega_b / p->omega_m;
   h->cm = 1.0 - h->fb;
+  h->dfb_dom = -h->fb / p->omega_m;
   h->sched = make_schedule(p->a_start, p->a_end, p->n_steps, p->omega_m, p->kdk_mode);
-  h->pref0 = 1.5 * p->omega_m / p->a_start;
-  h->dpref0 = 1.5 / p->a_start;
   // IC constants (Sec. 2.1): C = rms_target sqrt(n^3 / sum_k P(k))
   {
     const int n = p->n;
@@ -543,8 +743,13 @@ sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t
     const double e0 = p->T_init / temperature_per_energy(p->gamma, p->mu);
     h->a2e0 = p->a_start * p->a_start * e0;
   }
-  sim_status r = h->plans.create(p->n);
+  sim_status r = prepare_sweep_kernels();
+  if (r == SIM_OK) r = h->plans.create(p->n);
   if (r == SIM_OK) r = alloc_state(h);
+  if (r == SIM_OK && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("cudaStreamCreate failed");
+    r = SIM_ECUDA;
+  }
   cudaStream_t st = h->st;
   if (r == SIM_OK) {
     if (noise)
@@ -574,10 +779,20 @@ sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t
 void sim_destroy(sim_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
+  clear_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->plans.destroy();
   for (void* a : h->allocs)
     if (a) cudaFree(a);
   delete h;
+}
+
+sim_status sim_set_graphs(sim_t* h, int32_t on) {
+  if (!h) return SIM_EINVAL;
+  if (!on) clear_graphs(h);
+  h->graphs = on != 0;
+  return SIM_OK;
 }
 
 sim_status sim_step(sim_t* h) {
@@ -614,14 +829,14 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
   if (r != SIM_OK) return fail(h, r);
   const TapeSlot T = tape_slot(h, 0);
   double* slot = h->dslots;
+  const double a0 = h->sched[i].a0;
   auto run = [&]() -> sim_status {
     DH_TRY(dzero(h->dslots, 2 * SL_N * sizeof(double), st));
-    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + 8) * sizeof(double), st));
+    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + GX_N) * sizeof(double), st));
     // recompute the step from its input with the tape
     DH_TRY(dcopy(h->w_gas, h->prev_gas, 5 * N3 * sizeof(float), st));
     DH_TRY(dcopy(h->w_s, h->prev_part, 3 * N3 * sizeof(float), st));
     DH_TRY(dcopy(h->w_p, h->prev_part + 3 * N3, 3 * N3 * sizeof(float), st));
-    const double a0 = h->sched[i].a0;
     DH_TRY(compute_force(h, h->w_s, h->w_gas, 1.5 * h->prm.omega_m / a0, h->w_g));
     DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
     // reverse
@@ -635,42 +850,16 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
     DH_TRY(dcopy(adj_gas, h->lam_gas, 5 * N3 * sizeof(float), st));
     DH_TRY(dcopy(adj_part, h->lam_s, 3 * N3 * sizeof(float), st));
     DH_TRY(dcopy(adj_part + 3 * N3, h->lam_p, 3 * N3 * sizeof(float), st));
+    if (adj_params)
+      DH_TRY(launch_param_chain(h, i, i + 1, slot + SL_N, a0, false, true, adj_params, slot));
     return SIM_OK;
   };
-  r = run();
-  if (r != SIM_OK) return fail(h, r);
-  if (adj_params) {
-    std::vector<double> sl(2 * SL_N), gl(SIM_NPARAMS + 8), acc(SIM_NPARAMS);
-    if (cudaMemcpyAsync(sl.data(), h->dslots, sl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(gl.data(), h->dglob, gl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(acc.data(), adj_params, SIM_NPARAMS * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-      set_error("sim_step_adjoint: reading partial sums failed");
-      return fail(h, SIM_ECUDA);
-    }
-    const StepFactors& f = h->sched[i];
-    const double dfb = -h->fb / h->prm.omega_m;
-    double dom = 0.0;
-    dom += sl[SL_DK1] * f.dK1 + sl[SL_DK2] * f.dK2;
-    dom += (sl[SL_DNU] * h->inv_dx + sl[SL_DDTAU]) * f.ddtau;
-    dom += sl[SL_DPREF] / f.pref1 * f.dpref1;
-    dom += (-sl[SL_DCM] + sl[SL_DFB]) * dfb;
-    const double pa = 1.5 * h->prm.omega_m / f.a0;
-    dom += sl[SL_N + SL_DPREF] / pa * (1.5 / f.a0) + (-sl[SL_N + SL_DCM]) * dfb;
-    acc[SIM_P_OMEGA_M] += dom;
-    for (int k = SIM_P_DELTA_C; k < SIM_NPARAMS; ++k) acc[k] += gl[k];
-    if (cudaMemcpyAsync(adj_params, acc.data(), SIM_NPARAMS * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-      set_error("sim_step_adjoint: writing parameter gradient failed");
-      return fail(h, SIM_ECUDA);
-    }
-  }
-  return SIM_OK;
+  return fail(h, run());
 }
 
 sim_status sim_run(sim_t* h, int32_t n_steps) {
   if (!h) return SIM_EINVAL;
-  if (h->step != h->init_step || !h->ckpt.empty()) {
+  if (h->step != h->init_step || h->ckpt_count != 0) {
     set_error("sim_run: the handle must be at its initial state (sim_init / sim_reset)");
     return fail(h, SIM_EINVAL);
   }
@@ -678,25 +867,29 @@ sim_status sim_run(sim_t* h, int32_t n_steps) {
     set_error("sim_run: n_steps out of range");
     return fail(h, SIM_EINVAL);
   }
-  for (int k = 0; k < n_steps; ++k) {
-    sim_status r = SIM_OK;
-    if ((h->step - h->init_step) % h->prm.ckpt_every == 0) r = store_checkpoint(h);
-    if (r == SIM_OK) r = forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr);
-    if (r != SIM_OK) return fail(h, r);
-    h->step += 1;
-    if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
-      double c = 0;
-      r = sim_cfl(h, &c);
-      if (r != SIM_OK) return fail(h, r);
-      if (!(c <= h->prm.cfl_max)) {
-        set_error("sim_run: CFL number %.4g above cfl_max %.4g after step %d", c,
-                  h->prm.cfl_max, h->step);
-        return fail(h, std::isfinite(c) ? SIM_ECFL : SIM_ENAN);
+  sim_status r = ensure_ckpt_pool(h, (n_steps + h->prm.ckpt_every - 1) / h->prm.ckpt_every);
+  if (r != SIM_OK) return fail(h, r);
+  auto body = [&]() -> sim_status {
+    for (int k = 0; k < n_steps; ++k) {
+      if ((h->step - h->init_step) % h->prm.ckpt_every == 0) DH_TRY(store_checkpoint(h));
+      DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr));
+      h->step += 1;
+      if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
+        double c = 0;
+        DH_TRY(sim_cfl(h, &c));
+        if (!(c <= h->prm.cfl_max)) {
+          set_error("sim_run: CFL number %.4g above cfl_max %.4g after step %d", c,
+                    h->prm.cfl_max, h->step);
+          return std::isfinite(c) ? SIM_ECFL : SIM_ENAN;
+        }
       }
     }
-  }
-  h->prev_step = -1;
-  return SIM_OK;
+    h->prev_step = -1;
+    return SIM_OK;
+  };
+  // the CFL watchdog reads back every step: never captured
+  if (h->prm.cfl_max > 0) return fail(h, body());
+  return fail(h, run_maybe_graph(h, 1, {(uintptr_t)n_steps}, body));
 }
 
 sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart,
@@ -705,7 +898,7 @@ sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart
     set_error("sim_run_adjoint: null arguments");
     return fail(h, SIM_EINVAL);
   }
-  if (h->ckpt.empty()) {
+  if (h->ckpt_count == 0) {
     set_error("sim_run_adjoint: no sim_run to differentiate");
     return fail(h, SIM_EINVAL);
   }
@@ -714,15 +907,14 @@ sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart
     return fail(h, SIM_EINVAL);
   }
   const long long N3 = h->N3;
-  cudaStream_t st = h->st;
-  const int K = h->prm.ckpt_every;
-  sim_status r = ensure_adjoint_buffers(h, K);
+  sim_status r = ensure_adjoint_buffers(h, h->prm.ckpt_every);
   if (r != SIM_OK) return fail(h, r);
-  const int nseg = (int)h->ckpt.size();
+  const int nseg = h->ckpt_count;
   const int last = h->step;
   auto body = [&]() -> sim_status {
-    DH_TRY(dzero(h->dslots, (size_t)h->dslots_cap * SL_N * sizeof(double), st));
-    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + 8) * sizeof(double), st));
+    cudaStream_t st = h->st;
+    DH_TRY(dzero(h->dslots, (size_t)(h->prm.n_steps + 2) * SL_N * sizeof(double), st));
+    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + GX_N) * sizeof(double), st));
     if (dL_dgas)
       DH_TRY(dcopy(h->lam_gas, dL_dgas, 5 * N3 * sizeof(float), st));
     else
@@ -738,12 +930,11 @@ sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart
     for (int seg = nseg - 1; seg >= 0; --seg) {
       const int first = h->ckpt_step[seg];
       const int end = seg + 1 < nseg ? h->ckpt_step[seg + 1] : last;
-      const float* c = h->ckpt[seg];
+      const float* c = h->ckpt_pool[seg];
       DH_TRY(dcopy(h->w_gas, c, 5 * N3 * sizeof(float), st));
       DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
       DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
-      const double a0 = first == 0 ? h->prm.a_start : h->sched[first - 1].a1;
-      DH_TRY(compute_force(h, h->w_s, h->w_gas, 1.5 * h->prm.omega_m / a0, h->w_g));
+      DH_TRY(compute_force(h, h->w_s, h->w_gas, 1.5 * h->prm.omega_m / a_of_step(h, first), h->w_g));
       for (int i = first; i < end; ++i) {
         const TapeSlot T = tape_slot(h, i - first);
         DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
@@ -754,49 +945,23 @@ sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart
     // g at the start of the run is a function of the initial state
     const TapeSlot T0 = tape_slot(h, 0);
     const int s0 = h->ckpt_step[0];
-    const double a0 = s0 == 0 ? h->prm.a_start : h->sched[s0 - 1].a1;
+    const double a0 = a_of_step(h, s0);
     double* slot0 = h->dslots + (size_t)h->prm.n_steps * SL_N;
     DH_TRY(force_adjoint(h, T0.s0, T0.g0, 1.5 * h->prm.omega_m / a0, h->lamG1, slot0));
     // through the initial conditions to the white noise
     if (h->ics_valid) {
+      double* gx = h->dglob + SIM_NPARAMS;
       DH_TRY(launch_ic_adjoint(h->f4, h->lam_gas, h->lam_s, h->lam_p, h->lam4, dL_dnoise, h->ck,
                                h->n, h->prm.box, h->prm.kc_frac, h->C, h->rp, h->fb, h->a2e0,
-                               h->dglob + SIM_NPARAMS, h->dglob + SIM_NPARAMS + 1, h->plans, st));
-      DH_TRY(launch_dot(h->lam4, h->f4, 4 * N3, h->dglob + SIM_NPARAMS + 2, st));
+                               gx + GX_DRP, gx + GX_DFB_IC, h->plans, st));
+      DH_TRY(launch_dot(h->lam4, h->f4, 4 * N3, gx + GX_LAMC, st));
     }
-    return SIM_OK;
+    return launch_param_chain(h, s0, last, slot0, a0, h->ics_valid, false, dL_dparams,
+                              h->dslots + (size_t)s0 * SL_N);
   };
-  r = body();
-  if (r != SIM_OK) return fail(h, r);
-  std::vector<double> sl((size_t)h->dslots_cap * SL_N), gl(SIM_NPARAMS + 8);
-  if (cudaMemcpyAsync(sl.data(), h->dslots, sl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(gl.data(), h->dglob, gl.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    set_error("sim_run_adjoint: reading partial sums failed: %s", cudaGetErrorString(cudaGetLastError()));
-    return fail(h, SIM_ECUDA);
-  }
-  std::vector<double> out(SIM_NPARAMS, 0.0);
-  const double dfb = -h->fb / h->prm.omega_m;
-  double dom = omega_chain(h, sl, h->ckpt_step[0], last);
-  const double* s0 = sl.data() + (size_t)h->prm.n_steps * SL_N;
-  const int st0 = h->ckpt_step[0];
-  const double a0 = st0 == 0 ? h->prm.a_start : h->sched[st0 - 1].a1;
-  dom += s0[SL_DPREF] / (1.5 * h->prm.omega_m / a0) * (1.5 / a0) + (-s0[SL_DCM]) * dfb;
-  double dsig = 0.0;
-  if (h->ics_valid) {
-    const double drp = gl[SIM_NPARAMS], dfb_ic = gl[SIM_NPARAMS + 1], lamC_C = gl[SIM_NPARAMS + 2];
-    dom += lamC_C * h->dlnC_dom + drp * h->drp_dom + dfb_ic * dfb;
-    dsig = lamC_C / h->prm.sigma8;
-  }
-  out[SIM_P_OMEGA_M] = dom;
-  out[SIM_P_SIGMA8] = dsig;
-  for (int k = SIM_P_DELTA_C; k < SIM_NPARAMS; ++k) out[k] = gl[k];
-  if (cudaMemcpyAsync(dL_dparams, out.data(), SIM_NPARAMS * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    set_error("sim_run_adjoint: writing parameter gradient failed");
-    return fail(h, SIM_ECUDA);
-  }
-  return SIM_OK;
+  const std::vector<uintptr_t> key = {(uintptr_t)dL_dgas, (uintptr_t)dL_dpart,
+                                      (uintptr_t)dL_dnoise, (uintptr_t)dL_dparams};
+  return fail(h, run_maybe_graph(h, 2, key, body));
 }
 
 sim_status sim_reset(sim_t* h) {

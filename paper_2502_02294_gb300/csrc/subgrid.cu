@@ -113,7 +113,7 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
                                    SubgridConst c, double* __restrict__ dpar,
                                    double* __restrict__ dfb, long long N3) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double a_dc = 0, a_pi = 0, a_e0 = 0, a_t0 = 0, a_g = 0, a_fb = 0;
+  float a_dc = 0, a_pi = 0, a_e0 = 0, a_t0 = 0, a_g = 0, a_fb = 0;
   if (i < N3) {
     float u[5], l[5];
 #pragma unroll
@@ -135,26 +135,26 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
     if (r.use_floor) {
       const float lef = le2;
       lrho += lef * r.ef * c.gexp / rho;
-      a_t0 = (double)(lef * r.ef / c.T0);
-      a_g = (double)(lef * r.ef * logf(rho * c.inv_fb));
-      a_fb += (double)(lef * r.ef * (-c.gexp / c.fb));
+      a_t0 = lef * r.ef / c.T0;
+      a_g = lef * r.ef * logf(rho * c.inv_fb);
+      a_fb += lef * r.ef * (-c.gexp / c.fb);
     } else {
       le1 = le2;
     }
     float le = le1;
-    a_e0 = (double)(le1 * r.zhat);
+    a_e0 = le1 * r.zhat;
     const float lz = le1 * c.E0;
     const float ll = lz * r.zhat * (1.0f - r.zhat) * c.inv_tau;
     const float llnpi = ll / (1.0f - r.pi);
-    a_pi = (double)(llnpi / c.Pi0);
+    a_pi = llnpi / c.Pi0;
     const float lx1 = llnpi * sigmoidf_(-r.x1);
     const float lx2 = llnpi * sigmoidf_(-r.x2);
     const float ldelta = lx1 * c.inv_wd;
-    a_dc = -(double)ldelta;
+    a_dc = -ldelta;
     const float lT = -lx2 * c.inv_wT;
     le += lT * c.tpe;
     lrho += ldelta * c.inv_fb;
-    a_fb += -(double)(ldelta * rho * c.inv_fb * c.inv_fb);
+    a_fb += -(ldelta * rho * c.inv_fb * c.inv_fb);
     // e = (eps - ke) / (a^2 rho)
     const float inv_a2r = 1.0f / (c.a2 * rho);
     const float leps_in = le * inv_a2r;

@@ -83,3 +83,13 @@ def test_null_arguments_rejected(dh):
     assert L.sim_power_spectrum(None, None, 8, 8.0, 4, None, None, None, None) == dh._lib.SIM_EINVAL
     assert L.sim_step(None) == dh._lib.SIM_EINVAL
     L.sim_destroy(None)  # ignored
+
+
+def test_no_unresolved_library_symbols(dh):
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--undefined-only", dh._lib.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    ours = [ln for ln in out.splitlines() if "_ZN2dh" in ln or " sim_" in ln]
+    assert not ours, ours

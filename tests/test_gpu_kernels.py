@@ -31,7 +31,7 @@ def _nu(U, frac=0.4):
     return frac / hydro.signal_speed_max(U, GAMMA)
 
 
-@pytest.mark.parametrize("n", [8, 12, 48, 70])
+@pytest.mark.parametrize("n", [8, 12, 48, 64, 70, 128])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_sweep_forward(dh, n, axis):
     Ug, Uo = f32(gas(n, seed=n + axis))
@@ -61,7 +61,7 @@ def test_sweep_sharp_fronts_and_uniform(dh):
         assert torch.equal(dh.sweep(Ug, axis, 0.7), Ug)
 
 
-@pytest.mark.parametrize("n", [8, 20, 48])
+@pytest.mark.parametrize("n", [8, 20, 48, 64])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_sweep_adjoint(dh, n, axis):
     Ug, Uo = f32(gas(n, seed=7 * n + axis))
@@ -110,7 +110,7 @@ def test_deposit_deterministic(dh):
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("n", [8, 16, 48])
+@pytest.mark.parametrize("n", [8, 16, 48, 64])
 def test_gravity_and_adjoint(dh, n):
     box, pref = 1.3 * n, 0.77
     dg, do = f32(synth.field(n, 11))

@@ -113,9 +113,18 @@ def test_run_is_deterministic_and_resettable(dh):
     sim.close()
 
 
-def test_step_adjoint_matches_oracle_reverse_mode(dh):
-    n = 12
-    p = dh.default_params(n=n, box=12.0, n_steps=4, a_start=0.1, a_end=0.3, rms_ref=0.15, **SUB)
+# Without the UV floor the gas cools adiabatically while its bulk flow grows; at Mach >> 10
+# the single-energy pressure P = (gamma-1)(eps - |m|^2/2rho) is a small difference of large
+# numbers and the sound-speed derivative gamma/(2 c_s rho) diverges where P -> 0, so float32
+# and float64 gradients part there. The subgrid-off cases start warmer (T_init = 1e5 K) to
+# stay away from P ~ 0; the cold regime is exercised by the forward-parity tests.
+WARM = dict(T_init=1e5)
+
+
+@pytest.mark.parametrize("n,sub", [(12, True), (12, False), (64, False)])
+def test_step_adjoint_matches_oracle_reverse_mode(dh, n, sub):
+    p = dh.default_params(n=n, box=float(n), n_steps=4, a_start=0.1, a_end=0.3,
+                          rms_ref=0.15 if n < 32 else 0.05, **(SUB if sub else WARM))
     o = oracle_params(p)
     sim = dh.Simulation(p, f32(synth.white_noise(n, 2))[0])
     sim.step()
@@ -138,18 +147,19 @@ def test_step_adjoint_matches_oracle_reverse_mode(dh):
     out = osim.step(state, oo)
     L = (out["U"] * lg_o).sum() + (out["s"] * lp_o[:3]).sum() + (out["p"] * lp_o[3:]).sum()
     gU, gs, gp, gom = torch.autograd.grad(L, (U, s, pp, om))
+    # the gradient bar (1e-3); one step of FP32 reverse mode lands at 1e-5 .. 4e-4
     for k in range(5):
-        assert rel_l2(lam_gas[k], gU[k]) < 1e-4, (k, rel_l2(lam_gas[k], gU[k]))
-    assert rel_l2(lam_part[:3], gs) < 1e-4
-    assert rel_l2(lam_part[3:], gp) < 1e-4
+        assert rel_l2(lam_gas[k], gU[k]) < 1e-3, (k, rel_l2(lam_gas[k], gU[k]))
+    assert rel_l2(lam_part[:3], gs) < 1e-3
+    assert rel_l2(lam_part[3:], gp) < 1e-3
     assert abs(dpar[0].item() - gom.item()) < 1e-3 * abs(gom.item())
 
 
-@pytest.mark.parametrize("ckpt", [2, 5])
-def test_run_adjoint_matches_oracle_reverse_mode(dh, ckpt):
+@pytest.mark.parametrize("ckpt,sub", [(2, True), (5, True), (2, False)])
+def test_run_adjoint_matches_oracle_reverse_mode(dh, ckpt, sub):
     n = 12
     p = dh.default_params(n=n, box=12.0, n_steps=5, ckpt_every=ckpt, a_start=0.1, a_end=0.35,
-                          rms_ref=0.15, **SUB)
+                          rms_ref=0.15, **(SUB if sub else WARM))
     o = oracle_params(p)
     wg, wo = f32(synth.white_noise(n, 5))
     tg, to = f32(0.16 * (1 + 0.2 * synth.field(n, 7)))
@@ -165,11 +175,38 @@ def test_run_adjoint_matches_oracle_reverse_mode(dh, ckpt):
     X = wo.clone().requires_grad_(True)
     out = osim.run(X, dict(o, **leaves))
     L = osim.mse_density(out["U"], to)
-    grads = torch.autograd.grad(L, [X] + [leaves[k] for k in names])
+    grads = torch.autograd.grad(L, [X] + [leaves[k] for k in names], allow_unused=True)
     assert rel_l2(dnoise, grads[0]) < 1e-3, rel_l2(dnoise, grads[0])
     for j, k in enumerate(names):
-        want = grads[1 + j].item()
+        want = 0.0 if grads[1 + j] is None else grads[1 + j].item()
         assert abs(dpar[j].item() - want) <= 1e-3 * abs(want) + 1e-10, (k, dpar[j].item(), want)
+
+
+@pytest.mark.parametrize("n,steps,sub", [(40, 4, True), (64, 3, False)])
+def test_run_adjoint_multi_tile(dh, n, steps, sub):
+    """Grids spanning several sweep tiles along every axis (forward tiles of 32, adjoint
+    tiles of 16 along y and z), a ragged last tile at n = 40, two checkpoint segments."""
+    kw = dict(n=n, box=float(n), n_steps=steps, ckpt_every=2, a_start=0.1, a_end=0.25,
+              rms_ref=0.15 if n < 48 else 0.05)
+    kw.update(SUB if sub else WARM)
+    p = dh.default_params(**kw)
+    o = oracle_params(p)
+    wg, wo = f32(synth.white_noise(n, 15))
+    tg, to = f32(0.16 * (1 + 0.2 * synth.field(n, 16)))
+    sim = dh.Simulation(p, wg)
+    sim.run()
+    st = sim.state()
+    dL_dgas = torch.zeros(5, n, n, n, device="cuda")
+    dL_dgas[0] = (2.0 / n ** 3) * (st["gas"][0] - tg)
+    dnoise, dpar = sim.run_adjoint(dL_dgas.contiguous())
+    X = wo.clone().requires_grad_(True)
+    om = torch.tensor(o["omega_m"], dtype=DT, requires_grad=True)
+    out = osim.run(X, dict(o, omega_m=om))
+    L = osim.mse_density(out["U"], to)
+    gX, gom = torch.autograd.grad(L, (X, om))
+    assert rel_l2(dnoise, gX) < 1e-3, rel_l2(dnoise, gX)
+    assert abs(dpar[0].item() - gom.item()) <= 1e-3 * abs(gom.item())
+    sim.close()
 
 
 def test_cfl_matches_oracle(dh):
@@ -180,3 +217,39 @@ def test_cfl_matches_oracle(dh):
     from oracle import hydro
     want = hydro.cfl_number(st["gas"].double().cpu(), sim.schedule(0)["dtau"], 1.0, p.gamma)
     assert abs(sim.cfl() / want - 1) < 1e-5
+
+
+def test_graph_replay_matches_eager(dh):
+    """sim_run / sim_run_adjoint captured into CUDA graphs and replayed give the same bits
+    as eager execution, on the first (capturing) call and on later replays."""
+    n = 24
+    p = dh.default_params(n=n, box=24.0, n_steps=6, ckpt_every=4, a_start=0.1, a_end=0.4,
+                          rms_ref=0.15, **SUB)
+    wg, _ = f32(synth.white_noise(n, 21))
+    tg, _ = f32(0.16 * (1 + 0.2 * synth.field(n, 22)))
+    stream = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(stream):
+        for graphs in (0, 1):
+            sim = dh.Simulation(p, wg)
+            assert dh.lib.sim_set_graphs(sim.h, graphs) == 0
+            dnoise = torch.empty(n, n, n, device="cuda")
+            dpar = torch.zeros(dh.NPARAMS, dtype=torch.float64, device="cuda")
+            dL = torch.empty(5, n, n, n, device="cuda")
+            loss = torch.empty(1, dtype=torch.float64, device="cuda")
+            for rep in range(3):
+                sim.reinit(wg)
+                sim.run()
+                sim.loss_density(tg, 1.0 / n ** 3, out=dL, loss=loss)
+                assert dh.lib.sim_run_adjoint(sim.h, dh.api._ptr(dL), None, dh.api._ptr(dnoise),
+                                              dh.api._ptr(dpar)) == 0
+                stream.synchronize()
+                outs.append((graphs, rep, sim.state()["gas"].clone(), dnoise.clone(), dpar.clone()))
+            sim.close()
+    # the forward pass is bitwise reproducible (fixed-point deposit); the reverse pass
+    # scatters particle adjoints with float atomics, so its sums vary at round-off level
+    ref = outs[0]
+    for g, rep, gas, dn, dp in outs[1:]:
+        assert torch.equal(gas, ref[2]), (g, rep)
+        assert rel_l2(dn, ref[3]) < 1e-5, (g, rep)
+        assert rel_l2(dp, ref[4]) < 1e-5, (g, rep)
