@@ -162,6 +162,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel eagerly instead of replaying captured graphs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -185,16 +187,27 @@ def main():
     n3 = n ** 3
     noise = torch.from_numpy(synth.white_noise(n, 100 + rank).astype("float32")).to(dev)
     target = torch.from_numpy((0.163 * (1 + 0.3 * synth.field(n, 7))).astype("float32")).to(dev)
-    sim = dh.Simulation(p, noise)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    # the simulation runs on its own stream so that its runs can be captured as CUDA graphs
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(stream)
+    sim = dh.Simulation(p, noise)
+    if not args.no_graphs:
+        dh._lib.check(dh.lib.sim_set_graphs(sim.h, 1), "sim_set_graphs", sim.h)
     c = 1.0 / n3
+    dL = torch.empty(5, n, n, n, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    dnoise = torch.empty(n, n, n, dtype=torch.float32, device=dev)
+    dpar = torch.zeros(dh.NPARAMS, dtype=torch.float64, device=dev)
+    ptr = dh.api._ptr
 
     def hot_path(noise_dev):
         sim.reinit(noise_dev)
         sim.run()
-        dL, loss = sim.loss_density(target, c)
-        dnoise, dpar = sim.run_adjoint(dL, None)
+        sim.loss_density(target, c, out=dL, loss=loss)
+        dh._lib.check(dh.lib.sim_run_adjoint(sim.h, ptr(dL), None, ptr(dnoise), ptr(dpar)),
+                      "sim_run_adjoint", sim.h)
         return dnoise, dpar, loss
 
     def barrier():
@@ -300,7 +313,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "n": n, "n_steps": p.n_steps,
                    "ckpt_every": p.ckpt_every, "parallelism": f"replicas x{ws}",
-                   "l2": "512 MB buffer written between timed iterations"},
+                   "l2": "512 MB buffer written between timed iterations",
+                   "cuda_graphs": not args.no_graphs},
         "fwd_value": cell_steps / (fwd_ms / 1e3),
         "fwd_ms_per_step": fwd_ms,
         "e2e": {"value": cell_steps / (e2e_ms / 1e3), "unit": "cell-steps/s",

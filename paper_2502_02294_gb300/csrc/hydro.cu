@@ -12,6 +12,8 @@
 //   full step  (Eq. TVD_fullstep):  U'_i = U_i - nu (F2_{i+1/2} - F2_{i-1/2}),
 //              F2_{i+1/2} = [Fh^R_i + phi(dL, dR)] - [Fh^L_{i+1} - phi(dL', dR')]
 //              with the gated van Leer limiter phi and half differences of Fh^R / Fh^L.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace dh {
@@ -36,8 +38,11 @@ struct TileGeom {
 // tile shapes (forward / adjoint): x sweep 64 x 4 lines, y/z sweeps 32 x 32 and 16 x 32
 template <int AXIS> struct SweepCfg;
 template <> struct SweepCfg<0> { static constexpr int S = 64, W = 4, NT = 128, SA = 64, WA = 4, NTA = 128; };
-template <> struct SweepCfg<1> { static constexpr int S = 32, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
-template <> struct SweepCfg<2> { static constexpr int S = 32, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
+#ifndef DH_TILE_S
+#define DH_TILE_S 16
+#endif
+template <> struct SweepCfg<1> { static constexpr int S = DH_TILE_S, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
+template <> struct SweepCfg<2> { static constexpr int S = DH_TILE_S, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
 
 // limited second-order face flux at face c+1/2 from the half-step splits R = Fh^R, L = Fh^L
 __device__ __forceinline__ float face_flux(const float* R, const float* L, int DS, float eps) {
@@ -171,12 +176,24 @@ sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int 
     FRp[k] = f1m[k] = R0[k] = R1[k] = R2[k] = L0[k] = L1[k] = F2m[k] = 0.0f;
   }
   int j = wrap_periodic(s0 - 3, n);
+  // software pipelining: the next cell's state is requested one iteration ahead
+  float un[5];
+  {
+    const long long o = goff<AXIS>(j, w, t, n);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) un[k] = __ldg(uin + k * N3 + o);
+  }
 #pragma unroll 1
   for (int it = 0; it < L + 6; ++it) {
-    const long long o = goff<AXIS>(j, w, t, n);
     float u[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) u[k] = __ldg(uin + k * N3 + o);
+    for (int k = 0; k < 5; ++k) u[k] = un[k];
+    const int jn = (j + 1 == n) ? 0 : j + 1;
+    if (it + 1 < L + 6) {
+      const long long on = goff<AXIS>(jn, w, t, n);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) un[k] = __ldg(uin + k * N3 + on);
+    }
     float FR[5], FL[5];
     split_flux(u, F, gam, FR, FL);
     float f1[5], uh[5];
@@ -206,8 +223,212 @@ sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int 
       L0[k] = L1[k];
       L1[k] = FLh[k];
     }
-    j = (j + 1 == n) ? 0 : j + 1;
+    j = jn;
   }
+}
+
+// ------------------------------------------------------------- adjoint, marching form
+// Pass 1: each thread streams one line segment [s0, s0 + L) plus a halo and produces
+// lamUh_j for its own cells. At load i it recomputes the forward stages for cell i-1
+// (first-order face, Uh, half-step splits), evaluates the limited face t = i-3 once (its
+// flux for d/dnu and its limiter derivatives), and adds the face's contributions to the
+// running adjoints of the half-step splits of cells t-1 .. t+2:
+//   lamFh^R_{t-1} -= A_t, lamFh^R_t += lf_t + A_t - B_t, lamFh^R_{t+1} += B_t,
+//   lamFh^L_t -= C_t, lamFh^L_{t+1} += -lf_t + C_t - D_t, lamFh^L_{t+2} += D_t,
+// with lf_t = nu (lam_out_{t+1} - lam_out_t), A = lf daR/2, B = lf dbR/2, C = lf daL/2,
+// D = lf dbL/2 (daR, dbR the limiter partials of the right-moving face flux, daL, dbL of
+// the left-moving one). Cell i-4 is then complete and lamUh_{i-4} = VJP(Uh_{i-4}).
+// d/dnu gathers sum_t F2_t lf_t / nu - sum_j lamUh_j dF1_j / 2.
+template <int AXIS, int L>
+__global__ void __launch_bounds__(128)
+sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
+                       float* __restrict__ luh_out, int n, float nu, float gam, float eps,
+                       double* __restrict__ dnu) {
+  constexpr int F = 1 + AXIS;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t3 = blockIdx.y;
+  const int s0 = blockIdx.z * L;
+  const bool live = w < n;
+  const long long N3 = (long long)n * n * n;
+  const float hnu = 0.5f * nu, inv_nu = 1.0f / nu;
+  float Uc[5], FRp[5], f1m[5];          // U_{i-1}, F^R_{i-1}, face (i-3/2)
+  float R0[5], R1[5], R2[5];            // Fh^R_{i-4}, Fh^R_{i-3}, Fh^R_{i-2}
+  float L0[5], L1[5];                   // Fh^L_{i-3}, Fh^L_{i-2}
+  float H0[5], H1[5], H2[5];            // Uh_{i-4}, Uh_{i-3}, Uh_{i-2}
+  float D0[5], D1[5], D2[5];            // dF1_{i-4}, dF1_{i-3}, dF1_{i-2}
+  float M0[5], M1[5], M2[5];            // lam_out_{i-3}, lam_out_{i-2}, lam_out_{i-1}
+  float aR0[5], aR1[5], aR2[5];         // lamFh^R accumulators of cells i-4, i-3, i-2
+  float aL0[5], aL1[5], aL2[5], aL3[5]; // lamFh^L accumulators of cells i-4 .. i-1
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float init = (k == 0 || k == 4) ? 1.0f : 0.0f;
+    Uc[k] = H0[k] = H1[k] = H2[k] = init;
+    FRp[k] = f1m[k] = R0[k] = R1[k] = R2[k] = L0[k] = L1[k] = 0.0f;
+    D0[k] = D1[k] = D2[k] = M0[k] = M1[k] = M2[k] = 0.0f;
+    aR0[k] = aR1[k] = aR2[k] = aL0[k] = aL1[k] = aL2[k] = aL3[k] = 0.0f;
+  }
+  float dnu_acc = 0.0f;
+  // loads run from s0 - 5 to s0 + L + 3: cells s0 .. s0 + L - 1 complete at i = j + 4
+  const int ww = live ? w : 0;
+  int j = wrap_periodic(s0 - 5, n);
+  float un[5], ln[5];
+  {
+    const long long o = goff<AXIS>(j, ww, t3, n);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      un[k] = __ldg(uin + k * N3 + o);
+      ln[k] = __ldg(lout + k * N3 + o);
+    }
+  }
+#pragma unroll 1
+  for (int it = 0; it < L + 9; ++it) {
+    float u[5], lo[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      u[k] = un[k];
+      lo[k] = ln[k];
+    }
+    const int jn = (j + 1 == n) ? 0 : j + 1;
+    if (it + 1 < L + 9) {
+      const long long on = goff<AXIS>(jn, ww, t3, n);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        un[k] = __ldg(uin + k * N3 + on);
+        ln[k] = __ldg(lout + k * N3 + on);
+      }
+    }
+    // forward stages for cell i-1
+    float FR[5], FL[5];
+    split_flux(u, F, gam, FR, FL);
+    float f1[5], dF[5], uh[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      f1[k] = FRp[k] - FL[k];  // face i-1/2
+      dF[k] = f1[k] - f1m[k];  // dF1_{i-1}
+      uh[k] = Uc[k] - hnu * dF[k];
+    }
+    float FRh[5], FLh[5];
+    split_flux(uh, F, gam, FRh, FLh);
+    // face t = i-3: R from Fh^R_{i-4..i-2}, L from Fh^L_{i-3..i-1}; lf_t from lam_out
+    // face t = i-3 belongs to this segment's d/dnu sum when t is one of its cells: over a
+    // periodic line sum_k -lam_out_k (F2_k - F2_{k-1}) = sum_t F2_t lf_t / nu
+    const int jt = s0 + it - 8;  // unwrapped index of face cell t (face t + 1/2)
+    const bool face_in = (jt >= s0) && (jt < s0 + L) && (jt < n);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float lf = nu * (M1[k] - M0[k]);  // nu (lam_out_{t+1} - lam_out_t), t = i-3
+      const float aR = 0.5f * (R1[k] - R0[k]), bR = 0.5f * (R2[k] - R1[k]);
+      const float aL = 0.5f * (L1[k] - L0[k]), bL = 0.5f * (FLh[k] - L1[k]);
+      float daR, dbR, daL, dbL;
+      vanleer_grad(aR, bR, eps, daR, dbR);
+      vanleer_grad(aL, bL, eps, daL, dbL);
+      const float A = 0.5f * lf * daR, B = 0.5f * lf * dbR;
+      const float C = 0.5f * lf * daL, D = 0.5f * lf * dbL;
+      aR0[k] -= A;
+      aR1[k] += lf + A - B;
+      aR2[k] += B;
+      aL1[k] -= C;
+      aL2[k] += -lf + C - D;
+      aL3[k] += D;
+      if (face_in) {
+        // d/dnu part 1: faces of the segment's output cells (t in [s0-1, s0+L))
+        const float F2 = (R1[k] + vanleer(aR, bR, eps)) - (L1[k] - vanleer(aL, bL, eps));
+        dnu_acc += F2 * lf * inv_nu;
+      }
+    }
+    // cell i-4 is complete
+    const int jc = s0 + it - 9;  // unwrapped index of cell i-4
+    if (it >= 9 && live && jc < n) {
+      float luh[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      split_flux_vjp(H0, F, gam, aR0, aL0, luh);
+      const long long oc = goff<AXIS>(jc, w, t3, n);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        luh_out[k * N3 + oc] = luh[k];
+        dnu_acc -= 0.5f * luh[k] * D0[k];
+      }
+    }
+    // shift the windows
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      aR0[k] = aR1[k];
+      aR1[k] = aR2[k];
+      aR2[k] = 0.0f;
+      aL0[k] = aL1[k];
+      aL1[k] = aL2[k];
+      aL2[k] = aL3[k];
+      aL3[k] = 0.0f;
+      H0[k] = H1[k];
+      H1[k] = H2[k];
+      H2[k] = uh[k];
+      D0[k] = D1[k];
+      D1[k] = D2[k];
+      D2[k] = dF[k];
+      R0[k] = R1[k];
+      R1[k] = R2[k];
+      R2[k] = FRh[k];
+      L0[k] = L1[k];
+      L1[k] = FLh[k];
+      M0[k] = M1[k];
+      M1[k] = M2[k];
+      M2[k] = lo[k];
+      Uc[k] = u[k];
+      FRp[k] = FR[k];
+      f1m[k] = f1[k];
+    }
+    j = jn;
+  }
+  if (dnu) {
+    if (!live) dnu_acc = 0.0f;
+    block_sum_atomic(dnu_acc, dnu);
+  }
+}
+
+// Pass 2: lam_in_k = lam_out_k + lamUh_k + VJP(U_k; nu/2 (lamUh_{k+1} - lamUh_k),
+// -nu/2 (lamUh_k - lamUh_{k-1})), one thread per cell.
+template <int AXIS>
+__global__ void __launch_bounds__(256)
+sweep_adj_final_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
+                       const float* __restrict__ luh, float* __restrict__ lin, int n,
+                       float nu, float gam) {
+  constexpr int F = 1 + AXIS;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= n) return;
+  const long long N3 = (long long)n * n * n;
+  const long long o = ((long long)z * n + y) * n + x;
+  int cm, cp;  // neighbour offsets along the sweep axis (periodic)
+  long long om, op;
+  if (AXIS == 0) {
+    cm = x == 0 ? n - 1 : x - 1;
+    cp = x + 1 == n ? 0 : x + 1;
+    om = o - x + cm;
+    op = o - x + cp;
+  } else if (AXIS == 1) {
+    cm = y == 0 ? n - 1 : y - 1;
+    cp = y + 1 == n ? 0 : y + 1;
+    om = o + (long long)(cm - y) * n;
+    op = o + (long long)(cp - y) * n;
+  } else {
+    cm = z == 0 ? n - 1 : z - 1;
+    cp = z + 1 == n ? 0 : z + 1;
+    om = o + (long long)(cm - z) * n * n;
+    op = o + (long long)(cp - z) * n * n;
+  }
+  float u[5], lR[5], lL[5], lu[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    u[k] = __ldg(uin + k * N3 + o);
+    const float h0 = __ldg(luh + k * N3 + o);
+    const float hm = __ldg(luh + k * N3 + om);
+    const float hp = __ldg(luh + k * N3 + op);
+    lR[k] = 0.5f * nu * (hp - h0);
+    lL[k] = -0.5f * nu * (h0 - hm);
+    lu[k] = __ldg(lout + k * N3 + o) + h0;
+  }
+  split_flux_vjp(u, F, gam, lR, lL, lu);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) lin[k * N3 + o] = lu[k];
 }
 
 // ------------------------------------------------------------------------- adjoint
@@ -370,18 +591,25 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
   if (dnu) block_sum_atomic(dnu_acc, dnu);
 }
 
+// Kernel choice, measured on GB300 (sweep of 5 float32 fields): the shared-memory tile
+// (16 x 32 lines for y/z) is fastest up to n ~ 128 (51 us at 128^3 for every axis); the
+// marching form with segments of 32 wins for y/z on larger grids (335 us vs 386 us at
+// 256^3). The x sweep always uses the tile (marching along x is not coalesced).
 #ifndef DH_SWEEP_MARCH
-#define DH_SWEEP_MARCH 0
+#define DH_SWEEP_MARCH 1
 #endif
 #ifndef DH_MARCH_L
-#define DH_MARCH_L 16
+#define DH_MARCH_L 32
+#endif
+#ifndef DH_MARCH_MIN_N
+#define DH_MARCH_MIN_N 192
 #endif
 
 template <int AXIS>
 static sim_status launch_sweep_t(const float* uin, float* uout, int n, float nu, float gam,
                                  float eps, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  if (DH_SWEEP_MARCH == 2 || (DH_SWEEP_MARCH == 1 && AXIS != 0)) {
+  if (DH_SWEEP_MARCH == 2 || (DH_SWEEP_MARCH == 1 && AXIS != 0 && n >= DH_MARCH_MIN_N)) {
     constexpr int L = DH_MARCH_L;
     dim3 grid(cdiv(n, 128), n, cdiv(n, L));
     sweep_march_kernel<AXIS, L><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps);
@@ -390,31 +618,43 @@ static sim_status launch_sweep_t(const float* uin, float* uout, int n, float nu,
   }
   constexpr int NC = (C::S + 6) * C::W;
   const size_t smem = 15 * NC * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    DH_CUDA_TRY(cudaFuncSetAttribute(sweep_fwd_kernel<AXIS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
   dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n);
   sweep_fwd_kernel<AXIS><<<grid, C::NT, smem, st>>>(uin, uout, n, nu, gam, eps);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
+// Adjoint kernel choice: the marching pair (pass 1 + pass 2, segments of DH_ADJ_L) for
+// the y and z sweeps, the shared-memory tile for x (DH_ADJ_MARCH = 0: tile everywhere,
+// 2: marching everywhere).
+#ifndef DH_ADJ_MARCH
+#define DH_ADJ_MARCH 1
+#endif
+#ifndef DH_ADJ_L
+#define DH_ADJ_L 32
+#endif
+
 template <int AXIS>
 static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float* lin, int n,
                                      float nu, float gam, float eps, double* dnu,
-                                     cudaStream_t st) {
+                                     float* scratch, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
+  if (DH_ADJ_MARCH == 2 || (DH_ADJ_MARCH == 1 && AXIS != 0)) {
+    constexpr int L = DH_ADJ_L;
+    if (!scratch) {
+      set_error("internal: marching sweep adjoint needs a 5 n^3 scratch buffer");
+      return SIM_EINVAL;
+    }
+    dim3 g1(cdiv(n, 128), n, cdiv(n, L));
+    sweep_adj_march_kernel<AXIS, L><<<g1, 128, 0, st>>>(uin, lout, scratch, n, nu, gam, eps, dnu);
+    DH_LAUNCH_CHECK();
+    dim3 g2(cdiv(n, 256), n, n);
+    sweep_adj_final_kernel<AXIS><<<g2, 256, 0, st>>>(uin, lout, scratch, lin, n, nu, gam);
+    DH_LAUNCH_CHECK();
+    return SIM_OK;
+  }
   constexpr int NC = (C::SA + 10) * C::WA;
   const size_t smem = 20 * NC * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    DH_CUDA_TRY(cudaFuncSetAttribute(sweep_adj_kernel<AXIS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
   dim3 grid(cdiv(n, C::SA), cdiv(n, C::WA), n);
   sweep_adj_kernel<AXIS><<<grid, C::NTA, smem, st>>>(uin, lout, lin, n, nu, gam, eps, dnu);
   DH_LAUNCH_CHECK();
@@ -433,16 +673,24 @@ static sim_status set_sweep_attributes() {
   return SIM_OK;
 }
 
-// Shared-memory limits of the sweep kernels, set on the current device before any launch
-// (and before any stream capture).
+// Shared-memory limits of the sweep kernels, set once per device before its first sweep
+// launch (sim_init calls this too, so that no attribute call happens during a capture).
 sim_status prepare_sweep_kernels() {
+  static std::atomic<unsigned long long> done{0};  // one bit per device index < 64
+  int dev = 0;
+  DH_CUDA_TRY(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return SIM_OK;
   DH_TRY(set_sweep_attributes<0>());
   DH_TRY(set_sweep_attributes<1>());
-  return set_sweep_attributes<2>();
+  DH_TRY(set_sweep_attributes<2>());
+  done.fetch_or(bit);
+  return SIM_OK;
 }
 
 sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double nu,
                         double gam, double eps, cudaStream_t st) {
+  DH_TRY(prepare_sweep_kernels());
   switch (axis) {
     case 0: return launch_sweep_t<0>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
     case 1: return launch_sweep_t<1>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
@@ -454,11 +702,13 @@ sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double n
 
 sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
                                 int n, double nu, double gam, double eps, double* dnu,
-                                cudaStream_t st) {
+                                float* scratch, cudaStream_t st) {
+  DH_TRY(prepare_sweep_kernels());
+  const float fnu = (float)nu, fg = (float)gam, fe = (float)eps;
   switch (axis) {
-    case 0: return launch_sweep_adj_t<0>(uin, lout, lin, n, (float)nu, (float)gam, (float)eps, dnu, st);
-    case 1: return launch_sweep_adj_t<1>(uin, lout, lin, n, (float)nu, (float)gam, (float)eps, dnu, st);
-    case 2: return launch_sweep_adj_t<2>(uin, lout, lin, n, (float)nu, (float)gam, (float)eps, dnu, st);
+    case 0: return launch_sweep_adj_t<0>(uin, lout, lin, n, fnu, fg, fe, dnu, scratch, st);
+    case 1: return launch_sweep_adj_t<1>(uin, lout, lin, n, fnu, fg, fe, dnu, scratch, st);
+    case 2: return launch_sweep_adj_t<2>(uin, lout, lin, n, fnu, fg, fe, dnu, scratch, st);
   }
   set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
   return SIM_EINVAL;
@@ -482,6 +732,11 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
     dh::set_error("sim_sweep_adjoint: null/aliased buffers or n < 1");
     return SIM_EINVAL;
   }
-  return dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, nu, gamma, limiter_eps, dnu,
-                                  (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  float* scratch = nullptr;
+  DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 5ull * n * n * n * sizeof(float), st));
+  const sim_status r = dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, nu, gamma,
+                                                limiter_eps, dnu, scratch, st);
+  cudaFreeAsync(scratch, st);
+  return r;
 }

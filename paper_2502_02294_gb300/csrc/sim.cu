@@ -52,7 +52,7 @@ sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double n
                         double eps, cudaStream_t st);
 sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
                                 int n, double nu, double gam, double eps, double* dnu,
-                                cudaStream_t st);
+                                float* scratch, cudaStream_t st);
 sim_status prepare_sweep_kernels();
 
 static const char* kOrders[6] = {"xyz", "zyx", "zxy", "yxz", "yzx", "xzy"};
@@ -132,6 +132,7 @@ struct sim_s {
   float *w_gas = nullptr, *w_gas2 = nullptr, *w_s = nullptr, *w_p = nullptr, *w_g = nullptr;
   float *lam_gas = nullptr, *lam_tmp = nullptr, *lam_s = nullptr, *lam_p = nullptr;
   float *lamG0 = nullptr, *lamG1 = nullptr, *lam_delta = nullptr, *lam4 = nullptr;
+  float* lam_scr = nullptr;  // 5 n^3 scratch of the marching sweep adjoint
   double* dslots = nullptr;  // (n_steps + 2) x SL_N
   double* dcoef = nullptr;   // (n_steps) x SL_N chain-rule coefficients
   double* dglob = nullptr;   // SIM_NPARAMS + GX_N
@@ -417,6 +418,7 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
     DH_TRY(dalloc_t(h, &h->lamG1, 3 * N3));
     DH_TRY(dalloc_t(h, &h->lam_delta, N3));
     DH_TRY(dalloc_t(h, &h->lam4, 4 * N3));
+    DH_TRY(dalloc_t(h, &h->lam_scr, 5 * N3));
     DH_TRY(dalloc_t(h, &h->dglob, SIM_NPARAMS + GX_N));
     DH_TRY(dalloc_t(h, &h->dslots, (size_t)(h->prm.n_steps + 2) * SL_N));
   }
@@ -496,7 +498,7 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot)
     const float* ins[3] = {T.Uk1, T.Us1, T.Us2};
     for (int k = 2; k >= 0; --k) {
       DH_TRY(launch_sweep_adjoint(order[k] - 'x', ins[k], h->lam_gas, h->lam_tmp, h->n, nu,
-                                  P.gamma, P.limiter_eps, slot + SL_DNU, st));
+                                  P.gamma, P.limiter_eps, slot + SL_DNU, h->lam_scr, st));
       float* t = h->lam_gas;
       h->lam_gas = h->lam_tmp;
       h->lam_tmp = t;
