@@ -10,7 +10,8 @@ spectral Poisson), the density loss against a mock field, and the checkpointed a
 value     cell-steps/s of that pass = 128^3 * 100 / time, summed over ranks (replicas).
 e2e       the same through the C ABI with the noise copied from pinned host memory and
           the noise gradient plus the loss copied back inside the timed region.
-roofline  the dominant kernel (hydro sweeps), timed with CUDA events on its stream.
+roofline  the dominant kernel class (hydro sweeps or their adjoints), each launch timed with
+          CUDA events on the simulation stream during one eager pass of the same hot path.
 cpu_baseline  the FP64 oracle on the host cores on a bounded sample of the same workload.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -38,7 +39,17 @@ WORKLOAD = dict(n=128, box=128.0, n_steps=100, a_start=0.05, a_end=1.0, ckpt_eve
 WORKLOAD_NAME = ("128^3 cells + 128^3 DM particles, box 128 Mpc/h, 100 steps a=0.05->1.0, "
                  "subgrid on, ICs + forward + density-MSE loss + checkpointed adjoint "
                  "(every 10 steps) to the 2,097,152 white-noise amplitudes and 7 parameters")
-SWEEP_BYTES_PER_CELL = 40  # 5 float32 fields read + 5 written
+SWEEP_BYTES_PER_CELL = 40      # sweep: 5 float32 fields read + 5 written
+SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, input adjoint written
+# DRAM bytes per cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# captures summarised in profiles/; None where no capture of the current kernel exists
+TRAFFIC_BYTES_PER_CELL = {"sweep": 21.06, "sweep_adjoint": 97.99}  # 128^3, cold cache
+
+
+def _config(ws: int):
+    return {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "n_steps": WORKLOAD["n_steps"],
+            "ckpt_every": WORKLOAD["ckpt_every"], "parallelism": f"replicas x{ws}",
+            "l2": "512 MB buffer written between timed iterations"}
 
 
 def _peaks():
@@ -145,8 +156,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "one full step (forward + reverse) of the 128^3 workload "
-                                   "per bench step: " + WORKLOAD_NAME},
+            "config": _config(args.gpus),
             "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": threads,
                              "kind": "oracle",
                              "sample": "1 step fwd+reverse at 128^3 per bench step"},
@@ -223,6 +233,7 @@ def main():
     launches0 = dh.lib.sim_kernel_launches()
     times = []
     barrier()
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -231,6 +242,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = dh.lib.sim_kernel_launches() - launches0
     clk = clocks.stop()
@@ -266,25 +278,27 @@ def main():
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
     e2e_ms = statistics.mean(e2e_times)
-    # ---- dominant kernel: the three hydro sweeps, timed on the launching stream
-    gas = sim.state()["gas"]
-    out = torch.empty_like(gas)
-    nu = sim.schedule(50)["dtau"] * n / p.box
-    reps = 20
-    for axis in range(3):
-        dh.sweep(gas, axis, nu)
+    # ---- kernel classes inside one pass: the same hot path run eagerly with every sweep
+    # launch bracketed by CUDA events on the simulation's stream
+    sim.kernel_timing(True)
+    sim.kernel_times(reset=True)
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for r in range(reps):
-        for axis in range(3):
-            dh.lib.sim_sweep(dh.api._ptr(gas if r % 2 == 0 else out),
-                             dh.api._ptr(out if r % 2 == 0 else gas), n, axis, nu, p.gamma,
-                             p.limiter_eps, dh.api._stream())
+    hot_path(noise)
     e1.record(stream)
     e1.synchronize()
-    sweep_ms = e0.elapsed_time(e1) / (3 * reps)
-    sweep_gbs = SWEEP_BYTES_PER_CELL * n3 / (sweep_ms * 1e-3) / 1e9
+    inst_ms = e0.elapsed_time(e1)
+    kt = sim.kernel_times(reset=True)
+    sim.kernel_timing(False)
+    kclass = {}
+    for name, bpc in (("sweep", SWEEP_BYTES_PER_CELL), ("sweep_adjoint", SWEEP_ADJ_BYTES_PER_CELL)):
+        tot, cnt = kt[name]
+        avg = tot / max(cnt, 1)
+        kclass[name] = {"launches": cnt, "total_ms": tot, "share_of_pass": tot / inst_ms,
+                        "avg_launch_ms": avg,
+                        "achieved_gbs": bpc * n3 / (avg * 1e-3) / 1e9 if cnt else None}
+    dom = max(kclass, key=lambda k: kclass[k]["total_ms"])
 
     # ---- max over ranks
     vals = torch.tensor([ms, fwd_ms, e2e_ms], dtype=torch.float64, device=dev)
@@ -311,20 +325,25 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "n": n, "n_steps": p.n_steps,
-                   "ckpt_every": p.ckpt_every, "parallelism": f"replicas x{ws}",
-                   "l2": "512 MB buffer written between timed iterations",
-                   "cuda_graphs": not args.no_graphs},
+        "config": _config(ws),
+        "cuda_graphs": not args.no_graphs,
         "fwd_value": cell_steps / (fwd_ms / 1e3),
         "fwd_ms_per_step": fwd_ms,
         "e2e": {"value": cell_steps / (e2e_ms / 1e3), "unit": "cell-steps/s",
                 "h2d_bytes_per_step": n3 * 4, "d2h_bytes_per_step": n3 * 4 + 8},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": peak_bw, "unit": "GB/s",
-                     "frac": sweep_gbs / peak_bw, "traffic": None,
-                     "kernel": "sweep_fwd_kernel (x, y, z average)",
-                     "algorithmic_bytes_per_launch": SWEEP_BYTES_PER_CELL * n3,
-                     "launch_ms": sweep_ms,
+        "roofline": {"bound": "hbm", "achieved": kclass[dom]["achieved_gbs"], "peak": peak_bw,
+                     "unit": "GB/s", "frac": kclass[dom]["achieved_gbs"] / peak_bw,
+                     "traffic": (TRAFFIC_BYTES_PER_CELL[dom] * n3
+                                 if TRAFFIC_BYTES_PER_CELL[dom] is not None else None),
+                     "kernel": {"sweep": "hydro sweep (x, y, z average)",
+                                "sweep_adjoint": "adjoint hydro sweep (x, y, z average)"}[dom],
+                     "algorithmic_bytes_per_launch":
+                         (SWEEP_BYTES_PER_CELL if dom == "sweep" else SWEEP_ADJ_BYTES_PER_CELL) * n3,
+                     "launch_ms": kclass[dom]["avg_launch_ms"],
+                     "timed_in": "one eager pass of the hot path, CUDA events around every "
+                                 "launch on the simulation stream (%.1f ms pass)" % inst_ms,
+                     "classes": kclass,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
                      else "fallback 6.8 TB/s (of fallback)"},
         "clocks": clk,

@@ -135,6 +135,25 @@ void sim_destroy(sim_t* h);
  * on == 0 drops all graphs. Default off. */
 sim_status sim_set_graphs(sim_t* h, int32_t on);
 
+/* Kernel classes timed by sim_kernel_timing. The paper has no counterpart: these exist to
+ * measure the sweep kernels of Sec. 2.3 inside a real run. */
+enum {
+  SIM_KT_SWEEP = 0,          /* forward sweeps, including the reverse pass's recompute */
+  SIM_KT_SWEEP_ADJOINT = 1,  /* adjoint sweeps */
+  SIM_KT_N = 2
+};
+
+/* enable != 0: later sim_step / sim_run / sim_step_adjoint / sim_run_adjoint calls run
+ * eagerly (no graph replay) and bracket every launch of a timed class with two CUDA events
+ * on the handle's stream; up to 8192 launches are recorded between resets, later ones run
+ * untimed. enable == 0 stops recording. Default off. */
+sim_status sim_kernel_timing(sim_t* h, int32_t enable);
+
+/* Host arrays ms[SIM_KT_N] and count[SIM_KT_N] receive the summed device time (ms) and the
+ * number of recorded launches per class; waits for the last recorded event. reset != 0
+ * clears the records afterwards. SIM_EINVAL on a NULL argument. */
+sim_status sim_kernel_times(sim_t* h, double* ms, int64_t* count, int32_t reset);
+
 /* Advance one step a_n -> a_{n+1}: half kick (DM + gas), DM drift, three Strang-ordered
  * hydro sweeps (order XYZ, ZYX, ZXY, YXZ, YZX, XZY by n mod 6, Sec. 2.3.2), subgrid,
  * CIC deposit + Poisson (Sec. 2.2), half kick. Keeps a copy of the step's input state

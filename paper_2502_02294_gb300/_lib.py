@@ -17,6 +17,7 @@ SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ECFL, SIM_ENAN, SIM_ETIMEOUT, SIM
 STATUS_NAMES = ["SIM_OK", "SIM_EINVAL", "SIM_ENOMEM", "SIM_ECUDA", "SIM_ECFL", "SIM_ENAN",
                 "SIM_ETIMEOUT", "SIM_ENOTIMPL"]
 P_OMEGA_M, P_SIGMA8, P_DELTA_C, P_PI0, P_E0, P_T0_UV, P_GAMMA_UV, NPARAMS = range(8)
+KT_SWEEP, KT_SWEEP_ADJOINT, KT_N = range(3)
 PARAM_NAMES = ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"]
 
 
@@ -55,6 +56,8 @@ SIGNATURES = {
     "sim_init": (ctypes.c_int, [_PP, _P, _P, ctypes.POINTER(_P)]),
     "sim_destroy": (None, [_P]),
     "sim_set_graphs": (ctypes.c_int, [_P, _I32]),
+    "sim_kernel_timing": (ctypes.c_int, [_P, _I32]),
+    "sim_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
     "sim_step": (ctypes.c_int, [_P]),
     "sim_step_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "sim_run": (ctypes.c_int, [_P, _I32]),

@@ -9,7 +9,8 @@ import ctypes
 
 import torch
 
-from ._lib import (NPARAMS, SimParams, check, default_params, lib)
+from ._lib import (KT_N, KT_SWEEP, KT_SWEEP_ADJOINT, NPARAMS, SimParams, check,
+                   default_params, lib)
 
 F32, F64, U32 = torch.float32, torch.float64, torch.int32
 
@@ -235,6 +236,20 @@ class Simulation:
         c = ctypes.c_double()
         self._check(lib.sim_cfl(self.h, ctypes.byref(c)), "sim_cfl")
         return c.value
+
+    def set_graphs(self, on: bool = True):
+        self._check(lib.sim_set_graphs(self.h, int(on)), "sim_set_graphs")
+
+    def kernel_timing(self, on: bool = True):
+        self._check(lib.sim_kernel_timing(self.h, int(on)), "sim_kernel_timing")
+
+    def kernel_times(self, reset: bool = True):
+        """{class: (total ms, launches)} recorded since the last reset."""
+        ms = (ctypes.c_double * KT_N)()
+        cnt = (ctypes.c_int64 * KT_N)()
+        self._check(lib.sim_kernel_times(self.h, ms, cnt, int(reset)), "sim_kernel_times")
+        return {"sweep": (ms[KT_SWEEP], cnt[KT_SWEEP]),
+                "sweep_adjoint": (ms[KT_SWEEP_ADJOINT], cnt[KT_SWEEP_ADJOINT])}
 
 
 class SimRunFunction(torch.autograd.Function):

@@ -137,6 +137,12 @@ struct sim_s {
   double* dcoef = nullptr;   // (n_steps) x SL_N chain-rule coefficients
   double* dglob = nullptr;   // SIM_NPARAMS + GX_N
   unsigned int* speed_bits = nullptr;
+  // optional per-class kernel timing: event pairs around each timed launch (eager runs only)
+  bool kt_on = false;
+  std::vector<cudaEvent_t> kt_ev;  // 2 per recorded launch
+  std::vector<int> kt_cls;
+  size_t kt_used = 0;
+  long long kt_dropped = 0;
   // graphs
   bool graphs = false;
   cudaStream_t cap_stream = nullptr;
@@ -218,7 +224,7 @@ static void restore(sim_t* h, const HostState& s) {
 template <class Body>
 static sim_status run_maybe_graph(sim_t* h, int kind, const std::vector<uintptr_t>& key,
                                   Body body) {
-  if (!h->graphs) return body();
+  if (!h->graphs || h->kt_on) return body();
   const HostState before = snapshot(h);
   for (GraphEntry& e : h->graph_cache) {
     if (e.kind == kind && e.key == key && e.before == before) {
@@ -281,6 +287,32 @@ static void clear_graphs(sim_t* h) {
   for (GraphEntry& e : h->graph_cache)
     if (e.exec) cudaGraphExecDestroy(e.exec);
   h->graph_cache.clear();
+}
+
+// Launch through `launch`; with kernel timing on, bracket it with two events on the
+// handle's stream (class `cls`). At most kKtMax launches are recorded between resets.
+static constexpr size_t kKtMax = 8192;
+template <class Launch>
+static sim_status timed(sim_t* h, int cls, Launch launch) {
+  if (!h->kt_on) return launch();
+  if (h->kt_used >= kKtMax) {
+    ++h->kt_dropped;
+    return launch();
+  }
+  if (2 * h->kt_used + 2 > h->kt_ev.size()) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e;
+      DH_CUDA_TRY(cudaEventCreate(&e));
+      h->kt_ev.push_back(e);
+    }
+    h->kt_cls.push_back(cls);
+  }
+  h->kt_cls[h->kt_used] = cls;
+  DH_CUDA_TRY(cudaEventRecord(h->kt_ev[2 * h->kt_used], h->st));
+  DH_TRY(launch());
+  DH_CUDA_TRY(cudaEventRecord(h->kt_ev[2 * h->kt_used + 1], h->st));
+  ++h->kt_used;
+  return SIM_OK;
 }
 
 static sim_status validate(const sim_params* p) {
@@ -363,7 +395,9 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     float* outs_tape[3] = {T ? T->Us1 : nullptr, T ? T->Us2 : nullptr, T ? T->Us3 : nullptr};
     for (int k = 0; k < 3; ++k) {
       float* out = T ? outs_tape[k] : (cur == *gas ? *gas_tmp : *gas);
-      DH_TRY(launch_sweep(order[k] - 'x', cur, out, h->n, nu, P.gamma, P.limiter_eps, st));
+      DH_TRY(timed(h, SIM_KT_SWEEP, [&] {
+        return launch_sweep(order[k] - 'x', cur, out, h->n, nu, P.gamma, P.limiter_eps, st);
+      }));
       cur = out;
     }
   } else if (T) {
@@ -497,8 +531,10 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot)
     const double nu = f.dtau * h->inv_dx;
     const float* ins[3] = {T.Uk1, T.Us1, T.Us2};
     for (int k = 2; k >= 0; --k) {
-      DH_TRY(launch_sweep_adjoint(order[k] - 'x', ins[k], h->lam_gas, h->lam_tmp, h->n, nu,
-                                  P.gamma, P.limiter_eps, slot + SL_DNU, h->lam_scr, st));
+      DH_TRY(timed(h, SIM_KT_SWEEP_ADJOINT, [&] {
+        return launch_sweep_adjoint(order[k] - 'x', ins[k], h->lam_gas, h->lam_tmp, h->n, nu,
+                                    P.gamma, P.limiter_eps, slot + SL_DNU, h->lam_scr, st);
+      }));
       float* t = h->lam_gas;
       h->lam_gas = h->lam_tmp;
       h->lam_tmp = t;
@@ -783,6 +819,7 @@ void sim_destroy(sim_t* h) {
   cudaStreamSynchronize(h->st);
   if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
   clear_graphs(h);
+  for (cudaEvent_t e : h->kt_ev) cudaEventDestroy(e);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->plans.destroy();
   for (void* a : h->allocs)
@@ -794,6 +831,35 @@ sim_status sim_set_graphs(sim_t* h, int32_t on) {
   if (!h) return SIM_EINVAL;
   if (!on) clear_graphs(h);
   h->graphs = on != 0;
+  return SIM_OK;
+}
+
+sim_status sim_kernel_timing(sim_t* h, int32_t enable) {
+  if (!h) return SIM_EINVAL;
+  h->kt_on = enable != 0;
+  return SIM_OK;
+}
+
+sim_status sim_kernel_times(sim_t* h, double* ms, int64_t* count, int32_t reset) {
+  if (!h || !ms || !count) {
+    set_error("sim_kernel_times: null argument");
+    return SIM_EINVAL;
+  }
+  for (int c = 0; c < SIM_KT_N; ++c) {
+    ms[c] = 0.0;
+    count[c] = 0;
+  }
+  if (h->kt_used) DH_CUDA_TRY(cudaEventSynchronize(h->kt_ev[2 * h->kt_used - 1]));
+  for (size_t i = 0; i < h->kt_used; ++i) {
+    float t = 0.0f;
+    DH_CUDA_TRY(cudaEventElapsedTime(&t, h->kt_ev[2 * i], h->kt_ev[2 * i + 1]));
+    ms[h->kt_cls[i]] += t;
+    count[h->kt_cls[i]] += 1;
+  }
+  if (reset) {
+    h->kt_used = 0;
+    h->kt_dropped = 0;
+  }
   return SIM_OK;
 }
 

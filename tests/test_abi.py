@@ -82,6 +82,8 @@ def test_null_arguments_rejected(dh):
     assert L.sim_deposit_cic(None, None, 8, 8.0, None, None) == dh._lib.SIM_EINVAL
     assert L.sim_power_spectrum(None, None, 8, 8.0, 4, None, None, None, None) == dh._lib.SIM_EINVAL
     assert L.sim_step(None) == dh._lib.SIM_EINVAL
+    assert L.sim_kernel_timing(None, 1) == dh._lib.SIM_EINVAL
+    assert L.sim_kernel_times(None, None, None, 0) == dh._lib.SIM_EINVAL
     L.sim_destroy(None)  # ignored
 
 
