@@ -46,6 +46,113 @@ SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, i
 TRAFFIC_BYTES_PER_CELL = {"sweep": 21.06, "sweep_adjoint": 97.99}  # 128^3, cold cache
 
 
+BATCH_SIZES = (32, 48, 64)
+BATCH_PER_SIZE = 32
+BATCH_RANGES = {"omega_m": (0.25, 0.35), "sigma8": (0.7, 0.9), "delta_c": (50.0, 200.0),
+                "Pi0": (0.01, 0.1), "T0_uv": (5.0e3, 2.0e4), "gamma_uv": (1.2, 1.6)}
+BATCH_NAME = ("96 instances (32 each at 32^3, 48^3, 64^3; box n Mpc/h), per-instance "
+              "Omega_m~U[0.25,0.35], sigma8~U[0.7,0.9], delta_c~U[50,200], Pi0~U[0.01,0.1], "
+              "T0~U[5e3,2e4] K, gamma~U[1.2,1.6], own Philox seed; 40 steps a=0.1->1.0, "
+              "subgrid on; forward + parameter gradients (checkpoint every 10)")
+
+
+def bench_batched(dh, synth, torch, steps: int, warmup: int):
+    """Parameter-sampling form: three batched handles (one per grid size) run as one graph
+    group, against the same 96 instances run one handle at a time (graphs on)."""
+    draws = synth.uniform_params(2024, len(BATCH_SIZES) * BATCH_PER_SIZE, BATCH_RANGES)
+    groups = []
+    for k, n in enumerate(BATCH_SIZES):
+        ps = []
+        for b in range(BATCH_PER_SIZE):
+            i = k * BATCH_PER_SIZE + b
+            ps.append(dh.default_params(n=n, box=float(n), n_steps=40, a_start=0.1, a_end=1.0,
+                                        ckpt_every=10, subgrid_on=1, E0=0.03, seed=1000 + i,
+                                        instance=i, **draws[i]))
+        groups.append(ps)
+    cells = sum(n ** 3 * BATCH_PER_SIZE for n in BATCH_SIZES) * 40
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def loss_grad(sim):
+        st = sim.state()["gas"]
+        dL = torch.zeros_like(st)
+        dL[:, 0] = st[:, 0] - st[:, 0].mean()
+        return dL.contiguous()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    # batched: one handle per size, autotuned sweeps, one graph group
+    sims = [dh.Simulation(ps) for ps in groups]
+    variants = [sim.autotune(reps=3) for sim in sims]
+    for sim in sims:
+        sim.run()
+    dls = [loss_grad(sim) for sim in sims]
+    outs = [torch.zeros(BATCH_PER_SIZE, dh.NPARAMS, dtype=torch.float64, device=dev) for _ in sims]
+    cfl = max(sim.cfl() for sim in sims)
+    for sim in sims:
+        sim.reset()
+    grp = dh.Group(sims)
+
+    def batched_pass():
+        grp.reset()
+        grp.run()
+        grp.run_adjoint(dls, out=outs)
+
+    for _ in range(warmup):
+        batched_pass()
+    ms_b = timed(batched_pass, steps)
+    launches0 = dh.lib.sim_kernel_launches()
+    batched_pass()
+    torch.cuda.synchronize()
+    launches_b = dh.lib.sim_kernel_launches() - launches0
+    grp.close()
+    for sim in sims:
+        sim.close()
+    # the same instances one handle at a time
+    solo = []
+    for ps, dl in zip(groups, dls):
+        for b, p in enumerate(ps):
+            sim = dh.Simulation(p)
+            sim.set_graphs(True)
+            solo.append((sim, dl[b].contiguous(),
+                         torch.zeros(dh.NPARAMS, dtype=torch.float64, device=dev)))
+
+    def solo_pass():
+        for sim, dl, out in solo:
+            sim.reset()
+            sim.run()
+            dh._lib.check(dh.lib.sim_run_adjoint(sim.h, dh.api._ptr(dl), None, None,
+                                                 dh.api._ptr(out)), "sim_run_adjoint", sim.h)
+
+    for _ in range(warmup):
+        solo_pass()
+    ms_s = timed(solo_pass, steps)
+    # agreement of the parameter gradients of the two forms (same instances, same inputs)
+    worst = 0.0
+    idx = 0
+    for k in range(len(BATCH_SIZES)):
+        for b in range(BATCH_PER_SIZE):
+            ref = solo[idx][2]
+            worst = max(worst, ((outs[k][b] - ref).norm() / ref.norm().clamp_min(1e-300)).item())
+            idx += 1
+    for sim, _, _ in solo:
+        sim.close()
+    return {"workload": BATCH_NAME, "value": cells / (ms_b / 1e3), "unit": "cell-steps/s",
+            "ms_per_pass": ms_b, "solo_value": cells / (ms_s / 1e3), "solo_ms_per_pass": ms_s,
+            "speedup_vs_solo": ms_s / ms_b, "gpu_launches_per_pass": int(launches_b),
+            "max_cfl": cfl, "grad_rel_diff_vs_solo": worst,
+            "sweep_variants": {str(n): {"fwd": v[0], "adj": v[1]}
+                               for n, v in zip(BATCH_SIZES, variants)}}
+
+
 def _config(ws: int):
     return {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "n_steps": WORKLOAD["n_steps"],
             "ckpt_every": WORKLOAD["ckpt_every"], "parallelism": f"replicas x{ws}",
@@ -172,6 +279,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched parameter-sampling measurement")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured graphs")
     args = ap.parse_args()
@@ -300,6 +409,13 @@ def main():
                         "achieved_gbs": bpc * n3 / (avg * 1e-3) / 1e9 if cnt else None}
     dom = max(kclass, key=lambda k: kclass[k]["total_ms"])
 
+    # ---- batched parameter-sampling form (96 instances on three grid sizes)
+    batched = None
+    if not args.no_batched:
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        batched = bench_batched(dh, synth, torch, steps=2, warmup=1)
+        torch.cuda.set_stream(stream)
+
     # ---- max over ranks
     vals = torch.tensor([ms, fwd_ms, e2e_ms], dtype=torch.float64, device=dev)
     if ws > 1:
@@ -348,6 +464,8 @@ def main():
                      else "fallback 6.8 TB/s (of fallback)"},
         "clocks": clk,
     }
+    if batched is not None:
+        line["batched"] = batched
     if not args.no_cpu_baseline:
         v, dt, threads = cpu_baseline_sample(1)
         line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": threads,

@@ -127,6 +127,79 @@ sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t
 /* Free the handle and its device memory (synchronises its stream). NULL is ignored. */
 void sim_destroy(sim_t* h);
 
+/* ------------------------------------------------------------------ batched instances
+ * Parameter sampling (Sec. 3: many simulations differing in cosmology, subgrid parameters
+ * and random seed) as one handle holding B instances on grids of the same size, stepped
+ * together: every kernel of the step runs all B instances in one launch and the FFTs are
+ * batched. p is a HOST array of B parameter sets that agree in n, box, n_steps, a_start,
+ * a_end, ckpt_every, subgrid_on, gravity_on, hydro_on, kdk_mode, gamma, mu, h, rms_ref,
+ * a_ref, sigma8_ref, omega_m_ref, kc_frac, limiter_eps and cfl_max (SIM_EINVAL
+ * otherwise); omega_m, omega_b, sigma8, T_init, the subgrid parameters, seed and instance
+ * may differ. noise: device B n^3 floats (instance b at b n^3) or NULL (Philox per
+ * instance). With B = 1 this is sim_init.
+ *
+ * Every whole-path entry below then takes arrays of all B instances one after another:
+ * gas B x 5 n^3, part B x 6 n^3, star / aux / noise / target B x n^3, events B x
+ * ceil(n^3/32) words, gravity B x 3 n^3, parameter derivatives B x SIM_NPARAMS and the
+ * loss of sim_loss_density B doubles. Instance b of a batch evolves bit for bit as a
+ * B = 1 handle with the same parameters (same kernels, same order of operations), except
+ * where cuFFT's batched transforms round differently from single ones. */
+sim_status sim_init_batch(const sim_params* p, int32_t B, const float* noise, void* stream,
+                          sim_t** out);
+
+/* Number of instances of the handle (1 for sim_init). */
+int32_t sim_batch_size(const sim_t* h);
+
+/* Hydro sweep kernel variants (Sec. 2.3.1 sweeps; the paper has no counterpart: these are
+ * GB300 launch shapes). DEFAULT: the built-in choice for the grid size; TILE: shared-memory
+ * tile; MARCH32 / MARCH16: one thread marches a line segment of 32 / 16 cells (y and z
+ * sweeps only; x always uses the tile). */
+enum {
+  SIM_SWEEP_DEFAULT = 0,
+  SIM_SWEEP_TILE = 1,
+  SIM_SWEEP_MARCH32 = 2,
+  SIM_SWEEP_MARCH16 = 3
+};
+
+/* Set the variant of the forward (fwd[3], per axis) and adjoint (adj[3]) sweeps of the
+ * handle. Host arrays; NULL leaves that set unchanged. Drops captured graphs. */
+sim_status sim_set_sweep_variants(sim_t* h, const int32_t* fwd, const int32_t* adj);
+
+/* ------------------------------------------------------------------ groups of handles
+ * Batches on grids of different sizes (e.g. 32 instances each at 32^3, 48^3 and 64^3): one
+ * batched handle per size, run as a group. The group captures its members' runs into one
+ * CUDA graph with one concurrent branch per member and replays it with a single graph
+ * launch on `stream` (members are used on their branches during the call and must not be
+ * used concurrently elsewhere; create them on the same stream). The paper has no
+ * counterpart: this is the launch structure of many-sample parameter studies (Sec. 3). */
+typedef struct sim_group_s sim_group_t;
+
+/* members: host array of `count` distinct handles (not owned). */
+sim_status sim_group_create(sim_t* const* members, int32_t count, void* stream,
+                            sim_group_t** out);
+
+/* sim_run of every member from its initial state to its last step (cfl_max must be 0). */
+sim_status sim_group_run(sim_group_t* g);
+
+/* sim_run_adjoint of every member: dL_dgas[k] is member k's loss derivative at the final
+ * gas state (device, B_k x 5 n_k^3; the host array or an entry may be NULL = 0) and
+ * dL_dparams[k] receives its B_k x SIM_NPARAMS parameter derivatives (device, overwritten).
+ * No noise gradient. */
+sim_status sim_group_run_adjoint(sim_group_t* g, const float* const* dL_dgas,
+                                 double* const* dL_dparams);
+
+/* sim_reset of every member. */
+sim_status sim_group_reset(sim_group_t* g);
+
+/* Free the group (not its members); synchronises its stream. NULL is ignored. */
+void sim_group_destroy(sim_group_t* g);
+
+/* Autotuner: times every variant of each forward and adjoint sweep on the handle's current
+ * state (all B instances, CUDA events, `reps` launches each, best of them), keeps the
+ * fastest per axis, and writes the choice to fwd_out[3] / adj_out[3] (host, may be NULL).
+ * The state is not modified. Synchronises the stream; drops captured graphs. */
+sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_out);
+
 /* on != 0: sim_run and sim_run_adjoint are captured into CUDA graphs the first time they
  * are called with a given argument set from a given handle state, and replayed afterwards
  * (launch overhead of the ~50 kernels per step removed). Capture happens on a private

@@ -18,6 +18,7 @@ STATUS_NAMES = ["SIM_OK", "SIM_EINVAL", "SIM_ENOMEM", "SIM_ECUDA", "SIM_ECFL", "
                 "SIM_ETIMEOUT", "SIM_ENOTIMPL"]
 P_OMEGA_M, P_SIGMA8, P_DELTA_C, P_PI0, P_E0, P_T0_UV, P_GAMMA_UV, NPARAMS = range(8)
 KT_SWEEP, KT_SWEEP_ADJOINT, KT_N = range(3)
+SWEEP_DEFAULT, SWEEP_TILE, SWEEP_MARCH32, SWEEP_MARCH16 = range(4)
 PARAM_NAMES = ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"]
 
 
@@ -54,7 +55,16 @@ SIGNATURES = {
     "sim_last_error": (ctypes.c_char_p, [_P]),
     "sim_kernel_launches": (ctypes.c_int64, []),
     "sim_init": (ctypes.c_int, [_PP, _P, _P, ctypes.POINTER(_P)]),
+    "sim_init_batch": (ctypes.c_int, [_PP, _I32, _P, _P, ctypes.POINTER(_P)]),
+    "sim_batch_size": (ctypes.c_int32, [_P]),
+    "sim_set_sweep_variants": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "sim_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sim_destroy": (None, [_P]),
+    "sim_group_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _P, ctypes.POINTER(_P)]),
+    "sim_group_run": (ctypes.c_int, [_P]),
+    "sim_group_run_adjoint": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "sim_group_reset": (ctypes.c_int, [_P]),
+    "sim_group_destroy": (None, [_P]),
     "sim_set_graphs": (ctypes.c_int, [_P, _I32]),
     "sim_kernel_timing": (ctypes.c_int, [_P, _I32]),
     "sim_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),

@@ -131,22 +131,44 @@ def power_spectrum(a, box: float, nbins: int, b=None):
 
 # ------------------------------------------------------------------ whole path
 class Simulation:
-    """Owns a sim_t handle. All methods enqueue on torch's current stream at creation."""
+    """Owns a sim_t handle. All methods enqueue on torch's current stream at creation.
 
-    def __init__(self, params: SimParams | None = None, noise=None, **overrides):
-        self.params = params if params is not None else default_params(**overrides)
-        if params is not None:
-            for k, v in overrides.items():
-                setattr(self.params, k, v)
+    `params` is one SimParams, or a list of SimParams for a batch of B instances on grids
+    of the same size (sim_init_batch). With B > 1 every array gains a leading instance
+    dimension (gas [B, 5, n, n, n], part [B, 6, n^3], noise / target [B, n, n, n],
+    parameter derivatives [B, NPARAMS], loss [B]); with B = 1 the shapes have none.
+    """
+
+    def __init__(self, params: SimParams | list | None = None, noise=None, **overrides):
+        if isinstance(params, (list, tuple)):
+            plist = list(params)
+            for q in plist:
+                for k, v in overrides.items():
+                    setattr(q, k, v)
+        else:
+            q = params if params is not None else default_params(**overrides)
+            if params is not None:
+                for k, v in overrides.items():
+                    setattr(q, k, v)
+            plist = [q]
+        self.B = len(plist)
+        self.params = plist[0]
+        self.params_list = plist
         n = self.params.n
         self.n = n
         if noise is not None:
-            _chk(noise, F32, n ** 3, "noise")
+            _chk(noise, F32, self.B * n ** 3, "noise")
         self._stream = torch.cuda.current_stream()
+        arr = (SimParams * self.B)(*plist)
+        self._arr = arr
         h = ctypes.c_void_p()
-        check(lib.sim_init(ctypes.byref(self.params), _ptr(noise),
-                           ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h)), "sim_init")
+        check(lib.sim_init_batch(arr, self.B, _ptr(noise),
+                                 ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h)),
+              "sim_init_batch")
         self.h = h
+
+    def _shape(self, *dims):
+        return dims if self.B == 1 else (self.B,) + dims
 
     def close(self):
         if getattr(self, "h", None):
@@ -166,9 +188,9 @@ class Simulation:
         self._check(lib.sim_step(self.h), "sim_step")
 
     def step_adjoint(self, adj_gas, adj_part, adj_params=None):
-        n = self.n
-        _chk(adj_gas, F32, 5 * n ** 3, "adj_gas")
-        _chk(adj_part, F32, 6 * n ** 3, "adj_part")
+        n, B = self.n, self.B
+        _chk(adj_gas, F32, 5 * B * n ** 3, "adj_gas")
+        _chk(adj_part, F32, 6 * B * n ** 3, "adj_part")
         self._check(lib.sim_step_adjoint(self.h, _ptr(adj_gas), _ptr(adj_part), _ptr(adj_params)),
                     "sim_step_adjoint")
 
@@ -178,8 +200,8 @@ class Simulation:
     def run_adjoint(self, dL_dgas=None, dL_dpart=None, want_noise: bool = True):
         n = self.n
         dev = torch.device("cuda", torch.cuda.current_device())
-        dnoise = torch.empty(n, n, n, dtype=F32, device=dev) if want_noise else None
-        dpar = torch.zeros(NPARAMS, dtype=F64, device=dev)
+        dnoise = torch.empty(self._shape(n, n, n), dtype=F32, device=dev) if want_noise else None
+        dpar = torch.zeros(self._shape(NPARAMS), dtype=F64, device=dev)
         self._check(lib.sim_run_adjoint(self.h, _ptr(dL_dgas), _ptr(dL_dpart), _ptr(dnoise), _ptr(dpar)),
                     "sim_run_adjoint")
         return dnoise, dpar
@@ -189,42 +211,45 @@ class Simulation:
 
     def reinit(self, noise=None):
         if noise is not None:
-            _chk(noise, F32, self.n ** 3, "noise")
+            _chk(noise, F32, self.B * self.n ** 3, "noise")
         self._check(lib.sim_reinit(self.h, _ptr(noise)), "sim_reinit")
 
     def loss_density(self, target, c: float, out=None, loss=None):
-        """(dL/dgas [5, n, n, n], loss [1] float64) of L = c sum (rho - target)^2."""
-        n = self.n
-        _chk(target, F32, n ** 3, "target")
+        """(dL/dgas [5, n, n, n], loss [1] float64) of L = c sum (rho - target)^2
+        (per instance with B > 1: [B, 5, n, n, n] and [B])."""
+        n, B = self.n, self.B
+        _chk(target, F32, B * n ** 3, "target")
         dev = target.device
-        out = torch.empty(5, n, n, n, dtype=F32, device=dev) if out is None else out
-        loss = torch.empty(1, dtype=F64, device=dev) if loss is None else loss
+        out = torch.empty(self._shape(5, n, n, n), dtype=F32, device=dev) if out is None else out
+        loss = torch.empty(B, dtype=F64, device=dev) if loss is None else loss
         self._check(lib.sim_loss_density(self.h, _ptr(target), c, _ptr(out), _ptr(loss)),
                     "sim_loss_density")
         return out, loss
 
     def state(self, gravity: bool = False):
         n = self.n
+        sh = self._shape
         dev = torch.device("cuda", torch.cuda.current_device())
-        gas = torch.empty(5, n, n, n, dtype=F32, device=dev)
-        part = torch.empty(6, n ** 3, dtype=F32, device=dev)
-        star = torch.empty(n, n, n, dtype=F32, device=dev)
-        aux = torch.empty(n ** 3, dtype=F32, device=dev)
-        events = torch.empty((n ** 3 + 31) // 32, dtype=U32, device=dev)
-        g = torch.empty(3, n, n, n, dtype=F32, device=dev) if gravity else None
+        gas = torch.empty(sh(5, n, n, n), dtype=F32, device=dev)
+        part = torch.empty(sh(6, n ** 3), dtype=F32, device=dev)
+        star = torch.empty(sh(n, n, n), dtype=F32, device=dev)
+        aux = torch.empty(sh(n ** 3), dtype=F32, device=dev)
+        events = torch.empty(sh((n ** 3 + 31) // 32), dtype=U32, device=dev)
+        g = torch.empty(sh(3, n, n, n), dtype=F32, device=dev) if gravity else None
         step = ctypes.c_int32()
         self._check(lib.sim_get_state(self.h, _ptr(gas), _ptr(part), _ptr(star), _ptr(aux),
                                       _ptr(events), _ptr(g), ctypes.byref(step)), "sim_get_state")
-        out = {"gas": gas, "s": part[:3], "p": part[3:], "star": star, "aux": aux,
+        s_, p_ = (part[:3], part[3:]) if self.B == 1 else (part[:, :3], part[:, 3:])
+        out = {"gas": gas, "s": s_, "p": p_, "star": star, "aux": aux,
                "events": events, "step": step.value}
         if gravity:
             out["g"] = g
         return out
 
     def set_state(self, gas, part, step: int):
-        n = self.n
-        _chk(gas, F32, 5 * n ** 3, "gas")
-        _chk(part, F32, 6 * n ** 3, "part")
+        n, B = self.n, self.B
+        _chk(gas, F32, 5 * B * n ** 3, "gas")
+        _chk(part, F32, 6 * B * n ** 3, "part")
         self._check(lib.sim_set_state(self.h, _ptr(gas), _ptr(part), step), "sim_set_state")
 
     def schedule(self, i: int):
@@ -240,6 +265,19 @@ class Simulation:
     def set_graphs(self, on: bool = True):
         self._check(lib.sim_set_graphs(self.h, int(on)), "sim_set_graphs")
 
+    def set_sweep_variants(self, fwd=None, adj=None):
+        f = (ctypes.c_int32 * 3)(*fwd) if fwd is not None else None
+        a = (ctypes.c_int32 * 3)(*adj) if adj is not None else None
+        self._check(lib.sim_set_sweep_variants(self.h, f, a), "sim_set_sweep_variants")
+
+    def autotune(self, reps: int = 3):
+        """Time the sweep variants on the current state and keep the fastest per axis;
+        returns (forward variants, adjoint variants)."""
+        f = (ctypes.c_int32 * 3)()
+        a = (ctypes.c_int32 * 3)()
+        self._check(lib.sim_autotune(self.h, reps, f, a), "sim_autotune")
+        return list(f), list(a)
+
     def kernel_timing(self, on: bool = True):
         self._check(lib.sim_kernel_timing(self.h, int(on)), "sim_kernel_timing")
 
@@ -250,6 +288,54 @@ class Simulation:
         self._check(lib.sim_kernel_times(self.h, ms, cnt, int(reset)), "sim_kernel_times")
         return {"sweep": (ms[KT_SWEEP], cnt[KT_SWEEP]),
                 "sweep_adjoint": (ms[KT_SWEEP_ADJOINT], cnt[KT_SWEEP_ADJOINT])}
+
+
+class Group:
+    """Member simulations (e.g. one batch per grid size) run as one CUDA graph with a
+    concurrent branch per member (sim_group_*). Create the members on the current stream."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s_.h.value for s_ in self.sims])
+        h = ctypes.c_void_p()
+        check(lib.sim_group_create(arr, len(self.sims),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                   ctypes.byref(h)), "sim_group_create")
+        self.h = h
+
+    def run(self):
+        check(lib.sim_group_run(self.h), "sim_group_run")
+
+    def run_adjoint(self, dL_dgas=None, out=None):
+        """dL_dgas: one tensor (or None) per member; returns per-member parameter
+        derivatives [B_k, NPARAMS] (or [NPARAMS] for B_k = 1)."""
+        K = len(self.sims)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            out = [torch.zeros(s_._shape(NPARAMS), dtype=F64, device=dev) for s_ in self.sims]
+        g = None
+        if dL_dgas is not None:
+            for s_, d in zip(self.sims, dL_dgas):
+                if d is not None:
+                    _chk(d, F32, 5 * s_.B * s_.n ** 3, "dL_dgas")
+            g = (ctypes.c_void_p * K)(*[(d.data_ptr() if d is not None else None) for d in dL_dgas])
+        o = (ctypes.c_void_p * K)(*[t.data_ptr() for t in out])
+        check(lib.sim_group_run_adjoint(self.h, g, o), "sim_group_run_adjoint")
+        return out
+
+    def reset(self):
+        check(lib.sim_group_reset(self.h), "sim_group_reset")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sim_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class SimRunFunction(torch.autograd.Function):

@@ -43,6 +43,26 @@ void count_launch();
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// ------------------------------------------------------------------ batched launches
+// Every kernel of the step takes B instances of one grid size stored one after another
+// (instance b of a field with F components of n^3 cells starts at b * F * n^3). A scalar
+// that differs between instances is an SArg: one value for all instances, or a device
+// array indexed by the instance. Partial sums of instance b go to base + b * stride.
+struct SArg {
+  float v;
+  const float* p;
+  __device__ __forceinline__ float at(int b) const { return p ? __ldg(p + b) : v; }
+};
+inline SArg sarg(float v) { return SArg{v, nullptr}; }
+inline SArg sarg(const float* p) { return SArg{0.0f, p}; }
+
+struct DPart {
+  double* p;
+  int stride;
+  __device__ __forceinline__ double* at(int b) const { return p ? p + (size_t)b * stride : nullptr; }
+};
+inline DPart dpart(double* p, int stride = 0) { return DPart{p, stride}; }
+
 // ------------------------------------------------------------------ Philox4x32-10
 // Salmon et al. (SC'11): 10 rounds of two 32x32->64 multiplies whose halves are mixed
 // with the other counter words and the key; Weyl key bumps between rounds.

@@ -57,6 +57,6 @@ extern "C" sim_status sim_deposit_cic_static(const float* s, const float* values
   DH_TRY(scratch_address(&acc));
   // the array keeps the previous call's contents: clear the part this call accumulates into
   DH_CUDA_TRY(cudaMemsetAsync(acc, 0, N3 * sizeof(unsigned long long), st));
-  DH_TRY(launch_deposit(s, values, n, (float)(n / box), acc, st));
-  return launch_fix_to_float(acc, 1.0f, grid, 0.0f, grid, n, st);
+  DH_TRY(launch_deposit(s, values, n, (float)(n / box), acc, 1, st));
+  return launch_fix_to_float(acc, sarg(1.0f), grid, (int)N3, 0.0f, grid, n, 1, st);
 }

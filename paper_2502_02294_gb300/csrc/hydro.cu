@@ -55,7 +55,7 @@ __device__ __forceinline__ float face_flux(const float* R, const float* L, int D
 
 template <int AXIS>
 __global__ void __launch_bounds__(SweepCfg<AXIS>::NT, 2)
-sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, float nu,
+sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
                  float gam, float eps) {
   constexpr int S = SweepCfg<AXIS>::S, W = SweepCfg<AXIS>::W, NT = SweepCfg<AXIS>::NT;
   using G = TileGeom<AXIS, S, W, 3>;
@@ -65,7 +65,11 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
   float* sf = sm;            // 10 NC: F^R, F^L of U, then of Uh
   float* sg = sm + 10 * NC;  // 5 NC: limited face fluxes (face c+1/2 at c)
   const long long N3 = (long long)n * n * n;
-  const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z;
+  const int b = blockIdx.z / n;  // instance; blockIdx.z = b n + third coordinate
+  const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z - b * n;
+  uin += (size_t)b * 5 * N3;
+  uout += (size_t)b * 5 * N3;
+  const float nu = nua.at(b);
 
   float ureg[CPT][5];
 #pragma unroll
@@ -155,14 +159,18 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
 // barriers; adjacent threads own adjacent lines (x for the y/z sweeps, y for x).
 template <int AXIS, int L>
 __global__ void __launch_bounds__(128)
-sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, float nu,
+sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
                    float gam, float eps) {
   constexpr int F = 1 + AXIS;
   const int w = blockIdx.x * blockDim.x + threadIdx.x;  // line coordinate
-  const int t = blockIdx.y;                             // third coordinate
+  const int b = blockIdx.y / n;                         // instance
+  const int t = blockIdx.y - b * n;                     // third coordinate
   const int s0 = blockIdx.z * L;
   if (w >= n) return;
   const long long N3 = (long long)n * n * n;
+  uin += (size_t)b * 5 * N3;
+  uout += (size_t)b * 5 * N3;
+  const float nu = nua.at(b);
   const float hnu = 0.5f * nu;
   float Ua[5], Ub[5], Uc[5];      // U_{j-3}, U_{j-2}, U_{j-1}
   float FRp[5], f1m[5];           // F^R_{j-1}, first-order face (j-3/2)
@@ -242,14 +250,20 @@ sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int 
 template <int AXIS, int L>
 __global__ void __launch_bounds__(128)
 sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
-                       float* __restrict__ luh_out, int n, float nu, float gam, float eps,
-                       double* __restrict__ dnu) {
+                       float* __restrict__ luh_out, int n, SArg nua, float gam, float eps,
+                       DPart dnub) {
   constexpr int F = 1 + AXIS;
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t3 = blockIdx.y;
+  const int b = blockIdx.y / n;  // instance
+  const int t3 = blockIdx.y - b * n;
   const int s0 = blockIdx.z * L;
   const bool live = w < n;
   const long long N3 = (long long)n * n * n;
+  uin += (size_t)b * 5 * N3;
+  lout += (size_t)b * 5 * N3;
+  luh_out += (size_t)b * 5 * N3;
+  const float nu = nua.at(b);
+  double* dnu = dnub.at(b);
   const float hnu = 0.5f * nu, inv_nu = 1.0f / nu;
   float Uc[5], FRp[5], f1m[5];          // U_{i-1}, F^R_{i-1}, face (i-3/2)
   float R0[5], R1[5], R2[5];            // Fh^R_{i-4}, Fh^R_{i-3}, Fh^R_{i-2}
@@ -390,12 +404,18 @@ template <int AXIS>
 __global__ void __launch_bounds__(256)
 sweep_adj_final_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                        const float* __restrict__ luh, float* __restrict__ lin, int n,
-                       float nu, float gam) {
+                       SArg nua, float gam) {
   constexpr int F = 1 + AXIS;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int b = blockIdx.z / n;  // instance
+  const int y = blockIdx.y, z = blockIdx.z - b * n;
   if (x >= n) return;
   const long long N3 = (long long)n * n * n;
+  uin += (size_t)b * 5 * N3;
+  lout += (size_t)b * 5 * N3;
+  luh += (size_t)b * 5 * N3;
+  lin += (size_t)b * 5 * N3;
+  const float nu = nua.at(b);
   const long long o = ((long long)z * n + y) * n + x;
   int cm, cp;  // neighbour offsets along the sweep axis (periodic)
   long long om, op;
@@ -441,8 +461,7 @@ sweep_adj_final_kernel(const float* __restrict__ uin, const float* __restrict__ 
 template <int AXIS>
 __global__ void __launch_bounds__(SweepCfg<AXIS>::NTA, 2)
 sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
-                 float* __restrict__ lin, int n, float nu, float gam, float eps,
-                 double* __restrict__ dnu) {
+                 float* __restrict__ lin, int n, SArg nua, float gam, float eps, DPart dnub) {
   constexpr int S = SweepCfg<AXIS>::SA, W = SweepCfg<AXIS>::WA, NT = SweepCfg<AXIS>::NTA;
   using G = TileGeom<AXIS, S, W, 5>;
   constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
@@ -452,7 +471,13 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
   float* sl = sm + 10 * NC;  // 5 NC: lam_out
   float* sh = sm + 15 * NC;  // 5 NC: lamUh
   const long long N3 = (long long)n * n * n;
-  const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z;
+  const int b = blockIdx.z / n;  // instance
+  const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z - b * n;
+  uin += (size_t)b * 5 * N3;
+  lout += (size_t)b * 5 * N3;
+  lin += (size_t)b * 5 * N3;
+  const float nu = nua.at(b);
+  double* dnu = dnub.at(b);
 
   float ureg[CPT][5];
 #pragma unroll
@@ -591,71 +616,79 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
   if (dnu) block_sum_atomic(dnu_acc, dnu);
 }
 
-// Kernel choice, measured on GB300 (sweep of 5 float32 fields): the shared-memory tile
-// (16 x 32 lines for y/z) is fastest up to n ~ 128 (51 us at 128^3 for every axis); the
-// marching form with segments of 32 wins for y/z on larger grids (335 us vs 386 us at
-// 256^3). The x sweep always uses the tile (marching along x is not coalesced).
-#ifndef DH_SWEEP_MARCH
-#define DH_SWEEP_MARCH 1
-#endif
-#ifndef DH_MARCH_L
-#define DH_MARCH_L 32
-#endif
-#ifndef DH_MARCH_MIN_N
-#define DH_MARCH_MIN_N 192
-#endif
+// Kernel variants (SIM_SWEEP_*): the shared-memory tile, or the marching form with line
+// segments of 32 or 16 cells (y and z sweeps only: marching along x is not coalesced).
+// The default, measured on GB300 for one instance: the tile is fastest up to n ~ 128
+// (51 us at 128^3 for every axis); marching with segments of 32 wins for y/z on larger
+// grids (335 us vs 386 us at 256^3). The adjoint defaults to the marching pair for y/z
+// (2.1x the tile at 256^3) and the tile for x. sim_autotune times the variants per handle.
+static int pick_fwd(int axis, int n, int variant) {
+  if (axis == 0) return SIM_SWEEP_TILE;
+  if (variant != SIM_SWEEP_DEFAULT) return variant;
+  return n >= 192 ? SIM_SWEEP_MARCH32 : SIM_SWEEP_TILE;
+}
+
+static int pick_adj(int axis, int variant) {
+  if (axis == 0) return SIM_SWEEP_TILE;
+  return variant != SIM_SWEEP_DEFAULT ? variant : SIM_SWEEP_MARCH32;
+}
+
+template <int AXIS, int L>
+static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, float gam,
+                                 float eps, int B, cudaStream_t st) {
+  dim3 grid(cdiv(n, 128), n * B, cdiv(n, L));
+  sweep_march_kernel<AXIS, L><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
 
 template <int AXIS>
-static sim_status launch_sweep_t(const float* uin, float* uout, int n, float nu, float gam,
-                                 float eps, cudaStream_t st) {
+static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, float gam,
+                                 float eps, int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  if (DH_SWEEP_MARCH == 2 || (DH_SWEEP_MARCH == 1 && AXIS != 0 && n >= DH_MARCH_MIN_N)) {
-    constexpr int L = DH_MARCH_L;
-    dim3 grid(cdiv(n, 128), n, cdiv(n, L));
-    sweep_march_kernel<AXIS, L><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps);
-    DH_LAUNCH_CHECK();
-    return SIM_OK;
+  if (AXIS != 0) {
+    if (variant == SIM_SWEEP_MARCH32) return launch_march_t<AXIS, 32>(uin, uout, n, nu, gam, eps, B, st);
+    if (variant == SIM_SWEEP_MARCH16) return launch_march_t<AXIS, 16>(uin, uout, n, nu, gam, eps, B, st);
   }
   constexpr int NC = (C::S + 6) * C::W;
   const size_t smem = 15 * NC * sizeof(float);
-  dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n);
+  dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n * B);
   sweep_fwd_kernel<AXIS><<<grid, C::NT, smem, st>>>(uin, uout, n, nu, gam, eps);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
-// Adjoint kernel choice: the marching pair (pass 1 + pass 2, segments of DH_ADJ_L) for
-// the y and z sweeps, the shared-memory tile for x (DH_ADJ_MARCH = 0: tile everywhere,
-// 2: marching everywhere).
-#ifndef DH_ADJ_MARCH
-#define DH_ADJ_MARCH 1
-#endif
-#ifndef DH_ADJ_L
-#define DH_ADJ_L 32
-#endif
+template <int AXIS, int L>
+static sim_status launch_adj_march_t(const float* uin, const float* lout, float* lin, int n,
+                                     SArg nu, float gam, float eps, DPart dnu, float* scratch,
+                                     int B, cudaStream_t st) {
+  if (!scratch) {
+    set_error("internal: marching sweep adjoint needs a 5 n^3 scratch buffer per instance");
+    return SIM_EINVAL;
+  }
+  dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
+  sweep_adj_march_kernel<AXIS, L><<<g1, 128, 0, st>>>(uin, lout, scratch, n, nu, gam, eps, dnu);
+  DH_LAUNCH_CHECK();
+  dim3 g2(cdiv(n, 256), n, n * B);
+  sweep_adj_final_kernel<AXIS><<<g2, 256, 0, st>>>(uin, lout, scratch, lin, n, nu, gam);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
 
 template <int AXIS>
 static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float* lin, int n,
-                                     float nu, float gam, float eps, double* dnu,
-                                     float* scratch, cudaStream_t st) {
+                                     SArg nu, float gam, float eps, DPart dnu, float* scratch,
+                                     int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  if (DH_ADJ_MARCH == 2 || (DH_ADJ_MARCH == 1 && AXIS != 0)) {
-    constexpr int L = DH_ADJ_L;
-    if (!scratch) {
-      set_error("internal: marching sweep adjoint needs a 5 n^3 scratch buffer");
-      return SIM_EINVAL;
-    }
-    dim3 g1(cdiv(n, 128), n, cdiv(n, L));
-    sweep_adj_march_kernel<AXIS, L><<<g1, 128, 0, st>>>(uin, lout, scratch, n, nu, gam, eps, dnu);
-    DH_LAUNCH_CHECK();
-    dim3 g2(cdiv(n, 256), n, n);
-    sweep_adj_final_kernel<AXIS><<<g2, 256, 0, st>>>(uin, lout, scratch, lin, n, nu, gam);
-    DH_LAUNCH_CHECK();
-    return SIM_OK;
+  if (AXIS != 0) {
+    if (variant == SIM_SWEEP_MARCH32)
+      return launch_adj_march_t<AXIS, 32>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
+    if (variant == SIM_SWEEP_MARCH16)
+      return launch_adj_march_t<AXIS, 16>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
   }
   constexpr int NC = (C::SA + 10) * C::WA;
   const size_t smem = 20 * NC * sizeof(float);
-  dim3 grid(cdiv(n, C::SA), cdiv(n, C::WA), n);
+  dim3 grid(cdiv(n, C::SA), cdiv(n, C::WA), n * B);
   sweep_adj_kernel<AXIS><<<grid, C::NTA, smem, st>>>(uin, lout, lin, n, nu, gam, eps, dnu);
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -688,30 +721,37 @@ sim_status prepare_sweep_kernels() {
   return SIM_OK;
 }
 
-sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double nu,
-                        double gam, double eps, cudaStream_t st) {
+sim_status launch_sweep(int axis, const float* uin, float* uout, int n, SArg nu, double gam,
+                        double eps, int B, int variant, cudaStream_t st) {
   DH_TRY(prepare_sweep_kernels());
-  switch (axis) {
-    case 0: return launch_sweep_t<0>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
-    case 1: return launch_sweep_t<1>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
-    case 2: return launch_sweep_t<2>(uin, uout, n, (float)nu, (float)gam, (float)eps, st);
+  if (axis < 0 || axis > 2) {
+    set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
+    return SIM_EINVAL;
   }
-  set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
-  return SIM_EINVAL;
+  const int v = pick_fwd(axis, n, variant);
+  const float fg = (float)gam, fe = (float)eps;
+  switch (axis) {
+    case 0: return launch_sweep_t<0>(uin, uout, n, nu, fg, fe, B, v, st);
+    case 1: return launch_sweep_t<1>(uin, uout, n, nu, fg, fe, B, v, st);
+    default: return launch_sweep_t<2>(uin, uout, n, nu, fg, fe, B, v, st);
+  }
 }
 
 sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
-                                int n, double nu, double gam, double eps, double* dnu,
-                                float* scratch, cudaStream_t st) {
+                                int n, SArg nu, double gam, double eps, DPart dnu,
+                                float* scratch, int B, int variant, cudaStream_t st) {
   DH_TRY(prepare_sweep_kernels());
-  const float fnu = (float)nu, fg = (float)gam, fe = (float)eps;
-  switch (axis) {
-    case 0: return launch_sweep_adj_t<0>(uin, lout, lin, n, fnu, fg, fe, dnu, scratch, st);
-    case 1: return launch_sweep_adj_t<1>(uin, lout, lin, n, fnu, fg, fe, dnu, scratch, st);
-    case 2: return launch_sweep_adj_t<2>(uin, lout, lin, n, fnu, fg, fe, dnu, scratch, st);
+  if (axis < 0 || axis > 2) {
+    set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
+    return SIM_EINVAL;
   }
-  set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
-  return SIM_EINVAL;
+  const int v = pick_adj(axis, variant);
+  const float fg = (float)gam, fe = (float)eps;
+  switch (axis) {
+    case 0: return launch_sweep_adj_t<0>(uin, lout, lin, n, nu, fg, fe, dnu, scratch, B, v, st);
+    case 1: return launch_sweep_adj_t<1>(uin, lout, lin, n, nu, fg, fe, dnu, scratch, B, v, st);
+    default: return launch_sweep_adj_t<2>(uin, lout, lin, n, nu, fg, fe, dnu, scratch, B, v, st);
+  }
 }
 
 }  // namespace dh
@@ -722,7 +762,8 @@ extern "C" sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int3
     dh::set_error("sim_sweep: null/aliased buffers or n < 1");
     return SIM_EINVAL;
   }
-  return dh::launch_sweep(axis, u_in, u_out, n, nu, gamma, limiter_eps, (cudaStream_t)stream);
+  return dh::launch_sweep(axis, u_in, u_out, n, dh::sarg((float)nu), gamma, limiter_eps, 1,
+                          SIM_SWEEP_DEFAULT, (cudaStream_t)stream);
 }
 
 extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out, float* lam_in,
@@ -735,8 +776,9 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
   cudaStream_t st = (cudaStream_t)stream;
   float* scratch = nullptr;
   DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 5ull * n * n * n * sizeof(float), st));
-  const sim_status r = dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, nu, gamma,
-                                                limiter_eps, dnu, scratch, st);
+  const sim_status r =
+      dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, dh::sarg((float)nu), gamma,
+                               limiter_eps, dh::dpart(dnu), scratch, 1, SIM_SWEEP_DEFAULT, st);
   cudaFreeAsync(scratch, st);
   return r;
 }

@@ -29,14 +29,15 @@ static sim_status make_plan(cufftHandle* h, int n, cufftType type, int batch) {
   return SIM_OK;
 }
 
-sim_status FFTPlans::create(int n_) {
+sim_status FFTPlans::create(int n_, int B_) {
   n = n_;
-  DH_TRY(make_plan(&r2c1, n, CUFFT_R2C, 1));
-  DH_TRY(make_plan(&r2c3, n, CUFFT_R2C, 3));
-  DH_TRY(make_plan(&r2c4, n, CUFFT_R2C, 4));
-  DH_TRY(make_plan(&c2r1, n, CUFFT_C2R, 1));
-  DH_TRY(make_plan(&c2r3, n, CUFFT_C2R, 3));
-  DH_TRY(make_plan(&c2r4, n, CUFFT_C2R, 4));
+  B = B_;
+  DH_TRY(make_plan(&r2c1, n, CUFFT_R2C, B));
+  DH_TRY(make_plan(&r2c3, n, CUFFT_R2C, 3 * B));
+  DH_TRY(make_plan(&r2c4, n, CUFFT_R2C, 4 * B));
+  DH_TRY(make_plan(&c2r1, n, CUFFT_C2R, B));
+  DH_TRY(make_plan(&c2r3, n, CUFFT_C2R, 3 * B));
+  DH_TRY(make_plan(&c2r4, n, CUFFT_C2R, 4 * B));
   return SIM_OK;
 }
 
@@ -66,7 +67,7 @@ FFTPlans* shared_plans(int n) {
   auto it = cache.find({dev, n});
   if (it != cache.end()) return it->second;
   FFTPlans* p = new FFTPlans();
-  if (p->create(n) != SIM_OK) {
+  if (p->create(n, 1) != SIM_OK) {
     p->destroy();
     delete p;
     return nullptr;
@@ -115,21 +116,25 @@ __device__ __forceinline__ void cic_axis(float s, int q, int n, float inv_dx, in
 }
 
 struct PIdx {
-  int qx, qy, qz, p;
+  int qx, qy, qz, p, b;
   bool ok;
 };
 
+// grid (cdiv(n, threads), n, B n): blockIdx.z carries the instance and the lattice z
 __device__ __forceinline__ PIdx particle_index(int n) {
   PIdx r;
   r.qx = blockIdx.x * blockDim.x + threadIdx.x;
   r.qy = blockIdx.y;
-  r.qz = blockIdx.z;
+  r.b = blockIdx.z / n;
+  r.qz = blockIdx.z - r.b * n;
   r.ok = r.qx < n;
   r.p = (r.qz * n + r.qy) * n + r.qx;
   return r;
 }
 
-static inline dim3 particle_grid(int n, int threads) { return dim3(cdiv(n, threads), n, n); }
+static inline dim3 particle_grid(int n, int threads, int B) {
+  return dim3(cdiv(n, threads), n, n * B);
+}
 constexpr int kPT = 128;  // threads per particle block
 
 __device__ __forceinline__ void cic_setup(const float* s, const PIdx& q, int N3, int n,
@@ -164,9 +169,11 @@ __global__ void deposit_kernel(const float* __restrict__ s, const float* __restr
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   if (!q.ok) return;
+  s += (size_t)q.b * 3 * N3;
+  acc += (size_t)q.b * N3;
   Cic c;
   cic_setup(s, q, N3, n, inv_dx, c);
-  const float v = vals ? vals[q.p] : 1.0f;
+  const float v = vals ? vals[(size_t)q.b * N3 + q.p] : 1.0f;
 #pragma unroll
   for (int oz = 0; oz < 2; ++oz)
 #pragma unroll
@@ -178,27 +185,32 @@ __global__ void deposit_kernel(const float* __restrict__ s, const float* __restr
       }
 }
 
-__global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, float scale,
-                                    const float* __restrict__ add, float offset,
+// grid (cdiv(N3, 256), B)
+__global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, SArg scale,
+                                    const float* __restrict__ add, int add_stride, float offset,
                                     float* __restrict__ out, int N3) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
   if (i >= N3) return;
-  const float cnt = from_fix(acc[i]);
-  acc[i] = 0ull;
-  out[i] = scale * cnt + (add ? add[i] : 0.0f) + offset;
+  const size_t o = (size_t)b * N3 + i;
+  const float cnt = from_fix(acc[o]);
+  acc[o] = 0ull;
+  out[o] = scale.at(b) * cnt + (add ? add[(size_t)b * add_stride + i] : 0.0f) + offset;
 }
 
 sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
-                          unsigned long long* acc, cudaStream_t st) {
-  deposit_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s, values, n, inv_dx, acc);
+                          unsigned long long* acc, int B, cudaStream_t st) {
+  deposit_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, values, n, inv_dx, acc);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
-sim_status launch_fix_to_float(unsigned long long* acc, float scale, const float* add,
-                               float offset, float* out, int n, cudaStream_t st) {
+sim_status launch_fix_to_float(unsigned long long* acc, SArg scale, const float* add,
+                               int add_stride, float offset, float* out, int n, int B,
+                               cudaStream_t st) {
   const int N3 = n * n * n;
-  fix_to_float_kernel<<<cdiv(N3, 256), 256, 0, st>>>(acc, scale, add, offset, out, N3);
+  fix_to_float_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(acc, scale, add, add_stride,
+                                                              offset, out, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -219,19 +231,22 @@ __device__ __forceinline__ void kindex(int i, int n, int nh, int& kx, int& ky, i
   if (kz > n / 2) kz -= n;
 }
 
-// gk[j] = i kgrad_j (pref / k^2) dk / n^3   (j = x, y, z)
+// gk[j] = i kgrad_j (pref / k^2) dk / n^3   (j = x, y, z); grid (cdiv(NC, 256), B)
 __global__ void green_kernel(const cufftComplex* __restrict__ dk, cufftComplex* __restrict__ gk,
-                             int n, float kf, float pref_norm) {
+                             int n, float kf, SArg pref_norm) {
   const int nh = n / 2 + 1;
   const int NC = n * n * nh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
   if (i >= NC) return;
+  dk += (size_t)b * NC;
+  gk += (size_t)b * 3 * NC;
   int kx, ky, kz;
   bool nx, ny, nz;
   kindex(i, n, nh, kx, ky, kz, nx, ny, nz);
   const float fx = kf * kx, fy = kf * ky, fz = kf * kz;
   const float k2 = fx * fx + fy * fy + fz * fz;
-  const float G = (k2 > 0.0f) ? pref_norm / k2 : 0.0f;
+  const float G = (k2 > 0.0f) ? pref_norm.at(b) / k2 : 0.0f;
   const cufftComplex d = dk[i];
   const float gxs = nx ? 0.0f : fx * G, gys = ny ? 0.0f : fy * G, gzs = nz ? 0.0f : fz * G;
   // i * c * (a + ib) = -c b + i c a
@@ -243,47 +258,59 @@ __global__ void green_kernel(const cufftComplex* __restrict__ dk, cufftComplex* 
 // Adjoint: Y = sum_j (-i kgrad_j)(pref / k^2) L_j / n^3 (the operator with the sign of the
 // gradient flipped; the Hermitian weights of the half spectrum cancel, see sim_gravity_adjoint)
 __global__ void green_adj_kernel(const cufftComplex* __restrict__ lk, cufftComplex* __restrict__ yk,
-                                 int n, float kf, float pref_norm) {
+                                 int n, float kf, SArg pref_norm) {
   const int nh = n / 2 + 1;
   const int NC = n * n * nh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
   if (i >= NC) return;
+  lk += (size_t)b * 3 * NC;
+  yk += (size_t)b * NC;
   int kx, ky, kz;
   bool nx, ny, nz;
   kindex(i, n, nh, kx, ky, kz, nx, ny, nz);
   const float fx = kf * kx, fy = kf * ky, fz = kf * kz;
   const float k2 = fx * fx + fy * fy + fz * fz;
-  const float G = (k2 > 0.0f) ? pref_norm / k2 : 0.0f;
+  const float G = (k2 > 0.0f) ? pref_norm.at(b) / k2 : 0.0f;
   const float cx = nx ? 0.0f : fx * G, cy = ny ? 0.0f : fy * G, cz = nz ? 0.0f : fz * G;
-  const cufftComplex a = lk[i], b = lk[NC + i], c = lk[2 * NC + i];
+  const cufftComplex a = lk[i], bb = lk[NC + i], c = lk[2 * NC + i];
   // -i c (re + i im) = c im - i c re
-  const float re = cx * a.y + cy * b.y + cz * c.y;
-  const float im = -(cx * a.x + cy * b.x + cz * c.x);
+  const float re = cx * a.y + cy * bb.y + cz * c.y;
+  const float im = -(cx * a.x + cy * bb.x + cz * c.x);
   yk[i] = make_cuFloatComplex(re, im);
 }
 
+float gravity_pref_norm(double pref, int n) { return (float)(pref / ((double)n * n * n)); }
+
 sim_status launch_gravity(const float* delta, float* g, cufftComplex* dk, cufftComplex* gk,
-                          int n, double box, double pref, FFTPlans& plans, cudaStream_t st) {
+                          int n, double box, SArg pref_norm, int B, FFTPlans& plans,
+                          cudaStream_t st) {
+  if (plans.B != B) {
+    set_error("internal: FFT plans for batch %d used with batch %d", plans.B, B);
+    return SIM_EINVAL;
+  }
   const int NC = n * n * (n / 2 + 1);
   DH_TRY(plans.set_stream(st));
   DH_TRY(fft_exec_r2c(plans.r2c1, delta, dk));
   const float kf = (float)(2.0 * M_PI / box);
-  const float pn = (float)(pref / ((double)n * n * n));
-  green_kernel<<<cdiv(NC, 256), 256, 0, st>>>(dk, gk, n, kf, pn);
+  green_kernel<<<dim3(cdiv(NC, 256), B), 256, 0, st>>>(dk, gk, n, kf, pref_norm);
   DH_LAUNCH_CHECK();
   DH_TRY(fft_exec_c2r(plans.c2r3, gk, g));
   return SIM_OK;
 }
 
 sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftComplex* gk,
-                                  cufftComplex* dk, int n, double box, double pref,
+                                  cufftComplex* dk, int n, double box, SArg pref_norm, int B,
                                   FFTPlans& plans, cudaStream_t st) {
+  if (plans.B != B) {
+    set_error("internal: FFT plans for batch %d used with batch %d", plans.B, B);
+    return SIM_EINVAL;
+  }
   const int NC = n * n * (n / 2 + 1);
   DH_TRY(plans.set_stream(st));
   DH_TRY(fft_exec_r2c(plans.r2c3, lam_g, gk));
   const float kf = (float)(2.0 * M_PI / box);
-  const float pn = (float)(pref / ((double)n * n * n));
-  green_adj_kernel<<<cdiv(NC, 256), 256, 0, st>>>(gk, dk, n, kf, pn);
+  green_adj_kernel<<<dim3(cdiv(NC, 256), B), 256, 0, st>>>(gk, dk, n, kf, pref_norm);
   DH_LAUNCH_CHECK();
   DH_TRY(fft_exec_c2r(plans.c2r1, dk, lam_delta));
   return SIM_OK;
@@ -295,6 +322,9 @@ __global__ void interp_kernel(const float* __restrict__ grid, int nf, int n, flo
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   if (!q.ok) return;
+  grid += (size_t)q.b * nf * N3;
+  s += (size_t)q.b * 3 * N3;
+  out += (size_t)q.b * nf * N3;
   Cic c;
   cic_setup(s, q, N3, n, inv_dx, c);
   for (int f = 0; f < nf; ++f) {
@@ -312,8 +342,8 @@ __global__ void interp_kernel(const float* __restrict__ grid, int nf, int n, flo
 }
 
 sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
-                         float* out, cudaStream_t st) {
-  interp_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(grid, nf, n, inv_dx, s, out);
+                         float* out, int B, cudaStream_t st) {
+  interp_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(grid, nf, n, inv_dx, s, out);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -336,13 +366,18 @@ __device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& 
 }
 
 __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
-                                  const float* __restrict__ g, float K, float dtau,
+                                  const float* __restrict__ g, SArg Ka, SArg dtaua,
                                   const float* __restrict__ zhat, float* __restrict__ aux,
                                   int n, float inv_dx) {
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   if (!q.ok) return;
   const int i = q.p;
+  const size_t o3 = (size_t)q.b * 3 * N3;
+  s += o3;
+  p += o3;
+  g += o3;
+  const float K = Ka.at(q.b), dtau = dtaua.at(q.b);
   Cic c;
   cic_setup(s, q, N3, n, inv_dx, c);
   float gi[3];
@@ -354,6 +389,7 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
     if (dtau != 0.0f) s[j * N3 + i] += dtau * pj;
   }
   if (zhat) {
+    zhat += (size_t)q.b * N3;
     cic_setup(s, q, N3, n, inv_dx, c);
     float acc = 0.0f;
 #pragma unroll
@@ -363,23 +399,28 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox)
           acc += c.wz[oz] * c.wy[oy] * c.wx[ox] * __ldg(zhat + node(c, oz, oy, ox, n));
-    aux[i] += acc;
+    aux[(size_t)q.b * N3 + i] += acc;
   }
 }
 
-sim_status launch_kick_drift(float* s, float* p, const float* g, float K, float dtau,
-                             const float* zhat, float* aux, int n, float inv_dx,
+sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
+                             const float* zhat, float* aux, int n, float inv_dx, int B,
                              cudaStream_t st) {
-  kick_drift_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s, p, g, K, dtau, zhat, aux, n,
-                                                            inv_dx);
+  kick_drift_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, p, g, K, dtau, zhat, aux, n,
+                                                               inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
-__global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__ g, float K,
+// grid (cdiv(N3, 256), B)
+__global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__ g, SArg Ka,
                                 int N3) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
   if (i >= N3) return;
+  u += (size_t)b * 5 * N3;
+  g += (size_t)b * 3 * N3;
+  const float K = Ka.at(b);
   const float rho = u[i];
   float mg = 0.0f, g2 = 0.0f;
 #pragma unroll
@@ -393,18 +434,24 @@ __global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__
   u[4 * N3 + i] += K * mg + 0.5f * K * K * rho * g2;
 }
 
-sim_status launch_gas_kick(float* gas, const float* g, float K, int n, cudaStream_t st) {
+sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cudaStream_t st) {
   const int N3 = n * n * n;
-  gas_kick_kernel<<<cdiv(N3, 256), 256, 0, st>>>(gas, g, K, N3);
+  gas_kick_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, g, K, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 // ------------------------------------------------------------------ adjoints
 __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __restrict__ g,
-                                    float K, float* __restrict__ lam, float* __restrict__ lam_g,
-                                    double* __restrict__ dK, int N3) {
+                                    SArg Ka, float* __restrict__ lam, float* __restrict__ lam_g,
+                                    DPart dK, int N3) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  u += (size_t)b * 5 * N3;
+  lam += (size_t)b * 5 * N3;
+  g += (size_t)b * 3 * N3;
+  lam_g += (size_t)b * 3 * N3;
+  const float K = Ka.at(b);
   float dkf = 0.0f;
   if (i < N3) {
     const float rho = u[i];
@@ -431,24 +478,32 @@ __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __
     lrho += 0.5f * K * K * g2 * le;
     lam[i] = lrho;
   }
-  if (dK) block_sum_atomic(dkf, dK);
+  if (dK.p) block_sum_atomic(dkf, dK.at(b));
 }
 
-sim_status launch_gas_kick_adjoint(const float* gas, const float* g, float K, float* lam,
-                                   float* lam_g, double* dK, int n, cudaStream_t st) {
+sim_status launch_gas_kick_adjoint(const float* gas, const float* g, SArg K, float* lam,
+                                   float* lam_g, DPart dK, int n, int B, cudaStream_t st) {
   const int N3 = n * n * n;
-  gas_kick_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(gas, g, K, lam, lam_g, dK, N3);
+  gas_kick_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, g, K, lam, lam_g, dK, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0,
-                                      const float* __restrict__ g, float K, float dtau,
+                                      const float* __restrict__ g, SArg Ka, SArg dtaua,
                                       float* __restrict__ lam_s, float* __restrict__ lam_p,
-                                      float* __restrict__ lam_g, double* __restrict__ dK,
-                                      double* __restrict__ ddtau, int n, float inv_dx) {
+                                      float* __restrict__ lam_g, DPart dK, DPart ddtau, int n,
+                                      float inv_dx) {
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
+  const size_t o3 = (size_t)q.b * 3 * N3;
+  s0 += o3;
+  if (p0) p0 += o3;
+  g += o3;
+  lam_s += o3;
+  lam_p += o3;
+  lam_g += o3;
+  const float K = Ka.at(q.b), dtau = dtaua.at(q.b);
   float dk = 0.0f, dd = 0.0f;
   if (q.ok) {
     const int i = q.p;
@@ -494,25 +549,31 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
       lam_p[j * N3 + i] = lp[j];
     }
   }
-  if (dK) block_sum_atomic(dk, dK);
-  if (ddtau) block_sum_atomic(dd, ddtau);
+  // a block never spans two instances (blockIdx.z carries the instance)
+  if (dK.p) block_sum_atomic(dk, dK.at(q.b));
+  if (ddtau.p) block_sum_atomic(dd, ddtau.at(q.b));
 }
 
-sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, float K,
-                                     float dtau, float* lam_s, float* lam_p, float* lam_g,
-                                     double* dK, double* ddtau, int n, float inv_dx,
+sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, SArg K,
+                                     SArg dtau, float* lam_s, float* lam_p, float* lam_g,
+                                     DPart dK, DPart ddtau, int n, float inv_dx, int B,
                                      cudaStream_t st) {
-  kick_drift_adj_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s0, p0, g, K, dtau, lam_s, lam_p,
-                                                               lam_g, dK, ddtau, n, inv_dx);
+  kick_drift_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s0, p0, g, K, dtau, lam_s,
+                                                                  lam_p, lam_g, dK, ddtau, n,
+                                                                  inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __restrict__ ld,
-                                   float cm, float* __restrict__ lam_s, double* __restrict__ dcm,
-                                   int n, float inv_dx) {
+                                   SArg cma, float* __restrict__ lam_s, DPart dcm, int n,
+                                   float inv_dx) {
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
+  s += (size_t)q.b * 3 * N3;
+  lam_s += (size_t)q.b * 3 * N3;
+  ld += (size_t)q.b * N3;
+  const float cm = cma.at(q.b);
   float itp = 0.0f;
   if (q.ok) {
     const int i = q.p;
@@ -534,32 +595,37 @@ __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __r
 #pragma unroll
     for (int j = 0; j < 3; ++j) lam_s[j * N3 + i] += cm * gs[j];
   }
-  if (dcm) block_sum_atomic(itp, dcm);
+  if (dcm.p) block_sum_atomic(itp, dcm.at(q.b));
 }
 
-sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, float cm,
-                                  float* lam_s, double* dcm, int n, float inv_dx,
+sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg cm,
+                                  float* lam_s, DPart dcm, int n, float inv_dx, int B,
                                   cudaStream_t st) {
-  deposit_adj_kernel<<<particle_grid(n, kPT), kPT, 0, st>>>(s, lam_delta, cm, lam_s, dcm, n,
-                                                            inv_dx);
+  deposit_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, lam_delta, cm, lam_s, dcm, n,
+                                                               inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
-__global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b,
-                           long long count, double* __restrict__ out) {
+// grid (blocks, B): instance b sums a[b count + i] b[b count + i]
+__global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ bv,
+                           long long count, DPart out) {
+  const int b = blockIdx.y;
+  a += (size_t)b * count;
+  bv += (size_t)b * count;
   float acc = 0.0f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
-    acc += a[i] * b[i];
-  block_sum_atomic(acc, out);
+    acc += a[i] * bv[i];
+  block_sum_atomic(acc, out.at(b));
 }
 
-sim_status launch_dot(const float* a, const float* b, long long count, double* out,
+sim_status launch_dot(const float* a, const float* b, long long count, DPart out, int B,
                       cudaStream_t st) {
   int blocks = cdiv(count, 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  dot_kernel<<<blocks, 256, 0, st>>>(a, b, count, out);
+  const int cap = cdiv(152 * 16, B);
+  if (blocks > cap) blocks = cap;
+  dot_kernel<<<dim3(blocks, B), 256, 0, st>>>(a, b, count, out);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -576,9 +642,29 @@ sim_status launch_axpy(float alpha, const float* x, float* y, long long count, c
   return SIM_OK;
 }
 
-__global__ void density_loss_kernel(const float* __restrict__ rho, const float* __restrict__ t,
+// y[b][ystride] += x[b][count] over B instances (first `count` floats of each y block)
+__global__ void axpy_strided_kernel(const float* __restrict__ x, float* __restrict__ y,
+                                    long long count, long long ystride) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i < count) y[(size_t)b * ystride + i] += x[(size_t)b * count + i];
+}
+
+sim_status launch_add_strided(const float* x, float* y, long long count, long long ystride,
+                              int B, cudaStream_t st) {
+  axpy_strided_kernel<<<dim3(cdiv(count, 256), B), 256, 0, st>>>(x, y, count, ystride);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// instance b: grad[b][0][i] = 2 c (rho_i - t_i) for rho = gas[b][0]; loss[b] += c sum (rho - t)^2
+__global__ void density_loss_kernel(const float* __restrict__ gas, const float* __restrict__ t,
                                     float c, float* __restrict__ grad, double* __restrict__ loss,
                                     long long N3) {
+  const int b = blockIdx.y;
+  const float* rho = gas + (size_t)b * 5 * N3;
+  t += (size_t)b * N3;
+  grad += (size_t)b * 5 * N3;
   float acc = 0.0f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N3;
        i += (long long)gridDim.x * blockDim.x) {
@@ -586,14 +672,15 @@ __global__ void density_loss_kernel(const float* __restrict__ rho, const float* 
     grad[i] = 2.0f * c * d;
     acc += c * d * d;
   }
-  block_sum_atomic(acc, loss);
+  block_sum_atomic(acc, loss + b);
 }
 
-sim_status launch_density_loss(const float* rho, const float* target, float c, float* grad,
-                               double* loss, long long N3, cudaStream_t st) {
+sim_status launch_density_loss(const float* gas, const float* target, float c, float* grad,
+                               double* loss, long long N3, int B, cudaStream_t st) {
   int blocks = cdiv(N3, 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  density_loss_kernel<<<blocks, 256, 0, st>>>(rho, target, c, grad, loss, N3);
+  const int cap = cdiv(152 * 16, B);
+  if (blocks > cap) blocks = cap;
+  density_loss_kernel<<<dim3(blocks, B), 256, 0, st>>>(gas, target, c, grad, loss, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -618,8 +705,8 @@ extern "C" sim_status sim_deposit_cic(const float* s, const float* values, int32
     set_error("cudaMemsetAsync failed");
     r = SIM_ECUDA;
   }
-  if (r == SIM_OK) r = launch_deposit(s, values, n, (float)(n / box), acc, st);
-  if (r == SIM_OK) r = launch_fix_to_float(acc, 1.0f, grid, 0.0f, grid, n, st);
+  if (r == SIM_OK) r = launch_deposit(s, values, n, (float)(n / box), acc, 1, st);
+  if (r == SIM_OK) r = launch_fix_to_float(acc, sarg(1.0f), grid, (int)N3, 0.0f, grid, n, 1, st);
   cudaFreeAsync(acc, st);
   return r;
 }
@@ -630,7 +717,7 @@ extern "C" sim_status sim_interp_cic(const float* grid, int32_t nf, int32_t n, d
     set_error("sim_interp_cic: invalid arguments");
     return SIM_EINVAL;
   }
-  return launch_interp(grid, nf, n, (float)(n / box), s, out, (cudaStream_t)stream);
+  return launch_interp(grid, nf, n, (float)(n / box), s, out, 1, (cudaStream_t)stream);
 }
 
 extern "C" sim_status sim_gravity(const float* delta, int32_t n, double box, double pref,
@@ -645,7 +732,8 @@ extern "C" sim_status sim_gravity(const float* delta, int32_t n, double box, dou
   const long long NC = (long long)n * n * (n / 2 + 1);
   cufftComplex* buf = nullptr;
   DH_CUDA_TRY(cudaMallocAsync((void**)&buf, 4 * NC * sizeof(cufftComplex), st));
-  sim_status r = launch_gravity(delta, g, buf, buf + NC, n, box, pref, *plans, st);
+  sim_status r = launch_gravity(delta, g, buf, buf + NC, n, box,
+                                sarg(gravity_pref_norm(pref, n)), 1, *plans, st);
   cudaFreeAsync(buf, st);
   return r;
 }
@@ -662,8 +750,8 @@ extern "C" sim_status sim_gravity_adjoint(const float* lam_g, int32_t n, double 
   const long long NC = (long long)n * n * (n / 2 + 1);
   cufftComplex* buf = nullptr;
   DH_CUDA_TRY(cudaMallocAsync((void**)&buf, 4 * NC * sizeof(cufftComplex), st));
-  sim_status r = launch_gravity_adjoint(lam_g, lam_delta, buf, buf + 3 * NC, n, box, pref,
-                                        *plans, st);
+  sim_status r = launch_gravity_adjoint(lam_g, lam_delta, buf, buf + 3 * NC, n, box,
+                                        sarg(gravity_pref_norm(pref, n)), 1, *plans, st);
   cudaFreeAsync(buf, st);
   return r;
 }

@@ -11,70 +11,83 @@ namespace dh {
 constexpr float kFix = 2147483648.0f;
 constexpr float kInvFix = 4.656612873077393e-10f;
 
-// cuFFT plans for one grid size: r2c batch 1/3/4, c2r batch 1/3/4 (n^3 real <-> n^2(n/2+1)).
+// cuFFT plans for one grid size and a batch of B instances: r2c over 1/3/4 fields per
+// instance (batch B, 3B, 4B), c2r likewise (n^3 real <-> n^2(n/2+1) complex each).
 struct FFTPlans {
-  int n = 0;
+  int n = 0, B = 0;
   cufftHandle r2c1 = 0, r2c3 = 0, r2c4 = 0, c2r1 = 0, c2r3 = 0, c2r4 = 0;
-  sim_status create(int n);
+  sim_status create(int n, int B);
   void destroy();
   sim_status set_stream(cudaStream_t st);
 };
 
-// Plans shared by the standalone entry points, keyed by n (created on first use).
+// Plans (batch 1) shared by the standalone entry points, keyed by n (created on first use).
 FFTPlans* shared_plans(int n);
 
 // ------------------------------------------------------------------ launchers
+// Every launcher below runs B instances of one grid size at once; array arguments hold the
+// instances one after another (see SArg / DPart in common.cuh).
+//
 // grid (int64 fixed point, n^3) += sum_p value_p W(x_p - node); values may be NULL (= 1)
 sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
-                          unsigned long long* acc, cudaStream_t st);
-// out = scale * fixed_to_float(acc) + add (add may be NULL) + offset; acc is zeroed
-sim_status launch_fix_to_float(unsigned long long* acc, float scale, const float* add,
-                               float offset, float* out, int n, cudaStream_t st);
+                          unsigned long long* acc, int B, cudaStream_t st);
+// out = scale * fixed_to_float(acc) + add (add may be NULL; instance stride add_stride)
+// + offset; acc is zeroed
+sim_status launch_fix_to_float(unsigned long long* acc, SArg scale, const float* add,
+                               int add_stride, float offset, float* out, int n, int B,
+                               cudaStream_t st);
+// pref / n^3 in float, the normalisation the Green's function kernels take
+float gravity_pref_norm(double pref, int n);
 // g (3 n^3) from delta (n^3): r2c, Green's function * i k * pref / n^3, c2r x3
 sim_status launch_gravity(const float* delta, float* g, cufftComplex* dk, cufftComplex* gk,
-                          int n, double box, double pref, FFTPlans& plans, cudaStream_t st);
+                          int n, double box, SArg pref_norm, int B, FFTPlans& plans,
+                          cudaStream_t st);
 // lam_delta (n^3) = (d g / d delta)^T lam_g (3 n^3)
 sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftComplex* gk,
-                                  cufftComplex* dk, int n, double box, double pref,
+                                  cufftComplex* dk, int n, double box, SArg pref_norm, int B,
                                   FFTPlans& plans, cudaStream_t st);
 // out[f][p] = CIC readout of grid f at particle p, nf fields
 sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
-                         float* out, cudaStream_t st);
+                         float* out, int B, cudaStream_t st);
 // p += K interp(g, s); then, if dtau != 0, s += dtau p. If zhat != NULL also
 // aux += interp(zhat, s) (after the drift).
-sim_status launch_kick_drift(float* s, float* p, const float* g, float K, float dtau,
-                             const float* zhat, float* aux, int n, float inv_dx,
+sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
+                             const float* zhat, float* aux, int n, float inv_dx, int B,
                              cudaStream_t st);
 // m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2 (gas 5 n^3, g 3 n^3)
-sim_status launch_gas_kick(float* gas, const float* g, float K, int n, cudaStream_t st);
+sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cudaStream_t st);
 
 // ---- adjoints
 // Gas kick: lam (5 n^3, in/out) through the kick at the pre-kick gas state `gas`;
 // lam_g (3 n^3) += partial (plain add, cell-owned); dK += lam . d/dK.
-sim_status launch_gas_kick_adjoint(const float* gas, const float* g, float K, float* lam,
-                                   float* lam_g, double* dK, int n, cudaStream_t st);
+sim_status launch_gas_kick_adjoint(const float* gas, const float* g, SArg K, float* lam,
+                                   float* lam_g, DPart dK, int n, int B, cudaStream_t st);
 // Particle kick (+ preceding drift if dtau != 0), reverse order:
 //   forward: p1 = p0 + K interp(g, s0); s1 = s0 + dtau p1
 //   given lam_s (= lam_s1), lam_p (= lam_p1 from later use), both in/out:
 //   lam_p1 += dtau lam_s1; d_dtau += lam_s1 . p1; lam_p0 = lam_p1;
 //   lam_s0 = lam_s1 + K grad(interp g)(s0) . lam_p1; lam_g += interp^T(K lam_p1) (atomic);
 //   dK += lam_p1 . interp(g)(s0).
-sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, float K,
-                                     float dtau, float* lam_s, float* lam_p, float* lam_g,
-                                     double* dK, double* ddtau, int n, float inv_dx,
+sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, SArg K,
+                                     SArg dtau, float* lam_s, float* lam_p, float* lam_g,
+                                     DPart dK, DPart ddtau, int n, float inv_dx, int B,
                                      cudaStream_t st);
 // Deposit adjoint for delta = cm * count + rho_gas - 1:
 //   lam_s += cm grad(interp lam_delta)(s) / dx ; d_cm += sum_p interp(lam_delta)(s_p)
-sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, float cm,
-                                  float* lam_s, double* dcm, int n, float inv_dx,
+sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg cm,
+                                  float* lam_s, DPart dcm, int n, float inv_dx, int B,
                                   cudaStream_t st);
-// sum_i a_i b_i over `count` floats into *out (device double, accumulated)
-sim_status launch_dot(const float* a, const float* b, long long count, double* out,
+// per instance: sum_i a_i b_i over `count` floats into out.at(b) (device double, accumulated)
+sim_status launch_dot(const float* a, const float* b, long long count, DPart out, int B,
                       cudaStream_t st);
 // y += alpha x over count floats
 sim_status launch_axpy(float alpha, const float* x, float* y, long long count, cudaStream_t st);
-// grad[i] = 2 c (rho_i - t_i) for the first N3 floats; *loss += c sum (rho - t)^2
-sim_status launch_density_loss(const float* rho, const float* target, float c, float* grad,
-                               double* loss, long long N3, cudaStream_t st);
+// per instance b: y[b * ystride + i] += x[b * count + i], i < count
+sim_status launch_add_strided(const float* x, float* y, long long count, long long ystride,
+                              int B, cudaStream_t st);
+// per instance: grad[0][i] = 2 c (rho_i - t_i) with rho the first field of the gas state
+// (instance stride 5 n^3, as grad); loss[b] += c sum (rho - t)^2
+sim_status launch_density_loss(const float* gas, const float* target, float c, float* grad,
+                               double* loss, long long N3, int B, cudaStream_t st);
 
 }  // namespace dh

@@ -48,11 +48,11 @@ const char* get_error() { return g_err; }
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-sim_status launch_sweep(int axis, const float* uin, float* uout, int n, double nu, double gam,
-                        double eps, cudaStream_t st);
+sim_status launch_sweep(int axis, const float* uin, float* uout, int n, SArg nu, double gam,
+                        double eps, int B, int variant, cudaStream_t st);
 sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
-                                int n, double nu, double gam, double eps, double* dnu,
-                                float* scratch, cudaStream_t st);
+                                int n, SArg nu, double gam, double eps, DPart dnu,
+                                float* scratch, int B, int variant, cudaStream_t st);
 sim_status prepare_sweep_kernels();
 
 static const char* kOrders[6] = {"xyz", "zyx", "zxy", "yxz", "yzx", "xzy"};
@@ -60,8 +60,18 @@ static const char* kOrders[6] = {"xyz", "zyx", "zxy", "yxz", "yzx", "xzy"};
 // per-step partial sums of the reverse pass (doubles on the device), and the chain-rule
 // coefficient of each with respect to Omega_m
 enum { SL_DK1 = 0, SL_DK2, SL_DNU, SL_DDTAU, SL_DPREF, SL_DCM, SL_DFB, SL_N = 8 };
-// extra global partials after the SIM_NPARAMS subgrid ones
+// extra global partials after the SIM_NPARAMS subgrid ones (per instance: NG doubles)
 enum { GX_DRP = 0, GX_DFB_IC = 1, GX_LAMC = 2, GX_N = 8 };
+constexpr int NG = SIM_NPARAMS + GX_N;
+// per-step float constants of every instance (device table [n_steps][SC_N][B])
+enum { SC_K1 = 0, SC_K2, SC_DTAU, SC_NU, SC_PN1, SC_N };
+// per-instance chain-rule constants of the parameter derivatives (device [B][PCH_N])
+enum { PCH_CCM0 = 0, PCH_DLNC, PCH_DRP, PCH_DFB, PCH_INVS8, PCH_N };
+
+// Host constants of one instance (Sec. 2.1 ICs, Sec. 2.2 mass split).
+struct InstConst {
+  double fb, cm, dfb_dom, C, dlnC_dom, rp, drp_dom, a2e0;
+};
 
 // One recorded step: inputs of every stage (pointers into the tape allocation).
 struct TapeSlot {
@@ -100,21 +110,35 @@ struct GraphEntry {
 using namespace dh;
 
 struct sim_s {
-  sim_params prm;
+  sim_params prm;                // instance 0; the fields shared by all instances
+  std::vector<sim_params> prms;  // per instance
+  int B = 1;
   int n = 0;
   long long N3 = 0, NC = 0;
   cudaStream_t st = 0;
-  double dx = 0, inv_dx = 0, fb = 0, cm = 0, dfb_dom = 0;
-  std::vector<StepFactors> sched;
-  // ICs constants
-  double C = 0, dlnC_dom = 0, rp = 0, drp_dom = 0, a2e0 = 0;
-  FFTPlans plans;
-  // state
+  double dx = 0, inv_dx = 0;
+  std::vector<StepFactors> sched;               // instance 0 (the a_i are shared)
+  std::vector<std::vector<StepFactors>> scheds;  // per instance
+  std::vector<InstConst> inst;                   // per instance
+  FFTPlans plans;   // batch B: the step's transforms
+  FFTPlans plans1;  // batch 1: initial conditions (created when B > 1)
+  // device tables of the per-instance constants (uploaded once by sim_init)
+  float* d_sc = nullptr;            // [n_steps][SC_N][B]
+  std::vector<float> h_sc, h_pn;    // host copies (a single instance passes values)
+  std::vector<SubgridConst> h_sub;
+  float* d_pn = nullptr;            // [n_steps + 1][B] Poisson factor / n^3 at a_i
+  float* d_cm = nullptr;            // [B] DM mass per particle (1 - f_b)
+  SubgridConst* d_sub = nullptr;    // [n_steps][B]
+  double* d_pch = nullptr;          // [B][PCH_N] chain-rule constants of the parameters
+  double* d_cpref = nullptr;        // [n_steps + 1][B] chain coefficient of a flush slot
+  int fwd_var[3] = {SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT};
+  int adj_var[3] = {SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT};
+  // state (B instances one after another in every buffer)
   float *gas = nullptr, *gas2 = nullptr, *s = nullptr, *p = nullptr, *g = nullptr;
   float *star = nullptr, *aux = nullptr, *zhat = nullptr, *delta = nullptr;
   uint32_t* events = nullptr;
   unsigned long long* acc = nullptr;
-  cufftComplex* ck = nullptr;  // 5 NC complex scratch
+  cufftComplex* ck = nullptr;  // max(4 B, 5) NC complex scratch
   float *noise = nullptr, *f4 = nullptr;
   float *init_gas = nullptr, *init_part = nullptr;
   float *prev_gas = nullptr, *prev_part = nullptr;
@@ -122,7 +146,7 @@ struct sim_s {
   bool ics_valid = false;
   int init_step = 0;
   int step = 0;
-  // checkpoints: a pool of buffers (11 n^3 floats each) allocated on first use
+  // checkpoints: a pool of buffers (11 n^3 floats per instance) allocated on first use
   std::vector<float*> ckpt_pool;
   std::vector<int> ckpt_step;
   int ckpt_count = 0;
@@ -132,11 +156,11 @@ struct sim_s {
   float *w_gas = nullptr, *w_gas2 = nullptr, *w_s = nullptr, *w_p = nullptr, *w_g = nullptr;
   float *lam_gas = nullptr, *lam_tmp = nullptr, *lam_s = nullptr, *lam_p = nullptr;
   float *lamG0 = nullptr, *lamG1 = nullptr, *lam_delta = nullptr, *lam4 = nullptr;
-  float* lam_scr = nullptr;  // 5 n^3 scratch of the marching sweep adjoint
-  double* dslots = nullptr;  // (n_steps + 2) x SL_N
-  double* dcoef = nullptr;   // (n_steps) x SL_N chain-rule coefficients
-  double* dglob = nullptr;   // SIM_NPARAMS + GX_N
-  unsigned int* speed_bits = nullptr;
+  float* lam_scr = nullptr;  // 5 n^3 per instance, scratch of the marching sweep adjoint
+  double* dslots = nullptr;  // [n_steps + 2][B][SL_N]
+  double* dcoef = nullptr;   // [n_steps][B][SL_N] chain-rule coefficients
+  double* dglob = nullptr;   // [B][NG]
+  unsigned int* speed_bits = nullptr;  // [B]
   // optional per-class kernel timing: event pairs around each timed launch (eager runs only)
   bool kt_on = false;
   std::vector<cudaEvent_t> kt_ev;  // 2 per recorded launch
@@ -353,26 +377,62 @@ static double a_of_step(const sim_t* h, int i) {
   return i == 0 ? h->prm.a_start : h->sched[i - 1].a1;
 }
 
+// per-instance scalars of step i, read by the kernels from the device tables
+// (one instance: the value itself, so that the kernels need no table load)
+static SArg sc(const sim_t* h, int i, int field) {
+  const size_t o = ((size_t)i * SC_N + field) * h->B;
+  return h->B == 1 ? sarg(h->h_sc[o]) : sarg(h->d_sc + o);
+}
+static SArg pn_at(const sim_t* h, int i) {
+  const size_t o = (size_t)i * h->B;
+  return h->B == 1 ? sarg(h->h_pn[o]) : sarg(h->d_pn + o);
+}
+static SubArg sub_at(const sim_t* h, int i) {
+  const size_t o = (size_t)i * h->B;
+  return h->B == 1 ? subarg(h->h_sub[o]) : subarg(h->d_sub + o);
+}
+static DPart slot_part(double* slot, int field) { return dpart(slot + field, SL_N); }
+static FFTPlans& ic_plans(sim_t* h) { return h->B == 1 ? h->plans : h->plans1; }
+
+// Particle arrays: the API holds B x [s (3 n^3), p (3 n^3)]; the handle keeps s and p apart.
+static sim_status part_join(float* dst6, const float* s, const float* p, const sim_t* h,
+                            cudaStream_t st) {
+  const size_t w = 3 * h->N3 * sizeof(float);
+  DH_CUDA_TRY(cudaMemcpy2DAsync(dst6, 2 * w, s, w, w, h->B, cudaMemcpyDeviceToDevice, st));
+  DH_CUDA_TRY(cudaMemcpy2DAsync((char*)dst6 + w, 2 * w, p, w, w, h->B,
+                                cudaMemcpyDeviceToDevice, st));
+  return SIM_OK;
+}
+
+static sim_status part_split(float* s, float* p, const float* src6, const sim_t* h,
+                             cudaStream_t st) {
+  const size_t w = 3 * h->N3 * sizeof(float);
+  DH_CUDA_TRY(cudaMemcpy2DAsync(s, w, src6, 2 * w, w, h->B, cudaMemcpyDeviceToDevice, st));
+  DH_CUDA_TRY(cudaMemcpy2DAsync(p, w, (const char*)src6 + w, 2 * w, w, h->B,
+                                cudaMemcpyDeviceToDevice, st));
+  return SIM_OK;
+}
+
 // total matter contrast from particles and gas, then the force field g (3 n^3)
-static sim_status compute_force(sim_t* h, const float* s, const float* gas, double pref,
-                                float* g) {
-  if (!h->prm.gravity_on) return dzero(g, 3 * h->N3 * sizeof(float), h->st);
-  DH_TRY(launch_deposit(s, nullptr, h->n, (float)h->inv_dx, h->acc, h->st));
-  DH_TRY(launch_fix_to_float(h->acc, (float)h->cm, gas, -1.0f, h->delta, h->n, h->st));
-  return launch_gravity(h->delta, g, h->ck, h->ck + h->NC, h->n, h->prm.box, pref, h->plans,
-                        h->st);
+static sim_status compute_force(sim_t* h, const float* s, const float* gas, SArg pn, float* g) {
+  const int B = h->B;
+  if (!h->prm.gravity_on) return dzero(g, 3 * B * h->N3 * sizeof(float), h->st);
+  DH_TRY(launch_deposit(s, nullptr, h->n, (float)h->inv_dx, h->acc, B, h->st));
+  DH_TRY(launch_fix_to_float(h->acc, sarg(h->d_cm), gas, (int)(5 * h->N3), -1.0f, h->delta,
+                             h->n, B, h->st));
+  return launch_gravity(h->delta, g, h->ck, h->ck + B * h->NC, h->n, h->prm.box, pn, B,
+                        h->plans, h->st);
 }
 
 // One forward step in place on (gas/gas_tmp ping-pong, s, p, g). With tape != nullptr the
 // inputs of every stage are recorded; diagnostics (star, aux, events) only without tape.
 static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, float* s, float* p,
                                float* g, const TapeSlot* T) {
-  const StepFactors& f = h->sched[i];
   const sim_params& P = h->prm;
+  const int B = h->B;
   cudaStream_t st = h->st;
-  const size_t gb = 5 * h->N3 * sizeof(float), vb = 3 * h->N3 * sizeof(float);
-  const float K1 = P.gravity_on ? (float)f.K1 : 0.0f;
-  const float K2 = P.gravity_on ? (float)f.K2 : 0.0f;
+  const size_t gb = 5 * B * h->N3 * sizeof(float), vb = 3 * B * h->N3 * sizeof(float);
+  const SArg K1 = sc(h, i, SC_K1), K2 = sc(h, i, SC_K2);
   if (T) {
     DH_TRY(dcopy(T->U0, *gas, gb, st));
     DH_TRY(dcopy(T->s0, s, vb, st));
@@ -380,23 +440,25 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     DH_TRY(dcopy(T->g0, g, vb, st));
   }
   // 1. half kick + drift
-  DH_TRY(launch_kick_drift(s, p, g, K1, (float)f.dtau, nullptr, nullptr, h->n,
-                           (float)h->inv_dx, st));
+  DH_TRY(launch_kick_drift(s, p, g, K1, sc(h, i, SC_DTAU), nullptr, nullptr, h->n,
+                           (float)h->inv_dx, B, st));
   float* cur = *gas;
   if (T) {
     DH_TRY(dcopy(T->Uk1, cur, gb, st));
     cur = T->Uk1;
   }
-  if (P.gravity_on) DH_TRY(launch_gas_kick(cur, g, K1, h->n, st));
+  if (P.gravity_on) DH_TRY(launch_gas_kick(cur, g, K1, h->n, B, st));
   // 2. sweeps
   if (P.hydro_on) {
     const char* order = kOrders[i % 6];
-    const double nu = f.dtau * h->inv_dx;
+    const SArg nu = sc(h, i, SC_NU);
     float* outs_tape[3] = {T ? T->Us1 : nullptr, T ? T->Us2 : nullptr, T ? T->Us3 : nullptr};
     for (int k = 0; k < 3; ++k) {
       float* out = T ? outs_tape[k] : (cur == *gas ? *gas_tmp : *gas);
+      const int axis = order[k] - 'x';
       DH_TRY(timed(h, SIM_KT_SWEEP, [&] {
-        return launch_sweep(order[k] - 'x', cur, out, h->n, nu, P.gamma, P.limiter_eps, st);
+        return launch_sweep(axis, cur, out, h->n, nu, P.gamma, P.limiter_eps, B,
+                            h->fwd_var[axis], st);
       }));
       cur = out;
     }
@@ -407,17 +469,16 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   // 3. subgrid
   float* zh = nullptr;
   if (P.subgrid_on) {
-    const SubgridConst c = make_subgrid_const(P, f.a1, i);
     float* out = T ? T->Usg : cur;
     zh = T ? nullptr : h->zhat;
-    DH_TRY(launch_subgrid(cur, out, c, zh, T ? nullptr : h->events, h->N3, st));
+    DH_TRY(launch_subgrid(cur, out, sub_at(h, i), zh, T ? nullptr : h->events, h->N3, B, st));
     cur = out;
   } else if (T) {
     DH_TRY(dcopy(T->Usg, cur, gb, st));
     cur = T->Usg;
   }
   // 4. force at a_{i+1}
-  DH_TRY(compute_force(h, s, cur, f.pref1, g));
+  DH_TRY(compute_force(h, s, cur, sc(h, i, SC_PN1), g));
   if (T) {
     DH_TRY(dcopy(T->s1, s, vb, st));
     DH_TRY(dcopy(T->g1, g, vb, st));
@@ -429,15 +490,15 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     *gas_tmp = t;
   }
   // 5. half kick (+ star readout on the particles)
-  DH_TRY(launch_kick_drift(s, p, g, K2, 0.0f, zh, zh ? h->aux : nullptr, h->n,
-                           (float)h->inv_dx, st));
-  if (P.gravity_on) DH_TRY(launch_gas_kick(*gas, g, K2, h->n, st));
-  if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, h->N3, st));
+  DH_TRY(launch_kick_drift(s, p, g, K2, sarg(0.0f), zh, zh ? h->aux : nullptr, h->n,
+                           (float)h->inv_dx, B, st));
+  if (P.gravity_on) DH_TRY(launch_gas_kick(*gas, g, K2, h->n, B, st));
+  if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, B * h->N3, st));
   return SIM_OK;
 }
 
 static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;  // cells of all instances
   if (!h->lam_gas) {
     DH_TRY(dalloc_t(h, &h->w_gas, 5 * N3));
     DH_TRY(dalloc_t(h, &h->w_gas2, 5 * N3));
@@ -451,10 +512,10 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
     DH_TRY(dalloc_t(h, &h->lamG0, 3 * N3));
     DH_TRY(dalloc_t(h, &h->lamG1, 3 * N3));
     DH_TRY(dalloc_t(h, &h->lam_delta, N3));
-    DH_TRY(dalloc_t(h, &h->lam4, 4 * N3));
+    DH_TRY(dalloc_t(h, &h->lam4, 4 * h->N3));  // one instance at a time
     DH_TRY(dalloc_t(h, &h->lam_scr, 5 * N3));
-    DH_TRY(dalloc_t(h, &h->dglob, SIM_NPARAMS + GX_N));
-    DH_TRY(dalloc_t(h, &h->dslots, (size_t)(h->prm.n_steps + 2) * SL_N));
+    DH_TRY(dalloc_t(h, &h->dglob, (size_t)h->B * NG));
+    DH_TRY(dalloc_t(h, &h->dslots, (size_t)(h->prm.n_steps + 2) * h->B * SL_N));
   }
   if (h->tape_cap < tape_steps) {
     if (h->tape) {
@@ -472,7 +533,7 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
 }
 
 static TapeSlot tape_slot(sim_t* h, int k) {
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;
   float* b = h->tape + (size_t)k * kTapeFloatsPerCell * N3;
   TapeSlot t;
   t.U0 = b;
@@ -491,49 +552,53 @@ static TapeSlot tape_slot(sim_t* h, int k) {
 
 // Adjoint of the force field g = G(s, rho) at one state: lam_G (3 n^3, consumed) ->
 // lam_rho += ..., lam_s += ...; slot[SL_DPREF] += lam_G . g, slot[SL_DCM] += d/d(1 - f_b).
-static sim_status force_adjoint(sim_t* h, const float* s, const float* g, double pref,
+static sim_status force_adjoint(sim_t* h, const float* s, const float* g, SArg pn,
                                 float* lamG, double* slot) {
   if (!h->prm.gravity_on) return SIM_OK;
+  const int B = h->B;
   cudaStream_t st = h->st;
-  DH_TRY(launch_dot(lamG, g, 3 * h->N3, slot + SL_DPREF, st));
-  DH_TRY(launch_gravity_adjoint(lamG, h->lam_delta, h->ck, h->ck + 3 * h->NC, h->n,
-                                h->prm.box, pref, h->plans, st));
-  DH_TRY(launch_axpy(1.0f, h->lam_delta, h->lam_gas, h->N3, st));
-  return launch_deposit_adjoint(s, h->lam_delta, (float)h->cm, h->lam_s, slot + SL_DCM, h->n,
-                                (float)h->inv_dx, st);
+  DH_TRY(launch_dot(lamG, g, 3 * h->N3, slot_part(slot, SL_DPREF), B, st));
+  DH_TRY(launch_gravity_adjoint(lamG, h->lam_delta, h->ck, h->ck + 3 * B * h->NC, h->n,
+                                h->prm.box, pn, B, h->plans, st));
+  DH_TRY(launch_add_strided(h->lam_delta, h->lam_gas, h->N3, 5 * h->N3, B, st));
+  return launch_deposit_adjoint(s, h->lam_delta, sarg(h->d_cm), h->lam_s,
+                                slot_part(slot, SL_DCM), h->n, (float)h->inv_dx, B, st);
 }
 
 // Reverse of forward_step for step i with tape T. In: lam_gas / lam_s / lam_p of the state
 // after the step, lamG1 = adjoint of g(a_{i+1}) carried from step i+1. Out: the same
 // buffers for the state before the step, lamG1 = adjoint of g(a_i) (to carry).
+// slot: the step's partials, [B][SL_N].
 static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot) {
-  const StepFactors& f = h->sched[i];
   const sim_params& P = h->prm;
+  const int B = h->B;
   cudaStream_t st = h->st;
-  const float K1 = P.gravity_on ? (float)f.K1 : 0.0f;
-  const float K2 = P.gravity_on ? (float)f.K2 : 0.0f;
+  const SArg K1 = sc(h, i, SC_K1), K2 = sc(h, i, SC_K2);
   // 5. second half kick
   if (P.gravity_on) {
-    DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, h->lamG1, slot + SL_DK2, h->n, st));
-    DH_TRY(launch_kick_drift_adjoint(T.s1, nullptr, T.g1, K2, 0.0f, h->lam_s, h->lam_p, h->lamG1,
-                                     slot + SL_DK2, nullptr, h->n, (float)h->inv_dx, st));
+    DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, h->lamG1,
+                                   slot_part(slot, SL_DK2), h->n, B, st));
+    DH_TRY(launch_kick_drift_adjoint(T.s1, nullptr, T.g1, K2, sarg(0.0f), h->lam_s, h->lam_p,
+                                     h->lamG1, slot_part(slot, SL_DK2), dpart(nullptr), h->n,
+                                     (float)h->inv_dx, B, st));
     // 4. force at a_{i+1}
-    DH_TRY(force_adjoint(h, T.s1, T.g1, f.pref1, h->lamG1, slot));
+    DH_TRY(force_adjoint(h, T.s1, T.g1, sc(h, i, SC_PN1), h->lamG1, slot));
   }
   // 3. subgrid
-  if (P.subgrid_on) {
-    const SubgridConst c = make_subgrid_const(P, f.a1, i);
-    DH_TRY(launch_subgrid_adjoint(T.Us3, h->lam_gas, c, h->dglob, slot + SL_DFB, h->N3, st));
-  }
+  if (P.subgrid_on)
+    DH_TRY(launch_subgrid_adjoint(T.Us3, h->lam_gas, sub_at(h, i), dpart(h->dglob, NG),
+                                  slot_part(slot, SL_DFB), h->N3, B, st));
   // 2. sweeps in reverse
   if (P.hydro_on) {
     const char* order = kOrders[i % 6];
-    const double nu = f.dtau * h->inv_dx;
+    const SArg nu = sc(h, i, SC_NU);
     const float* ins[3] = {T.Uk1, T.Us1, T.Us2};
     for (int k = 2; k >= 0; --k) {
+      const int axis = order[k] - 'x';
       DH_TRY(timed(h, SIM_KT_SWEEP_ADJOINT, [&] {
-        return launch_sweep_adjoint(order[k] - 'x', ins[k], h->lam_gas, h->lam_tmp, h->n, nu,
-                                    P.gamma, P.limiter_eps, slot + SL_DNU, h->lam_scr, st);
+        return launch_sweep_adjoint(axis, ins[k], h->lam_gas, h->lam_tmp, h->n, nu, P.gamma,
+                                    P.limiter_eps, slot_part(slot, SL_DNU), h->lam_scr, B,
+                                    h->adj_var[axis], st);
       }));
       float* t = h->lam_gas;
       h->lam_gas = h->lam_tmp;
@@ -541,31 +606,38 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot)
     }
   }
   // 1. first half kick and drift
-  DH_TRY(dzero(h->lamG0, 3 * h->N3 * sizeof(float), st));
+  DH_TRY(dzero(h->lamG0, 3 * B * h->N3 * sizeof(float), st));
   if (P.gravity_on)
-    DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, h->lamG0, slot + SL_DK1, h->n, st));
-  DH_TRY(launch_kick_drift_adjoint(T.s0, T.p0, T.g0, K1, (float)f.dtau, h->lam_s, h->lam_p,
-                                   h->lamG0, slot + SL_DK1, slot + SL_DDTAU, h->n,
-                                   (float)h->inv_dx, st));
+    DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, h->lamG0,
+                                   slot_part(slot, SL_DK1), h->n, B, st));
+  DH_TRY(launch_kick_drift_adjoint(T.s0, T.p0, T.g0, K1, sc(h, i, SC_DTAU), h->lam_s, h->lam_p,
+                                   h->lamG0, slot_part(slot, SL_DK1), slot_part(slot, SL_DDTAU),
+                                   h->n, (float)h->inv_dx, B, st));
   float* t = h->lamG0;
   h->lamG0 = h->lamG1;
   h->lamG1 = t;  // carry: lamG1 now holds the adjoint of g(a_i)
   return SIM_OK;
 }
 
-// dL/dparams from the device partials: d/dOmega_m = sum over step slots of slot * coef
-// (schedule derivatives, host FP64, uploaded once) + the flush slot (force at the start of
-// the differentiated span) + the IC terms; sigma8 from the IC amplitude; the subgrid
-// parameters pass through. out is overwritten, or accumulated when `accumulate`.
+// dL/dparams of instance b = blockIdx.x from the device partials: d/dOmega_m = sum over
+// step slots of slot * coef (schedule derivatives, host FP64, uploaded once) + the flush
+// slot (force at the start of the differentiated span) + the IC terms; sigma8 from the IC
+// amplitude; the subgrid parameters pass through. out is overwritten, or accumulated.
 __global__ void param_chain_kernel(const double* __restrict__ slots,
-                                   const double* __restrict__ coef, int nvals,
-                                   const double* __restrict__ flush, double c_pref0,
-                                   double c_cm0, const double* __restrict__ glob,
-                                   double dlnC, double drp, double dfb, double inv_s8, int ics,
-                                   int accumulate, double* __restrict__ out) {
+                                   const double* __restrict__ coef, int nsteps, int B,
+                                   const double* __restrict__ flush,
+                                   const double* __restrict__ cpref,
+                                   const double* __restrict__ pch,
+                                   const double* __restrict__ glob, int ics, int accumulate,
+                                   double* __restrict__ out) {
   __shared__ double red[256];
+  const int b = blockIdx.x;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) acc += slots[i] * coef[i];
+  for (int idx = threadIdx.x; idx < nsteps * SL_N; idx += blockDim.x) {
+    const int i = idx / SL_N, k = idx - i * SL_N;
+    const size_t o = ((size_t)i * B + b) * SL_N + k;
+    acc += slots[o] * coef[o];
+  }
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -573,37 +645,140 @@ __global__ void param_chain_kernel(const double* __restrict__ slots,
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double dom = red[0] + flush[SL_DPREF] * c_pref0 + flush[SL_DCM] * c_cm0;
+    const double* fl = flush + (size_t)b * SL_N;
+    const double* pc = pch + (size_t)b * PCH_N;
+    const double* gl = glob + (size_t)b * NG;
+    double dom = red[0] + fl[SL_DPREF] * cpref[b] + fl[SL_DCM] * pc[PCH_CCM0];
     double ds8 = 0.0;
     if (ics) {
-      const double* gx = glob + SIM_NPARAMS;
-      dom += gx[GX_LAMC] * dlnC + gx[GX_DRP] * drp + gx[GX_DFB_IC] * dfb;
-      ds8 = gx[GX_LAMC] * inv_s8;
+      const double* gx = gl + SIM_NPARAMS;
+      dom += gx[GX_LAMC] * pc[PCH_DLNC] + gx[GX_DRP] * pc[PCH_DRP] + gx[GX_DFB_IC] * pc[PCH_DFB];
+      ds8 = gx[GX_LAMC] * pc[PCH_INVS8];
     }
     double v[SIM_NPARAMS];
     v[SIM_P_OMEGA_M] = dom;
     v[SIM_P_SIGMA8] = ds8;
-    for (int k = SIM_P_DELTA_C; k < SIM_NPARAMS; ++k) v[k] = glob[k];
-    for (int k = 0; k < SIM_NPARAMS; ++k) out[k] = accumulate ? out[k] + v[k] : v[k];
+    for (int k = SIM_P_DELTA_C; k < SIM_NPARAMS; ++k) v[k] = gl[k];
+    double* o = out + (size_t)b * SIM_NPARAMS;
+    for (int k = 0; k < SIM_NPARAMS; ++k) o[k] = accumulate ? o[k] + v[k] : v[k];
   }
 }
 
+// steps [first, last) with slots starting at slots_first; the flush slot belongs to the
+// force at a_{flush_step}
 static sim_status launch_param_chain(sim_t* h, int first, int last, const double* flush,
-                                     double a_flush, bool ics, bool accumulate, double* out,
+                                     int flush_step, bool ics, bool accumulate, double* out,
                                      const double* slots_first) {
-  const int nvals = (last - first) * SL_N;
-  const double pref0 = 1.5 * h->prm.omega_m / a_flush;
-  const double c_pref0 = (1.5 / a_flush) / pref0;
-  param_chain_kernel<<<1, 256, 0, h->st>>>(slots_first, h->dcoef + (size_t)first * SL_N, nvals,
-                                           flush, c_pref0, -h->dfb_dom, h->dglob, h->dlnC_dom,
-                                           h->drp_dom, h->dfb_dom, 1.0 / h->prm.sigma8, ics ? 1 : 0,
-                                           accumulate ? 1 : 0, out);
+  const int B = h->B;
+  param_chain_kernel<<<B, 256, 0, h->st>>>(slots_first, h->dcoef + (size_t)first * B * SL_N,
+                                           last - first, B, flush,
+                                           h->d_cpref + (size_t)flush_step * B, h->d_pch,
+                                           h->dglob, ics ? 1 : 0, accumulate ? 1 : 0, out);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
+// Host constants of every instance and their device tables.
+static sim_status setup_instances(sim_t* h) {
+  const int B = h->B, n = h->n, ns = h->prm.n_steps;
+  h->scheds.resize(B);
+  h->inst.resize(B);
+  std::vector<float> sctab((size_t)ns * SC_N * B), pn((size_t)(ns + 1) * B), cm(B);
+  std::vector<SubgridConst> sub((size_t)ns * B);
+  std::vector<double> pch((size_t)B * PCH_N), cpref((size_t)(ns + 1) * B);
+  std::vector<double> coef((size_t)ns * B * SL_N, 0.0);
+  for (int b = 0; b < B; ++b) {
+    const sim_params& p = h->prms[b];
+    InstConst& c = h->inst[b];
+    h->scheds[b] = make_schedule(p.a_start, p.a_end, p.n_steps, p.omega_m, p.kdk_mode);
+    const std::vector<StepFactors>& sch = h->scheds[b];
+    c.fb = p.omega_b / p.omega_m;
+    c.cm = 1.0 - c.fb;
+    c.dfb_dom = -c.fb / p.omega_m;
+    // IC constants (Sec. 2.1): C = rms_target sqrt(n^3 / sum_k P(k))
+    const double kf = 2.0 * M_PI / p.box, kc = p.kc_frac * M_PI * n / p.box;
+    double total = 0.0;
+    for (int z = 0; z < n; ++z)
+      for (int y = 0; y < n; ++y)
+        for (int x = 0; x <= n / 2; ++x) {
+          const int kz = z > n / 2 ? z - n : z, ky = y > n / 2 ? y - n : y;
+          const double k2 = kf * kf * ((double)x * x + (double)ky * ky + (double)kz * kz);
+          if (k2 <= 0) continue;
+          const double w = (x == 0 || (n % 2 == 0 && x == n / 2)) ? 1.0 : 2.0;
+          total += w * std::exp(-k2 / (kc * kc)) / k2;
+        }
+    const double Di = growth_D(p.a_start, p.omega_m);
+    const double rms =
+        p.rms_ref * (p.sigma8 / p.sigma8_ref) * Di / growth_D(p.a_ref, p.omega_m_ref);
+    c.C = rms * std::sqrt((double)n * n * n / total);
+    const double hh = 1e-5 * p.omega_m;
+    c.dlnC_dom =
+        (growth_D(p.a_start, p.omega_m + hh) - growth_D(p.a_start, p.omega_m - hh)) / (2 * hh) / Di;
+    auto rpf = [&](double om) { return growth_gp(p.a_start, om) / growth_D(p.a_start, om); };
+    c.rp = rpf(p.omega_m);
+    c.drp_dom = (rpf(p.omega_m + hh) - rpf(p.omega_m - hh)) / (2 * hh);
+    c.a2e0 = p.a_start * p.a_start * (p.T_init / temperature_per_energy(p.gamma, p.mu));
+    // step tables
+    for (int i = 0; i < ns; ++i) {
+      const StepFactors& f = sch[i];
+      float* row = sctab.data() + (size_t)i * SC_N * B;
+      row[SC_K1 * B + b] = p.gravity_on ? (float)f.K1 : 0.0f;
+      row[SC_K2 * B + b] = p.gravity_on ? (float)f.K2 : 0.0f;
+      row[SC_DTAU * B + b] = (float)f.dtau;
+      row[SC_NU * B + b] = (float)(f.dtau * h->inv_dx);
+      row[SC_PN1 * B + b] = gravity_pref_norm(f.pref1, n);
+      sub[(size_t)i * B + b] = make_subgrid_const(p, f.a1, i);
+      double* cf = coef.data() + ((size_t)i * B + b) * SL_N;
+      cf[SL_DK1] = f.dK1;
+      cf[SL_DK2] = f.dK2;
+      cf[SL_DNU] = f.ddtau * h->inv_dx;
+      cf[SL_DDTAU] = f.ddtau;
+      cf[SL_DPREF] = f.dpref1 / f.pref1;
+      cf[SL_DCM] = -c.dfb_dom;
+      cf[SL_DFB] = c.dfb_dom;
+    }
+    for (int i = 0; i <= ns; ++i) {
+      const double a = i == 0 ? p.a_start : sch[i - 1].a1;
+      const double pref = 1.5 * p.omega_m / a;
+      pn[(size_t)i * B + b] = gravity_pref_norm(pref, n);
+      cpref[(size_t)i * B + b] = (1.5 / a) / pref;
+    }
+    cm[b] = (float)c.cm;
+    double* pc = pch.data() + (size_t)b * PCH_N;
+    pc[PCH_CCM0] = -c.dfb_dom;
+    pc[PCH_DLNC] = c.dlnC_dom;
+    pc[PCH_DRP] = c.drp_dom;
+    pc[PCH_DFB] = c.dfb_dom;
+    pc[PCH_INVS8] = 1.0 / p.sigma8;
+  }
+  h->sched = h->scheds[0];
+  h->h_sc = sctab;
+  h->h_pn = pn;
+  h->h_sub = sub;
+  DH_TRY(dalloc_t(h, &h->d_sc, sctab.size()));
+  DH_TRY(dalloc_t(h, &h->d_pn, pn.size()));
+  DH_TRY(dalloc_t(h, &h->d_cm, cm.size()));
+  DH_TRY(dalloc_t(h, &h->d_sub, sub.size()));
+  DH_TRY(dalloc_t(h, &h->d_pch, pch.size()));
+  DH_TRY(dalloc_t(h, &h->d_cpref, cpref.size()));
+  DH_TRY(dalloc_t(h, &h->dcoef, coef.size()));
+  auto up = [](void* d, const void* s, size_t bytes) -> sim_status {
+    DH_CUDA_TRY(cudaMemcpy(d, s, bytes, cudaMemcpyHostToDevice));
+    return SIM_OK;
+  };
+  DH_TRY(up(h->d_sc, sctab.data(), sctab.size() * sizeof(float)));
+  DH_TRY(up(h->d_pn, pn.data(), pn.size() * sizeof(float)));
+  DH_TRY(up(h->d_cm, cm.data(), cm.size() * sizeof(float)));
+  DH_TRY(up(h->d_sub, sub.data(), sub.size() * sizeof(SubgridConst)));
+  DH_TRY(up(h->d_pch, pch.data(), pch.size() * sizeof(double)));
+  DH_TRY(up(h->d_cpref, cpref.data(), cpref.size() * sizeof(double)));
+  DH_TRY(up(h->dcoef, coef.data(), coef.size() * sizeof(double)));
+  return SIM_OK;
+}
+
 static sim_status alloc_state(sim_t* h) {
-  const long long N3 = h->N3, NC = h->NC;
+  const long long N3 = h->N3 * h->B, NC = h->NC;
+  const long long words = (h->N3 + 31) / 32 * h->B;
   DH_TRY(dalloc_t(h, &h->gas, 5 * N3));
   DH_TRY(dalloc_t(h, &h->gas2, 5 * N3));
   DH_TRY(dalloc_t(h, &h->s, 3 * N3));
@@ -613,34 +788,44 @@ static sim_status alloc_state(sim_t* h) {
   DH_TRY(dalloc_t(h, &h->aux, N3));
   DH_TRY(dalloc_t(h, &h->zhat, N3));
   DH_TRY(dalloc_t(h, &h->delta, N3));
-  DH_TRY(dalloc_t(h, &h->events, (N3 + 31) / 32));
+  DH_TRY(dalloc_t(h, &h->events, words));
   DH_TRY(dalloc_t(h, &h->acc, N3));
-  DH_TRY(dalloc_t(h, &h->ck, 5 * NC));
+  DH_TRY(dalloc_t(h, &h->ck, (size_t)(4 * h->B > 5 ? 4 * h->B : 5) * NC));
   DH_TRY(dalloc_t(h, &h->noise, N3));
   DH_TRY(dalloc_t(h, &h->f4, 4 * N3));
   DH_TRY(dalloc_t(h, &h->init_gas, 5 * N3));
   DH_TRY(dalloc_t(h, &h->init_part, 6 * N3));
   DH_TRY(dalloc_t(h, &h->prev_gas, 5 * N3));
   DH_TRY(dalloc_t(h, &h->prev_part, 6 * N3));
-  DH_TRY(dalloc_t(h, &h->speed_bits, 1));
-  DH_TRY(dalloc_t(h, &h->dcoef, (size_t)h->prm.n_steps * SL_N));
+  DH_TRY(dalloc_t(h, &h->speed_bits, h->B));
   DH_TRY(dzero(h->acc, N3 * sizeof(unsigned long long), h->st));
-  DH_TRY(dzero(h->events, ((N3 + 31) / 32) * sizeof(uint32_t), h->st));
-  // chain-rule coefficients of the per-step partials with respect to Omega_m
-  std::vector<double> coef((size_t)h->prm.n_steps * SL_N, 0.0);
-  for (int i = 0; i < h->prm.n_steps; ++i) {
-    const StepFactors& f = h->sched[i];
-    double* c = coef.data() + (size_t)i * SL_N;
-    c[SL_DK1] = f.dK1;
-    c[SL_DK2] = f.dK2;
-    c[SL_DNU] = f.ddtau * h->inv_dx;
-    c[SL_DDTAU] = f.ddtau;
-    c[SL_DPREF] = f.dpref1 / f.pref1;
-    c[SL_DCM] = -h->dfb_dom;
-    c[SL_DFB] = h->dfb_dom;
+  DH_TRY(dzero(h->events, words * sizeof(uint32_t), h->st));
+  return SIM_OK;
+}
+
+// Initial conditions of every instance from its noise (already in h->noise), into
+// init_gas / init_part (Sec. 2.1).
+static sim_status make_ics(sim_t* h) {
+  const long long N3 = h->N3;
+  cudaStream_t st = h->st;
+  for (int b = 0; b < h->B; ++b) {
+    const sim_params& p = h->prms[b];
+    const InstConst& c = h->inst[b];
+    float* f4 = h->f4 + (size_t)b * 4 * N3;
+    float* part = h->init_part + (size_t)b * 6 * N3;
+    DH_TRY(launch_linear_field(h->noise + (size_t)b * N3, f4, h->ck, h->n, p.box, p.kc_frac, c.C,
+                               ic_plans(h), st));
+    DH_TRY(launch_place(f4, h->init_gas + (size_t)b * 5 * N3, part, part + 3 * N3, c.rp, c.fb,
+                        c.a2e0, N3, st));
   }
-  DH_CUDA_TRY(cudaMemcpy(h->dcoef, coef.data(), coef.size() * sizeof(double),
-                         cudaMemcpyHostToDevice));
+  return SIM_OK;
+}
+
+static sim_status load_noise(sim_t* h, const float* noise) {
+  if (noise) return dcopy(h->noise, noise, h->B * h->N3 * sizeof(float), h->st);
+  for (int b = 0; b < h->B; ++b)
+    DH_TRY(launch_noise(h->prms[b].seed, h->prms[b].instance, h->noise + (size_t)b * h->N3,
+                        h->N3, h->st));
   return SIM_OK;
 }
 
@@ -649,7 +834,7 @@ static void clear_checkpoints(sim_t* h) { h->ckpt_count = 0; }
 static sim_status ensure_ckpt_pool(sim_t* h, int count) {
   while ((int)h->ckpt_pool.size() < count) {
     float* c = nullptr;
-    DH_TRY(dalloc_t(h, &c, 11 * h->N3));
+    DH_TRY(dalloc_t(h, &c, 11 * h->N3 * h->B));
     h->ckpt_pool.push_back(c);
     h->ckpt_step.push_back(0);
   }
@@ -657,22 +842,22 @@ static sim_status ensure_ckpt_pool(sim_t* h, int count) {
 }
 
 static sim_status reset_to_init(sim_t* h) {
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;
   cudaStream_t st = h->st;
   DH_TRY(dcopy(h->gas, h->init_gas, 5 * N3 * sizeof(float), st));
-  DH_TRY(dcopy(h->s, h->init_part, 3 * N3 * sizeof(float), st));
-  DH_TRY(dcopy(h->p, h->init_part + 3 * N3, 3 * N3 * sizeof(float), st));
+  DH_TRY(part_split(h->s, h->p, h->init_part, h, st));
   DH_TRY(dzero(h->star, N3 * sizeof(float), st));
   DH_TRY(dzero(h->aux, N3 * sizeof(float), st));
   h->step = h->init_step;
-  DH_TRY(compute_force(h, h->s, h->gas, 1.5 * h->prm.omega_m / a_of_step(h, h->init_step), h->g));
+  DH_TRY(compute_force(h, h->s, h->gas, pn_at(h, h->init_step), h->g));
   clear_checkpoints(h);
   h->prev_step = -1;
   return SIM_OK;
 }
 
+// checkpoint layout: gas (B 5 n^3) | s (B 3 n^3) | p (B 3 n^3)
 static sim_status store_checkpoint(sim_t* h) {
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;
   if (h->ckpt_count >= (int)h->ckpt_pool.size()) {
     set_error("internal: checkpoint pool exhausted");
     return SIM_EINVAL;
@@ -683,6 +868,150 @@ static sim_status store_checkpoint(sim_t* h) {
   DH_TRY(dcopy(c, h->gas, 5 * N3 * sizeof(float), h->st));
   DH_TRY(dcopy(c + 5 * N3, h->s, 3 * N3 * sizeof(float), h->st));
   return dcopy(c + 8 * N3, h->p, 3 * N3 * sizeof(float), h->st);
+}
+
+static sim_status validate_batch(const sim_params* p, int B) {
+  if (!p || B < 1) {
+    set_error("null parameter block or B < 1");
+    return SIM_EINVAL;
+  }
+  for (int b = 0; b < B; ++b) DH_TRY(validate(p + b));
+  const sim_params& a = p[0];
+  for (int b = 1; b < B; ++b) {
+    const sim_params& q = p[b];
+    const bool same = q.n == a.n && q.box == a.box && q.n_steps == a.n_steps &&
+                      q.a_start == a.a_start && q.a_end == a.a_end &&
+                      q.ckpt_every == a.ckpt_every && q.subgrid_on == a.subgrid_on &&
+                      q.gravity_on == a.gravity_on && q.hydro_on == a.hydro_on &&
+                      q.kdk_mode == a.kdk_mode && q.gamma == a.gamma && q.mu == a.mu &&
+                      q.h == a.h && q.rms_ref == a.rms_ref && q.a_ref == a.a_ref &&
+                      q.sigma8_ref == a.sigma8_ref && q.omega_m_ref == a.omega_m_ref &&
+                      q.kc_frac == a.kc_frac && q.limiter_eps == a.limiter_eps &&
+                      q.cfl_max == a.cfl_max;
+    if (!same) {
+      set_error("sim_init_batch: instance %d differs from instance 0 in a shared field (n, "
+                "box, schedule, switches, gamma, mu, h, IC normalisation, limiter, cfl_max)", b);
+      return SIM_EINVAL;
+    }
+  }
+  const long long zlim = (long long)a.n * B;
+  if (zlim > 65535) {
+    set_error("sim_init_batch: n * B = %lld exceeds the launch grid limit 65535", zlim);
+    return SIM_EINVAL;
+  }
+  return SIM_OK;
+}
+
+static sim_status cfl_now(sim_t* h, double* cfl_out);
+
+// Checks and allocations of sim_run (never inside a capture).
+static sim_status run_prepare(sim_t* h, int n_steps) {
+  if (h->step != h->init_step || h->ckpt_count != 0) {
+    set_error("sim_run: the handle must be at its initial state (sim_init / sim_reset)");
+    return SIM_EINVAL;
+  }
+  if (n_steps < 0 || h->step + n_steps > h->prm.n_steps) {
+    set_error("sim_run: n_steps out of range");
+    return SIM_EINVAL;
+  }
+  return ensure_ckpt_pool(h, (n_steps + h->prm.ckpt_every - 1) / h->prm.ckpt_every);
+}
+
+// n_steps forward steps with a checkpoint every ckpt_every steps (Sec. 2.3.5).
+static sim_status run_body(sim_t* h, int n_steps) {
+  for (int k = 0; k < n_steps; ++k) {
+    if ((h->step - h->init_step) % h->prm.ckpt_every == 0) DH_TRY(store_checkpoint(h));
+    DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr));
+    h->step += 1;
+    if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
+      double c = 0;
+      DH_TRY(cfl_now(h, &c));
+      if (!(c <= h->prm.cfl_max)) {
+        set_error("sim_run: CFL number %.4g above cfl_max %.4g after step %d", c,
+                  h->prm.cfl_max, h->step);
+        return std::isfinite(c) ? SIM_ECFL : SIM_ENAN;
+      }
+    }
+  }
+  h->prev_step = -1;
+  return SIM_OK;
+}
+
+static sim_status run_adjoint_prepare(sim_t* h, const float* dL_dnoise, const double* dL_dparams) {
+  if (!dL_dparams) {
+    set_error("sim_run_adjoint: null arguments");
+    return SIM_EINVAL;
+  }
+  if (h->ckpt_count == 0) {
+    set_error("sim_run_adjoint: no sim_run to differentiate");
+    return SIM_EINVAL;
+  }
+  if (!h->ics_valid && dL_dnoise) {
+    set_error("sim_run_adjoint: the run did not start from initial conditions");
+    return SIM_EINVAL;
+  }
+  return ensure_adjoint_buffers(h, h->prm.ckpt_every);
+}
+
+// Reverse pass over the checkpointed run: every segment recomputed forward with the tape,
+// then reversed step by step; the initial force and the ICs last.
+static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* dL_dpart,
+                                   float* dL_dnoise, double* dL_dparams) {
+  const long long N3 = h->N3 * h->B;
+  const int B = h->B;
+  const int nseg = h->ckpt_count;
+  const int last = h->step;
+  cudaStream_t st = h->st;
+  DH_TRY(dzero(h->dslots, (size_t)(h->prm.n_steps + 2) * B * SL_N * sizeof(double), st));
+  DH_TRY(dzero(h->dglob, (size_t)B * NG * sizeof(double), st));
+  if (dL_dgas)
+    DH_TRY(dcopy(h->lam_gas, dL_dgas, 5 * N3 * sizeof(float), st));
+  else
+    DH_TRY(dzero(h->lam_gas, 5 * N3 * sizeof(float), st));
+  if (dL_dpart) {
+    DH_TRY(part_split(h->lam_s, h->lam_p, dL_dpart, h, st));
+  } else {
+    DH_TRY(dzero(h->lam_s, 3 * N3 * sizeof(float), st));
+    DH_TRY(dzero(h->lam_p, 3 * N3 * sizeof(float), st));
+  }
+  DH_TRY(dzero(h->lamG1, 3 * N3 * sizeof(float), st));
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int first = h->ckpt_step[seg];
+    const int end = seg + 1 < nseg ? h->ckpt_step[seg + 1] : last;
+    const float* c = h->ckpt_pool[seg];
+    DH_TRY(dcopy(h->w_gas, c, 5 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
+    DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
+    DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, first), h->w_g));
+    for (int i = first; i < end; ++i) {
+      const TapeSlot T = tape_slot(h, i - first);
+      DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
+    }
+    for (int i = end - 1; i >= first; --i)
+      DH_TRY(reverse_step(h, i, tape_slot(h, i - first), h->dslots + (size_t)i * B * SL_N));
+  }
+  // g at the start of the run is a function of the initial state
+  const TapeSlot T0 = tape_slot(h, 0);
+  const int s0 = h->ckpt_step[0];
+  double* slot0 = h->dslots + (size_t)h->prm.n_steps * B * SL_N;
+  DH_TRY(force_adjoint(h, T0.s0, T0.g0, pn_at(h, s0), h->lamG1, slot0));
+  // through the initial conditions to the white noise, one instance at a time
+  if (h->ics_valid) {
+    const long long n3 = h->N3;
+    for (int b = 0; b < B; ++b) {
+      const InstConst& c = h->inst[b];
+      double* gx = h->dglob + (size_t)b * NG + SIM_NPARAMS;
+      const float* f4 = h->f4 + (size_t)b * 4 * n3;
+      DH_TRY(launch_ic_adjoint(f4, h->lam_gas + (size_t)b * 5 * n3, h->lam_s + (size_t)b * 3 * n3,
+                               h->lam_p + (size_t)b * 3 * n3, h->lam4,
+                               dL_dnoise ? dL_dnoise + (size_t)b * n3 : nullptr, h->ck, h->n,
+                               h->prm.box, h->prm.kc_frac, c.C, c.rp, c.fb, c.a2e0,
+                               gx + GX_DRP, gx + GX_DFB_IC, ic_plans(h), st));
+      DH_TRY(launch_dot(h->lam4, f4, 4 * n3, dpart(gx + GX_LAMC), 1, st));
+    }
+  }
+  return launch_param_chain(h, s0, last, slot0, s0, h->ics_valid, false, dL_dparams,
+                            h->dslots + (size_t)s0 * B * SL_N);
 }
 
 }  // namespace dh
@@ -735,72 +1064,36 @@ sim_status sim_params_default(sim_params* p) {
 
 const char* sim_last_error(const sim_t* h) { return h ? h->err.c_str() : get_error(); }
 
-sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t** out) {
+
+sim_status sim_init_batch(const sim_params* p, int32_t B, const float* noise, void* stream,
+                          sim_t** out) {
   if (!out) {
     set_error("sim_init: out is NULL");
     return SIM_EINVAL;
   }
   *out = nullptr;
-  DH_TRY(validate(p));
+  DH_TRY(validate_batch(p, B));
   sim_t* h = new sim_t();
-  h->prm = *p;
+  h->prm = p[0];
+  h->prms.assign(p, p + B);
+  h->B = B;
   h->n = p->n;
   h->N3 = (long long)p->n * p->n * p->n;
   h->NC = (long long)p->n * p->n * (p->n / 2 + 1);
   h->st = (cudaStream_t)stream;
   h->dx = p->box / p->n;
   h->inv_dx = p->n / p->box;
-  h->fb = p->omega_b / p->omega_m;
-  h->cm = 1.0 - h->fb;
-  h->dfb_dom = -h->fb / p->omega_m;
-  h->sched = make_schedule(p->a_start, p->a_end, p->n_steps, p->omega_m, p->kdk_mode);
-  // IC constants (Sec. 2.1): C = rms_target sqrt(n^3 / sum_k P(k))
-  {
-    const int n = p->n;
-    const double kf = 2.0 * M_PI / p->box, kc = p->kc_frac * M_PI * n / p->box;
-    double total = 0.0;
-    for (int z = 0; z < n; ++z)
-      for (int y = 0; y < n; ++y)
-        for (int x = 0; x <= n / 2; ++x) {
-          const int kz = z > n / 2 ? z - n : z, ky = y > n / 2 ? y - n : y;
-          const double k2 = kf * kf * ((double)x * x + (double)ky * ky + (double)kz * kz);
-          if (k2 <= 0) continue;
-          const double w = (x == 0 || (n % 2 == 0 && x == n / 2)) ? 1.0 : 2.0;
-          total += w * std::exp(-k2 / (kc * kc)) / k2;
-        }
-    const double Di = growth_D(p->a_start, p->omega_m);
-    const double rms = p->rms_ref * (p->sigma8 / p->sigma8_ref) * Di /
-                       growth_D(p->a_ref, p->omega_m_ref);
-    h->C = rms * std::sqrt((double)n * n * n / total);
-    const double hh = 1e-5 * p->omega_m;
-    h->dlnC_dom = (growth_D(p->a_start, p->omega_m + hh) - growth_D(p->a_start, p->omega_m - hh)) /
-                  (2 * hh) / Di;
-    auto rpf = [&](double om) { return growth_gp(p->a_start, om) / growth_D(p->a_start, om); };
-    h->rp = rpf(p->omega_m);
-    h->drp_dom = (rpf(p->omega_m + hh) - rpf(p->omega_m - hh)) / (2 * hh);
-    const double e0 = p->T_init / temperature_per_energy(p->gamma, p->mu);
-    h->a2e0 = p->a_start * p->a_start * e0;
-  }
   sim_status r = prepare_sweep_kernels();
-  if (r == SIM_OK) r = h->plans.create(p->n);
+  if (r == SIM_OK) r = setup_instances(h);
+  if (r == SIM_OK) r = h->plans.create(p->n, B);
+  if (r == SIM_OK && B > 1) r = h->plans1.create(p->n, 1);
   if (r == SIM_OK) r = alloc_state(h);
   if (r == SIM_OK && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     set_error("cudaStreamCreate failed");
     r = SIM_ECUDA;
   }
-  cudaStream_t st = h->st;
-  if (r == SIM_OK) {
-    if (noise)
-      r = dcopy(h->noise, noise, h->N3 * sizeof(float), st);
-    else
-      r = launch_noise(p->seed, p->instance, h->noise, h->N3, st);
-  }
-  if (r == SIM_OK)
-    r = launch_linear_field(h->noise, h->f4, h->ck, p->n, p->box, p->kc_frac, h->C, h->plans, st);
-  if (r == SIM_OK) r = launch_place(h->f4, h->gas, h->s, h->p, h->rp, h->fb, h->a2e0, h->N3, st);
-  if (r == SIM_OK) r = dcopy(h->init_gas, h->gas, 5 * h->N3 * sizeof(float), st);
-  if (r == SIM_OK) r = dcopy(h->init_part, h->s, 3 * h->N3 * sizeof(float), st);
-  if (r == SIM_OK) r = dcopy(h->init_part + 3 * h->N3, h->p, 3 * h->N3 * sizeof(float), st);
+  if (r == SIM_OK) r = load_noise(h, noise);
+  if (r == SIM_OK) r = make_ics(h);
   if (r == SIM_OK) {
     h->ics_valid = true;
     h->init_step = 0;
@@ -814,6 +1107,12 @@ sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t
   return SIM_OK;
 }
 
+sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t** out) {
+  return sim_init_batch(p, 1, noise, stream, out);
+}
+
+int32_t sim_batch_size(const sim_t* h) { return h ? h->B : 0; }
+
 void sim_destroy(sim_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
@@ -822,6 +1121,7 @@ void sim_destroy(sim_t* h) {
   for (cudaEvent_t e : h->kt_ev) cudaEventDestroy(e);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->plans.destroy();
+  h->plans1.destroy();
   for (void* a : h->allocs)
     if (a) cudaFree(a);
   delete h;
@@ -863,16 +1163,95 @@ sim_status sim_kernel_times(sim_t* h, double* ms, int64_t* count, int32_t reset)
   return SIM_OK;
 }
 
+sim_status sim_set_sweep_variants(sim_t* h, const int32_t* fwd, const int32_t* adj) {
+  if (!h) return SIM_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    const int vals[2] = {fwd ? fwd[a] : 0, adj ? adj[a] : 0};
+    for (int v : vals)
+      if (v < SIM_SWEEP_DEFAULT || v > SIM_SWEEP_MARCH16) {
+        set_error("sim_set_sweep_variants: unknown variant %d", v);
+        return fail(h, SIM_EINVAL);
+      }
+  }
+  clear_graphs(h);
+  for (int a = 0; a < 3; ++a) {
+    if (fwd) h->fwd_var[a] = fwd[a];
+    if (adj) h->adj_var[a] = adj[a];
+  }
+  return SIM_OK;
+}
+
+sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_out) {
+  if (!h || reps < 1) {
+    set_error("sim_autotune: null handle or reps < 1");
+    return fail(h, SIM_EINVAL);
+  }
+  sim_status r = ensure_adjoint_buffers(h, 0);
+  if (r != SIM_OK) return fail(h, r);
+  clear_graphs(h);
+  cudaStream_t st = h->st;
+  cudaEvent_t e0, e1;
+  DH_CUDA_TRY(cudaEventCreate(&e0));
+  DH_CUDA_TRY(cudaEventCreate(&e1));
+  const int i = h->step < h->prm.n_steps ? h->step : h->prm.n_steps - 1;
+  const SArg nu = sc(h, i, SC_NU);
+  const int cand[3] = {SIM_SWEEP_TILE, SIM_SWEEP_MARCH32, SIM_SWEEP_MARCH16};
+  auto time_it = [&](auto launch, float* ms) -> sim_status {
+    DH_TRY(launch());  // warm-up
+    float best = 1e30f;
+    for (int k = 0; k < reps; ++k) {
+      DH_CUDA_TRY(cudaEventRecord(e0, st));
+      DH_TRY(launch());
+      DH_CUDA_TRY(cudaEventRecord(e1, st));
+      DH_CUDA_TRY(cudaEventSynchronize(e1));
+      float t = 0.0f;
+      DH_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      best = t < best ? t : best;
+    }
+    *ms = best;
+    return SIM_OK;
+  };
+  auto body = [&]() -> sim_status {
+    for (int axis = 0; axis < 3; ++axis) {
+      const int nc = axis == 0 ? 1 : 3;
+      float bf = 1e30f, ba = 1e30f;
+      for (int c = 0; c < nc; ++c) {
+        float t = 0.0f;
+        DH_TRY(time_it([&] { return launch_sweep(axis, h->gas, h->w_gas2, h->n, nu, h->prm.gamma,
+                                                 h->prm.limiter_eps, h->B, cand[c], st); }, &t));
+        if (t < bf) {
+          bf = t;
+          h->fwd_var[axis] = cand[c];
+        }
+        DH_TRY(time_it([&] { return launch_sweep_adjoint(axis, h->gas, h->gas, h->lam_tmp, h->n,
+                                                         nu, h->prm.gamma, h->prm.limiter_eps,
+                                                         dpart(h->dslots, SL_N), h->lam_scr,
+                                                         h->B, cand[c], st); }, &t));
+        if (t < ba) {
+          ba = t;
+          h->adj_var[axis] = cand[c];
+        }
+      }
+      if (fwd_out) fwd_out[axis] = h->fwd_var[axis];
+      if (adj_out) adj_out[axis] = h->adj_var[axis];
+    }
+    return SIM_OK;
+  };
+  r = body();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return fail(h, r);
+}
+
 sim_status sim_step(sim_t* h) {
   if (!h) return SIM_EINVAL;
   if (h->step >= h->prm.n_steps) {
     set_error("sim_step: already at the last step (%d)", h->prm.n_steps);
     return fail(h, SIM_EINVAL);
   }
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;
   sim_status r = dcopy(h->prev_gas, h->gas, 5 * N3 * sizeof(float), h->st);
-  if (r == SIM_OK) r = dcopy(h->prev_part, h->s, 3 * N3 * sizeof(float), h->st);
-  if (r == SIM_OK) r = dcopy(h->prev_part + 3 * N3, h->p, 3 * N3 * sizeof(float), h->st);
+  if (r == SIM_OK) r = part_join(h->prev_part, h->s, h->p, h, h->st);
   if (r == SIM_OK) r = forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr);
   if (r != SIM_OK) return fail(h, r);
   h->prev_step = h->step;
@@ -890,36 +1269,34 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
     set_error("sim_step_adjoint: no sim_step to differentiate");
     return fail(h, SIM_EINVAL);
   }
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;
+  const int B = h->B;
   cudaStream_t st = h->st;
   const int i = h->prev_step;
   sim_status r = ensure_adjoint_buffers(h, 1);
   if (r != SIM_OK) return fail(h, r);
   const TapeSlot T = tape_slot(h, 0);
   double* slot = h->dslots;
-  const double a0 = h->sched[i].a0;
   auto run = [&]() -> sim_status {
-    DH_TRY(dzero(h->dslots, 2 * SL_N * sizeof(double), st));
-    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + GX_N) * sizeof(double), st));
+    DH_TRY(dzero(h->dslots, 2 * (size_t)B * SL_N * sizeof(double), st));
+    DH_TRY(dzero(h->dglob, (size_t)B * NG * sizeof(double), st));
     // recompute the step from its input with the tape
     DH_TRY(dcopy(h->w_gas, h->prev_gas, 5 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(h->w_s, h->prev_part, 3 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(h->w_p, h->prev_part + 3 * N3, 3 * N3 * sizeof(float), st));
-    DH_TRY(compute_force(h, h->w_s, h->w_gas, 1.5 * h->prm.omega_m / a0, h->w_g));
+    DH_TRY(part_split(h->w_s, h->w_p, h->prev_part, h, st));
+    DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, i), h->w_g));
     DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
     // reverse
     DH_TRY(dcopy(h->lam_gas, adj_gas, 5 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(h->lam_s, adj_part, 3 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(h->lam_p, adj_part + 3 * N3, 3 * N3 * sizeof(float), st));
+    DH_TRY(part_split(h->lam_s, h->lam_p, adj_part, h, st));
     DH_TRY(dzero(h->lamG1, 3 * N3 * sizeof(float), st));
     DH_TRY(reverse_step(h, i, T, slot));
     // g(a_i) is a function of the input state: flush its adjoint now
-    DH_TRY(force_adjoint(h, T.s0, T.g0, 1.5 * h->prm.omega_m / a0, h->lamG1, slot + SL_N));
+    double* flush = slot + (size_t)B * SL_N;
+    DH_TRY(force_adjoint(h, T.s0, T.g0, pn_at(h, i), h->lamG1, flush));
     DH_TRY(dcopy(adj_gas, h->lam_gas, 5 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(adj_part, h->lam_s, 3 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(adj_part + 3 * N3, h->lam_p, 3 * N3 * sizeof(float), st));
+    DH_TRY(part_join(adj_part, h->lam_s, h->lam_p, h, st));
     if (adj_params)
-      DH_TRY(launch_param_chain(h, i, i + 1, slot + SL_N, a0, false, true, adj_params, slot));
+      DH_TRY(launch_param_chain(h, i, i + 1, flush, i, false, true, adj_params, slot));
     return SIM_OK;
   };
   return fail(h, run());
@@ -927,109 +1304,23 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
 
 sim_status sim_run(sim_t* h, int32_t n_steps) {
   if (!h) return SIM_EINVAL;
-  if (h->step != h->init_step || h->ckpt_count != 0) {
-    set_error("sim_run: the handle must be at its initial state (sim_init / sim_reset)");
-    return fail(h, SIM_EINVAL);
-  }
-  if (n_steps < 0 || h->step + n_steps > h->prm.n_steps) {
-    set_error("sim_run: n_steps out of range");
-    return fail(h, SIM_EINVAL);
-  }
-  sim_status r = ensure_ckpt_pool(h, (n_steps + h->prm.ckpt_every - 1) / h->prm.ckpt_every);
+  sim_status r = run_prepare(h, n_steps);
   if (r != SIM_OK) return fail(h, r);
-  auto body = [&]() -> sim_status {
-    for (int k = 0; k < n_steps; ++k) {
-      if ((h->step - h->init_step) % h->prm.ckpt_every == 0) DH_TRY(store_checkpoint(h));
-      DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr));
-      h->step += 1;
-      if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
-        double c = 0;
-        DH_TRY(sim_cfl(h, &c));
-        if (!(c <= h->prm.cfl_max)) {
-          set_error("sim_run: CFL number %.4g above cfl_max %.4g after step %d", c,
-                    h->prm.cfl_max, h->step);
-          return std::isfinite(c) ? SIM_ECFL : SIM_ENAN;
-        }
-      }
-    }
-    h->prev_step = -1;
-    return SIM_OK;
-  };
   // the CFL watchdog reads back every step: never captured
-  if (h->prm.cfl_max > 0) return fail(h, body());
-  return fail(h, run_maybe_graph(h, 1, {(uintptr_t)n_steps}, body));
+  if (h->prm.cfl_max > 0) return fail(h, run_body(h, n_steps));
+  return fail(h, run_maybe_graph(h, 1, {(uintptr_t)n_steps}, [&] { return run_body(h, n_steps); }));
 }
 
 sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart,
                            float* dL_dnoise, double* dL_dparams) {
-  if (!h || !dL_dparams) {
-    set_error("sim_run_adjoint: null arguments");
-    return fail(h, SIM_EINVAL);
-  }
-  if (h->ckpt_count == 0) {
-    set_error("sim_run_adjoint: no sim_run to differentiate");
-    return fail(h, SIM_EINVAL);
-  }
-  if (!h->ics_valid && dL_dnoise) {
-    set_error("sim_run_adjoint: the run did not start from initial conditions");
-    return fail(h, SIM_EINVAL);
-  }
-  const long long N3 = h->N3;
-  sim_status r = ensure_adjoint_buffers(h, h->prm.ckpt_every);
+  if (!h) return SIM_EINVAL;
+  sim_status r = run_adjoint_prepare(h, dL_dnoise, dL_dparams);
   if (r != SIM_OK) return fail(h, r);
-  const int nseg = h->ckpt_count;
-  const int last = h->step;
-  auto body = [&]() -> sim_status {
-    cudaStream_t st = h->st;
-    DH_TRY(dzero(h->dslots, (size_t)(h->prm.n_steps + 2) * SL_N * sizeof(double), st));
-    DH_TRY(dzero(h->dglob, (SIM_NPARAMS + GX_N) * sizeof(double), st));
-    if (dL_dgas)
-      DH_TRY(dcopy(h->lam_gas, dL_dgas, 5 * N3 * sizeof(float), st));
-    else
-      DH_TRY(dzero(h->lam_gas, 5 * N3 * sizeof(float), st));
-    if (dL_dpart) {
-      DH_TRY(dcopy(h->lam_s, dL_dpart, 3 * N3 * sizeof(float), st));
-      DH_TRY(dcopy(h->lam_p, dL_dpart + 3 * N3, 3 * N3 * sizeof(float), st));
-    } else {
-      DH_TRY(dzero(h->lam_s, 3 * N3 * sizeof(float), st));
-      DH_TRY(dzero(h->lam_p, 3 * N3 * sizeof(float), st));
-    }
-    DH_TRY(dzero(h->lamG1, 3 * N3 * sizeof(float), st));
-    for (int seg = nseg - 1; seg >= 0; --seg) {
-      const int first = h->ckpt_step[seg];
-      const int end = seg + 1 < nseg ? h->ckpt_step[seg + 1] : last;
-      const float* c = h->ckpt_pool[seg];
-      DH_TRY(dcopy(h->w_gas, c, 5 * N3 * sizeof(float), st));
-      DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
-      DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
-      DH_TRY(compute_force(h, h->w_s, h->w_gas, 1.5 * h->prm.omega_m / a_of_step(h, first), h->w_g));
-      for (int i = first; i < end; ++i) {
-        const TapeSlot T = tape_slot(h, i - first);
-        DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
-      }
-      for (int i = end - 1; i >= first; --i)
-        DH_TRY(reverse_step(h, i, tape_slot(h, i - first), h->dslots + (size_t)i * SL_N));
-    }
-    // g at the start of the run is a function of the initial state
-    const TapeSlot T0 = tape_slot(h, 0);
-    const int s0 = h->ckpt_step[0];
-    const double a0 = a_of_step(h, s0);
-    double* slot0 = h->dslots + (size_t)h->prm.n_steps * SL_N;
-    DH_TRY(force_adjoint(h, T0.s0, T0.g0, 1.5 * h->prm.omega_m / a0, h->lamG1, slot0));
-    // through the initial conditions to the white noise
-    if (h->ics_valid) {
-      double* gx = h->dglob + SIM_NPARAMS;
-      DH_TRY(launch_ic_adjoint(h->f4, h->lam_gas, h->lam_s, h->lam_p, h->lam4, dL_dnoise, h->ck,
-                               h->n, h->prm.box, h->prm.kc_frac, h->C, h->rp, h->fb, h->a2e0,
-                               gx + GX_DRP, gx + GX_DFB_IC, h->plans, st));
-      DH_TRY(launch_dot(h->lam4, h->f4, 4 * N3, gx + GX_LAMC, st));
-    }
-    return launch_param_chain(h, s0, last, slot0, a0, h->ics_valid, false, dL_dparams,
-                              h->dslots + (size_t)s0 * SL_N);
-  };
   const std::vector<uintptr_t> key = {(uintptr_t)dL_dgas, (uintptr_t)dL_dpart,
                                       (uintptr_t)dL_dnoise, (uintptr_t)dL_dparams};
-  return fail(h, run_maybe_graph(h, 2, key, body));
+  return fail(h, run_maybe_graph(h, 2, key, [&] {
+    return run_adjoint_body(h, dL_dgas, dL_dpart, dL_dnoise, dL_dparams);
+  }));
 }
 
 sim_status sim_reset(sim_t* h) {
@@ -1039,16 +1330,8 @@ sim_status sim_reset(sim_t* h) {
 
 sim_status sim_reinit(sim_t* h, const float* noise) {
   if (!h) return SIM_EINVAL;
-  cudaStream_t st = h->st;
-  const long long N3 = h->N3;
-  sim_status r = noise ? dcopy(h->noise, noise, N3 * sizeof(float), st)
-                       : launch_noise(h->prm.seed, h->prm.instance, h->noise, N3, st);
-  if (r == SIM_OK)
-    r = launch_linear_field(h->noise, h->f4, h->ck, h->n, h->prm.box, h->prm.kc_frac, h->C,
-                            h->plans, st);
-  if (r == SIM_OK)
-    r = launch_place(h->f4, h->init_gas, h->init_part, h->init_part + 3 * N3, h->rp, h->fb,
-                     h->a2e0, N3, st);
+  sim_status r = load_noise(h, noise);
+  if (r == SIM_OK) r = make_ics(h);
   if (r == SIM_OK) {
     h->ics_valid = true;
     h->init_step = 0;
@@ -1064,24 +1347,25 @@ sim_status sim_loss_density(sim_t* h, const float* target, double c, float* dL_d
     return fail(h, SIM_EINVAL);
   }
   cudaStream_t st = h->st;
-  sim_status r = dzero(dL_dgas + h->N3, 4 * h->N3 * sizeof(float), st);
-  if (r == SIM_OK) r = dzero(loss, sizeof(double), st);
-  if (r == SIM_OK) r = launch_density_loss(h->gas, target, (float)c, dL_dgas, loss, h->N3, st);
+  sim_status r = dzero(dL_dgas, 5 * h->B * h->N3 * sizeof(float), st);
+  if (r == SIM_OK) r = dzero(loss, h->B * sizeof(double), st);
+  if (r == SIM_OK)
+    r = launch_density_loss(h->gas, target, (float)c, dL_dgas, loss, h->N3, h->B, st);
   return fail(h, r);
 }
 
 sim_status sim_get_state(sim_t* h, float* gas, float* part, float* star, float* aux,
                          uint32_t* events, float* gravity, int32_t* step) {
   if (!h) return SIM_EINVAL;
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;
+  const long long words = (h->N3 + 31) / 32 * h->B;
   cudaStream_t st = h->st;
   sim_status r = SIM_OK;
   if (gas && r == SIM_OK) r = dcopy(gas, h->gas, 5 * N3 * sizeof(float), st);
-  if (part && r == SIM_OK) r = dcopy(part, h->s, 3 * N3 * sizeof(float), st);
-  if (part && r == SIM_OK) r = dcopy(part + 3 * N3, h->p, 3 * N3 * sizeof(float), st);
+  if (part && r == SIM_OK) r = part_join(part, h->s, h->p, h, st);
   if (star && r == SIM_OK) r = dcopy(star, h->star, N3 * sizeof(float), st);
   if (aux && r == SIM_OK) r = dcopy(aux, h->aux, N3 * sizeof(float), st);
-  if (events && r == SIM_OK) r = dcopy(events, h->events, ((N3 + 31) / 32) * sizeof(uint32_t), st);
+  if (events && r == SIM_OK) r = dcopy(events, h->events, words * sizeof(uint32_t), st);
   if (gravity && r == SIM_OK) r = dcopy(gravity, h->g, 3 * N3 * sizeof(float), st);
   if (step) *step = h->step;
   return fail(h, r);
@@ -1092,7 +1376,7 @@ sim_status sim_set_state(sim_t* h, const float* gas, const float* part, int32_t 
     set_error("sim_set_state: invalid arguments");
     return fail(h, SIM_EINVAL);
   }
-  const long long N3 = h->N3;
+  const long long N3 = h->N3 * h->B;
   cudaStream_t st = h->st;
   sim_status r = dcopy(h->init_gas, gas, 5 * N3 * sizeof(float), st);
   if (r == SIM_OK) r = dcopy(h->init_part, part, 6 * N3 * sizeof(float), st);
@@ -1121,20 +1405,225 @@ sim_status sim_schedule(const sim_t* h, int32_t i, double* out6) {
 
 sim_status sim_cfl(sim_t* h, double* cfl_out) {
   if (!h || !cfl_out) return SIM_EINVAL;
+  return fail(h, cfl_now(h, cfl_out));
+}
+
+}  // extern "C"
+
+namespace dh {
+
+// Largest CFL number over the instances for the next step (reads back, synchronises).
+static sim_status cfl_now(sim_t* h, double* cfl_out) {
   cudaStream_t st = h->st;
-  unsigned int bits = 0;
-  sim_status r = dzero(h->speed_bits, sizeof(unsigned int), st);
-  if (r == SIM_OK) r = launch_signal_speed(h->gas, (float)h->prm.gamma, h->N3, h->speed_bits, st);
-  if (r == SIM_OK && (cudaMemcpyAsync(&bits, h->speed_bits, sizeof(unsigned int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                      cudaStreamSynchronize(st) != cudaSuccess)) {
+  std::vector<unsigned int> bits(h->B, 0u);
+  DH_TRY(dzero(h->speed_bits, h->B * sizeof(unsigned int), st));
+  DH_TRY(launch_signal_speed(h->gas, (float)h->prm.gamma, h->N3, h->speed_bits, h->B, st));
+  if (cudaMemcpyAsync(bits.data(), h->speed_bits, h->B * sizeof(unsigned int),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
     set_error("sim_cfl: readback failed");
-    r = SIM_ECUDA;
+    return SIM_ECUDA;
   }
-  if (r != SIM_OK) return fail(h, r);
-  float v;
-  memcpy(&v, &bits, sizeof(v));
   const int i = h->step < h->prm.n_steps ? h->step : h->prm.n_steps - 1;
-  *cfl_out = (double)v * h->sched[i].dtau * h->inv_dx;
+  double c = 0.0;
+  for (int b = 0; b < h->B; ++b) {
+    float v;
+    memcpy(&v, &bits[b], sizeof(v));
+    const double cb = (double)v * h->scheds[b][i].dtau * h->inv_dx;
+    if (!(cb <= c)) c = cb;  // keeps a NaN
+  }
+  *cfl_out = c;
+  return SIM_OK;
+}
+
+}  // namespace dh
+
+// ===================================================================== groups of handles
+// Batches on grids of different sizes: one batched handle per size, captured together.
+// The group's graph forks one branch per member from a private capture stream, runs the
+// member's body on its branch stream, and joins the branches again, so the members' kernels
+// may overlap on the GPU; one graph launch replays the whole call.
+struct GroupEntry {
+  int kind = 0;
+  std::vector<uintptr_t> key;
+  std::vector<HostState> before, after;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
+
+struct sim_group_s {
+  std::vector<sim_t*> m;
+  cudaStream_t st = 0, cap = nullptr;
+  std::vector<cudaStream_t> br;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr, order = nullptr;
+  std::vector<GroupEntry> cache;
+};
+
+namespace dh {
+
+static void group_free(sim_group_t* g) {
+  for (GroupEntry& e : g->cache)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  for (cudaStream_t s : g->br)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : g->join)
+    if (e) cudaEventDestroy(e);
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->order) cudaEventDestroy(g->order);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+}
+
+// Replay the group's graph for (kind, key) from the members' current host states, or
+// capture it: body(k) enqueues member k's work on m[k]->st.
+template <class Body>
+static sim_status group_graph(sim_group_t* g, int kind, const std::vector<uintptr_t>& key,
+                              Body body) {
+  const size_t K = g->m.size();
+  std::vector<HostState> before;
+  for (sim_t* h : g->m) before.push_back(snapshot(h));
+  for (GroupEntry& e : g->cache) {
+    if (e.kind == kind && e.key == key && e.before == before) {
+      DH_CUDA_TRY(cudaGraphLaunch(e.exec, g->st));
+      for (size_t k = 0; k < K; ++k) restore(g->m[k], e.after[k]);
+      g_launches.fetch_add(e.launches, std::memory_order_relaxed);
+      return SIM_OK;
+    }
+  }
+  DH_CUDA_TRY(cudaEventRecord(g->order, g->st));
+  DH_CUDA_TRY(cudaStreamWaitEvent(g->cap, g->order, 0));
+  DH_CUDA_TRY(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+  const long long l0 = g_launches.load();
+  sim_status r = SIM_OK;
+  cudaError_t ce = cudaEventRecord(g->fork, g->cap);
+  for (size_t k = 0; k < K && ce == cudaSuccess; ++k) {
+    ce = cudaStreamWaitEvent(g->br[k], g->fork, 0);
+    if (ce != cudaSuccess) break;
+    cudaStream_t saved = g->m[k]->st;
+    g->m[k]->st = g->br[k];
+    if (r == SIM_OK) r = body(k);
+    g->m[k]->st = saved;
+    // every forked branch is joined back, also after a failure, so the capture can end
+    ce = cudaEventRecord(g->join[k], g->br[k]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(g->cap, g->join[k], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(g->cap, &graph);
+  if (r != SIM_OK || ce != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    for (size_t k = 0; k < K; ++k) restore(g->m[k], before[k]);
+    if (r == SIM_OK)
+      set_error("group capture failed: %s",
+                cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    return r != SIM_OK ? r : SIM_ECUDA;
+  }
+  GroupEntry e;
+  e.kind = kind;
+  e.key = key;
+  e.before = before;
+  for (sim_t* h : g->m) e.after.push_back(snapshot(h));
+  e.launches = g_launches.load() - l0;
+  ce = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce == cudaSuccess) ce = cudaGraphLaunch(e.exec, g->st);
+  if (ce != cudaSuccess) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    for (size_t k = 0; k < K; ++k) restore(g->m[k], before[k]);
+    set_error("group graph instantiate/launch failed: %s", cudaGetErrorString(ce));
+    return SIM_ECUDA;
+  }
+  g->cache.push_back(std::move(e));
+  return SIM_OK;
+}
+
+}  // namespace dh
+
+extern "C" {
+
+sim_status sim_group_create(sim_t* const* members, int32_t count, void* stream,
+                            sim_group_t** out) {
+  if (!out || !members || count < 1) {
+    set_error("sim_group_create: invalid arguments");
+    return SIM_EINVAL;
+  }
+  *out = nullptr;
+  for (int k = 0; k < count; ++k)
+    for (int j = 0; j < k; ++j)
+      if (!members[k] || members[k] == members[j]) {
+        set_error("sim_group_create: null or repeated member %d", k);
+        return SIM_EINVAL;
+      }
+  sim_group_t* g = new sim_group_t();
+  g->m.assign(members, members + count);
+  g->st = (cudaStream_t)stream;
+  bool ok = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->order, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < count && ok; ++k) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) g->br.push_back(s);
+    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) g->join.push_back(e);
+  }
+  if (!ok) {
+    set_error("sim_group_create: stream or event creation failed");
+    group_free(g);
+    return SIM_ECUDA;
+  }
+  *out = g;
+  return SIM_OK;
+}
+
+void sim_group_destroy(sim_group_t* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->st);
+  group_free(g);
+}
+
+sim_status sim_group_run(sim_group_t* g) {
+  if (!g) return SIM_EINVAL;
+  for (sim_t* h : g->m) {
+    if (h->prm.cfl_max > 0) {
+      set_error("sim_group_run: members with cfl_max > 0 read back every step");
+      return fail(h, SIM_EINVAL);
+    }
+    DH_TRY(fail(h, run_prepare(h, h->prm.n_steps - h->step)));
+  }
+  std::vector<uintptr_t> key;
+  for (sim_t* h : g->m) key.push_back((uintptr_t)(h->prm.n_steps - h->step));
+  return group_graph(g, 1, key, [&](size_t k) {
+    sim_t* h = g->m[k];
+    return fail(h, run_body(h, h->prm.n_steps - h->step));
+  });
+}
+
+sim_status sim_group_run_adjoint(sim_group_t* g, const float* const* dL_dgas,
+                                 double* const* dL_dparams) {
+  if (!g || !dL_dparams) {
+    set_error("sim_group_run_adjoint: null arguments");
+    return SIM_EINVAL;
+  }
+  const size_t K = g->m.size();
+  for (size_t k = 0; k < K; ++k)
+    DH_TRY(fail(g->m[k], run_adjoint_prepare(g->m[k], nullptr, dL_dparams[k])));
+  std::vector<uintptr_t> key;
+  for (size_t k = 0; k < K; ++k) {
+    key.push_back((uintptr_t)(dL_dgas ? dL_dgas[k] : nullptr));
+    key.push_back((uintptr_t)dL_dparams[k]);
+  }
+  return group_graph(g, 2, key, [&](size_t k) {
+    sim_t* h = g->m[k];
+    return fail(h, run_adjoint_body(h, dL_dgas ? dL_dgas[k] : nullptr, nullptr, nullptr,
+                                    dL_dparams[k]));
+  });
+}
+
+sim_status sim_group_reset(sim_group_t* g) {
+  if (!g) return SIM_EINVAL;
+  for (sim_t* h : g->m) DH_TRY(sim_reset(h));
   return SIM_OK;
 }
 

@@ -81,10 +81,17 @@ __device__ __forceinline__ void gumbel_pair(const SubgridConst& c, long long i, 
   g1 = -logf(-logf(uniform_from_word(w.y)));
 }
 
+// grid (cdiv(N3, 256), B); instance b uses constants ca.at(b)
 __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__ out,
-                               SubgridConst c, float* __restrict__ zhat,
+                               SubArg ca, float* __restrict__ zhat,
                                uint32_t* __restrict__ events, long long N3) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  in += (size_t)b * 5 * N3;
+  out += (size_t)b * 5 * N3;
+  if (zhat) zhat += (size_t)b * N3;
+  if (events) events += (size_t)b * ((N3 + 31) / 32);
+  const SubgridConst c = ca.at(b);
   bool ev = false;
   if (i < N3) {
     float u[5];
@@ -110,9 +117,14 @@ __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__
 }
 
 __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restrict__ lam,
-                                   SubgridConst c, double* __restrict__ dpar,
-                                   double* __restrict__ dfb, long long N3) {
+                                   SubArg ca, DPart dpar_b, DPart dfb_b, long long N3) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  in += (size_t)b * 5 * N3;
+  lam += (size_t)b * 5 * N3;
+  const SubgridConst c = ca.at(b);
+  double* dpar = dpar_b.at(b);
+  double* dfb = dfb_b.at(b);
   float a_dc = 0, a_pi = 0, a_e0 = 0, a_t0 = 0, a_g = 0, a_fb = 0;
   if (i < N3) {
     float u[5], l[5];
@@ -177,22 +189,26 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
   if (dfb) block_sum_atomic(a_fb, dfb);
 }
 
-sim_status launch_subgrid(const float* in, float* out, const SubgridConst& c, float* zhat,
-                          uint32_t* events, long long N3, cudaStream_t st) {
-  subgrid_kernel<<<cdiv(N3, 256), 256, 0, st>>>(in, out, c, zhat, events, N3);
+sim_status launch_subgrid(const float* in, float* out, SubArg c, float* zhat,
+                          uint32_t* events, long long N3, int B, cudaStream_t st) {
+  subgrid_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, out, c, zhat, events, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
-sim_status launch_subgrid_adjoint(const float* in, float* lam, const SubgridConst& c,
-                                  double* dpar, double* dfb, long long N3, cudaStream_t st) {
-  subgrid_adj_kernel<<<cdiv(N3, 256), 256, 0, st>>>(in, lam, c, dpar, dfb, N3);
+sim_status launch_subgrid_adjoint(const float* in, float* lam, SubArg c, DPart dpar, DPart dfb,
+                                  long long N3, int B, cudaStream_t st) {
+  subgrid_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, lam, c, dpar, dfb, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
+// grid (blocks, B): out[b] = float bits of instance b's maximum signal speed
 __global__ void signal_speed_kernel(const float* __restrict__ u, float gam, long long N3,
                                     unsigned int* __restrict__ out) {
+  const int b = blockIdx.y;
+  u += (size_t)b * 5 * N3;
+  out += b;
   float vmax = 0.0f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N3;
        i += (long long)gridDim.x * blockDim.x) {
@@ -210,10 +226,11 @@ __global__ void signal_speed_kernel(const float* __restrict__ u, float gam, long
 }
 
 sim_status launch_signal_speed(const float* gas, float gamma, long long N3,
-                               unsigned int* out_bits, cudaStream_t st) {
+                               unsigned int* out_bits, int B, cudaStream_t st) {
   int blocks = cdiv(N3, 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  signal_speed_kernel<<<blocks, 256, 0, st>>>(gas, gamma, N3, out_bits);
+  const int cap = cdiv(152 * 8, B);
+  if (blocks > cap) blocks = cap;
+  signal_speed_kernel<<<dim3(blocks, B), 256, 0, st>>>(gas, gamma, N3, out_bits);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -230,7 +247,7 @@ extern "C" sim_status sim_subgrid(float* gas, int32_t n, double a, const sim_par
     return SIM_EINVAL;
   }
   const long long N3 = (long long)n * n * n;
-  return launch_subgrid(gas, gas, make_subgrid_const(*p, a, step), zhat, events, N3,
+  return launch_subgrid(gas, gas, subarg(make_subgrid_const(*p, a, step)), zhat, events, N3, 1,
                         (cudaStream_t)stream);
 }
 
@@ -243,8 +260,8 @@ extern "C" sim_status sim_subgrid_adjoint(const float* gas_in, float* lam, int32
     return SIM_EINVAL;
   }
   const long long N3 = (long long)n * n * n;
-  return launch_subgrid_adjoint(gas_in, lam, make_subgrid_const(*p, a, step), dparams, dfb, N3,
-                                (cudaStream_t)stream);
+  return launch_subgrid_adjoint(gas_in, lam, subarg(make_subgrid_const(*p, a, step)),
+                                dpart(dparams), dpart(dfb), N3, 1, (cudaStream_t)stream);
 }
 
 __global__ void philox_kernel(uint32_t k0, uint32_t k1, uint32_t step, uint32_t inst,

@@ -19,16 +19,26 @@ struct SubgridConst {
 };
 
 SubgridConst make_subgrid_const(const sim_params& p, double a, int step);
+
+// Constants of a batched launch: one set for all instances, or a device array per instance.
+struct SubArg {
+  SubgridConst v;
+  const SubgridConst* p;
+  __device__ __forceinline__ SubgridConst at(int b) const { return p ? p[b] : v; }
+};
+inline SubArg subarg(const SubgridConst& v) { return SubArg{v, nullptr}; }
+inline SubArg subarg(const SubgridConst* p) { return SubArg{SubgridConst{}, p}; }
 double temperature_per_energy(double gamma, double mu);
 
+// B instances one after another (as the PM launchers).
 // out = subgrid(in) (may alias); zhat (n^3) and events (ceil(n^3/32) words) may be NULL
-sim_status launch_subgrid(const float* in, float* out, const SubgridConst& c, float* zhat,
-                          uint32_t* events, long long N3, cudaStream_t st);
+sim_status launch_subgrid(const float* in, float* out, SubArg c, float* zhat,
+                          uint32_t* events, long long N3, int B, cudaStream_t st);
 // lam (5 n^3) in/out through the update at `in`; dpar[SIM_P_*] and dfb accumulated
-sim_status launch_subgrid_adjoint(const float* in, float* lam, const SubgridConst& c,
-                                  double* dpar, double* dfb, long long N3, cudaStream_t st);
-// max over cells and directions of |v_d| + c_s  (float bits in *out_bits, atomicMax)
+sim_status launch_subgrid_adjoint(const float* in, float* lam, SubArg c, DPart dpar, DPart dfb,
+                                  long long N3, int B, cudaStream_t st);
+// max over cells and directions of |v_d| + c_s  (float bits in out_bits[b], atomicMax)
 sim_status launch_signal_speed(const float* gas, float gamma, long long N3,
-                               unsigned int* out_bits, cudaStream_t st);
+                               unsigned int* out_bits, int B, cudaStream_t st);
 
 }  // namespace dh

@@ -152,16 +152,22 @@ def test_step_adjoint_matches_oracle_reverse_mode(dh, n, sub):
 
     X = (st0["gas"].double().cpu(), st0["s"].double().cpu(), st0["p"].double().cpu())
     gU, gs, gp, gom = oracle_grad(*X)
-    # The reverse mode of a step has kinks (limiter gates, CIC cell edges): moving the input
-    # by float32 round-off flips a few of them and moves the float64 gradient itself. That
-    # conditioning floor is measured here (inputs perturbed by 6e-8 relative) and the GPU
-    # must agree within max(1e-3, 3 x floor); on small grids the floor is ~1e-5.
+    # The reverse mode of a step has kinks (limiter gates, CIC cell edges). The float32
+    # forward rounds every intermediate state (kicked gas, half step, fluxes), and where a
+    # flux difference is near zero that flips a gate, so the two gradients differ in a few
+    # isolated cells. The oracle's own gradient moves as much when its input moves by 1e-6
+    # relative: that floor is measured here and the GPU must agree within
+    # max(1e-3, 3 x floor) overall and within 1e-4 outside the 0.1 % worst cells.
     gen = torch.Generator().manual_seed(0)
-    Xp = [x * (1 + 6e-8 * torch.randn(x.shape, generator=gen, dtype=DT)) for x in X]
+    Xp = [x * (1 + 1e-6 * torch.randn(x.shape, generator=gen, dtype=DT)) for x in X]
     fU, fs, fp, _ = oracle_grad(*Xp)
     for k in range(5):
-        bar = max(1e-3, 3 * rel_l2(fU[k], gU[k]))
-        assert rel_l2(lam_gas[k], gU[k]) < bar, (k, rel_l2(lam_gas[k], gU[k]), bar)
+        err = rel_l2(lam_gas[k], gU[k])
+        assert err < max(1e-3, 3 * rel_l2(fU[k], gU[k])), (k, err, rel_l2(fU[k], gU[k]))
+        d = (lam_gas[k].double().cpu() - gU[k]).flatten()
+        keep = torch.ones_like(d, dtype=torch.bool)
+        keep[torch.topk(d.abs(), max(1, d.numel() // 1000)).indices] = False
+        assert d[keep].norm().item() < 1e-4 * gU[k].norm().item(), (k, "outside worst cells")
     assert rel_l2(lam_part[:3], gs) < max(1e-3, 3 * rel_l2(fs, gs))
     assert rel_l2(lam_part[3:], gp) < max(1e-3, 3 * rel_l2(fp, gp))
     assert abs(dpar[0].item() - gom.item()) < 1e-3 * abs(gom.item())
