@@ -22,6 +22,9 @@ Modules and the passages they follow:
 * ``ics``        -- Gaussian realisation and Zel'dovich displacement of DM and gas (Sec. 2.1).
 * ``spectra``    -- binned power spectrum and cross-correlation coefficient r_c (Sec. 3.1, 3.2).
 * ``sim``        -- one full time step and a run, parameters, losses.
+* ``closure``    -- the learned per-step correction (Sec. 4, solver-in-the-loop): periodic
+                    3x3x3 convolutions with GELU in bfloat16-quantised float64, its loss and
+                    Adam update, and the coarse/fine pairing operators of its training runs.
 
 Every function here is pinned by a ``-m "not gpu"`` test against something other than
 itself (closed forms, textbook solutions, published constants, invariants, finite
