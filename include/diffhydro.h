@@ -288,6 +288,81 @@ sim_status sim_schedule(const sim_t* h, int32_t i, double* out6);
  * current state and the next step's dtau (Eq. dt). Synchronises the stream. */
 sim_status sim_cfl(sim_t* h, double* cfl_out);
 
+/* ------------------------------------------------------------------ learned closure
+ * Solver-in-the-loop refinement (Sec. 4 lists it among the uses of a differentiable
+ * solver): after every step the five gas fields get a residual correction
+ *   u <- u + s * NN((u - mu) / sigma)        (mu, sigma, s: one value per field)
+ * from a network of four periodic 3x3x3 convolutions 5 -> 16 -> 16 -> 16 -> 5 with GELU
+ * between them, bfloat16 weights and activations, float32 accumulation on the tensor
+ * cores. conv(h, W)[v, co] = sum over taps t and input channels ci of
+ * h[v + off(t), ci] W[t, ci, co], tap t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1).
+ * Weight vector (host float32, SIM_CLOSURE_NWEIGHTS values): for layers (Cin, Cout) =
+ * (5, 16), (16, 16), (16, 16), (16, 5): W[t][ci][co] (co fastest), then b[co].
+ * Gas arrays are B x 5 n^3 as everywhere else. */
+#define SIM_CLOSURE_NWEIGHTS 18197
+
+typedef struct sim_closure_s sim_closure_t;
+
+/* weights: host vector or NULL (all zero: the correction is the identity). */
+sim_status sim_closure_create(const float* weights, void* stream, sim_closure_t** out);
+void sim_closure_destroy(sim_closure_t* c);
+
+/* Per-field normalisation: host arrays of 5 (sigma, scale > 0). Default 0 / 1 / 1. */
+sim_status sim_closure_set_norm(sim_closure_t* c, const float* mu, const float* sigma,
+                                const float* scale);
+
+/* Copy the weights out / in (host vectors). Setting them clears the optimiser state;
+ * both synchronise the closure's stream. */
+sim_status sim_closure_get_weights(sim_closure_t* c, float* host_out);
+sim_status sim_closure_set_weights(sim_closure_t* c, const float* host_in);
+
+/* y = NN((gas - mu) / sigma) (device, B x 5 n^3, normalised units; gas unchanged). */
+sim_status sim_closure_forward(sim_closure_t* c, const float* gas, int32_t n, int32_t B,
+                               float* y);
+
+/* gas += s * NN((gas - mu) / sigma) in place. */
+sim_status sim_closure_apply(sim_closure_t* c, float* gas, int32_t n, int32_t B);
+
+/* Loss L = mean over fields, cells and instances of (y - (target - gas) / s)^2 and its
+ * gradient with respect to the weights (host vector, SIM_CLOSURE_NWEIGHTS), for the
+ * training pair (gas before the correction, target state). Synchronises. */
+sim_status sim_closure_gradient(sim_closure_t* c, const float* gas, const float* target,
+                                int32_t n, int32_t B, double* loss_host, float* grad_host);
+
+/* One training step on that loss: gradient, then Adam (beta 0.9 / 0.999, eps 1e-8, bias
+ * corrected) with learning rate lr. loss_out (device double, may be NULL) receives the
+ * loss before the update. Stream-ordered, no synchronisation. */
+sim_status sim_closure_train_step(sim_closure_t* c, const float* gas, const float* target,
+                                  int32_t n, int32_t B, double lr, double* loss_out);
+
+/* Synchronise and report a timed-out tensor-core wait of an earlier call (SIM_ETIMEOUT). */
+sim_status sim_closure_status(sim_closure_t* c);
+
+/* Apply `c` at the end of every step of the handle (sim_step, sim_run, groups), on the
+ * handle's stream; NULL removes it (the plain solver). Prepares the closure's workspace for
+ * the handle's grid. While a closure is set the adjoint entry points return SIM_ENOTIMPL.
+ * The closure must outlive its use by the handle. */
+sim_status sim_set_closure(sim_t* h, sim_closure_t* c);
+
+/* Training pairs of the closure: coarse runs against runs twice as fine.
+ * sim_refine_noise: w_f (n_f^3) = scale * band-limited interpolation of w_c (n_c^3): the
+ *   coarse Fourier modes, with an even n_c's Nyquist modes split equally between +k and
+ *   -k, the finer modes zero. With scale = C_coarse / C_fine (sim_ic_amplitude) and the
+ *   fine handle's kc_frac halved, the fine run's linear field equals the coarse one.
+ * sim_restrict_gas: coarse cell j = tent-weighted (1/4, 1/2, 1/4 per axis) mean of the
+ *   fine cells around fine cell 2j; B x 5 fields.
+ * sim_restrict_particles: the fine particle at lattice site 2q is coarse particle q;
+ *   B x 6 n^3 (s then p). */
+sim_status sim_refine_noise(const float* w_c, int32_t n_c, float* w_f, int32_t n_f,
+                            double scale, void* stream);
+sim_status sim_restrict_gas(const float* gas_f, int32_t n_f, float* gas_c, int32_t B,
+                            void* stream);
+sim_status sim_restrict_particles(const float* part_f, int32_t n_f, float* part_c, int32_t B,
+                                  void* stream);
+
+/* Amplitude C of instance b's initial conditions (delta_k = C sqrt(P(k)) w_k / n^3), host. */
+sim_status sim_ic_amplitude(const sim_t* h, int32_t b, double* C);
+
 /* ------------------------------------------------------------------ single kernels */
 
 /* One relaxing-TVD sweep along axis (0 = x, 1 = y, 2 = z) with nu = dtau/dx:

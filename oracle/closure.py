@@ -115,6 +115,22 @@ def network(x, weights, quantise=True):
     return h
 
 
+def network_window(xwin, weights, quantise=True):
+    """The network's output at the centre of a (2R + 1)^3 window of the input, R = 4 (one
+    voxel per layer), with unpadded convolutions: xwin [5, 9, 9, 9] -> y [5] (float64).
+    Equal to network() at that voxel for any periodic input (pinned in the tests); used to
+    check single voxels of large grids."""
+    q = bf16 if quantise else (lambda a: a)
+    h = q(torch.as_tensor(xwin, dtype=_DT))
+    layers = unpack(weights) if not isinstance(weights, list) else weights
+    for l, (W, b) in enumerate(layers):
+        ci, co = W.shape[1], W.shape[2]
+        k = q(W).reshape(3, 3, 3, ci, co).permute(4, 3, 0, 1, 2).contiguous()
+        z = F.conv3d(h.unsqueeze(0), k)[0] + b[:, None, None, None]
+        h = q(gelu(z)) if l < 3 else z
+    return h[:, 0, 0, 0]
+
+
 def apply(gas, weights, mu, sigma, scale, quantise=True):
     """u' = u + s * NN((u - mu) / sigma) for gas [5, n, n, n]."""
     mu = torch.as_tensor(mu, dtype=_DT)[:, None, None, None]

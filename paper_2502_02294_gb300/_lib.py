@@ -19,6 +19,7 @@ STATUS_NAMES = ["SIM_OK", "SIM_EINVAL", "SIM_ENOMEM", "SIM_ECUDA", "SIM_ECFL", "
 P_OMEGA_M, P_SIGMA8, P_DELTA_C, P_PI0, P_E0, P_T0_UV, P_GAMMA_UV, NPARAMS = range(8)
 KT_SWEEP, KT_SWEEP_ADJOINT, KT_N = range(3)
 SWEEP_DEFAULT, SWEEP_TILE, SWEEP_MARCH32, SWEEP_MARCH16 = range(4)
+CLOSURE_NWEIGHTS = 18197
 PARAM_NAMES = ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"]
 
 
@@ -60,6 +61,21 @@ SIGNATURES = {
     "sim_set_sweep_variants": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sim_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sim_destroy": (None, [_P]),
+    "sim_closure_create": (ctypes.c_int, [_P, _P, ctypes.POINTER(_P)]),
+    "sim_closure_destroy": (None, [_P]),
+    "sim_closure_set_norm": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sim_closure_get_weights": (ctypes.c_int, [_P, _P]),
+    "sim_closure_set_weights": (ctypes.c_int, [_P, _P]),
+    "sim_closure_forward": (ctypes.c_int, [_P, _P, _I32, _I32, _P]),
+    "sim_closure_apply": (ctypes.c_int, [_P, _P, _I32, _I32]),
+    "sim_closure_gradient": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _P, _P]),
+    "sim_closure_train_step": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _D, _P]),
+    "sim_closure_status": (ctypes.c_int, [_P]),
+    "sim_set_closure": (ctypes.c_int, [_P, _P]),
+    "sim_refine_noise": (ctypes.c_int, [_P, _I32, _P, _I32, _D, _P]),
+    "sim_restrict_gas": (ctypes.c_int, [_P, _I32, _P, _I32, _P]),
+    "sim_restrict_particles": (ctypes.c_int, [_P, _I32, _P, _I32, _P]),
+    "sim_ic_amplitude": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_D)]),
     "sim_group_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _P, ctypes.POINTER(_P)]),
     "sim_group_run": (ctypes.c_int, [_P]),
     "sim_group_run_adjoint": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),

@@ -9,8 +9,10 @@ import ctypes
 
 import torch
 
-from ._lib import (KT_N, KT_SWEEP, KT_SWEEP_ADJOINT, NPARAMS, SimParams, check,
-                   default_params, lib)
+import numpy as np
+
+from ._lib import (CLOSURE_NWEIGHTS, KT_N, KT_SWEEP, KT_SWEEP_ADJOINT, NPARAMS, SimParams,
+                   check, default_params, lib)
 
 F32, F64, U32 = torch.float32, torch.float64, torch.int32
 
@@ -262,6 +264,17 @@ class Simulation:
         self._check(lib.sim_cfl(self.h, ctypes.byref(c)), "sim_cfl")
         return c.value
 
+    def set_closure(self, closure=None):
+        """Apply a learned closure after every step (None: the plain solver)."""
+        self._closure = closure
+        self._check(lib.sim_set_closure(self.h, closure.h if closure is not None else None),
+                    "sim_set_closure")
+
+    def ic_amplitude(self, b: int = 0) -> float:
+        c = ctypes.c_double()
+        check(lib.sim_ic_amplitude(self.h, b, ctypes.byref(c)), "sim_ic_amplitude", self.h)
+        return c.value
+
     def set_graphs(self, on: bool = True):
         self._check(lib.sim_set_graphs(self.h, int(on)), "sim_set_graphs")
 
@@ -288,6 +301,119 @@ class Simulation:
         self._check(lib.sim_kernel_times(self.h, ms, cnt, int(reset)), "sim_kernel_times")
         return {"sweep": (ms[KT_SWEEP], cnt[KT_SWEEP]),
                 "sweep_adjoint": (ms[KT_SWEEP_ADJOINT], cnt[KT_SWEEP_ADJOINT])}
+
+
+def _host_f32(a, count, name):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(-1))
+    if a.size != count:
+        raise ValueError(f"{name}: expected {count} values, got {a.size}")
+    return a
+
+
+class Closure:
+    """Learned per-step correction u <- u + s NN((u - mu) / sigma) (sim_closure_*).
+    Weights are a flat float32 vector of CLOSURE_NWEIGHTS values (layout in diffhydro.h)."""
+
+    def __init__(self, weights=None):
+        self._stream = torch.cuda.current_stream()
+        w = None if weights is None else _host_f32(weights, CLOSURE_NWEIGHTS, "weights")
+        h = ctypes.c_void_p()
+        check(lib.sim_closure_create(w.ctypes.data if w is not None else None,
+                                     ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h)),
+              "sim_closure_create")
+        self.h = h
+
+    def set_norm(self, mu, sigma, scale):
+        m, sg, sc = (_host_f32(v, 5, nm) for v, nm in ((mu, "mu"), (sigma, "sigma"), (scale, "scale")))
+        check(lib.sim_closure_set_norm(self.h, m.ctypes.data, sg.ctypes.data, sc.ctypes.data),
+              "sim_closure_set_norm")
+        self.norm = (m.tolist(), sg.tolist(), sc.tolist())
+
+    def weights(self):
+        out = np.empty(CLOSURE_NWEIGHTS, dtype=np.float32)
+        check(lib.sim_closure_get_weights(self.h, out.ctypes.data), "sim_closure_get_weights")
+        return out
+
+    def set_weights(self, w):
+        w = _host_f32(w, CLOSURE_NWEIGHTS, "weights")
+        check(lib.sim_closure_set_weights(self.h, w.ctypes.data), "sim_closure_set_weights")
+
+    @staticmethod
+    def _dims(gas):
+        n = gas.shape[-1]
+        B = gas.numel() // (5 * n ** 3)
+        _chk(gas, F32, 5 * B * n ** 3, "gas")
+        return n, B
+
+    def forward(self, gas):
+        n, B = self._dims(gas)
+        y = torch.empty_like(gas)
+        check(lib.sim_closure_forward(self.h, _ptr(gas), n, B, _ptr(y)), "sim_closure_forward")
+        return y
+
+    def apply(self, gas):
+        n, B = self._dims(gas)
+        check(lib.sim_closure_apply(self.h, _ptr(gas), n, B), "sim_closure_apply")
+        return gas
+
+    def gradient(self, gas, target):
+        n, B = self._dims(gas)
+        _chk(target, F32, 5 * B * n ** 3, "target")
+        loss = ctypes.c_double()
+        g = np.empty(CLOSURE_NWEIGHTS, dtype=np.float32)
+        check(lib.sim_closure_gradient(self.h, _ptr(gas), _ptr(target), n, B, ctypes.byref(loss),
+                                       g.ctypes.data), "sim_closure_gradient")
+        return loss.value, g
+
+    def train_step(self, gas, target, lr: float, loss_out=None):
+        n, B = self._dims(gas)
+        _chk(target, F32, 5 * B * n ** 3, "target")
+        check(lib.sim_closure_train_step(self.h, _ptr(gas), _ptr(target), n, B, lr,
+                                         _ptr(loss_out)), "sim_closure_train_step")
+
+    def status(self):
+        check(lib.sim_closure_status(self.h), "sim_closure_status")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sim_closure_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def refine_noise(w_c, n_f: int, scale: float):
+    """Band-limited interpolation of coarse white noise onto an n_f^3 grid, times scale."""
+    n_c = w_c.shape[-1]
+    _chk(w_c, F32, n_c ** 3, "w_c")
+    out = torch.empty(n_f, n_f, n_f, dtype=F32, device=w_c.device)
+    check(lib.sim_refine_noise(_ptr(w_c), n_c, _ptr(out), n_f, scale, _stream()), "sim_refine_noise")
+    return out
+
+
+def restrict_gas(gas_f):
+    """Fine gas [(B,) 5, 2n, 2n, 2n] -> coarse [(B,) 5, n, n, n] (tent weights)."""
+    n_f = gas_f.shape[-1]
+    B = gas_f.numel() // (5 * n_f ** 3)
+    _chk(gas_f, F32, 5 * B * n_f ** 3, "gas_f")
+    nc = n_f // 2
+    out = torch.empty(gas_f.shape[:-3] + (nc, nc, nc), dtype=F32, device=gas_f.device)
+    check(lib.sim_restrict_gas(_ptr(gas_f), n_f, _ptr(out), B, _stream()), "sim_restrict_gas")
+    return out
+
+
+def restrict_particles(part_f, n_f: int):
+    """Fine particles [(B,) 6, n_f^3] -> coarse [(B,) 6, (n_f/2)^3] (even lattice sites)."""
+    B = part_f.numel() // (6 * n_f ** 3)
+    _chk(part_f, F32, 6 * B * n_f ** 3, "part_f")
+    out = torch.empty(part_f.shape[:-1] + ((n_f // 2) ** 3,), dtype=F32, device=part_f.device)
+    check(lib.sim_restrict_particles(_ptr(part_f), n_f, _ptr(out), B, _stream()),
+          "sim_restrict_particles")
+    return out
 
 
 class Group:

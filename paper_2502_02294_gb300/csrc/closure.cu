@@ -1,0 +1,969 @@
+// Learned closure (Sec. 4 of arXiv 2502.02294 lists solver-in-the-loop refinement: a
+// network trained against better-resolved runs corrects the coarse solution every step).
+//
+// Network: four periodic 3x3x3 convolutions 5 -> 16 -> 16 -> 16 -> 5, GELU between them,
+// bfloat16 weights and activations, float32 accumulation, applied as a residual update of
+// the five gas fields on normalised inputs: u <- u + s * NN((u - mu) / sigma).
+//
+// Every convolution runs as an implicit GEMM on the tensor cores (tcgen05, M = 128 voxels,
+// N = 16 output channels, K = 16 input channels per tap, 27 taps accumulated in TMEM). All
+// activations are channels-last bfloat16 with 16 channels (the 5 gas fields are padded with
+// zeros), so every layer is the same 16 -> 16 kernel with zero-padded weights. A CTA stages
+// the input lines around its output lines in shared memory with one padding column on each
+// side (line pitch P = n + 2), in the no-swizzle K-major operand layout (two planes of 8
+// channels, 16 bytes per position). With a uniform 16-byte row pitch, the operand of tap
+// (dx, dy, dz) for a tile of 128 consecutive positions is the same tile shifted by
+// ((dz (L + 2) + dy) P + dx) positions: 27 descriptors, no gather. Positions that fall on a
+// padding column produce results that are discarded.
+//
+// Backward: the gradient with respect to a layer's input is the same convolution with the
+// taps mirrored and each tap's matrix transposed (same kernel, other weight packing), its
+// epilogue multiplied by GELU' of the previous layer's pre-activation. The weight gradient
+// (a reduction over voxels of 27 rank-1 updates of 16 x 16) runs on the CUDA cores.
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "closure.cuh"
+#include "pm.cuh"
+#include "umma.cuh"
+
+namespace dh {
+
+typedef __nv_bfloat16 bf16;
+constexpr int CH = 16;                 // channels of every activation
+constexpr int NL = 4;                  // layers
+constexpr int WL = 27 * CH * CH;       // padded weights of one layer [tap][ci][co]
+constexpr int NPAD = NL * WL + NL * CH;  // padded parameters: weights, then biases [l][co]
+constexpr int LAYER_CIN[NL] = {5, 16, 16, 16};
+constexpr int LAYER_COUT[NL] = {16, 16, 16, 5};
+constexpr int SLK_BEFORE = 8, SLK_AFTER = 136;  // slack positions around the staged region
+constexpr int PACK = 27 * 512 / 2;              // bf16 elements of one packed layer
+
+// ------------------------------------------------------------------ geometry
+struct ConvGeom {
+  int n, P, L, T, tpl, contig, pos_total, ncols;
+  size_t smem;
+};
+
+static size_t conv_smem(int L, int P) {
+  const int pos_total = SLK_BEFORE + 3 * (L + 2) * P + SLK_AFTER;
+  return (size_t)2 * pos_total * 16 + 27 * 512 + 16;
+}
+
+// Lines per CTA and tiles: n >= 128 keeps each 128-row tile inside one line
+// (ceil(n/128) tiles per line); smaller grids let tiles run across consecutive padded
+// lines ("contiguous" rows) and choose the line count with the fewest tiles per plane.
+static ConvGeom conv_geom(int n) {
+  ConvGeom g;
+  g.n = n;
+  g.P = n + 2;
+  const size_t limit = 112 * 1024;
+  if (n >= 128) {
+    g.contig = 0;
+    g.tpl = (n + 127) / 128;
+    g.L = conv_smem(2, g.P) <= limit ? 2 : 1;
+    g.T = g.L * g.tpl;
+  } else {
+    g.contig = 1;
+    g.tpl = 0;
+    int bestL = 1, bestCost = 1 << 30;
+    size_t bestSmem = 0;
+    for (int L = 1; L <= n; ++L) {
+      const int T = cdiv((long long)L * g.P, 128);
+      if (T > 8) break;
+      const size_t sm = conv_smem(L, g.P);
+      if (sm > limit) break;
+      const int cost = cdiv(n, L) * T;
+      if (cost < bestCost || (cost == bestCost && sm < bestSmem)) {
+        bestCost = cost;
+        bestL = L;
+        bestSmem = sm;
+      }
+    }
+    g.L = bestL;
+    g.T = cdiv((long long)bestL * g.P, 128);
+  }
+  g.pos_total = SLK_BEFORE + 3 * (g.L + 2) * g.P + SLK_AFTER;
+  g.smem = conv_smem(g.L, g.P);
+  int nc = 32;
+  while (nc < 16 * g.T) nc <<= 1;
+  g.ncols = nc;
+  return g;
+}
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+
+// d GELU / dz = Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+         z * 0.3989422804014327f * __expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
+}
+
+__device__ __forceinline__ void store_bf16x16(bf16* dst, const float v[16]) {
+  uint32_t w[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    w[j] = *reinterpret_cast<const uint32_t*>(&p);
+  }
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+struct F5 {
+  float v[5];
+};
+
+// ------------------------------------------------------------------ convolution
+enum { CONV_HIDDEN = 0, CONV_OUT_Y = 1, CONV_OUT_APPLY = 2, CONV_BWD = 3 };
+
+struct ConvArgs {
+  const bf16* in;      // [B][n^3][16]
+  const bf16* w;       // packed [27][2][16 rows][8]: row = output channel, K = input channel
+  const float* bias;   // [16] (forward) or NULL
+  int n, P, L, T, tpl, contig, pos_total, ncols;
+  bf16* out;           // HIDDEN / BWD: [B][n^3][16]
+  float* zout;         // HIDDEN: pre-activation [B][n^3][16] or NULL
+  const float* zprev;  // BWD: pre-activation whose GELU' multiplies the result
+  float* y;            // OUT_Y: [B][5][n^3]
+  float* gas;          // OUT_APPLY: [B][5][n^3], += scale * y
+  F5 scale;
+  int* err;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128) conv3_kernel(ConvArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int n = a.n, P = a.P, L = a.L;
+  const long long N3 = (long long)n * n * n;
+  const int b = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * L;
+  const int tid = threadIdx.x;
+  const int plane_bytes = a.pos_total * 16;
+  uint8_t* sa = smem;                         // two planes of pos_total x 16 bytes
+  uint8_t* sw = smem + 2 * plane_bytes;       // 27 x 512 bytes of packed weights
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sw + 27 * 512);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const bf16* in = a.in + (size_t)b * N3 * CH;
+
+  // 1. stage 3 planes x (L + 2) lines x P positions (periodic) with asynchronous 16-byte
+  //    copies (every copy of the CTA in flight at once), zero the slack
+  const int nreg = 3 * (L + 2) * P;
+  const uint32_t sa0 = smem_u32(sa) + SLK_BEFORE * 16;
+  for (int pos = tid; pos < nreg; pos += 128) {
+    const int pz = pos / ((L + 2) * P);
+    const int rem = pos - pz * (L + 2) * P;
+    const int ly = rem / P, px = rem - ly * P;
+    const int gx = wrapi(px - 1, n), gy = wrapi(y0 - 1 + ly, n), gz = wrapi(z - 1 + pz, n);
+    const bf16* src = in + (((size_t)gz * n + gy) * n + gx) * CH;
+    const uint32_t d = sa0 + (uint32_t)pos * 16u;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + (uint32_t)plane_bytes),
+                 "l"(src + 8) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int i = tid; i < SLK_BEFORE + SLK_AFTER; i += 128) {
+    const int slot = i < SLK_BEFORE ? i : SLK_BEFORE + nreg + (i - SLK_BEFORE);
+    *reinterpret_cast<uint4*>(sa + (size_t)slot * 16) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sa + plane_bytes + (size_t)slot * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int i = tid; i < 27 * 512 / 16; i += 128)
+    reinterpret_cast<uint4*>(sw)[i] = __ldg(reinterpret_cast<const uint4*>(a.w) + i);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (tid == 0) mbar_init(mbar, 1);
+  fence_async_smem();
+  __syncthreads();
+  if (tid < 32) tmem_alloc_warp(tslot, (uint32_t)a.ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  // 2. one thread issues T tiles x 27 taps
+  if (tid == 0) {
+    const uint32_t idesc = umma_idesc_bf16(128, 16);
+    const uint32_t a0 = smem_u32(sa) + SLK_BEFORE * 16;
+    const uint32_t w0 = smem_u32(sw);
+    for (int t = 0; t < a.T; ++t) {
+      int vb;
+      if (a.contig) {
+        vb = 128 * t;
+      } else {
+        const int ly = t / a.tpl;
+        vb = ly * P + 1 + 128 * (t - ly * a.tpl);
+      }
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const int pos = ((dz + 1) * (L + 2) + 1 + dy) * P + dx + vb;
+        const uint64_t da = umma_desc(a0 + (uint32_t)pos * 16u, (uint32_t)plane_bytes, 128u);
+        const uint64_t db = umma_desc(w0 + (uint32_t)tap * 512u, 256u, 128u);
+        umma_bf16(tmem + 16u * (uint32_t)t, da, db, idesc, tap > 0 ? 1u : 0u);
+      }
+    }
+    umma_commit(mbar);
+  }
+  const uint32_t done = mbar_wait_bounded(mbar, 0, 1 << 24);
+  const int all_done = __syncthreads_and((int)done);
+  tc_fence_after();
+  if (!all_done) {
+    if (tid == 0) atomicExch(a.err, 1);
+  } else {
+    const int w = tid >> 5, lane = tid & 31;
+    for (int t = 0; t < a.T; ++t) {
+      float acc[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * w) << 16) + 16u * (uint32_t)t, acc);
+      const int r = 32 * w + lane;
+      int ly, x;
+      bool valid;
+      if (a.contig) {
+        const int v = 128 * t + r;
+        ly = v / P;
+        const int px = v - ly * P;
+        x = px - 1;
+        valid = px >= 1 && px <= n && ly < L;
+      } else {
+        ly = t / a.tpl;
+        x = 128 * (t - ly * a.tpl) + r;
+        valid = x < n;
+      }
+      const int gy = y0 + ly;
+      if (!valid || gy >= n) continue;
+      const size_t v = ((size_t)z * n + gy) * n + x;
+      if (MODE == CONV_HIDDEN) {
+        float h[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float zc = acc[c] + __ldg(a.bias + c);
+          acc[c] = zc;
+          h[c] = gelu_f(zc);
+        }
+        if (a.zout) {
+          float4* zo = reinterpret_cast<float4*>(a.zout + ((size_t)b * N3 + v) * CH);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+        store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, h);
+      } else if (MODE == CONV_OUT_Y) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) a.y[((size_t)b * 5 + c) * N3 + v] = acc[c] + __ldg(a.bias + c);
+      } else if (MODE == CONV_OUT_APPLY) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          float* g = a.gas + ((size_t)b * 5 + c) * N3 + v;
+          *g += a.scale.v[c] * (acc[c] + __ldg(a.bias + c));
+        }
+      } else {  // CONV_BWD
+        const float4* zp = reinterpret_cast<const float4*>(a.zprev + ((size_t)b * N3 + v) * CH);
+        float d[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 zz = __ldg(zp + q);
+          d[4 * q] = acc[4 * q] * gelu_grad_f(zz.x);
+          d[4 * q + 1] = acc[4 * q + 1] * gelu_grad_f(zz.y);
+          d[4 * q + 2] = acc[4 * q + 2] * gelu_grad_f(zz.z);
+          d[4 * q + 3] = acc[4 * q + 3] * gelu_grad_f(zz.w);
+        }
+        store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, d);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid < 32) tmem_dealloc_warp(tmem, (uint32_t)a.ncols);
+}
+
+static sim_status prepare_conv_kernels() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  DH_CUDA_TRY(cudaGetDevice(&dev));
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return SIM_OK;
+  const int maxsm = 200 * 1024;
+  DH_CUDA_TRY(cudaFuncSetAttribute(conv3_kernel<CONV_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  DH_CUDA_TRY(cudaFuncSetAttribute(conv3_kernel<CONV_OUT_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  DH_CUDA_TRY(cudaFuncSetAttribute(conv3_kernel<CONV_OUT_APPLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  DH_CUDA_TRY(cudaFuncSetAttribute(conv3_kernel<CONV_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  done.fetch_or(bit);
+  return SIM_OK;
+}
+
+static sim_status launch_conv(int mode, ConvArgs a, int B, cudaStream_t st) {
+  const ConvGeom g = conv_geom(a.n);
+  if (g.smem > 200 * 1024) {
+    set_error("closure: grid n = %d needs %zu bytes of shared memory per CTA", a.n, g.smem);
+    return SIM_EINVAL;
+  }
+  a.P = g.P;
+  a.L = g.L;
+  a.T = g.T;
+  a.tpl = g.tpl;
+  a.contig = g.contig;
+  a.pos_total = g.pos_total;
+  a.ncols = g.ncols;
+  const dim3 grid(cdiv(a.n, g.L), a.n, B);
+  switch (mode) {
+    case CONV_HIDDEN: conv3_kernel<CONV_HIDDEN><<<grid, 128, g.smem, st>>>(a); break;
+    case CONV_OUT_Y: conv3_kernel<CONV_OUT_Y><<<grid, 128, g.smem, st>>>(a); break;
+    case CONV_OUT_APPLY: conv3_kernel<CONV_OUT_APPLY><<<grid, 128, g.smem, st>>>(a); break;
+    default: conv3_kernel<CONV_BWD><<<grid, 128, g.smem, st>>>(a); break;
+  }
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ weight gradient
+// dW[tap][ci][co] += sum_v in[v + off(tap)][ci] dz[v][co]; db[co] += sum_v dz[v][co].
+// One CTA per (instance, plane, chunk of L lines); thread (ci, co) keeps 27 sums.
+__global__ void __launch_bounds__(256) conv_dw_kernel(const bf16* __restrict__ in,
+                                                      const bf16* __restrict__ dz, int n, int L,
+                                                      float* __restrict__ dW,
+                                                      float* __restrict__ db) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int P = n + 2;
+  const long long N3 = (long long)n * n * n;
+  const int b = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * L;
+  bf16* si = reinterpret_cast<bf16*>(smem);        // [3][L + 2][P][16]
+  bf16* sd = si + (size_t)3 * (L + 2) * P * CH;     // [L][n][16]
+  in += (size_t)b * N3 * CH;
+  dz += (size_t)b * N3 * CH;
+  const int nreg = 3 * (L + 2) * P;
+  for (int i = threadIdx.x; i < nreg; i += 256) {
+    const int pz = i / ((L + 2) * P);
+    const int rem = i - pz * (L + 2) * P;
+    const int ly = rem / P, px = rem - ly * P;
+    const int gx = wrapi(px - 1, n), gy = wrapi(y0 - 1 + ly, n), gz = wrapi(z - 1 + pz, n);
+    const uint4* src = reinterpret_cast<const uint4*>(in + (((size_t)gz * n + gy) * n + gx) * CH);
+    uint4* dst = reinterpret_cast<uint4*>(si + (size_t)i * CH);
+    dst[0] = __ldg(src);
+    dst[1] = __ldg(src + 1);
+  }
+  for (int i = threadIdx.x; i < L * n; i += 256) {
+    const int ly = i / n, x = i - ly * n;
+    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+    if (y0 + ly < n) {
+      const uint4* src = reinterpret_cast<const uint4*>(dz + (((size_t)z * n + y0 + ly) * n + x) * CH);
+      lo = __ldg(src);
+      hi = __ldg(src + 1);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(sd + (size_t)i * CH);
+    dst[0] = lo;
+    dst[1] = hi;
+  }
+  __syncthreads();
+  const int ci = threadIdx.x >> 4, co = threadIdx.x & 15;
+  float acc[27];
+#pragma unroll
+  for (int t = 0; t < 27; ++t) acc[t] = 0.0f;
+  float bacc = 0.0f;
+  for (int ly = 0; ly < L; ++ly) {
+    for (int x = 0; x < n; ++x) {
+      const float d = __bfloat162float(sd[((size_t)ly * n + x) * CH + co]);
+      bacc += d;
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
+        const float v = __bfloat162float(si[(((size_t)kz * (L + 2) + ly + ky) * P + x + kx) * CH + ci]);
+        acc[t] = fmaf(v, d, acc[t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 27; ++t) atomicAdd(dW + (t * CH + ci) * CH + co, acc[t]);
+  if (ci == 0) atomicAdd(db + co, bacc);
+}
+
+static int dw_lines(int n) {
+  for (int L = 8; L > 1; L /= 2) {
+    const size_t sm = ((size_t)3 * (L + 2) * (n + 2) + (size_t)L * n) * CH * 2;
+    if (sm <= 112 * 1024) return L;
+  }
+  return 1;
+}
+
+static sim_status launch_dw(const bf16* in, const bf16* dz, int n, int B, float* dW, float* db,
+                            cudaStream_t st) {
+  const int L = dw_lines(n);
+  const size_t sm = ((size_t)3 * (L + 2) * (n + 2) + (size_t)L * n) * CH * 2;
+  if (sm > 200 * 1024) {
+    set_error("closure: weight gradient at n = %d needs too much shared memory", n);
+    return SIM_EINVAL;
+  }
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  DH_CUDA_TRY(cudaGetDevice(&dev));
+  if (!(done.load() & (1ull << (dev & 63)))) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(conv_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    done.fetch_or(1ull << (dev & 63));
+  }
+  conv_dw_kernel<<<dim3(cdiv(n, L), n, B), 256, sm, st>>>(in, dz, n, L, dW, db);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ elementwise kernels
+// x[b][v][f] = bf16((gas[b][f][v] - mu_f) / sigma_f), f < 5; channels 5..15 are zero
+__global__ void closure_pack_kernel(const float* __restrict__ gas, F5 mu, F5 inv_sigma,
+                                    bf16* __restrict__ x, long long N3) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= N3) return;
+  float v[16];
+#pragma unroll
+  for (int f = 0; f < 16; ++f) v[f] = 0.0f;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) v[f] = (gas[((size_t)b * 5 + f) * N3 + i] - mu.v[f]) * inv_sigma.v[f];
+  store_bf16x16(x + ((size_t)b * N3 + i) * CH, v);
+}
+
+// loss += norm sum (y - (tgt - in) / s)^2 over 5 fields; dz4 = bf16(2 norm (y - t))
+__global__ void closure_loss_kernel(const float* __restrict__ y, const float* __restrict__ gin,
+                                    const float* __restrict__ gtg, F5 inv_s, float norm,
+                                    bf16* __restrict__ dz4, double* __restrict__ loss,
+                                    long long N3) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  float acc = 0.0f;
+  if (i < N3) {
+    float g[16];
+#pragma unroll
+    for (int f = 0; f < 16; ++f) g[f] = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const size_t o = ((size_t)b * 5 + f) * N3 + i;
+      const float t = (gtg[o] - gin[o]) * inv_s.v[f];
+      const float d = y[o] - t;
+      acc += d * d;
+      g[f] = 2.0f * norm * d;
+    }
+    store_bf16x16(dz4 + ((size_t)b * N3 + i) * CH, g);
+  }
+  block_sum_atomic(acc * norm, loss);
+}
+
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, int count, float lr,
+                            float b1, float b2, float eps, float bc1, float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// packed forward weights: wf[l][tap][kc][co][j] = W[l][tap][8 kc + j][co];
+// packed backward weights: wb[l][tap][kc][ci][j] = W[l][26 - tap][ci][8 kc + j]
+__global__ void repack_kernel(const float* __restrict__ W, bf16* __restrict__ wf,
+                              bf16* __restrict__ wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over NL * 27 * 256
+  if (i >= NL * 27 * 256) return;
+  const int l = i / (27 * 256);
+  const int r = i - l * 27 * 256;
+  const int tap = r / 256, e = r % 256;
+  const int kc = e / 128, row = (e / 8) % 16, j = e % 8;
+  const int k = 8 * kc + j;
+  const float* Wl = W + (size_t)l * WL;
+  wf[i] = __float2bfloat16_rn(Wl[(tap * CH + k) * CH + row]);
+  wb[i] = __float2bfloat16_rn(Wl[((26 - tap) * CH + row) * CH + k]);
+}
+
+}  // namespace dh
+
+// ===================================================================== closure object
+using namespace dh;
+
+struct sim_closure_s {
+  cudaStream_t st = 0;
+  float mu[5] = {0, 0, 0, 0, 0}, inv_sigma[5] = {1, 1, 1, 1, 1}, scale[5] = {1, 1, 1, 1, 1};
+  float* prm = nullptr;   // NPAD: padded weights then biases (float32 master copy)
+  float* grad = nullptr;  // NPAD
+  float *m = nullptr, *v = nullptr;
+  int adam_t = 0;
+  bf16 *wf = nullptr, *wb = nullptr;  // NL x PACK each
+  int* err = nullptr;
+  double* loss = nullptr;
+  // workspace
+  int wn = 0, wB = 0;
+  bool wtrain = false;
+  uint64_t gen = 0;  // bumped whenever the workspace moves (captured graphs must be redone)
+  bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *d1 = nullptr, *d2 = nullptr;
+  float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr;
+  std::vector<void*> ws;
+};
+
+namespace dh {
+
+static void ws_free(sim_closure_s* c) {
+  for (void* p : c->ws) cudaFree(p);
+  c->ws.clear();
+  c->x = c->a1 = c->a2 = c->a3 = c->d1 = c->d2 = nullptr;
+  c->z1 = c->z2 = c->z3 = c->y = nullptr;
+  c->wn = c->wB = 0;
+}
+
+template <class T>
+static sim_status ws_alloc(sim_closure_s* c, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("closure: cudaMalloc(%zu bytes) failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return SIM_ENOMEM;
+  }
+  c->ws.push_back(*p);
+  return SIM_OK;
+}
+
+sim_status closure_prepare(sim_closure_s* c, int n, int B, bool training) {
+  DH_TRY(prepare_conv_kernels());
+  if (c->wn == n && c->wB >= B && (c->wtrain || !training)) return SIM_OK;
+  // the old buffers may be in use on any stream (a simulation's, this closure's)
+  DH_CUDA_TRY(cudaDeviceSynchronize());
+  ws_free(c);
+  c->gen += 1;
+  const size_t V = (size_t)n * n * n * B;
+  DH_TRY(ws_alloc(c, &c->x, V * CH));
+  DH_TRY(ws_alloc(c, &c->a1, V * CH));
+  DH_TRY(ws_alloc(c, &c->a2, V * CH));
+  if (training) {
+    DH_TRY(ws_alloc(c, &c->a3, V * CH));
+    DH_TRY(ws_alloc(c, &c->d1, V * CH));
+    DH_TRY(ws_alloc(c, &c->d2, V * CH));
+    DH_TRY(ws_alloc(c, &c->z1, V * CH));
+    DH_TRY(ws_alloc(c, &c->z2, V * CH));
+    DH_TRY(ws_alloc(c, &c->z3, V * CH));
+    DH_TRY(ws_alloc(c, &c->y, V * 5));
+  }
+  c->wn = n;
+  c->wB = B;
+  c->wtrain = training;
+  return SIM_OK;
+}
+
+static ConvArgs conv_args(sim_closure_s* c, int l, bool backward, const bf16* in, int n) {
+  ConvArgs a;
+  memset(&a, 0, sizeof(a));
+  a.in = in;
+  a.w = (backward ? c->wb : c->wf) + (size_t)l * PACK;
+  a.bias = backward ? nullptr : c->prm + NL * WL + l * CH;
+  a.n = n;
+  a.err = c->err;
+  for (int f = 0; f < 5; ++f) a.scale.v[f] = c->scale[f];
+  return a;
+}
+
+static F5 f5(const float* v) {
+  F5 r;
+  for (int f = 0; f < 5; ++f) r.v[f] = v[f];
+  return r;
+}
+
+// Forward through the four layers. mode CONV_OUT_APPLY adds s y to `gas`; CONV_OUT_Y
+// writes y (and, for training, every pre-activation).
+static sim_status closure_forward(sim_closure_s* c, const float* gas, int n, int B, int mode,
+                                  float* gas_apply, bool keep, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  closure_pack_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, f5(c->mu), f5(c->inv_sigma),
+                                                              c->x, N3);
+  DH_LAUNCH_CHECK();
+  bf16* acts[4] = {c->x, c->a1, c->a2, keep ? c->a3 : c->a1};
+  float* zs[3] = {keep ? c->z1 : nullptr, keep ? c->z2 : nullptr, keep ? c->z3 : nullptr};
+  for (int l = 0; l < 3; ++l) {
+    ConvArgs a = conv_args(c, l, false, acts[l], n);
+    a.out = acts[l + 1];
+    a.zout = zs[l];
+    DH_TRY(launch_conv(CONV_HIDDEN, a, B, st));
+  }
+  ConvArgs a = conv_args(c, 3, false, acts[3], n);
+  if (mode == CONV_OUT_APPLY) {
+    a.gas = gas_apply;
+    return launch_conv(CONV_OUT_APPLY, a, B, st);
+  }
+  a.y = c->y;
+  return launch_conv(CONV_OUT_Y, a, B, st);
+}
+
+uint64_t closure_generation(const sim_closure_s* c) { return c->gen; }
+
+sim_status closure_apply(sim_closure_s* c, float* gas, int n, int B, cudaStream_t st) {
+  if (c->wn != n || c->wB < B) {
+    set_error("closure: workspace not prepared for n = %d, B = %d", n, B);
+    return SIM_EINVAL;
+  }
+  return closure_forward(c, gas, n, B, CONV_OUT_APPLY, gas, false, st);
+}
+
+// loss and the gradient of every parameter (c->grad, overwritten) for one batch
+static sim_status closure_backprop(sim_closure_s* c, const float* gas, const float* target,
+                                   int n, int B, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  DH_TRY(closure_forward(c, gas, n, B, CONV_OUT_Y, nullptr, true, st));
+  DH_CUDA_TRY(cudaMemsetAsync(c->loss, 0, sizeof(double), st));
+  DH_CUDA_TRY(cudaMemsetAsync(c->grad, 0, NPAD * sizeof(float), st));
+  F5 inv_s;
+  for (int f = 0; f < 5; ++f) inv_s.v[f] = 1.0f / c->scale[f];
+  const float norm = (float)(1.0 / (5.0 * (double)N3 * B));
+  closure_loss_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(c->y, gas, target, inv_s, norm,
+                                                              c->d1, c->loss, N3);
+  DH_LAUNCH_CHECK();
+  // layer l: input activation acts[l], pre-activation of layer l - 1: zs[l - 1]
+  const bf16* acts[4] = {c->x, c->a1, c->a2, c->a3};
+  const float* zs[3] = {c->z1, c->z2, c->z3};
+  bf16* dcur = c->d1;
+  bf16* dnext = c->d2;
+  for (int l = 3; l >= 0; --l) {
+    DH_TRY(launch_dw(acts[l], dcur, n, B, c->grad + (size_t)l * WL, c->grad + NL * WL + l * CH, st));
+    if (l == 0) break;
+    ConvArgs a = conv_args(c, l, true, dcur, n);
+    a.out = dnext;
+    a.zprev = zs[l - 1];
+    DH_TRY(launch_conv(CONV_BWD, a, B, st));
+    bf16* t = dcur;
+    dcur = dnext;
+    dnext = t;
+  }
+  return SIM_OK;
+}
+
+static sim_status repack(sim_closure_s* c, cudaStream_t st) {
+  repack_kernel<<<cdiv(NL * 27 * 256, 256), 256, 0, st>>>(c->prm, c->wf, c->wb);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// flat weight vector (real layer shapes) <-> padded parameters
+static void flat_to_pad(const float* flat, std::vector<float>& pad) {
+  pad.assign(NPAD, 0.0f);
+  size_t o = 0;
+  for (int l = 0; l < NL; ++l) {
+    const int ci = LAYER_CIN[l], co = LAYER_COUT[l];
+    for (int t = 0; t < 27; ++t)
+      for (int i = 0; i < ci; ++i)
+        for (int j = 0; j < co; ++j) pad[(size_t)l * WL + (t * CH + i) * CH + j] = flat[o++];
+    for (int j = 0; j < co; ++j) pad[NL * WL + l * CH + j] = flat[o++];
+  }
+}
+
+static void pad_to_flat(const std::vector<float>& pad, float* flat) {
+  size_t o = 0;
+  for (int l = 0; l < NL; ++l) {
+    const int ci = LAYER_CIN[l], co = LAYER_COUT[l];
+    for (int t = 0; t < 27; ++t)
+      for (int i = 0; i < ci; ++i)
+        for (int j = 0; j < co; ++j) flat[o++] = pad[(size_t)l * WL + (t * CH + i) * CH + j];
+    for (int j = 0; j < co; ++j) flat[o++] = pad[NL * WL + l * CH + j];
+  }
+}
+
+static int check_err(sim_closure_s* c) {
+  int e = 0;
+  cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+  return e;
+}
+
+// ------------------------------------------------------------------ coarse / fine pairing
+// fine half-complex mode <- coarse mode (band-limited interpolation, Nyquist split)
+__global__ void refine_map_kernel(const cufftComplex* __restrict__ Wc, int nc,
+                                  cufftComplex* __restrict__ Xf, int nf, float s) {
+  const int nhf = nf / 2 + 1, nhc = nc / 2 + 1;
+  const long long NCf = (long long)nf * nf * nhf;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NCf) return;
+  const int kx = (int)(i % nhf);
+  const long long r = i / nhf;
+  int ky = (int)(r % nf), kz = (int)(r / nf);
+  if (ky > nf / 2) ky -= nf;
+  if (kz > nf / 2) kz -= nf;
+  const bool even = (nc % 2 == 0);
+  const int lim = nc / 2;  // |k| <= nc/2 (even: the Nyquist index; odd: (nc-1)/2)
+  float f = s;
+  bool in = kx <= lim && abs(ky) <= lim && abs(kz) <= lim;
+  if (in && even) {
+    if (kx == lim) f *= 0.5f;
+    if (abs(ky) == lim) f *= 0.5f;
+    if (abs(kz) == lim) f *= 0.5f;
+  }
+  cufftComplex out = make_cuFloatComplex(0.0f, 0.0f);
+  if (in) {
+    const int cy = ky < 0 ? ky + nc : ky, cz = kz < 0 ? kz + nc : kz;
+    const cufftComplex w = Wc[((long long)cz * nc + cy) * nhc + kx];
+    out = make_cuFloatComplex(f * w.x, f * w.y);
+  }
+  Xf[i] = out;
+}
+
+// coarse cell j = tent-weighted mean of the 27 fine cells around fine cell 2j
+__global__ void restrict_gas_kernel(const float* __restrict__ gf, int nf,
+                                    float* __restrict__ gc) {
+  const int nc = nf / 2;
+  const long long NCc = (long long)nc * nc * nc, NFf = (long long)nf * nf * nf;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bf = blockIdx.y;  // instance x field
+  if (i >= NCc) return;
+  const int x = (int)(i % nc), y = (int)((i / nc) % nc), z = (int)(i / ((long long)nc * nc));
+  const float w[3] = {0.25f, 0.5f, 0.25f};
+  const float* src = gf + (size_t)bf * NFf;
+  float acc = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    const int fz = wrapi(2 * z + c - 1, nf);
+    for (int bb = 0; bb < 3; ++bb) {
+      const int fy = wrapi(2 * y + bb - 1, nf);
+      const float* row = src + ((size_t)fz * nf + fy) * nf;
+      const float wzy = w[c] * w[bb];
+      for (int a = 0; a < 3; ++a) acc += wzy * w[a] * row[wrapi(2 * x + a - 1, nf)];
+    }
+  }
+  gc[(size_t)bf * NCc + i] = acc;
+}
+
+__global__ void restrict_part_kernel(const float* __restrict__ pf, int nf, float* __restrict__ pc) {
+  const int nc = nf / 2;
+  const long long NCc = (long long)nc * nc * nc, NFf = (long long)nf * nf * nf;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bc = blockIdx.y;  // instance x component
+  if (i >= NCc) return;
+  const int x = (int)(i % nc), y = (int)((i / nc) % nc), z = (int)(i / ((long long)nc * nc));
+  pc[(size_t)bc * NCc + i] = pf[(size_t)bc * NFf + ((size_t)(2 * z) * nf + 2 * y) * nf + 2 * x];
+}
+
+}  // namespace dh
+
+// ===================================================================== C ABI
+extern "C" {
+
+sim_status sim_closure_create(const float* weights, void* stream, sim_closure_t** out) {
+  if (!out) {
+    set_error("sim_closure_create: out is NULL");
+    return SIM_EINVAL;
+  }
+  *out = nullptr;
+  sim_closure_s* c = new sim_closure_s();
+  c->st = (cudaStream_t)stream;
+  auto bad = [&](sim_status s) {
+    sim_closure_destroy(c);
+    return s;
+  };
+  if (cudaMalloc((void**)&c->prm, NPAD * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&c->grad, NPAD * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&c->m, NPAD * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&c->v, NPAD * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&c->wf, (size_t)NL * PACK * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc((void**)&c->wb, (size_t)NL * PACK * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc((void**)&c->err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->loss, sizeof(double)) != cudaSuccess) {
+    set_error("sim_closure_create: cudaMalloc failed");
+    return bad(SIM_ENOMEM);
+  }
+  std::vector<float> pad(NPAD, 0.0f);
+  if (weights) flat_to_pad(weights, pad);
+  if (cudaMemcpy(c->prm, pad.data(), NPAD * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->m, 0, NPAD * sizeof(float)) != cudaSuccess ||
+      cudaMemset(c->v, 0, NPAD * sizeof(float)) != cudaSuccess ||
+      cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) {
+    set_error("sim_closure_create: upload failed");
+    return bad(SIM_ECUDA);
+  }
+  sim_status r = prepare_conv_kernels();
+  if (r == SIM_OK) r = repack(c, c->st);
+  if (r != SIM_OK) return bad(r);
+  *out = c;
+  return SIM_OK;
+}
+
+void sim_closure_destroy(sim_closure_t* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  ws_free(c);
+  for (void* p : {(void*)c->prm, (void*)c->grad, (void*)c->m, (void*)c->v, (void*)c->wf,
+                  (void*)c->wb, (void*)c->err, (void*)c->loss})
+    if (p) cudaFree(p);
+  delete c;
+}
+
+sim_status sim_closure_set_norm(sim_closure_t* c, const float* mu, const float* sigma,
+                                const float* scale) {
+  if (!c || !mu || !sigma || !scale) return SIM_EINVAL;
+  for (int f = 0; f < 5; ++f)
+    if (!(sigma[f] > 0) || !(scale[f] > 0)) {
+      set_error("sim_closure_set_norm: sigma and scale must be > 0");
+      return SIM_EINVAL;
+    }
+  for (int f = 0; f < 5; ++f) {
+    c->mu[f] = mu[f];
+    c->inv_sigma[f] = 1.0f / sigma[f];
+    c->scale[f] = scale[f];
+  }
+  return SIM_OK;
+}
+
+sim_status sim_closure_get_weights(sim_closure_t* c, float* host_out) {
+  if (!c || !host_out) return SIM_EINVAL;
+  std::vector<float> pad(NPAD);
+  DH_CUDA_TRY(cudaStreamSynchronize(c->st));
+  DH_CUDA_TRY(cudaMemcpy(pad.data(), c->prm, NPAD * sizeof(float), cudaMemcpyDeviceToHost));
+  pad_to_flat(pad, host_out);
+  return SIM_OK;
+}
+
+sim_status sim_closure_set_weights(sim_closure_t* c, const float* host_in) {
+  if (!c || !host_in) return SIM_EINVAL;
+  std::vector<float> pad;
+  flat_to_pad(host_in, pad);
+  DH_CUDA_TRY(cudaStreamSynchronize(c->st));
+  DH_CUDA_TRY(cudaMemcpy(c->prm, pad.data(), NPAD * sizeof(float), cudaMemcpyHostToDevice));
+  DH_CUDA_TRY(cudaMemset(c->m, 0, NPAD * sizeof(float)));
+  DH_CUDA_TRY(cudaMemset(c->v, 0, NPAD * sizeof(float)));
+  c->adam_t = 0;
+  return repack(c, c->st);
+}
+
+sim_status sim_closure_forward(sim_closure_t* c, const float* gas, int32_t n, int32_t B,
+                               float* y) {
+  if (!c || !gas || !y || n < 2 || B < 1) {
+    set_error("sim_closure_forward: invalid arguments");
+    return SIM_EINVAL;
+  }
+  DH_TRY(closure_prepare(c, n, B, true));
+  DH_TRY(closure_forward(c, gas, n, B, CONV_OUT_Y, nullptr, false, c->st));
+  DH_CUDA_TRY(cudaMemcpyAsync(y, c->y, (size_t)B * 5 * n * n * n * sizeof(float),
+                              cudaMemcpyDeviceToDevice, c->st));
+  return SIM_OK;
+}
+
+sim_status sim_closure_apply(sim_closure_t* c, float* gas, int32_t n, int32_t B) {
+  if (!c || !gas || n < 2 || B < 1) {
+    set_error("sim_closure_apply: invalid arguments");
+    return SIM_EINVAL;
+  }
+  DH_TRY(closure_prepare(c, n, B, false));
+  return closure_apply(c, gas, n, B, c->st);
+}
+
+sim_status sim_closure_gradient(sim_closure_t* c, const float* gas, const float* target,
+                                int32_t n, int32_t B, double* loss_host, float* grad_host) {
+  if (!c || !gas || !target || n < 2 || B < 1) {
+    set_error("sim_closure_gradient: invalid arguments");
+    return SIM_EINVAL;
+  }
+  DH_TRY(closure_prepare(c, n, B, true));
+  DH_TRY(closure_backprop(c, gas, target, n, B, c->st));
+  DH_CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (check_err(c)) {
+    set_error("closure: a tensor-core wait timed out");
+    return SIM_ETIMEOUT;
+  }
+  if (loss_host) DH_CUDA_TRY(cudaMemcpy(loss_host, c->loss, sizeof(double), cudaMemcpyDeviceToHost));
+  if (grad_host) {
+    std::vector<float> pad(NPAD);
+    DH_CUDA_TRY(cudaMemcpy(pad.data(), c->grad, NPAD * sizeof(float), cudaMemcpyDeviceToHost));
+    pad_to_flat(pad, grad_host);
+  }
+  return SIM_OK;
+}
+
+sim_status sim_closure_train_step(sim_closure_t* c, const float* gas, const float* target,
+                                  int32_t n, int32_t B, double lr, double* loss_out) {
+  if (!c || !gas || !target || n < 2 || B < 1 || !(lr > 0)) {
+    set_error("sim_closure_train_step: invalid arguments");
+    return SIM_EINVAL;
+  }
+  DH_TRY(closure_prepare(c, n, B, true));
+  DH_TRY(closure_backprop(c, gas, target, n, B, c->st));
+  c->adam_t += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  adam_kernel<<<cdiv(NPAD, 256), 256, 0, c->st>>>(
+      c->prm, c->grad, c->m, c->v, NPAD, (float)lr, (float)b1, (float)b2, 1e-8f,
+      (float)(1.0 - std::pow(b1, c->adam_t)), (float)(1.0 - std::pow(b2, c->adam_t)));
+  DH_LAUNCH_CHECK();
+  DH_TRY(repack(c, c->st));
+  if (loss_out)
+    DH_CUDA_TRY(cudaMemcpyAsync(loss_out, c->loss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  return SIM_OK;
+}
+
+sim_status sim_closure_status(sim_closure_t* c) {
+  if (!c) return SIM_EINVAL;
+  DH_CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (check_err(c)) {
+    set_error("closure: a tensor-core wait timed out");
+    return SIM_ETIMEOUT;
+  }
+  return SIM_OK;
+}
+
+sim_status sim_refine_noise(const float* w_c, int32_t n_c, float* w_f, int32_t n_f,
+                            double scale, void* stream) {
+  if (!w_c || !w_f || n_c < 2 || n_f <= n_c) {
+    set_error("sim_refine_noise: invalid arguments (need n_f > n_c >= 2)");
+    return SIM_EINVAL;
+  }
+  FFTPlans* pc = shared_plans(n_c);
+  FFTPlans* pf = shared_plans(n_f);
+  if (!pc || !pf) return SIM_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long NCc = (long long)n_c * n_c * (n_c / 2 + 1);
+  const long long NCf = (long long)n_f * n_f * (n_f / 2 + 1);
+  cufftComplex* buf = nullptr;
+  DH_CUDA_TRY(cudaMallocAsync((void**)&buf, (NCc + NCf) * sizeof(cufftComplex), st));
+  sim_status r = pc->set_stream(st);
+  if (r == SIM_OK) r = pf->set_stream(st);
+  if (r == SIM_OK && cufftExecR2C(pc->r2c1, const_cast<float*>(w_c), buf) != CUFFT_SUCCESS) {
+    set_error("sim_refine_noise: cufftExecR2C failed");
+    r = SIM_ECUDA;
+  }
+  if (r == SIM_OK) {
+    const float s = (float)(scale / ((double)n_c * n_c * n_c));
+    refine_map_kernel<<<cdiv(NCf, 256), 256, 0, st>>>(buf, n_c, buf + NCc, n_f, s);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("sim_refine_noise: launch failed");
+      r = SIM_ECUDA;
+    }
+  }
+  if (r == SIM_OK && cufftExecC2R(pf->c2r1, buf + NCc, w_f) != CUFFT_SUCCESS) {
+    set_error("sim_refine_noise: cufftExecC2R failed");
+    r = SIM_ECUDA;
+  }
+  cudaFreeAsync(buf, st);
+  return r;
+}
+
+sim_status sim_restrict_gas(const float* gas_f, int32_t n_f, float* gas_c, int32_t B,
+                            void* stream) {
+  if (!gas_f || !gas_c || n_f < 2 || n_f % 2 || B < 1) {
+    set_error("sim_restrict_gas: invalid arguments (n_f even)");
+    return SIM_EINVAL;
+  }
+  const long long NCc = (long long)(n_f / 2) * (n_f / 2) * (n_f / 2);
+  restrict_gas_kernel<<<dim3(cdiv(NCc, 256), 5 * B), 256, 0, (cudaStream_t)stream>>>(gas_f, n_f, gas_c);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+sim_status sim_restrict_particles(const float* part_f, int32_t n_f, float* part_c, int32_t B,
+                                  void* stream) {
+  if (!part_f || !part_c || n_f < 2 || n_f % 2 || B < 1) {
+    set_error("sim_restrict_particles: invalid arguments (n_f even)");
+    return SIM_EINVAL;
+  }
+  const long long NCc = (long long)(n_f / 2) * (n_f / 2) * (n_f / 2);
+  restrict_part_kernel<<<dim3(cdiv(NCc, 256), 6 * B), 256, 0, (cudaStream_t)stream>>>(part_f, n_f, part_c);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+}  // extern "C"

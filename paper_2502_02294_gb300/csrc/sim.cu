@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include "closure.cuh"
 #include "ics.cuh"
 #include "pm.cuh"
 #include "schedule.h"
@@ -131,6 +132,8 @@ struct sim_s {
   SubgridConst* d_sub = nullptr;    // [n_steps][B]
   double* d_pch = nullptr;          // [B][PCH_N] chain-rule constants of the parameters
   double* d_cpref = nullptr;        // [n_steps + 1][B] chain coefficient of a flush slot
+  sim_closure_t* closure = nullptr;  // learned correction after every step (not owned)
+  uint64_t closure_gen = 0;
   int fwd_var[3] = {SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT};
   int adj_var[3] = {SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT, SIM_SWEEP_DEFAULT};
   // state (B instances one after another in every buffer)
@@ -494,6 +497,8 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
                            (float)h->inv_dx, B, st));
   if (P.gravity_on) DH_TRY(launch_gas_kick(*gas, g, K2, h->n, B, st));
   if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, B * h->N3, st));
+  // 6. learned correction of the gas fields (solver in the loop, Sec. 4)
+  if (h->closure) DH_TRY(closure_apply(h->closure, *gas, h->n, B, st));
   return SIM_OK;
 }
 
@@ -904,6 +909,19 @@ static sim_status validate_batch(const sim_params* p, int B) {
 
 static sim_status cfl_now(sim_t* h, double* cfl_out);
 
+// The closure's workspace for this handle's grid; graphs that captured an older workspace
+// are dropped.
+static sim_status closure_ready(sim_t* h) {
+  if (!h->closure) return SIM_OK;
+  DH_TRY(closure_prepare(h->closure, h->n, h->B, false));
+  const uint64_t g = closure_generation(h->closure);
+  if (g != h->closure_gen) {
+    clear_graphs(h);
+    h->closure_gen = g;
+  }
+  return SIM_OK;
+}
+
 // Checks and allocations of sim_run (never inside a capture).
 static sim_status run_prepare(sim_t* h, int n_steps) {
   if (h->step != h->init_step || h->ckpt_count != 0) {
@@ -914,6 +932,7 @@ static sim_status run_prepare(sim_t* h, int n_steps) {
     set_error("sim_run: n_steps out of range");
     return SIM_EINVAL;
   }
+  DH_TRY(closure_ready(h));
   return ensure_ckpt_pool(h, (n_steps + h->prm.ckpt_every - 1) / h->prm.ckpt_every);
 }
 
@@ -938,6 +957,10 @@ static sim_status run_body(sim_t* h, int n_steps) {
 }
 
 static sim_status run_adjoint_prepare(sim_t* h, const float* dL_dnoise, const double* dL_dparams) {
+  if (h->closure) {
+    set_error("sim_run_adjoint: not available while a learned closure is set");
+    return SIM_ENOTIMPL;
+  }
   if (!dL_dparams) {
     set_error("sim_run_adjoint: null arguments");
     return SIM_EINVAL;
@@ -1250,7 +1273,8 @@ sim_status sim_step(sim_t* h) {
     return fail(h, SIM_EINVAL);
   }
   const long long N3 = h->N3 * h->B;
-  sim_status r = dcopy(h->prev_gas, h->gas, 5 * N3 * sizeof(float), h->st);
+  sim_status r = closure_ready(h);
+  if (r == SIM_OK) r = dcopy(h->prev_gas, h->gas, 5 * N3 * sizeof(float), h->st);
   if (r == SIM_OK) r = part_join(h->prev_part, h->s, h->p, h, h->st);
   if (r == SIM_OK) r = forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr);
   if (r != SIM_OK) return fail(h, r);
@@ -1268,6 +1292,10 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
   if (h->prev_step < 0 || h->prev_step + 1 != h->step) {
     set_error("sim_step_adjoint: no sim_step to differentiate");
     return fail(h, SIM_EINVAL);
+  }
+  if (h->closure) {
+    set_error("sim_step_adjoint: not available while a learned closure is set");
+    return fail(h, SIM_ENOTIMPL);
   }
   const long long N3 = h->N3 * h->B;
   const int B = h->B;
@@ -1400,6 +1428,31 @@ sim_status sim_schedule(const sim_t* h, int32_t i, double* out6) {
   out6[3] = f.dtau;
   out6[4] = f.K2;
   out6[5] = f.pref1;
+  return SIM_OK;
+}
+
+sim_status sim_set_closure(sim_t* h, sim_closure_t* c) {
+  if (!h) return SIM_EINVAL;
+  clear_graphs(h);
+  h->closure = c;
+  h->closure_gen = 0;
+  if (c) {
+    sim_status r = closure_prepare(c, h->n, h->B, false);
+    if (r != SIM_OK) {
+      h->closure = nullptr;
+      return fail(h, r);
+    }
+    h->closure_gen = closure_generation(c);
+  }
+  return SIM_OK;
+}
+
+sim_status sim_ic_amplitude(const sim_t* h, int32_t b, double* C) {
+  if (!h || !C || b < 0 || b >= h->B) {
+    set_error("sim_ic_amplitude: invalid arguments");
+    return SIM_EINVAL;
+  }
+  *C = h->inst[b].C;
   return SIM_OK;
 }
 
@@ -1589,6 +1642,10 @@ sim_status sim_group_run(sim_group_t* g) {
     if (h->prm.cfl_max > 0) {
       set_error("sim_group_run: members with cfl_max > 0 read back every step");
       return fail(h, SIM_EINVAL);
+    }
+    if (h->closure) {
+      set_error("sim_group_run: members with a learned closure are run on their own");
+      return fail(h, SIM_ENOTIMPL);
     }
     DH_TRY(fail(h, run_prepare(h, h->prm.n_steps - h->step)));
   }

@@ -15,10 +15,11 @@ from __future__ import annotations
 import argparse
 import statistics
 
+import numpy as np
 import torch
 
 from . import api
-from ._lib import default_params
+from ._lib import CLOSURE_NWEIGHTS, default_params
 
 # algorithmic bytes per cell (one particle per cell) of one call
 BYTES_PER_CELL = {
@@ -28,7 +29,10 @@ BYTES_PER_CELL = {
     "interp_cic": 36,      # 3 mesh fields + 3 displacements read, 3 values written
     "gravity": 16,         # density contrast read, 3 force components written
     "subgrid": 44,         # 5 fields read + written in place, star indicator written
+    "closure_apply": 296,  # pack (20 + 32), 4 layers x (32 in + 32 out), gas 40 read+write
 }
+# useful closure flops per voxel: 2 x 27 x (5 x 16 + 16 x 16 + 16 x 16 + 16 x 5)
+CLOSURE_FLOPS = 2 * 27 * (5 * 16 + 16 * 16 + 16 * 16 + 16 * 5)
 BENCH = dict(n_steps=100, a_start=0.05, a_end=1.0, ckpt_every=10, subgrid_on=1,
              delta_c=100.0, Pi0=0.05, E0=0.03, T_c=3.0e4, w_delta=5.0, w_T=1500.0,
              T0_uv=1.0e4, gamma_uv=1.4, seed=1)
@@ -56,6 +60,9 @@ def main(argv=None):
     delta = (gas[0] / gas[0].mean() - 1).contiguous()
     g = api.gravity(delta, p.box, sch["pref1"])
     gsub = gas.clone()
+    gcl = gas.clone()
+    clo = api.Closure(np.random.default_rng(0).standard_normal(CLOSURE_NWEIGHTS).astype(np.float32) * 0.05)
+    clo.set_norm([0.15, 0, 0, 0, 1e-3], [0.05, 0.01, 0.01, 0.01, 1e-3], [1e-4] * 5)
     grid = torch.zeros(n, n, n, dtype=torch.float32, device=gas.device)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=gas.device)
 
@@ -67,6 +74,7 @@ def main(argv=None):
         "interp_cic": [("interp_cic (3 fields)", lambda: api.interp_cic(g, s, n, p.box))],
         "gravity": [("gravity (r2c, Green, 3 c2r)", lambda: api.gravity(delta, p.box, sch["pref1"]))],
         "subgrid": [("subgrid (in place)", lambda: api.subgrid(gsub, sch["a1"], p, args.steps))],
+        "closure_apply": [("closure apply (4 tcgen05 convs)", lambda: clo.apply(gcl))],
     }
     for key in only:
         for label, fn in entries[key]:
@@ -83,7 +91,12 @@ def main(argv=None):
                 ts.append(e0.elapsed_time(e1))
             ms = statistics.median(ts)
             gbs = BYTES_PER_CELL[key] * n3 / (ms * 1e-3) / 1e9
-            print(f"{label:32s} n={n:4d} {1e3 * ms:9.1f} us {gbs:8.0f} GB/s algorithmic", flush=True)
+            extra = ""
+            if key == "closure_apply":
+                extra = f" {CLOSURE_FLOPS * n3 / (ms * 1e-3) / 1e12:7.1f} TFLOP/s useful"
+            print(f"{label:32s} n={n:4d} {1e3 * ms:9.1f} us {gbs:8.0f} GB/s algorithmic{extra}",
+                  flush=True)
+    clo.close()
     sim.close()
 
 

@@ -152,3 +152,15 @@ def test_restrict_particles_picks_even_lattice_sites():
         i_c = (qz * 3 + qy) * 3 + qx
         i_f = ((2 * qz) * n_f + 2 * qy) * n_f + 2 * qx
         assert torch.equal(out[:, i_c], part[:, i_f])
+
+
+def test_network_window_matches_periodic_network():
+    n = 10
+    x = _rand((5, n, n, n), 11)
+    w = oc.he_init(12).astype(np.float64)
+    w[-5:] = 0.05
+    y = oc.network(x, w)
+    for (z0, y0, x0) in [(0, 0, 0), (9, 3, 5), (4, 9, 1)]:
+        idx = [torch.arange(c - 4, c + 5) % n for c in (z0, y0, x0)]
+        win = x[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+        assert torch.allclose(oc.network_window(win, w), y[:, z0, y0, x0], atol=1e-12)
