@@ -56,6 +56,12 @@ BATCH_NAME = ("96 instances (32 each at 32^3, 48^3, 64^3; box n Mpc/h), per-inst
               "subgrid on; forward + parameter gradients (checkpoint every 10)")
 
 
+CLOSURE_NAME = ("learned closure (4 periodic 3x3x3 convs 5-16-16-16-5, GELU, bf16 on tcgen05): "
+                "600 pairs from six 64^3 / 128^3 run pairs (100 steps a=0.1->1.0), 600 Adam "
+                "iterations; applied every step of 256^3 runs (100 steps), field error against "
+                "the 512^3 run restricted to 256^3")
+
+
 def bench_batched(dh, synth, torch, steps: int, warmup: int):
     """Parameter-sampling form: three batched handles (one per grid size) run as one graph
     group, against the same 96 instances run one handle at a time (graphs on)."""
@@ -281,6 +287,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched parameter-sampling measurement")
+    ap.add_argument("--no-closure", action="store_true",
+                    help="skip the learned-closure training and 256^3 application")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured graphs")
     args = ap.parse_args()
@@ -416,6 +424,15 @@ def main():
         batched = bench_batched(dh, synth, torch, steps=2, warmup=1)
         torch.cuda.set_stream(stream)
 
+    # ---- learned closure: trained on 64^3 / 128^3 pairs, applied in 256^3 runs
+    closure = None
+    if not args.no_closure:
+        from paper_2502_02294_gb300 import learned
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        closure = learned.experiment()
+        closure["workload"] = CLOSURE_NAME
+        torch.cuda.set_stream(stream)
+
     # ---- max over ranks
     vals = torch.tensor([ms, fwd_ms, e2e_ms], dtype=torch.float64, device=dev)
     if ws > 1:
@@ -466,6 +483,8 @@ def main():
     }
     if batched is not None:
         line["batched"] = batched
+    if closure is not None:
+        line["closure"] = closure
     if not args.no_cpu_baseline:
         v, dt, threads = cpu_baseline_sample(1)
         line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": threads,

@@ -44,54 +44,67 @@ constexpr int SLK_BEFORE = 8, SLK_AFTER = 136;  // slack positions around the st
 constexpr int PACK = 27 * 512 / 2;              // bf16 elements of one packed layer
 
 // ------------------------------------------------------------------ geometry
+// A CTA owns L output lines of Zc consecutive planes and walks through the input planes
+// z0 - 1 .. z0 + Zc. Input plane p contributes to output planes p - 1, p, p + 1 through the
+// taps dz = +1, 0, -1; for one in-plane shift (dy, dx) those three weight blocks sit side
+// by side in one B operand (N = 48), so one MMA adds the shifted input to three output-plane
+// accumulators at once: 9 MMAs per input plane and tile. The accumulators of all Zc + 4
+// planes a CTA touches live in TMEM ([tile][plane][16 columns], zeroed first); output plane
+// q is final once input q + 1 is in, and its epilogue runs while the next input's MMAs do.
+// Input planes stream through a ring of three shared-memory slots ((L + 2) padded lines in
+// two 8-channel planes of 16-byte positions, with slack positions around them).
+constexpr int RING = 3;
+constexpr int CONV_THREADS = 256;
+
 struct ConvGeom {
-  int n, P, L, T, tpl, contig, pos_total, ncols;
+  int n, P, L, T, tpl, contig, Zc, slot_pos, ncols;
   size_t smem;
 };
 
+static int slot_positions(int L, int P) { return SLK_BEFORE + (L + 2) * P + SLK_AFTER; }
+
 static size_t conv_smem(int L, int P) {
-  const int pos_total = SLK_BEFORE + 3 * (L + 2) * P + SLK_AFTER;
-  return (size_t)2 * pos_total * 16 + 27 * 512 + 16;
+  return (size_t)RING * 2 * slot_positions(L, P) * 16 + 9 * 1536 + 32;  // + mbarriers, flags
 }
 
-// Lines per CTA and tiles: n >= 128 keeps each 128-row tile inside one line
-// (ceil(n/128) tiles per line); smaller grids let tiles run across consecutive padded
-// lines ("contiguous" rows) and choose the line count with the fewest tiles per plane.
-static ConvGeom conv_geom(int n) {
+static ConvGeom conv_geom(int n, int B) {
   ConvGeom g;
   g.n = n;
   g.P = n + 2;
-  const size_t limit = 112 * 1024;
+  const size_t limit = 112 * 1024;  // two CTAs per SM
   if (n >= 128) {
+    // 128-row tiles inside one line, ceil(n / 128) per line
     g.contig = 0;
     g.tpl = (n + 127) / 128;
-    g.L = conv_smem(2, g.P) <= limit ? 2 : 1;
-    g.T = g.L * g.tpl;
+    g.L = 1;
+    g.T = g.tpl;
   } else {
+    // tiles run across consecutive padded lines; fewest tiles per plane with T <= 2
     g.contig = 1;
     g.tpl = 0;
     int bestL = 1, bestCost = 1 << 30;
-    size_t bestSmem = 0;
     for (int L = 1; L <= n; ++L) {
       const int T = cdiv((long long)L * g.P, 128);
-      if (T > 8) break;
-      const size_t sm = conv_smem(L, g.P);
-      if (sm > limit) break;
+      if (T > 2 || (L > 1 && conv_smem(L, g.P) > limit)) break;
       const int cost = cdiv(n, L) * T;
-      if (cost < bestCost || (cost == bestCost && sm < bestSmem)) {
+      if (cost < bestCost) {
         bestCost = cost;
         bestL = L;
-        bestSmem = sm;
       }
     }
     g.L = bestL;
     g.T = cdiv((long long)bestL * g.P, 128);
   }
-  g.pos_total = SLK_BEFORE + 3 * (g.L + 2) * g.P + SLK_AFTER;
+  // accumulators of Zc + 4 planes in at most 256 columns (two CTAs per SM)
+  g.Zc = 16 / g.T - 4;
+  if (g.Zc < 1) g.Zc = 1;
+  if (g.Zc > n) g.Zc = n;
+  g.slot_pos = slot_positions(g.L, g.P);
   g.smem = conv_smem(g.L, g.P);
   int nc = 32;
-  while (nc < 16 * g.T) nc <<= 1;
+  while (nc < 16 * g.T * (g.Zc + 4)) nc <<= 1;
   g.ncols = nc;
+  (void)B;
   return g;
 }
 
@@ -135,7 +148,7 @@ struct ConvArgs {
   const bf16* in;      // [B][n^3][16]
   const bf16* w;       // packed [27][2][16 rows][8]: row = output channel, K = input channel
   const float* bias;   // [16] (forward) or NULL
-  int n, P, L, T, tpl, contig, pos_total, ncols;
+  int n, P, L, T, tpl, contig, Zc, slot_pos, ncols;
   bf16* out;           // HIDDEN / BWD: [B][n^3][16]
   float* zout;         // HIDDEN: pre-activation [B][n^3][16] or NULL
   const float* zprev;  // BWD: pre-activation whose GELU' multiplies the result
@@ -145,142 +158,235 @@ struct ConvArgs {
   int* err;
 };
 
+// fetch input plane gz (periodic) into ring slot `slot`: (L + 2) lines x P positions
+__device__ __forceinline__ void conv_fetch_plane(const ConvArgs& a, const bf16* in, uint32_t slot_addr,
+                                                 int gz, int L_unused, int y0, int tid) {
+  const int n = a.n, P = a.P, L = a.L;
+  const uint32_t plane_bytes = (uint32_t)a.slot_pos * 16u;
+  const int npos = (L + 2) * P;
+  gz = gz < 0 ? gz + n : (gz >= n ? gz - n : gz);
+  for (int pos = tid; pos < npos; pos += CONV_THREADS) {
+    const int ly = pos / P, px = pos - ly * P;
+    int gx = px - 1;
+    gx = gx < 0 ? gx + n : (gx >= n ? gx - n : gx);
+    const int gy = wrapi(y0 - 1 + ly, n);
+    const bf16* src = in + (((size_t)gz * n + gy) * n + gx) * CH;
+    const uint32_t d = slot_addr + (uint32_t)(SLK_BEFORE + pos) * 16u;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + plane_bytes), "l"(src + 8)
+                 : "memory");
+  }
+}
+
+// TMEM zeroing: every lane of every accumulator column
+__device__ __forceinline__ void tmem_zero(uint32_t tmem, int ncols, int w) {
+  const uint32_t lane_base = (uint32_t)(32 * (w & 3)) << 16;
+  uint32_t z[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) z[j] = 0u;
+  for (int c = 16 * (w >> 2); c < ncols; c += 16 * (CONV_THREADS / 128)) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};" ::"r"(tmem + lane_base + (uint32_t)c),
+        "r"(z[0]), "r"(z[1]), "r"(z[2]), "r"(z[3]), "r"(z[4]), "r"(z[5]), "r"(z[6]), "r"(z[7]),
+        "r"(z[8]), "r"(z[9]), "r"(z[10]), "r"(z[11]), "r"(z[12]), "r"(z[13]), "r"(z[14]),
+        "r"(z[15]));
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// The 9 x T MMAs of input plane i (slot i mod RING): block (dy, dx) of the weights against
+// the input shifted by (dy, dx), into planes j = i, i + 1, i + 2 of every tile.
+__device__ __forceinline__ void conv_issue_input(const ConvArgs& a, int i, uint32_t tmem,
+                                                 uint64_t a_base, uint64_t b_base,
+                                                 uint32_t slot_units, uint32_t idesc) {
+  const int P = a.P, T = a.T, ZP = a.Zc + 4;
+  const uint64_t a_slot = a_base + (uint64_t)((i % RING) * slot_units);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int j = (dy + 1) * 3 + (dx + 1);
+      const uint64_t db = b_base + (uint64_t)(j * 96);  // 1536-byte blocks
+      for (int t = 0; t < T; ++t) {
+        int vb;
+        if (a.contig) {
+          vb = 128 * t;
+        } else {
+          const int ly = t / a.tpl;
+          vb = ly * P + 1 + 128 * (t - ly * a.tpl);
+        }
+        // descriptors are linear in the start address (16-byte units, low 14 bits)
+        const uint64_t da = a_slot + (uint64_t)(SLK_BEFORE + (1 + dy) * P + dx + vb);
+        umma_bf16(tmem + 16u * (uint32_t)(t * ZP + i), da, db, idesc, 1u);
+      }
+    }
+  }
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(128) conv3_kernel(ConvArgs a) {
-  extern __shared__ __align__(1024) uint8_t smem[];
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc_in[16], int b,
+                                              int z, int y0, int t, int r) {
   const int n = a.n, P = a.P, L = a.L;
   const long long N3 = (long long)n * n * n;
-  const int b = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * L;
-  const int tid = threadIdx.x;
-  const int plane_bytes = a.pos_total * 16;
-  uint8_t* sa = smem;                         // two planes of pos_total x 16 bytes
-  uint8_t* sw = smem + 2 * plane_bytes;       // 27 x 512 bytes of packed weights
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sw + 27 * 512);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  const bf16* in = a.in + (size_t)b * N3 * CH;
+  int ly, x;
+  bool valid;
+  if (a.contig) {
+    const int v = 128 * t + r;
+    ly = v / P;
+    const int px = v - ly * P;
+    x = px - 1;
+    valid = px >= 1 && px <= n && ly < L;
+  } else {
+    ly = t / a.tpl;
+    x = 128 * (t - ly * a.tpl) + r;
+    valid = x < n;
+  }
+  const int gy = y0 + ly;
+  if (!valid || gy >= n) return;
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = acc_in[c];
+  const size_t v = ((size_t)z * n + gy) * n + x;
+  if (MODE == CONV_HIDDEN) {
+    float h[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float zc = acc[c] + __ldg(a.bias + c);
+      acc[c] = zc;
+      h[c] = gelu_f(zc);
+    }
+    if (a.zout) {
+      float4* zo = reinterpret_cast<float4*>(a.zout + ((size_t)b * N3 + v) * CH);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+    store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, h);
+  } else if (MODE == CONV_OUT_Y) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a.y[((size_t)b * 5 + c) * N3 + v] = acc[c] + __ldg(a.bias + c);
+  } else if (MODE == CONV_OUT_APPLY) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float* g = a.gas + ((size_t)b * 5 + c) * N3 + v;
+      *g += a.scale.v[c] * (acc[c] + __ldg(a.bias + c));
+    }
+  } else {  // CONV_BWD
+    const float4* zp = reinterpret_cast<const float4*>(a.zprev + ((size_t)b * N3 + v) * CH);
+    float d[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 zz = __ldg(zp + q);
+      d[4 * q] = acc[4 * q] * gelu_grad_f(zz.x);
+      d[4 * q + 1] = acc[4 * q + 1] * gelu_grad_f(zz.y);
+      d[4 * q + 2] = acc[4 * q + 2] * gelu_grad_f(zz.z);
+      d[4 * q + 3] = acc[4 * q + 3] * gelu_grad_f(zz.w);
+    }
+    store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, d);
+  }
+}
 
-  // 1. stage 3 planes x (L + 2) lines x P positions (periodic) with asynchronous 16-byte
-  //    copies (every copy of the CTA in flight at once), zero the slack
-  const int nreg = 3 * (L + 2) * P;
-  const uint32_t sa0 = smem_u32(sa) + SLK_BEFORE * 16;
-  for (int pos = tid; pos < nreg; pos += 128) {
-    const int pz = pos / ((L + 2) * P);
-    const int rem = pos - pz * (L + 2) * P;
-    const int ly = rem / P, px = rem - ly * P;
-    const int gx = wrapi(px - 1, n), gy = wrapi(y0 - 1 + ly, n), gz = wrapi(z - 1 + pz, n);
-    const bf16* src = in + (((size_t)gz * n + gy) * n + gx) * CH;
-    const uint32_t d = sa0 + (uint32_t)pos * 16u;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + (uint32_t)plane_bytes),
-                 "l"(src + 8) : "memory");
+template <int MODE>
+__global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int n = a.n;
+  const long long N3 = (long long)n * n * n;
+  const int b = blockIdx.z, y0 = blockIdx.x * a.L, z0 = blockIdx.y * a.Zc;
+  const int nz = min(a.Zc, n - z0);  // output planes of this CTA
+  const int nin = nz + 2;            // input planes z0 - 1 .. z0 + nz
+  const int tid = threadIdx.x;
+  const int w = tid >> 5, lane = tid & 31;
+  const uint32_t slot_bytes = 2u * (uint32_t)a.slot_pos * 16u;
+  uint8_t* sa = smem;
+  uint8_t* sw = smem + RING * slot_bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sw + 9 * 1536);  // two, by input parity
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  int* sflag = reinterpret_cast<int*>(tslot + 1);
+  const bf16* in = a.in + (size_t)b * N3 * CH;
+  const uint32_t sa0 = smem_u32(sa);
+
+  // inputs 0, 1, 2 (planes z0 - 1 .. z0 + 1) into slots 0..2: commit groups 0..2
+  for (int i = 0; i < RING; ++i) {
+    if (i < nin) conv_fetch_plane(a, in, sa0 + (uint32_t)i * slot_bytes, z0 - 1 + i, a.L, y0, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  for (int i = tid; i < SLK_BEFORE + SLK_AFTER; i += 128) {
-    const int slot = i < SLK_BEFORE ? i : SLK_BEFORE + nreg + (i - SLK_BEFORE);
-    *reinterpret_cast<uint4*>(sa + (size_t)slot * 16) = make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(sa + plane_bytes + (size_t)slot * 16) = make_uint4(0u, 0u, 0u, 0u);
+  const int nslack = SLK_BEFORE + SLK_AFTER;
+  for (int i = tid; i < RING * 2 * nslack; i += CONV_THREADS) {
+    const int sp = i / nslack, k = i - sp * nslack;
+    const int pos = k < SLK_BEFORE ? k : a.slot_pos - SLK_AFTER + (k - SLK_BEFORE);
+    *reinterpret_cast<uint4*>(sa + (size_t)sp * a.slot_pos * 16 + (size_t)pos * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
   }
-  for (int i = tid; i < 27 * 512 / 16; i += 128)
+  for (int i = tid; i < 9 * 1536 / 16; i += CONV_THREADS)
     reinterpret_cast<uint4*>(sw)[i] = __ldg(reinterpret_cast<const uint4*>(a.w) + i);
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (tid == 0) mbar_init(mbar, 1);
-  fence_async_smem();
-  __syncthreads();
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(mbar + 1, 1);
+    *sflag = 0;
+  }
   if (tid < 32) tmem_alloc_warp(tslot, (uint32_t)a.ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  tmem_zero(tmem, a.ncols, w);
+  const uint32_t idesc = umma_idesc_bf16(128, 48);
+  const uint64_t a_base = umma_desc(sa0, (uint32_t)a.slot_pos * 16u, 128u);
+  const uint64_t b_base = umma_desc(smem_u32(sw), 768u, 128u);
+  const uint32_t slot_units = slot_bytes >> 4;
+  const int ZP = a.Zc + 4;
 
-  // 2. one thread issues T tiles x 27 taps
-  if (tid == 0) {
-    const uint32_t idesc = umma_idesc_bf16(128, 16);
-    const uint32_t a0 = smem_u32(sa) + SLK_BEFORE * 16;
-    const uint32_t w0 = smem_u32(sw);
-    for (int t = 0; t < a.T; ++t) {
-      int vb;
-      if (a.contig) {
-        vb = 128 * t;
-      } else {
-        const int ly = t / a.tpl;
-        vb = ly * P + 1 + 128 * (t - ly * a.tpl);
-      }
-      for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const int pos = ((dz + 1) * (L + 2) + 1 + dy) * P + dx + vb;
-        const uint64_t da = umma_desc(a0 + (uint32_t)pos * 16u, (uint32_t)plane_bytes, 128u);
-        const uint64_t db = umma_desc(w0 + (uint32_t)tap * 512u, 256u, 128u);
-        umma_bf16(tmem + 16u * (uint32_t)t, da, db, idesc, tap > 0 ? 1u : 0u);
+  for (int i = 0; i < nin; ++i) {
+    // input i has landed: group i for i < 3, group i + 1 after (one group per iteration)
+    if (i < 3)
+      asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      conv_issue_input(a, i, tmem, a_base, b_base, slot_units, idesc);
+      umma_commit(mbar + (i & 1));
+      if (i >= 1 && !mbar_wait_bounded(mbar + ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), 1 << 24))
+        *sflag = 1;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (*sflag) break;
+    // input i - 1 is consumed: its slot takes input i + 2
+    if (i >= 1 && i + 2 < nin)
+      conv_fetch_plane(a, in, sa0 + (uint32_t)((i + 2) % RING) * slot_bytes, z0 + 1 + i, a.L, y0, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // output plane q = z0 - 3 + i (TMEM plane i - 1) is complete: its epilogue overlaps
+    // the MMAs of input i
+    const int q = z0 - 3 + i;
+    if (i >= 3 && q < z0 + nz) {
+      for (int t = w >> 2; t < a.T; t += CONV_THREADS / 128) {
+        float acc[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)(t * ZP + i - 1), acc);
+        conv_epilogue<MODE>(a, acc, b, q, y0, t, 32 * (w & 3) + lane);
       }
     }
-    umma_commit(mbar);
   }
-  const uint32_t done = mbar_wait_bounded(mbar, 0, 1 << 24);
-  const int all_done = __syncthreads_and((int)done);
+  // the last output plane (TMEM plane nz + 1) after the last input's MMAs
+  if (tid == 0 && !*sflag &&
+      !mbar_wait_bounded(mbar + ((nin - 1) & 1), (uint32_t)(((nin - 1) >> 1) & 1), 1 << 24))
+    *sflag = 1;
+  __syncthreads();
   tc_fence_after();
-  if (!all_done) {
-    if (tid == 0) atomicExch(a.err, 1);
-  } else {
-    const int w = tid >> 5, lane = tid & 31;
-    for (int t = 0; t < a.T; ++t) {
+  if (!*sflag) {
+    for (int t = w >> 2; t < a.T; t += CONV_THREADS / 128) {
       float acc[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * w) << 16) + 16u * (uint32_t)t, acc);
-      const int r = 32 * w + lane;
-      int ly, x;
-      bool valid;
-      if (a.contig) {
-        const int v = 128 * t + r;
-        ly = v / P;
-        const int px = v - ly * P;
-        x = px - 1;
-        valid = px >= 1 && px <= n && ly < L;
-      } else {
-        ly = t / a.tpl;
-        x = 128 * (t - ly * a.tpl) + r;
-        valid = x < n;
-      }
-      const int gy = y0 + ly;
-      if (!valid || gy >= n) continue;
-      const size_t v = ((size_t)z * n + gy) * n + x;
-      if (MODE == CONV_HIDDEN) {
-        float h[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float zc = acc[c] + __ldg(a.bias + c);
-          acc[c] = zc;
-          h[c] = gelu_f(zc);
-        }
-        if (a.zout) {
-          float4* zo = reinterpret_cast<float4*>(a.zout + ((size_t)b * N3 + v) * CH);
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-        }
-        store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, h);
-      } else if (MODE == CONV_OUT_Y) {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) a.y[((size_t)b * 5 + c) * N3 + v] = acc[c] + __ldg(a.bias + c);
-      } else if (MODE == CONV_OUT_APPLY) {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          float* g = a.gas + ((size_t)b * 5 + c) * N3 + v;
-          *g += a.scale.v[c] * (acc[c] + __ldg(a.bias + c));
-        }
-      } else {  // CONV_BWD
-        const float4* zp = reinterpret_cast<const float4*>(a.zprev + ((size_t)b * N3 + v) * CH);
-        float d[16];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 zz = __ldg(zp + q);
-          d[4 * q] = acc[4 * q] * gelu_grad_f(zz.x);
-          d[4 * q + 1] = acc[4 * q + 1] * gelu_grad_f(zz.y);
-          d[4 * q + 2] = acc[4 * q + 2] * gelu_grad_f(zz.z);
-          d[4 * q + 3] = acc[4 * q + 3] * gelu_grad_f(zz.w);
-        }
-        store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, d);
-      }
+      tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)(t * ZP + nz + 1), acc);
+      conv_epilogue<MODE>(a, acc, b, z0 + nz - 1, y0, t, 32 * (w & 3) + lane);
     }
+  } else if (tid == 0) {
+    atomicExch(a.err, 1);
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   if (tid < 32) tmem_dealloc_warp(tmem, (uint32_t)a.ncols);
@@ -302,7 +408,7 @@ static sim_status prepare_conv_kernels() {
 }
 
 static sim_status launch_conv(int mode, ConvArgs a, int B, cudaStream_t st) {
-  const ConvGeom g = conv_geom(a.n);
+  const ConvGeom g = conv_geom(a.n, B);
   if (g.smem > 200 * 1024) {
     set_error("closure: grid n = %d needs %zu bytes of shared memory per CTA", a.n, g.smem);
     return SIM_EINVAL;
@@ -312,14 +418,15 @@ static sim_status launch_conv(int mode, ConvArgs a, int B, cudaStream_t st) {
   a.T = g.T;
   a.tpl = g.tpl;
   a.contig = g.contig;
-  a.pos_total = g.pos_total;
+  a.Zc = g.Zc;
+  a.slot_pos = g.slot_pos;
   a.ncols = g.ncols;
-  const dim3 grid(cdiv(a.n, g.L), a.n, B);
+  const dim3 grid(cdiv(a.n, g.L), cdiv(a.n, g.Zc), B);
   switch (mode) {
-    case CONV_HIDDEN: conv3_kernel<CONV_HIDDEN><<<grid, 128, g.smem, st>>>(a); break;
-    case CONV_OUT_Y: conv3_kernel<CONV_OUT_Y><<<grid, 128, g.smem, st>>>(a); break;
-    case CONV_OUT_APPLY: conv3_kernel<CONV_OUT_APPLY><<<grid, 128, g.smem, st>>>(a); break;
-    default: conv3_kernel<CONV_BWD><<<grid, 128, g.smem, st>>>(a); break;
+    case CONV_HIDDEN: conv3_kernel<CONV_HIDDEN><<<grid, CONV_THREADS, g.smem, st>>>(a); break;
+    case CONV_OUT_Y: conv3_kernel<CONV_OUT_Y><<<grid, CONV_THREADS, g.smem, st>>>(a); break;
+    case CONV_OUT_APPLY: conv3_kernel<CONV_OUT_APPLY><<<grid, CONV_THREADS, g.smem, st>>>(a); break;
+    default: conv3_kernel<CONV_BWD><<<grid, CONV_THREADS, g.smem, st>>>(a); break;
   }
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -467,20 +574,23 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g,
   w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
-// packed forward weights: wf[l][tap][kc][co][j] = W[l][tap][8 kc + j][co];
-// packed backward weights: wb[l][tap][kc][ci][j] = W[l][26 - tap][ci][8 kc + j]
+// Packed weights, per layer 9 blocks (dy, dx) of [kc][48 rows][8]: row 16 d + c holds output
+// channel c of tap dz = 1 - d (the input plane's contribution to output planes p - 1, p,
+// p + 1 in that order), K = input channel 8 kc + e. Forward: W[tap][k][c]; backward (the
+// transposed, mirrored convolution): W[26 - tap][c][k].
 __global__ void repack_kernel(const float* __restrict__ W, bf16* __restrict__ wf,
                               bf16* __restrict__ wb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over NL * 27 * 256
-  if (i >= NL * 27 * 256) return;
-  const int l = i / (27 * 256);
-  const int r = i - l * 27 * 256;
-  const int tap = r / 256, e = r % 256;
-  const int kc = e / 128, row = (e / 8) % 16, j = e % 8;
-  const int k = 8 * kc + j;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over NL * PACK
+  if (i >= NL * PACK) return;
+  const int l = i / PACK;
+  const int r = i - l * PACK;
+  const int j = r / 768, e = r % 768;
+  const int kc = e / 384, row = (e / 8) % 48, el = e % 8;
+  const int dz = 1 - row / 16, c = row % 16, k = 8 * kc + el;
+  const int tap = (dz + 1) * 9 + j;
   const float* Wl = W + (size_t)l * WL;
-  wf[i] = __float2bfloat16_rn(Wl[(tap * CH + k) * CH + row]);
-  wb[i] = __float2bfloat16_rn(Wl[((26 - tap) * CH + row) * CH + k]);
+  wf[i] = __float2bfloat16_rn(Wl[(tap * CH + k) * CH + c]);
+  wb[i] = __float2bfloat16_rn(Wl[((26 - tap) * CH + c) * CH + k]);
 }
 
 }  // namespace dh
@@ -640,7 +750,7 @@ static sim_status closure_backprop(sim_closure_s* c, const float* gas, const flo
 }
 
 static sim_status repack(sim_closure_s* c, cudaStream_t st) {
-  repack_kernel<<<cdiv(NL * 27 * 256, 256), 256, 0, st>>>(c->prm, c->wf, c->wb);
+  repack_kernel<<<cdiv(NL * PACK, 256), 256, 0, st>>>(c->prm, c->wf, c->wb);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

@@ -166,6 +166,51 @@ def run_params(n: int, n_steps: int):
                           T_init=1e4)
 
 
+def experiment(n: int = 64, seeds: int = 6, run_steps: int = 100, iters: int = 600,
+               batch: int = 2, lr: float = 2e-3, eval_n: int = 256, fine_eval: bool = True):
+    """Pairs, training, held-out loss, a-posteriori run error at n, and the trained network
+    in eval_n^3 runs (cost with and without it, field error against the 2 eval_n run)."""
+    p = run_params(n, run_steps)
+    t0 = time.perf_counter()
+    pairs = make_pairs(p, range(1, seeds + 1), run_steps)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    mu, sigma, scale = normalisation(pairs)
+    clo = api.Closure(_init_weights(0))
+    clo.set_norm(mu, sigma, scale)
+    held = make_pairs(p, [1000], run_steps)[::10]
+    before, plain_loss = pair_loss(clo, held)
+    t0 = time.perf_counter()
+    losses = train(clo, pairs, iters, lr, batch, lr_final=lr / 10)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    after, _ = pair_loss(clo, held)
+    res = {"pairs": len(pairs), "grid": n, "fine_grid": 2 * n,
+           "run": f"{run_steps} steps a=0.1->1.0, box n Mpc/h",
+           "pair_seconds": t_pairs, "train_seconds": t_train, "iters": iters,
+           "batch": batch, "train_loss_first": float(losses[:10].mean()),
+           "train_loss_last": float(losses[-10:].mean()),
+           "heldout_loss_plain_solver": plain_loss, "heldout_loss_untrained": before,
+           "heldout_loss_trained": after,
+           "run_error": evaluate(p, 2000, clo)}
+    if eval_n:
+        pl = run_params(eval_n, run_steps)
+        clo_eval = api.Closure(clo.weights())
+        clo_eval.set_norm(mu, sigma, scale)
+        ms_plain = timed_run(pl)
+        ms_clo = timed_run(pl, clo_eval)
+        cells = eval_n ** 3 * run_steps
+        res["apply"] = {"grid": eval_n, "steps": run_steps,
+                        "plain_cell_steps_per_s": cells / (ms_plain / 1e3),
+                        "closure_cell_steps_per_s": cells / (ms_clo / 1e3),
+                        "plain_ms": ms_plain, "closure_ms": ms_clo}
+        if fine_eval:
+            res["apply"]["field_error"] = evaluate(pl, 3000, clo_eval)
+        clo_eval.close()
+    clo.close()
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
@@ -176,47 +221,10 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--eval-n", type=int, default=256)
     ap.add_argument("--no-fine-eval", action="store_true")
-    args = ap.parse_args(argv)
-    p = run_params(args.n, args.run_steps)
-    t0 = time.perf_counter()
-    pairs = make_pairs(p, range(1, args.seeds + 1), args.run_steps)
-    torch.cuda.synchronize()
-    t_pairs = time.perf_counter() - t0
-    mu, sigma, scale = normalisation(pairs)
-    clo = api.Closure(_init_weights(0))
-    clo.set_norm(mu, sigma, scale)
-    held = make_pairs(p, [1000], args.run_steps)[::10]
-    before, plain_loss = pair_loss(clo, held)
-    t0 = time.perf_counter()
-    losses = train(clo, pairs, args.iters, args.lr, args.batch, lr_final=args.lr / 10)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    after, _ = pair_loss(clo, held)
-    res = {"pairs": len(pairs), "grid": args.n, "fine_grid": 2 * args.n,
-           "run": f"{args.run_steps} steps a=0.1->1.0, box n Mpc/h",
-           "pair_seconds": t_pairs, "train_seconds": t_train, "iters": args.iters,
-           "batch": args.batch, "train_loss_first": float(losses[:10].mean()),
-           "train_loss_last": float(losses[-10:].mean()),
-           "heldout_loss_plain_solver": plain_loss, "heldout_loss_untrained": before,
-           "heldout_loss_trained": after,
-           "run_error": evaluate(p, 2000, clo)}
-    # the trained network in larger runs: cost and field error with and without it
-    if args.eval_n:
-        pl = run_params(args.eval_n, args.run_steps)
-        clo_eval = api.Closure(clo.weights())
-        clo_eval.set_norm(mu, sigma, scale)
-        ms_plain = timed_run(pl)
-        ms_clo = timed_run(pl, clo_eval)
-        cells = args.eval_n ** 3 * args.run_steps
-        res["apply"] = {"grid": args.eval_n, "steps": args.run_steps,
-                        "plain_cell_steps_per_s": cells / (ms_plain / 1e3),
-                        "closure_cell_steps_per_s": cells / (ms_clo / 1e3),
-                        "plain_ms": ms_plain, "closure_ms": ms_clo}
-        if not args.no_fine_eval:
-            res["apply"]["field_error"] = evaluate(pl, 3000, clo_eval)
-        clo_eval.close()
+    a = ap.parse_args(argv)
+    res = experiment(a.n, a.seeds, a.run_steps, a.iters, a.batch, a.lr, a.eval_n,
+                     not a.no_fine_eval)
     print(json.dumps(res), flush=True)
-    clo.close()
     return res
 
 
