@@ -64,7 +64,7 @@ struct ConvGeom {
 static int slot_positions(int L, int P) { return SLK_BEFORE + (L + 2) * P + SLK_AFTER; }
 
 static size_t conv_smem(int L, int P) {
-  return (size_t)RING * 2 * slot_positions(L, P) * 16 + 9 * 1536 + 32;  // + mbarriers, flags
+  return (size_t)RING * 2 * slot_positions(L, P) * 16 + 9 * 1536 + 2 * 20 * 8 + 16;  // + barriers
 }
 
 static ConvGeom conv_geom(int n, int B) {
@@ -160,12 +160,12 @@ struct ConvArgs {
 
 // fetch input plane gz (periodic) into ring slot `slot`: (L + 2) lines x P positions
 __device__ __forceinline__ void conv_fetch_plane(const ConvArgs& a, const bf16* in, uint32_t slot_addr,
-                                                 int gz, int L_unused, int y0, int tid) {
+                                                 int gz, int nthreads, int y0, int tid) {
   const int n = a.n, P = a.P, L = a.L;
   const uint32_t plane_bytes = (uint32_t)a.slot_pos * 16u;
   const int npos = (L + 2) * P;
   gz = gz < 0 ? gz + n : (gz >= n ? gz - n : gz);
-  for (int pos = tid; pos < npos; pos += CONV_THREADS) {
+  for (int pos = tid; pos < npos; pos += nthreads) {
     const int ly = pos / P, px = pos - ly * P;
     int gx = px - 1;
     gx = gx < 0 ? gx + n : (gx >= n ? gx - n : gx);
@@ -287,6 +287,14 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc
   }
 }
 
+// Warp roles: warps 0-1 fetch input planes (cp.async, then a proxy fence and an mbarrier
+// arrive per plane), warp 2 lane 0 issues the MMAs of each plane once it has landed and
+// commits them to that plane's barrier, warps 4-7 run the epilogue of every output plane
+// once its last input's MMAs are done. Every barrier is used once (one per input plane),
+// every wait is bounded; a timeout sets an error flag and the CTA still frees its TMEM.
+constexpr int MAX_IN = 20;  // input planes per CTA (Zc + 2)
+constexpr int LOADERS = 64;
+
 template <int MODE>
 __global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -300,17 +308,15 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
   const uint32_t slot_bytes = 2u * (uint32_t)a.slot_pos * 16u;
   uint8_t* sa = smem;
   uint8_t* sw = smem + RING * slot_bytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sw + 9 * 1536);  // two, by input parity
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sw + 9 * 1536);  // [MAX_IN]: input landed
+  uint64_t* done = full + MAX_IN;                                // [MAX_IN]: its MMAs done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + MAX_IN);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const bf16* in = a.in + (size_t)b * N3 * CH;
   const uint32_t sa0 = smem_u32(sa);
+  const int limit = 1 << 24;
 
-  // inputs 0, 1, 2 (planes z0 - 1 .. z0 + 1) into slots 0..2: commit groups 0..2
-  for (int i = 0; i < RING; ++i) {
-    if (i < nin) conv_fetch_plane(a, in, sa0 + (uint32_t)i * slot_bytes, z0 - 1 + i, a.L, y0, tid);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
+  // setup: slack zeroed, weights staged, barriers, TMEM allocated and zeroed
   const int nslack = SLK_BEFORE + SLK_AFTER;
   for (int i = tid; i < RING * 2 * nslack; i += CONV_THREADS) {
     const int sp = i / nslack, k = i - sp * nslack;
@@ -321,75 +327,85 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
   for (int i = tid; i < 9 * 1536 / 16; i += CONV_THREADS)
     reinterpret_cast<uint4*>(sw)[i] = __ldg(reinterpret_cast<const uint4*>(a.w) + i);
   if (tid == 0) {
-    mbar_init(mbar, 1);
-    mbar_init(mbar + 1, 1);
+    for (int i = 0; i < MAX_IN; ++i) {
+      mbar_init(full + i, LOADERS);
+      mbar_init(done + i, 1);
+    }
     *sflag = 0;
   }
-  if (tid < 32) tmem_alloc_warp(tslot, (uint32_t)a.ncols);
+  if (w == 0) tmem_alloc_warp(tslot, (uint32_t)a.ncols);
+  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
   tmem_zero(tmem, a.ncols, w);
-  const uint32_t idesc = umma_idesc_bf16(128, 48);
-  const uint64_t a_base = umma_desc(sa0, (uint32_t)a.slot_pos * 16u, 128u);
-  const uint64_t b_base = umma_desc(smem_u32(sw), 768u, 128u);
-  const uint32_t slot_units = slot_bytes >> 4;
-  const int ZP = a.Zc + 4;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
-  for (int i = 0; i < nin; ++i) {
-    // input i has landed: group i for i < 3, group i + 1 after (one group per iteration)
-    if (i < 3)
-      asm volatile("cp.async.wait_group 2;" ::: "memory");
-    else
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) {
-      conv_issue_input(a, i, tmem, a_base, b_base, slot_units, idesc);
-      umma_commit(mbar + (i & 1));
-      if (i >= 1 && !mbar_wait_bounded(mbar + ((i - 1) & 1), (uint32_t)(((i - 1) >> 1) & 1), 1 << 24))
-        *sflag = 1;
+  if (w < 2) {
+    // ---- loaders: input i into slot i mod RING once input i - RING's MMAs are done
+    for (int i = 0; i <= nin; ++i) {
+      if (i < nin) {
+        if (i >= RING && !mbar_wait_bounded(done + (i - RING), 0, limit)) {
+          *sflag = 1;
+          break;
+        }
+        conv_fetch_plane(a, in, sa0 + (uint32_t)(i % RING) * slot_bytes, z0 - 1 + i, LOADERS, y0, tid);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      if (i >= 1) {
+        // input i - 1 has landed (only the newest group may be in flight)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        fence_async_smem();
+        uint64_t state;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+                     : "=l"(state)
+                     : "r"(smem_u32(full + i - 1))
+                     : "memory");
+        (void)state;
+      }
     }
-    __syncthreads();
-    tc_fence_after();
-    if (*sflag) break;
-    // input i - 1 is consumed: its slot takes input i + 2
-    if (i >= 1 && i + 2 < nin)
-      conv_fetch_plane(a, in, sa0 + (uint32_t)((i + 2) % RING) * slot_bytes, z0 + 1 + i, a.L, y0, tid);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    // output plane q = z0 - 3 + i (TMEM plane i - 1) is complete: its epilogue overlaps
-    // the MMAs of input i
-    const int q = z0 - 3 + i;
-    if (i >= 3 && q < z0 + nz) {
-      for (int t = w >> 2; t < a.T; t += CONV_THREADS / 128) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else if (w == 2) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_bf16(128, 48);
+      const uint64_t a_base = umma_desc(sa0, (uint32_t)a.slot_pos * 16u, 128u);
+      const uint64_t b_base = umma_desc(smem_u32(sw), 768u, 128u);
+      const uint32_t slot_units = slot_bytes >> 4;
+      for (int i = 0; i < nin; ++i) {
+        if (!mbar_wait_bounded(full + i, 0, limit)) {
+          *sflag = 1;
+          break;
+        }
+        tc_fence_after();
+        conv_issue_input(a, i, tmem, a_base, b_base, slot_units, idesc);
+        umma_commit(done + i);
+      }
+    }
+    __syncwarp();
+  } else if (w >= 4) {
+    // ---- epilogue: output plane z0 + jj is final once input jj + 2 is in
+    const int ZP = a.Zc + 4;
+    for (int jj = 0; jj < nz; ++jj) {
+      if (!mbar_wait_bounded(done + jj + 2, 0, limit)) {
+        *sflag = 1;
+        break;
+      }
+      tc_fence_after();
+      for (int t = 0; t < a.T; ++t) {
         float acc[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)(t * ZP + i - 1), acc);
-        conv_epilogue<MODE>(a, acc, b, q, y0, t, 32 * (w & 3) + lane);
+        tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)(t * ZP + jj + 2), acc);
+        conv_epilogue<MODE>(a, acc, b, z0 + jj, y0, t, 32 * (w & 3) + lane);
       }
     }
   }
-  // the last output plane (TMEM plane nz + 1) after the last input's MMAs
-  if (tid == 0 && !*sflag &&
-      !mbar_wait_bounded(mbar + ((nin - 1) & 1), (uint32_t)(((nin - 1) >> 1) & 1), 1 << 24))
-    *sflag = 1;
-  __syncthreads();
-  tc_fence_after();
-  if (!*sflag) {
-    for (int t = w >> 2; t < a.T; t += CONV_THREADS / 128) {
-      float acc[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)(t * ZP + nz + 1), acc);
-      conv_epilogue<MODE>(a, acc, b, z0 + nz - 1, y0, t, 32 * (w & 3) + lane);
-    }
-  } else if (tid == 0) {
-    atomicExch(a.err, 1);
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
-  if (tid < 32) tmem_dealloc_warp(tmem, (uint32_t)a.ncols);
+  if (tid == 0 && *sflag) atomicExch(a.err, 1);
+  if (w == 0) tmem_dealloc_warp(tmem, (uint32_t)a.ncols);
 }
 
 static sim_status prepare_conv_kernels() {
