@@ -11,7 +11,8 @@ value     cell-steps/s of that pass = 128^3 * 100 / time, summed over ranks (rep
 e2e       the same through the C ABI with the noise copied from pinned host memory and
           the noise gradient plus the loss copied back inside the timed region.
 roofline  the dominant kernel class (hydro sweeps or their adjoints), each launch timed with
-          CUDA events on the simulation stream during one eager pass of the same hot path.
+          CUDA events on the simulation stream during one eager pass of the same hot path;
+          roofline.classes holds that pass's time per stage of the step and adjoint.
 cpu_baseline  the FP64 oracle on the host cores on a bounded sample of the same workload.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -44,6 +45,9 @@ SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, i
 # DRAM bytes per cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
 # captures summarised in profiles/; None where no capture of the current kernel exists
 TRAFFIC_BYTES_PER_CELL = {"sweep": 21.06, "sweep_adjoint": 97.99}  # 128^3, cold cache
+# algorithmic bytes per cell of one timed launch group of each class (one particle per cell)
+CLASS_BYTES_PER_CELL = {"sweep": SWEEP_BYTES_PER_CELL, "sweep_adjoint": SWEEP_ADJ_BYTES_PER_CELL,
+                        "deposit": 28, "poisson": 16, "subgrid": 44, "subgrid_adjoint": 60}
 
 
 BATCH_SIZES = (32, 48, 64)
@@ -409,13 +413,13 @@ def main():
     kt = sim.kernel_times(reset=True)
     sim.kernel_timing(False)
     kclass = {}
-    for name, bpc in (("sweep", SWEEP_BYTES_PER_CELL), ("sweep_adjoint", SWEEP_ADJ_BYTES_PER_CELL)):
-        tot, cnt = kt[name]
+    for name, (tot, cnt) in kt.items():
         avg = tot / max(cnt, 1)
+        bpc = CLASS_BYTES_PER_CELL.get(name)
         kclass[name] = {"launches": cnt, "total_ms": tot, "share_of_pass": tot / inst_ms,
                         "avg_launch_ms": avg,
-                        "achieved_gbs": bpc * n3 / (avg * 1e-3) / 1e9 if cnt else None}
-    dom = max(kclass, key=lambda k: kclass[k]["total_ms"])
+                        "achieved_gbs": (bpc * n3 / (avg * 1e-3) / 1e9) if (cnt and bpc) else None}
+    dom = max(("sweep", "sweep_adjoint"), key=lambda k: kclass[k]["total_ms"])
 
     # ---- batched parameter-sampling form (96 instances on three grid sizes)
     batched = None

@@ -209,11 +209,19 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
 sim_status sim_set_graphs(sim_t* h, int32_t on);
 
 /* Kernel classes timed by sim_kernel_timing. The paper has no counterpart: these exist to
- * measure the sweep kernels of Sec. 2.3 inside a real run. */
+ * measure the stages of the step (Secs. 2.2-2.4) and their adjoints inside a real run. */
 enum {
-  SIM_KT_SWEEP = 0,          /* forward sweeps, including the reverse pass's recompute */
-  SIM_KT_SWEEP_ADJOINT = 1,  /* adjoint sweeps */
-  SIM_KT_N = 2
+  SIM_KT_SWEEP = 0,            /* forward sweeps, including the reverse pass's recompute */
+  SIM_KT_SWEEP_ADJOINT = 1,    /* adjoint sweeps */
+  SIM_KT_KICK = 2,             /* particle kick + drift, gas kick */
+  SIM_KT_KICK_ADJOINT = 3,     /* their adjoints */
+  SIM_KT_DEPOSIT = 4,          /* CIC deposit and fixed-point conversion */
+  SIM_KT_DEPOSIT_ADJOINT = 5,  /* deposit adjoint (CIC gradient readout) */
+  SIM_KT_POISSON = 6,          /* r2c, Green's function, 3 c2r */
+  SIM_KT_POISSON_ADJOINT = 7,  /* its adjoint, with the force dot product */
+  SIM_KT_SUBGRID = 8,          /* subgrid step */
+  SIM_KT_SUBGRID_ADJOINT = 9,  /* its adjoint */
+  SIM_KT_N = 10
 };
 
 /* enable != 0: later sim_step / sim_run / sim_step_adjoint / sim_run_adjoint calls run

@@ -17,7 +17,10 @@ SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ECFL, SIM_ENAN, SIM_ETIMEOUT, SIM
 STATUS_NAMES = ["SIM_OK", "SIM_EINVAL", "SIM_ENOMEM", "SIM_ECUDA", "SIM_ECFL", "SIM_ENAN",
                 "SIM_ETIMEOUT", "SIM_ENOTIMPL"]
 P_OMEGA_M, P_SIGMA8, P_DELTA_C, P_PI0, P_E0, P_T0_UV, P_GAMMA_UV, NPARAMS = range(8)
-KT_SWEEP, KT_SWEEP_ADJOINT, KT_N = range(3)
+KT_NAMES = ("sweep", "sweep_adjoint", "kick", "kick_adjoint", "deposit", "deposit_adjoint",
+            "poisson", "poisson_adjoint", "subgrid", "subgrid_adjoint")
+KT_N = len(KT_NAMES)
+KT_SWEEP, KT_SWEEP_ADJOINT = 0, 1
 SWEEP_DEFAULT, SWEEP_TILE, SWEEP_MARCH32, SWEEP_MARCH16 = range(4)
 CLOSURE_NWEIGHTS = 18197
 PARAM_NAMES = ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"]

@@ -11,7 +11,7 @@ import torch
 
 import numpy as np
 
-from ._lib import (CLOSURE_NWEIGHTS, KT_N, KT_SWEEP, KT_SWEEP_ADJOINT, NPARAMS, SimParams,
+from ._lib import (CLOSURE_NWEIGHTS, KT_N, KT_NAMES, NPARAMS, SimParams,
                    check, default_params, lib)
 
 F32, F64, U32 = torch.float32, torch.float64, torch.int32
@@ -299,8 +299,7 @@ class Simulation:
         ms = (ctypes.c_double * KT_N)()
         cnt = (ctypes.c_int64 * KT_N)()
         self._check(lib.sim_kernel_times(self.h, ms, cnt, int(reset)), "sim_kernel_times")
-        return {"sweep": (ms[KT_SWEEP], cnt[KT_SWEEP]),
-                "sweep_adjoint": (ms[KT_SWEEP_ADJOINT], cnt[KT_SWEEP_ADJOINT])}
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(KT_NAMES)}
 
 
 def _host_f32(a, count, name):

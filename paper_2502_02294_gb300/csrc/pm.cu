@@ -388,9 +388,9 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
     p[j * N3 + i] = pj;
     if (dtau != 0.0f) s[j * N3 + i] += dtau * pj;
   }
+  // star readout at the position the kick saw (before this launch's drift)
   if (zhat) {
     zhat += (size_t)q.b * N3;
-    cic_setup(s, q, N3, n, inv_dx, c);
     float acc = 0.0f;
 #pragma unroll
     for (int oz = 0; oz < 2; ++oz)

@@ -50,7 +50,7 @@ sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftCom
 sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
                          float* out, int B, cudaStream_t st);
 // p += K interp(g, s); then, if dtau != 0, s += dtau p. If zhat != NULL also
-// aux += interp(zhat, s) (after the drift).
+// aux += interp(zhat, s) at the position before the drift.
 sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
                              const float* zhat, float* aux, int n, float inv_dx, int B,
                              cudaStream_t st);

@@ -60,12 +60,13 @@ static const char* kOrders[6] = {"xyz", "zyx", "zxy", "yxz", "yzx", "xzy"};
 
 // per-step partial sums of the reverse pass (doubles on the device), and the chain-rule
 // coefficient of each with respect to Omega_m
-enum { SL_DK1 = 0, SL_DK2, SL_DNU, SL_DDTAU, SL_DPREF, SL_DCM, SL_DFB, SL_N = 8 };
+// SL_DKM: the merged kick K2_{i-1} + K1_i that opens step i inside a checkpoint segment
+enum { SL_DK1 = 0, SL_DK2, SL_DNU, SL_DDTAU, SL_DPREF, SL_DCM, SL_DFB, SL_DKM, SL_N = 8 };
 // extra global partials after the SIM_NPARAMS subgrid ones (per instance: NG doubles)
 enum { GX_DRP = 0, GX_DFB_IC = 1, GX_LAMC = 2, GX_N = 8 };
 constexpr int NG = SIM_NPARAMS + GX_N;
 // per-step float constants of every instance (device table [n_steps][SC_N][B])
-enum { SC_K1 = 0, SC_K2, SC_DTAU, SC_NU, SC_PN1, SC_N };
+enum { SC_K1 = 0, SC_K2, SC_DTAU, SC_NU, SC_PN1, SC_KM, SC_N };
 // per-instance chain-rule constants of the parameter derivatives (device [B][PCH_N])
 enum { PCH_CCM0 = 0, PCH_DLNC, PCH_DRP, PCH_DFB, PCH_INVS8, PCH_N };
 
@@ -420,22 +421,31 @@ static sim_status part_split(float* s, float* p, const float* src6, const sim_t*
 static sim_status compute_force(sim_t* h, const float* s, const float* gas, SArg pn, float* g) {
   const int B = h->B;
   if (!h->prm.gravity_on) return dzero(g, 3 * B * h->N3 * sizeof(float), h->st);
-  DH_TRY(launch_deposit(s, nullptr, h->n, (float)h->inv_dx, h->acc, B, h->st));
-  DH_TRY(launch_fix_to_float(h->acc, sarg(h->d_cm), gas, (int)(5 * h->N3), -1.0f, h->delta,
-                             h->n, B, h->st));
-  return launch_gravity(h->delta, g, h->ck, h->ck + B * h->NC, h->n, h->prm.box, pn, B,
-                        h->plans, h->st);
+  DH_TRY(timed(h, SIM_KT_DEPOSIT, [&] {
+    DH_TRY(launch_deposit(s, nullptr, h->n, (float)h->inv_dx, h->acc, B, h->st));
+    return launch_fix_to_float(h->acc, sarg(h->d_cm), gas, (int)(5 * h->N3), -1.0f, h->delta,
+                               h->n, B, h->st);
+  }));
+  return timed(h, SIM_KT_POISSON, [&] {
+    return launch_gravity(h->delta, g, h->ck, h->ck + B * h->NC, h->n, h->prm.box, pn, B,
+                          h->plans, h->st);
+  });
 }
 
 // One forward step in place on (gas/gas_tmp ping-pong, s, p, g). With tape != nullptr the
 // inputs of every stage are recorded; diagnostics (star, aux, events) only without tape.
+// merged_in: the step opens with the merged kick K2_{i-1} + K1_i (the previous step ran
+// without its closing kick), which also does the previous step's star readout;
+// kick_out: the step ends with its closing half kick K2_i.
 static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, float* s, float* p,
-                               float* g, const TapeSlot* T) {
+                               float* g, const TapeSlot* T, bool merged_in = false,
+                               bool kick_out = true) {
   const sim_params& P = h->prm;
   const int B = h->B;
   cudaStream_t st = h->st;
   const size_t gb = 5 * B * h->N3 * sizeof(float), vb = 3 * B * h->N3 * sizeof(float);
-  const SArg K1 = sc(h, i, SC_K1), K2 = sc(h, i, SC_K2);
+  const SArg K1 = sc(h, i, merged_in ? SC_KM : SC_K1), K2 = sc(h, i, SC_K2);
+  float* zh_prev = (merged_in && P.subgrid_on && !T) ? h->zhat : nullptr;
   if (T) {
     DH_TRY(dcopy(T->U0, *gas, gb, st));
     DH_TRY(dcopy(T->s0, s, vb, st));
@@ -443,14 +453,17 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     DH_TRY(dcopy(T->g0, g, vb, st));
   }
   // 1. half kick + drift
-  DH_TRY(launch_kick_drift(s, p, g, K1, sc(h, i, SC_DTAU), nullptr, nullptr, h->n,
-                           (float)h->inv_dx, B, st));
+  DH_TRY(timed(h, SIM_KT_KICK, [&] {
+    return launch_kick_drift(s, p, g, K1, sc(h, i, SC_DTAU), zh_prev, zh_prev ? h->aux : nullptr,
+                             h->n, (float)h->inv_dx, B, st);
+  }));
   float* cur = *gas;
   if (T) {
     DH_TRY(dcopy(T->Uk1, cur, gb, st));
     cur = T->Uk1;
   }
-  if (P.gravity_on) DH_TRY(launch_gas_kick(cur, g, K1, h->n, B, st));
+  if (P.gravity_on)
+    DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(cur, g, K1, h->n, B, st); }));
   // 2. sweeps
   if (P.hydro_on) {
     const char* order = kOrders[i % 6];
@@ -474,7 +487,9 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   if (P.subgrid_on) {
     float* out = T ? T->Usg : cur;
     zh = T ? nullptr : h->zhat;
-    DH_TRY(launch_subgrid(cur, out, sub_at(h, i), zh, T ? nullptr : h->events, h->N3, B, st));
+    DH_TRY(timed(h, SIM_KT_SUBGRID, [&] {
+      return launch_subgrid(cur, out, sub_at(h, i), zh, T ? nullptr : h->events, h->N3, B, st);
+    }));
     cur = out;
   } else if (T) {
     DH_TRY(dcopy(T->Usg, cur, gb, st));
@@ -492,10 +507,16 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     *gas = *gas_tmp;
     *gas_tmp = t;
   }
-  // 5. half kick (+ star readout on the particles)
-  DH_TRY(launch_kick_drift(s, p, g, K2, sarg(0.0f), zh, zh ? h->aux : nullptr, h->n,
-                           (float)h->inv_dx, B, st));
-  if (P.gravity_on) DH_TRY(launch_gas_kick(*gas, g, K2, h->n, B, st));
+  // 5. half kick (+ star readout on the particles); deferred into the next step's opening
+  //    kick when that one is merged
+  if (kick_out) {
+    DH_TRY(timed(h, SIM_KT_KICK, [&] {
+      return launch_kick_drift(s, p, g, K2, sarg(0.0f), zh, zh ? h->aux : nullptr, h->n,
+                               (float)h->inv_dx, B, st);
+    }));
+    if (P.gravity_on)
+      DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(*gas, g, K2, h->n, B, st); }));
+  }
   if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, B * h->N3, st));
   // 6. learned correction of the gas fields (solver in the loop, Sec. 4)
   if (h->closure) DH_TRY(closure_apply(h->closure, *gas, h->n, B, st));
@@ -562,37 +583,48 @@ static sim_status force_adjoint(sim_t* h, const float* s, const float* g, SArg p
   if (!h->prm.gravity_on) return SIM_OK;
   const int B = h->B;
   cudaStream_t st = h->st;
-  DH_TRY(launch_dot(lamG, g, 3 * h->N3, slot_part(slot, SL_DPREF), B, st));
-  DH_TRY(launch_gravity_adjoint(lamG, h->lam_delta, h->ck, h->ck + 3 * B * h->NC, h->n,
-                                h->prm.box, pn, B, h->plans, st));
-  DH_TRY(launch_add_strided(h->lam_delta, h->lam_gas, h->N3, 5 * h->N3, B, st));
-  return launch_deposit_adjoint(s, h->lam_delta, sarg(h->d_cm), h->lam_s,
-                                slot_part(slot, SL_DCM), h->n, (float)h->inv_dx, B, st);
+  DH_TRY(timed(h, SIM_KT_POISSON_ADJOINT, [&] {
+    DH_TRY(launch_dot(lamG, g, 3 * h->N3, slot_part(slot, SL_DPREF), B, st));
+    return launch_gravity_adjoint(lamG, h->lam_delta, h->ck, h->ck + 3 * B * h->NC, h->n,
+                                  h->prm.box, pn, B, h->plans, st);
+  }));
+  return timed(h, SIM_KT_DEPOSIT_ADJOINT, [&] {
+    DH_TRY(launch_add_strided(h->lam_delta, h->lam_gas, h->N3, 5 * h->N3, B, st));
+    return launch_deposit_adjoint(s, h->lam_delta, sarg(h->d_cm), h->lam_s,
+                                  slot_part(slot, SL_DCM), h->n, (float)h->inv_dx, B, st);
+  });
 }
 
 // Reverse of forward_step for step i with tape T. In: lam_gas / lam_s / lam_p of the state
 // after the step, lamG1 = adjoint of g(a_{i+1}) carried from step i+1. Out: the same
 // buffers for the state before the step, lamG1 = adjoint of g(a_i) (to carry).
 // slot: the step's partials, [B][SL_N].
-static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot) {
+static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot,
+                               bool merged_in = false, bool kick_out = true) {
   const sim_params& P = h->prm;
   const int B = h->B;
   cudaStream_t st = h->st;
-  const SArg K1 = sc(h, i, SC_K1), K2 = sc(h, i, SC_K2);
-  // 5. second half kick
-  if (P.gravity_on) {
-    DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, h->lamG1,
-                                   slot_part(slot, SL_DK2), h->n, B, st));
-    DH_TRY(launch_kick_drift_adjoint(T.s1, nullptr, T.g1, K2, sarg(0.0f), h->lam_s, h->lam_p,
-                                     h->lamG1, slot_part(slot, SL_DK2), dpart(nullptr), h->n,
-                                     (float)h->inv_dx, B, st));
-    // 4. force at a_{i+1}
-    DH_TRY(force_adjoint(h, T.s1, T.g1, sc(h, i, SC_PN1), h->lamG1, slot));
+  const SArg K1 = sc(h, i, merged_in ? SC_KM : SC_K1), K2 = sc(h, i, SC_K2);
+  const int slot_in = merged_in ? SL_DKM : SL_DK1;
+  // 5. second half kick (when the step ran it; otherwise the next step's merged opening kick
+  //    has already put its adjoint of g(a_{i+1}) into lamG1)
+  if (P.gravity_on && kick_out) {
+    DH_TRY(timed(h, SIM_KT_KICK_ADJOINT, [&] {
+      DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, h->lamG1,
+                                     slot_part(slot, SL_DK2), h->n, B, st));
+      return launch_kick_drift_adjoint(T.s1, nullptr, T.g1, K2, sarg(0.0f), h->lam_s, h->lam_p,
+                                       h->lamG1, slot_part(slot, SL_DK2), dpart(nullptr), h->n,
+                                       (float)h->inv_dx, B, st);
+    }));
   }
+  // 4. force at a_{i+1}
+  if (P.gravity_on) DH_TRY(force_adjoint(h, T.s1, T.g1, sc(h, i, SC_PN1), h->lamG1, slot));
   // 3. subgrid
   if (P.subgrid_on)
-    DH_TRY(launch_subgrid_adjoint(T.Us3, h->lam_gas, sub_at(h, i), dpart(h->dglob, NG),
-                                  slot_part(slot, SL_DFB), h->N3, B, st));
+    DH_TRY(timed(h, SIM_KT_SUBGRID_ADJOINT, [&] {
+      return launch_subgrid_adjoint(T.Us3, h->lam_gas, sub_at(h, i), dpart(h->dglob, NG),
+                                    slot_part(slot, SL_DFB), h->N3, B, st);
+    }));
   // 2. sweeps in reverse
   if (P.hydro_on) {
     const char* order = kOrders[i % 6];
@@ -612,12 +644,14 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot)
   }
   // 1. first half kick and drift
   DH_TRY(dzero(h->lamG0, 3 * B * h->N3 * sizeof(float), st));
-  if (P.gravity_on)
-    DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, h->lamG0,
-                                   slot_part(slot, SL_DK1), h->n, B, st));
-  DH_TRY(launch_kick_drift_adjoint(T.s0, T.p0, T.g0, K1, sc(h, i, SC_DTAU), h->lam_s, h->lam_p,
-                                   h->lamG0, slot_part(slot, SL_DK1), slot_part(slot, SL_DDTAU),
-                                   h->n, (float)h->inv_dx, B, st));
+  DH_TRY(timed(h, SIM_KT_KICK_ADJOINT, [&] {
+    if (P.gravity_on)
+      DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, h->lamG0,
+                                     slot_part(slot, slot_in), h->n, B, st));
+    return launch_kick_drift_adjoint(T.s0, T.p0, T.g0, K1, sc(h, i, SC_DTAU), h->lam_s, h->lam_p,
+                                     h->lamG0, slot_part(slot, slot_in), slot_part(slot, SL_DDTAU),
+                                     h->n, (float)h->inv_dx, B, st);
+  }));
   float* t = h->lamG0;
   h->lamG0 = h->lamG1;
   h->lamG1 = t;  // carry: lamG1 now holds the adjoint of g(a_i)
@@ -729,6 +763,10 @@ static sim_status setup_instances(sim_t* h) {
       float* row = sctab.data() + (size_t)i * SC_N * B;
       row[SC_K1 * B + b] = p.gravity_on ? (float)f.K1 : 0.0f;
       row[SC_K2 * B + b] = p.gravity_on ? (float)f.K2 : 0.0f;
+      // the closing half kick of step i - 1 and the opening one of step i see the same force
+      // at the same positions: inside a segment they are one kick of K2_{i-1} + K1_i
+      const double km = f.K1 + (i > 0 ? sch[i - 1].K2 : 0.0);
+      row[SC_KM * B + b] = p.gravity_on ? (float)km : 0.0f;
       row[SC_DTAU * B + b] = (float)f.dtau;
       row[SC_NU * B + b] = (float)(f.dtau * h->inv_dx);
       row[SC_PN1 * B + b] = gravity_pref_norm(f.pref1, n);
@@ -736,6 +774,7 @@ static sim_status setup_instances(sim_t* h) {
       double* cf = coef.data() + ((size_t)i * B + b) * SL_N;
       cf[SL_DK1] = f.dK1;
       cf[SL_DK2] = f.dK2;
+      cf[SL_DKM] = f.dK1 + (i > 0 ? sch[i - 1].dK2 : 0.0);
       cf[SL_DNU] = f.ddtau * h->inv_dx;
       cf[SL_DDTAU] = f.ddtau;
       cf[SL_DPREF] = f.dpref1 / f.pref1;
@@ -938,9 +977,17 @@ static sim_status run_prepare(sim_t* h, int n_steps) {
 
 // n_steps forward steps with a checkpoint every ckpt_every steps (Sec. 2.3.5).
 static sim_status run_body(sim_t* h, int n_steps) {
+  const int last = h->step + n_steps;
   for (int k = 0; k < n_steps; ++k) {
-    if ((h->step - h->init_step) % h->prm.ckpt_every == 0) DH_TRY(store_checkpoint(h));
-    DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr));
+    const int rel = h->step - h->init_step, every = h->prm.ckpt_every;
+    if (rel % every == 0) DH_TRY(store_checkpoint(h));
+    // kicks merge inside a checkpoint segment (not with a closure, which acts on the state
+    // after the closing kick, nor with the CFL watchdog, which reads every step's state)
+    const bool plain = h->closure || h->prm.cfl_max > 0;
+    const bool merged_in = !plain && rel % every != 0;
+    const bool kick_out = plain || h->step + 1 == last || (rel + 1) % every == 0;
+    DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr, merged_in,
+                        kick_out));
     h->step += 1;
     if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
       double c = 0;
@@ -1006,12 +1053,17 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
     DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
     DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
     DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, first), h->w_g));
+    // the same kick merging as the forward run: opening kicks merged after the segment's
+    // first step, the closing kick only at the segment's end
+    const bool plain = h->prm.cfl_max > 0;
     for (int i = first; i < end; ++i) {
       const TapeSlot T = tape_slot(h, i - first);
-      DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T));
+      DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T,
+                          !plain && i != first, plain || i == end - 1));
     }
     for (int i = end - 1; i >= first; --i)
-      DH_TRY(reverse_step(h, i, tape_slot(h, i - first), h->dslots + (size_t)i * B * SL_N));
+      DH_TRY(reverse_step(h, i, tape_slot(h, i - first), h->dslots + (size_t)i * B * SL_N,
+                          !plain && i != first, plain || i == end - 1));
   }
   // g at the start of the run is a function of the initial state
   const TapeSlot T0 = tape_slot(h, 0);
