@@ -152,8 +152,9 @@ int32_t sim_batch_size(const sim_t* h);
 
 /* Hydro sweep kernel variants (Sec. 2.3.1 sweeps; the paper has no counterpart: these are
  * GB300 launch shapes). DEFAULT: the built-in choice for the grid size; TILE: shared-memory
- * tile; MARCH32 / MARCH16: one thread marches a line segment of 32 / 16 cells (y and z
- * sweeps only; x always uses the tile). */
+ * tile; MARCH32 / MARCH16: one thread marches a line segment of 32 / 16 cells (forward: y
+ * and z only, the forward x sweep always uses the tile; adjoint: every axis, x on x <-> y
+ * transposed copies). */
 enum {
   SIM_SWEEP_DEFAULT = 0,
   SIM_SWEEP_TILE = 1,

@@ -247,12 +247,12 @@ sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int 
 // D = lf dbL/2 (daR, dbR the limiter partials of the right-moving face flux, daL, dbL of
 // the left-moving one). Cell i-4 is then complete and lamUh_{i-4} = VJP(Uh_{i-4}).
 // d/dnu gathers sum_t F2_t lf_t / nu - sum_j lamUh_j dF1_j / 2.
-template <int AXIS, int L>
+template <int AXIS, int L, int FC = 1 + AXIS>
 __global__ void __launch_bounds__(128)
 sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                        float* __restrict__ luh_out, int n, SArg nua, float gam, float eps,
                        DPart dnub) {
-  constexpr int F = 1 + AXIS;
+  constexpr int F = FC;  // momentum component along the sweep
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y / n;  // instance
   const int t3 = blockIdx.y - b * n;
@@ -400,12 +400,12 @@ sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ 
 
 // Pass 2: lam_in_k = lam_out_k + lamUh_k + VJP(U_k; nu/2 (lamUh_{k+1} - lamUh_k),
 // -nu/2 (lamUh_k - lamUh_{k-1})), one thread per cell.
-template <int AXIS>
+template <int AXIS, int FC = 1 + AXIS>
 __global__ void __launch_bounds__(256)
 sweep_adj_final_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                        const float* __restrict__ luh, float* __restrict__ lin, int n,
                        SArg nua, float gam) {
-  constexpr int F = 1 + AXIS;
+  constexpr int F = FC;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.z / n;  // instance
   const int y = blockIdx.y, z = blockIdx.z - b * n;
@@ -620,8 +620,10 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
 // segments of 32 or 16 cells (y and z sweeps only: marching along x is not coalesced).
 // The default, measured on GB300 for one instance: the tile is fastest up to n ~ 128
 // (51 us at 128^3 for every axis); marching with segments of 32 wins for y/z on larger
-// grids (335 us vs 386 us at 256^3). The adjoint defaults to the marching pair for y/z
-// (2.1x the tile at 256^3) and the tile for x. sim_autotune times the variants per handle.
+// grids (335 us vs 386 us at 256^3). The adjoint defaults to the marching pair for every
+// axis: y/z directly (2.1x the tile at 256^3), x on x <-> y transposed copies (the x tile
+// takes ~320 us at 128^3 against ~170 us for a y/z pair). sim_autotune times the variants
+// per handle.
 static int pick_fwd(int axis, int n, int variant) {
   if (axis == 0) return SIM_SWEEP_TILE;
   if (variant != SIM_SWEEP_DEFAULT) return variant;
@@ -629,7 +631,7 @@ static int pick_fwd(int axis, int n, int variant) {
 }
 
 static int pick_adj(int axis, int variant) {
-  if (axis == 0) return SIM_SWEEP_TILE;
+  (void)axis;
   return variant != SIM_SWEEP_DEFAULT ? variant : SIM_SWEEP_MARCH32;
 }
 
@@ -658,6 +660,33 @@ static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, 
   return SIM_OK;
 }
 
+// out[f][z][x][y] = in[f][z][y][x] for nf fields of B instances (32 x 32 tiles through
+// shared memory; the transpose is its own inverse)
+__global__ void __launch_bounds__(256) transpose_xy_kernel(const float* __restrict__ in,
+                                                           float* __restrict__ out, int n) {
+  __shared__ float tile[32][33];
+  const int fz = blockIdx.z;  // field x plane (all instances)
+  const long long plane = (long long)fz * n * n;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const int x = x0 + tx, y = y0 + j;
+    if (x < n && y < n) tile[j][tx] = __ldg(in + plane + (long long)y * n + x);
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int y = y0 + tx, x = x0 + j;  // out row index x, column y
+    if (x < n && y < n) out[plane + (long long)x * n + y] = tile[tx][j];
+  }
+}
+
+static sim_status launch_transpose_xy(const float* in, float* out, int n, int nfields,
+                                      cudaStream_t st) {
+  transpose_xy_kernel<<<dim3(cdiv(n, 32), cdiv(n, 32), nfields * n), 256, 0, st>>>(in, out, n);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
 template <int AXIS, int L>
 static sim_status launch_adj_march_t(const float* uin, const float* lout, float* lin, int n,
                                      SArg nu, float gam, float eps, DPart dnu, float* scratch,
@@ -675,11 +704,39 @@ static sim_status launch_adj_march_t(const float* uin, const float* lout, float*
   return SIM_OK;
 }
 
+// The x adjoint as the y-marching pair on x <-> y transposed copies (momentum component 1
+// stays the one along the sweep). scratch: 4 x 5 n^3 floats per instance.
+template <int L>
+static sim_status launch_adj_x_transposed(const float* uin, const float* lout, float* lin, int n,
+                                          SArg nu, float gam, float eps, DPart dnu,
+                                          float* scratch, int B, cudaStream_t st) {
+  const size_t F5 = (size_t)5 * n * n * n * B;
+  float *ut = scratch, *lt = scratch + F5, *it = scratch + 2 * F5, *luh = scratch + 3 * F5;
+  DH_TRY(launch_transpose_xy(uin, ut, n, 5 * B, st));
+  DH_TRY(launch_transpose_xy(lout, lt, n, 5 * B, st));
+  dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
+  sweep_adj_march_kernel<1, L, 1><<<g1, 128, 0, st>>>(ut, lt, luh, n, nu, gam, eps, dnu);
+  DH_LAUNCH_CHECK();
+  dim3 g2(cdiv(n, 256), n, n * B);
+  sweep_adj_final_kernel<1, 1><<<g2, 256, 0, st>>>(ut, lt, luh, it, n, nu, gam);
+  DH_LAUNCH_CHECK();
+  return launch_transpose_xy(it, lin, n, 5 * B, st);
+}
+
 template <int AXIS>
 static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float* lin, int n,
                                      SArg nu, float gam, float eps, DPart dnu, float* scratch,
                                      int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
+  if (AXIS == 0 && (variant == SIM_SWEEP_MARCH32 || variant == SIM_SWEEP_MARCH16)) {
+    if (!scratch) {
+      set_error("internal: the transposed x adjoint needs a 20 n^3 scratch buffer per instance");
+      return SIM_EINVAL;
+    }
+    return variant == SIM_SWEEP_MARCH32
+               ? launch_adj_x_transposed<32>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st)
+               : launch_adj_x_transposed<16>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
+  }
   if (AXIS != 0) {
     if (variant == SIM_SWEEP_MARCH32)
       return launch_adj_march_t<AXIS, 32>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
@@ -775,7 +832,7 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
   }
   cudaStream_t st = (cudaStream_t)stream;
   float* scratch = nullptr;
-  DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 5ull * n * n * n * sizeof(float), st));
+  DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 20ull * n * n * n * sizeof(float), st));
   const sim_status r =
       dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, dh::sarg((float)nu), gamma,
                                limiter_eps, dh::dpart(dnu), scratch, 1, SIM_SWEEP_DEFAULT, st);

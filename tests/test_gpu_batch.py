@@ -138,7 +138,7 @@ def test_autotune_and_variants_agree(dh, n):
         sim = dh.Simulation(ps, noise.contiguous())
         if mode == "auto":
             fwd, adj = sim.autotune(reps=2)
-            assert fwd[0] == 1 and adj[0] == 1 and all(v in (1, 2, 3) for v in fwd + adj)
+            assert fwd[0] == 1 and all(v in (1, 2, 3) for v in fwd + adj)
         elif mode != "default":
             v = {"tile": 1, "march32": 2, "march16": 3}[mode]
             sim.set_sweep_variants([v] * 3, [v] * 3)
