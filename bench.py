@@ -324,6 +324,8 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.set_stream(stream)
     sim = dh.Simulation(p, noise)
+    # the library's autotuner picks the sweep kernels for this grid (timed on the ICs)
+    variants = sim.autotune(reps=3)
     if not args.no_graphs:
         dh._lib.check(dh.lib.sim_set_graphs(sim.h, 1), "sim_set_graphs", sim.h)
     c = 1.0 / n3
@@ -464,6 +466,7 @@ def main():
         "data": "synthetic",
         "config": _config(ws),
         "cuda_graphs": not args.no_graphs,
+        "sweep_variants": {"fwd": variants[0], "adj": variants[1]},
         "fwd_value": cell_steps / (fwd_ms / 1e3),
         "fwd_ms_per_step": fwd_ms,
         "e2e": {"value": cell_steps / (e2e_ms / 1e3), "unit": "cell-steps/s",
