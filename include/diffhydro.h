@@ -377,15 +377,18 @@ sim_status sim_ic_amplitude(const sim_t* h, int32_t b, double* C);
 /* One relaxing-TVD sweep along axis (0 = x, 1 = y, 2 = z) with nu = dtau/dx:
  * half step with first-order upwind relaxed fluxes (Eq. TVD_halfstep), full step with
  * limited second-order fluxes on the half-step state (Eq. TVD_fullstep). u_in, u_out:
- * 5 n^3 each, must not alias. */
+ * 5 n^3 each, must not alias. variant: SIM_SWEEP_* kernel form (SIM_SWEEP_DEFAULT = the
+ * built-in choice for the axis and n; every form gives the same result up to float32
+ * rounding order), other values SIM_EINVAL. */
 sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int32_t axis, double nu,
-                     double gamma, double limiter_eps, void* stream);
+                     double gamma, double limiter_eps, int32_t variant, void* stream);
 
 /* Adjoint of sim_sweep at u_in: lam_in = (d u_out / d u_in)^T lam_out (5 n^3 each, no
- * aliasing). If dnu (device double) is not NULL, adds lam_out . d u_out / d nu to it. */
+ * aliasing). If dnu (device double) is not NULL, adds lam_out . d u_out / d nu to it.
+ * variant as for sim_sweep. */
 sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out, float* lam_in,
                              int32_t n, int32_t axis, double nu, double gamma,
-                             double limiter_eps, double* dnu, void* stream);
+                             double limiter_eps, double* dnu, int32_t variant, void* stream);
 
 /* Cloud-in-cell deposit (Sec. 2.2): grid[node] += sum_p value_p W(x_p - node) with
  * W the CIC weights, cell decision floor(s/dx) taken in float32. values may be NULL (=1).

@@ -98,8 +98,8 @@ SIGNATURES = {
     "sim_set_state": (ctypes.c_int, [_P, _P, _P, _I32]),
     "sim_schedule": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_D)]),
     "sim_cfl": (ctypes.c_int, [_P, ctypes.POINTER(_D)]),
-    "sim_sweep": (ctypes.c_int, [_P, _P, _I32, _I32, _D, _D, _D, _P]),
-    "sim_sweep_adjoint": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _D, _D, _D, _P, _P]),
+    "sim_sweep": (ctypes.c_int, [_P, _P, _I32, _I32, _D, _D, _D, _I32, _P]),
+    "sim_sweep_adjoint": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _D, _D, _D, _P, _I32, _P]),
     "sim_deposit_cic": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P]),
     "sim_deposit_cic_static": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P]),
     "sim_interp_cic": (ctypes.c_int, [_P, _I32, _I32, _D, _P, _P, _P]),

@@ -42,23 +42,26 @@ def _side(cells: int) -> int:
     return n
 
 
-def sweep(u_in, axis: int, nu: float, gamma: float = 5.0 / 3.0, limiter_eps: float = 1e-30):
+def sweep(u_in, axis: int, nu: float, gamma: float = 5.0 / 3.0, limiter_eps: float = 1e-30,
+          variant: int = 0):
+    """variant: SWEEP_* kernel form (0 = the built-in choice)."""
     n = _side(u_in.numel() // 5)
     _chk(u_in, F32, 5 * n ** 3, "u_in")
     out = torch.empty_like(u_in)
-    check(lib.sim_sweep(_ptr(u_in), _ptr(out), n, axis, nu, gamma, limiter_eps, _stream()), "sim_sweep")
+    check(lib.sim_sweep(_ptr(u_in), _ptr(out), n, axis, nu, gamma, limiter_eps, variant,
+                        _stream()), "sim_sweep")
     return out
 
 
 def sweep_adjoint(u_in, lam_out, axis: int, nu: float, gamma: float = 5.0 / 3.0,
-                  limiter_eps: float = 1e-30):
+                  limiter_eps: float = 1e-30, variant: int = 0):
     n = _side(u_in.numel() // 5)
     _chk(u_in, F32, 5 * n ** 3, "u_in")
     _chk(lam_out, F32, 5 * n ** 3, "lam_out")
     lam_in = torch.empty_like(u_in)
     dnu = torch.zeros(1, dtype=F64, device=u_in.device)
     check(lib.sim_sweep_adjoint(_ptr(u_in), _ptr(lam_out), _ptr(lam_in), n, axis, nu, gamma,
-                                limiter_eps, _ptr(dnu), _stream()), "sim_sweep_adjoint")
+                                limiter_eps, _ptr(dnu), variant, _stream()), "sim_sweep_adjoint")
     return lam_in, dnu
 
 

@@ -198,6 +198,26 @@ __device__ __forceinline__ void vanleer_grad(float a, float b, float eps, float&
   }
 }
 
+// Limiter value and both partials in one pass (the adjoint needs the face flux for d/dnu):
+// phi as vanleer() up to the rounding of the reciprocal, da = dphi/da, db = dphi/db.
+__device__ __forceinline__ void vanleer_vg(float a, float b, float eps, float& phi, float& da,
+                                           float& db) {
+  const float ab = a * b;
+  if (ab > 0.0f) {
+    const float s = a + b;
+    const float D = s + copysignf(eps, s);
+    const float q = 2.0f * fast_rcp(D);  // 2 / D
+    const float q2 = 0.5f * q * q;       // 2 / D^2
+    phi = ab * q;
+    da = b * (D - a) * q2;
+    db = a * (D - b) * q2;
+  } else {
+    phi = 0.0f;
+    da = 0.0f;
+    db = 0.0f;
+  }
+}
+
 // ------------------------------------------------------------------ reductions
 // Per-thread partial sums stay in float32 (GB300's FP64 rate is a small fraction of FP32);
 // each block converts its float32 total once and adds it to a double accumulator.

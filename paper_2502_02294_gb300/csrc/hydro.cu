@@ -333,9 +333,9 @@ sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ 
       const float lf = nu * (M1[k] - M0[k]);  // nu (lam_out_{t+1} - lam_out_t), t = i-3
       const float aR = 0.5f * (R1[k] - R0[k]), bR = 0.5f * (R2[k] - R1[k]);
       const float aL = 0.5f * (L1[k] - L0[k]), bL = 0.5f * (FLh[k] - L1[k]);
-      float daR, dbR, daL, dbL;
-      vanleer_grad(aR, bR, eps, daR, dbR);
-      vanleer_grad(aL, bL, eps, daL, dbL);
+      float pR, daR, dbR, pL, daL, dbL;
+      vanleer_vg(aR, bR, eps, pR, daR, dbR);
+      vanleer_vg(aL, bL, eps, pL, daL, dbL);
       const float A = 0.5f * lf * daR, B = 0.5f * lf * dbR;
       const float C = 0.5f * lf * daL, D = 0.5f * lf * dbL;
       aR0[k] -= A;
@@ -344,11 +344,8 @@ sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ 
       aL1[k] -= C;
       aL2[k] += -lf + C - D;
       aL3[k] += D;
-      if (face_in) {
-        // d/dnu part 1: faces of the segment's output cells (t in [s0-1, s0+L))
-        const float F2 = (R1[k] + vanleer(aR, bR, eps)) - (L1[k] - vanleer(aL, bL, eps));
-        dnu_acc += F2 * lf * inv_nu;
-      }
+      // d/dnu part 1: faces of the segment's output cells (t in [s0-1, s0+L))
+      if (face_in) dnu_acc += ((R1[k] + pR) - (L1[k] - pL)) * lf * inv_nu;
     }
     // cell i-4 is complete
     const int jc = s0 + it - 9;  // unwrapped index of cell i-4
@@ -660,29 +657,73 @@ static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, 
   return SIM_OK;
 }
 
-// out[f][z][x][y] = in[f][z][y][x] for nf fields of B instances (32 x 32 tiles through
-// shared memory; the transpose is its own inverse)
-__global__ void __launch_bounds__(256) transpose_xy_kernel(const float* __restrict__ in,
-                                                           float* __restrict__ out, int n) {
+// out[z][x][y] = in[z][y][x] for the planes of up to two arrays (plane q < np0 of in0 ->
+// out0, the rest of in1 -> out1; a plane is n x n floats). 32 x 32 tiles through shared
+// memory, TP planes per CTA; VEC: float4 rows (n % 4 == 0, 16-byte aligned arrays). The
+// transpose is its own inverse.
+struct TPair {
+  const float* in0;
+  float* out0;
+  const float* in1;
+  float* out1;
+  int np0, np;
+};
+constexpr int TP = 4;
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) transpose_xy_kernel(TPair a, int n) {
   __shared__ float tile[32][33];
-  const int fz = blockIdx.z;  // field x plane (all instances)
-  const long long plane = (long long)fz * n * n;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int j = ty; j < 32; j += 8) {
-    const int x = x0 + tx, y = y0 + j;
-    if (x < n && y < n) tile[j][tx] = __ldg(in + plane + (long long)y * n + x);
-  }
-  __syncthreads();
-  for (int j = ty; j < 32; j += 8) {
-    const int y = y0 + tx, x = x0 + j;  // out row index x, column y
-    if (x < n && y < n) out[plane + (long long)x * n + y] = tile[tx][j];
+  const int t = threadIdx.x;
+  const long long nn = (long long)n * n;
+  for (int pi = 0; pi < TP; ++pi) {
+    const int q = blockIdx.z * TP + pi;
+    if (q >= a.np) break;
+    const bool first = q < a.np0;
+    const float* in = (first ? a.in0 : a.in1) + (first ? q : q - a.np0) * nn;
+    float* out = (first ? a.out0 : a.out1) + (first ? q : q - a.np0) * nn;
+    if (pi) __syncthreads();  // the previous plane's tile has been read
+    if (VEC) {
+      const int r = t >> 3, c = (t & 7) * 4;  // load: tile row r (y), columns c..c+3 (x)
+      if (y0 + r < n && x0 + c < n) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(in + (long long)(y0 + r) * n + x0 + c));
+        tile[r][c] = v.x;
+        tile[r][c + 1] = v.y;
+        tile[r][c + 2] = v.z;
+        tile[r][c + 3] = v.w;
+      }
+      __syncthreads();
+      if (x0 + r < n && y0 + c < n) {  // store: out row x0 + r, columns y0 + c..c+3
+        const float4 v = make_float4(tile[c][r], tile[c + 1][r], tile[c + 2][r], tile[c + 3][r]);
+        *reinterpret_cast<float4*>(out + (long long)(x0 + r) * n + y0 + c) = v;
+      }
+    } else {
+      const int tx = t & 31, ty = t >> 5;  // 32 x 8
+      for (int j = ty; j < 32; j += 8) {
+        const int x = x0 + tx, y = y0 + j;
+        if (x < n && y < n) tile[j][tx] = __ldg(in + (long long)y * n + x);
+      }
+      __syncthreads();
+      for (int j = ty; j < 32; j += 8) {
+        const int y = y0 + tx, x = x0 + j;  // out row index x, column y
+        if (x < n && y < n) out[(long long)x * n + y] = tile[tx][j];
+      }
+    }
   }
 }
 
-static sim_status launch_transpose_xy(const float* in, float* out, int n, int nfields,
-                                      cudaStream_t st) {
-  transpose_xy_kernel<<<dim3(cdiv(n, 32), cdiv(n, 32), nfields * n), 256, 0, st>>>(in, out, n);
+// nf planes-of-fields: in0 -> out0 (nf0 fields of n planes), then in1 -> out1 (nf1 fields;
+// nf1 = 0 transposes one array)
+static sim_status launch_transpose_xy(const float* in0, float* out0, int nf0, const float* in1,
+                                      float* out1, int nf1, int n, cudaStream_t st) {
+  const TPair a{in0, out0, in1, out1, nf0 * n, (nf0 + nf1) * n};
+  const dim3 grid(cdiv(n, 32), cdiv(n, 32), cdiv(a.np, TP));
+  const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(in0) | reinterpret_cast<uintptr_t>(out0) |
+                                     reinterpret_cast<uintptr_t>(in1) | reinterpret_cast<uintptr_t>(out1)) % 16 == 0);
+  if (vec)
+    transpose_xy_kernel<true><<<grid, 256, 0, st>>>(a, n);
+  else
+    transpose_xy_kernel<false><<<grid, 256, 0, st>>>(a, n);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -712,15 +753,14 @@ static sim_status launch_adj_x_transposed(const float* uin, const float* lout, f
                                           float* scratch, int B, cudaStream_t st) {
   const size_t F5 = (size_t)5 * n * n * n * B;
   float *ut = scratch, *lt = scratch + F5, *it = scratch + 2 * F5, *luh = scratch + 3 * F5;
-  DH_TRY(launch_transpose_xy(uin, ut, n, 5 * B, st));
-  DH_TRY(launch_transpose_xy(lout, lt, n, 5 * B, st));
+  DH_TRY(launch_transpose_xy(uin, ut, 5 * B, lout, lt, 5 * B, n, st));
   dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
   sweep_adj_march_kernel<1, L, 1><<<g1, 128, 0, st>>>(ut, lt, luh, n, nu, gam, eps, dnu);
   DH_LAUNCH_CHECK();
   dim3 g2(cdiv(n, 256), n, n * B);
   sweep_adj_final_kernel<1, 1><<<g2, 256, 0, st>>>(ut, lt, luh, it, n, nu, gam);
   DH_LAUNCH_CHECK();
-  return launch_transpose_xy(it, lin, n, 5 * B, st);
+  return launch_transpose_xy(it, lin, 5 * B, nullptr, nullptr, 0, n, st);
 }
 
 template <int AXIS>
@@ -814,20 +854,24 @@ sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, f
 }  // namespace dh
 
 extern "C" sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int32_t axis,
-                                double nu, double gamma, double limiter_eps, void* stream) {
-  if (!u_in || !u_out || n < 1 || u_in == u_out) {
-    dh::set_error("sim_sweep: null/aliased buffers or n < 1");
+                                double nu, double gamma, double limiter_eps, int32_t variant,
+                                void* stream) {
+  if (!u_in || !u_out || n < 1 || u_in == u_out || variant < SIM_SWEEP_DEFAULT ||
+      variant > SIM_SWEEP_MARCH16) {
+    dh::set_error("sim_sweep: null/aliased buffers, n < 1 or unknown variant");
     return SIM_EINVAL;
   }
   return dh::launch_sweep(axis, u_in, u_out, n, dh::sarg((float)nu), gamma, limiter_eps, 1,
-                          SIM_SWEEP_DEFAULT, (cudaStream_t)stream);
+                          variant, (cudaStream_t)stream);
 }
 
 extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out, float* lam_in,
                                         int32_t n, int32_t axis, double nu, double gamma,
-                                        double limiter_eps, double* dnu, void* stream) {
-  if (!u_in || !lam_out || !lam_in || n < 1 || lam_in == lam_out || lam_in == u_in) {
-    dh::set_error("sim_sweep_adjoint: null/aliased buffers or n < 1");
+                                        double limiter_eps, double* dnu, int32_t variant,
+                                        void* stream) {
+  if (!u_in || !lam_out || !lam_in || n < 1 || lam_in == lam_out || lam_in == u_in ||
+      variant < SIM_SWEEP_DEFAULT || variant > SIM_SWEEP_MARCH16) {
+    dh::set_error("sim_sweep_adjoint: null/aliased buffers, n < 1 or unknown variant");
     return SIM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -835,7 +879,7 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
   DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 20ull * n * n * n * sizeof(float), st));
   const sim_status r =
       dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, dh::sarg((float)nu), gamma,
-                               limiter_eps, dh::dpart(dnu), scratch, 1, SIM_SWEEP_DEFAULT, st);
+                               limiter_eps, dh::dpart(dnu), scratch, 1, variant, st);
   cudaFreeAsync(scratch, st);
   return r;
 }

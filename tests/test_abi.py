@@ -78,7 +78,7 @@ def test_invalid_params_rejected_before_device_work(dh, field, value):
 
 def test_null_arguments_rejected(dh):
     L = dh.lib
-    assert L.sim_sweep(None, None, 8, 0, 0.1, 5 / 3, 1e-30, None) == dh._lib.SIM_EINVAL
+    assert L.sim_sweep(None, None, 8, 0, 0.1, 5 / 3, 1e-30, 0, None) == dh._lib.SIM_EINVAL
     assert L.sim_deposit_cic(None, None, 8, 8.0, None, None) == dh._lib.SIM_EINVAL
     assert L.sim_power_spectrum(None, None, 8, 8.0, 4, None, None, None, None) == dh._lib.SIM_EINVAL
     assert L.sim_step(None) == dh._lib.SIM_EINVAL
