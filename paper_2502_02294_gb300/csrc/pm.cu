@@ -185,17 +185,41 @@ __global__ void deposit_kernel(const float* __restrict__ s, const float* __restr
       }
 }
 
-// grid (cdiv(N3, 256), B)
+// grid (cdiv(N3, 1024), B): four cells per thread, 16-byte vector accesses where N3 and the
+// instance's pointers allow (add may alias out: each cell is read before it is written)
 __global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, SArg scale,
-                                    const float* __restrict__ add, int add_stride, float offset,
-                                    float* __restrict__ out, int N3) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+                                    const float* add, int add_stride, float offset, float* out,
+                                    int N3) {
   const int b = blockIdx.y;
-  if (i >= N3) return;
-  const size_t o = (size_t)b * N3 + i;
-  const float cnt = from_fix(acc[o]);
-  acc[o] = 0ull;
-  out[o] = scale.at(b) * cnt + (add ? add[(size_t)b * add_stride + i] : 0.0f) + offset;
+  const float sc = scale.at(b);
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= N3) return;
+  unsigned long long* a = acc + (size_t)b * N3;
+  float* o = out + (size_t)b * N3;
+  const float* ad = add ? add + (size_t)b * add_stride : nullptr;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(o) |
+                       reinterpret_cast<uintptr_t>(ad);
+  if ((N3 & 3) == 0 && (al & 15) == 0) {
+    const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(a + i0);
+    const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(a + i0 + 2);
+    const float4 r = ad ? *reinterpret_cast<const float4*>(ad + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const ulonglong2 z = make_ulonglong2(0ull, 0ull);
+    *reinterpret_cast<ulonglong2*>(a + i0) = z;
+    *reinterpret_cast<ulonglong2*>(a + i0 + 2) = z;
+    float4 w;
+    w.x = sc * from_fix(v0.x) + r.x + offset;
+    w.y = sc * from_fix(v0.y) + r.y + offset;
+    w.z = sc * from_fix(v1.x) + r.z + offset;
+    w.w = sc * from_fix(v1.y) + r.w + offset;
+    *reinterpret_cast<float4*>(o + i0) = w;
+  } else {
+    const int i1 = i0 + 4 < N3 ? i0 + 4 : N3;
+    for (int i = i0; i < i1; ++i) {
+      const float cnt = from_fix(a[i]);
+      a[i] = 0ull;
+      o[i] = sc * cnt + (ad ? ad[i] : 0.0f) + offset;
+    }
+  }
 }
 
 sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
@@ -209,8 +233,8 @@ sim_status launch_fix_to_float(unsigned long long* acc, SArg scale, const float*
                                int add_stride, float offset, float* out, int n, int B,
                                cudaStream_t st) {
   const int N3 = n * n * n;
-  fix_to_float_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(acc, scale, add, add_stride,
-                                                              offset, out, N3);
+  fix_to_float_kernel<<<dim3(cdiv(N3, 1024), B), 256, 0, st>>>(acc, scale, add, add_stride,
+                                                               offset, out, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -443,14 +467,14 @@ sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cud
 
 // ------------------------------------------------------------------ adjoints
 __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __restrict__ g,
-                                    SArg Ka, float* __restrict__ lam, float* __restrict__ lam_g,
+                                    SArg Ka, float* __restrict__ lam, float4* __restrict__ lam_g4,
                                     DPart dK, int N3) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   u += (size_t)b * 5 * N3;
   lam += (size_t)b * 5 * N3;
   g += (size_t)b * 3 * N3;
-  lam_g += (size_t)b * 3 * N3;
+  lam_g4 += (size_t)b * N3;
   const float K = Ka.at(b);
   float dkf = 0.0f;
   if (i < N3) {
@@ -468,13 +492,16 @@ __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __
       g2 += gg[j] * gg[j];
     }
     dkf = le * (mg + K * rho * g2);
+    float4 lg = lam_g4[i];
+    float* lgj = &lg.x;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       lrho += K * lm[j] * gg[j];
       dkf += lm[j] * rho * gg[j];
-      lam_g[j * N3 + i] += lm[j] * rho * K + le * (K * m[j] + K * K * rho * gg[j]);
+      lgj[j] += lm[j] * rho * K + le * (K * m[j] + K * K * rho * gg[j]);
       lam[(1 + j) * N3 + i] = lm[j] + le * K * gg[j];
     }
+    lam_g4[i] = lg;
     lrho += 0.5f * K * K * g2 * le;
     lam[i] = lrho;
   }
@@ -482,17 +509,20 @@ __global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __
 }
 
 sim_status launch_gas_kick_adjoint(const float* gas, const float* g, SArg K, float* lam,
-                                   float* lam_g, DPart dK, int n, int B, cudaStream_t st) {
+                                   float4* lam_g4, DPart dK, int n, int B, cudaStream_t st) {
   const int N3 = n * n * n;
-  gas_kick_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, g, K, lam, lam_g, dK, N3);
+  gas_kick_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, g, K, lam, lam_g4, dK, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
-__global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0,
+// 64 registers (8 blocks of 128 per SM): twice the warps of the unconstrained 96, for a
+// kernel that waits on CIC gathers and vector atomics
+__global__ void __launch_bounds__(kPT, 8)
+kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0,
                                       const float* __restrict__ g, SArg Ka, SArg dtaua,
                                       float* __restrict__ lam_s, float* __restrict__ lam_p,
-                                      float* __restrict__ lam_g, DPart dK, DPart ddtau, int n,
+                                      float4* __restrict__ lam_g4, DPart dK, DPart ddtau, int n,
                                       float inv_dx) {
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
@@ -502,7 +532,7 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
   g += o3;
   lam_s += o3;
   lam_p += o3;
-  lam_g += o3;
+  lam_g4 += (size_t)q.b * N3;
   const float K = Ka.at(q.b), dtau = dtaua.at(q.b);
   float dk = 0.0f, dd = 0.0f;
   if (q.ok) {
@@ -534,11 +564,9 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
           const float dwz = (oz ? inv_dx : -inv_dx) * c.wx[ox] * c.wy[oy];
           float lg = 0.0f;
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            const float gv = __ldg(g + j * N3 + o);
-            lg += lp[j] * gv;
-            atomicAdd(lam_g + j * N3 + o, K * lp[j] * w);
-          }
+          for (int j = 0; j < 3; ++j) lg += lp[j] * __ldg(g + j * N3 + o);
+          const float kw = K * w;
+          atomicAdd(lam_g4 + o, make_float4(kw * lp[0], kw * lp[1], kw * lp[2], 0.0f));
           gs[0] += dwx * lg;
           gs[1] += dwy * lg;
           gs[2] += dwz * lg;
@@ -555,11 +583,11 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
 }
 
 sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, SArg K,
-                                     SArg dtau, float* lam_s, float* lam_p, float* lam_g,
+                                     SArg dtau, float* lam_s, float* lam_p, float4* lam_g4,
                                      DPart dK, DPart ddtau, int n, float inv_dx, int B,
                                      cudaStream_t st) {
   kick_drift_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s0, p0, g, K, dtau, lam_s,
-                                                                  lam_p, lam_g, dK, ddtau, n,
+                                                                  lam_p, lam_g4, dK, ddtau, n,
                                                                   inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -603,6 +631,36 @@ sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg c
                                   cudaStream_t st) {
   deposit_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, lam_delta, cm, lam_s, dcm, n,
                                                                inv_dx);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// grid (blocks, B): lam_g[b][j][i] = lam_g4[b][i].j, out.at(b) += sum lam_g4[b][i].j g[b][j][i]
+__global__ void unpack_dot_kernel(const float4* __restrict__ lam_g4, const float* __restrict__ g,
+                                  float* __restrict__ lam_g, DPart out, long long N3) {
+  const int b = blockIdx.y;
+  lam_g4 += (size_t)b * N3;
+  g += (size_t)b * 3 * N3;
+  lam_g += (size_t)b * 3 * N3;
+  float acc = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = lam_g4[i];
+    lam_g[i] = v.x;
+    lam_g[N3 + i] = v.y;
+    lam_g[2 * N3 + i] = v.z;
+    acc += v.x * __ldg(g + i) + v.y * __ldg(g + N3 + i) + v.z * __ldg(g + 2 * N3 + i);
+  }
+  if (out.p) block_sum_atomic(acc, out.at(b));
+}
+
+sim_status launch_unpack_dot(const float4* lam_g4, const float* g, float* lam_g, DPart out,
+                             int n, int B, cudaStream_t st) {
+  const long long N3 = (long long)n * n * n;
+  int blocks = cdiv(N3, 256);
+  const int cap = cdiv(152 * 16, B);
+  if (blocks > cap) blocks = cap;
+  unpack_dot_kernel<<<dim3(blocks, B), 256, 0, st>>>(lam_g4, g, lam_g, out, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

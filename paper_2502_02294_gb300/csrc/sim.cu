@@ -535,8 +535,8 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
     DH_TRY(dalloc_t(h, &h->lam_tmp, 5 * N3));
     DH_TRY(dalloc_t(h, &h->lam_s, 3 * N3));
     DH_TRY(dalloc_t(h, &h->lam_p, 3 * N3));
-    DH_TRY(dalloc_t(h, &h->lamG0, 3 * N3));
-    DH_TRY(dalloc_t(h, &h->lamG1, 3 * N3));
+    DH_TRY(dalloc_t(h, &h->lamG0, 4 * N3));  // node-interleaved (x, y, z, 0)
+    DH_TRY(dalloc_t(h, &h->lamG1, 4 * N3));
     DH_TRY(dalloc_t(h, &h->lam_delta, N3));
     DH_TRY(dalloc_t(h, &h->lam4, 4 * h->N3));  // one instance at a time
     DH_TRY(dalloc_t(h, &h->lam_scr, 20 * N3));
@@ -576,16 +576,20 @@ static TapeSlot tape_slot(sim_t* h, int k) {
   return t;
 }
 
-// Adjoint of the force field g = G(s, rho) at one state: lam_G (3 n^3, consumed) ->
-// lam_rho += ..., lam_s += ...; slot[SL_DPREF] += lam_G . g, slot[SL_DCM] += d/d(1 - f_b).
+static inline float4* lam_g4(float* p) { return reinterpret_cast<float4*>(p); }
+
+// Adjoint of the force field g = G(s, rho) at one state: lam_G (n^3 float4 (x, y, z, 0),
+// consumed) -> lam_rho += ..., lam_s += ...; slot[SL_DPREF] += lam_G . g,
+// slot[SL_DCM] += d/d(1 - f_b). The three components go to lam_scr for the transforms.
 static sim_status force_adjoint(sim_t* h, const float* s, const float* g, SArg pn,
                                 float* lamG, double* slot) {
   if (!h->prm.gravity_on) return SIM_OK;
   const int B = h->B;
   cudaStream_t st = h->st;
   DH_TRY(timed(h, SIM_KT_POISSON_ADJOINT, [&] {
-    DH_TRY(launch_dot(lamG, g, 3 * h->N3, slot_part(slot, SL_DPREF), B, st));
-    return launch_gravity_adjoint(lamG, h->lam_delta, h->ck, h->ck + 3 * B * h->NC, h->n,
+    DH_TRY(launch_unpack_dot(reinterpret_cast<const float4*>(lamG), g, h->lam_scr,
+                             slot_part(slot, SL_DPREF), h->n, B, st));
+    return launch_gravity_adjoint(h->lam_scr, h->lam_delta, h->ck, h->ck + 3 * B * h->NC, h->n,
                                   h->prm.box, pn, B, h->plans, st);
   }));
   return timed(h, SIM_KT_DEPOSIT_ADJOINT, [&] {
@@ -610,10 +614,10 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot,
   //    has already put its adjoint of g(a_{i+1}) into lamG1)
   if (P.gravity_on && kick_out) {
     DH_TRY(timed(h, SIM_KT_KICK_ADJOINT, [&] {
-      DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, h->lamG1,
+      DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, lam_g4(h->lamG1),
                                      slot_part(slot, SL_DK2), h->n, B, st));
       return launch_kick_drift_adjoint(T.s1, nullptr, T.g1, K2, sarg(0.0f), h->lam_s, h->lam_p,
-                                       h->lamG1, slot_part(slot, SL_DK2), dpart(nullptr), h->n,
+                                       lam_g4(h->lamG1), slot_part(slot, SL_DK2), dpart(nullptr), h->n,
                                        (float)h->inv_dx, B, st);
     }));
   }
@@ -643,13 +647,13 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot,
     }
   }
   // 1. first half kick and drift
-  DH_TRY(dzero(h->lamG0, 3 * B * h->N3 * sizeof(float), st));
+  DH_TRY(dzero(h->lamG0, 4 * B * h->N3 * sizeof(float), st));
   DH_TRY(timed(h, SIM_KT_KICK_ADJOINT, [&] {
     if (P.gravity_on)
-      DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, h->lamG0,
+      DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, lam_g4(h->lamG0),
                                      slot_part(slot, slot_in), h->n, B, st));
     return launch_kick_drift_adjoint(T.s0, T.p0, T.g0, K1, sc(h, i, SC_DTAU), h->lam_s, h->lam_p,
-                                     h->lamG0, slot_part(slot, slot_in), slot_part(slot, SL_DDTAU),
+                                     lam_g4(h->lamG0), slot_part(slot, slot_in), slot_part(slot, SL_DDTAU),
                                      h->n, (float)h->inv_dx, B, st);
   }));
   float* t = h->lamG0;
@@ -1044,7 +1048,7 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
     DH_TRY(dzero(h->lam_s, 3 * N3 * sizeof(float), st));
     DH_TRY(dzero(h->lam_p, 3 * N3 * sizeof(float), st));
   }
-  DH_TRY(dzero(h->lamG1, 3 * N3 * sizeof(float), st));
+  DH_TRY(dzero(h->lamG1, 4 * N3 * sizeof(float), st));
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int first = h->ckpt_step[seg];
     const int end = seg + 1 < nseg ? h->ckpt_step[seg + 1] : last;
@@ -1370,7 +1374,7 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
     // reverse
     DH_TRY(dcopy(h->lam_gas, adj_gas, 5 * N3 * sizeof(float), st));
     DH_TRY(part_split(h->lam_s, h->lam_p, adj_part, h, st));
-    DH_TRY(dzero(h->lamG1, 3 * N3 * sizeof(float), st));
+    DH_TRY(dzero(h->lamG1, 4 * N3 * sizeof(float), st));
     DH_TRY(reverse_step(h, i, T, slot));
     // g(a_i) is a function of the input state: flush its adjoint now
     double* flush = slot + (size_t)B * SL_N;

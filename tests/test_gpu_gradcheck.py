@@ -4,12 +4,18 @@ the final density of a run from another seed. Gradients with respect to the 64^3
 noise (20 random directions) and to (Omega_m, sigma8) against central finite differences.
 
 The loss is piecewise smooth: CIC cell crossings, the limiter gate, |v| and the sound-speed
-clamp are kinks, and a 50-step run crosses many of them. Central differences then measure
-a mean slope over [-h, h]; in float64 the oracle's own reverse mode and finite differences
-agree to 0.05-3% for h in [2e-6, 2e-2] on this kind of run (16^3), and float32 cannot use
-h below ~1e-3. The check therefore uses h = 5e-3 and a mixed bar: each direction within
-2% of the RMS directional derivative, and the median relative error below 1%. Exact
-agreement with reverse mode is tested against the float64 oracle on smaller runs
+clamp are kinks. Measured on this grid (12 directions, h = 1e-3, 5e-3, 2e-2):
+  - 10 steps a = 0.1 -> 0.2 (before shocks): adjoint and differences agree to 6e-4 of the
+    RMS directional derivative at h = 1e-3 (median 1.4e-4 relative), the gap growing with
+    h as the truncation error does: the smooth regime, checked below at 2e-3 / 1e-3;
+  - 50 steps a = 0.1 -> 1.0: the gap is 1-3.5% of the RMS and does not shrink with h
+    (3.5%, 3.4%, 3.5%): the run crosses kinks at spacings far below any usable h, so the
+    differences measure a mean slope while reverse mode gives the slope of the branch at
+    the point (the float64 oracle shows the same 0.05-3% spread on 16^3 runs). Which
+    kinks lie near the point also moves with the last bit of the forward's rounding. The
+    50-step check therefore bars each direction at 5% of the RMS and the median relative
+    gap at 2.5%.
+Exact agreement with reverse mode is tested against the float64 oracle on smaller runs
 (tests/test_gpu_sim.py), and against float64 finite differences at h = 2e-6 below.
 """
 import numpy as np
@@ -65,8 +71,42 @@ def test_noise_gradient_matches_finite_differences(setup):
         fds.append((lp - lm) / (2 * h))
     ads, fds = np.array(ads), np.array(fds)
     scale = np.sqrt(np.mean(fds ** 2))
-    assert np.all(np.abs(ads - fds) <= 0.02 * scale), np.abs(ads - fds) / scale
-    assert np.median(np.abs(ads - fds) / np.abs(fds)) < 0.01
+    assert np.all(np.abs(ads - fds) <= 0.05 * scale), np.abs(ads - fds) / scale
+    assert np.median(np.abs(ads - fds) / np.abs(fds)) < 0.025, np.abs(ads - fds) / np.abs(fds)
+
+
+def test_noise_gradient_matches_finite_differences_smooth_regime():
+    """64^3, 10 steps a = 0.1 -> 0.2 (before shell crossing and shocks), h = 1e-3."""
+    need_gpu()
+    dh = lib()
+    steps, a1 = 10, 0.2
+    p = dh.default_params(n=N, box=float(N), n_steps=steps, a_start=0.1, a_end=a1,
+                          ckpt_every=5, seed=1)
+    tsim = dh.Simulation(dh.default_params(n=N, box=float(N), n_steps=steps, a_start=0.1,
+                                           a_end=a1, seed=2))
+    tsim.run()
+    target = tsim.state()["gas"][0].contiguous().clone()
+    tsim.close()
+    noise = torch.from_numpy(synth.white_noise(N, 11).astype(np.float32)).cuda()
+    L0, sim = _loss(dh, p, noise, target)
+    dL, _ = sim.loss_density(target, 1.0 / N ** 3)
+    dnoise, _ = sim.run_adjoint(dL)
+    sim.close()
+    g = torch.Generator().manual_seed(321)
+    h = 1e-3
+    ads, fds = [], []
+    for k in range(20):
+        d = torch.randn(N, N, N, generator=g).cuda()
+        ads.append((dnoise.double() * d.double()).sum().item())
+        lp, s1 = _loss(dh, p, (noise + h * d).contiguous(), target)
+        s1.close()
+        lm, s2 = _loss(dh, p, (noise - h * d).contiguous(), target)
+        s2.close()
+        fds.append((lp - lm) / (2 * h))
+    ads, fds = np.array(ads), np.array(fds)
+    scale = np.sqrt(np.mean(fds ** 2))
+    assert np.all(np.abs(ads - fds) <= 2e-3 * scale), np.abs(ads - fds) / scale
+    assert np.median(np.abs(ads - fds) / np.abs(fds)) < 1e-3, np.abs(ads - fds) / np.abs(fds)
 
 
 @pytest.mark.parametrize("name,idx", [("omega_m", 0), ("sigma8", 1)])
