@@ -164,25 +164,56 @@ __device__ __forceinline__ float from_fix(unsigned long long a) {
   return 2.0f * __int2float_rn(hi) + __uint2float_rn(lo) * kInvFix;
 }
 
+// Warp-aggregated CIC scatter. The lanes of a warp hold consecutive lattice x sites of one
+// (y, z) row (particle order is Lagrangian), so where the flow has not crossed, a lane's
+// upper x corner is its right neighbour's lower x corner. Per (z, y) corner pair each lane
+// adds its neighbour's upper-corner value into its own lower corner when the nodes agree
+// and skips the upper corner its neighbour has taken: about four atomics per particle
+// instead of eight, with the same sums. All lanes of the warp must call it (ok = false for
+// lanes without a particle).
+struct XPair {
+  bool take;   // this lane adds the left lane's upper value into its lower node
+  bool given;  // the right lane took this lane's upper value
+};
+
+__device__ __forceinline__ XPair xpair(int a0, int a1, bool ok) {
+  const int lane = threadIdx.x & 31;
+  const int pa1 = __shfl_up_sync(0xffffffffu, ok ? a1 : -1, 1);
+  const bool take = ok && lane > 0 && pa1 == a0;
+  const unsigned tk = __ballot_sync(0xffffffffu, take);
+  return XPair{take, lane < 31 && ((tk >> (lane + 1)) & 1u)};
+}
+
 __global__ void deposit_kernel(const float* __restrict__ s, const float* __restrict__ vals,
                                int n, float inv_dx, unsigned long long* __restrict__ acc) {
   const int N3 = n * n * n;
-  const PIdx q = particle_index(n);
-  if (!q.ok) return;
+  const PIdx q = particle_index(n);  // lanes past the row end stay for the warp exchange
   s += (size_t)q.b * 3 * N3;
   acc += (size_t)q.b * N3;
   Cic c;
-  cic_setup(s, q, N3, n, inv_dx, c);
-  const float v = vals ? vals[(size_t)q.b * N3 + q.p] : 1.0f;
+  float v = 0.0f;
+  if (q.ok) {
+    cic_setup(s, q, N3, n, inv_dx, c);
+    v = vals ? vals[(size_t)q.b * N3 + q.p] : 1.0f;
+  } else {
+    c = Cic{{0, 0}, {0, 0}, {0, 0}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  }
 #pragma unroll
   for (int oz = 0; oz < 2; ++oz)
 #pragma unroll
-    for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-      for (int ox = 0; ox < 2; ++ox) {
-        const unsigned long long fx = to_fix(c.wz[oz] * c.wy[oy] * c.wx[ox] * v);
-        if (fx) atomicAdd(acc + node(c, oz, oy, ox, n), fx);
+    for (int oy = 0; oy < 2; ++oy) {
+      const int a0 = node(c, oz, oy, 0, n), a1 = node(c, oz, oy, 1, n);
+      const float wyz = c.wz[oz] * c.wy[oy];
+      unsigned long long f0 = to_fix(wyz * c.wx[0] * v);
+      const unsigned long long f1 = to_fix(wyz * c.wx[1] * v);
+      const XPair x = xpair(a0, a1, q.ok);
+      const unsigned long long fl = __shfl_up_sync(0xffffffffu, f1, 1);
+      if (x.take) f0 += fl;
+      if (q.ok) {
+        if (f0) atomicAdd(acc + a0, f0);
+        if (!x.given && f1) atomicAdd(acc + a1, f1);
       }
+    }
 }
 
 // grid (cdiv(N3, 1024), B): four cells per thread, 16-byte vector accesses where N3 and the
@@ -516,10 +547,7 @@ sim_status launch_gas_kick_adjoint(const float* gas, const float* g, SArg K, flo
   return SIM_OK;
 }
 
-// 64 registers (8 blocks of 128 per SM): twice the warps of the unconstrained 96, for a
-// kernel that waits on CIC gathers and vector atomics
-__global__ void __launch_bounds__(kPT, 8)
-kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0,
+__global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0,
                                       const float* __restrict__ g, SArg Ka, SArg dtaua,
                                       float* __restrict__ lam_s, float* __restrict__ lam_p,
                                       float4* __restrict__ lam_g4, DPart dK, DPart ddtau, int n,
@@ -535,13 +563,14 @@ kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0
   lam_g4 += (size_t)q.b * N3;
   const float K = Ka.at(q.b), dtau = dtaua.at(q.b);
   float dk = 0.0f, dd = 0.0f;
+  Cic c = Cic{{0, 0}, {0, 0}, {0, 0}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  float lp[3] = {0.0f, 0.0f, 0.0f};
   if (q.ok) {
     const int i = q.p;
-    Cic c;
     cic_setup(s0, q, N3, n, inv_dx, c);
     float gi[3];
     interp3(g, c, n, N3, gi);
-    float lp[3], ls[3];
+    float ls[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       ls[j] = lam_s[j * N3 + i];
@@ -549,7 +578,7 @@ kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0
       lp[j] = lam_p[j * N3 + i] + dtau * ls[j];
       dk += lp[j] * gi[j];
     }
-    // lam_s0 += K d/ds (sum_j lp_j interp(g_j)) ; lam_g += interp^T(K lp)
+    // lam_s0 += K d/ds (sum_j lp_j interp(g_j))
     float gs[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int oz = 0; oz < 2; ++oz)
@@ -558,15 +587,12 @@ kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox) {
           const int o = node(c, oz, oy, ox, n);
-          const float w = c.wz[oz] * c.wy[oy] * c.wx[ox];
           const float dwx = (ox ? inv_dx : -inv_dx) * c.wy[oy] * c.wz[oz];
           const float dwy = (oy ? inv_dx : -inv_dx) * c.wx[ox] * c.wz[oz];
           const float dwz = (oz ? inv_dx : -inv_dx) * c.wx[ox] * c.wy[oy];
           float lg = 0.0f;
 #pragma unroll
           for (int j = 0; j < 3; ++j) lg += lp[j] * __ldg(g + j * N3 + o);
-          const float kw = K * w;
-          atomicAdd(lam_g4 + o, make_float4(kw * lp[0], kw * lp[1], kw * lp[2], 0.0f));
           gs[0] += dwx * lg;
           gs[1] += dwy * lg;
           gs[2] += dwz * lg;
@@ -577,6 +603,30 @@ kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0
       lam_p[j * N3 + i] = lp[j];
     }
   }
+  // lam_g += interp^T(K lp): warp-aggregated float4 atomics (all lanes take part)
+  float lpl[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) lpl[j] = __shfl_up_sync(0xffffffffu, lp[j], 1);
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const int a0 = node(c, oz, oy, 0, n), a1 = node(c, oz, oy, 1, n);
+      const float kyz = K * c.wz[oz] * c.wy[oy];
+      const float w0 = kyz * c.wx[0], w1 = kyz * c.wx[1];
+      const XPair x = xpair(a0, a1, q.ok);
+      const float wl = __shfl_up_sync(0xffffffffu, w1, 1);
+      if (q.ok) {
+        float4 v0 = make_float4(w0 * lp[0], w0 * lp[1], w0 * lp[2], 0.0f);
+        if (x.take) {
+          v0.x += wl * lpl[0];
+          v0.y += wl * lpl[1];
+          v0.z += wl * lpl[2];
+        }
+        atomicAdd(lam_g4 + a0, v0);
+        if (!x.given) atomicAdd(lam_g4 + a1, make_float4(w1 * lp[0], w1 * lp[1], w1 * lp[2], 0.0f));
+      }
+    }
   // a block never spans two instances (blockIdx.z carries the instance)
   if (dK.p) block_sum_atomic(dk, dK.at(q.b));
   if (ddtau.p) block_sum_atomic(dd, ddtau.at(q.b));
