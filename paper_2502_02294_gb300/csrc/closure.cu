@@ -22,6 +22,7 @@
 // (a reduction over voxels of 27 rank-1 updates of 16 x 16) runs on the CUDA cores.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -44,50 +45,58 @@ constexpr int SLK_BEFORE = 8, SLK_AFTER = 136;  // slack positions around the st
 constexpr int PACK = 27 * 512 / 2;              // bf16 elements of one packed layer
 
 // ------------------------------------------------------------------ geometry
-// A CTA owns L output lines of Zc consecutive planes and walks through the input planes
-// z0 - 1 .. z0 + Zc. Input plane p contributes to output planes p - 1, p, p + 1 through the
-// taps dz = +1, 0, -1; for one in-plane shift (dy, dx) those three weight blocks sit side
-// by side in one B operand (N = 48), so one MMA adds the shifted input to three output-plane
-// accumulators at once: 9 MMAs per input plane and tile. The accumulators of all Zc + 4
-// planes a CTA touches live in TMEM ([tile][plane][16 columns], zeroed first); output plane
-// q is final once input q + 1 is in, and its epilogue runs while the next input's MMAs do.
-// Input planes stream through a ring of three shared-memory slots ((L + 2) padded lines in
-// two 8-channel planes of 16-byte positions, with slack positions around them).
-constexpr int RING = 3;
-constexpr int CONV_THREADS = 256;
+// A CTA owns L output lines (T tiles of 128 positions per plane) of Zc consecutive output
+// planes z0 .. z0 + Zc - 1 and marches through the input planes z0 - 1 .. z0 + Zc, which
+// stream through a ring of `ring` shared-memory slots ((L + 2) padded lines in two
+// 8-channel planes of 16-byte positions, with slack positions around them). Input plane p
+// contributes to output planes p - 1, p, p + 1 through the taps dz = +1, 0, -1; for one
+// in-plane shift (dy, dx) those three weight blocks sit side by side in one B operand
+// (N = 48), so one MMA adds the shifted input to three output-plane accumulators at once:
+// 9 MMAs per input plane and tile. Inputs are taken in groups of G; the accumulators a
+// group writes (the outputs of its G inputs' planes minus one, i.e. G + 2 planes) occupy
+// G + 2 consecutive plane slots of one of two TMEM buffers ([buffer][tile][slot][16
+// columns]), groups alternating between the buffers. An output plane whose three inputs
+// straddle two groups is the sum of its slots in both buffers. The epilogue drains each
+// output plane once its last input's MMAs are done and, after the last plane that touches
+// a buffer, zeroes that buffer for the group after next. One CTA per SM (all 512 TMEM
+// columns when T = 4); weights, barriers and TMEM are set up once per column of planes.
+constexpr int EPI_SETS = 4;                         // epilogue warps per TMEM lane quarter
+constexpr int CONV_THREADS = 128 + 128 * EPI_SETS;  // loaders, MMA issuer, epilogue
+constexpr int ZC_MAX = 128;           // output planes per CTA
+constexpr int NB_MAX = ZC_MAX + 2;    // input planes (and barriers of each kind) per CTA
 
 struct ConvGeom {
-  int n, P, L, T, tpl, contig, Zc, slot_pos, ncols;
+  int n, P, L, T, tpl, contig, Zc, G, ring, slot_pos, ncols;
   size_t smem;
 };
 
 static int slot_positions(int L, int P) { return SLK_BEFORE + (L + 2) * P + SLK_AFTER; }
 
-static size_t conv_smem(int L, int P) {
-  return (size_t)RING * 2 * slot_positions(L, P) * 16 + 9 * 1536 + 2 * 20 * 8 + 16;  // + barriers
+static size_t conv_smem(int ring, int L, int P) {
+  return (size_t)ring * 2 * slot_positions(L, P) * 16 + 9 * 1536 + 3 * NB_MAX * 8 + 16;
 }
 
 static ConvGeom conv_geom(int n, int B) {
   ConvGeom g;
   g.n = n;
   g.P = n + 2;
-  const size_t limit = 112 * 1024;  // two CTAs per SM
+  const size_t limit = 200 * 1024;
   if (n >= 128) {
-    // 128-row tiles inside one line, ceil(n / 128) per line
+    // 128-position tiles inside a line, ceil(n / 128) per line, up to 4 tiles per plane
     g.contig = 0;
     g.tpl = (n + 127) / 128;
-    g.L = 1;
-    g.T = g.tpl;
+    g.L = 4 / g.tpl > 1 ? 4 / g.tpl : 1;
+    g.T = g.L * g.tpl;
   } else {
-    // tiles run across consecutive padded lines; fewest tiles per plane with T <= 2
+    // tiles run across consecutive padded lines: fewest tiles per plane with T <= 4
     g.contig = 1;
     g.tpl = 0;
     int bestL = 1, bestCost = 1 << 30;
     for (int L = 1; L <= n; ++L) {
       const int T = cdiv((long long)L * g.P, 128);
-      if (T > 2 || (L > 1 && conv_smem(L, g.P) > limit)) break;
+      if (T > 4 || conv_smem(3, L, g.P) > limit) break;
       const int cost = cdiv(n, L) * T;
-      if (cost < bestCost) {
+      if (cost <= bestCost) {
         bestCost = cost;
         bestL = L;
       }
@@ -95,28 +104,63 @@ static ConvGeom conv_geom(int n, int B) {
     g.L = bestL;
     g.T = cdiv((long long)bestL * g.P, 128);
   }
-  // accumulators of Zc + 4 planes in at most 256 columns (two CTAs per SM)
-  g.Zc = 16 / g.T - 4;
-  if (g.Zc < 1) g.Zc = 1;
-  if (g.Zc > n) g.Zc = n;
+  // two buffers of T x (G + 2) accumulator planes in 512 columns
+  g.G = 16 / g.T - 2;
+  if (g.G < 2) g.G = 2;
+  g.ncols = 512;
+  g.ring = conv_smem(4, g.L, g.P) <= limit ? 4 : 3;
+  // output planes per CTA: the split of the planes into chunks that keeps the SMs busiest
+  // (whole waves of one CTA per SM), counting the two extra input planes of every chunk
+  const int ny = cdiv(n, g.L);
+  double best = -1.0;
+  g.Zc = n < ZC_MAX ? n : ZC_MAX;
+  for (int k = 1; k <= 64; ++k) {
+    const int Zc = cdiv(n, k);
+    if (Zc > ZC_MAX) continue;
+    const long long ctas = (long long)ny * cdiv(n, Zc) * B;
+    const double waves = (double)ctas / 152.0;
+    const double eff = waves / std::ceil(waves) * (double)Zc / (Zc + 2);
+    if (eff > best + 1e-9) {
+      best = eff;
+      g.Zc = Zc;
+    }
+    if (Zc <= 2) break;
+  }
   g.slot_pos = slot_positions(g.L, g.P);
-  g.smem = conv_smem(g.L, g.P);
-  int nc = 32;
-  while (nc < 16 * g.T * (g.Zc + 4)) nc <<= 1;
-  g.ncols = nc;
-  (void)B;
+  // at least 116 KB so that a second CTA never shares the SM (and its 512 TMEM columns)
+  g.smem = std::max(conv_smem(g.ring, g.L, g.P), (size_t)116 * 1024);
   return g;
 }
 
 // ------------------------------------------------------------------ device helpers
-__device__ __forceinline__ float gelu_f(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+// erfc(|x|) by Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26
+// (absolute error below 1.5e-7 for all x >= 0): t = 1 / (1 + p |x|),
+// erfc(|x|) ~ (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) e^{-x^2}. Branch-free; e receives
+// e^{-x^2}. 1 + erf(x) is then 2 - erfc(|x|) for x >= 0 and erfc(|x|) for x < 0, without
+// cancellation on the negative side.
+__device__ __forceinline__ float erfc_abs(float ax, float& e) {
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+  e = __expf(-ax * ax);
+  const float poly =
+      fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+           0.254829592f);
+  return t * poly * e;
 }
 
-// d GELU / dz = Phi(z) + z phi(z)
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2
+__device__ __forceinline__ float gelu_f(float z) {
+  const float x = z * 0.70710678118654752f;
+  float e;
+  const float q = erfc_abs(fabsf(x), e);
+  return 0.5f * z * (x >= 0.0f ? 2.0f - q : q);
+}
+
+// d GELU / dz = Phi(z) + z phi(z), phi(z) = e^{-z^2 / 2} / sqrt(2 pi)
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-         z * 0.3989422804014327f * __expf(-0.5f * z * z);
+  const float x = z * 0.70710678118654752f;
+  float e;
+  const float q = erfc_abs(fabsf(x), e);
+  return 0.5f * (x >= 0.0f ? 2.0f - q : q) + z * 0.3989422804014327f * e;
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {
@@ -125,16 +169,24 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return i;
 }
 
-__device__ __forceinline__ void store_bf16x16(bf16* dst, const float v[16]) {
+// Activations are bfloat16 [B][z][y][2][x][8]: every line holds its 8-channel halves one
+// after the other, each half a contiguous run of 16-byte positions, the row layout of the
+// convolution's shared-memory operand (so a line half arrives with one bulk copy).
+// Element offset of position x, half h of line `line` = (b n + z) n + y:
+__device__ __forceinline__ size_t act_off(long long line, int n, int h, int x) {
+  return ((size_t)(line * 2 + h) * n + x) * 8;
+}
+
+__device__ __forceinline__ void act_store(bf16* base, long long line, int n, int x,
+                                          const float v[16]) {
   uint32_t w[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
     w[j] = *reinterpret_cast<const uint32_t*>(&p);
   }
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  *reinterpret_cast<uint4*>(base + act_off(line, n, 0, x)) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(base + act_off(line, n, 1, x)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
 struct F5 {
@@ -145,11 +197,11 @@ struct F5 {
 enum { CONV_HIDDEN = 0, CONV_OUT_Y = 1, CONV_OUT_APPLY = 2, CONV_BWD = 3 };
 
 struct ConvArgs {
-  const bf16* in;      // [B][n^3][16]
+  const bf16* in;      // activations [B][n][n][2][n][8]
   const bf16* w;       // packed [27][2][16 rows][8]: row = output channel, K = input channel
   const float* bias;   // [16] (forward) or NULL
-  int n, P, L, T, tpl, contig, Zc, slot_pos, ncols;
-  bf16* out;           // HIDDEN / BWD: [B][n^3][16]
+  int n, P, L, T, tpl, contig, Zc, G, ring, slot_pos, ncols;
+  bf16* out;           // HIDDEN / BWD: activations, as in
   float* zout;         // HIDDEN: pre-activation [B][n^3][16] or NULL
   const float* zprev;  // BWD: pre-activation whose GELU' multiplies the result
   float* y;            // OUT_Y: [B][5][n^3]
@@ -158,33 +210,46 @@ struct ConvArgs {
   int* err;
 };
 
-// fetch input plane gz (periodic) into ring slot `slot`: (L + 2) lines x P positions
+// Bulk copies (async proxy, completion counted in bytes on the plane's mbarrier) of input
+// plane gz (periodic) into ring slot `slot_addr`: for each of the L + 2 lines and each
+// 8-channel half, the n interior positions (one copy) and the two periodic padding
+// positions (16 bytes each). Lane k of the issuing warp copies line half k, k + 32, ...
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t plane_tx_bytes(const ConvArgs& a) {
+  return (uint32_t)(a.L + 2) * 2u * (uint32_t)(a.n + 2) * 16u;
+}
+
 __device__ __forceinline__ void conv_fetch_plane(const ConvArgs& a, const bf16* in, uint32_t slot_addr,
-                                                 int gz, int nthreads, int y0, int tid) {
+                                                 int gz, int y0, int lane, uint64_t* mbar) {
   const int n = a.n, P = a.P, L = a.L;
   const uint32_t plane_bytes = (uint32_t)a.slot_pos * 16u;
-  const int npos = (L + 2) * P;
   gz = gz < 0 ? gz + n : (gz >= n ? gz - n : gz);
-  for (int pos = tid; pos < npos; pos += nthreads) {
-    const int ly = pos / P, px = pos - ly * P;
-    int gx = px - 1;
-    gx = gx < 0 ? gx + n : (gx >= n ? gx - n : gx);
+  for (int k = lane; k < 2 * (L + 2); k += 32) {
+    const int ly = k >> 1, h = k & 1;
     const int gy = wrapi(y0 - 1 + ly, n);
-    const bf16* src = in + (((size_t)gz * n + gy) * n + gx) * CH;
-    const uint32_t d = slot_addr + (uint32_t)(SLK_BEFORE + pos) * 16u;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + plane_bytes), "l"(src + 8)
-                 : "memory");
+    const bf16* src = in + act_off((long long)gz * n + gy, n, h, 0);
+    const uint32_t d = slot_addr + (uint32_t)h * plane_bytes + (uint32_t)(SLK_BEFORE + ly * P) * 16u;
+    bulk_g2s(d + 16u, src, (uint32_t)n * 16u, mbar);                    // x = 0 .. n - 1
+    bulk_g2s(d, src + (size_t)(n - 1) * 8, 16u, mbar);                  // x = -1 -> n - 1
+    bulk_g2s(d + (uint32_t)(n + 1) * 16u, src, 16u, mbar);              // x = n -> 0
   }
 }
 
-// TMEM zeroing: every lane of every accumulator column
-__device__ __forceinline__ void tmem_zero(uint32_t tmem, int ncols, int w) {
+// TMEM zeroing of columns [c0, c1) (multiples of 16) in the 32 lanes of warp w % 4; the
+// warps w / 4 = 0 .. nsplit - 1 share the columns
+__device__ __forceinline__ void tmem_zero(uint32_t tmem, int c0, int c1, int w, int nsplit) {
   const uint32_t lane_base = (uint32_t)(32 * (w & 3)) << 16;
   uint32_t z[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) z[j] = 0u;
-  for (int c = 16 * (w >> 2); c < ncols; c += 16 * (CONV_THREADS / 128)) {
+  for (int c = c0 + 16 * (w >> 2); c < c1; c += 16 * nsplit) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
         "%13,%14,%15,%16};" ::"r"(tmem + lane_base + (uint32_t)c),
@@ -195,38 +260,49 @@ __device__ __forceinline__ void tmem_zero(uint32_t tmem, int ncols, int w) {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// The 9 x T MMAs of input plane i (slot i mod RING): block (dy, dx) of the weights against
-// the input shifted by (dy, dx), into planes j = i, i + 1, i + 2 of every tile.
-__device__ __forceinline__ void conv_issue_input(const ConvArgs& a, int i, uint32_t tmem,
-                                                 uint64_t a_base, uint64_t b_base,
+// TMEM column of accumulator plane slot s of tile t in buffer beta
+__device__ __forceinline__ uint32_t acc_col(const ConvArgs& a, int beta, int t, int s) {
+  return 16u * (uint32_t)((beta * a.T + t) * (a.G + 2) + s);
+}
+
+// The 9 x T MMAs of input plane i (ring slot i mod ring): block (dy, dx) of the weights
+// against the input shifted by (dy, dx), into plane slots s, s + 1, s + 2 of buffer beta
+// (output planes i - 2, i - 1, i relative to z0) of every tile.
+__device__ __forceinline__ void conv_issue_input(const ConvArgs& a, int i, int beta, int s,
+                                                 uint32_t tmem, uint64_t a_base, uint64_t b_base,
                                                  uint32_t slot_units, uint32_t idesc) {
-  const int P = a.P, T = a.T, ZP = a.Zc + 4;
-  const uint64_t a_slot = a_base + (uint64_t)((i % RING) * slot_units);
+  const int P = a.P, T = a.T;
+  const uint64_t a_slot = a_base + (uint64_t)((i % a.ring) * slot_units);
+  // tile-major: the 9 MMAs of one tile chain into the same accumulator (switching the
+  // accumulator between consecutive MMAs costs several times a chained MMA)
+  for (int t = 0; t < T; ++t) {
+    int vb;
+    if (a.contig) {
+      vb = 128 * t;
+    } else {
+      const int ly = t / a.tpl;
+      vb = ly * P + 1 + 128 * (t - ly * a.tpl);
+    }
+    const uint32_t d = tmem + acc_col(a, beta, t, s);
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
+    for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int j = (dy + 1) * 3 + (dx + 1);
-      const uint64_t db = b_base + (uint64_t)(j * 96);  // 1536-byte blocks
-      for (int t = 0; t < T; ++t) {
-        int vb;
-        if (a.contig) {
-          vb = 128 * t;
-        } else {
-          const int ly = t / a.tpl;
-          vb = ly * P + 1 + 128 * (t - ly * a.tpl);
-        }
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int j = (dy + 1) * 3 + (dx + 1);
+        const uint64_t db = b_base + (uint64_t)(j * 96);  // 1536-byte blocks
         // descriptors are linear in the start address (16-byte units, low 14 bits)
         const uint64_t da = a_slot + (uint64_t)(SLK_BEFORE + (1 + dy) * P + dx + vb);
-        umma_bf16(tmem + 16u * (uint32_t)(t * ZP + i), da, db, idesc, 1u);
+        umma_bf16(d, da, db, idesc, 1u);
       }
     }
   }
 }
 
+// Epilogue of row r of tile t of output plane z (all 16 channels).
 template <int MODE>
-__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc_in[16], int b,
-                                              int z, int y0, int t, int r) {
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc[16],
+                                              const float bias[16], int b, int z, int y0, int t,
+                                              int r) {
   const int n = a.n, P = a.P, L = a.L;
   const long long N3 = (long long)n * n * n;
   int ly, x;
@@ -244,33 +320,30 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc
   }
   const int gy = y0 + ly;
   if (!valid || gy >= n) return;
-  float acc[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) acc[c] = acc_in[c];
   const size_t v = ((size_t)z * n + gy) * n + x;
+  const long long line = ((long long)b * n + z) * n + gy;
   if (MODE == CONV_HIDDEN) {
-    float h[16];
+    float zc[16], hv[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const float zc = acc[c] + __ldg(a.bias + c);
-      acc[c] = zc;
-      h[c] = gelu_f(zc);
+      zc[c] = acc[c] + bias[c];
+      hv[c] = gelu_f(zc[c]);
     }
     if (a.zout) {
       float4* zo = reinterpret_cast<float4*>(a.zout + ((size_t)b * N3 + v) * CH);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        zo[q] = make_float4(zc[4 * q], zc[4 * q + 1], zc[4 * q + 2], zc[4 * q + 3]);
     }
-    store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, h);
+    act_store(a.out, line, n, x, hv);
   } else if (MODE == CONV_OUT_Y) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) a.y[((size_t)b * 5 + c) * N3 + v] = acc[c] + __ldg(a.bias + c);
+    for (int c = 0; c < 5; ++c) a.y[((size_t)b * 5 + c) * N3 + v] = acc[c] + bias[c];
   } else if (MODE == CONV_OUT_APPLY) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       float* g = a.gas + ((size_t)b * 5 + c) * N3 + v;
-      *g += a.scale.v[c] * (acc[c] + __ldg(a.bias + c));
+      *g += a.scale.v[c] * (acc[c] + bias[c]);
     }
   } else {  // CONV_BWD
     const float4* zp = reinterpret_cast<const float4*>(a.zprev + ((size_t)b * N3 + v) * CH);
@@ -283,34 +356,39 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc
       d[4 * q + 2] = acc[4 * q + 2] * gelu_grad_f(zz.z);
       d[4 * q + 3] = acc[4 * q + 3] * gelu_grad_f(zz.w);
     }
-    store_bf16x16(a.out + ((size_t)b * N3 + v) * CH, d);
+    act_store(a.out, line, n, x, d);
   }
 }
 
-// Warp roles: warps 0-1 fetch input planes (cp.async, then a proxy fence and an mbarrier
-// arrive per plane), warp 2 lane 0 issues the MMAs of each plane once it has landed and
-// commits them to that plane's barrier, warps 4-7 run the epilogue of every output plane
-// once its last input's MMAs are done. Every barrier is used once (one per input plane),
-// every wait is bounded; a timeout sets an error flag and the CTA still frees its TMEM.
-constexpr int MAX_IN = 20;  // input planes per CTA (Zc + 2)
-constexpr int LOADERS = 64;
+// Warp roles: warp 0 fetches input planes (bulk copies completing on the plane's mbarrier),
+// warp 2 lane 0 issues the MMAs of each
+// plane once it has landed (and, at the start of a group, once the buffer is free) and
+// commits them to that plane's barrier, warps 4 .. 4 + 4 EPI_SETS - 1 run the epilogue of
+// every output plane once its last input's MMAs are done (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 of the tiles t = (w - 4) / 4 mod EPI_SETS) and free each buffer
+// after its last plane. Every
+// barrier is used once (one per input plane or group), every wait is bounded; a timeout
+// sets an error flag and the CTA still frees its TMEM.
 
 template <int MODE>
-__global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
+__global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int n = a.n;
   const long long N3 = (long long)n * n * n;
   const int b = blockIdx.z, y0 = blockIdx.x * a.L, z0 = blockIdx.y * a.Zc;
   const int nz = min(a.Zc, n - z0);  // output planes of this CTA
   const int nin = nz + 2;            // input planes z0 - 1 .. z0 + nz
+  const int G = a.G, ring = a.ring;
+  const int ngroups = (nin + G - 1) / G;
   const int tid = threadIdx.x;
   const int w = tid >> 5, lane = tid & 31;
   const uint32_t slot_bytes = 2u * (uint32_t)a.slot_pos * 16u;
   uint8_t* sa = smem;
-  uint8_t* sw = smem + RING * slot_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sw + 9 * 1536);  // [MAX_IN]: input landed
-  uint64_t* done = full + MAX_IN;                                // [MAX_IN]: its MMAs done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + MAX_IN);
+  uint8_t* sw = smem + ring * slot_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sw + 9 * 1536);  // [NB_MAX]: input landed
+  uint64_t* done = full + NB_MAX;                                // [NB_MAX]: its MMAs done
+  uint64_t* freeb = done + NB_MAX;                               // [NB_MAX]: group drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(freeb + NB_MAX);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const bf16* in = a.in + (size_t)b * N3 * CH;
   const uint32_t sa0 = smem_u32(sa);
@@ -318,7 +396,7 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
 
   // setup: slack zeroed, weights staged, barriers, TMEM allocated and zeroed
   const int nslack = SLK_BEFORE + SLK_AFTER;
-  for (int i = tid; i < RING * 2 * nslack; i += CONV_THREADS) {
+  for (int i = tid; i < ring * 2 * nslack; i += CONV_THREADS) {
     const int sp = i / nslack, k = i - sp * nslack;
     const int pos = k < SLK_BEFORE ? k : a.slot_pos - SLK_AFTER + (k - SLK_BEFORE);
     *reinterpret_cast<uint4*>(sa + (size_t)sp * a.slot_pos * 16 + (size_t)pos * 16) =
@@ -327,10 +405,11 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
   for (int i = tid; i < 9 * 1536 / 16; i += CONV_THREADS)
     reinterpret_cast<uint4*>(sw)[i] = __ldg(reinterpret_cast<const uint4*>(a.w) + i);
   if (tid == 0) {
-    for (int i = 0; i < MAX_IN; ++i) {
-      mbar_init(full + i, LOADERS);
+    for (int i = 0; i < nin; ++i) {
+      mbar_init(full + i, 1);
       mbar_init(done + i, 1);
     }
+    for (int g = 0; g < ngroups; ++g) mbar_init(freeb + g, 4 * EPI_SETS);
     *sflag = 0;
   }
   if (w == 0) tmem_alloc_warp(tslot, (uint32_t)a.ncols);
@@ -339,35 +418,43 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  tmem_zero(tmem, a.ncols, w);
+  tmem_zero(tmem, 0, a.ncols, w, CONV_THREADS / 128);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
 
   if (w < 2) {
-    // ---- loaders: input i into slot i mod RING once input i - RING's MMAs are done
-    for (int i = 0; i <= nin; ++i) {
-      if (i < nin) {
-        if (i >= RING && !mbar_wait_bounded(done + (i - RING), 0, limit)) {
-          *sflag = 1;
+    // ---- loader warp: input i into slot i mod ring once input i - ring's MMAs are done;
+    //      the plane's barrier completes when all its bytes have landed
+    if (w == 0) {
+      const uint32_t tx = plane_tx_bytes(a);
+      int issued = 0;
+      for (int i = 0; i < nin; ++i) {
+        uint32_t ok = 1;
+        if (i >= ring && lane == 0) ok = mbar_wait_bounded(done + (i - ring), 0, limit);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) *sflag = 1;
           break;
         }
-        conv_fetch_plane(a, in, sa0 + (uint32_t)(i % RING) * slot_bytes, z0 - 1 + i, LOADERS, y0, tid);
+        if (lane == 0) {
+          uint64_t state;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                       : "=l"(state)
+                       : "r"(smem_u32(full + i)), "r"(tx)
+                       : "memory");
+          (void)state;
+        }
+        __syncwarp();
+        conv_fetch_plane(a, in, sa0 + (uint32_t)(i % ring) * slot_bytes, z0 - 1 + i, y0, lane, full + i);
+        issued = i + 1;
       }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      if (i >= 1) {
-        // input i - 1 has landed (only the newest group may be in flight)
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        fence_async_smem();
-        uint64_t state;
-        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
-                     : "=l"(state)
-                     : "r"(smem_u32(full + i - 1))
-                     : "memory");
-        (void)state;
-      }
+      // no copy may still be writing shared memory when the CTA exits
+      if (lane == 0)
+        for (int i = 0; i < issued; ++i)
+          if (!mbar_wait_bounded(full + i, 0, limit)) *sflag = 1;
+      __syncwarp();
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else if (w == 2) {
     // ---- MMA issuer
     if (lane == 0) {
@@ -376,29 +463,66 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3_kernel(ConvArgs a) {
       const uint64_t b_base = umma_desc(smem_u32(sw), 768u, 128u);
       const uint32_t slot_units = slot_bytes >> 4;
       for (int i = 0; i < nin; ++i) {
+        const int g = i / G, s = i - g * G;
+        if (s == 0 && g >= 2 && !mbar_wait_bounded(freeb + (g - 2), 0, limit)) {
+          *sflag = 1;
+          break;
+        }
         if (!mbar_wait_bounded(full + i, 0, limit)) {
           *sflag = 1;
           break;
         }
         tc_fence_after();
-        conv_issue_input(a, i, tmem, a_base, b_base, slot_units, idesc);
+        conv_issue_input(a, i, g & 1, s, tmem, a_base, b_base, slot_units, idesc);
         umma_commit(done + i);
       }
     }
     __syncwarp();
   } else if (w >= 4) {
-    // ---- epilogue: output plane z0 + jj is final once input jj + 2 is in
-    const int ZP = a.Zc + 4;
-    for (int jj = 0; jj < nz; ++jj) {
-      if (!mbar_wait_bounded(done + jj + 2, 0, limit)) {
+    // ---- epilogue: output plane z0 + o is final once input o + 2 is in; its accumulator
+    //      is slot o - ga G + 2 of group ga = o / G, plus slot o - gb G + 2 of group
+    //      gb = (o + 2) / G when its inputs straddle two groups
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 of the tiles t = (w - 4) / 4 mod EPI_SETS
+    const uint32_t lane_base = (uint32_t)(32 * (w & 3)) << 16;
+    const int es = (w - 4) >> 2;
+    float bias[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) bias[c] = a.bias ? __ldg(a.bias + c) : 0.0f;
+    for (int o = 0; o < nz; ++o) {
+      if (!mbar_wait_bounded(done + o + 2, 0, limit)) {
         *sflag = 1;
         break;
       }
       tc_fence_after();
-      for (int t = 0; t < a.T; ++t) {
+      const int ga = o / G, gb = (o + 2) / G;
+      for (int t = es; t < a.T; t += EPI_SETS) {
         float acc[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + 16u * (uint32_t)(t * ZP + jj + 2), acc);
-        conv_epilogue<MODE>(a, acc, b, z0 + jj, y0, t, 32 * (w & 3) + lane);
+        tmem_ld16(tmem + lane_base + acc_col(a, ga & 1, t, o - ga * G + 2), acc);
+        if (gb != ga) {
+          float acc2[16];
+          tmem_ld16(tmem + lane_base + acc_col(a, gb & 1, t, o - gb * G + 2), acc2);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] += acc2[c];
+        }
+        conv_epilogue<MODE>(a, acc, bias, b, z0 + o, y0, t, 32 * (w & 3) + lane);
+      }
+      if ((o + 1) % G == 0) {
+        // the last output touching group g = (o + 1) / G - 1: clear its buffer for group g + 2
+        const int g = (o + 1) / G - 1;
+        if (g + 2 < ngroups) {
+          for (int t = es; t < a.T; t += EPI_SETS)
+            tmem_zero(tmem, (int)acc_col(a, g & 1, t, 0), (int)acc_col(a, g & 1, t + 1, 0), w & 3, 1);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            uint64_t state;
+            asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+                         : "=l"(state)
+                         : "r"(smem_u32(freeb + g))
+                         : "memory");
+            (void)state;
+          }
+        }
       }
     }
   }
@@ -435,6 +559,8 @@ static sim_status launch_conv(int mode, ConvArgs a, int B, cudaStream_t st) {
   a.tpl = g.tpl;
   a.contig = g.contig;
   a.Zc = g.Zc;
+  a.G = g.G;
+  a.ring = g.ring;
   a.slot_pos = g.slot_pos;
   a.ncols = g.ncols;
   const dim3 grid(cdiv(a.n, g.L), cdiv(a.n, g.Zc), B);
@@ -469,18 +595,18 @@ __global__ void __launch_bounds__(256) conv_dw_kernel(const bf16* __restrict__ i
     const int rem = i - pz * (L + 2) * P;
     const int ly = rem / P, px = rem - ly * P;
     const int gx = wrapi(px - 1, n), gy = wrapi(y0 - 1 + ly, n), gz = wrapi(z - 1 + pz, n);
-    const uint4* src = reinterpret_cast<const uint4*>(in + (((size_t)gz * n + gy) * n + gx) * CH);
+    const long long line = (long long)gz * n + gy;
     uint4* dst = reinterpret_cast<uint4*>(si + (size_t)i * CH);
-    dst[0] = __ldg(src);
-    dst[1] = __ldg(src + 1);
+    dst[0] = __ldg(reinterpret_cast<const uint4*>(in + act_off(line, n, 0, gx)));
+    dst[1] = __ldg(reinterpret_cast<const uint4*>(in + act_off(line, n, 1, gx)));
   }
   for (int i = threadIdx.x; i < L * n; i += 256) {
     const int ly = i / n, x = i - ly * n;
     uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
     if (y0 + ly < n) {
-      const uint4* src = reinterpret_cast<const uint4*>(dz + (((size_t)z * n + y0 + ly) * n + x) * CH);
-      lo = __ldg(src);
-      hi = __ldg(src + 1);
+      const long long line = (long long)z * n + y0 + ly;
+      lo = __ldg(reinterpret_cast<const uint4*>(dz + act_off(line, n, 0, x)));
+      hi = __ldg(reinterpret_cast<const uint4*>(dz + act_off(line, n, 1, x)));
     }
     uint4* dst = reinterpret_cast<uint4*>(sd + (size_t)i * CH);
     dst[0] = lo;
@@ -540,7 +666,7 @@ static sim_status launch_dw(const bf16* in, const bf16* dz, int n, int B, float*
 // ------------------------------------------------------------------ elementwise kernels
 // x[b][v][f] = bf16((gas[b][f][v] - mu_f) / sigma_f), f < 5; channels 5..15 are zero
 __global__ void closure_pack_kernel(const float* __restrict__ gas, F5 mu, F5 inv_sigma,
-                                    bf16* __restrict__ x, long long N3) {
+                                    bf16* __restrict__ x, long long N3, int n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (i >= N3) return;
@@ -549,14 +675,14 @@ __global__ void closure_pack_kernel(const float* __restrict__ gas, F5 mu, F5 inv
   for (int f = 0; f < 16; ++f) v[f] = 0.0f;
 #pragma unroll
   for (int f = 0; f < 5; ++f) v[f] = (gas[((size_t)b * 5 + f) * N3 + i] - mu.v[f]) * inv_sigma.v[f];
-  store_bf16x16(x + ((size_t)b * N3 + i) * CH, v);
+  act_store(x, (long long)b * (N3 / n) + i / n, n, (int)(i % n), v);
 }
 
 // loss += norm sum (y - (tgt - in) / s)^2 over 5 fields; dz4 = bf16(2 norm (y - t))
 __global__ void closure_loss_kernel(const float* __restrict__ y, const float* __restrict__ gin,
                                     const float* __restrict__ gtg, F5 inv_s, float norm,
                                     bf16* __restrict__ dz4, double* __restrict__ loss,
-                                    long long N3) {
+                                    long long N3, int n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   float acc = 0.0f;
@@ -572,7 +698,7 @@ __global__ void closure_loss_kernel(const float* __restrict__ y, const float* __
       acc += d * d;
       g[f] = 2.0f * norm * d;
     }
-    store_bf16x16(dz4 + ((size_t)b * N3 + i) * CH, g);
+    act_store(dz4, (long long)b * (N3 / n) + i / n, n, (int)(i % n), g);
   }
   block_sum_atomic(acc * norm, loss);
 }
@@ -704,7 +830,7 @@ static sim_status closure_forward(sim_closure_s* c, const float* gas, int n, int
                                   float* gas_apply, bool keep, cudaStream_t st) {
   const long long N3 = (long long)n * n * n;
   closure_pack_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, f5(c->mu), f5(c->inv_sigma),
-                                                              c->x, N3);
+                                                              c->x, N3, n);
   DH_LAUNCH_CHECK();
   bf16* acts[4] = {c->x, c->a1, c->a2, keep ? c->a3 : c->a1};
   float* zs[3] = {keep ? c->z1 : nullptr, keep ? c->z2 : nullptr, keep ? c->z3 : nullptr};
@@ -744,7 +870,7 @@ static sim_status closure_backprop(sim_closure_s* c, const float* gas, const flo
   for (int f = 0; f < 5; ++f) inv_s.v[f] = 1.0f / c->scale[f];
   const float norm = (float)(1.0 / (5.0 * (double)N3 * B));
   closure_loss_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(c->y, gas, target, inv_s, norm,
-                                                              c->d1, c->loss, N3);
+                                                              c->d1, c->loss, N3, n);
   DH_LAUNCH_CHECK();
   // layer l: input activation acts[l], pre-activation of layer l - 1: zs[l - 1]
   const bf16* acts[4] = {c->x, c->a1, c->a2, c->a3};
