@@ -155,6 +155,27 @@ __device__ __forceinline__ float gelu_f(float z) {
   return 0.5f * z * (x >= 0.0f ? 2.0f - q : q);
 }
 
+// GELU of two values with packed float32 arithmetic (FFMA2 / FMUL2); the same formula
+__device__ __forceinline__ float2 ff2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 gelu2_f(float2 z) {
+  const float2 x = __fmul2_rn(z, ff2(0.70710678118654752f));
+  const float2 ax = make_float2(fabsf(x.x), fabsf(x.y));
+  const float2 den = __ffma2_rn(ff2(0.3275911f), ax, ff2(1.0f));
+  const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+  const float2 x2 = __fmul2_rn(ax, ax);
+  const float2 e = make_float2(__expf(-x2.x), __expf(-x2.y));
+  float2 poly = __ffma2_rn(t, ff2(1.061405429f), ff2(-1.453152027f));
+  poly = __ffma2_rn(t, poly, ff2(1.421413741f));
+  poly = __ffma2_rn(t, poly, ff2(-0.284496736f));
+  poly = __ffma2_rn(t, poly, ff2(0.254829592f));
+  const float2 q = __fmul2_rn(__fmul2_rn(t, poly), e);
+  // 1 + erf(x) = 2 - q (x >= 0) or q (x < 0)
+  const float2 sg = make_float2(x.x >= 0.0f ? -1.0f : 1.0f, x.y >= 0.0f ? -1.0f : 1.0f);
+  const float2 base = make_float2(x.x >= 0.0f ? 2.0f : 0.0f, x.y >= 0.0f ? 2.0f : 0.0f);
+  const float2 r = __ffma2_rn(sg, q, base);
+  return __fmul2_rn(__fmul2_rn(z, ff2(0.5f)), r);
+}
+
 // d GELU / dz = Phi(z) + z phi(z), phi(z) = e^{-z^2 / 2} / sqrt(2 pi)
 __device__ __forceinline__ float gelu_grad_f(float z) {
   const float x = z * 0.70710678118654752f;
@@ -325,9 +346,13 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc
   if (MODE == CONV_HIDDEN) {
     float zc[16], hv[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      zc[c] = acc[c] + bias[c];
-      hv[c] = gelu_f(zc[c]);
+    for (int c = 0; c < 16; c += 2) {
+      const float2 zz = __fadd2_rn(make_float2(acc[c], acc[c + 1]), make_float2(bias[c], bias[c + 1]));
+      const float2 gg = gelu2_f(zz);
+      zc[c] = zz.x;
+      zc[c + 1] = zz.y;
+      hv[c] = gg.x;
+      hv[c + 1] = gg.y;
     }
     if (a.zout) {
       float4* zo = reinterpret_cast<float4*>(a.zout + ((size_t)b * N3 + v) * CH);
