@@ -141,6 +141,47 @@ def evaluate(p: SimParams, seed: int, closure, n_steps: int | None = None):
     return out
 
 
+def equal_error(p: SimParams, closure, seed: int = 4000):
+    """The closure's run against the plain solver at the error it reaches.
+
+    Runs from one linear field: plain and closure at n, plain at 2n, and a reference at 4n
+    (noise refined twice); every field error is taken on the n^3 grid against the reference
+    restricted twice (4:1). A power law err(m) = C m^-k through the plain errors at n and 2n
+    gives the resolution n_eq at which the plain solver would reach the closure's density
+    error, and the measured run times at n and 2n (t ~ m^q) its cost there."""
+    n = p.n
+    p2 = fine_params(p)
+    p4 = fine_params(p2)
+    noise = white_noise(n, seed)
+    plain = api.Simulation(p, noise)
+    corr = api.Simulation(p, noise)
+    corr.set_closure(closure)
+    mid = api.Simulation(p2)
+    w2 = api.refine_noise(noise, 2 * n, plain.ic_amplitude() / mid.ic_amplitude())
+    mid.reinit(w2)
+    ref = api.Simulation(p4)
+    ref.reinit(api.refine_noise(w2, 4 * n, mid.ic_amplitude() / ref.ic_amplitude()))
+    for s_ in (plain, corr, mid, ref):
+        s_.run()
+    truth = api.restrict_gas(api.restrict_gas(ref.state()["gas"]))
+    err = {"plain_n": rel_err(plain.state()["gas"][0], truth[0]),
+           "closure_n": rel_err(corr.state()["gas"][0], truth[0]),
+           "plain_2n": rel_err(api.restrict_gas(mid.state()["gas"])[0], truth[0])}
+    for s_ in (plain, corr, mid, ref):
+        s_.close()
+    ms = {"plain_n": timed_run(p), "closure_n": timed_run(p, closure), "plain_2n": timed_run(p2)}
+    out = {"grid": n, "reference_grid": 4 * n, "density_error": err, "ms_per_run": ms}
+    if err["plain_2n"] < err["plain_n"] and err["closure_n"] < err["plain_n"]:
+        k = np.log(err["plain_n"] / err["plain_2n"]) / np.log(2.0)
+        q = np.log(ms["plain_2n"] / ms["plain_n"]) / np.log(2.0)
+        n_eq = n * (err["plain_n"] / err["closure_n"]) ** (1.0 / k)
+        ms_eq = ms["plain_n"] * (n_eq / n) ** q
+        out.update({"error_exponent": k, "cost_exponent": q, "plain_grid_at_closure_error": n_eq,
+                    "plain_ms_at_closure_error": ms_eq,
+                    "closure_speedup_at_equal_error": ms_eq / ms["closure_n"]})
+    return out
+
+
 def timed_run(p: SimParams, closure=None, reps: int = 2):
     """ms per forward run (all steps) of the solver, with or without the closure."""
     sim = api.Simulation(p, white_noise(p.n, 99))
@@ -192,7 +233,8 @@ def experiment(n: int = 64, seeds: int = 6, run_steps: int = 100, iters: int = 6
            "train_loss_last": float(losses[-10:].mean()),
            "heldout_loss_plain_solver": plain_loss, "heldout_loss_untrained": before,
            "heldout_loss_trained": after,
-           "run_error": evaluate(p, 2000, clo)}
+           "run_error": evaluate(p, 2000, clo),
+           "equal_error": equal_error(p, clo)}
     if eval_n:
         pl = run_params(eval_n, run_steps)
         clo_eval = api.Closure(clo.weights())
