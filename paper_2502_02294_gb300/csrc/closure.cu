@@ -147,15 +147,8 @@ __device__ __forceinline__ float erfc_abs(float ax, float& e) {
   return t * poly * e;
 }
 
-// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2
-__device__ __forceinline__ float gelu_f(float z) {
-  const float x = z * 0.70710678118654752f;
-  float e;
-  const float q = erfc_abs(fabsf(x), e);
-  return 0.5f * z * (x >= 0.0f ? 2.0f - q : q);
-}
-
-// GELU of two values with packed float32 arithmetic (FFMA2 / FMUL2); the same formula
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2, on two values with packed float32
+// arithmetic (FFMA2 / FMUL2)
 __device__ __forceinline__ float2 ff2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 gelu2_f(float2 z) {
   const float2 x = __fmul2_rn(z, ff2(0.70710678118654752f));
