@@ -42,11 +42,10 @@ WORKLOAD_NAME = ("128^3 cells + 128^3 DM particles, box 128 Mpc/h, 100 steps a=0
                  "(every 10 steps) to the 2,097,152 white-noise amplitudes and 7 parameters")
 SWEEP_BYTES_PER_CELL = 40      # sweep: 5 float32 fields read + 5 written
 SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, input adjoint written
-# DRAM bytes per cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# captures summarised in profiles/; None where no capture of the current kernel exists
-# DRAM bytes per cell of one launch group from ncu (128^3, cold cache): forward sweep 44.2 MB
-# per call; adjoint sweep (x, y, z average of the marching pair, x with its transposes)
-# (417.6 + 252.3 + 252.7) / 3 MB
+# DRAM bytes per cell of one launch group (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised in profiles/ (128^3, cold cache): forward sweep 44.2 MB per
+# call; adjoint sweep (x, y, z average of the marching pair, x with its transposes)
+# (417.6 + 252.3 + 252.7) / 3 MB; None where no capture of the current kernel exists
 TRAFFIC_BYTES_PER_CELL = {"sweep": 21.06, "sweep_adjoint": 146.6}
 # algorithmic bytes per cell of one timed launch group of each class (one particle per cell)
 CLASS_BYTES_PER_CELL = {"sweep": SWEEP_BYTES_PER_CELL, "sweep_adjoint": SWEEP_ADJ_BYTES_PER_CELL,
