@@ -152,14 +152,16 @@ int32_t sim_batch_size(const sim_t* h);
 
 /* Hydro sweep kernel variants (Sec. 2.3.1 sweeps; the paper has no counterpart: these are
  * GB300 launch shapes). DEFAULT: the built-in choice for the grid size; TILE: shared-memory
- * tile; MARCH32 / MARCH16: one thread marches a line segment of 32 / 16 cells (forward: y
- * and z only, the forward x sweep always uses the tile; adjoint: every axis, x on x <-> y
- * transposed copies). */
+ * tile; MARCH32 / MARCH16: one thread marches a line segment of 32 / 16 cells; MARCH_FIT:
+ * the same with the segment length that fits the launch to whole waves of resident blocks
+ * (forward: y and z only, the forward x sweep always uses the tile; adjoint: every axis,
+ * x on x <-> y transposed copies). */
 enum {
   SIM_SWEEP_DEFAULT = 0,
   SIM_SWEEP_TILE = 1,
   SIM_SWEEP_MARCH32 = 2,
-  SIM_SWEEP_MARCH16 = 3
+  SIM_SWEEP_MARCH16 = 3,
+  SIM_SWEEP_MARCH_FIT = 4
 };
 
 /* Set the variant of the forward (fwd[3], per axis) and adjoint (adj[3]) sweeps of the

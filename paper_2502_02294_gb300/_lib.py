@@ -21,7 +21,7 @@ KT_NAMES = ("sweep", "sweep_adjoint", "kick", "kick_adjoint", "deposit", "deposi
             "poisson", "poisson_adjoint", "subgrid", "subgrid_adjoint")
 KT_N = len(KT_NAMES)
 KT_SWEEP, KT_SWEEP_ADJOINT = 0, 1
-SWEEP_DEFAULT, SWEEP_TILE, SWEEP_MARCH32, SWEEP_MARCH16 = range(4)
+SWEEP_DEFAULT, SWEEP_TILE, SWEEP_MARCH32, SWEEP_MARCH16, SWEEP_MARCH_FIT = range(5)
 CLOSURE_NWEIGHTS = 18197
 PARAM_NAMES = ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"]
 

@@ -157,10 +157,10 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
 // at load j it forms the first-order face j-1/2, the half-step state Uh_{j-1} and its
 // splits, the limited face (j-3)+1/2 and the output U'_{j-3}. No shared memory, no
 // barriers; adjacent threads own adjacent lines (x for the y/z sweeps, y for x).
-template <int AXIS, int L>
+template <int AXIS>
 __global__ void __launch_bounds__(128)
 sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
-                   float gam, float eps) {
+                   float gam, float eps, int L) {
   constexpr int F = 1 + AXIS;
   const int w = blockIdx.x * blockDim.x + threadIdx.x;  // line coordinate
   const int b = blockIdx.y / n;                         // instance
@@ -247,11 +247,11 @@ sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int 
 // D = lf dbL/2 (daR, dbR the limiter partials of the right-moving face flux, daL, dbL of
 // the left-moving one). Cell i-4 is then complete and lamUh_{i-4} = VJP(Uh_{i-4}).
 // d/dnu gathers sum_t F2_t lf_t / nu - sum_j lamUh_j dF1_j / 2.
-template <int AXIS, int L, int FC = 1 + AXIS>
+template <int AXIS, int FC = 1 + AXIS>
 __global__ void __launch_bounds__(128)
 sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                        float* __restrict__ luh_out, int n, SArg nua, float gam, float eps,
-                       DPart dnub) {
+                       DPart dnub, int L) {
   constexpr int F = FC;  // momentum component along the sweep
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y / n;  // instance
@@ -619,8 +619,10 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
 // (51 us at 128^3 for every axis); marching with segments of 32 wins for y/z on larger
 // grids (335 us vs 386 us at 256^3). The adjoint defaults to the marching pair for every
 // axis: y/z directly (2.1x the tile at 256^3), x on x <-> y transposed copies (the x tile
-// takes ~320 us at 128^3 against ~170 us for a y/z pair). sim_autotune times the variants
-// per handle.
+// takes ~320 us at 128^3 against ~170 us for a y/z pair), with segments fitted to whole
+// waves (at 128^3 three segments of 43 cells: every block resident at once, 140 us per
+// call in the benchmark pass against 156 us with 16-cell segments). sim_autotune times the
+// variants per handle.
 static int pick_fwd(int axis, int n, int variant) {
   if (axis == 0) return SIM_SWEEP_TILE;
   if (variant != SIM_SWEEP_DEFAULT) return variant;
@@ -629,14 +631,53 @@ static int pick_fwd(int axis, int n, int variant) {
 
 static int pick_adj(int axis, int variant) {
   (void)axis;
-  return variant != SIM_SWEEP_DEFAULT ? variant : SIM_SWEEP_MARCH32;
+  return variant != SIM_SWEEP_DEFAULT ? variant : SIM_SWEEP_MARCH_FIT;
 }
 
-template <int AXIS, int L>
+// Segment length of a marching kernel for an n^3 grid of B instances: the number k of
+// segments per line that minimises waves(k) x (n / k + halo), a wave being the blocks of
+// 128 threads that stay resident on all SMs at the kernel's register use (each thread
+// streams its segment plus the halo once).
+template <class Kern>
+static int fit_segment(Kern kernel, int n, int B, int halo) {
+  static std::atomic<int> resident{0};  // blocks resident on the device (first device used)
+  if (resident.load() == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 32;
+    }
+    resident.store(per_sm * sms > 0 ? per_sm * sms : 1);
+  }
+  const long long layer = (long long)cdiv(n, 128) * n * B;  // blocks of one segment layer
+  int best = n, best_cost = 1 << 30;
+  for (int k = 1; k <= n; ++k) {
+    const int L = cdiv(n, k);
+    if (L < 8) break;
+    const long long blocks = layer * cdiv(n, L);
+    const long long waves = (blocks + resident.load() - 1) / resident.load();
+    const long long cost = waves * (L + halo);
+    if (cost < best_cost) {
+      best_cost = (int)cost;
+      best = L;
+    }
+  }
+  return best;
+}
+
+static int segment_length(int variant) {
+  return variant == SIM_SWEEP_MARCH16 ? 16 : 32;
+}
+
+template <int AXIS>
 static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, float gam,
-                                 float eps, int B, cudaStream_t st) {
+                                 float eps, int B, int variant, cudaStream_t st) {
+  const int L = variant == SIM_SWEEP_MARCH_FIT ? fit_segment(sweep_march_kernel<AXIS>, n, B, 6)
+                                               : segment_length(variant);
   dim3 grid(cdiv(n, 128), n * B, cdiv(n, L));
-  sweep_march_kernel<AXIS, L><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps);
+  sweep_march_kernel<AXIS><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps, L);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -645,10 +686,8 @@ template <int AXIS>
 static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, float gam,
                                  float eps, int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  if (AXIS != 0) {
-    if (variant == SIM_SWEEP_MARCH32) return launch_march_t<AXIS, 32>(uin, uout, n, nu, gam, eps, B, st);
-    if (variant == SIM_SWEEP_MARCH16) return launch_march_t<AXIS, 16>(uin, uout, n, nu, gam, eps, B, st);
-  }
+  if (AXIS != 0 && variant != SIM_SWEEP_TILE)
+    return launch_march_t<AXIS>(uin, uout, n, nu, gam, eps, B, variant, st);
   constexpr int NC = (C::S + 6) * C::W;
   const size_t smem = 15 * NC * sizeof(float);
   dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n * B);
@@ -728,16 +767,16 @@ static sim_status launch_transpose_xy(const float* in0, float* out0, int nf0, co
   return SIM_OK;
 }
 
-template <int AXIS, int L>
+template <int AXIS>
 static sim_status launch_adj_march_t(const float* uin, const float* lout, float* lin, int n,
                                      SArg nu, float gam, float eps, DPart dnu, float* scratch,
-                                     int B, cudaStream_t st) {
+                                     int B, int L, cudaStream_t st) {
   if (!scratch) {
     set_error("internal: marching sweep adjoint needs a 5 n^3 scratch buffer per instance");
     return SIM_EINVAL;
   }
   dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
-  sweep_adj_march_kernel<AXIS, L><<<g1, 128, 0, st>>>(uin, lout, scratch, n, nu, gam, eps, dnu);
+  sweep_adj_march_kernel<AXIS><<<g1, 128, 0, st>>>(uin, lout, scratch, n, nu, gam, eps, dnu, L);
   DH_LAUNCH_CHECK();
   dim3 g2(cdiv(n, 256), n, n * B);
   sweep_adj_final_kernel<AXIS><<<g2, 256, 0, st>>>(uin, lout, scratch, lin, n, nu, gam);
@@ -747,15 +786,14 @@ static sim_status launch_adj_march_t(const float* uin, const float* lout, float*
 
 // The x adjoint as the y-marching pair on x <-> y transposed copies (momentum component 1
 // stays the one along the sweep). scratch: 4 x 5 n^3 floats per instance.
-template <int L>
 static sim_status launch_adj_x_transposed(const float* uin, const float* lout, float* lin, int n,
                                           SArg nu, float gam, float eps, DPart dnu,
-                                          float* scratch, int B, cudaStream_t st) {
+                                          float* scratch, int B, int L, cudaStream_t st) {
   const size_t F5 = (size_t)5 * n * n * n * B;
   float *ut = scratch, *lt = scratch + F5, *it = scratch + 2 * F5, *luh = scratch + 3 * F5;
   DH_TRY(launch_transpose_xy(uin, ut, 5 * B, lout, lt, 5 * B, n, st));
   dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
-  sweep_adj_march_kernel<1, L, 1><<<g1, 128, 0, st>>>(ut, lt, luh, n, nu, gam, eps, dnu);
+  sweep_adj_march_kernel<1, 1><<<g1, 128, 0, st>>>(ut, lt, luh, n, nu, gam, eps, dnu, L);
   DH_LAUNCH_CHECK();
   dim3 g2(cdiv(n, 256), n, n * B);
   sweep_adj_final_kernel<1, 1><<<g2, 256, 0, st>>>(ut, lt, luh, it, n, nu, gam);
@@ -768,20 +806,19 @@ static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float*
                                      SArg nu, float gam, float eps, DPart dnu, float* scratch,
                                      int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  if (AXIS == 0 && (variant == SIM_SWEEP_MARCH32 || variant == SIM_SWEEP_MARCH16)) {
-    if (!scratch) {
-      set_error("internal: the transposed x adjoint needs a 20 n^3 scratch buffer per instance");
-      return SIM_EINVAL;
+  if (variant != SIM_SWEEP_TILE) {
+    const int L = variant == SIM_SWEEP_MARCH_FIT
+                      ? fit_segment(sweep_adj_march_kernel<AXIS == 0 ? 1 : AXIS, AXIS == 0 ? 1 : 1 + AXIS>,
+                                    n, B, 9)
+                      : segment_length(variant);
+    if (AXIS == 0) {
+      if (!scratch) {
+        set_error("internal: the transposed x adjoint needs a 20 n^3 scratch buffer per instance");
+        return SIM_EINVAL;
+      }
+      return launch_adj_x_transposed(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, L, st);
     }
-    return variant == SIM_SWEEP_MARCH32
-               ? launch_adj_x_transposed<32>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st)
-               : launch_adj_x_transposed<16>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
-  }
-  if (AXIS != 0) {
-    if (variant == SIM_SWEEP_MARCH32)
-      return launch_adj_march_t<AXIS, 32>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
-    if (variant == SIM_SWEEP_MARCH16)
-      return launch_adj_march_t<AXIS, 16>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
+    return launch_adj_march_t<AXIS>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, L, st);
   }
   constexpr int NC = (C::SA + 10) * C::WA;
   const size_t smem = 20 * NC * sizeof(float);
@@ -857,7 +894,7 @@ extern "C" sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int3
                                 double nu, double gamma, double limiter_eps, int32_t variant,
                                 void* stream) {
   if (!u_in || !u_out || n < 1 || u_in == u_out || variant < SIM_SWEEP_DEFAULT ||
-      variant > SIM_SWEEP_MARCH16) {
+      variant > SIM_SWEEP_MARCH_FIT) {
     dh::set_error("sim_sweep: null/aliased buffers, n < 1 or unknown variant");
     return SIM_EINVAL;
   }
@@ -870,7 +907,7 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
                                         double limiter_eps, double* dnu, int32_t variant,
                                         void* stream) {
   if (!u_in || !lam_out || !lam_in || n < 1 || lam_in == lam_out || lam_in == u_in ||
-      variant < SIM_SWEEP_DEFAULT || variant > SIM_SWEEP_MARCH16) {
+      variant < SIM_SWEEP_DEFAULT || variant > SIM_SWEEP_MARCH_FIT) {
     dh::set_error("sim_sweep_adjoint: null/aliased buffers, n < 1 or unknown variant");
     return SIM_EINVAL;
   }

@@ -1247,7 +1247,7 @@ sim_status sim_set_sweep_variants(sim_t* h, const int32_t* fwd, const int32_t* a
   for (int a = 0; a < 3; ++a) {
     const int vals[2] = {fwd ? fwd[a] : 0, adj ? adj[a] : 0};
     for (int v : vals)
-      if (v < SIM_SWEEP_DEFAULT || v > SIM_SWEEP_MARCH16) {
+      if (v < SIM_SWEEP_DEFAULT || v > SIM_SWEEP_MARCH_FIT) {
         set_error("sim_set_sweep_variants: unknown variant %d", v);
         return fail(h, SIM_EINVAL);
       }
@@ -1274,7 +1274,7 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
   DH_CUDA_TRY(cudaEventCreate(&e1));
   const int i = h->step < h->prm.n_steps ? h->step : h->prm.n_steps - 1;
   const SArg nu = sc(h, i, SC_NU);
-  const int cand[3] = {SIM_SWEEP_TILE, SIM_SWEEP_MARCH32, SIM_SWEEP_MARCH16};
+  const int cand[4] = {SIM_SWEEP_TILE, SIM_SWEEP_MARCH32, SIM_SWEEP_MARCH16, SIM_SWEEP_MARCH_FIT};
   auto time_it = [&](auto launch, float* ms) -> sim_status {
     DH_TRY(launch());  // warm-up
     float best = 1e30f;
@@ -1293,7 +1293,7 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
   auto body = [&]() -> sim_status {
     for (int axis = 0; axis < 3; ++axis) {
       float bf = 1e30f, ba = 1e30f;
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < 4; ++c) {
         float t = 0.0f;
         if (axis != 0 || c == 0) {  // forward x: the tile only
           DH_TRY(time_it([&] { return launch_sweep(axis, h->gas, h->w_gas2, h->n, nu,

@@ -62,10 +62,11 @@ def test_sweep_sharp_fronts_and_uniform(dh):
 
 
 @pytest.mark.parametrize("n", [20, 70])
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_sweep_forms_match_oracle(dh, n, variant):
-    """Every kernel form (tile, marching in 32- and 16-cell segments; x adjoint via
-    transposed copies) against the oracle, on a grid with a ragged last segment.
+    """Every kernel form (tile, marching in 32- and 16-cell segments or in the segment length
+    fitted to whole waves; x adjoint via transposed copies) against the oracle, on a grid
+    with a ragged last segment.
 
     The forms recompute the forward identically, so they take the same float32 limiter
     and sign decisions: their adjoints agree with each other to float32 rounding (1e-6).
