@@ -44,9 +44,10 @@ SWEEP_BYTES_PER_CELL = 40      # sweep: 5 float32 fields read + 5 written
 SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, input adjoint written
 # DRAM bytes per cell of one launch group (dram__bytes_read.sum + dram__bytes_write.sum) from
 # the ncu captures summarised in profiles/ (128^3, cold cache): forward sweep 44.2 MB per
-# call; adjoint sweep (x, y, z average of the marching pair, x with its transposes)
-# (417.6 + 252.3 + 252.7) / 3 MB; None where no capture of the current kernel exists
-TRAFFIC_BYTES_PER_CELL = {"sweep": 21.06, "sweep_adjoint": 146.6}
+# call; adjoint sweep (x, y, z average of the marching pair with fitted segments, x with its
+# transposes) (427.2 + 262.0 + 262.8) / 3 MB; None where no capture of the current kernel
+# exists
+TRAFFIC_BYTES_PER_CELL = {"sweep": 21.06, "sweep_adjoint": 151.3}
 # algorithmic bytes per cell of one timed launch group of each class (one particle per cell)
 CLASS_BYTES_PER_CELL = {"sweep": SWEEP_BYTES_PER_CELL, "sweep_adjoint": SWEEP_ADJ_BYTES_PER_CELL,
                         "deposit": 28, "poisson": 16, "subgrid": 44, "subgrid_adjoint": 60}
