@@ -5,16 +5,17 @@
 // bfloat16 weights and activations, float32 accumulation, applied as a residual update of
 // the five gas fields on normalised inputs: u <- u + s * NN((u - mu) / sigma).
 //
-// Every convolution runs as an implicit GEMM on the tensor cores (tcgen05, M = 128 voxels,
-// N = 16 output channels, K = 16 input channels per tap, 27 taps accumulated in TMEM). All
-// activations are channels-last bfloat16 with 16 channels (the 5 gas fields are padded with
-// zeros), so every layer is the same 16 -> 16 kernel with zero-padded weights. A CTA stages
-// the input lines around its output lines in shared memory with one padding column on each
-// side (line pitch P = n + 2), in the no-swizzle K-major operand layout (two planes of 8
-// channels, 16 bytes per position). With a uniform 16-byte row pitch, the operand of tap
-// (dx, dy, dz) for a tile of 128 consecutive positions is the same tile shifted by
-// ((dz (L + 2) + dy) P + dx) positions: 27 descriptors, no gather. Positions that fall on a
-// padding column produce results that are discarded.
+// Every convolution runs as an implicit GEMM on the tensor cores (tcgen05, M = 128
+// positions, K = 16 input channels per tap, accumulators in TMEM). All activations are
+// bfloat16 with 16 channels (the 5 gas fields are padded with zeros), so every layer is the
+// same 16 -> 16 kernel with zero-padded weights. Activations are stored line-half-major
+// ([z][y][2][x][8]): each 8-channel half of a line is a contiguous run of 16-byte positions,
+// the row layout of the no-swizzle K-major operand, so an input plane reaches shared memory
+// as bulk copies. One padding column on each side of every staged line (pitch P = n + 2)
+// makes the operand of an in-plane shift (dy, dx) the same tile moved by (dy P + dx) rows:
+// descriptors only, no gather; positions that fall on a padding column give discarded
+// results. The three dz taps of one (dy, dx) form one N = 48 operand that updates three
+// output planes at once (see the geometry section).
 //
 // Backward: the gradient with respect to a layer's input is the same convolution with the
 // taps mirrored and each tap's matrix transposed (same kernel, other weight packing), its
