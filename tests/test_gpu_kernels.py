@@ -61,12 +61,13 @@ def test_sweep_sharp_fronts_and_uniform(dh):
         assert torch.equal(dh.sweep(Ug, axis, 0.7), Ug)
 
 
-@pytest.mark.parametrize("n", [20, 70])
+@pytest.mark.parametrize("n", [2, 3, 5, 20, 70])
 @pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_sweep_forms_match_oracle(dh, n, variant):
     """Every kernel form (tile, marching in 32- and 16-cell segments or in the segment length
-    fitted to whole waves; x adjoint via transposed copies) against the oracle, on a grid
-    with a ragged last segment.
+    fitted to whole waves; x adjoint via transposed copies) against the oracle, on grids
+    smaller than the stencil (2, 3, 5 cells: every halo wraps onto the line itself) and on
+    grids with a ragged last tile and segment.
 
     The forms recompute the forward identically, so they take the same float32 limiter
     and sign decisions: their adjoints agree with each other to float32 rounding (1e-6).
@@ -127,7 +128,7 @@ def _positions(n, seed, scale):
     return s
 
 
-@pytest.mark.parametrize("n", [8, 16, 33])
+@pytest.mark.parametrize("n", [2, 3, 8, 16, 33])
 def test_deposit_and_readout(dh, n):
     box = 10.0
     sg, so = f32(_positions(n, 5, 2.5 * box / n))
