@@ -13,6 +13,9 @@
 //              F2_{i+1/2} = [Fh^R_i + phi(dL, dR)] - [Fh^L_{i+1} - phi(dL', dR')]
 //              with the gated van Leer limiter phi and half differences of Fh^R / Fh^L.
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "common.cuh"
 
@@ -640,16 +643,29 @@ static int pick_adj(int axis, int variant) {
 // streams its segment plus the halo once).
 template <class Kern>
 static int fit_segment(Kern kernel, int n, int B, int halo) {
-  static std::atomic<int> resident{0};  // blocks resident on the device (first device used)
-  if (resident.load() == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0) != cudaSuccess) {
-      cudaGetLastError();
-      return 32;
+  // blocks of 128 threads resident on the current device, per kernel and device
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, long long> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 32;
+  }
+  long long resident = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+      int sms = 0, per_sm = 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 32;
+      }
+      it = cache.emplace(key, per_sm * sms > 0 ? (long long)per_sm * sms : 1).first;
     }
-    resident.store(per_sm * sms > 0 ? per_sm * sms : 1);
+    resident = it->second;
   }
   const long long layer = (long long)cdiv(n, 128) * n * B;  // blocks of one segment layer
   int best = n, best_cost = 1 << 30;
@@ -657,7 +673,7 @@ static int fit_segment(Kern kernel, int n, int B, int halo) {
     const int L = cdiv(n, k);
     if (L < 8) break;
     const long long blocks = layer * cdiv(n, L);
-    const long long waves = (blocks + resident.load() - 1) / resident.load();
+    const long long waves = (blocks + resident - 1) / resident;
     const long long cost = waves * (L + halo);
     if (cost < best_cost) {
       best_cost = (int)cost;
