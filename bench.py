@@ -186,6 +186,21 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(vals, ws):
+    """Entry-wise maximum of a tensor over the ranks of the default process group (the
+    slowest rank's times); the tensor itself for one rank."""
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    return vals.tolist()
+
+
+def job_throughput(cells_per_rank, ws, ms):
+    """Whole-job cell-steps/s: every rank's cells over the slowest rank's time (weak scaling:
+    each rank runs its own replica of the workload)."""
+    return cells_per_rank * ws / (ms / 1e3)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -444,10 +459,7 @@ def main():
 
     # ---- max over ranks
     vals = torch.tensor([ms, fwd_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    ms, fwd_ms, e2e_ms = vals.tolist()
-    cell_steps = n3 * p.n_steps * ws
+    ms, fwd_ms, e2e_ms = max_over_ranks(vals, ws)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -456,7 +468,7 @@ def main():
     peak_bw = peaks["hbm_gbs"] if peaks else 6800.0
     line = {
         "metric": METRIC,
-        "value": cell_steps / (ms / 1e3),
+        "value": job_throughput(n3 * p.n_steps, ws, ms),
         "unit": "cell-steps/s",
         "n_gpus": ws,
         "steps": args.steps,
@@ -470,9 +482,9 @@ def main():
         "config": _config(ws),
         "cuda_graphs": not args.no_graphs,
         "sweep_variants": {"fwd": variants[0], "adj": variants[1]},
-        "fwd_value": cell_steps / (fwd_ms / 1e3),
+        "fwd_value": job_throughput(n3 * p.n_steps, ws, fwd_ms),
         "fwd_ms_per_step": fwd_ms,
-        "e2e": {"value": cell_steps / (e2e_ms / 1e3), "unit": "cell-steps/s",
+        "e2e": {"value": job_throughput(n3 * p.n_steps, ws, e2e_ms), "unit": "cell-steps/s",
                 "h2d_bytes_per_step": n3 * 4, "d2h_bytes_per_step": n3 * 4 + 8},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": kclass[dom]["achieved_gbs"], "peak": peak_bw,
