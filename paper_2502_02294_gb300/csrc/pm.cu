@@ -497,61 +497,15 @@ sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cud
 }
 
 // ------------------------------------------------------------------ adjoints
-__global__ void gas_kick_adj_kernel(const float* __restrict__ u, const float* __restrict__ g,
-                                    SArg Ka, float* __restrict__ lam, float4* __restrict__ lam_g4,
-                                    DPart dK, int N3) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  u += (size_t)b * 5 * N3;
-  lam += (size_t)b * 5 * N3;
-  g += (size_t)b * 3 * N3;
-  lam_g4 += (size_t)b * N3;
-  const float K = Ka.at(b);
-  float dkf = 0.0f;
-  if (i < N3) {
-    const float rho = u[i];
-    const float le = lam[4 * N3 + i];
-    float lrho = lam[i];
-    float mg = 0.0f, g2 = 0.0f;
-    float m[3], gg[3], lm[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      gg[j] = g[j * N3 + i];
-      m[j] = u[(1 + j) * N3 + i];
-      lm[j] = lam[(1 + j) * N3 + i];
-      mg += m[j] * gg[j];
-      g2 += gg[j] * gg[j];
-    }
-    dkf = le * (mg + K * rho * g2);
-    float4 lg = lam_g4[i];
-    float* lgj = &lg.x;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      lrho += K * lm[j] * gg[j];
-      dkf += lm[j] * rho * gg[j];
-      lgj[j] += lm[j] * rho * K + le * (K * m[j] + K * K * rho * gg[j]);
-      lam[(1 + j) * N3 + i] = lm[j] + le * K * gg[j];
-    }
-    lam_g4[i] = lg;
-    lrho += 0.5f * K * K * g2 * le;
-    lam[i] = lrho;
-  }
-  if (dK.p) block_sum_atomic(dkf, dK.at(b));
-}
-
-sim_status launch_gas_kick_adjoint(const float* gas, const float* g, SArg K, float* lam,
-                                   float4* lam_g4, DPart dK, int n, int B, cudaStream_t st) {
-  const int N3 = n * n * n;
-  gas_kick_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, g, K, lam, lam_g4, dK, N3);
-  DH_LAUNCH_CHECK();
-  return SIM_OK;
-}
-
+// Adjoint of kick_drift_kernel: the particle part and, when lam_gas is not NULL, the gas
+// kick of the cell with the same index at the pre-kick gas state gas_u (its force adjoint
+// goes to lam_g4 with a float4 atomic: other particles scatter into the node concurrently).
 __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float* __restrict__ p0,
                                       const float* __restrict__ g, SArg Ka, SArg dtaua,
                                       float* __restrict__ lam_s, float* __restrict__ lam_p,
-                                      float4* __restrict__ lam_g4, DPart dK, DPart ddtau, int n,
-                                      float inv_dx) {
+                                      float4* __restrict__ lam_g4, DPart dK, DPart ddtau,
+                                      const float* __restrict__ gas_u, float* __restrict__ lam_gas,
+                                      int n, float inv_dx) {
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   const size_t o3 = (size_t)q.b * 3 * N3;
@@ -602,6 +556,36 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
       lam_s[j * N3 + i] = ls[j] + K * gs[j];
       lam_p[j * N3 + i] = lp[j];
     }
+    if (lam_gas) {
+      // gas kick of cell i: m' = m + rho g K, eps' = eps + K m.g + K^2 rho |g|^2 / 2
+      const float* u = gas_u + (size_t)q.b * 5 * N3;
+      float* lam = lam_gas + (size_t)q.b * 5 * N3;
+      const float rho = u[i];
+      const float le = lam[4 * N3 + i];
+      float lrho = lam[i];
+      float mg = 0.0f, g2 = 0.0f;
+      float m[3], gg[3], lm[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        gg[j] = g[j * N3 + i];
+        m[j] = u[(1 + j) * N3 + i];
+        lm[j] = lam[(1 + j) * N3 + i];
+        mg += m[j] * gg[j];
+        g2 += gg[j] * gg[j];
+      }
+      dk += le * (mg + K * rho * g2);
+      float lg[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        lrho += K * lm[j] * gg[j];
+        dk += lm[j] * rho * gg[j];
+        lg[j] = lm[j] * rho * K + le * (K * m[j] + K * K * rho * gg[j]);
+        lam[(1 + j) * N3 + i] = lm[j] + le * K * gg[j];
+      }
+      lrho += 0.5f * K * K * g2 * le;
+      lam[i] = lrho;
+      atomicAdd(lam_g4 + i, make_float4(lg[0], lg[1], lg[2], 0.0f));
+    }
   }
   // lam_g += interp^T(K lp): warp-aggregated float4 atomics (all lanes take part)
   float lpl[3];
@@ -634,11 +618,10 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
 
 sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, SArg K,
                                      SArg dtau, float* lam_s, float* lam_p, float4* lam_g4,
-                                     DPart dK, DPart ddtau, int n, float inv_dx, int B,
-                                     cudaStream_t st) {
-  kick_drift_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s0, p0, g, K, dtau, lam_s,
-                                                                  lam_p, lam_g4, dK, ddtau, n,
-                                                                  inv_dx);
+                                     DPart dK, DPart ddtau, const float* gas_u, float* lam_gas,
+                                     int n, float inv_dx, int B, cudaStream_t st) {
+  kick_drift_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(
+      s0, p0, g, K, dtau, lam_s, lam_p, lam_g4, dK, ddtau, gas_u, lam_gas, n, inv_dx);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

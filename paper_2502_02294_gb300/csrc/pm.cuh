@@ -61,20 +61,19 @@ sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cud
 // The adjoint of the force field is accumulated node-interleaved: lam_g4[b][i] = (lam_gx,
 // lam_gy, lam_gz, 0) for node i of instance b (16-byte aligned), so that a particle adds
 // its three components at a CIC corner with one vector atomic.
-// Gas kick: lam (5 n^3, in/out) through the kick at the pre-kick gas state `gas`;
-// lam_g4 (n^3 float4) += partial (plain add, cell-owned); dK += lam . d/dK.
-sim_status launch_gas_kick_adjoint(const float* gas, const float* g, SArg K, float* lam,
-                                   float4* lam_g4, DPart dK, int n, int B, cudaStream_t st);
 // Particle kick (+ preceding drift if dtau != 0), reverse order:
 //   forward: p1 = p0 + K interp(g, s0); s1 = s0 + dtau p1
 //   given lam_s (= lam_s1), lam_p (= lam_p1 from later use), both in/out:
 //   lam_p1 += dtau lam_s1; d_dtau += lam_s1 . p1; lam_p0 = lam_p1;
 //   lam_s0 = lam_s1 + K grad(interp g)(s0) . lam_p1; lam_g4 += interp^T(K lam_p1) (float4
 //   atomics); dK += lam_p1 . interp(g)(s0).
+// If lam_gas != NULL, in the same launch the gas kick's adjoint at the pre-kick gas state
+// gas_u: lam_gas (5 n^3, in/out, cell-owned), lam_g4 += its partial (float4 atomic),
+// dK += lam_gas . d/dK.
 sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const float* g, SArg K,
                                      SArg dtau, float* lam_s, float* lam_p, float4* lam_g4,
-                                     DPart dK, DPart ddtau, int n, float inv_dx, int B,
-                                     cudaStream_t st);
+                                     DPart dK, DPart ddtau, const float* gas_u, float* lam_gas,
+                                     int n, float inv_dx, int B, cudaStream_t st);
 // Deposit adjoint for delta = cm * count + rho_gas - 1:
 //   lam_s += cm grad(interp lam_delta)(s) / dx ; d_cm += sum_p interp(lam_delta)(s_p)
 sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg cm,

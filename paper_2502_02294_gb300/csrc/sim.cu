@@ -614,11 +614,9 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot,
   //    has already put its adjoint of g(a_{i+1}) into lamG1)
   if (P.gravity_on && kick_out) {
     DH_TRY(timed(h, SIM_KT_KICK_ADJOINT, [&] {
-      DH_TRY(launch_gas_kick_adjoint(T.Usg, T.g1, K2, h->lam_gas, lam_g4(h->lamG1),
-                                     slot_part(slot, SL_DK2), h->n, B, st));
       return launch_kick_drift_adjoint(T.s1, nullptr, T.g1, K2, sarg(0.0f), h->lam_s, h->lam_p,
-                                       lam_g4(h->lamG1), slot_part(slot, SL_DK2), dpart(nullptr), h->n,
-                                       (float)h->inv_dx, B, st);
+                                       lam_g4(h->lamG1), slot_part(slot, SL_DK2), dpart(nullptr),
+                                       T.Usg, h->lam_gas, h->n, (float)h->inv_dx, B, st);
     }));
   }
   // 4. force at a_{i+1}
@@ -649,11 +647,9 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot,
   // 1. first half kick and drift
   DH_TRY(dzero(h->lamG0, 4 * B * h->N3 * sizeof(float), st));
   DH_TRY(timed(h, SIM_KT_KICK_ADJOINT, [&] {
-    if (P.gravity_on)
-      DH_TRY(launch_gas_kick_adjoint(T.U0, T.g0, K1, h->lam_gas, lam_g4(h->lamG0),
-                                     slot_part(slot, slot_in), h->n, B, st));
     return launch_kick_drift_adjoint(T.s0, T.p0, T.g0, K1, sc(h, i, SC_DTAU), h->lam_s, h->lam_p,
                                      lam_g4(h->lamG0), slot_part(slot, slot_in), slot_part(slot, SL_DDTAU),
+                                     P.gravity_on ? T.U0 : nullptr, P.gravity_on ? h->lam_gas : nullptr,
                                      h->n, (float)h->inv_dx, B, st);
   }));
   float* t = h->lamG0;
