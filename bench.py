@@ -201,6 +201,19 @@ def job_throughput(cells_per_rank, ws, ms):
     return cells_per_rank * ws / (ms / 1e3)
 
 
+def nvsmi_id(dev: int) -> str:
+    """nvidia-smi --id of CUDA device `dev`: its UUID (nvidia-smi's own indices need not
+    follow CUDA_VISIBLE_DEVICES), else the CUDA ordinal."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    return str(dev)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -208,8 +221,8 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
         self.proc = None
         self.path = None
 
@@ -369,7 +382,7 @@ def main():
     for _ in range(args.warmup):
         hot_path(noise)
     # ---- device-resident timing (value)
-    clocks = Clocks(torch.cuda.current_device())
+    clocks = Clocks(nvsmi_id(torch.cuda.current_device()))
     clocks.start()
     launches0 = dh.lib.sim_kernel_launches()
     times = []

@@ -296,7 +296,9 @@ sim_status sim_set_state(sim_t* h, const float* gas, const float* part, int32_t 
 sim_status sim_schedule(const sim_t* h, int32_t i, double* out6);
 
 /* Largest CFL number max(|v_d| + c_s) dtau / dx over cells and directions for the
- * current state and the next step's dtau (Eq. dt). Synchronises the stream. */
+ * current state and the next step's dtau (Eq. dt). Synchronises the stream. A non-finite
+ * value anywhere in the gas state makes the result NaN (sim_run with cfl_max > 0 then
+ * returns SIM_ENAN). */
 sim_status sim_cfl(sim_t* h, double* cfl_out);
 
 /* ------------------------------------------------------------------ learned closure
@@ -346,8 +348,20 @@ sim_status sim_closure_gradient(sim_closure_t* c, const float* gas, const float*
 sim_status sim_closure_train_step(sim_closure_t* c, const float* gas, const float* target,
                                   int32_t n, int32_t B, double lr, double* loss_out);
 
-/* Synchronise and report a timed-out tensor-core wait of an earlier call (SIM_ETIMEOUT). */
+/* Synchronise and report a timed-out tensor-core wait of an earlier call (SIM_ETIMEOUT),
+ * then clear the report: a later call returns SIM_OK unless a wait timed out again. The
+ * outputs of a call whose wait timed out are undefined. */
 sim_status sim_closure_status(sim_closure_t* c);
+
+/* Time limit of each wait inside the closure's tensor-core kernels (a stage waiting for an
+ * input plane, for its MMAs, or for a free accumulator buffer), in nanoseconds of the GPU's
+ * global timer; default 1e9 (1 s). A wait that runs out records SIM_ETIMEOUT for
+ * sim_closure_status and its kernel stops early, after waiting (up to 4 s) for the copies
+ * and MMAs it has already issued, so the context stays usable. ns = 0 allows a single
+ * non-blocking check per wait (which makes the first waits of a launch give up: the way to
+ * exercise this path). Applies to later launches; graphs captured earlier keep the limit
+ * they were captured with. The paper has no counterpart. SIM_EINVAL if ns < 0. */
+sim_status sim_closure_set_wait_limit(sim_closure_t* c, int64_t ns);
 
 /* Apply `c` at the end of every step of the handle (sim_step, sim_run, groups), on the
  * handle's stream; NULL removes it (the plain solver). Prepares the closure's workspace for

@@ -74,6 +74,7 @@ SIGNATURES = {
     "sim_closure_gradient": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _P, _P]),
     "sim_closure_train_step": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _D, _P]),
     "sim_closure_status": (ctypes.c_int, [_P]),
+    "sim_closure_set_wait_limit": (ctypes.c_int, [_P, _I64]),
     "sim_set_closure": (ctypes.c_int, [_P, _P]),
     "sim_refine_noise": (ctypes.c_int, [_P, _I32, _P, _I32, _D, _P]),
     "sim_restrict_gas": (ctypes.c_int, [_P, _I32, _P, _I32, _P]),

@@ -376,6 +376,10 @@ class Closure:
     def status(self):
         check(lib.sim_closure_status(self.h), "sim_closure_status")
 
+    def set_wait_limit(self, ns: int):
+        """Time limit of each tensor-core pipeline wait, in nanoseconds (default 1e9)."""
+        check(lib.sim_closure_set_wait_limit(self.h, int(ns)), "sim_closure_set_wait_limit")
+
     def close(self):
         if getattr(self, "h", None):
             lib.sim_closure_destroy(self.h)
@@ -481,6 +485,7 @@ class SimRunFunction(torch.autograd.Function):
         sim.run()
         st = sim.state()
         ctx.sim = sim
+        ctx.pdev = pvec.device
         return st["gas"]
 
     @staticmethod
@@ -490,7 +495,7 @@ class SimRunFunction(torch.autograd.Function):
                                        want_noise=ctx.needs_input_grad[0])
         sim.close()
         ctx.sim = None
-        return dnoise, dpar.to(torch.float64), None
+        return dnoise, dpar.to(device=ctx.pdev, dtype=torch.float64), None
 
 
 def simulate(noise, pvec, params: SimParams):

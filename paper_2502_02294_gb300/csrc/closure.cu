@@ -223,7 +223,12 @@ struct ConvArgs {
   float* gas;          // OUT_APPLY: [B][5][n^3], += scale * y
   F5 scale;
   int* err;
+  unsigned long long wait_ns;  // limit of each pipeline wait (global-timer nanoseconds)
 };
+
+// Limit of the final waits for a CTA's own bulk copies and MMAs in flight: those complete
+// without help from other warps, so they are drained even after a pipeline wait gave up.
+constexpr unsigned long long kDrainNs = 4000000000ull;
 
 // Bulk copies (async proxy, completion counted in bytes on the plane's mbarrier) of input
 // plane gz (periodic) into ring slot `slot_addr`: for each of the L + 2 lines and each
@@ -386,8 +391,12 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc
 // every output plane once its last input's MMAs are done (warp w reads TMEM lanes
 // 32 (w % 4) .. + 31 of the tiles t = (w - 4) / 4 mod EPI_SETS) and free each buffer
 // after its last plane. Every
-// barrier is used once (one per input plane or group), every wait is bounded; a timeout
-// sets an error flag and the CTA still frees its TMEM.
+// barrier is used once (one per input plane or group), every wait is bounded by a.wait_ns;
+// a wait that gives up sets an error flag and its role stops. Before the CTA frees its TMEM
+// and exits, the loader waits for every bulk copy it issued and the MMA thread for the
+// commit of the last MMAs it issued (kDrainNs each), so nothing asynchronous still writes
+// shared or tensor memory. A warp's wait outcome is taken by lane 0 and broadcast, so the
+// warp-wide TMEM loads are never reached by part of a warp.
 
 template <int MODE>
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
@@ -411,7 +420,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const bf16* in = a.in + (size_t)b * N3 * CH;
   const uint32_t sa0 = smem_u32(sa);
-  const int limit = 1 << 24;
+  const unsigned long long limit = a.wait_ns;
 
   // setup: slack zeroed, weights staged, barriers, TMEM allocated and zeroed
   const int nslack = SLK_BEFORE + SLK_AFTER;
@@ -450,7 +459,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
       int issued = 0;
       for (int i = 0; i < nin; ++i) {
         uint32_t ok = 1;
-        if (i >= ring && lane == 0) ok = mbar_wait_bounded(done + (i - ring), 0, limit);
+        if (i >= ring && lane == 0) ok = mbar_wait_ns(done + (i - ring), 0, limit);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) {
           if (lane == 0) *sflag = 1;
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
       // no copy may still be writing shared memory when the CTA exits
       if (lane == 0)
         for (int i = 0; i < issued; ++i)
-          if (!mbar_wait_bounded(full + i, 0, limit)) *sflag = 1;
+          if (!mbar_wait_ns(full + i, 0, kDrainNs)) *sflag = 1;
       __syncwarp();
     }
   } else if (w == 2) {
@@ -481,20 +490,24 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
       const uint64_t a_base = umma_desc(sa0, (uint32_t)a.slot_pos * 16u, 128u);
       const uint64_t b_base = umma_desc(smem_u32(sw), 768u, 128u);
       const uint32_t slot_units = slot_bytes >> 4;
+      int committed = 0;
       for (int i = 0; i < nin; ++i) {
         const int g = i / G, s = i - g * G;
-        if (s == 0 && g >= 2 && !mbar_wait_bounded(freeb + (g - 2), 0, limit)) {
+        if (s == 0 && g >= 2 && !mbar_wait_ns(freeb + (g - 2), 0, limit)) {
           *sflag = 1;
           break;
         }
-        if (!mbar_wait_bounded(full + i, 0, limit)) {
+        if (!mbar_wait_ns(full + i, 0, limit)) {
           *sflag = 1;
           break;
         }
         tc_fence_after();
         conv_issue_input(a, i, g & 1, s, tmem, a_base, b_base, slot_units, idesc);
         umma_commit(done + i);
+        committed = i + 1;
       }
+      // the commit of the last issued input completes once every MMA issued before it has
+      if (committed > 0 && !mbar_wait_ns(done + committed - 1, 0, kDrainNs)) *sflag = 1;
     }
     __syncwarp();
   } else if (w >= 4) {
@@ -508,8 +521,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
 #pragma unroll
     for (int c = 0; c < 16; ++c) bias[c] = a.bias ? __ldg(a.bias + c) : 0.0f;
     for (int o = 0; o < nz; ++o) {
-      if (!mbar_wait_bounded(done + o + 2, 0, limit)) {
-        *sflag = 1;
+      uint32_t ok = 0;
+      if (lane == 0) ok = mbar_wait_ns(done + o + 2, 0, limit);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) *sflag = 1;
         break;
       }
       tc_fence_after();
@@ -768,6 +784,7 @@ struct sim_closure_s {
   int adam_t = 0;
   bf16 *wf = nullptr, *wb = nullptr;  // NL x PACK each
   int* err = nullptr;
+  unsigned long long wait_ns = 1000000000ull;  // 1 s per tensor-core pipeline wait
   double* loss = nullptr;
   // workspace
   int wn = 0, wB = 0;
@@ -833,6 +850,7 @@ static ConvArgs conv_args(sim_closure_s* c, int l, bool backward, const bf16* in
   a.bias = backward ? nullptr : c->prm + NL * WL + l * CH;
   a.n = n;
   a.err = c->err;
+  a.wait_ns = c->wait_ns;
   for (int f = 0; f < 5; ++f) a.scale.v[f] = c->scale[f];
   return a;
 }
@@ -940,9 +958,11 @@ static void pad_to_flat(const std::vector<float>& pad, float* flat) {
   }
 }
 
+// Reads and clears the timeout flag (the closure's stream must be idle).
 static int check_err(sim_closure_s* c) {
   int e = 0;
   cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) cudaMemset(c->err, 0, sizeof(int));
   return e;
 }
 
@@ -1163,6 +1183,15 @@ sim_status sim_closure_train_step(sim_closure_t* c, const float* gas, const floa
   DH_TRY(repack(c, c->st));
   if (loss_out)
     DH_CUDA_TRY(cudaMemcpyAsync(loss_out, c->loss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  return SIM_OK;
+}
+
+sim_status sim_closure_set_wait_limit(sim_closure_t* c, int64_t ns) {
+  if (!c || ns < 0) {
+    set_error("sim_closure_set_wait_limit: invalid arguments");
+    return SIM_EINVAL;
+  }
+  c->wait_ns = (unsigned long long)ns;
   return SIM_OK;
 }
 

@@ -1537,7 +1537,7 @@ static sim_status cfl_now(sim_t* h, double* cfl_out) {
     float v;
     memcpy(&v, &bits[b], sizeof(v));
     const double cb = (double)v * h->scheds[b][i].dtau * h->inv_dx;
-    if (!(cb <= c)) c = cb;  // keeps a NaN
+    if (std::isnan(cb) || (!std::isnan(c) && cb > c)) c = cb;  // a NaN of any instance wins
   }
   *cfl_out = c;
   return SIM_OK;

@@ -204,6 +204,11 @@ sim_status launch_subgrid_adjoint(const float* in, float* lam, SubArg c, DPart d
 }
 
 // grid (blocks, B): out[b] = float bits of instance b's maximum signal speed
+// max that keeps a NaN from either operand
+__device__ __forceinline__ float max_keep_nan(float a, float b) {
+  return (a != a || b != b) ? __int_as_float(0x7fc00000) : fmaxf(a, b);
+}
+
 __global__ void signal_speed_kernel(const float* __restrict__ u, float gam, long long N3,
                                     unsigned int* __restrict__ out) {
   const int b = blockIdx.y;
@@ -218,11 +223,16 @@ __global__ void signal_speed_kernel(const float* __restrict__ u, float gam, long
     const float cs2 = gam * P * inv;
     const float cs = cs2 > 0.0f ? sqrtf(cs2) : 0.0f;
     const float v = fmaxf(fabsf(mx), fmaxf(fabsf(my), fabsf(mz))) * inv;
-    vmax = fmaxf(vmax, v + cs);
+    vmax = max_keep_nan(vmax, v + cs);
+    // fmaxf drops NaN operands: a non-finite energy or momentum must still reach the host
+    if (!isfinite(rho) || !isfinite(mx) || !isfinite(my) || !isfinite(mz) ||
+        !isfinite(u[4 * N3 + i]))
+      vmax = __int_as_float(0x7fc00000);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(vmax));
+  for (int o = 16; o > 0; o >>= 1) vmax = max_keep_nan(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  // speeds are >= 0 and a quiet NaN (0x7fc00000) orders above every finite float's bits
+  if ((threadIdx.x & 31) == 0) atomicMax(out, vmax != vmax ? 0x7fc00000u : __float_as_uint(vmax));
 }
 
 sim_status launch_signal_speed(const float* gas, float gamma, long long N3,

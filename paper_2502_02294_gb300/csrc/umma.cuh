@@ -51,18 +51,43 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
 }
 
-// Wait for phase `parity` of the mbarrier with at most `limit` polls; returns 1 when done.
-__device__ __forceinline__ uint32_t mbar_wait_bounded(uint64_t* mbar, uint32_t parity, int limit) {
-  uint32_t done = 0;
-  for (int it = 0; it < limit && !done; ++it) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Non-blocking check of phase `parity` of the mbarrier; 1 when it has completed.
+__device__ __forceinline__ uint32_t mbar_test(uint64_t* mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return done;
+}
+
+// Wait for phase `parity` of the mbarrier for at most limit_ns nanoseconds of the global
+// timer (and at most 2^26 polls); returns 1 when the phase completed, 0 when the wait gave
+// up. limit_ns = 0: one non-blocking check only.
+__device__ __forceinline__ uint32_t mbar_wait_ns(uint64_t* mbar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_test(mbar, parity)) return 1;
+  if (limit_ns == 0) return 0;
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
+    uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
         : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
+    if (done) return 1;
+    if (global_ns() - t0 >= limit_ns) return 0;
   }
-  return done;
+  return 0;
 }
 
 // TMEM allocation of `ncols` columns (power of two, 32..512) by one whole warp; the base

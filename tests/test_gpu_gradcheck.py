@@ -15,8 +15,11 @@ clamp are kinks. Measured on this grid (12 directions, h = 1e-3, 5e-3, 2e-2):
     kinks lie near the point also moves with the last bit of the forward's rounding. The
     50-step check therefore bars each direction at 5% of the RMS and the median relative
     gap at 2.5%.
-Exact agreement with reverse mode is tested against the float64 oracle on smaller runs
-(tests/test_gpu_sim.py), and against float64 finite differences at h = 2e-6 below.
+The 50-step test here is therefore a robustness check of the adjoint against float32
+differences, not the gradient bar of the workload (1e-3). That bar is checked against the
+float64 oracle's reverse mode of whole runs: 50 steps a = 0.1 -> 1.0 at 16^3 and 32^3
+(tests/test_gpu_parity_runs.py), shorter runs from 12^3 to 64^3 (tests/test_gpu_sim.py),
+and the smooth-regime differences and float64 differences at h = 2e-6 below.
 """
 import numpy as np
 import pytest
@@ -52,7 +55,7 @@ def _loss(dh, p, noise, target, n=N):
     return loss.item(), sim
 
 
-def test_noise_gradient_matches_finite_differences(setup):
+def test_noise_gradient_robust_against_float32_differences_50_steps(setup):
     dh, p, noise, target = setup
     L0, sim = _loss(dh, p, noise, target)
     dL, _ = sim.loss_density(target, 1.0 / N ** 3)

@@ -1,0 +1,172 @@
+"""Whole-run parity against the FP64 oracle at the workload bars (Sec. 2.3.5 gradients,
+Sec. 2.2-2.4 forward):
+
+* the reverse pass of a whole 50-step run (a = 0.1 -> 1.0, the config-2 schedule; subgrid
+  with the UV floor on) against the oracle's float64 reverse mode of the same run: noise
+  gradient within 1e-3 relative L2 and each of the 7 parameter partials within 1e-3;
+* the 128^3, 100-step benchmark run (a = 0.05 -> 1.0, subgrid on) against the oracle's run
+  from the same white noise: density, momentum and energy within 1e-3 relative L2 at the
+  end; the hard events of the last step and the particles' CIC cells, which are decisions
+  taken on each side's own state, are counted where they differ (decisions within a
+  guard band of the threshold may differ, none outside it);
+* batched instances with different Omega_m, sigma8, seeds and subgrid parameters, each
+  against its own oracle run (forward 1e-3, gradients 1e-3);
+* the torch.autograd.Function over a run (simulate) against the oracle's autograd.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_helpers import f32, lib, need_gpu, oracle_params, rel_l2
+from oracle import sim as osim
+
+pytestmark = pytest.mark.gpu
+DT = torch.float64
+NAMES = ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"]
+# subgrid settings that form stars in small boxes, with the UV floor (warm gas)
+SUB = dict(subgrid_on=1, delta_c=0.3, w_delta=0.05, T_c=1e6, w_T=1e5, Pi0=0.2, T0_uv=5e3)
+
+
+@pytest.fixture(scope="module")
+def dh():
+    need_gpu()
+    return lib()
+
+
+def _oracle_grads(o, wo, to):
+    leaves = {k: torch.tensor(float(o[k]), dtype=DT, requires_grad=True) for k in NAMES}
+    X = wo.clone().requires_grad_(True)
+    out = osim.run(X, dict(o, **leaves))
+    L = osim.mse_density(out["U"], to)
+    g = torch.autograd.grad(L, [X] + [leaves[k] for k in NAMES], allow_unused=True)
+    return out, g[0], [0.0 if v is None else v.item() for v in g[1:]]
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_fifty_step_adjoint_matches_oracle_reverse_mode(dh, n):
+    p = dh.default_params(n=n, box=float(n), n_steps=50, ckpt_every=10, a_start=0.1,
+                          a_end=1.0, rms_ref=0.05, **SUB)
+    o = oracle_params(p)
+    wg, wo = f32(synth.white_noise(n, 60 + n))
+    tg, to = f32(0.163 * (1 + 0.3 * synth.field(n, 61 + n)))
+    sim = dh.Simulation(p, wg)
+    sim.run()
+    st = sim.state()
+    dL = torch.zeros(5, n, n, n, device="cuda")
+    dL[0] = (2.0 / n ** 3) * (st["gas"][0] - tg)
+    dnoise, dpar = sim.run_adjoint(dL.contiguous())
+    out, gX, gp = _oracle_grads(o, wo, to)
+    err_state = [rel_l2(st["gas"][k], out["U"][k]) for k in range(5)]
+    err_noise = rel_l2(dnoise, gX)
+    err_par = [abs(dpar[j].item() - gp[j]) / max(abs(gp[j]), 1e-30) for j in range(7)]
+    print(f"\n{n}^3 x 50 steps: state {err_state}, noise grad {err_noise:.3e}, "
+          f"params {[f'{e:.2e}' for e in err_par]}")
+    assert max(err_state) < 1e-3, err_state
+    assert err_noise < 1e-3, err_noise
+    for j, k in enumerate(NAMES):
+        assert abs(dpar[j].item() - gp[j]) <= 1e-3 * abs(gp[j]) + 1e-12, (k, dpar[j].item(), gp[j])
+    sim.close()
+
+
+def _bits(words, n3):
+    b = words.cpu().numpy().view(np.uint32)
+    return np.unpackbits(b.view(np.uint8), bitorder="little")[:n3].astype(bool)
+
+
+def test_headline_run_matches_oracle(dh):
+    """The benchmark workload (128^3, 100 steps a = 0.05 -> 1.0, subgrid on, sweep kernels
+    picked by the autotuner) run once on the GPU and once by the oracle."""
+    W = dict(n=128, box=128.0, n_steps=100, a_start=0.05, a_end=1.0, ckpt_every=10,
+             subgrid_on=1, delta_c=100.0, Pi0=0.05, E0=0.03, T_c=3.0e4, w_delta=5.0,
+             w_T=1500.0, T0_uv=1.0e4, gamma_uv=1.4, seed=1)
+    n = W["n"]
+    p = dh.default_params(**W)
+    o = oracle_params(p)
+    wg, wo = f32(synth.white_noise(n, 100))
+    sim = dh.Simulation(p, wg)
+    sim.autotune()
+    sim.run()
+    st = sim.state()
+    gas, s = st["gas"].double().cpu(), st["s"].double().cpu()
+    ev_gpu = _bits(st["events"], n ** 3)
+    sim.close()
+    torch.cuda.empty_cache()
+    with torch.no_grad():
+        ref = osim.run(wo, o)
+    errs = [rel_l2(gas[k], ref["U"][k]) for k in range(5)]
+    err_s = rel_l2(s, ref["s"])
+    ev_or = ref["events"][-1].reshape(-1).numpy()
+    ev_diff = int((ev_gpu != ev_or).sum())
+    # CIC cells: t = s N / L; a cell decision may differ only within the band around an edge
+    t_or = (ref["s"] * (n / W["box"])).numpy()
+    t_gpu = (s * (n / W["box"])).numpy()
+    diff = np.floor(t_gpu) != np.floor(t_or)
+    edge = np.abs(t_or - np.round(t_or))
+    band = 1e-3
+    print(f"\n128^3 x 100 steps: rho/m/eps {errs}, s {err_s:.2e}; events differing "
+          f"{ev_diff} of {int(ev_or.sum())} set; CIC cells differing {int(diff.sum())}, "
+          f"all within {band} cell of an edge: {bool((edge[diff] < band).all())}")
+    assert max(errs) < 1e-3, errs
+    assert err_s < 1e-3, err_s
+    assert ev_diff <= 1e-5 * n ** 3, ev_diff
+    assert (edge[diff] < band).all(), edge[diff].max()
+
+
+def test_batched_instances_match_their_oracle_runs(dh):
+    n, B = 16, 3
+    vary = dict(omega_m=[0.27, 0.30, 0.33], sigma8=[0.75, 0.8, 0.85], delta_c=[0.2, 0.3, 0.4],
+                Pi0=[0.1, 0.2, 0.3], T0_uv=[4e3, 5e3, 6e3], gamma_uv=[1.3, 1.4, 1.5])
+    ps = []
+    for b in range(B):
+        kw = dict(n=n, box=float(n), n_steps=10, ckpt_every=4, a_start=0.1, a_end=0.5,
+                  rms_ref=0.15, **SUB)
+        kw.update({k: v[b] for k, v in vary.items()})
+        kw.update(seed=500 + b, instance=b)
+        ps.append(dh.default_params(**kw))
+    sim = dh.Simulation(ps)                      # noise drawn per instance from Philox
+    sim.run()
+    st = sim.state()
+    tgs = [f32(0.16 * (1 + 0.2 * synth.field(n, 70 + b))) for b in range(B)]
+    dL = torch.zeros(B, 5, n, n, n, device="cuda")
+    for b in range(B):
+        dL[b, 0] = (2.0 / n ** 3) * (st["gas"][b, 0] - tgs[b][0])
+    dnoise, dpar = sim.run_adjoint(dL.contiguous())
+    for b in range(B):
+        o = oracle_params(ps[b])
+        wo = osim.noise_field(o)
+        out, gX, gp = _oracle_grads(o, wo, tgs[b][1])
+        for k in range(5):
+            assert rel_l2(st["gas"][b, k], out["U"][k]) < 1e-3, (b, k)
+        assert rel_l2(st["s"][b], out["s"]) < 1e-3, b
+        assert rel_l2(dnoise[b], gX) < 1e-3, (b, rel_l2(dnoise[b], gX))
+        for j, k in enumerate(NAMES):
+            assert abs(dpar[b, j].item() - gp[j]) <= 1e-3 * abs(gp[j]) + 1e-12, (b, k, dpar[b, j].item(), gp[j])
+    sim.close()
+
+
+def test_autograd_function_matches_oracle(dh):
+    n = 12
+    p = dh.default_params(n=n, box=12.0, n_steps=5, ckpt_every=2, a_start=0.1, a_end=0.35,
+                          rms_ref=0.15, **SUB)
+    o = oracle_params(p)
+    wg, wo = f32(synth.white_noise(n, 80))
+    tg, to = f32(0.16 * (1 + 0.2 * synth.field(n, 81)))
+    noise = wg.clone().requires_grad_(True)
+    pvec = torch.tensor([getattr(p, k) for k in NAMES], dtype=DT, requires_grad=True)
+    gas = dh.simulate(noise, pvec, p)
+    L = ((gas[0] - tg) ** 2).mean()
+    L.backward()
+    out, gX, gp = _oracle_grads(o, wo, to)
+    assert abs(L.item() / osim.mse_density(out["U"], to).item() - 1) < 1e-3
+    assert rel_l2(noise.grad, gX) < 1e-3, rel_l2(noise.grad, gX)
+    for j, k in enumerate(NAMES):
+        assert abs(pvec.grad[j].item() - gp[j]) <= 1e-3 * abs(gp[j]) + 1e-12, (k, pvec.grad[j].item(), gp[j])
+    # a second call from a changed parameter vector differentiates at the new point
+    pv2 = pvec.detach().clone()
+    pv2[0] = 0.32
+    pv2.requires_grad_(True)
+    gas2 = dh.simulate(wg, pv2, p)
+    assert not torch.equal(gas2, gas)
+    ((gas2[0] - tg) ** 2).mean().backward()
+    assert torch.isfinite(pv2.grad).all()

@@ -20,8 +20,8 @@ from gpu_helpers import f32, lib, need_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _deposit(L, fn, s, vals, n, box):
-    grid = torch.zeros(n, n, n, dtype=torch.float32, device="cuda")
+def _deposit(L, fn, s, vals, n, box, grid0=None):
+    grid = torch.zeros(n, n, n, dtype=torch.float32, device="cuda") if grid0 is None else grid0.clone()
     st = fn(ctypes.c_void_p(s.data_ptr()),
             None if vals is None else ctypes.c_void_p(vals.data_ptr()), n, box,
             ctypes.c_void_p(grid.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -42,6 +42,25 @@ def test_static_deposit_matches_allocating_deposit_twice():
         # the same fixed-point arithmetic: the deposit tests' tolerance, met exactly here
         assert (got - want).abs().max().item() <= 2e-6 * want.abs().max().item(), call
         assert torch.equal(got, want), call
+
+
+def test_static_deposit_accumulates_and_takes_the_largest_grid():
+    """The output grid is accumulated (grid += deposit), and n = 128 (exactly the static
+    array's SIM_DEPOSIT_STATIC_MAX_CELLS) is accepted and matches the allocating deposit."""
+    need_gpu()
+    dh = lib()
+    L = dh.lib
+    for n, box in ((20, 20.0), (128, 128.0)):
+        s, _ = f32(synth.displacements(n, 30 + n, 1.5 * box / n))
+        grid0, _ = f32(synth.field(n, 31 + n))
+        want = _deposit(L, L.sim_deposit_cic, s, None, n, box, grid0)
+        got = _deposit(L, L.sim_deposit_cic_static, s, None, n, box, grid0)
+        fresh = _deposit(L, L.sim_deposit_cic_static, s, None, n, box)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want), n
+        # accumulated, not overwritten: the result is grid0 plus the deposit alone
+        assert (got - (grid0 + fresh)).abs().max().item() <= 1e-6 * got.abs().max().item(), n
+        assert abs(fresh.double().sum().item() / n ** 3 - 1.0) < 1e-6   # unit mass per particle
 
 
 def test_static_deposit_rejects_oversize_grid():
