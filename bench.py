@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the differentiable hydro step on GB300: cell-steps/s forward + adjoint.
 
-One bench step is one pass of the whole hot path on a 128^3 grid with 128^3 dark-matter
-particles: initial conditions from device-resident white noise, 100 steps a = 0.05 -> 1.0
-(FastPM kick-drift-kick, three relaxing-TVD sweeps, subgrid with Gumbel-softmax, CIC +
-spectral Poisson), the density loss against a mock field, and the checkpointed adjoint
-(checkpoint every 10 steps) back to the white noise and the parameters.
+One bench step is one iteration of field-level inference (Sec. 3.2) on a 128^3 grid with
+128^3 dark-matter particles: initial conditions from the device-resident white-noise
+amplitudes, 100 steps a = 0.05 -> 1.0 (FastPM kick-drift-kick, three relaxing-TVD sweeps,
+subgrid with Gumbel-softmax, CIC + spectral Poisson), the posterior against a mock final
+density, the checkpointed adjoint (checkpoint every 10 steps) back to the 2,097,152
+amplitudes, and an Adam step on them (one sim_fli_step call).
 
-value     cell-steps/s of that pass = 128^3 * 100 / time, summed over ranks (replicas).
-e2e       the same through the C ABI with the noise copied from pinned host memory and
-          the noise gradient plus the loss copied back inside the timed region.
+value     cell-steps/s of that iteration = 128^3 * 100 / time, summed over ranks (replicas).
+e2e       the same through the C ABI with the amplitudes copied from pinned host memory and
+          the updated amplitudes plus the loss copied back inside the timed region.
+fli       200 iterations from zero amplitudes: seconds per iteration, the loss, and r_c(k)
+          of the recovered amplitudes and final density against the truth.
 roofline  the dominant kernel class (hydro sweeps or their adjoints), each launch timed with
           CUDA events on the simulation stream during one eager pass of the same hot path;
           roofline.classes holds that pass's time per stage of the step and adjoint.
@@ -38,8 +41,15 @@ WORKLOAD = dict(n=128, box=128.0, n_steps=100, a_start=0.05, a_end=1.0, ckpt_eve
                 subgrid_on=1, delta_c=100.0, Pi0=0.05, E0=0.03, T_c=3.0e4, w_delta=5.0,
                 w_T=1500.0, T0_uv=1.0e4, gamma_uv=1.4, seed=1)
 WORKLOAD_NAME = ("128^3 cells + 128^3 DM particles, box 128 Mpc/h, 100 steps a=0.05->1.0, "
-                 "subgrid on, ICs + forward + density-MSE loss + checkpointed adjoint "
-                 "(every 10 steps) to the 2,097,152 white-noise amplitudes and 7 parameters")
+                 "subgrid on; one field-level-inference iteration: ICs + forward + posterior "
+                 "(mock: seed-7 final density + 10% noise) + checkpointed adjoint (every 10 "
+                 "steps) to the 2,097,152 white-noise amplitudes + Adam step")
+# field-level inference (Sec. 3.2, the 128^3 / 100-step / checkpoint-10 workload): mock data
+# from the held seed's run plus 10% noise, Adam on the amplitudes (learning rate 0.05)
+FLI_TRUTH_SEED = 7
+FLI_NOISE_FRAC = 0.1
+FLI_LR = 0.05
+FLI_ITERS = 200
 SWEEP_BYTES_PER_CELL = 40      # sweep: 5 float32 fields read + 5 written
 SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, input adjoint written
 # DRAM bytes per cell of one launch group (dram__bytes_read.sum + dram__bytes_write.sum) from
@@ -286,6 +296,32 @@ def cpu_baseline_sample(steps: int = 1):
     return n ** 3 * steps / dt, dt, torch.get_num_threads()
 
 
+def cpu_forward_sample(steps: int, threads: int | None = None):
+    """The oracle's forward alone (no tape) on `steps` steps of the 128^3 workload with
+    `threads` host threads (None: torch's default, all cores); returns (cell-steps/s,
+    seconds, threads used)."""
+    import torch
+    from oracle import sim as osim
+
+    prev = torch.get_num_threads()
+    if threads:
+        torch.set_num_threads(threads)
+    try:
+        prm = dict(osim.Params().as_dict(), **WORKLOAD)
+        n = prm["n"]
+        noise = torch.randn(n, n, n, dtype=torch.float64, generator=torch.Generator().manual_seed(1))
+        with torch.no_grad():
+            st = osim.init_state(noise, prm)
+            sched = osim.schedule(prm)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                st = osim.step(st, prm, sched)
+            dt = time.perf_counter() - t0
+        return n ** 3 * steps / dt, dt, torch.get_num_threads()
+    finally:
+        torch.set_num_threads(prev)
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, same metric and unit."""
     ws, rank, _ = _dist()
@@ -320,6 +356,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fli", action="store_true",
+                    help="skip the field-level-inference record (Adam iterations from zero)")
+    ap.add_argument("--fli-iters", type=int, default=FLI_ITERS)
+    ap.add_argument("--cpu-full-forward", action="store_true",
+                    help="also time the oracle's whole 128^3 x 100-step forward run (minutes)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched parameter-sampling measurement")
     ap.add_argument("--no-closure", action="store_true",
@@ -348,7 +389,6 @@ def main():
     n = p.n
     n3 = n ** 3
     noise = torch.from_numpy(synth.white_noise(n, 100 + rank).astype("float32")).to(dev)
-    target = torch.from_numpy((0.163 * (1 + 0.3 * synth.field(n, 7))).astype("float32")).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # the simulation runs on its own stream so that its runs can be captured as CUDA graphs
     stream = torch.cuda.Stream(device=dev)
@@ -359,20 +399,27 @@ def main():
     variants = sim.autotune(reps=3)
     if not args.no_graphs:
         dh._lib.check(dh.lib.sim_set_graphs(sim.h, 1), "sim_set_graphs", sim.h)
-    c = 1.0 / n3
-    dL = torch.empty(5, n, n, n, dtype=torch.float32, device=dev)
+    # the field-level-inference mock (Sec. 3.2): the final gas density of the run from the
+    # held seed's amplitudes plus Gaussian noise at 10% of the field's rms
+    truth = torch.from_numpy(synth.white_noise(n, FLI_TRUTH_SEED).astype("float32")).to(dev)
+    sim.reinit(truth)
+    sim.run()
+    rho_true = sim.state()["gas"][0].clone()
+    sigma_n = FLI_NOISE_FRAC * rho_true.std().item()
+    data = (rho_true + sigma_n * torch.from_numpy(
+        synth.field(n, FLI_TRUTH_SEED + 1).astype("float32")).to(dev)).contiguous()
+    # one step of the hot path = one inference iteration on the n^3 amplitudes: ICs, the
+    # 100-step run, posterior, checkpointed reverse pass, Adam update
+    x = noise.clone()
+    mom = torch.zeros_like(x)
+    vel = torch.zeros_like(x)
     loss = torch.empty(1, dtype=torch.float64, device=dev)
-    dnoise = torch.empty(n, n, n, dtype=torch.float32, device=dev)
-    dpar = torch.zeros(dh.NPARAMS, dtype=torch.float64, device=dev)
-    ptr = dh.api._ptr
+    it = [0]
 
-    def hot_path(noise_dev):
-        sim.reinit(noise_dev)
-        sim.run()
-        sim.loss_density(target, c, out=dL, loss=loss)
-        dh._lib.check(dh.lib.sim_run_adjoint(sim.h, ptr(dL), None, ptr(dnoise), ptr(dpar)),
-                      "sim_run_adjoint", sim.h)
-        return dnoise, dpar, loss
+    def hot_path(x_dev):
+        it[0] += 1
+        sim.fli_step(x_dev, mom, vel, data, sigma_n, FLI_LR, it[0], loss=loss)
+        return x_dev, loss
 
     def barrier():
         if ws > 1:
@@ -380,7 +427,7 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        hot_path(noise)
+        hot_path(x)
     # ---- device-resident timing (value)
     clocks = Clocks(nvsmi_id(torch.cuda.current_device()))
     clocks.start()
@@ -392,7 +439,7 @@ def main():
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        hot_path(noise)
+        hot_path(x)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -414,20 +461,19 @@ def main():
         fwd_times.append(e0.elapsed_time(e1))
     fwd_ms = statistics.mean(fwd_times)
     # ---- end to end through host buffers
-    host_noise = noise.cpu().pin_memory()
-    host_grad = torch.empty(n3, dtype=torch.float32).pin_memory()
+    host_x = x.cpu().pin_memory()
     host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
-    dev_noise = torch.empty_like(noise)
+    dev_x = torch.empty_like(x)
     e2e_times = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        dev_noise.copy_(host_noise, non_blocking=True)
-        dnoise, dpar, loss = hot_path(dev_noise)
-        host_grad.copy_(dnoise.view(-1), non_blocking=True)
-        host_loss.copy_(loss, non_blocking=True)
+        dev_x.copy_(host_x, non_blocking=True)
+        xo, lo = hot_path(dev_x)
+        host_x.copy_(xo, non_blocking=True)
+        host_loss.copy_(lo, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
@@ -439,7 +485,7 @@ def main():
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    hot_path(noise)
+    hot_path(x)
     e1.record(stream)
     e1.synchronize()
     inst_ms = e0.elapsed_time(e1)
@@ -453,6 +499,40 @@ def main():
                         "avg_launch_ms": avg,
                         "achieved_gbs": (bpc * n3 / (avg * 1e-3) / 1e9) if (cnt and bpc) else None}
     dom = max(("sweep", "sweep_adjoint"), key=lambda k: kclass[k]["total_ms"])
+
+    # ---- field-level inference: FLI_ITERS Adam iterations from zero amplitudes
+    fli = None
+    if not args.no_fli:
+        xs = torch.zeros_like(x)
+        fm = torch.zeros_like(x)
+        fv = torch.zeros_like(x)
+        floss = torch.empty(args.fli_iters, 1, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(1, args.fli_iters + 1):
+            sim.fli_step(xs, fm, fv, data, sigma_n, FLI_LR, t, loss=floss[t - 1])
+        e1.record(stream)
+        e1.synchronize()
+        fli_ms = e0.elapsed_time(e1)
+        sim.reinit(xs)
+        sim.run()
+        rho_fit = sim.state()["gas"][0].contiguous()
+        nb = n // 2
+        kk, rc_ic, _ = dh.cross_correlation(xs, truth, p.box, nb)
+        _, rc_fin, _ = dh.cross_correlation(rho_fit, rho_true.contiguous(), p.box, nb)
+        fl = floss[:, 0].cpu().numpy()
+        pick = [0, 1, 3, 7, 15, 31, nb - 1]
+        fli = {"iterations": args.fli_iters, "seconds_per_iteration": fli_ms / 1e3 / args.fli_iters,
+               "lr": FLI_LR, "sigma_n": sigma_n, "noise_frac_of_rms": FLI_NOISE_FRAC,
+               "loss_first": float(fl[0]), "loss_last": float(fl[-1]),
+               "loss_expected_at_truth": 0.5 * 2 * n3,
+               "k": [float(kk[j]) for j in pick],
+               "r_c_initial_amplitudes": [float(rc_ic[j]) for j in pick],
+               "r_c_final_density": [float(rc_fin[j]) for j in pick],
+               "workload": "Adam on the 2,097,152 white-noise amplitudes from zero; mock = final "
+                           "gas density of seed %d plus N(0, (0.1 rms)^2); 100 steps "
+                           "a=0.05->1.0, checkpoint every 10" % FLI_TRUTH_SEED}
 
     # ---- batched parameter-sampling form (96 instances on three grid sizes)
     batched = None
@@ -516,15 +596,28 @@ def main():
                      else "fallback 6.8 TB/s (of fallback)"},
         "clocks": clk,
     }
+    if fli is not None:
+        line["fli"] = fli
     if batched is not None:
         line["batched"] = batched
     if closure is not None:
         line["closure"] = closure
     if not args.no_cpu_baseline:
         v, dt, threads = cpu_baseline_sample(1)
+        fa, fdt, fth = cpu_forward_sample(2)
+        f1, f1dt, _ = cpu_forward_sample(1, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": threads,
                                 "kind": "oracle",
-                                "sample": f"1 full step fwd+reverse at 128^3 ({dt:.1f} s)"}
+                                "sample": f"1 full step fwd+reverse at 128^3 ({dt:.1f} s)",
+                                "forward_all_cores": {"value": fa, "cores": fth,
+                                                      "sample": f"2 steps at 128^3 ({fdt:.1f} s)"},
+                                "forward_one_core": {"value": f1, "cores": 1,
+                                                     "sample": f"1 step at 128^3 ({f1dt:.1f} s)"}}
+        if args.cpu_full_forward:
+            ff, ffdt, ffth = cpu_forward_sample(WORKLOAD["n_steps"])
+            line["cpu_baseline"]["forward_full_run"] = {
+                "value": ff, "cores": ffth, "seconds": ffdt,
+                "sample": "the whole 128^3 x 100-step forward run"}
     print(json.dumps(line), flush=True)
     sim.close()
     if ws > 1:

@@ -279,6 +279,44 @@ sim_status sim_reinit(sim_t* h, const float* noise);
 sim_status sim_loss_density(sim_t* h, const float* target, double c, float* dL_dgas,
                             double* loss);
 
+/* ------------------------------------------------------------------ field-level inference
+ * Sec. 3.2: the initial conditions are inferred from a final density field d by minimising
+ * the negative log posterior of the white-noise amplitudes s,
+ *   L(s) = 1/2 [ sum_cells (d - rho_gas(s))^2 / sigma_n^2 + sum_cells s^2 ],
+ * rho_gas(s) the final gas density of the handle's whole run (sim_init parameters) from
+ * initial conditions made of s (Sec. 2.1). */
+
+/* One iteration: sim_reinit(noise), sim_run of all n_steps (checkpoints every ckpt_every),
+ * L and dL/ds through the checkpointed reverse pass (sim_run_adjoint) plus the prior's s,
+ * then one Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias corrected
+ * with step t >= 1) on s with learning rate lr. All device arrays, B instances one after
+ * another: noise (B n^3, in: s, out: the updated s), m and v (B n^3, Adam moments, in/out;
+ * zero them before t = 1), data (B n^3). Outputs: loss (B doubles: L at the input s),
+ * grad (B n^3 or NULL: dL/ds at the input s). Stream-ordered, no synchronisation; the
+ * handle's state is the run from the input s afterwards. SIM_EINVAL for NULL arrays,
+ * sigma_n <= 0, lr <= 0 or t < 1; SIM_ENOTIMPL while a learned closure is set. */
+sim_status sim_fli_step(sim_t* h, float* noise, float* m, float* v, const float* data,
+                        double sigma_n, double lr, int32_t t, double* loss, float* grad);
+
+/* Adam step on a device vector (Kingma & Ba 2015, Algorithm 1, bias corrected with step
+ * t >= 1) with the gradient g + prior_w x, the gradient of a data term plus that of the
+ * Gaussian prior prior_w |x|^2 / 2 (prior_w = 1 for the white-noise amplitudes of Sec. 3.2,
+ * 0 for plain Adam). x, m, v (count floats, in/out), g (count floats). grad_out (count
+ * floats or NULL) receives g + prior_w x; prior (one device double or NULL) is ACCUMULATED
+ * with prior_w / 2 |x|^2 at the input x. SIM_EINVAL for NULL arrays, count < 1, t < 1,
+ * lr <= 0, beta outside [0, 1) or eps <= 0. */
+sim_status sim_adam(float* x, const float* g, float* m, float* v, int64_t count, double lr,
+                    double beta1, double beta2, double eps, int32_t t, double prior_w,
+                    float* grad_out, double* prior, void* stream);
+
+/* Cross-correlation coefficient r_c(k) = P_ab / sqrt(P_aa P_bb) (Sec. 3.2) of two n^3 fields,
+ * binned as sim_power_spectrum (width 2 pi / box, index round(|k| box / 2 pi), bins
+ * 1..nbins): k (mode-weighted mean |k|), rc (0 where a power is 0), nmodes; device doubles
+ * of length nbins (1 <= nbins <= 1024). Uses cuFFT. */
+sim_status sim_cross_correlation(const float* a, const float* b, int32_t n, double box,
+                                 int32_t nbins, double* k, double* rc, double* nmodes,
+                                 void* stream);
+
 /* Copy the current state out (device pointers; any may be NULL):
  * gas 5 n^3, part 6 n^3 (s then p), star n^3 (accumulated relaxed star field),
  * aux n^3 (per-particle star readout, Sec. 2.4.1), events n^3/32 uint32 words (bit i of

@@ -165,6 +165,16 @@ def mse_density(U, target):
     return ((U[0] - target) ** 2).mean()
 
 
+def fli_value_and_grad(noise, data, sigma_noise, prm, n_steps: int | None = None):
+    """Posterior of field-level inference (Sec. 3.2) at the amplitudes `noise` and its
+    gradient by reverse mode through the whole run (float64)."""
+    s = noise.detach().clone().requires_grad_(True)
+    U = run(s, prm, n_steps)["U"]
+    L = fli_loss(U, data, sigma_noise, s)
+    (g,) = torch.autograd.grad(L, s)
+    return L.detach(), g
+
+
 def fli_loss(U, data, sigma_noise, noise):
     """Negative log posterior of field-level inference (Sec. 3.2):
     1/2 sum[(d - F(s))^2 / N + |s|^2], here on the final gas density and white noise s."""

@@ -110,6 +110,9 @@ SIGNATURES = {
     "sim_subgrid_adjoint": (ctypes.c_int, [_P, _P, _I32, _D, _PP, _I32, _P, _P, _P]),
     "sim_philox": (ctypes.c_int, [_U64, _U32, _U32, _U32, _I64, _P, _P]),
     "sim_power_spectrum": (ctypes.c_int, [_P, _P, _I32, _D, _I32, _P, _P, _P, _P]),
+    "sim_fli_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _D, _D, _I32, _P, _P]),
+    "sim_adam": (ctypes.c_int, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I32, _D, _P, _P, _P]),
+    "sim_cross_correlation": (ctypes.c_int, [_P, _P, _I32, _D, _I32, _P, _P, _P, _P]),
 }
 
 

@@ -134,6 +134,30 @@ def power_spectrum(a, box: float, nbins: int, b=None):
     return k, pk, nm
 
 
+def cross_correlation(a, b, box: float, nbins: int):
+    """(k, r_c(k), nmodes) of two n^3 fields (sim_cross_correlation)."""
+    n = a.shape[-1]
+    _chk(a, F32, n ** 3, "a")
+    _chk(b, F32, n ** 3, "b")
+    k = torch.empty(nbins, dtype=F64, device=a.device)
+    rc = torch.empty_like(k)
+    nm = torch.empty_like(k)
+    check(lib.sim_cross_correlation(_ptr(a), _ptr(b), n, box, nbins, _ptr(k), _ptr(rc), _ptr(nm),
+                                    _stream()), "sim_cross_correlation")
+    return k, rc, nm
+
+
+def adam(x, g, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+         eps: float = 1e-8, prior_w: float = 0.0, grad_out=None, prior=None):
+    """In-place Adam step on x (m, v moments) with gradient g + prior_w x (sim_adam)."""
+    cnt = x.numel()
+    for t_, nm in ((x, "x"), (g, "g"), (m, "m"), (v, "v")):
+        _chk(t_, F32, cnt, nm)
+    check(lib.sim_adam(_ptr(x), _ptr(g), _ptr(m), _ptr(v), cnt, lr, beta1, beta2, eps, t,
+                       prior_w, _ptr(grad_out), _ptr(prior), _stream()), "sim_adam")
+    return x
+
+
 # ------------------------------------------------------------------ whole path
 class Simulation:
     """Owns a sim_t handle. All methods enqueue on torch's current stream at creation.
@@ -230,6 +254,21 @@ class Simulation:
         self._check(lib.sim_loss_density(self.h, _ptr(target), c, _ptr(out), _ptr(loss)),
                     "sim_loss_density")
         return out, loss
+
+    def fli_step(self, noise, m, v, data, sigma_n: float, lr: float, t: int, grad=None,
+                 loss=None):
+        """One field-level-inference iteration (sim_fli_step): posterior and its gradient at
+        `noise`, then an Adam step that updates noise, m, v in place. Returns the loss
+        tensor ([1] float64, [B] with B > 1) at the input noise."""
+        n, B = self.n, self.B
+        for t_, nm in ((noise, "noise"), (m, "m"), (v, "v"), (data, "data")):
+            _chk(t_, F32, B * n ** 3, nm)
+        if grad is not None:
+            _chk(grad, F32, B * n ** 3, "grad")
+        loss = torch.empty(B, dtype=F64, device=noise.device) if loss is None else loss
+        self._check(lib.sim_fli_step(self.h, _ptr(noise), _ptr(m), _ptr(v), _ptr(data), sigma_n,
+                                     lr, t, _ptr(loss), _ptr(grad)), "sim_fli_step")
+        return loss
 
     def state(self, gravity: bool = False):
         n = self.n
@@ -500,3 +539,20 @@ class SimRunFunction(torch.autograd.Function):
 
 def simulate(noise, pvec, params: SimParams):
     return SimRunFunction.apply(noise, pvec, params)
+
+
+def fli_infer(sim: Simulation, data, sigma_n: float, iters: int, lr: float, noise0=None,
+              losses_out=None):
+    """Field-level inference (Sec. 3.2): `iters` Adam iterations of sim_fli_step from noise0
+    (zeros if None). Returns (amplitudes, per-iteration losses [iters, B] float64 on the
+    device). The loop only sequences library calls; no value leaves the device."""
+    n, B = sim.n, sim.B
+    dev = data.device
+    shape = (n, n, n) if B == 1 else (B, n, n, n)
+    x = torch.zeros(shape, dtype=F32, device=dev) if noise0 is None else noise0.clone().contiguous()
+    m = torch.zeros_like(x)
+    v = torch.zeros_like(x)
+    losses = torch.empty(iters, B, dtype=F64, device=dev) if losses_out is None else losses_out
+    for t in range(1, iters + 1):
+        sim.fli_step(x, m, v, data, sigma_n, lr, t, loss=losses[t - 1])
+    return x, losses

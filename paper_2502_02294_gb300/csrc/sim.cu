@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "closure.cuh"
+#include "fli.cuh"
 #include "ics.cuh"
 #include "pm.cuh"
 #include "schedule.h"
@@ -164,6 +165,9 @@ struct sim_s {
   double* dslots = nullptr;  // [n_steps + 2][B][SL_N]
   double* dcoef = nullptr;   // [n_steps][B][SL_N] chain-rule coefficients
   double* dglob = nullptr;   // [B][NG]
+  // field-level inference (allocated on the first sim_fli_step)
+  float *fli_g = nullptr, *fli_dL = nullptr;  // B n^3 data-term gradient; B 5 n^3 dL/dgas
+  double* fli_dpar = nullptr;                 // B x SIM_NPARAMS
   unsigned int* speed_bits = nullptr;  // [B]
   // optional per-class kernel timing: event pairs around each timed launch (eager runs only)
   bool kt_on = false;
@@ -1434,6 +1438,42 @@ sim_status sim_loss_density(sim_t* h, const float* target, double c, float* dL_d
   if (r == SIM_OK)
     r = launch_density_loss(h->gas, target, (float)c, dL_dgas, loss, h->N3, h->B, st);
   return fail(h, r);
+}
+
+// One iteration of field-level inference (Sec. 3.2): the posterior at the amplitudes
+// `noise`, its gradient through the whole checkpointed run, and an Adam step on the
+// amplitudes. Every stage is a library kernel or cuFFT call on the handle's stream.
+sim_status sim_fli_step(sim_t* h, float* noise, float* m, float* v, const float* data,
+                        double sigma_n, double lr, int32_t t, double* loss, float* grad) {
+  if (!h || !noise || !m || !v || !data || !loss || !(sigma_n > 0) || !(lr > 0) || t < 1) {
+    set_error("sim_fli_step: null arrays, sigma_n <= 0, lr <= 0 or t < 1");
+    return fail(h, SIM_EINVAL);
+  }
+  if (h->closure) {
+    set_error("sim_fli_step: not available while a learned closure is set");
+    return fail(h, SIM_ENOTIMPL);
+  }
+  const long long N3 = h->N3 * h->B;
+  if (!h->fli_g) {
+    sim_status a = dalloc_t(h, &h->fli_g, N3);
+    if (a == SIM_OK) a = dalloc_t(h, &h->fli_dL, 5 * N3);
+    if (a == SIM_OK) a = dalloc_t(h, &h->fli_dpar, (size_t)h->B * SIM_NPARAMS);
+    // only the density field of dL/dgas is ever written: the other four stay zero
+    if (a == SIM_OK) a = dzero(h->fli_dL, 5 * N3 * sizeof(float), h->st);
+    if (a != SIM_OK) return fail(h, a);
+  }
+  sim_status r = sim_reinit(h, noise);
+  if (r == SIM_OK) r = sim_run(h, h->prm.n_steps);
+  if (r != SIM_OK) return r;
+  r = dzero(loss, h->B * sizeof(double), h->st);
+  if (r == SIM_OK)
+    r = launch_density_loss(h->gas, data, (float)(0.5 / (sigma_n * sigma_n)), h->fli_dL, loss,
+                            h->N3, h->B, h->st);
+  if (r != SIM_OK) return fail(h, r);
+  r = sim_run_adjoint(h, h->fli_dL, nullptr, h->fli_g, h->fli_dpar);
+  if (r != SIM_OK) return r;
+  return fail(h, launch_fli_adam(noise, h->fli_g, m, v, h->N3, h->B, lr, 0.9, 0.999, 1e-8, t,
+                                 1.0, grad, loss, h->st));
 }
 
 sim_status sim_get_state(sim_t* h, float* gas, float* part, float* star, float* aux,

@@ -57,11 +57,17 @@ def test_fifty_step_adjoint_matches_oracle_reverse_mode(dh, n):
     dL[0] = (2.0 / n ** 3) * (st["gas"][0] - tg)
     dnoise, dpar = sim.run_adjoint(dL.contiguous())
     out, gX, gp = _oracle_grads(o, wo, to)
+    ev_gpu = _bits(st["events"], n ** 3)
+    ev_or = out["events"][-1].reshape(-1).numpy()
+    ev_diff = int((ev_gpu != ev_or).sum())
     err_state = [rel_l2(st["gas"][k], out["U"][k]) for k in range(5)]
     err_noise = rel_l2(dnoise, gX)
     err_par = [abs(dpar[j].item() - gp[j]) / max(abs(gp[j]), 1e-30) for j in range(7)]
     print(f"\n{n}^3 x 50 steps: state {err_state}, noise grad {err_noise:.3e}, "
-          f"params {[f'{e:.2e}' for e in err_par]}")
+          f"params {[f'{e:.2e}' for e in err_par]}; last-step events set {int(ev_or.sum())}, "
+          f"differing {ev_diff}")
+    assert ev_or.sum() > 0                       # the subgrid forms stars in this box
+    assert ev_diff <= 1e-4 * n ** 3, ev_diff
     assert max(err_state) < 1e-3, err_state
     assert err_noise < 1e-3, err_noise
     for j, k in enumerate(NAMES):

@@ -146,3 +146,37 @@ def test_gradient_wrt_parameters_matches_finite_differences(name):
     x0 = torch.tensor(float(prm[name]), dtype=DT)
     ad, fd = _fd_check(fun, x0, torch.tensor(1.0, dtype=DT), 1e-6 * max(abs(x0.item()), 1e-2))
     assert abs(ad - fd) <= 1e-5 * abs(fd) + 1e-12
+
+
+def test_fli_posterior_is_the_wiener_filter_for_a_linear_forward():
+    """With gravity, hydro and subgrid off and no steps, the final gas density is the
+    initial rho = f_b (1 + delta_L(s)), linear in s: delta_k = A_k s_k with A_k = C sqrt(P_k)
+    per Fourier mode. The posterior 1/2 [|d - rho|^2 / sigma^2 + |s|^2] is then a quadratic
+    whose minimiser is the Wiener filter s_k = f_b A_k d'_k / (sigma^2 + f_b^2 A_k^2),
+    d' = d - f_b, and whose gradient is s - f_b A (d' - f_b A s) / sigma^2 (the test's own
+    FFTs); the oracle's reverse-mode gradient must equal it and vanish at the minimiser."""
+    n, box, sig = 8, 8.0, 0.02
+    prm = sim.Params(n=n, box=box, n_steps=1, gravity_on=0, hydro_on=0, subgrid_on=0,
+                     rms_ref=0.2).as_dict()
+    fb = prm["omega_b"] / prm["omega_m"]
+    g = np.random.default_rng(9)
+    # A_k from the response to one mode at a time is avoided: A is diagonal in Fourier
+    # space, so its multiplier is the transfer of an impulse
+    imp = torch.zeros(n, n, n, dtype=DT)
+    imp[0, 0, 0] = 1.0
+    d_imp = sim.run(imp, prm, n_steps=0)["U"][0] / fb - 1.0       # delta_L of an impulse
+    A = np.fft.fftn(d_imp.numpy()).real                           # real, even multiplier
+    assert np.abs(np.fft.fftn(d_imp.numpy()).imag).max() < 1e-14
+    d = fb * (1 + 0.3 * g.normal(size=(n, n, n)))
+    dp = np.fft.fftn(d - fb)
+    s_star = np.fft.ifftn(fb * A * dp / (sig ** 2 + fb ** 2 * A ** 2)).real
+    Ls, gs = sim.fli_value_and_grad(torch.tensor(s_star), torch.tensor(d), sig, prm, n_steps=0)
+    assert np.abs(gs.numpy()).max() < 1e-9 * np.abs(s_star).max() / sig ** 2
+    s1 = g.normal(size=(n, n, n))
+    L1, g1 = sim.fli_value_and_grad(torch.tensor(s1), torch.tensor(d), sig, prm, n_steps=0)
+    As1 = np.fft.ifftn(A * np.fft.fftn(s1)).real
+    want = s1 - np.fft.ifftn(fb * A * np.fft.fftn(d - fb - fb * As1)).real / sig ** 2
+    assert np.allclose(g1.numpy(), want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+    L1_want = 0.5 * (((d - fb - fb * As1) ** 2).sum() / sig ** 2 + (s1 ** 2).sum())
+    assert abs(L1.item() / L1_want - 1) < 1e-12
+    assert L1.item() > Ls.item()
