@@ -409,16 +409,18 @@ def main():
     data = (rho_true + sigma_n * torch.from_numpy(
         synth.field(n, FLI_TRUTH_SEED + 1).astype("float32")).to(dev)).contiguous()
     # one step of the hot path = one inference iteration on the n^3 amplitudes: ICs, the
-    # 100-step run, posterior, checkpointed reverse pass, Adam update
+    # 100-step run, posterior, checkpointed reverse pass, Adam update. Every timed step is
+    # the first iteration from the same amplitudes (moments cleared), so each times the
+    # same work.
     x = noise.clone()
     mom = torch.zeros_like(x)
     vel = torch.zeros_like(x)
     loss = torch.empty(1, dtype=torch.float64, device=dev)
-    it = [0]
 
     def hot_path(x_dev):
-        it[0] += 1
-        sim.fli_step(x_dev, mom, vel, data, sigma_n, FLI_LR, it[0], loss=loss)
+        mom.zero_()
+        vel.zero_()
+        sim.fli_step(x_dev, mom, vel, data, sigma_n, FLI_LR, 1, loss=loss)
         return x_dev, loss
 
     def barrier():
@@ -427,6 +429,7 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
+        x.copy_(noise)
         hot_path(x)
     # ---- device-resident timing (value)
     clocks = Clocks(nvsmi_id(torch.cuda.current_device()))
@@ -437,6 +440,7 @@ def main():
     torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         flush.zero_()
+        x.copy_(noise)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         hot_path(x)
@@ -461,7 +465,8 @@ def main():
         fwd_times.append(e0.elapsed_time(e1))
     fwd_ms = statistics.mean(fwd_times)
     # ---- end to end through host buffers
-    host_x = x.cpu().pin_memory()
+    host_x = noise.cpu().pin_memory()
+    host_out = torch.empty_like(host_x).pin_memory()
     host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
     dev_x = torch.empty_like(x)
     e2e_times = []
@@ -472,7 +477,7 @@ def main():
         e0.record(stream)
         dev_x.copy_(host_x, non_blocking=True)
         xo, lo = hot_path(dev_x)
-        host_x.copy_(xo, non_blocking=True)
+        host_out.copy_(xo, non_blocking=True)
         host_loss.copy_(lo, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
@@ -483,6 +488,7 @@ def main():
     sim.kernel_timing(True)
     sim.kernel_times(reset=True)
     flush.zero_()
+    x.copy_(noise)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     hot_path(x)

@@ -280,23 +280,47 @@ sim_status sim_loss_density(sim_t* h, const float* target, double c, float* dL_d
                             double* loss);
 
 /* ------------------------------------------------------------------ field-level inference
- * Sec. 3.2: the initial conditions are inferred from a final density field d by minimising
+ * Sec. 3.2: the initial conditions are inferred from a final observed field d by minimising
  * the negative log posterior of the white-noise amplitudes s,
- *   L(s) = 1/2 [ sum_cells (d - rho_gas(s))^2 / sigma_n^2 + sum_cells s^2 ],
- * rho_gas(s) the final gas density of the handle's whole run (sim_init parameters) from
- * initial conditions made of s (Sec. 2.1). */
+ *   L(s) = 1/2 [ sum_cells (d - O(s))^2 / sigma_n^2 + sum_cells s^2 ],
+ * O(s) an observable of the final gas state of the handle's whole run (sim_init
+ * parameters) from initial conditions made of s (Sec. 2.1). Observables: */
+enum {
+  SIM_OBS_DENSITY = 0,  /* gas density rho                                              */
+  SIM_OBS_THERMAL = 1   /* internal energy density eps - |m|^2/(2 rho) = a^2 rho e, which is
+                           proportional to the gas-mass-weighted temperature rho T (the
+                           delta_b T probe of Sec. 3.2)                                   */
+};
 
-/* One iteration: sim_reinit(noise), sim_run of all n_steps (checkpoints every ckpt_every),
- * L and dL/ds through the checkpointed reverse pass (sim_run_adjoint) plus the prior's s,
- * then one Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias corrected
- * with step t >= 1) on s with learning rate lr. All device arrays, B instances one after
- * another: noise (B n^3, in: s, out: the updated s), m and v (B n^3, Adam moments, in/out;
- * zero them before t = 1), data (B n^3). Outputs: loss (B doubles: L at the input s),
- * grad (B n^3 or NULL: dL/ds at the input s). Stream-ordered, no synchronisation; the
- * handle's state is the run from the input s afterwards. SIM_EINVAL for NULL arrays,
- * sigma_n <= 0, lr <= 0 or t < 1; SIM_ENOTIMPL while a learned closure is set. */
-sim_status sim_fli_step(sim_t* h, float* noise, float* m, float* v, const float* data,
-                        double sigma_n, double lr, int32_t t, double* loss, float* grad);
+/* Loss of an observable of the current state: L = c sum_cells (O - target)^2 per instance
+ * (loss: B device doubles, overwritten) and dL/d(gas) (5 B n^3, overwritten). */
+sim_status sim_loss_field(sim_t* h, int32_t observable, const float* target, double c,
+                          float* dL_dgas, double* loss);
+
+/* Posterior and its gradient at the amplitudes `noise` (B n^3, device, read only): ICs from
+ * noise (sim_reinit), sim_run of all n_steps (checkpoints every ckpt_every), the checkpointed
+ * reverse pass, plus the prior. loss (B device doubles): L; grad (B n^3): dL/ds. The
+ * handle's state is the run from `noise` afterwards. Requires cfl_max = 0; SIM_ENOTIMPL
+ * while a learned closure is set. */
+sim_status sim_posterior(sim_t* h, int32_t observable, const float* noise, const float* data,
+                         double sigma_n, double* loss, float* grad);
+
+/* One Adam iteration: sim_posterior at the input amplitudes, then one Adam step (Kingma &
+ * Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias corrected with step t >= 1) on them with
+ * learning rate lr. noise (B n^3, in: s, out: the updated s), m and v (B n^3, Adam moments,
+ * in/out; zero them before t = 1), data (B n^3). loss (B doubles: L at the input s), grad
+ * (B n^3 or NULL: dL/ds at the input s). Stream-ordered, no synchronisation. SIM_EINVAL for
+ * NULL arrays, sigma_n <= 0, lr <= 0, t < 1 or an unknown observable. */
+sim_status sim_fli_step(sim_t* h, int32_t observable, float* noise, float* m, float* v,
+                        const float* data, double sigma_n, double lr, int32_t t, double* loss,
+                        float* grad);
+
+/* Vector kernels for host-driven optimisers (L-BFGS two-loop recursion, line searches) on
+ * device vectors of `count` floats: sim_dot writes sum a_i b_i to *out (one device double,
+ * overwritten); sim_axpby sets y = alpha x + beta y. The paper has no counterpart. */
+sim_status sim_dot(const float* a, const float* b, int64_t count, double* out, void* stream);
+sim_status sim_axpby(double alpha, const float* x, double beta, float* y, int64_t count,
+                     void* stream);
 
 /* Adam step on a device vector (Kingma & Ba 2015, Algorithm 1, bias corrected with step
  * t >= 1) with the gradient g + prior_w x, the gradient of a data term plus that of the
@@ -316,6 +340,41 @@ sim_status sim_adam(float* x, const float* g, float* m, float* v, int64_t count,
 sim_status sim_cross_correlation(const float* a, const float* b, int32_t n, double box,
                                  int32_t nbins, double* k, double* rc, double* nmodes,
                                  void* stream);
+
+/* ------------------------------------------------------------------ diagnostics
+ * Per-step record of a run, for time-step control (Eq. dt) and for conservation checks of
+ * the finite-volume scheme (Sec. 2.3): after every step of sim_step / sim_run (and for the
+ * initial state at the start of a run) one kernel sums the state into a device record.
+ * Entries of a record (doubles), per instance: */
+enum {
+  SIM_DG_A = 0,       /* scale factor of the recorded state                      */
+  SIM_DG_MASS,        /* sum over cells of rho (gas mass / cell volume)         */
+  SIM_DG_MX,          /* sums of the gas momentum density m_x, m_y, m_z          */
+  SIM_DG_MY,
+  SIM_DG_MZ,
+  SIM_DG_ENERGY,      /* sum of eps                                              */
+  SIM_DG_PX,          /* DM momentum: particle mass x sum of p_x, p_y, p_z       */
+  SIM_DG_PY,
+  SIM_DG_PZ,
+  SIM_DG_STARS,       /* sum of the step's relaxed star field zhat (Sec. 2.4.2)  */
+  SIM_DG_EVENTS,      /* number of hard star-formation events of the step        */
+  SIM_DG_NONFINITE,   /* cells with a non-finite field or pressure (left out of
+                         the sums and minima above)                             */
+  SIM_DG_RHO_MIN,     /* smallest density (NaN if no finite cell)                */
+  SIM_DG_P_MIN,       /* smallest pressure P = (gamma-1)(eps - |m|^2/2rho)       */
+  SIM_DG_N
+};
+
+/* on != 0: record every later step (allocates (n_steps + 1) x B records on the first call;
+ * never call it inside a stream capture). While on, sim_run keeps each step's closing half
+ * kick apart from the next opening one so that every record holds a whole step's end
+ * state; keep the setting unchanged between a sim_run and its sim_run_adjoint. Drops
+ * captured graphs when the setting changes. The paper has no counterpart. */
+sim_status sim_set_diagnostics(sim_t* h, int32_t on);
+
+/* Record of the state after step `step` (0 = the run's initial state): host out[B][SIM_DG_N].
+ * Synchronises the handle's stream. SIM_EINVAL if that step was not recorded. */
+sim_status sim_diagnostics(sim_t* h, int32_t step, double* out);
 
 /* Copy the current state out (device pointers; any may be NULL):
  * gas 5 n^3, part 6 n^3 (s then p), star n^3 (accumulated relaxed star field),

@@ -24,6 +24,10 @@ KT_SWEEP, KT_SWEEP_ADJOINT = 0, 1
 SWEEP_DEFAULT, SWEEP_TILE, SWEEP_MARCH32, SWEEP_MARCH16, SWEEP_MARCH_FIT = range(5)
 CLOSURE_NWEIGHTS = 18197
 PARAM_NAMES = ["omega_m", "sigma8", "delta_c", "Pi0", "E0", "T0_uv", "gamma_uv"]
+DG_NAMES = ("a", "mass", "mx", "my", "mz", "energy", "px", "py", "pz", "stars", "events",
+            "nonfinite", "rho_min", "p_min")
+DG_N = len(DG_NAMES)
+OBS_DENSITY, OBS_THERMAL = 0, 1
 
 
 class SimParams(ctypes.Structure):
@@ -110,7 +114,13 @@ SIGNATURES = {
     "sim_subgrid_adjoint": (ctypes.c_int, [_P, _P, _I32, _D, _PP, _I32, _P, _P, _P]),
     "sim_philox": (ctypes.c_int, [_U64, _U32, _U32, _U32, _I64, _P, _P]),
     "sim_power_spectrum": (ctypes.c_int, [_P, _P, _I32, _D, _I32, _P, _P, _P, _P]),
-    "sim_fli_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _D, _D, _I32, _P, _P]),
+    "sim_set_diagnostics": (ctypes.c_int, [_P, _I32]),
+    "sim_diagnostics": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_D)]),
+    "sim_fli_step": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _D, _D, _I32, _P, _P]),
+    "sim_posterior": (ctypes.c_int, [_P, _I32, _P, _P, _D, _P, _P]),
+    "sim_loss_field": (ctypes.c_int, [_P, _I32, _P, _D, _P, _P]),
+    "sim_dot": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "sim_axpby": (ctypes.c_int, [_D, _P, _D, _P, _I64, _P]),
     "sim_adam": (ctypes.c_int, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I32, _D, _P, _P, _P]),
     "sim_cross_correlation": (ctypes.c_int, [_P, _P, _I32, _D, _I32, _P, _P, _P, _P]),
 }

@@ -11,8 +11,8 @@ import torch
 
 import numpy as np
 
-from ._lib import (CLOSURE_NWEIGHTS, KT_N, KT_NAMES, NPARAMS, SimParams,
-                   check, default_params, lib)
+from ._lib import (CLOSURE_NWEIGHTS, DG_N, DG_NAMES, KT_N, KT_NAMES, NPARAMS, OBS_DENSITY,
+                   OBS_THERMAL, SimParams, check, default_params, lib)
 
 F32, F64, U32 = torch.float32, torch.float64, torch.int32
 
@@ -147,6 +147,21 @@ def cross_correlation(a, b, box: float, nbins: int):
     return k, rc, nm
 
 
+def dot(a, b):
+    """sum a_i b_i of two float32 device vectors, as a [1] float64 device tensor (sim_dot)."""
+    _chk(b, F32, a.numel(), "b")
+    out = torch.empty(1, dtype=F64, device=a.device)
+    check(lib.sim_dot(_ptr(a), _ptr(b), a.numel(), _ptr(out), _stream()), "sim_dot")
+    return out
+
+
+def axpby(alpha: float, x, beta: float, y):
+    """y = alpha x + beta y in place (sim_axpby)."""
+    _chk(x, F32, y.numel(), "x")
+    check(lib.sim_axpby(alpha, _ptr(x), beta, _ptr(y), y.numel(), _stream()), "sim_axpby")
+    return y
+
+
 def adam(x, g, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
          eps: float = 1e-8, prior_w: float = 0.0, grad_out=None, prior=None):
     """In-place Adam step on x (m, v moments) with gradient g + prior_w x (sim_adam)."""
@@ -255,8 +270,21 @@ class Simulation:
                     "sim_loss_density")
         return out, loss
 
+    def set_diagnostics(self, on: bool = True):
+        self._check(lib.sim_set_diagnostics(self.h, int(on)), "sim_set_diagnostics")
+
+    def diagnostics(self, step: int):
+        """Record of the state after `step` (0: initial): {name: value} (a list per name
+        with B > 1)."""
+        out = (ctypes.c_double * (DG_N * self.B))()
+        self._check(lib.sim_diagnostics(self.h, step, out), "sim_diagnostics")
+        vals = list(out)
+        if self.B == 1:
+            return dict(zip(DG_NAMES, vals))
+        return {nm: [vals[b * DG_N + j] for b in range(self.B)] for j, nm in enumerate(DG_NAMES)}
+
     def fli_step(self, noise, m, v, data, sigma_n: float, lr: float, t: int, grad=None,
-                 loss=None):
+                 loss=None, observable: int = OBS_DENSITY):
         """One field-level-inference iteration (sim_fli_step): posterior and its gradient at
         `noise`, then an Adam step that updates noise, m, v in place. Returns the loss
         tensor ([1] float64, [B] with B > 1) at the input noise."""
@@ -266,9 +294,31 @@ class Simulation:
         if grad is not None:
             _chk(grad, F32, B * n ** 3, "grad")
         loss = torch.empty(B, dtype=F64, device=noise.device) if loss is None else loss
-        self._check(lib.sim_fli_step(self.h, _ptr(noise), _ptr(m), _ptr(v), _ptr(data), sigma_n,
-                                     lr, t, _ptr(loss), _ptr(grad)), "sim_fli_step")
+        self._check(lib.sim_fli_step(self.h, observable, _ptr(noise), _ptr(m), _ptr(v), _ptr(data),
+                                     sigma_n, lr, t, _ptr(loss), _ptr(grad)), "sim_fli_step")
         return loss
+
+    def posterior(self, noise, data, sigma_n: float, grad=None, loss=None,
+                  observable: int = OBS_DENSITY):
+        """(loss, dL/dnoise) of the posterior of Sec. 3.2 at `noise` (sim_posterior)."""
+        n, B = self.n, self.B
+        _chk(noise, F32, B * n ** 3, "noise")
+        _chk(data, F32, B * n ** 3, "data")
+        grad = torch.empty_like(noise) if grad is None else grad
+        loss = torch.empty(B, dtype=F64, device=noise.device) if loss is None else loss
+        self._check(lib.sim_posterior(self.h, observable, _ptr(noise), _ptr(data), sigma_n,
+                                      _ptr(loss), _ptr(grad)), "sim_posterior")
+        return loss, grad
+
+    def loss_field(self, target, c: float, observable: int = OBS_DENSITY, out=None, loss=None):
+        """(dL/dgas, loss) of L = c sum (O - target)^2 for an observable O of the state."""
+        n, B = self.n, self.B
+        _chk(target, F32, B * n ** 3, "target")
+        out = torch.empty(self._shape(5, n, n, n), dtype=F32, device=target.device) if out is None else out
+        loss = torch.empty(B, dtype=F64, device=target.device) if loss is None else loss
+        self._check(lib.sim_loss_field(self.h, observable, _ptr(target), c, _ptr(out), _ptr(loss)),
+                    "sim_loss_field")
+        return out, loss
 
     def state(self, gravity: bool = False):
         n = self.n
@@ -542,7 +592,7 @@ def simulate(noise, pvec, params: SimParams):
 
 
 def fli_infer(sim: Simulation, data, sigma_n: float, iters: int, lr: float, noise0=None,
-              losses_out=None):
+              losses_out=None, observable: int = OBS_DENSITY):
     """Field-level inference (Sec. 3.2): `iters` Adam iterations of sim_fli_step from noise0
     (zeros if None). Returns (amplitudes, per-iteration losses [iters, B] float64 on the
     device). The loop only sequences library calls; no value leaves the device."""
@@ -554,5 +604,5 @@ def fli_infer(sim: Simulation, data, sigma_n: float, iters: int, lr: float, nois
     v = torch.zeros_like(x)
     losses = torch.empty(iters, B, dtype=F64, device=dev) if losses_out is None else losses_out
     for t in range(1, iters + 1):
-        sim.fli_step(x, m, v, data, sigma_n, lr, t, loss=losses[t - 1])
+        sim.fli_step(x, m, v, data, sigma_n, lr, t, loss=losses[t - 1], observable=observable)
     return x, losses

@@ -18,13 +18,14 @@
 
 namespace dh {
 
+// 1 - beta is formed in double on the host: in float32, 1 - fl(0.999) is 1.3e-5 off 0.001
 struct AdamConst {
-  float lr, b1, b2, eps, inv_bc1, inv_bc2, prior_w;
+  float lr, b1, b2, omb1, omb2, eps, inv_bc1, inv_bc2, prior_w;
 };
 
 __device__ __forceinline__ float adam_one(float x, float g, float& m, float& v, const AdamConst& c) {
-  m = c.b1 * m + (1.0f - c.b1) * g;
-  v = c.b2 * v + (1.0f - c.b2) * g * g;
+  m = c.b1 * m + c.omb1 * g;
+  v = c.b2 * v + c.omb2 * g * g;
   const float mh = m * c.inv_bc1, vh = v * c.inv_bc2;
   return x - c.lr * mh / (sqrtf(vh) + c.eps);
 }
@@ -96,6 +97,8 @@ sim_status launch_fli_adam(float* x, const float* g, float* m, float* v, long lo
   c.lr = (float)lr;
   c.b1 = (float)beta1;
   c.b2 = (float)beta2;
+  c.omb1 = (float)(1.0 - beta1);
+  c.omb2 = (float)(1.0 - beta2);
   c.eps = (float)eps;
   c.inv_bc1 = (float)(1.0 / (1.0 - std::pow(beta1, t)));
   c.inv_bc2 = (float)(1.0 / (1.0 - std::pow(beta2, t)));
@@ -115,6 +118,42 @@ sim_status launch_fli_adam(float* x, const float* g, float* m, float* v, long lo
     fli_adam_kernel<false><<<grid, 256, 0, st>>>(x, g, m, v, count, c, grad_out, prior);
   DH_LAUNCH_CHECK();
   return SIM_OK;
+}
+
+// grad = g + prior_w x and prior[b] += prior_w / 2 sum x^2 (the posterior's gradient and
+// prior term without an update)
+__global__ void __launch_bounds__(256) prior_grad_kernel(const float* __restrict__ x,
+                                                         const float* __restrict__ g,
+                                                         float* __restrict__ grad, long long count,
+                                                         float prior_w, double* __restrict__ prior) {
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * count;
+  float acc = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float xi = x[off + i];
+    grad[off + i] = g[off + i] + prior_w * xi;
+    acc += xi * xi;
+  }
+  if (prior) block_sum_atomic(0.5f * prior_w * acc, prior + b);
+}
+
+sim_status launch_prior_grad(const float* x, const float* g, float* grad, long long count,
+                             int B, double prior_w, double* prior, cudaStream_t st) {
+  int blocks = cdiv(count, 256);
+  const int cap = cdiv(152 * 8, B);
+  if (blocks > cap) blocks = cap;
+  prior_grad_kernel<<<dim3(blocks, B), 256, 0, st>>>(x, g, grad, count, (float)prior_w, prior);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// y = alpha x + beta y over count floats
+__global__ void axpby_kernel(float alpha, const float* __restrict__ x, float beta,
+                             float* __restrict__ y, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = alpha * x[i] + beta * y[i];
 }
 
 // ------------------------------------------------------------------ r_c(k)
@@ -174,6 +213,30 @@ extern "C" sim_status sim_adam(float* x, const float* g, float* m, float* v, int
   }
   return launch_fli_adam(x, g, m, v, count, 1, lr, beta1, beta2, eps, t, prior_w, grad_out,
                          prior, (cudaStream_t)stream);
+}
+
+extern "C" sim_status sim_dot(const float* a, const float* b, int64_t count, double* out,
+                              void* stream) {
+  if (!a || !b || !out || count < 1) {
+    set_error("sim_dot: null arrays or count < 1");
+    return SIM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  DH_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), st));
+  return launch_dot(a, b, count, dpart(out), 1, st);
+}
+
+extern "C" sim_status sim_axpby(double alpha, const float* x, double beta, float* y,
+                                int64_t count, void* stream) {
+  if (!x || !y || count < 1) {
+    set_error("sim_axpby: null arrays or count < 1");
+    return SIM_EINVAL;
+  }
+  int blocks = cdiv(count, 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  axpby_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((float)alpha, x, (float)beta, y, count);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
 }
 
 extern "C" sim_status sim_cross_correlation(const float* a, const float* b, int32_t n,

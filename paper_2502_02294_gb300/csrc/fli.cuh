@@ -14,4 +14,8 @@ sim_status launch_fli_adam(float* x, const float* g, float* m, float* v, long lo
                            int B, double lr, double beta1, double beta2, double eps, int t,
                            double prior_w, float* grad_out, double* prior, cudaStream_t st);
 
+// grad = g + prior_w x; prior (may be NULL, B doubles) += prior_w / 2 sum x^2
+sim_status launch_prior_grad(const float* x, const float* g, float* grad, long long count,
+                             int B, double prior_w, double* prior, cudaStream_t st);
+
 }  // namespace dh

@@ -108,7 +108,10 @@ __device__ __forceinline__ void cic_axis(float s, int q, int n, float inv_dx, in
   const float t = __fmul_rn(s, inv_dx);
   const float fl = floorf(t);
   const float f = t - fl;
-  const int b = wrap_periodic(q + (int)fl, n);
+  // the clamp (a no-op for displacements within 64 boxes) bounds the periodic wrap for any
+  // input, a non-finite one included (fminf/fmaxf return the other operand for a NaN)
+  const float flc = fminf(fmaxf(fl, -64.0f * n), 64.0f * n);
+  const int b = wrap_periodic(q + (int)flc, n);
   idx[0] = b;
   idx[1] = (b + 1 == n) ? 0 : b + 1;
   w[0] = 1.0f - f;
@@ -764,6 +767,44 @@ __global__ void density_loss_kernel(const float* __restrict__ gas, const float* 
     acc += c * d * d;
   }
   block_sum_atomic(acc, loss + b);
+}
+
+// instance b: u = eps - |m|^2 / (2 rho), the internal energy density a^2 rho e (proportional
+// to the gas-mass-weighted temperature rho T, the delta_b T observable of Sec. 3.2);
+// loss[b] += c sum (u - t)^2, grad[b] = 2 c (u - t) du/d(rho, m, eps) (all five fields)
+__global__ void thermal_loss_kernel(const float* __restrict__ gas, const float* __restrict__ t,
+                                    float c, float* __restrict__ grad, double* __restrict__ loss,
+                                    long long N3) {
+  const int b = blockIdx.y;
+  const float* g = gas + (size_t)b * 5 * N3;
+  t += (size_t)b * N3;
+  grad += (size_t)b * 5 * N3;
+  float acc = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float rho = g[i], mx = g[N3 + i], my = g[2 * N3 + i], mz = g[3 * N3 + i];
+    const float inv = 1.0f / rho;
+    const float ke = 0.5f * (mx * mx + my * my + mz * mz) * inv;
+    const float d = (g[4 * N3 + i] - ke) - t[i];
+    const float w = 2.0f * c * d;
+    grad[i] = w * ke * inv;  // du/drho = |m|^2 / (2 rho^2)
+    grad[N3 + i] = -w * mx * inv;
+    grad[2 * N3 + i] = -w * my * inv;
+    grad[3 * N3 + i] = -w * mz * inv;
+    grad[4 * N3 + i] = w;
+    acc += c * d * d;
+  }
+  block_sum_atomic(acc, loss + b);
+}
+
+sim_status launch_thermal_loss(const float* gas, const float* target, float c, float* grad,
+                               double* loss, long long N3, int B, cudaStream_t st) {
+  int blocks = cdiv(N3, 256);
+  const int cap = cdiv(152 * 16, B);
+  if (blocks > cap) blocks = cap;
+  thermal_loss_kernel<<<dim3(blocks, B), 256, 0, st>>>(gas, target, c, grad, loss, N3);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
 }
 
 sim_status launch_density_loss(const float* gas, const float* target, float c, float* grad,

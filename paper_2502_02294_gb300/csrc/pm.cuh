@@ -95,5 +95,9 @@ sim_status launch_add_strided(const float* x, float* y, long long count, long lo
 // (instance stride 5 n^3, as grad); loss[b] += c sum (rho - t)^2
 sim_status launch_density_loss(const float* gas, const float* target, float c, float* grad,
                                double* loss, long long N3, int B, cudaStream_t st);
+// per instance: u = eps - |m|^2/(2 rho); grad (5 n^3, all fields written) = 2 c (u - t) du/dU;
+// loss[b] += c sum (u - t)^2
+sim_status launch_thermal_loss(const float* gas, const float* target, float c, float* grad,
+                               double* loss, long long N3, int B, cudaStream_t st);
 
 }  // namespace dh

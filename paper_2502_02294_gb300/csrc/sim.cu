@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "closure.cuh"
+#include "diag.cuh"
 #include "fli.cuh"
 #include "ics.cuh"
 #include "pm.cuh"
@@ -165,6 +166,11 @@ struct sim_s {
   double* dslots = nullptr;  // [n_steps + 2][B][SL_N]
   double* dcoef = nullptr;   // [n_steps][B][SL_N] chain-rule coefficients
   double* dglob = nullptr;   // [B][NG]
+  // per-step diagnostics: records [n_steps + 1][B] (allocated by sim_set_diagnostics)
+  bool diag_on = false;
+  double* d_diag_sums = nullptr;  // [n_steps + 1][B][DG_NSUM]
+  int* d_diag_mins = nullptr;     // [n_steps + 1][B][2]
+  std::vector<char> diag_recorded;
   // field-level inference (allocated on the first sim_fli_step)
   float *fli_g = nullptr, *fli_dL = nullptr;  // B n^3 data-term gradient; B 5 n^3 dL/dgas
   double* fli_dpar = nullptr;                 // B x SIM_NPARAMS
@@ -436,6 +442,16 @@ static sim_status compute_force(sim_t* h, const float* s, const float* gas, SArg
   });
 }
 
+// Diagnostics record `idx` (the state after step idx - 1; idx 0 is the initial state).
+static sim_status record_diag(sim_t* h, int idx, const float* gas, const float* p,
+                              const float* zhat, const uint32_t* events) {
+  if (idx < 0 || idx > h->prm.n_steps) return SIM_OK;
+  const size_t r = (size_t)idx * h->B;
+  h->diag_recorded[idx] = 1;
+  return launch_diag(gas, p, zhat, events, h->N3, (float)h->prm.gamma, sarg(h->d_cm), h->B,
+                     h->d_diag_sums + r * DG_NSUM, h->d_diag_mins + r * 2, h->st);
+}
+
 // One forward step in place on (gas/gas_tmp ping-pong, s, p, g). With tape != nullptr the
 // inputs of every stage are recorded; diagnostics (star, aux, events) only without tape.
 // merged_in: the step opens with the merged kick K2_{i-1} + K1_i (the previous step ran
@@ -524,6 +540,9 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, B * h->N3, st));
   // 6. learned correction of the gas fields (solver in the loop, Sec. 4)
   if (h->closure) DH_TRY(closure_apply(h->closure, *gas, h->n, B, st));
+  // 7. diagnostics of the state after the step (eager steps only, not the recompute)
+  if (h->diag_on && !T)
+    DH_TRY(record_diag(h, i + 1, *gas, p, zh, P.subgrid_on ? h->events : nullptr));
   return SIM_OK;
 }
 
@@ -965,6 +984,12 @@ static sim_status closure_ready(sim_t* h) {
   return SIM_OK;
 }
 
+// Whether sim_run keeps each step's closing half kick apart from the next step's opening
+// one (the reverse pass recomputes segments the same way).
+static bool kicks_apart(const sim_t* h) {
+  return h->closure || h->prm.cfl_max > 0 || h->diag_on;
+}
+
 // Checks and allocations of sim_run (never inside a capture).
 static sim_status run_prepare(sim_t* h, int n_steps) {
   if (h->step != h->init_step || h->ckpt_count != 0) {
@@ -982,12 +1007,15 @@ static sim_status run_prepare(sim_t* h, int n_steps) {
 // n_steps forward steps with a checkpoint every ckpt_every steps (Sec. 2.3.5).
 static sim_status run_body(sim_t* h, int n_steps) {
   const int last = h->step + n_steps;
+  if (h->diag_on && n_steps > 0)
+    DH_TRY(record_diag(h, h->step, h->gas, h->p, nullptr, nullptr));
   for (int k = 0; k < n_steps; ++k) {
     const int rel = h->step - h->init_step, every = h->prm.ckpt_every;
     if (rel % every == 0) DH_TRY(store_checkpoint(h));
     // kicks merge inside a checkpoint segment (not with a closure, which acts on the state
-    // after the closing kick, nor with the CFL watchdog, which reads every step's state)
-    const bool plain = h->closure || h->prm.cfl_max > 0;
+    // after the closing kick, nor with the CFL watchdog or the diagnostics, which read every
+    // step's state)
+    const bool plain = kicks_apart(h);
     const bool merged_in = !plain && rel % every != 0;
     const bool kick_out = plain || h->step + 1 == last || (rel + 1) % every == 0;
     DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr, merged_in,
@@ -1059,7 +1087,7 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
     DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, first), h->w_g));
     // the same kick merging as the forward run: opening kicks merged after the segment's
     // first step, the closing kick only at the segment's end
-    const bool plain = h->prm.cfl_max > 0;
+    const bool plain = kicks_apart(h);
     for (int i = first; i < end; ++i) {
       const TapeSlot T = tape_slot(h, i - first);
       DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T,
@@ -1332,6 +1360,8 @@ sim_status sim_step(sim_t* h) {
   }
   const long long N3 = h->N3 * h->B;
   sim_status r = closure_ready(h);
+  if (r == SIM_OK && h->diag_on && h->step == h->init_step)
+    r = record_diag(h, h->step, h->gas, h->p, nullptr, nullptr);
   if (r == SIM_OK) r = dcopy(h->prev_gas, h->gas, 5 * N3 * sizeof(float), h->st);
   if (r == SIM_OK) r = part_join(h->prev_part, h->s, h->p, h, h->st);
   if (r == SIM_OK) r = forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr);
@@ -1440,40 +1470,162 @@ sim_status sim_loss_density(sim_t* h, const float* target, double c, float* dL_d
   return fail(h, r);
 }
 
+}  // extern "C"
+
+namespace dh {
+
+// Loss of an observable of the current gas state against `target` (B n^3), c sum (o - t)^2,
+// with dL/dgas (5 B n^3, fully written) and loss (B doubles, overwritten).
+static sim_status field_loss(sim_t* h, int obs, const float* target, double c, float* dL_dgas,
+                             double* loss) {
+  cudaStream_t st = h->st;
+  DH_TRY(dzero(loss, h->B * sizeof(double), st));
+  if (obs == SIM_OBS_THERMAL)
+    return launch_thermal_loss(h->gas, target, (float)c, dL_dgas, loss, h->N3, h->B, st);
+  DH_TRY(dzero(dL_dgas, 5 * h->B * h->N3 * sizeof(float), st));
+  return launch_density_loss(h->gas, target, (float)c, dL_dgas, loss, h->N3, h->B, st);
+}
+
+// The data term of the posterior of Sec. 3.2 at the amplitudes `noise`: ICs, the whole run,
+// loss (B doubles) and its gradient with respect to the amplitudes in h->fli_g.
+static sim_status posterior_data_term(sim_t* h, int obs, const float* noise, const float* data,
+                                      double sigma_n, double* loss) {
+  const long long N3 = h->N3 * h->B;
+  if (!h->fli_g) {
+    DH_TRY(dalloc_t(h, &h->fli_g, N3));
+    DH_TRY(dalloc_t(h, &h->fli_dL, 5 * N3));
+    DH_TRY(dalloc_t(h, &h->fli_dpar, (size_t)h->B * SIM_NPARAMS));
+  }
+  DH_TRY(load_noise(h, noise));
+  DH_TRY(make_ics(h));
+  h->ics_valid = true;
+  h->init_step = 0;
+  DH_TRY(reset_to_init(h));
+  DH_TRY(run_prepare(h, h->prm.n_steps));
+  DH_TRY(run_maybe_graph(h, 1, {(uintptr_t)h->prm.n_steps}, [&] { return run_body(h, h->prm.n_steps); }));
+  DH_TRY(field_loss(h, obs, data, 0.5 / (sigma_n * sigma_n), h->fli_dL, loss));
+  DH_TRY(run_adjoint_prepare(h, h->fli_g, h->fli_dpar));
+  const std::vector<uintptr_t> key = {(uintptr_t)h->fli_dL, (uintptr_t)0, (uintptr_t)h->fli_g,
+                                      (uintptr_t)h->fli_dpar};
+  return run_maybe_graph(h, 2, key, [&] {
+    return run_adjoint_body(h, h->fli_dL, nullptr, h->fli_g, h->fli_dpar);
+  });
+}
+
+static sim_status check_posterior_args(sim_t* h, int obs, const void* noise, const void* data,
+                                       const void* loss, double sigma_n, const char* who) {
+  if (!noise || !data || !loss || !(sigma_n > 0) || (obs != SIM_OBS_DENSITY && obs != SIM_OBS_THERMAL)) {
+    set_error("%s: null arrays, sigma_n <= 0 or unknown observable", who);
+    return SIM_EINVAL;
+  }
+  if (h->closure) {
+    set_error("%s: not available while a learned closure is set", who);
+    return SIM_ENOTIMPL;
+  }
+  if (h->prm.cfl_max > 0) {
+    set_error("%s: needs cfl_max = 0 (the run is differentiated as a whole)", who);
+    return SIM_EINVAL;
+  }
+  return SIM_OK;
+}
+
+}  // namespace dh
+
+extern "C" {
+
+sim_status sim_loss_field(sim_t* h, int32_t observable, const float* target, double c,
+                          float* dL_dgas, double* loss) {
+  if (!h || !target || !dL_dgas || !loss ||
+      (observable != SIM_OBS_DENSITY && observable != SIM_OBS_THERMAL)) {
+    set_error("sim_loss_field: null arguments or unknown observable");
+    return fail(h, SIM_EINVAL);
+  }
+  return fail(h, field_loss(h, observable, target, c, dL_dgas, loss));
+}
+
 // One iteration of field-level inference (Sec. 3.2): the posterior at the amplitudes
 // `noise`, its gradient through the whole checkpointed run, and an Adam step on the
 // amplitudes. Every stage is a library kernel or cuFFT call on the handle's stream.
-sim_status sim_fli_step(sim_t* h, float* noise, float* m, float* v, const float* data,
-                        double sigma_n, double lr, int32_t t, double* loss, float* grad) {
-  if (!h || !noise || !m || !v || !data || !loss || !(sigma_n > 0) || !(lr > 0) || t < 1) {
-    set_error("sim_fli_step: null arrays, sigma_n <= 0, lr <= 0 or t < 1");
+sim_status sim_fli_step(sim_t* h, int32_t observable, float* noise, float* m, float* v,
+                        const float* data, double sigma_n, double lr, int32_t t, double* loss,
+                        float* grad) {
+  if (!h) return SIM_EINVAL;
+  sim_status r = check_posterior_args(h, observable, noise, data, loss, sigma_n, "sim_fli_step");
+  if (r == SIM_OK && (!m || !v || !(lr > 0) || t < 1)) {
+    set_error("sim_fli_step: null moments, lr <= 0 or t < 1");
+    r = SIM_EINVAL;
+  }
+  if (r == SIM_OK) r = posterior_data_term(h, observable, noise, data, sigma_n, loss);
+  if (r == SIM_OK)
+    r = launch_fli_adam(noise, h->fli_g, m, v, h->N3, h->B, lr, 0.9, 0.999, 1e-8, t, 1.0, grad,
+                        loss, h->st);
+  return fail(h, r);
+}
+
+sim_status sim_posterior(sim_t* h, int32_t observable, const float* noise, const float* data,
+                         double sigma_n, double* loss, float* grad) {
+  if (!h) return SIM_EINVAL;
+  sim_status r = check_posterior_args(h, observable, noise, data, loss, sigma_n, "sim_posterior");
+  if (r == SIM_OK && !grad) {
+    set_error("sim_posterior: null gradient");
+    r = SIM_EINVAL;
+  }
+  if (r == SIM_OK) r = posterior_data_term(h, observable, noise, data, sigma_n, loss);
+  if (r == SIM_OK) r = launch_prior_grad(noise, h->fli_g, grad, h->N3, h->B, 1.0, loss, h->st);
+  return fail(h, r);
+}
+
+sim_status sim_set_diagnostics(sim_t* h, int32_t on) {
+  if (!h) return SIM_EINVAL;
+  if (on && !h->d_diag_sums) {
+    const size_t recs = (size_t)(h->prm.n_steps + 1) * h->B;
+    sim_status r = dalloc_t(h, &h->d_diag_sums, recs * DG_NSUM);
+    if (r == SIM_OK) r = dalloc_t(h, &h->d_diag_mins, recs * 2);
+    if (r != SIM_OK) return fail(h, r);
+    h->diag_recorded.assign(h->prm.n_steps + 1, 0);
+  }
+  if ((on != 0) != h->diag_on) clear_graphs(h);
+  h->diag_on = on != 0;
+  return SIM_OK;
+}
+
+sim_status sim_diagnostics(sim_t* h, int32_t step, double* out) {
+  if (!h || !out || step < 0 || step > h->prm.n_steps) {
+    set_error("sim_diagnostics: invalid arguments");
     return fail(h, SIM_EINVAL);
   }
-  if (h->closure) {
-    set_error("sim_fli_step: not available while a learned closure is set");
-    return fail(h, SIM_ENOTIMPL);
+  if (!h->d_diag_sums || !h->diag_recorded[step]) {
+    set_error("sim_diagnostics: no record of step %d (diagnostics off when it ran?)", step);
+    return fail(h, SIM_EINVAL);
   }
-  const long long N3 = h->N3 * h->B;
-  if (!h->fli_g) {
-    sim_status a = dalloc_t(h, &h->fli_g, N3);
-    if (a == SIM_OK) a = dalloc_t(h, &h->fli_dL, 5 * N3);
-    if (a == SIM_OK) a = dalloc_t(h, &h->fli_dpar, (size_t)h->B * SIM_NPARAMS);
-    // only the density field of dL/dgas is ever written: the other four stay zero
-    if (a == SIM_OK) a = dzero(h->fli_dL, 5 * N3 * sizeof(float), h->st);
-    if (a != SIM_OK) return fail(h, a);
+  const int B = h->B;
+  std::vector<double> sums((size_t)B * DG_NSUM);
+  std::vector<int> mins((size_t)B * 2);
+  const size_t r = (size_t)step * B;
+  DH_CUDA_TRY(cudaStreamSynchronize(h->st));
+  DH_CUDA_TRY(cudaMemcpy(sums.data(), h->d_diag_sums + r * DG_NSUM, sums.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost));
+  DH_CUDA_TRY(cudaMemcpy(mins.data(), h->d_diag_mins + r * 2, mins.size() * sizeof(int),
+                         cudaMemcpyDeviceToHost));
+  for (int b = 0; b < B; ++b) {
+    double* o = out + (size_t)b * SIM_DG_N;
+    const double* sb = sums.data() + (size_t)b * DG_NSUM;
+    o[SIM_DG_A] = a_of_step(h, step);
+    o[SIM_DG_MASS] = sb[DG_S_MASS];
+    o[SIM_DG_MX] = sb[DG_S_MX];
+    o[SIM_DG_MY] = sb[DG_S_MY];
+    o[SIM_DG_MZ] = sb[DG_S_MZ];
+    o[SIM_DG_ENERGY] = sb[DG_S_ENERGY];
+    o[SIM_DG_PX] = sb[DG_S_PX];
+    o[SIM_DG_PY] = sb[DG_S_PY];
+    o[SIM_DG_PZ] = sb[DG_S_PZ];
+    o[SIM_DG_STARS] = sb[DG_S_STARS];
+    o[SIM_DG_EVENTS] = sb[DG_S_EVENTS];
+    o[SIM_DG_NONFINITE] = sb[DG_S_NONFINITE];
+    o[SIM_DG_RHO_MIN] = ordered_to_float(mins[2 * b]);
+    o[SIM_DG_P_MIN] = ordered_to_float(mins[2 * b + 1]);
   }
-  sim_status r = sim_reinit(h, noise);
-  if (r == SIM_OK) r = sim_run(h, h->prm.n_steps);
-  if (r != SIM_OK) return r;
-  r = dzero(loss, h->B * sizeof(double), h->st);
-  if (r == SIM_OK)
-    r = launch_density_loss(h->gas, data, (float)(0.5 / (sigma_n * sigma_n)), h->fli_dL, loss,
-                            h->N3, h->B, h->st);
-  if (r != SIM_OK) return fail(h, r);
-  r = sim_run_adjoint(h, h->fli_dL, nullptr, h->fli_g, h->fli_dpar);
-  if (r != SIM_OK) return r;
-  return fail(h, launch_fli_adam(noise, h->fli_g, m, v, h->N3, h->B, lr, 0.9, 0.999, 1e-8, t,
-                                 1.0, grad, loss, h->st));
+  return SIM_OK;
 }
 
 sim_status sim_get_state(sim_t* h, float* gas, float* part, float* star, float* aux,
