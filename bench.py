@@ -45,10 +45,11 @@ WORKLOAD_NAME = ("128^3 cells + 128^3 DM particles, box 128 Mpc/h, 100 steps a=0
                  "(mock: seed-7 final density + 10% noise) + checkpointed adjoint (every 10 "
                  "steps) to the 2,097,152 white-noise amplitudes + Adam step")
 # field-level inference (Sec. 3.2, the 128^3 / 100-step / checkpoint-10 workload): mock data
-# from the held seed's run plus 10% noise, Adam on the amplitudes (learning rate 0.05)
+# from the held seed's run plus 10% noise, Adam on the amplitudes (learning rate 0.003: 0.01
+# oscillates and 0.03 diverges on this workload, measured over 200 iterations)
 FLI_TRUTH_SEED = 7
 FLI_NOISE_FRAC = 0.1
-FLI_LR = 0.05
+FLI_LR = 0.003
 FLI_ITERS = 200
 SWEEP_BYTES_PER_CELL = 40      # sweep: 5 float32 fields read + 5 written
 SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, input adjoint written

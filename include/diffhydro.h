@@ -147,6 +147,17 @@ void sim_destroy(sim_t* h);
 sim_status sim_init_batch(const sim_params* p, int32_t B, const float* noise, void* stream,
                           sim_t** out);
 
+/* Replace the parameters of every instance (host array of B sets) keeping the handle's
+ * allocations: n, box, the schedule (n_steps, a_start, a_end, ckpt_every), the switches,
+ * gamma, mu, limiter_eps and cfl_max must equal those at creation (SIM_EINVAL otherwise);
+ * cosmology (omega_m, omega_b, sigma8), T_init, the IC normalisation, the subgrid
+ * parameters and the seeds may change. The schedules and per-instance tables are
+ * recomputed, the initial conditions are rebuilt from the current white noise (or stay
+ * invalid after sim_set_state), the handle is rewound to its initial state and captured
+ * graphs are dropped. Synchronises the handle's stream. This is the entry of parameter
+ * inference (Sec. 3.1): one handle evaluated at many parameter points. */
+sim_status sim_set_params(sim_t* h, const sim_params* p);
+
 /* Number of instances of the handle (1 for sim_init). */
 int32_t sim_batch_size(const sim_t* h);
 
@@ -161,7 +172,10 @@ enum {
   SIM_SWEEP_TILE = 1,
   SIM_SWEEP_MARCH32 = 2,
   SIM_SWEEP_MARCH16 = 3,
-  SIM_SWEEP_MARCH_FIT = 4
+  SIM_SWEEP_MARCH_FIT = 4,
+  SIM_SWEEP_PAIR = 5  /* forward y / z sweeps with even n: the fitted marching form on two
+                         adjacent lines per thread in packed FP32x2 arithmetic (elsewhere,
+                         and for the adjoint, as MARCH_FIT / the tile)                  */
 };
 
 /* Set the variant of the forward (fwd[3], per axis) and adjoint (adj[3]) sweeps of the
@@ -333,6 +347,13 @@ sim_status sim_adam(float* x, const float* g, float* m, float* v, int64_t count,
                     double beta1, double beta2, double eps, int32_t t, double prior_w,
                     float* grad_out, double* prior, void* stream);
 
+/* Adjoint of sim_power_spectrum (auto spectrum): dL_da (n^3, overwritten) = sum over bins b
+ * of dL_dpk[b] dP_b/da, for dL_dpk device doubles of length nbins, same binning. Uses cuFFT.
+ * With it a likelihood of the binned spectrum is differentiated back to the density field
+ * and, through sim_run_adjoint, to the parameters (Sec. 3.1). */
+sim_status sim_power_spectrum_adjoint(const float* a, int32_t n, double box, int32_t nbins,
+                                      const double* dL_dpk, float* dL_da, void* stream);
+
 /* Cross-correlation coefficient r_c(k) = P_ab / sqrt(P_aa P_bb) (Sec. 3.2) of two n^3 fields,
  * binned as sim_power_spectrum (width 2 pi / box, index round(|k| box / 2 pi), bins
  * 1..nbins): k (mode-weighted mean |k|), rc (0 where a power is 0), nmodes; device doubles
@@ -495,6 +516,12 @@ sim_status sim_ic_amplitude(const sim_t* h, int32_t b, double* C);
  * rounding order), other values SIM_EINVAL. */
 sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int32_t axis, double nu,
                      double gamma, double limiter_eps, int32_t variant, void* stream);
+
+/* Largest signal speed max over cells of max(|v_x|, |v_y|, |v_z|) + c_s of a gas state
+ * (5 n^3), written to *out (one device float); NaN if any cell is not finite. With a step
+ * dt the CFL number of Eq. dt is *out dt / dx. */
+sim_status sim_max_signal_speed(const float* gas, int32_t n, double gamma, float* out,
+                                void* stream);
 
 /* Adjoint of sim_sweep at u_in: lam_in = (d u_out / d u_in)^T lam_out (5 n^3 each, no
  * aliasing). If dnu (device double) is not NULL, adds lam_out . d u_out / d nu to it.

@@ -165,17 +165,31 @@ def mse_density(U, target):
     return ((U[0] - target) ** 2).mean()
 
 
-def fli_value_and_grad(noise, data, sigma_noise, prm, n_steps: int | None = None):
+def observable(U, kind: str = "density"):
+    """Observed field of the final gas state (Sec. 3): the density, or ("thermal") the
+    internal energy density eps - |m|^2 / (2 rho) = a^2 rho e, proportional to the
+    gas-mass-weighted temperature rho T of the delta_b T probe of Sec. 3.2."""
+    if kind == "density":
+        return U[0]
+    if kind == "thermal":
+        return U[4] - (U[1:4] ** 2).sum(0) / (2.0 * U[0])
+    raise ValueError(kind)
+
+
+def fli_value_and_grad(noise, data, sigma_noise, prm, n_steps: int | None = None,
+                       kind: str = "density"):
     """Posterior of field-level inference (Sec. 3.2) at the amplitudes `noise` and its
     gradient by reverse mode through the whole run (float64)."""
     s = noise.detach().clone().requires_grad_(True)
     U = run(s, prm, n_steps)["U"]
-    L = fli_loss(U, data, sigma_noise, s)
+    L = fli_loss(U, data, sigma_noise, s, kind)
     (g,) = torch.autograd.grad(L, s)
     return L.detach(), g
 
 
-def fli_loss(U, data, sigma_noise, noise):
+def fli_loss(U, data, sigma_noise, noise, kind: str = "density"):
     """Negative log posterior of field-level inference (Sec. 3.2):
-    1/2 sum[(d - F(s))^2 / N + |s|^2], here on the final gas density and white noise s."""
-    return 0.5 * (((data - U[0]) ** 2).sum() / sigma_noise ** 2 + (noise ** 2).sum())
+    1/2 sum[(d - F(s))^2 / N + |s|^2], F the observable of the final gas state and s the
+    white noise."""
+    return 0.5 * (((data - observable(U, kind)) ** 2).sum() / sigma_noise ** 2 +
+                  (noise ** 2).sum())

@@ -65,6 +65,7 @@ SIGNATURES = {
     "sim_init": (ctypes.c_int, [_PP, _P, _P, ctypes.POINTER(_P)]),
     "sim_init_batch": (ctypes.c_int, [_PP, _I32, _P, _P, ctypes.POINTER(_P)]),
     "sim_batch_size": (ctypes.c_int32, [_P]),
+    "sim_set_params": (ctypes.c_int, [_P, _PP]),
     "sim_set_sweep_variants": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sim_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "sim_destroy": (None, [_P]),
@@ -105,6 +106,7 @@ SIGNATURES = {
     "sim_cfl": (ctypes.c_int, [_P, ctypes.POINTER(_D)]),
     "sim_sweep": (ctypes.c_int, [_P, _P, _I32, _I32, _D, _D, _D, _I32, _P]),
     "sim_sweep_adjoint": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _D, _D, _D, _P, _I32, _P]),
+    "sim_max_signal_speed": (ctypes.c_int, [_P, _I32, _D, _P, _P]),
     "sim_deposit_cic": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P]),
     "sim_deposit_cic_static": (ctypes.c_int, [_P, _P, _I32, _D, _P, _P]),
     "sim_interp_cic": (ctypes.c_int, [_P, _I32, _I32, _D, _P, _P, _P]),
@@ -122,6 +124,7 @@ SIGNATURES = {
     "sim_dot": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
     "sim_axpby": (ctypes.c_int, [_D, _P, _D, _P, _I64, _P]),
     "sim_adam": (ctypes.c_int, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I32, _D, _P, _P, _P]),
+    "sim_power_spectrum_adjoint": (ctypes.c_int, [_P, _I32, _D, _I32, _P, _P, _P]),
     "sim_cross_correlation": (ctypes.c_int, [_P, _P, _I32, _D, _I32, _P, _P, _P, _P]),
 }
 

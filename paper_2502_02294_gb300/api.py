@@ -53,6 +53,16 @@ def sweep(u_in, axis: int, nu: float, gamma: float = 5.0 / 3.0, limiter_eps: flo
     return out
 
 
+def max_signal_speed(gas, gamma: float = 5.0 / 3.0) -> float:
+    """max over cells of max_d |v_d| + c_s (sim_max_signal_speed; synchronises)."""
+    n = _side(gas.numel() // 5)
+    _chk(gas, F32, 5 * n ** 3, "gas")
+    out = torch.empty(1, dtype=F32, device=gas.device)
+    check(lib.sim_max_signal_speed(_ptr(gas), n, gamma, _ptr(out), _stream()),
+          "sim_max_signal_speed")
+    return out.item()
+
+
 def sweep_adjoint(u_in, lam_out, axis: int, nu: float, gamma: float = 5.0 / 3.0,
                   limiter_eps: float = 1e-30, variant: int = 0):
     n = _side(u_in.numel() // 5)
@@ -134,6 +144,17 @@ def power_spectrum(a, box: float, nbins: int, b=None):
     return k, pk, nm
 
 
+def power_spectrum_adjoint(a, box: float, nbins: int, dL_dpk):
+    """dL/da for a loss of the binned auto spectrum of a (sim_power_spectrum_adjoint)."""
+    n = a.shape[-1]
+    _chk(a, F32, n ** 3, "a")
+    _chk(dL_dpk, F64, nbins, "dL_dpk")
+    out = torch.empty_like(a)
+    check(lib.sim_power_spectrum_adjoint(_ptr(a), n, box, nbins, _ptr(dL_dpk), _ptr(out),
+                                         _stream()), "sim_power_spectrum_adjoint")
+    return out
+
+
 def cross_correlation(a, b, box: float, nbins: int):
     """(k, r_c(k), nmodes) of two n^3 fields (sim_cross_correlation)."""
     n = a.shape[-1]
@@ -210,6 +231,13 @@ class Simulation:
                                  ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h)),
               "sim_init_batch")
         self.h = h
+
+    def set_params(self, params):
+        """New parameter set(s) for the same grid and schedule (sim_set_params)."""
+        plist = list(params) if isinstance(params, (list, tuple)) else [params]
+        arr = (SimParams * self.B)(*plist)
+        self._check(lib.sim_set_params(self.h, arr), "sim_set_params")
+        self.params, self.params_list, self._arr = plist[0], plist, arr
 
     def _shape(self, *dims):
         return dims if self.B == 1 else (self.B,) + dims

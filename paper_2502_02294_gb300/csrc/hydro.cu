@@ -238,6 +238,128 @@ sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int 
   }
 }
 
+// ------------------------------------------------------------- forward, paired marching form
+// The marching form above for two adjacent lines per thread (x columns w, w + 1 of a y or z
+// sweep): each field is one 8-byte load per cell, and every per-cell operation runs on the
+// pair with the packed FP32x2 instructions of sm_100+ (FADD2 / FMUL2 / FFMA2: one issue slot
+// for two lanes), so the instruction count per cell roughly halves; reciprocals, square
+// roots, sign tests and selects stay per lane. The half differences of the limiter inputs
+// are formed once per cell and kept in the window (face j uses those of cells j and j + 1).
+__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, pk(-1.0f), a); }
+
+// flux splits of two cells (F^R = (cU + F)/2, F^L = (cU - F)/2), as split_flux
+__device__ __forceinline__ void split_flux2(const float2 u[5], int f, float gam, float2 FR[5],
+                                            float2 FL[5]) {
+  const float2 inv = make_float2(fast_rcp(u[0].x), fast_rcp(u[0].y));
+  const float2 hinv = mul2(inv, pk(0.5f));
+  const float2 hv = mul2(u[f], hinv);  // v / 2
+  const float2 m2 = fma2(u[1], u[1], fma2(u[2], u[2], mul2(u[3], u[3])));
+  const float2 P = mul2(pk(gam - 1.0f), fma2(mul2(m2, hinv), pk(-1.0f), u[4]));
+  const float2 cs2 = mul2(mul2(P, inv), pk(gam));
+  const float csx = cs2.x > 0.0f ? cs2.x * rsqrtf(cs2.x) : 0.0f;
+  const float csy = cs2.y > 0.0f ? cs2.y * rsqrtf(cs2.y) : 0.0f;
+  const float2 hc = fma2(make_float2(csx, csy), pk(0.5f), make_float2(fabsf(hv.x), fabsf(hv.y)));
+  float2 hF[5];
+  hF[0] = mul2(u[f], pk(0.5f));
+  hF[1] = mul2(u[1], hv);
+  hF[2] = mul2(u[2], hv);
+  hF[3] = mul2(u[3], hv);
+  hF[f] = fma2(P, pk(0.5f), hF[f]);
+  hF[4] = mul2(add2(u[4], P), hv);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    FR[k] = fma2(hc, u[k], hF[k]);
+    FL[k] = fma2(hF[k], pk(-2.0f), FR[k]);
+  }
+}
+
+// gated van Leer limiter of two lanes, as vanleer
+__device__ __forceinline__ float2 vanleer2(float2 a, float2 b, float eps) {
+  const float2 ab = mul2(a, b);
+  const float2 s = add2(a, b);
+  const float2 D = add2(s, make_float2(copysignf(eps, s.x), copysignf(eps, s.y)));
+  const float2 t = mul2(add2(ab, ab), make_float2(fast_rcp(D.x), fast_rcp(D.y)));
+  return make_float2(ab.x > 0.0f ? t.x : 0.0f, ab.y > 0.0f ? t.y : 0.0f);
+}
+
+// AXIS 1 or 2; n even (8-byte aligned pairs). Thread: lines w, w + 1 (w even), segment of L
+// output cells from s0 along the sweep axis.
+template <int AXIS>
+__global__ void __launch_bounds__(128)
+sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
+                    float gam, float eps, int L) {
+  constexpr int F = 1 + AXIS;
+  const int w = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int b = blockIdx.y / n;
+  const int t = blockIdx.y - b * n;
+  const int s0 = blockIdx.z * L;
+  if (w >= n) return;
+  const long long N3 = (long long)n * n * n;
+  uin += (size_t)b * 5 * N3;
+  uout += (size_t)b * 5 * N3;
+  const float nu = nua.at(b);
+  const float2 hnu = pk(0.5f * nu), mnu = pk(-nu);
+  float2 Ua[5], Ub[5], Uc[5];  // U_{j-3}, U_{j-2}, U_{j-1}
+  float2 FRp[5], f1m[5];       // F^R_{j-1}, first-order face j-3/2
+  float2 R1[5], R2[5];         // Fh^R_{j-3}, Fh^R_{j-2}
+  float2 dRa[5], dRb[5];       // (Fh^R_{j-3} - Fh^R_{j-4}) / 2, (Fh^R_{j-2} - Fh^R_{j-3}) / 2
+  float2 L1[5], dLa[5];        // Fh^L_{j-2}, (Fh^L_{j-2} - Fh^L_{j-3}) / 2
+  float2 F2m[5];               // limited face (j-4)+1/2
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float init = (k == 0 || k == 4) ? 1.0f : 0.0f;
+    Ua[k] = Ub[k] = Uc[k] = pk(init);
+    FRp[k] = f1m[k] = R1[k] = R2[k] = dRa[k] = dRb[k] = L1[k] = dLa[k] = F2m[k] = pk(0.0f);
+  }
+  int j = wrap_periodic(s0 - 3, n);
+#pragma unroll 1
+  for (int it = 0; it < L + 6; ++it) {
+    float2 u[5];
+    const long long o = goff<AXIS>(j, w, t, n);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) u[k] = __ldg(reinterpret_cast<const float2*>(uin + k * N3 + o));
+    float2 FR[5], FL[5];
+    split_flux2(u, F, gam, FR, FL);
+    float2 f1[5], uh[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      f1[k] = sub2(FRp[k], FL[k]);                       // face j-1/2
+      uh[k] = fma2(hnu, sub2(f1m[k], f1[k]), Uc[k]);     // Uh_{j-1}
+    }
+    float2 FRh[5], FLh[5];
+    split_flux2(uh, F, gam, FRh, FLh);
+    const int jo = s0 + it - 6;  // output cell j-3 (unwrapped)
+    const bool store = it >= 6 && jo < n;
+    const long long oo = goff<AXIS>(jo < n ? jo : 0, w, t, n);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float2 dLb = mul2(sub2(FLh[k], L1[k]), pk(0.5f));
+      const float2 fr = add2(R1[k], vanleer2(dRa[k], dRb[k], eps));
+      const float2 fl = sub2(L1[k], vanleer2(dLa[k], dLb, eps));
+      const float2 F2 = sub2(fr, fl);                    // face (j-3)+1/2
+      if (store)
+        *reinterpret_cast<float2*>(uout + k * N3 + oo) = fma2(mnu, sub2(F2, F2m[k]), Ua[k]);
+      F2m[k] = F2;
+      dRa[k] = dRb[k];
+      dRb[k] = mul2(sub2(FRh[k], R2[k]), pk(0.5f));
+      R1[k] = R2[k];
+      R2[k] = FRh[k];
+      dLa[k] = dLb;
+      L1[k] = FLh[k];
+      Ua[k] = Ub[k];
+      Ub[k] = Uc[k];
+      Uc[k] = u[k];
+      FRp[k] = FR[k];
+      f1m[k] = f1[k];
+    }
+    j = (j + 1 == n) ? 0 : j + 1;
+  }
+}
+
 // ------------------------------------------------------------- adjoint, marching form
 // Pass 1: each thread streams one line segment [s0, s0 + L) plus a halo and produces
 // lamUh_j for its own cells. At load i it recomputes the forward stages for cell i-1
@@ -634,7 +756,8 @@ static int pick_fwd(int axis, int n, int variant) {
 
 static int pick_adj(int axis, int variant) {
   (void)axis;
-  return variant != SIM_SWEEP_DEFAULT ? variant : SIM_SWEEP_MARCH_FIT;
+  // the paired form is forward only; its adjoint is the fitted marching pair
+  return (variant != SIM_SWEEP_DEFAULT && variant != SIM_SWEEP_PAIR) ? variant : SIM_SWEEP_MARCH_FIT;
 }
 
 // Segment length of a marching kernel for an n^3 grid of B instances: the number k of
@@ -642,7 +765,7 @@ static int pick_adj(int axis, int variant) {
 // 128 threads that stay resident on all SMs at the kernel's register use (each thread
 // streams its segment plus the halo once).
 template <class Kern>
-static int fit_segment(Kern kernel, int n, int B, int halo) {
+static int fit_segment(Kern kernel, int n, int B, int halo, int xthreads = 0) {
   // blocks of 128 threads resident on the current device, per kernel and device
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, long long> cache;
@@ -667,7 +790,8 @@ static int fit_segment(Kern kernel, int n, int B, int halo) {
     }
     resident = it->second;
   }
-  const long long layer = (long long)cdiv(n, 128) * n * B;  // blocks of one segment layer
+  // blocks of one segment layer: xthreads threads along x (n: one line per thread)
+  const long long layer = (long long)cdiv(xthreads > 0 ? xthreads : n, 128) * n * B;
   int best = n, best_cost = 1 << 30;
   for (int k = 1; k <= n; ++k) {
     const int L = cdiv(n, k);
@@ -699,10 +823,24 @@ static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, 
 }
 
 template <int AXIS>
+static sim_status launch_march2_t(const float* uin, float* uout, int n, SArg nu, float gam,
+                                  float eps, int B, cudaStream_t st) {
+  const int L = fit_segment(sweep_march2_kernel<AXIS == 0 ? 1 : AXIS>, n, B, 6, n / 2);
+  dim3 grid(cdiv(n / 2, 128), n * B, cdiv(n, L));
+  sweep_march2_kernel<AXIS == 0 ? 1 : AXIS><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps, L);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+template <int AXIS>
 static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, float gam,
                                  float eps, int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  if (AXIS != 0 && variant != SIM_SWEEP_TILE)
+  // the paired form needs two adjacent x columns per thread: y / z sweeps, n even
+  if (AXIS != 0 && variant == SIM_SWEEP_PAIR && n % 2 == 0 &&
+      ((reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(uout)) % 8) == 0)
+    return launch_march2_t<AXIS>(uin, uout, n, nu, gam, eps, B, st);
+  if (AXIS != 0 && variant != SIM_SWEEP_TILE && variant != SIM_SWEEP_PAIR)
     return launch_march_t<AXIS>(uin, uout, n, nu, gam, eps, B, variant, st);
   constexpr int NC = (C::S + 6) * C::W;
   const size_t smem = 15 * NC * sizeof(float);
@@ -910,7 +1048,7 @@ extern "C" sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int3
                                 double nu, double gamma, double limiter_eps, int32_t variant,
                                 void* stream) {
   if (!u_in || !u_out || n < 1 || u_in == u_out || variant < SIM_SWEEP_DEFAULT ||
-      variant > SIM_SWEEP_MARCH_FIT) {
+      variant > SIM_SWEEP_PAIR) {
     dh::set_error("sim_sweep: null/aliased buffers, n < 1 or unknown variant");
     return SIM_EINVAL;
   }
@@ -923,7 +1061,7 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
                                         double limiter_eps, double* dnu, int32_t variant,
                                         void* stream) {
   if (!u_in || !lam_out || !lam_in || n < 1 || lam_in == lam_out || lam_in == u_in ||
-      variant < SIM_SWEEP_DEFAULT || variant > SIM_SWEEP_MARCH_FIT) {
+      variant < SIM_SWEEP_DEFAULT || variant > SIM_SWEEP_PAIR) {
     dh::set_error("sim_sweep_adjoint: null/aliased buffers, n < 1 or unknown variant");
     return SIM_EINVAL;
   }

@@ -822,13 +822,16 @@ static sim_status setup_instances(sim_t* h) {
   h->h_sc = sctab;
   h->h_pn = pn;
   h->h_sub = sub;
-  DH_TRY(dalloc_t(h, &h->d_sc, sctab.size()));
-  DH_TRY(dalloc_t(h, &h->d_pn, pn.size()));
-  DH_TRY(dalloc_t(h, &h->d_cm, cm.size()));
-  DH_TRY(dalloc_t(h, &h->d_sub, sub.size()));
-  DH_TRY(dalloc_t(h, &h->d_pch, pch.size()));
-  DH_TRY(dalloc_t(h, &h->d_cpref, cpref.size()));
-  DH_TRY(dalloc_t(h, &h->dcoef, coef.size()));
+  // the tables keep their size for a handle's life (sim_set_params refills them in place)
+  if (!h->d_sc) {
+    DH_TRY(dalloc_t(h, &h->d_sc, sctab.size()));
+    DH_TRY(dalloc_t(h, &h->d_pn, pn.size()));
+    DH_TRY(dalloc_t(h, &h->d_cm, cm.size()));
+    DH_TRY(dalloc_t(h, &h->d_sub, sub.size()));
+    DH_TRY(dalloc_t(h, &h->d_pch, pch.size()));
+    DH_TRY(dalloc_t(h, &h->d_cpref, cpref.size()));
+    DH_TRY(dalloc_t(h, &h->dcoef, coef.size()));
+  }
   auto up = [](void* d, const void* s, size_t bytes) -> sim_status {
     DH_CUDA_TRY(cudaMemcpy(d, s, bytes, cudaMemcpyHostToDevice));
     return SIM_OK;
@@ -1214,6 +1217,34 @@ sim_status sim_init_batch(const sim_params* p, int32_t B, const float* noise, vo
   return SIM_OK;
 }
 
+sim_status sim_set_params(sim_t* h, const sim_params* p) {
+  if (!h) return SIM_EINVAL;
+  sim_status r = validate_batch(p, h->B);
+  if (r != SIM_OK) return fail(h, r);
+  const sim_params& a = h->prm;
+  const sim_params& q = p[0];
+  const bool same = q.n == a.n && q.box == a.box && q.n_steps == a.n_steps &&
+                    q.a_start == a.a_start && q.a_end == a.a_end && q.ckpt_every == a.ckpt_every &&
+                    q.subgrid_on == a.subgrid_on && q.gravity_on == a.gravity_on &&
+                    q.hydro_on == a.hydro_on && q.kdk_mode == a.kdk_mode && q.gamma == a.gamma &&
+                    q.mu == a.mu && q.limiter_eps == a.limiter_eps && q.cfl_max == a.cfl_max;
+  if (!same) {
+    set_error("sim_set_params: n, box, schedule, switches, gamma, mu, limiter_eps and cfl_max "
+              "must stay as at sim_init");
+    return fail(h, SIM_EINVAL);
+  }
+  // the tables are read by captured graphs in place, but one instance passes its scalars by
+  // value: drop the graphs
+  DH_CUDA_TRY(cudaStreamSynchronize(h->st));
+  clear_graphs(h);
+  h->prms.assign(p, p + h->B);
+  h->prm = p[0];
+  r = setup_instances(h);
+  if (r == SIM_OK && h->ics_valid) r = make_ics(h);
+  if (r == SIM_OK) r = reset_to_init(h);
+  return fail(h, r);
+}
+
 sim_status sim_init(const sim_params* p, const float* noise, void* stream, sim_t** out) {
   return sim_init_batch(p, 1, noise, stream, out);
 }
@@ -1275,7 +1306,7 @@ sim_status sim_set_sweep_variants(sim_t* h, const int32_t* fwd, const int32_t* a
   for (int a = 0; a < 3; ++a) {
     const int vals[2] = {fwd ? fwd[a] : 0, adj ? adj[a] : 0};
     for (int v : vals)
-      if (v < SIM_SWEEP_DEFAULT || v > SIM_SWEEP_MARCH_FIT) {
+      if (v < SIM_SWEEP_DEFAULT || v > SIM_SWEEP_PAIR) {
         set_error("sim_set_sweep_variants: unknown variant %d", v);
         return fail(h, SIM_EINVAL);
       }
@@ -1302,7 +1333,8 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
   DH_CUDA_TRY(cudaEventCreate(&e1));
   const int i = h->step < h->prm.n_steps ? h->step : h->prm.n_steps - 1;
   const SArg nu = sc(h, i, SC_NU);
-  const int cand[4] = {SIM_SWEEP_TILE, SIM_SWEEP_MARCH32, SIM_SWEEP_MARCH16, SIM_SWEEP_MARCH_FIT};
+  const int cand[5] = {SIM_SWEEP_TILE, SIM_SWEEP_MARCH32, SIM_SWEEP_MARCH16, SIM_SWEEP_MARCH_FIT,
+                       SIM_SWEEP_PAIR};
   auto time_it = [&](auto launch, float* ms) -> sim_status {
     DH_TRY(launch());  // warm-up
     float best = 1e30f;
@@ -1321,9 +1353,10 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
   auto body = [&]() -> sim_status {
     for (int axis = 0; axis < 3; ++axis) {
       float bf = 1e30f, ba = 1e30f;
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < 5; ++c) {
         float t = 0.0f;
-        if (axis != 0 || c == 0) {  // forward x: the tile only
+        // forward x: the tile only; the paired form needs an even n
+        if ((axis != 0 || c == 0) && (cand[c] != SIM_SWEEP_PAIR || h->n % 2 == 0)) {
           DH_TRY(time_it([&] { return launch_sweep(axis, h->gas, h->w_gas2, h->n, nu,
                                                    h->prm.gamma, h->prm.limiter_eps, h->B,
                                                    cand[c], st); }, &t));
@@ -1332,6 +1365,7 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
             h->fwd_var[axis] = cand[c];
           }
         }
+        if (cand[c] == SIM_SWEEP_PAIR) continue;  // forward only
         DH_TRY(time_it([&] { return launch_sweep_adjoint(axis, h->gas, h->gas, h->lam_tmp, h->n,
                                                          nu, h->prm.gamma, h->prm.limiter_eps,
                                                          dpart(h->dslots, SL_N), h->lam_scr,

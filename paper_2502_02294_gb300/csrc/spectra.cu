@@ -46,9 +46,91 @@ __global__ void pk_finish_kernel(const double* __restrict__ sums, int nbins, dou
   pk[j] = w > 0 ? norm * sums[2 * nbins + j] / w : 0.0;
 }
 
+// Adjoint of the binned spectrum: for the half-complex mode k of bin b,
+//   ak <- ak * 2 norm dL/dP_b / W_b   (W_b the bin's mode weight, from sums[0..nbins)),
+// modes outside bins 1..nbins <- 0. The unnormalised c2r of the result is dL/da: each P_b is
+// norm / W_b sum_half w |a_k|^2, and the half-complex weights w make sum_half w Re(conj(a_k)
+// e^{-ikx}) the full-grid sum that c2r evaluates.
+__global__ void pk_adj_scale_kernel(cufftComplex* __restrict__ ak, int n, int nbins,
+                                    const double* __restrict__ dL_dpk,
+                                    const double* __restrict__ sums, double norm) {
+  const int nh = n / 2 + 1;
+  const long long NC = (long long)n * n * nh;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < NC;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % nh);
+    const long long r = i / nh;
+    int ky = (int)(r % n), kz = (int)(r / n);
+    if (ky > n / 2) ky -= n;
+    if (kz > n / 2) kz -= n;
+    const int bin = (int)rint(sqrt((double)kx * kx + (double)ky * ky + (double)kz * kz));
+    float c = 0.0f;
+    if (bin >= 1 && bin <= nbins && sums[bin - 1] > 0)
+      c = (float)(2.0 * norm * dL_dpk[bin - 1] / sums[bin - 1]);
+    ak[i].x *= c;
+    ak[i].y *= c;
+  }
+}
+
 }  // namespace dh
 
 using namespace dh;
+
+extern "C" sim_status sim_power_spectrum_adjoint(const float* a, int32_t n, double box,
+                                                 int32_t nbins, const double* dL_dpk,
+                                                 float* dL_da, void* stream) {
+  if (!a || !dL_dpk || !dL_da || n < 2 || !(box > 0) || nbins < 1 || nbins > 2048) {
+    set_error("sim_power_spectrum_adjoint: invalid arguments (1 <= nbins <= 2048)");
+    return SIM_EINVAL;
+  }
+  FFTPlans* plans = shared_plans(n);
+  if (!plans) return SIM_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long NC = (long long)n * n * (n / 2 + 1);
+  cufftComplex* ak = nullptr;
+  double* sums = nullptr;
+  DH_CUDA_TRY(cudaMallocAsync((void**)&ak, NC * sizeof(cufftComplex), st));
+  if (cudaMallocAsync((void**)&sums, 3 * nbins * sizeof(double), st) != cudaSuccess) {
+    cudaFreeAsync(ak, st);
+    set_error("cudaMallocAsync failed");
+    return SIM_ENOMEM;
+  }
+  sim_status r = plans->set_stream(st);
+  if (r == SIM_OK && cudaMemsetAsync(sums, 0, 3 * nbins * sizeof(double), st) != cudaSuccess) {
+    set_error("cudaMemsetAsync failed");
+    r = SIM_ECUDA;
+  }
+  if (r == SIM_OK && cufftExecR2C(plans->r2c1, const_cast<float*>(a), ak) != CUFFT_SUCCESS) {
+    set_error("cufftExecR2C failed");
+    r = SIM_ECUDA;
+  }
+  int blocks = cdiv(NC, 256);
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  if (r == SIM_OK) {  // mode weights per bin (the power sums are not needed)
+    pk_bin_kernel<<<blocks, 256, 3 * nbins * sizeof(double), st>>>(ak, ak, n, nbins, sums);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("pk_bin_kernel launch failed");
+      r = SIM_ECUDA;
+    }
+  }
+  if (r == SIM_OK) {
+    const double norm = box * box * box / ((double)n * n * n * (double)n * n * n);
+    pk_adj_scale_kernel<<<blocks, 256, 0, st>>>(ak, n, nbins, dL_dpk, sums, norm);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("pk_adj_scale_kernel launch failed");
+      r = SIM_ECUDA;
+    }
+  }
+  if (r == SIM_OK && cufftExecC2R(plans->c2r1, ak, dL_da) != CUFFT_SUCCESS) {
+    set_error("cufftExecC2R failed");
+    r = SIM_ECUDA;
+  }
+  cudaFreeAsync(ak, st);
+  cudaFreeAsync(sums, st);
+  return r;
+}
 
 extern "C" sim_status sim_power_spectrum(const float* a, const float* b, int32_t n, double box,
                                          int32_t nbins, double* k, double* pk, double* nmodes,

@@ -249,6 +249,19 @@ sim_status launch_signal_speed(const float* gas, float gamma, long long N3,
 
 using namespace dh;
 
+extern "C" sim_status sim_max_signal_speed(const float* gas, int32_t n, double gamma,
+                                           float* out, void* stream) {
+  if (!gas || !out || n < 1 || !(gamma > 1)) {
+    set_error("sim_max_signal_speed: invalid arguments");
+    return SIM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  DH_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(float), st));
+  // speeds are >= 0, so the largest float is the largest bit pattern (a NaN above all)
+  return launch_signal_speed(gas, (float)gamma, (long long)n * n * n,
+                             reinterpret_cast<unsigned int*>(out), 1, st);
+}
+
 extern "C" sim_status sim_subgrid(float* gas, int32_t n, double a, const sim_params* p,
                                   int32_t step, float* zhat, uint32_t* events, void* stream) {
   if (!gas || !p || n < 1 || !(a > 0) || !(p->Pi0 > 0 && p->Pi0 < 1) || !(p->tau > 0) ||

@@ -180,3 +180,19 @@ def test_fli_posterior_is_the_wiener_filter_for_a_linear_forward():
     L1_want = 0.5 * (((d - fb - fb * As1) ** 2).sum() / sig ** 2 + (s1 ** 2).sum())
     assert abs(L1.item() / L1_want - 1) < 1e-12
     assert L1.item() > Ls.item()
+
+
+def test_thermal_observable_is_internal_energy_density():
+    """eps - |m|^2/(2 rho) = a^2 rho e: for a uniform gas at T it is a^2 f_b T / t_per_e,
+    with any bulk velocity (the kinetic part is removed)."""
+    n, a = 4, 0.3
+    prm = sim.Params(n=n, box=4.0, a_start=a, T_init=2e4).as_dict()
+    s, p, U = sim.ics.initial_conditions(torch.zeros(n, n, n, dtype=DT), prm)
+    fb = prm["omega_b"] / prm["omega_m"]
+    want = a * a * fb * 2e4 / t_per_e(prm["gamma"], prm["mu"])
+    assert torch.allclose(sim.observable(U, "thermal"), torch.full((n, n, n), want, dtype=DT),
+                          rtol=1e-12)
+    U2 = U.clone()
+    U2[1] = 0.3 * U2[0]
+    U2[4] = U2[4] + 0.5 * U2[1] ** 2 / U2[0]
+    assert torch.allclose(sim.observable(U2, "thermal"), sim.observable(U, "thermal"), rtol=1e-12)
