@@ -177,6 +177,41 @@ def bench_batched(dh, synth, torch, steps: int, warmup: int):
                                for n, v in zip(BATCH_SIZES, variants)}}
 
 
+def bench_lbfgs(dh, synth, torch, sim, truth, p, iters: int):
+    """Sec. 3.2 as the paper runs it: subgrid off, the delta_b T probe (internal energy
+    density), pixel noise of variance 1x (S/N = 1) and 5x (S/N = 5) the data variance,
+    L-BFGS with M = 8 from zero amplitudes; r_c(k) of the recovered amplitudes."""
+    from paper_2502_02294_gb300.inference import fli_lbfgs
+    n = p.n
+    q = dh.SimParams.from_buffer_copy(p)
+    q.subgrid_on = 0
+    s2 = dh.Simulation(q, truth)
+    s2.set_graphs(True)
+    s2.run()
+    g = s2.state()["gas"]
+    u = (g[4] - 0.5 * (g[1] ** 2 + g[2] ** 2 + g[3] ** 2) / g[0]).contiguous()
+    out = {"workload": "128^3, 100 steps a=0.05->1.0, subgrid off; data = internal energy "
+                       "density of the seed-%d run + Gaussian pixel noise; L-BFGS M=8 from "
+                       "zero amplitudes, at most %d iterations" % (FLI_TRUTH_SEED, iters)}
+    nb = n // 2
+    for snr in (1.0, 5.0):
+        sig = float(snr ** 0.5 * u.std().item())
+        data = (u + sig * torch.from_numpy(synth.field(n, 900 + int(snr)).astype("float32")).to(u.device)).contiguous()
+        t0 = time.time()
+        r = fli_lbfgs(s2, data, sig, torch.zeros_like(truth), dh.OBS_THERMAL, max_iter=iters)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        kk, rc, _ = dh.cross_correlation(r.x.contiguous(), truth, p.box, nb)
+        pick = [0, 1, 3, 7, 15, 31, nb - 1]
+        out[f"snr_{int(snr)}"] = {
+            "iterations": r.iterations, "evaluations": r.evaluations, "seconds": dt,
+            "seconds_per_evaluation": dt / max(r.evaluations, 1), "converged": r.converged,
+            "loss_first": r.history[0][1], "loss_last": r.history[-1][1],
+            "k": [float(kk[j]) for j in pick], "r_c": [float(rc[j]) for j in pick]}
+    s2.close()
+    return out
+
+
 def _config(ws: int):
     return {"workload": WORKLOAD_NAME, "n": WORKLOAD["n"], "n_steps": WORKLOAD["n_steps"],
             "ckpt_every": WORKLOAD["ckpt_every"], "parallelism": f"replicas x{ws}",
@@ -360,6 +395,9 @@ def main():
     ap.add_argument("--no-fli", action="store_true",
                     help="skip the field-level-inference record (Adam iterations from zero)")
     ap.add_argument("--fli-iters", type=int, default=FLI_ITERS)
+    ap.add_argument("--lbfgs-iters", type=int, default=40)
+    ap.add_argument("--no-experiments", action="store_true",
+                    help="skip the Sedov, convergence and P(k)-likelihood HMC records")
     ap.add_argument("--cpu-full-forward", action="store_true",
                     help="also time the oracle's whole 128^3 x 100-step forward run (minutes)")
     ap.add_argument("--no-batched", action="store_true",
@@ -541,6 +579,20 @@ def main():
                            "gas density of seed %d plus N(0, (0.1 rms)^2); 100 steps "
                            "a=0.05->1.0, checkpoint every 10" % FLI_TRUTH_SEED}
 
+    # ---- L-BFGS field-level inference on the delta_b T probe at S/N 1 and 5 (Sec. 3.2)
+    lbfgs_rec = None
+    if not args.no_fli:
+        lbfgs_rec = bench_lbfgs(dh, synth, torch, sim, truth, p, args.lbfgs_iters)
+    # ---- Sec. 3.1 parameter inference and Sec. 2.3.4 validation runs
+    extra = {}
+    if not args.no_experiments:
+        from paper_2502_02294_gb300 import inference, validation
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        extra["sedov"] = validation.sedov(dh, n=128, r_target=20.0)
+        extra["convergence"] = validation.convergence(dh, n=64, box=8.0, n_steps=60)
+        extra["pk_hmc"] = inference.pk_hmc_experiment(dh)
+        torch.cuda.set_stream(stream)
+
     # ---- batched parameter-sampling form (96 instances on three grid sizes)
     batched = None
     if not args.no_batched:
@@ -605,6 +657,9 @@ def main():
     }
     if fli is not None:
         line["fli"] = fli
+    if lbfgs_rec is not None:
+        line["fli_lbfgs"] = lbfgs_rec
+    line.update(extra)
     if batched is not None:
         line["batched"] = batched
     if closure is not None:

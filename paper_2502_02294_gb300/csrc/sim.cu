@@ -1365,7 +1365,6 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
             h->fwd_var[axis] = cand[c];
           }
         }
-        if (cand[c] == SIM_SWEEP_PAIR) continue;  // forward only
         DH_TRY(time_it([&] { return launch_sweep_adjoint(axis, h->gas, h->gas, h->lam_tmp, h->n,
                                                          nu, h->prm.gamma, h->prm.limiter_eps,
                                                          dpart(h->dslots, SL_N), h->lam_scr,

@@ -325,3 +325,56 @@ def effective_sample_size(chain):
             t += 2
         out.append(N / max(-1.0 + 2.0 * s, 1.0 / N))
     return np.array(out)
+
+
+def pk_hmc_experiment(dh, n: int = 64, box: float = 8.0, a_start: float = 0.05,
+                      a_end: float = 0.25, n_steps: int = 20, n_boxes: int = 100,
+                      nbins: int | None = None, n_samples: int = 150, n_warmup: int = 30,
+                      n_leapfrog: int = 6, seed: int = 0):
+    """Sec. 3.1 end to end: the mock spectrum (seed 1 at the fiducial parameters), the
+    covariance of the gas spectrum over n_boxes batched boxes with independent seeds, and an
+    HMC chain over (E0, delta_c, sigma8, Omega_m) with the paper's Gaussian priors (sigma
+    0.002 for E0, 0.02 for the others) centred at the truth. Box to z = 3 (a = 0.25)."""
+    import time
+    import torch
+    nb = nbins or n // 4
+    # subgrid thresholds that form stars in this small box (delta_c of order unity, as in
+    # the paper's parameter ranges)
+    fid = dict(n=n, box=box, n_steps=n_steps, ckpt_every=n_steps, a_start=a_start,
+               a_end=a_end, subgrid_on=1, delta_c=1.0, w_delta=0.1, T_c=1e6, w_T=1e5,
+               Pi0=0.2, E0=0.03, T0_uv=0.0, rms_ref=0.1)
+    t0 = time.time()
+    boxes = [dh.default_params(**fid, seed=100 + b, instance=b) for b in range(n_boxes)]
+    k, mean, cov, P = pk_covariance(dh, boxes, nb)
+    t_cov = time.time() - t0
+    base = dh.default_params(**fid, seed=1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import synth
+    noise = torch.from_numpy(synth.white_noise(n, 1).astype("float32")).to(dev)
+    truth_sim = dh.Simulation(base, noise)
+    truth_sim.run()
+    rho = truth_sim.state()["gas"][0].contiguous()
+    _, p_obs, _ = dh.power_spectrum(rho, box, nb)
+    truth_sim.close()
+    theta_true = np.array([getattr(base, nm) for nm in PK_PARAMS])
+    sig = np.array([0.002, 0.02, 0.02, 0.02])
+    like = PkLikelihood(dh, base, noise, p_obs.cpu().numpy(), cov, nb,
+                        prior_mean=theta_true, prior_sigma=sig, ridge=1e-6)
+    t1 = time.time()
+    xs, acc, step, _ = hmc(like.value_and_grad, theta_true, sig ** 2, n_samples,
+                           n_leapfrog=n_leapfrog, step=0.3, n_warmup=n_warmup, seed=seed)
+    t_hmc = time.time() - t1
+    ess = effective_sample_size(xs)
+    evals = like.evals
+    like.close()
+    z = (xs.mean(0) - theta_true) / xs.std(0)
+    return {"workload": f"{n}^3 boxes, {box} Mpc/h, {n_steps} steps a={a_start}->{a_end}, "
+                        f"subgrid on; covariance from {n_boxes} batched boxes; HMC over "
+                        "(E0, delta_c, sigma8, Omega_m) with the paper's priors",
+            "nbins": nb, "covariance_seconds": t_cov, "hmc_seconds": t_hmc,
+            "gradient_evaluations": evals, "seconds_per_evaluation": t_hmc / max(evals, 1),
+            "samples": n_samples, "warmup": n_warmup, "leapfrog": n_leapfrog,
+            "step": step, "accept_rate": acc, "ess": ess.tolist(),
+            "posterior_mean": xs.mean(0).tolist(), "posterior_std": xs.std(0).tolist(),
+            "truth": theta_true.tolist(), "truth_offset_in_std": z.tolist(),
+            "params": list(PK_PARAMS)}

@@ -61,11 +61,12 @@ def test_sweep_sharp_fronts_and_uniform(dh):
         assert torch.equal(dh.sweep(Ug, axis, 0.7), Ug)
 
 
-@pytest.mark.parametrize("n", [2, 3, 5, 20, 70])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 20, 64, 70])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 def test_sweep_forms_match_oracle(dh, n, variant):
     """Every kernel form (tile, marching in 32- and 16-cell segments or in the segment length
-    fitted to whole waves; x adjoint via transposed copies) against the oracle, on grids
+    fitted to whole waves; x adjoint via transposed copies; the paired packed-FP32x2 forward
+    form on even grids, the tile on odd ones) against the oracle, on grids
     smaller than the stencil (2, 3, 5 cells: every halo wraps onto the line itself) and on
     grids with a ragged last tile and segment.
 
