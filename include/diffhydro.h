@@ -165,7 +165,7 @@ int32_t sim_batch_size(const sim_t* h);
  * GB300 launch shapes). DEFAULT: the built-in choice for the grid size; TILE: shared-memory
  * tile; MARCH32 / MARCH16: one thread marches a line segment of 32 / 16 cells; MARCH_FIT:
  * the same with the segment length that fits the launch to whole waves of resident blocks
- * (forward: y and z only, the forward x sweep always uses the tile; adjoint: every axis,
+ * (forward: y and z only, the forward x sweep then uses the tile; adjoint: every axis,
  * x on x <-> y transposed copies, two passes through a 5-field scratch); PAIR: below. */
 enum {
   SIM_SWEEP_DEFAULT = 0,
@@ -173,10 +173,10 @@ enum {
   SIM_SWEEP_MARCH32 = 2,
   SIM_SWEEP_MARCH16 = 3,
   SIM_SWEEP_MARCH_FIT = 4,
-  SIM_SWEEP_PAIR = 5  /* forward: y / z sweeps with even n, the fitted marching form on two
-                         adjacent lines per thread in packed FP32x2 arithmetic (the tile
-                         elsewhere); adjoint: the single-pass marching form (no scratch
-                         round trip; x on transposed copies)                              */
+  SIM_SWEEP_PAIR = 5  /* forward, n even: the fitted marching form on two adjacent lines per
+                         thread (x columns for y / z, y rows for x) in packed FP32x2
+                         arithmetic (the tile for odd n); adjoint: the single-pass
+                         marching form (no scratch round trip; x on transposed copies)    */
 };
 
 /* Set the variant of the forward (fwd[3], per axis) and adjoint (adj[3]) sweeps of the

@@ -286,8 +286,25 @@ __device__ __forceinline__ float2 vanleer2(float2 a, float2 b, float eps) {
   return make_float2(ab.x > 0.0f ? t.x : 0.0f, ab.y > 0.0f ? t.y : 0.0f);
 }
 
-// AXIS 1 or 2; n even (8-byte aligned pairs). Thread: lines w, w + 1 (w even), segment of L
-// output cells from s0 along the sweep axis.
+// AXIS 1 or 2: lines w, w + 1 are adjacent x columns (one 8-byte load per field, n even).
+// AXIS 0: lines w, w + 1 are adjacent y rows of one z plane, read with two 4-byte loads a
+// field (a warp's loads touch 64 rows; each 32-byte sector serves 8 consecutive cells of the
+// march from L1). Thread: lines w, w + 1 (w even), a segment of L output cells from s0.
+template <int AXIS>
+__device__ __forceinline__ float2 ld_pair(const float* __restrict__ p, long long o, int n) {
+  if (AXIS == 0) return make_float2(__ldg(p + o), __ldg(p + o + n));
+  return __ldg(reinterpret_cast<const float2*>(p + o));
+}
+
+template <int AXIS>
+__device__ __forceinline__ void st_pair(float* __restrict__ p, long long o, int n, float2 v) {
+  if (AXIS == 0) {
+    p[o] = v.x;
+    p[o + n] = v.y;
+  } else {
+    *reinterpret_cast<float2*>(p + o) = v;
+  }
+}
 template <int AXIS, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
@@ -321,7 +338,7 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
     float2 u[5];
     const long long o = goff<AXIS>(j, w, t, n);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) u[k] = __ldg(reinterpret_cast<const float2*>(uin + k * N3 + o));
+    for (int k = 0; k < 5; ++k) u[k] = ld_pair<AXIS>(uin + k * N3, o, n);
     float2 FR[5], FL[5];
     split_flux2(u, F, gam, FR, FL);
     float2 f1[5], uh[5];
@@ -341,8 +358,7 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
       const float2 fr = add2(R1[k], vanleer2(dRa[k], dRb[k], eps));
       const float2 fl = sub2(L1[k], vanleer2(dLa[k], dLb, eps));
       const float2 F2 = sub2(fr, fl);                    // face (j-3)+1/2
-      if (store)
-        *reinterpret_cast<float2*>(uout + k * N3 + oo) = fma2(mnu, sub2(F2, F2m[k]), Ua[k]);
+      if (store) st_pair<AXIS>(uout + k * N3, oo, n, fma2(mnu, sub2(F2, F2m[k]), Ua[k]));
       F2m[k] = F2;
       dRa[k] = dRb[k];
       dRb[k] = mul2(sub2(FRh[k], R2[k]), pk(0.5f));
@@ -898,7 +914,7 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
 // call in the benchmark pass against 156 us with 16-cell segments). sim_autotune times the
 // variants per handle.
 static int pick_fwd(int axis, int n, int variant) {
-  if (axis == 0) return SIM_SWEEP_TILE;
+  if (axis == 0) return variant == SIM_SWEEP_PAIR ? SIM_SWEEP_PAIR : SIM_SWEEP_TILE;
   if (variant != SIM_SWEEP_DEFAULT) return variant;
   return n >= 192 ? SIM_SWEEP_MARCH32 : SIM_SWEEP_TILE;
 }
@@ -973,11 +989,10 @@ static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, 
 template <int AXIS, int MINB>
 static sim_status launch_march2_mb(const float* uin, float* uout, int n, SArg nu, float gam,
                                    float eps, int B, cudaStream_t st) {
-  constexpr int A = AXIS == 0 ? 1 : AXIS;
   const int threads = n / 2 >= 128 ? 128 : (n / 2 >= 64 ? 64 : 32);
-  const int L = fit_segment(sweep_march2_kernel<A, MINB>, n, B, 6, n / 2, threads);
+  const int L = fit_segment(sweep_march2_kernel<AXIS, MINB>, n, B, 6, n / 2, threads);
   dim3 grid(cdiv(n / 2, threads), n * B, cdiv(n, L));
-  sweep_march2_kernel<A, MINB><<<grid, threads, 0, st>>>(uin, uout, n, nu, gam, eps, L);
+  sweep_march2_kernel<AXIS, MINB><<<grid, threads, 0, st>>>(uin, uout, n, nu, gam, eps, L);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -995,8 +1010,8 @@ template <int AXIS>
 static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, float gam,
                                  float eps, int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  // the paired form needs two adjacent x columns per thread: y / z sweeps, n even
-  if (AXIS != 0 && variant == SIM_SWEEP_PAIR && n % 2 == 0 &&
+  // the paired form needs two adjacent lines per thread (n even; 8-byte pairs for y / z)
+  if (variant == SIM_SWEEP_PAIR && n % 2 == 0 &&
       ((reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(uout)) % 8) == 0)
     return launch_march2_t<AXIS>(uin, uout, n, nu, gam, eps, B, st);
   if (AXIS != 0 && variant != SIM_SWEEP_TILE && variant != SIM_SWEEP_PAIR)
@@ -1253,11 +1268,14 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
     return SIM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  // the tile and the single-pass y / z forms need no scratch; the others 20 n^3 floats
+  const int v = variant == SIM_SWEEP_DEFAULT ? SIM_SWEEP_MARCH_FIT : variant;
+  const bool need = !(v == SIM_SWEEP_TILE || (v == SIM_SWEEP_PAIR && axis != 0));
   float* scratch = nullptr;
-  DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 20ull * n * n * n * sizeof(float), st));
+  if (need) DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 20ull * n * n * n * sizeof(float), st));
   const sim_status r =
       dh::launch_sweep_adjoint(axis, u_in, lam_out, lam_in, n, dh::sarg((float)nu), gamma,
                                limiter_eps, dh::dpart(dnu), scratch, 1, variant, st);
-  cudaFreeAsync(scratch, st);
+  if (scratch) cudaFreeAsync(scratch, st);
   return r;
 }
