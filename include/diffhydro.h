@@ -173,10 +173,9 @@ enum {
   SIM_SWEEP_MARCH32 = 2,
   SIM_SWEEP_MARCH16 = 3,
   SIM_SWEEP_MARCH_FIT = 4,
-  SIM_SWEEP_PAIR = 5  /* forward, n even: the fitted marching form on two adjacent lines per
-                         thread (x columns for y / z, y rows for x) in packed FP32x2
-                         arithmetic (the tile for odd n); adjoint: the single-pass
-                         marching form (no scratch round trip; x on transposed copies)    */
+  SIM_SWEEP_PAIR = 5  /* forward y / z sweeps with even n: the fitted marching form on two
+                         adjacent x columns per thread in packed FP32x2 arithmetic (the
+                         tile for x and for odd n); adjoint: as MARCH_FIT                 */
 };
 
 /* Set the variant of the forward (fwd[3], per axis) and adjoint (adj[3]) sweeps of the

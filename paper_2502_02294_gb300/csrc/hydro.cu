@@ -286,25 +286,10 @@ __device__ __forceinline__ float2 vanleer2(float2 a, float2 b, float eps) {
   return make_float2(ab.x > 0.0f ? t.x : 0.0f, ab.y > 0.0f ? t.y : 0.0f);
 }
 
-// AXIS 1 or 2: lines w, w + 1 are adjacent x columns (one 8-byte load per field, n even).
-// AXIS 0: lines w, w + 1 are adjacent y rows of one z plane, read with two 4-byte loads a
-// field (a warp's loads touch 64 rows; each 32-byte sector serves 8 consecutive cells of the
-// march from L1). Thread: lines w, w + 1 (w even), a segment of L output cells from s0.
-template <int AXIS>
-__device__ __forceinline__ float2 ld_pair(const float* __restrict__ p, long long o, int n) {
-  if (AXIS == 0) return make_float2(__ldg(p + o), __ldg(p + o + n));
-  return __ldg(reinterpret_cast<const float2*>(p + o));
-}
-
-template <int AXIS>
-__device__ __forceinline__ void st_pair(float* __restrict__ p, long long o, int n, float2 v) {
-  if (AXIS == 0) {
-    p[o] = v.x;
-    p[o + n] = v.y;
-  } else {
-    *reinterpret_cast<float2*>(p + o) = v;
-  }
-}
+// AXIS 1 or 2; n even (8-byte aligned pairs). Thread: lines w, w + 1 (adjacent x columns,
+// w even), a segment of L output cells from s0 along the sweep axis. (An x sweep on pairs of
+// y rows measured 2.2x slower than the tile at 128^3 and 6.7x at 256^3: its loads touch 64
+// rows per warp and thrash L1.)
 template <int AXIS, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
@@ -338,7 +323,7 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
     float2 u[5];
     const long long o = goff<AXIS>(j, w, t, n);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) u[k] = ld_pair<AXIS>(uin + k * N3, o, n);
+    for (int k = 0; k < 5; ++k) u[k] = __ldg(reinterpret_cast<const float2*>(uin + k * N3 + o));
     float2 FR[5], FL[5];
     split_flux2(u, F, gam, FR, FL);
     float2 f1[5], uh[5];
@@ -358,7 +343,8 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
       const float2 fr = add2(R1[k], vanleer2(dRa[k], dRb[k], eps));
       const float2 fl = sub2(L1[k], vanleer2(dLa[k], dLb, eps));
       const float2 F2 = sub2(fr, fl);                    // face (j-3)+1/2
-      if (store) st_pair<AXIS>(uout + k * N3, oo, n, fma2(mnu, sub2(F2, F2m[k]), Ua[k]));
+      if (store)
+        *reinterpret_cast<float2*>(uout + k * N3 + oo) = fma2(mnu, sub2(F2, F2m[k]), Ua[k]);
       F2m[k] = F2;
       dRa[k] = dRb[k];
       dRb[k] = mul2(sub2(FRh[k], R2[k]), pk(0.5f));
@@ -529,155 +515,6 @@ sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ 
       f1m[k] = f1[k];
     }
     j = jn;
-  }
-  if (dnu) {
-    if (!live) dnu_acc = 0.0f;
-    block_sum_atomic(dnu_acc, dnu);
-  }
-}
-
-// Single-pass form: the march above, started one cell earlier and ended one later so that
-// lamUh is known on [s0 - 1, s0 + L], finishes cell k = i - 5 in the same iteration in which
-// lamUh_{k+1} completes: lam_in_k = lam_out_k + lamUh_k + VJP(U_k; nu/2 (lamUh_{k+1} -
-// lamUh_k), -nu/2 (lamUh_k - lamUh_{k-1})). U_k and lam_out_k are read again (loaded five
-// iterations earlier by this thread, so from L1) instead of held in more registers; the
-// 5-field scratch of the two-pass form and its write and re-read are gone.
-template <int AXIS, int FC = 1 + AXIS>
-__global__ void __launch_bounds__(128, 3)
-sweep_adj_fused_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
-                       float* __restrict__ lin, int n, SArg nua, float gam, float eps,
-                       DPart dnub, int L) {
-  constexpr int F = FC;
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y / n;
-  const int t3 = blockIdx.y - b * n;
-  const int s0 = blockIdx.z * L;
-  const bool live = w < n;
-  const long long N3 = (long long)n * n * n;
-  uin += (size_t)b * 5 * N3;
-  lout += (size_t)b * 5 * N3;
-  lin += (size_t)b * 5 * N3;
-  const float nu = nua.at(b);
-  double* dnu = dnub.at(b);
-  const float hnu = 0.5f * nu, inv_nu = 1.0f / nu;
-  float Uc[5], FRp[5], f1m[5];
-  float R0[5], R1[5], R2[5];
-  float L0[5], L1[5];
-  float H0[5], H1[5], H2[5];
-  float D0[5], D1[5], D2[5];
-  float M0[5], M1[5], M2[5];
-  float aR0[5], aR1[5], aR2[5];
-  float aL0[5], aL1[5], aL2[5], aL3[5];
-  float Pm[5], Pc[5];  // lamUh_{k-1}, lamUh_k of the cell k being finished next
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const float init = (k == 0 || k == 4) ? 1.0f : 0.0f;
-    Uc[k] = H0[k] = H1[k] = H2[k] = init;
-    FRp[k] = f1m[k] = R0[k] = R1[k] = R2[k] = L0[k] = L1[k] = 0.0f;
-    D0[k] = D1[k] = D2[k] = M0[k] = M1[k] = M2[k] = 0.0f;
-    aR0[k] = aR1[k] = aR2[k] = aL0[k] = aL1[k] = aL2[k] = aL3[k] = 0.0f;
-    Pm[k] = Pc[k] = 0.0f;
-  }
-  float dnu_acc = 0.0f;
-  const int ww = live ? w : 0;
-  int j = wrap_periodic(s0 - 6, n);
-#pragma unroll 1
-  for (int it = 0; it < L + 11; ++it) {
-    float u[5], lo[5];
-    {
-      const long long o = goff<AXIS>(j, ww, t3, n);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        u[k] = __ldg(uin + k * N3 + o);
-        lo[k] = __ldg(lout + k * N3 + o);
-      }
-    }
-    float FR[5], FL[5];
-    split_flux(u, F, gam, FR, FL);
-    float f1[5], dF[5], uh[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      f1[k] = FRp[k] - FL[k];
-      dF[k] = f1[k] - f1m[k];
-      uh[k] = Uc[k] - hnu * dF[k];
-    }
-    float FRh[5], FLh[5];
-    split_flux(uh, F, gam, FRh, FLh);
-    const int jt = s0 + it - 9;  // unwrapped index of face cell t (face t + 1/2)
-    const bool face_in = (jt >= s0) && (jt < s0 + L) && (jt < n);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const float lf = nu * (M1[k] - M0[k]);
-      const float aR = 0.5f * (R1[k] - R0[k]), bR = 0.5f * (R2[k] - R1[k]);
-      const float aL = 0.5f * (L1[k] - L0[k]), bL = 0.5f * (FLh[k] - L1[k]);
-      float pR, daR, dbR, pL, daL, dbL;
-      vanleer_vg(aR, bR, eps, pR, daR, dbR);
-      vanleer_vg(aL, bL, eps, pL, daL, dbL);
-      const float A = 0.5f * lf * daR, Bq = 0.5f * lf * dbR;
-      const float C = 0.5f * lf * daL, D = 0.5f * lf * dbL;
-      aR0[k] -= A;
-      aR1[k] += lf + A - Bq;
-      aR2[k] += Bq;
-      aL1[k] -= C;
-      aL2[k] += -lf + C - D;
-      aL3[k] += D;
-      if (face_in) dnu_acc += ((R1[k] + pR) - (L1[k] - pL)) * lf * inv_nu;
-    }
-    // cell i-4 (unwrapped jc) has its lamUh; the cell before it, kf = jc - 1, is finished
-    const int jc = s0 + it - 10;
-    float luh[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (it >= 9) {
-      split_flux_vjp(H0, F, gam, aR0, aL0, luh);
-      if (jc >= s0 && jc < s0 + L && jc < n) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) dnu_acc -= 0.5f * luh[k] * D0[k];
-      }
-    }
-    const int kf = jc - 1;
-    if (it >= 11 && live && kf < n && kf < s0 + L) {
-      const long long of = goff<AXIS>(kf, w, t3, n);
-      float uf[5], lR[5], lL[5], lu[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        uf[k] = __ldg(uin + k * N3 + of);
-        lu[k] = __ldg(lout + k * N3 + of) + Pc[k];
-        lR[k] = hnu * (luh[k] - Pc[k]);
-        lL[k] = -hnu * (Pc[k] - Pm[k]);
-      }
-      split_flux_vjp(uf, F, gam, lR, lL, lu);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) lin[k * N3 + of] = lu[k];
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      Pm[k] = Pc[k];
-      Pc[k] = luh[k];
-      aR0[k] = aR1[k];
-      aR1[k] = aR2[k];
-      aR2[k] = 0.0f;
-      aL0[k] = aL1[k];
-      aL1[k] = aL2[k];
-      aL2[k] = aL3[k];
-      aL3[k] = 0.0f;
-      H0[k] = H1[k];
-      H1[k] = H2[k];
-      H2[k] = uh[k];
-      D0[k] = D1[k];
-      D1[k] = D2[k];
-      D2[k] = dF[k];
-      R0[k] = R1[k];
-      R1[k] = R2[k];
-      R2[k] = FRh[k];
-      L0[k] = L1[k];
-      L1[k] = FLh[k];
-      M0[k] = M1[k];
-      M1[k] = M2[k];
-      M2[k] = lo[k];
-      Uc[k] = u[k];
-      FRp[k] = FR[k];
-      f1m[k] = f1[k];
-    }
-    j = (j + 1 == n) ? 0 : j + 1;
   }
   if (dnu) {
     if (!live) dnu_acc = 0.0f;
@@ -914,14 +751,15 @@ sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
 // call in the benchmark pass against 156 us with 16-cell segments). sim_autotune times the
 // variants per handle.
 static int pick_fwd(int axis, int n, int variant) {
-  if (axis == 0) return variant == SIM_SWEEP_PAIR ? SIM_SWEEP_PAIR : SIM_SWEEP_TILE;
+  if (axis == 0) return SIM_SWEEP_TILE;
   if (variant != SIM_SWEEP_DEFAULT) return variant;
   return n >= 192 ? SIM_SWEEP_MARCH32 : SIM_SWEEP_TILE;
 }
 
 static int pick_adj(int axis, int variant) {
   (void)axis;
-  return variant != SIM_SWEEP_DEFAULT ? variant : SIM_SWEEP_MARCH_FIT;
+  // the paired form is forward only; its adjoint is the fitted marching pair
+  return (variant != SIM_SWEEP_DEFAULT && variant != SIM_SWEEP_PAIR) ? variant : SIM_SWEEP_MARCH_FIT;
 }
 
 // Segment length of a marching kernel for an n^3 grid of B instances: the number k of
@@ -1010,8 +848,8 @@ template <int AXIS>
 static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, float gam,
                                  float eps, int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  // the paired form needs two adjacent lines per thread (n even; 8-byte pairs for y / z)
-  if (variant == SIM_SWEEP_PAIR && n % 2 == 0 &&
+  // the paired form needs two adjacent x columns per thread: y / z sweeps, n even
+  if (AXIS != 0 && variant == SIM_SWEEP_PAIR && n % 2 == 0 &&
       ((reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(uout)) % 8) == 0)
     return launch_march2_t<AXIS>(uin, uout, n, nu, gam, eps, B, st);
   if (AXIS != 0 && variant != SIM_SWEEP_TILE && variant != SIM_SWEEP_PAIR)
@@ -1129,39 +967,11 @@ static sim_status launch_adj_x_transposed(const float* uin, const float* lout, f
   return launch_transpose_xy(it, lin, 5 * B, nullptr, nullptr, 0, n, st);
 }
 
-// The single-pass form: y / z directly, x on x <-> y transposed copies (scratch: 3 x 5 n^3
-// floats per instance for the two inputs and the result).
-template <int AXIS>
-static sim_status launch_adj_fused_t(const float* uin, const float* lout, float* lin, int n,
-                                     SArg nu, float gam, float eps, DPart dnu, float* scratch,
-                                     int B, cudaStream_t st) {
-  constexpr int A = AXIS == 0 ? 1 : AXIS, FCOMP = AXIS == 0 ? 1 : 1 + AXIS;
-  const int L = fit_segment(sweep_adj_fused_kernel<A, FCOMP>, n, B, 11);
-  dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
-  if (AXIS != 0) {
-    sweep_adj_fused_kernel<A, FCOMP><<<g1, 128, 0, st>>>(uin, lout, lin, n, nu, gam, eps, dnu, L);
-    DH_LAUNCH_CHECK();
-    return SIM_OK;
-  }
-  if (!scratch) {
-    set_error("internal: the transposed x adjoint needs a 20 n^3 scratch buffer per instance");
-    return SIM_EINVAL;
-  }
-  const size_t F5 = (size_t)5 * n * n * n * B;
-  float *ut = scratch, *lt = scratch + F5, *it = scratch + 2 * F5;
-  DH_TRY(launch_transpose_xy(uin, ut, 5 * B, lout, lt, 5 * B, n, st));
-  sweep_adj_fused_kernel<A, FCOMP><<<g1, 128, 0, st>>>(ut, lt, it, n, nu, gam, eps, dnu, L);
-  DH_LAUNCH_CHECK();
-  return launch_transpose_xy(it, lin, 5 * B, nullptr, nullptr, 0, n, st);
-}
-
 template <int AXIS>
 static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float* lin, int n,
                                      SArg nu, float gam, float eps, DPart dnu, float* scratch,
                                      int B, int variant, cudaStream_t st) {
   using C = SweepCfg<AXIS>;
-  if (variant == SIM_SWEEP_PAIR)
-    return launch_adj_fused_t<AXIS>(uin, lout, lin, n, nu, gam, eps, dnu, scratch, B, st);
   if (variant != SIM_SWEEP_TILE) {
     const int L = variant == SIM_SWEEP_MARCH_FIT
                       ? fit_segment(sweep_adj_march_kernel<AXIS == 0 ? 1 : AXIS, AXIS == 0 ? 1 : 1 + AXIS>,
@@ -1268,9 +1078,8 @@ extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out,
     return SIM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  // the tile and the single-pass y / z forms need no scratch; the others 20 n^3 floats
-  const int v = variant == SIM_SWEEP_DEFAULT ? SIM_SWEEP_MARCH_FIT : variant;
-  const bool need = !(v == SIM_SWEEP_TILE || (v == SIM_SWEEP_PAIR && axis != 0));
+  // the tile needs no scratch; the marching pairs 20 n^3 floats
+  const bool need = variant != SIM_SWEEP_TILE;
   float* scratch = nullptr;
   if (need) DH_CUDA_TRY(cudaMallocAsync((void**)&scratch, 20ull * n * n * n * sizeof(float), st));
   const sim_status r =

@@ -1355,9 +1355,8 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
       float bf = 1e30f, ba = 1e30f;
       for (int c = 0; c < 5; ++c) {
         float t = 0.0f;
-        // forward x: the tile or the paired form; the paired form needs an even n
-        if ((axis != 0 || c == 0 || cand[c] == SIM_SWEEP_PAIR) &&
-            (cand[c] != SIM_SWEEP_PAIR || h->n % 2 == 0)) {
+        // forward x: the tile only; the paired form needs an even n
+        if ((axis != 0 || c == 0) && (cand[c] != SIM_SWEEP_PAIR || h->n % 2 == 0)) {
           DH_TRY(time_it([&] { return launch_sweep(axis, h->gas, h->w_gas2, h->n, nu,
                                                    h->prm.gamma, h->prm.limiter_eps, h->B,
                                                    cand[c], st); }, &t));
@@ -1366,6 +1365,7 @@ sim_status sim_autotune(sim_t* h, int32_t reps, int32_t* fwd_out, int32_t* adj_o
             h->fwd_var[axis] = cand[c];
           }
         }
+        if (cand[c] == SIM_SWEEP_PAIR) continue;  // forward only
         DH_TRY(time_it([&] { return launch_sweep_adjoint(axis, h->gas, h->gas, h->lam_tmp, h->n,
                                                          nu, h->prm.gamma, h->prm.limiter_eps,
                                                          dpart(h->dslots, SL_N), h->lam_scr,

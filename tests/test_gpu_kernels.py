@@ -66,7 +66,7 @@ def test_sweep_sharp_fronts_and_uniform(dh):
 def test_sweep_forms_match_oracle(dh, n, variant):
     """Every kernel form (tile, marching in 32- and 16-cell segments or in the segment length
     fitted to whole waves; x adjoint via transposed copies; the paired packed-FP32x2 forward
-    form on even grids, the tile on odd ones) against the oracle, on grids
+    form for y / z on even grids) against the oracle, on grids
     smaller than the stencil (2, 3, 5 cells: every halo wraps onto the line itself) and on
     grids with a ragged last tile and segment.
 
