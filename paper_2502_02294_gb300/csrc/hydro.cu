@@ -575,6 +575,103 @@ sweep_adj_final_kernel(const float* __restrict__ uin, const float* __restrict__ 
   for (int k = 0; k < 5; ++k) lin[k * N3 + o] = lu[k];
 }
 
+// Pass 2 on two adjacent x cells per thread (n even), in packed FP32x2 arithmetic: the same
+// operations as split_flux_vjp and sweep_adj_final_kernel, for the pair.
+__device__ __forceinline__ void split_flux_vjp2(const float2 u[5], int f, float gam,
+                                                const float2 lR[5], const float2 lL[5],
+                                                float2 lu[5]) {
+  const float2 inv = make_float2(fast_rcp(u[0].x), fast_rcp(u[0].y));
+  const float2 v = mul2(u[f], inv);
+  const float2 m2 = fma2(u[1], u[1], fma2(u[2], u[2], mul2(u[3], u[3])));
+  const float2 hm2inv = mul2(mul2(m2, inv), pk(0.5f));
+  const float2 P = mul2(pk(gam - 1.0f), sub2(u[4], hm2inv));
+  const float2 cs2 = mul2(mul2(P, inv), pk(gam));
+  const float rx = cs2.x > 0.0f ? rsqrtf(cs2.x) : 0.0f;
+  const float ry = cs2.y > 0.0f ? rsqrtf(cs2.y) : 0.0f;
+  const float2 rcs = make_float2(rx, ry);
+  const float2 cs = mul2(cs2, rcs);
+  const float2 c = add2(make_float2(fabsf(v.x), fabsf(v.y)), cs);
+  float2 sig[5], del[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    sig[k] = mul2(add2(lR[k], lL[k]), pk(0.5f));
+    del[k] = mul2(sub2(lR[k], lL[k]), pk(0.5f));
+  }
+  float2 lc = pk(0.0f);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    lu[k] = fma2(c, sig[k], lu[k]);
+    lc = fma2(sig[k], u[k], lc);
+  }
+  float2 lv = pk(0.0f), lP = del[f], lrho = pk(0.0f);
+  lu[f] = add2(lu[f], del[0]);
+#pragma unroll
+  for (int k = 1; k <= 3; ++k) {
+    lu[k] = fma2(del[k], v, lu[k]);
+    lv = fma2(del[k], u[k], lv);
+  }
+  lu[4] = fma2(del[4], v, lu[4]);
+  lP = fma2(del[4], v, lP);
+  lv = fma2(del[4], add2(u[4], P), lv);
+  const float2 sgn = make_float2((float)((v.x > 0.0f) - (v.x < 0.0f)), (float)((v.y > 0.0f) - (v.y < 0.0f)));
+  lv = fma2(lc, sgn, lv);
+  // where cs2 <= 0: rcs = 0 and cs = 0, so both terms below vanish, as in split_flux_vjp
+  lP = fma2(mul2(lc, pk(0.5f * gam)), mul2(rcs, inv), lP);
+  lrho = fma2(mul2(lc, pk(-0.5f)), mul2(cs, inv), lrho);
+  const float2 gP = mul2(pk(gam - 1.0f), lP);
+  lu[4] = add2(lu[4], gP);
+  const float2 gPinv = mul2(gP, inv);
+#pragma unroll
+  for (int k = 1; k <= 3; ++k) lu[k] = fma2(mul2(gPinv, pk(-1.0f)), u[k], lu[k]);
+  lrho = fma2(gPinv, hm2inv, lrho);
+  lu[f] = fma2(lv, inv, lu[f]);
+  lrho = fma2(mul2(lv, pk(-1.0f)), mul2(v, inv), lrho);
+  lu[0] = add2(lu[0], lrho);
+}
+
+// grid (cdiv(n / 2, 128), n, n B); thread: cells x = 2 t, 2 t + 1 of row (y, z)
+template <int AXIS, int FC = 1 + AXIS>
+__global__ void __launch_bounds__(128)
+sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
+                        const float* __restrict__ luh, float* __restrict__ lin, int n,
+                        SArg nua, float gam) {
+  constexpr int F = FC;
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int b = blockIdx.z / n;
+  const int y = blockIdx.y, z = blockIdx.z - b * n;
+  if (x >= n) return;
+  const long long N3 = (long long)n * n * n;
+  uin += (size_t)b * 5 * N3;
+  lout += (size_t)b * 5 * N3;
+  luh += (size_t)b * 5 * N3;
+  lin += (size_t)b * 5 * N3;
+  const float nu = nua.at(b);
+  const long long o = ((long long)z * n + y) * n + x;
+  long long om, op;  // neighbours along the sweep axis (y or z), periodic
+  if (AXIS == 1) {
+    om = o + (long long)((y == 0 ? n - 1 : y - 1) - y) * n;
+    op = o + (long long)((y + 1 == n ? 0 : y + 1) - y) * n;
+  } else {
+    om = o + (long long)((z == 0 ? n - 1 : z - 1) - z) * n * n;
+    op = o + (long long)((z + 1 == n ? 0 : z + 1) - z) * n * n;
+  }
+  const float2 hnu = pk(0.5f * nu), mhnu = pk(-0.5f * nu);
+  float2 u[5], lR[5], lL[5], lu[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    u[k] = __ldg(reinterpret_cast<const float2*>(uin + k * N3 + o));
+    const float2 h0 = __ldg(reinterpret_cast<const float2*>(luh + k * N3 + o));
+    const float2 hm = __ldg(reinterpret_cast<const float2*>(luh + k * N3 + om));
+    const float2 hp = __ldg(reinterpret_cast<const float2*>(luh + k * N3 + op));
+    lR[k] = mul2(hnu, sub2(hp, h0));
+    lL[k] = mul2(mhnu, sub2(h0, hm));
+    lu[k] = add2(__ldg(reinterpret_cast<const float2*>(lout + k * N3 + o)), h0);
+  }
+  split_flux_vjp2(u, F, gam, lR, lL, lu);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) *reinterpret_cast<float2*>(lin + k * N3 + o) = lu[k];
+}
+
 // ------------------------------------------------------------------------- adjoint
 // lam_in_k = lam_out_k + lamUh_k + VJP_{F^R,F^L}(U_k; lamF^R_k, lamF^L_k), with
 // lamF^R_k = nu/2 (lamUh_{k+1} - lamUh_k), lamF^L_k = -nu/2 (lamUh_k - lamUh_{k-1}), and
@@ -933,6 +1030,24 @@ static sim_status launch_transpose_xy(const float* in0, float* out0, int nf0, co
   return SIM_OK;
 }
 
+// Pass 2 of the marching adjoint: the paired packed form when n is even and the arrays are
+// 8-byte aligned, else one cell per thread.
+template <int AXIS, int FC>
+static sim_status launch_adj_final(const float* uin, const float* lout, const float* luh,
+                                   float* lin, int n, SArg nu, float gam, int B, cudaStream_t st) {
+  const uintptr_t al = reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(lout) |
+                       reinterpret_cast<uintptr_t>(luh) | reinterpret_cast<uintptr_t>(lin);
+  if (AXIS != 0 && n % 2 == 0 && al % 8 == 0) {  // x runs as AXIS 1 on transposed copies
+    dim3 g(cdiv(n / 2, 128), n, n * B);
+    sweep_adj_final2_kernel<AXIS, FC><<<g, 128, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
+  } else {
+    dim3 g(cdiv(n, 256), n, n * B);
+    sweep_adj_final_kernel<AXIS, FC><<<g, 256, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
+  }
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
 template <int AXIS>
 static sim_status launch_adj_march_t(const float* uin, const float* lout, float* lin, int n,
                                      SArg nu, float gam, float eps, DPart dnu, float* scratch,
@@ -944,10 +1059,7 @@ static sim_status launch_adj_march_t(const float* uin, const float* lout, float*
   dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
   sweep_adj_march_kernel<AXIS><<<g1, 128, 0, st>>>(uin, lout, scratch, n, nu, gam, eps, dnu, L);
   DH_LAUNCH_CHECK();
-  dim3 g2(cdiv(n, 256), n, n * B);
-  sweep_adj_final_kernel<AXIS><<<g2, 256, 0, st>>>(uin, lout, scratch, lin, n, nu, gam);
-  DH_LAUNCH_CHECK();
-  return SIM_OK;
+  return launch_adj_final<AXIS, 1 + AXIS>(uin, lout, scratch, lin, n, nu, gam, B, st);
 }
 
 // The x adjoint as the y-marching pair on x <-> y transposed copies (momentum component 1
@@ -961,9 +1073,7 @@ static sim_status launch_adj_x_transposed(const float* uin, const float* lout, f
   dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
   sweep_adj_march_kernel<1, 1><<<g1, 128, 0, st>>>(ut, lt, luh, n, nu, gam, eps, dnu, L);
   DH_LAUNCH_CHECK();
-  dim3 g2(cdiv(n, 256), n, n * B);
-  sweep_adj_final_kernel<1, 1><<<g2, 256, 0, st>>>(ut, lt, luh, it, n, nu, gam);
-  DH_LAUNCH_CHECK();
+  DH_TRY((launch_adj_final<1, 1>(ut, lt, luh, it, n, nu, gam, B, st)));
   return launch_transpose_xy(it, lin, 5 * B, nullptr, nullptr, 0, n, st);
 }
 

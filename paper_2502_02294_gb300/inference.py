@@ -1,10 +1,10 @@
 """Inference drivers over the library's posterior and gradient entry points (Sec. 3).
 
 * ``lbfgs`` -- limited-memory BFGS (Nocedal & Wright, *Numerical Optimization*, 2nd ed.,
-  Algorithm 7.4 two-loop recursion, Algorithm 7.5 outer loop) with a backtracking line search
-  on the Armijo condition. The paper's field-level inference (Sec. 3.2) optimises the
-  white-noise amplitudes with L-BFGS keeping M = 8 pairs and stopping at a relative
-  tolerance of 1e-5. The algorithm is written over a small set of vector operations so that
+  Algorithm 7.4 two-loop recursion, Algorithm 7.5 outer loop) with an Armijo line search
+  (expanding on steepest-descent steps, backtracking otherwise). The paper's field-level
+  inference (Sec. 3.2) optimises the white-noise amplitudes with L-BFGS keeping M = 8 pairs
+  and a tolerance of 1e-5 (read here as the gradient norm relative to its initial value). The algorithm is written over a small set of vector operations so that
   the same code runs on device vectors (the library's ``sim_dot`` / ``sim_axpby`` kernels:
   the 2,097,152 amplitudes never leave the GPU; only scalars reach the host) and on numpy
   arrays (its CPU tests).
@@ -77,18 +77,27 @@ class LbfgsResult:
 
 
 def lbfgs(fun_grad, x0, ops, m: int = 8, max_iter: int = 100, rtol: float = 1e-5,
-          gtol: float = 0.0, c1: float = 1e-4, max_backtracks: int = 20, callback=None):
+          c1: float = 1e-4, max_backtracks: int = 30, max_expand: int = 40, callback=None):
     """Minimise f from x0. fun_grad(x) -> (f, g) with g a new vector; ops: NumpyOps or
-    DeviceOps. Stops when the relative decrease of f over an iteration falls below rtol,
-    when |g| <= gtol, or after max_iter iterations."""
+    DeviceOps. Stops when |g| <= rtol |g(x0)| (converged), when an iteration no longer lowers
+    f or the line search finds no Armijo step, or after max_iter iterations.
+
+    Line search: from the step 1 of the quasi-Newton direction (the first direction is the
+    steepest descent, whose scale is unknown: there the step starts at 1 / |g| and is doubled
+    while f keeps falling and the Armijo condition holds, so a badly scaled first step does
+    not stall the run), halved until the Armijo condition f(x + a d) <= f + c1 a g.d holds."""
     x = ops.copy(x0)
     f, g = fun_grad(x)
     evals = 1
+    g0n = math.sqrt(ops.dot(g, g))
     S, Y, R = [], [], []          # curvature pairs s_i, y_i and 1 / (y_i . s_i)
-    hist = [(0, f, math.sqrt(ops.dot(g, g)))]
-    converged = False
+    hist = [(0, f, g0n)]
+    converged = g0n == 0.0
     it = 0
     for it in range(1, max_iter + 1):
+        if converged:
+            it -= 1
+            break
         # two-loop recursion: d = -H g with H0 = (s.y / y.y) I from the newest pair
         q = ops.copy(g)
         alpha = []
@@ -96,35 +105,46 @@ def lbfgs(fun_grad, x0, ops, m: int = 8, max_iter: int = 100, rtol: float = 1e-5
             a_i = r_i * ops.dot(s_i, q)
             alpha.append(a_i)
             ops.axpby(-a_i, y_i, 1.0, q)
-        if S:
-            gamma = ops.dot(S[-1], Y[-1]) / ops.dot(Y[-1], Y[-1])
-        else:
-            gamma = 1.0 / max(math.sqrt(ops.dot(g, g)), 1e-300)   # first step of length 1
+        gamma = ops.dot(S[-1], Y[-1]) / ops.dot(Y[-1], Y[-1]) if S else 1.0
         ops.axpby(0.0, q, gamma, q)
         for (s_i, y_i, r_i), a_i in zip(zip(S, Y, R), reversed(alpha)):
             b_i = r_i * ops.dot(y_i, q)
             ops.axpby(a_i - b_i, s_i, 1.0, q)
         d = ops.axpby(0.0, q, -1.0, q)
         gd = ops.dot(g, d)
+        steepest = not S
         if not gd < 0:                      # not a descent direction: restart on -g
             S, Y, R = [], [], []
-            d = ops.axpby(0.0, g, 0.0, d)
-            ops.axpby(-1.0 / max(math.sqrt(ops.dot(g, g)), 1e-300), g, 0.0, d)
+            d = ops.axpby(-1.0, g, 0.0, d)
             gd = ops.dot(g, d)
-        # backtracking line search on the Armijo condition
-        step = 1.0
-        xn = ops.copy(x)
-        accepted = False
-        for _ in range(max_backtracks):
-            ops.assign(xn, x)
-            ops.axpby(step, d, 1.0, xn)
-            fn, gn = fun_grad(xn)
-            evals += 1
-            if math.isfinite(fn) and fn <= f + c1 * step * gd:
-                accepted = True
-                break
-            step *= 0.5
-        if not accepted:
+            steepest = True
+        step = 1.0 / max(math.sqrt(-gd), 1e-300) if steepest else 1.0
+
+        def trial(a):
+            xt = ops.copy(x)
+            ops.axpby(a, d, 1.0, xt)
+            ft, gt = fun_grad(xt)
+            return xt, ft, gt
+
+        xn, fn, gn = trial(step)
+        evals += 1
+        ok = math.isfinite(fn) and fn <= f + c1 * step * gd
+        if ok and steepest:
+            for _ in range(max_expand):       # expand while f keeps falling
+                x2, f2, g2 = trial(2.0 * step)
+                evals += 1
+                if not (math.isfinite(f2) and f2 < fn and f2 <= f + c1 * 2.0 * step * gd):
+                    break
+                step, xn, fn, gn = 2.0 * step, x2, f2, g2
+        else:
+            for _ in range(max_backtracks):
+                if ok:
+                    break
+                step *= 0.5
+                xn, fn, gn = trial(step)
+                evals += 1
+                ok = math.isfinite(fn) and fn <= f + c1 * step * gd
+        if not ok:
             break
         s_new = ops.axpby(-1.0, x, 1.0, ops.copy(xn))
         y_new = ops.axpby(-1.0, g, 1.0, ops.copy(gn))
@@ -143,8 +163,8 @@ def lbfgs(fun_grad, x0, ops, m: int = 8, max_iter: int = 100, rtol: float = 1e-5
         hist.append((it, f, gn2))
         if callback is not None:
             callback(it, x, f, g)
-        if df <= rtol * max(abs(f), 1e-300) or gn2 <= gtol:
-            converged = True
+        if gn2 <= rtol * g0n or not df > 0:
+            converged = gn2 <= rtol * g0n
             break
     return LbfgsResult(x=x, f=f, iterations=it, evaluations=evals, converged=converged,
                        history=hist)
