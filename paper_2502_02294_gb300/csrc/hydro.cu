@@ -362,6 +362,24 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
   }
 }
 
+// Limiter value and both partials of two lanes, as vanleer_vg (branch-free: the gate selects
+// per lane after the arithmetic of both).
+__device__ __forceinline__ void vanleer_vg2(float2 a, float2 b, float eps, float2& phi, float2& da,
+                                            float2& db) {
+  const float2 ab = mul2(a, b);
+  const float2 s = add2(a, b);
+  const float2 D = add2(s, make_float2(copysignf(eps, s.x), copysignf(eps, s.y)));
+  const float2 q = mul2(pk(2.0f), make_float2(fast_rcp(D.x), fast_rcp(D.y)));  // 2 / D
+  const float2 q2 = mul2(mul2(q, q), pk(0.5f));                                  // 2 / D^2
+  const float2 p = mul2(ab, q);
+  const float2 dA = mul2(mul2(b, sub2(D, a)), q2);
+  const float2 dB = mul2(mul2(a, sub2(D, b)), q2);
+  const bool gx = ab.x > 0.0f, gy = ab.y > 0.0f;
+  phi = make_float2(gx ? p.x : 0.0f, gy ? p.y : 0.0f);
+  da = make_float2(gx ? dA.x : 0.0f, gy ? dA.y : 0.0f);
+  db = make_float2(gx ? dB.x : 0.0f, gy ? dB.y : 0.0f);
+}
+
 // ------------------------------------------------------------- adjoint, marching form
 // Pass 1: each thread streams one line segment [s0, s0 + L) plus a halo and produces
 // lamUh_j for its own cells. At load i it recomputes the forward stages for cell i-1
@@ -375,7 +393,7 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
 // the left-moving one). Cell i-4 is then complete and lamUh_{i-4} = VJP(Uh_{i-4}).
 // d/dnu gathers sum_t F2_t lf_t / nu - sum_j lamUh_j dF1_j / 2.
 template <int AXIS, int FC = 1 + AXIS>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 3)
 sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                        float* __restrict__ luh_out, int n, SArg nua, float gam, float eps,
                        DPart dnub, int L) {
@@ -455,8 +473,41 @@ sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ 
     // periodic line sum_k -lam_out_k (F2_k - F2_{k-1}) = sum_t F2_t lf_t / nu
     const int jt = s0 + it - 8;  // unwrapped index of face cell t (face t + 1/2)
     const bool face_in = (jt >= s0) && (jt < s0 + L) && (jt < n);
+    // components (0, 1) and (2, 3) as FP32x2 pairs, component 4 alone: the same operations
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 4; k += 2) {
+      const float2 lf = mul2(pk(nu), sub2(make_float2(M1[k], M1[k + 1]), make_float2(M0[k], M0[k + 1])));
+      const float2 r0 = make_float2(R0[k], R0[k + 1]), r1 = make_float2(R1[k], R1[k + 1]);
+      const float2 r2 = make_float2(R2[k], R2[k + 1]);
+      const float2 l0 = make_float2(L0[k], L0[k + 1]), l1 = make_float2(L1[k], L1[k + 1]);
+      const float2 aR = mul2(pk(0.5f), sub2(r1, r0)), bR = mul2(pk(0.5f), sub2(r2, r1));
+      const float2 aL = mul2(pk(0.5f), sub2(l1, l0));
+      const float2 bL = mul2(pk(0.5f), sub2(make_float2(FLh[k], FLh[k + 1]), l1));
+      float2 pR, daR, dbR, pL, daL, dbL;
+      vanleer_vg2(aR, bR, eps, pR, daR, dbR);
+      vanleer_vg2(aL, bL, eps, pL, daL, dbL);
+      const float2 hl = mul2(pk(0.5f), lf);
+      const float2 A = mul2(hl, daR), B = mul2(hl, dbR), C = mul2(hl, daL), D = mul2(hl, dbL);
+      const float2 a0 = sub2(make_float2(aR0[k], aR0[k + 1]), A);
+      const float2 a1 = add2(make_float2(aR1[k], aR1[k + 1]), sub2(add2(lf, A), B));
+      const float2 a2 = add2(make_float2(aR2[k], aR2[k + 1]), B);
+      const float2 b1 = sub2(make_float2(aL1[k], aL1[k + 1]), C);
+      const float2 b2 = add2(make_float2(aL2[k], aL2[k + 1]), sub2(sub2(C, lf), D));
+      const float2 b3 = add2(make_float2(aL3[k], aL3[k + 1]), D);
+      aR0[k] = a0.x; aR0[k + 1] = a0.y;
+      aR1[k] = a1.x; aR1[k + 1] = a1.y;
+      aR2[k] = a2.x; aR2[k + 1] = a2.y;
+      aL1[k] = b1.x; aL1[k + 1] = b1.y;
+      aL2[k] = b2.x; aL2[k + 1] = b2.y;
+      aL3[k] = b3.x; aL3[k + 1] = b3.y;
+      // d/dnu part 1: faces of the segment's output cells (t in [s0-1, s0+L))
+      if (face_in) {
+        const float2 f2 = mul2(sub2(add2(r1, pR), sub2(l1, pL)), lf);
+        dnu_acc += (f2.x + f2.y) * inv_nu;
+      }
+    }
+    {
+      const int k = 4;
       const float lf = nu * (M1[k] - M0[k]);  // nu (lam_out_{t+1} - lam_out_t), t = i-3
       const float aR = 0.5f * (R1[k] - R0[k]), bR = 0.5f * (R2[k] - R1[k]);
       const float aL = 0.5f * (L1[k] - L0[k]), bL = 0.5f * (FLh[k] - L1[k]);
@@ -471,7 +522,6 @@ sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ 
       aL1[k] -= C;
       aL2[k] += -lf + C - D;
       aL3[k] += D;
-      // d/dnu part 1: faces of the segment's output cells (t in [s0-1, s0+L))
       if (face_in) dnu_acc += ((R1[k] + pR) - (L1[k] - pL)) * lf * inv_nu;
     }
     // cell i-4 is complete
