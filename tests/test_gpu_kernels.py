@@ -71,7 +71,11 @@ def test_sweep_forms_match_oracle(dh, n, variant):
     grids with a ragged last tile and segment.
 
     The forms recompute the forward identically, so they take the same float32 limiter
-    and sign decisions: their adjoints agree with each other to float32 rounding (1e-6).
+    and sign decisions: their adjoints agree with each other to float32 rounding. They
+    evaluate the same expressions in different orders (gather vs scatter of the face terms)
+    and the marching form's face block runs in packed FP32x2 instructions, which round every
+    product separately where scalar code may contract a product into an FMA: measured
+    1.0-1.7e-6 relative L2 between forms, bar 5e-6.
     Against the float64 oracle a face whose limiter arguments straddle zero within float32
     rounding takes the other branch in a few isolated cells (e.g. one cell at n = 20, seed
     101, y axis: 3.4e-3 overall); the oracle bar is therefore 1e-4 outside the 0.1 %
@@ -91,7 +95,7 @@ def test_sweep_forms_match_oracle(dh, n, variant):
         out = (hydro.sweep(X, "xyz"[axis], nut, GAMMA) * lam_o).sum()
         gx, gnu = torch.autograd.grad(out, (X, nut))
         for k in range(5):
-            assert rel_l2(gl[k], ref_form[k].double().cpu()) < 1e-6, (axis, k, "forms differ")
+            assert rel_l2(gl[k], ref_form[k].double().cpu()) < 5e-6, (axis, k, "forms differ")
             err = rel_l2(gl[k], gx[k])
             assert err < 1e-2, (axis, k, err)
             d = (gl[k].double().cpu() - gx[k]).flatten()
