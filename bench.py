@@ -452,16 +452,15 @@ def main():
         synth.field(n, FLI_TRUTH_SEED + 1).astype("float32")).to(dev)).contiguous()
     # one step of the hot path = one inference iteration on the n^3 amplitudes: ICs, the
     # 100-step run, posterior, checkpointed reverse pass, Adam update. Every timed step is
-    # the first iteration from the same amplitudes (moments cleared), so each times the
-    # same work.
+    # the first iteration from the same amplitudes (Adam's moments start from zero), so each
+    # times the same work.
     x = noise.clone()
     mom = torch.zeros_like(x)
     vel = torch.zeros_like(x)
     loss = torch.empty(1, dtype=torch.float64, device=dev)
 
     def hot_path(x_dev):
-        mom.zero_()
-        vel.zero_()
+        # step t = 1: the library starts the moments from zero (their contents are not read)
         sim.fli_step(x_dev, mom, vel, data, sigma_n, FLI_LR, 1, loss=loss)
         return x_dev, loss
 

@@ -322,7 +322,8 @@ sim_status sim_posterior(sim_t* h, int32_t observable, const float* noise, const
 /* One Adam iteration: sim_posterior at the input amplitudes, then one Adam step (Kingma &
  * Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias corrected with step t >= 1) on them with
  * learning rate lr. noise (B n^3, in: s, out: the updated s), m and v (B n^3, Adam moments,
- * in/out; zero them before t = 1), data (B n^3). loss (B doubles: L at the input s), grad
+ * in/out; at t = 1 their contents are ignored and the moments start from zero), data
+ * (B n^3). loss (B doubles: L at the input s), grad
  * (B n^3 or NULL: dL/ds at the input s). Stream-ordered, no synchronisation. SIM_EINVAL for
  * NULL arrays, sigma_n <= 0, lr <= 0, t < 1 or an unknown observable. */
 sim_status sim_fli_step(sim_t* h, int32_t observable, float* noise, float* m, float* v,
@@ -339,7 +340,8 @@ sim_status sim_axpby(double alpha, const float* x, double beta, float* y, int64_
 /* Adam step on a device vector (Kingma & Ba 2015, Algorithm 1, bias corrected with step
  * t >= 1) with the gradient g + prior_w x, the gradient of a data term plus that of the
  * Gaussian prior prior_w |x|^2 / 2 (prior_w = 1 for the white-noise amplitudes of Sec. 3.2,
- * 0 for plain Adam). x, m, v (count floats, in/out), g (count floats). grad_out (count
+ * 0 for plain Adam). x, m, v (count floats, in/out; at t = 1 the moments start from zero
+ * and their contents are not read), g (count floats). grad_out (count
  * floats or NULL) receives g + prior_w x; prior (one device double or NULL) is ACCUMULATED
  * with prior_w / 2 |x|^2 at the input x. SIM_EINVAL for NULL arrays, count < 1, t < 1,
  * lr <= 0, beta outside [0, 1) or eps <= 0. */

@@ -18,14 +18,16 @@
 
 namespace dh {
 
-// 1 - beta is formed in double on the host: in float32, 1 - fl(0.999) is 1.3e-5 off 0.001
+// 1 - beta is formed in double on the host: in float32, 1 - fl(0.999) is 1.3e-5 off 0.001.
+// At step t = 1 the moments start from zero (Adam's initialisation): m and v are not read.
 struct AdamConst {
   float lr, b1, b2, omb1, omb2, eps, inv_bc1, inv_bc2, prior_w;
+  int first;
 };
 
 __device__ __forceinline__ float adam_one(float x, float g, float& m, float& v, const AdamConst& c) {
-  m = c.b1 * m + c.omb1 * g;
-  v = c.b2 * v + c.omb2 * g * g;
+  m = c.first ? c.omb1 * g : c.b1 * m + c.omb1 * g;
+  v = c.first ? c.omb2 * g * g : c.b2 * v + c.omb2 * g * g;
   const float mh = m * c.inv_bc1, vh = v * c.inv_bc2;
   return x - c.lr * mh / (sqrtf(vh) + c.eps);
 }
@@ -53,8 +55,8 @@ __global__ void __launch_bounds__(256) fli_adam_kernel(float* __restrict__ x, co
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
       float4 xv = reinterpret_cast<float4*>(x)[q];
       const float4 gv = __ldg(reinterpret_cast<const float4*>(g) + q);
-      float4 mv = reinterpret_cast<float4*>(m)[q];
-      float4 vv = reinterpret_cast<float4*>(v)[q];
+      float4 mv = c.first ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<float4*>(m)[q];
+      float4 vv = c.first ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<float4*>(v)[q];
       float4 gt;
       gt.x = gv.x + c.prior_w * xv.x;
       gt.y = gv.y + c.prior_w * xv.y;
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(256) fli_adam_kernel(float* __restrict__ x, co
       const float gt = __ldg(g + i) + c.prior_w * xi;
       acc += xi * xi;
       if (grad_out) grad_out[i] = gt;
-      float mi = m[i], vi = v[i];
+      float mi = c.first ? 0.0f : m[i], vi = c.first ? 0.0f : v[i];
       x[i] = adam_one(xi, gt, mi, vi, c);
       m[i] = mi;
       v[i] = vi;
@@ -103,6 +105,7 @@ sim_status launch_fli_adam(float* x, const float* g, float* m, float* v, long lo
   c.inv_bc1 = (float)(1.0 / (1.0 - std::pow(beta1, t)));
   c.inv_bc2 = (float)(1.0 / (1.0 - std::pow(beta2, t)));
   c.prior_w = (float)prior_w;
+  c.first = t == 1;
   const uintptr_t align = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(g) |
                           reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v) |
                           reinterpret_cast<uintptr_t>(grad_out);
