@@ -525,17 +525,15 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
   if (q.ok) {
     const int i = q.p;
     cic_setup(s0, q, N3, n, inv_dx, c);
-    float gi[3];
-    interp3(g, c, n, N3, gi);
     float ls[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       ls[j] = lam_s[j * N3 + i];
-      if (p0) dd += ls[j] * (p0[j * N3 + i] + K * gi[j]);
       lp[j] = lam_p[j * N3 + i] + dtau * ls[j];
-      dk += lp[j] * gi[j];
     }
-    // lam_s0 += K d/ds (sum_j lp_j interp(g_j))
+    // one pass over the 8 corners gathers g once for both uses: gi = interp(g) (summed in
+    // the order of interp3) and lam_s0 += K d/ds (sum_j lp_j interp(g_j))
+    float gi[3] = {0.0f, 0.0f, 0.0f};
     float gs[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int oz = 0; oz < 2; ++oz)
@@ -544,16 +542,28 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox) {
           const int o = node(c, oz, oy, ox, n);
+          const float w = c.wz[oz] * c.wy[oy] * c.wx[ox];
           const float dwx = (ox ? inv_dx : -inv_dx) * c.wy[oy] * c.wz[oz];
           const float dwy = (oy ? inv_dx : -inv_dx) * c.wx[ox] * c.wz[oz];
           const float dwz = (oz ? inv_dx : -inv_dx) * c.wx[ox] * c.wy[oy];
+          float gv[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            gv[j] = __ldg(g + j * N3 + o);
+            gi[j] += w * gv[j];
+          }
           float lg = 0.0f;
 #pragma unroll
-          for (int j = 0; j < 3; ++j) lg += lp[j] * __ldg(g + j * N3 + o);
+          for (int j = 0; j < 3; ++j) lg += lp[j] * gv[j];
           gs[0] += dwx * lg;
           gs[1] += dwy * lg;
           gs[2] += dwz * lg;
         }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (p0) dd += ls[j] * (p0[j * N3 + i] + K * gi[j]);
+      dk += lp[j] * gi[j];
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       lam_s[j * N3 + i] = ls[j] + K * gs[j];

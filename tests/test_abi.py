@@ -85,6 +85,22 @@ def test_null_arguments_rejected(dh):
     assert L.sim_kernel_timing(None, 1) == dh._lib.SIM_EINVAL
     assert L.sim_kernel_times(None, None, None, 0) == dh._lib.SIM_EINVAL
     L.sim_destroy(None)  # ignored
+    E = dh._lib.SIM_EINVAL
+    # the entry points of field-level inference, diagnostics and validation runs
+    assert L.sim_fli_step(None, 0, None, None, None, None, 0.1, 0.01, 1, None, None) == E
+    assert L.sim_posterior(None, 0, None, None, 0.1, None, None) == E
+    assert L.sim_loss_field(None, 0, None, 1.0, None, None) == E
+    assert L.sim_adam(None, None, None, None, 8, 0.1, 0.9, 0.999, 1e-8, 1, 0.0, None, None, None) == E
+    assert L.sim_dot(None, None, 8, None, None) == E
+    assert L.sim_axpby(1.0, None, 1.0, None, 8, None) == E
+    assert L.sim_cross_correlation(None, None, 8, 8.0, 4, None, None, None, None) == E
+    assert L.sim_power_spectrum_adjoint(None, 8, 8.0, 4, None, None, None) == E
+    assert L.sim_max_signal_speed(None, 8, 5 / 3, None, None) == E
+    assert L.sim_set_params(None, None) == E
+    assert L.sim_set_diagnostics(None, 1) == E
+    assert L.sim_diagnostics(None, 0, None) == E
+    assert L.sim_closure_set_wait_limit(None, 0) == E
+    assert L.sim_deposit_cic_static(None, None, 8, 8.0, None, None) == E
 
 
 def test_no_unresolved_library_symbols(dh):
