@@ -57,8 +57,8 @@ SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, i
 # the ncu captures summarised in profiles/ (128^3, cold cache): forward sweep, the x tile
 # (44.2 MB) and the paired y / z forms (46.0, 46.2 MB) averaged; adjoint sweep (x, y, z
 # average of the marching pair with fitted segments, x with its transposes)
-# (427.2 + 262.0 + 262.8) / 3 MB; None where no capture of the current kernel exists
-TRAFFIC_BYTES_PER_CELL = {"sweep": 21.70, "sweep_adjoint": 151.3}
+# (423.5 + 259.0 + 259.9) / 3 MB; None where no capture of the current kernel exists
+TRAFFIC_BYTES_PER_CELL = {"sweep": 21.70, "sweep_adjoint": 149.8}
 # the kernel forms (SWEEP_* per axis x, y, z) those captures measured
 PROFILED_VARIANTS = {"sweep": [1, 5, 5], "sweep_adjoint": [4, 4, 4]}
 # algorithmic bytes per cell of one timed launch group of each class (one particle per cell)
