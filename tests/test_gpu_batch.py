@@ -134,13 +134,14 @@ def test_autotune_and_variants_agree(dh, n):
     ps = _params(dh, n, B, n_steps=3, rms_ref=0.05)
     noise = _noise(n, B)
     results = []
-    for mode in ("default", "tile", "march32", "march16", "marchfit", "auto"):
+    for mode in ("default", "tile", "march32", "march16", "marchfit", "pair", "auto"):
         sim = dh.Simulation(ps, noise.contiguous())
         if mode == "auto":
             fwd, adj = sim.autotune(reps=2)
-            assert fwd[0] == 1 and all(v in (1, 2, 3, 4) for v in fwd + adj)
+            assert fwd[0] == 1 and all(v in (1, 2, 3, 4, 5) for v in fwd)
+            assert all(v in (1, 2, 3, 4) for v in adj)
         elif mode != "default":
-            v = {"tile": 1, "march32": 2, "march16": 3, "marchfit": 4}[mode]
+            v = {"tile": 1, "march32": 2, "march16": 3, "marchfit": 4, "pair": 5}[mode]
             sim.set_sweep_variants([v] * 3, [v] * 3)
         sim.run()
         st = sim.state()
