@@ -423,31 +423,10 @@ __device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& 
       }
 }
 
-// Gas kick of cell i over a kick of length K at frozen rho and g (the gravity source S_g of
-// Eq. conservation integrated exactly): m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2.
-// u and uo may be the same array (every value is read before it is written).
-__device__ __forceinline__ void gas_kick_cell(const float* u, float* uo,
-                                              const float* __restrict__ g, float K, int N3, int i) {
-  const float rho = u[i];
-  float mg = 0.0f, g2 = 0.0f;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const float gj = g[j * N3 + i];
-    const float mj = u[(1 + j) * N3 + i];
-    mg += mj * gj;
-    g2 += gj * gj;
-    uo[(1 + j) * N3 + i] = mj + rho * gj * K;
-  }
-  uo[4 * N3 + i] = u[4 * N3 + i] + K * mg + 0.5f * K * K * rho * g2;
-  if (uo != u) uo[i] = rho;
-}
-
-// With gas_in != NULL the same launch also kicks gas cell i (the cell of lattice site i) with
-// the same K: gas_out = kick(gas_in), in place when they are equal (gas_kick_cell).
 __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
                                   const float* __restrict__ g, SArg Ka, SArg dtaua,
                                   const float* __restrict__ zhat, float* __restrict__ aux,
-                                  const float* gas_in, float* gas_out, int n, float inv_dx) {
+                                  int n, float inv_dx) {
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   if (!q.ok) return;
@@ -457,8 +436,6 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
   p += o3;
   g += o3;
   const float K = Ka.at(q.b), dtau = dtaua.at(q.b);
-  if (gas_in)
-    gas_kick_cell(gas_in + (size_t)q.b * 5 * N3, gas_out + (size_t)q.b * 5 * N3, g, K, N3, i);
   Cic c;
   cic_setup(s, q, N3, n, inv_dx, c);
   float gi[3];
@@ -486,9 +463,38 @@ __global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
 
 sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
                              const float* zhat, float* aux, int n, float inv_dx, int B,
-                             cudaStream_t st, const float* gas_in, float* gas_out) {
-  kick_drift_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, p, g, K, dtau, zhat, aux,
-                                                               gas_in, gas_out, n, inv_dx);
+                             cudaStream_t st) {
+  kick_drift_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, p, g, K, dtau, zhat, aux, n,
+                                                               inv_dx);
+  DH_LAUNCH_CHECK();
+  return SIM_OK;
+}
+
+// grid (cdiv(N3, 256), B)
+__global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__ g, SArg Ka,
+                                int N3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= N3) return;
+  u += (size_t)b * 5 * N3;
+  g += (size_t)b * 3 * N3;
+  const float K = Ka.at(b);
+  const float rho = u[i];
+  float mg = 0.0f, g2 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float gj = g[j * N3 + i];
+    const float mj = u[(1 + j) * N3 + i];
+    mg += mj * gj;
+    g2 += gj * gj;
+    u[(1 + j) * N3 + i] = mj + rho * gj * K;
+  }
+  u[4 * N3 + i] += K * mg + 0.5f * K * K * rho * g2;
+}
+
+sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cudaStream_t st) {
+  const int N3 = n * n * n;
+  gas_kick_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, g, K, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

@@ -50,14 +50,12 @@ sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftCom
 sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
                          float* out, int B, cudaStream_t st);
 // p += K interp(g, s); then, if dtau != 0, s += dtau p. If zhat != NULL also
-// aux += interp(zhat, s) at the position before the drift. If gas_in != NULL the same launch
-// kicks the gas (gas 5 n^3, g 3 n^3) with the same K: m += rho g K, eps += K m.g +
-// K^2 rho |g|^2 / 2 (exact for frozen rho, g), gas_out = kick(gas_in) (gas_out may equal
-// gas_in; otherwise all five fields of gas_out are written).
+// aux += interp(zhat, s) at the position before the drift.
 sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
                              const float* zhat, float* aux, int n, float inv_dx, int B,
-                             cudaStream_t st, const float* gas_in = nullptr,
-                             float* gas_out = nullptr);
+                             cudaStream_t st);
+// m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2 (gas 5 n^3, g 3 n^3)
+sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cudaStream_t st);
 
 // ---- adjoints
 // The adjoint of the force field is accumulated node-interleaved: lam_g4[b][i] = (lam_gx,

@@ -472,17 +472,18 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     DH_TRY(dcopy(T->p0, p, vb, st));
     DH_TRY(dcopy(T->g0, g, vb, st));
   }
-  // 1. half kick + drift of the particles and, in the same launch, the gas half kick (out of
-  //    place into the tape's kicked-gas slot when recording)
-  float* cur = *gas;
-  float* kicked = T ? T->Uk1 : cur;
+  // 1. half kick + drift
   DH_TRY(timed(h, SIM_KT_KICK, [&] {
     return launch_kick_drift(s, p, g, K1, sc(h, i, SC_DTAU), zh_prev, zh_prev ? h->aux : nullptr,
-                             h->n, (float)h->inv_dx, B, st, P.gravity_on ? cur : nullptr,
-                             P.gravity_on ? kicked : nullptr);
+                             h->n, (float)h->inv_dx, B, st);
   }));
-  if (T && !P.gravity_on) DH_TRY(dcopy(T->Uk1, cur, gb, st));
-  cur = kicked;
+  float* cur = *gas;
+  if (T) {
+    DH_TRY(dcopy(T->Uk1, cur, gb, st));
+    cur = T->Uk1;
+  }
+  if (P.gravity_on)
+    DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(cur, g, K1, h->n, B, st); }));
   // 2. sweeps
   if (P.hydro_on) {
     const char* order = kOrders[i % 6];
@@ -531,9 +532,10 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   if (kick_out) {
     DH_TRY(timed(h, SIM_KT_KICK, [&] {
       return launch_kick_drift(s, p, g, K2, sarg(0.0f), zh, zh ? h->aux : nullptr, h->n,
-                               (float)h->inv_dx, B, st, P.gravity_on ? *gas : nullptr,
-                               P.gravity_on ? *gas : nullptr);
+                               (float)h->inv_dx, B, st);
     }));
+    if (P.gravity_on)
+      DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(*gas, g, K2, h->n, B, st); }));
   }
   if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, B * h->N3, st));
   // 6. learned correction of the gas fields (solver in the loop, Sec. 4)
