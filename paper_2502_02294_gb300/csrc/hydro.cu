@@ -47,6 +47,22 @@ template <> struct SweepCfg<0> { static constexpr int S = 64, W = 4, NT = 128, S
 template <> struct SweepCfg<1> { static constexpr int S = DH_TILE_S, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
 template <> struct SweepCfg<2> { static constexpr int S = DH_TILE_S, W = 32, NT = 256, SA = 16, WA = 32, NTA = 256; };
 
+// packed FP32x2 arithmetic of sm_100+ (FADD2 / FMUL2 / FFMA2: one issue slot for two lanes)
+__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, pk(-1.0f), a); }
+
+// gated van Leer limiter of two lanes, as vanleer
+__device__ __forceinline__ float2 vanleer2(float2 a, float2 b, float eps) {
+  const float2 ab = mul2(a, b);
+  const float2 s = add2(a, b);
+  const float2 D = add2(s, make_float2(copysignf(eps, s.x), copysignf(eps, s.y)));
+  const float2 t = mul2(add2(ab, ab), make_float2(fast_rcp(D.x), fast_rcp(D.y)));
+  return make_float2(ab.x > 0.0f ? t.x : 0.0f, ab.y > 0.0f ? t.y : 0.0f);
+}
+
 // limited second-order face flux at face c+1/2 from the half-step splits R = Fh^R, L = Fh^L
 __device__ __forceinline__ float face_flux(const float* R, const float* L, int DS, float eps) {
   const float Rm1 = R[-DS], R0 = R[0], Rp1 = R[DS];
@@ -56,6 +72,18 @@ __device__ __forceinline__ float face_flux(const float* R, const float* L, int D
   return fr - fl;
 }
 
+// the same face flux for components (k, k + 1) as one FP32x2 pair
+__device__ __forceinline__ float2 face_flux2(const float2* R, const float2* L, int DS, float eps) {
+  const float2 Rm1 = R[-DS], R0 = R[0], Rp1 = R[DS];
+  const float2 L0 = L[0], Lp1 = L[DS], Lp2 = L[2 * DS];
+  const float2 fr = add2(R0, vanleer2(mul2(pk(0.5f), sub2(R0, Rm1)), mul2(pk(0.5f), sub2(Rp1, R0)), eps));
+  const float2 fl = sub2(Lp1, vanleer2(mul2(pk(0.5f), sub2(Lp1, L0)), mul2(pk(0.5f), sub2(Lp2, Lp1)), eps));
+  return sub2(fr, fl);
+}
+
+// Shared memory holds the flux splits and face fluxes with components (0, 1) and (2, 3) as
+// interleaved float pairs (one 8-byte access and one FP32x2 instruction for two components)
+// and component 4 alone: per array [pair 0: NC float2][pair 1: NC float2][component 4: NC].
 template <int AXIS>
 __global__ void __launch_bounds__(SweepCfg<AXIS>::NT, 2)
 sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
@@ -64,15 +92,21 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
   using G = TileGeom<AXIS, S, W, 3>;
   constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
   constexpr int F = 1 + AXIS;
+  static_assert(NC % 2 == 0, "float2 regions need an even cell count");
   extern __shared__ float sm[];
-  float* sf = sm;            // 10 NC: F^R, F^L of U, then of Uh
-  float* sg = sm + 10 * NC;  // 5 NC: limited face fluxes (face c+1/2 at c)
+  float2* rp = reinterpret_cast<float2*>(sm);            // F^R pairs  [2][NC]
+  float* r4 = sm + 4 * NC;                                // F^R_4      [NC]
+  float2* lp = reinterpret_cast<float2*>(sm + 5 * NC);   // F^L pairs
+  float* l4 = sm + 9 * NC;
+  float2* gp = reinterpret_cast<float2*>(sm + 10 * NC);  // face fluxes (face c+1/2 at c)
+  float* g4 = sm + 14 * NC;
   const long long N3 = (long long)n * n * n;
   const int b = blockIdx.z / n;  // instance; blockIdx.z = b n + third coordinate
   const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z - b * n;
   uin += (size_t)b * 5 * N3;
   uout += (size_t)b * 5 * N3;
   const float nu = nua.at(b);
+  const float2 hnu = pk(0.5f * nu), mnu = pk(-nu);
 
   float ureg[CPT][5];
 #pragma unroll
@@ -90,11 +124,13 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
       float FR[5], FL[5];
       split_flux(u, F, gam, FR, FL);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        ureg[i][k] = u[k];
-        sf[k * NC + c] = FR[k];
-        sf[(5 + k) * NC + c] = FL[k];
-      }
+      for (int k = 0; k < 5; ++k) ureg[i][k] = u[k];
+      rp[c] = make_float2(FR[0], FR[1]);
+      rp[NC + c] = make_float2(FR[2], FR[3]);
+      r4[c] = FR[4];
+      lp[c] = make_float2(FL[0], FL[1]);
+      lp[NC + c] = make_float2(FL[2], FL[3]);
+      l4[c] = FL[4];
     }
   }
   __syncthreads();
@@ -105,11 +141,18 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
     const int s = G::s_of(c);
     if (c < NC && s >= 1 && s < SP - 1) {
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const float fp = sf[k * NC + c] - sf[(5 + k) * NC + c + DS];
-        const float fm = sf[k * NC + c - DS] - sf[(5 + k) * NC + c];
-        uh[i][k] = ureg[i][k] - 0.5f * nu * (fp - fm);
+      for (int j = 0; j < 2; ++j) {
+        const float2* R = rp + j * NC;
+        const float2* Lq = lp + j * NC;
+        const float2 fp = sub2(R[c], Lq[c + DS]);
+        const float2 fm = sub2(R[c - DS], Lq[c]);
+        const float2 h = fma2(hnu, sub2(fm, fp), make_float2(ureg[i][2 * j], ureg[i][2 * j + 1]));
+        uh[i][2 * j] = h.x;
+        uh[i][2 * j + 1] = h.y;
       }
+      const float fp = r4[c] - l4[c + DS];
+      const float fm = r4[c - DS] - l4[c];
+      uh[i][4] = ureg[i][4] - 0.5f * nu * (fp - fm);
     }
   }
   __syncthreads();
@@ -120,11 +163,12 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
     if (c < NC && s >= 1 && s < SP - 1) {
       float FR[5], FL[5];
       split_flux(uh[i], F, gam, FR, FL);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        sf[k * NC + c] = FR[k];
-        sf[(5 + k) * NC + c] = FL[k];
-      }
+      rp[c] = make_float2(FR[0], FR[1]);
+      rp[NC + c] = make_float2(FR[2], FR[3]);
+      r4[c] = FR[4];
+      lp[c] = make_float2(FL[0], FL[1]);
+      lp[NC + c] = make_float2(FL[2], FL[3]);
+      l4[c] = FL[4];
     }
   }
   __syncthreads();
@@ -134,9 +178,9 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
     const int c = threadIdx.x + i * NT;
     const int s = G::s_of(c);
     if (c < NC && s >= 2 && s < S + 3) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k)
-        sg[k * NC + c] = face_flux(sf + k * NC + c, sf + (5 + k) * NC + c, DS, eps);
+      gp[c] = face_flux2(rp + c, lp + c, DS, eps);
+      gp[NC + c] = face_flux2(rp + NC + c, lp + NC + c, DS, eps);
+      g4[c] = face_flux(r4 + c, l4 + c, DS, eps);
     }
   }
   __syncthreads();
@@ -148,8 +192,13 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
     if (c < NC && s >= 3 && s < S + 3 && sgl < n && wg < n) {
       const long long o = goff<AXIS>(sgl, wg, t, n);
 #pragma unroll
-      for (int k = 0; k < 5; ++k)
-        uout[k * N3 + o] = ureg[i][k] - nu * (sg[k * NC + c] - sg[k * NC + c - DS]);
+      for (int j = 0; j < 2; ++j) {
+        const float2 v = fma2(mnu, sub2(gp[j * NC + c], gp[j * NC + c - DS]),
+                              make_float2(ureg[i][2 * j], ureg[i][2 * j + 1]));
+        uout[2 * j * N3 + o] = v.x;
+        uout[(2 * j + 1) * N3 + o] = v.y;
+      }
+      uout[4 * N3 + o] = ureg[i][4] - nu * (g4[c] - g4[c - DS]);
     }
   }
 }
@@ -245,12 +294,6 @@ sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int 
 // for two lanes), so the instruction count per cell roughly halves; reciprocals, square
 // roots, sign tests and selects stay per lane. The half differences of the limiter inputs
 // are formed once per cell and kept in the window (face j uses those of cells j and j + 1).
-__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, pk(-1.0f), a); }
-
 // flux splits of two cells (F^R = (cU + F)/2, F^L = (cU - F)/2), as split_flux
 __device__ __forceinline__ void split_flux2(const float2 u[5], int f, float gam, float2 FR[5],
                                             float2 FL[5]) {
@@ -275,15 +318,6 @@ __device__ __forceinline__ void split_flux2(const float2 u[5], int f, float gam,
     FR[k] = fma2(hc, u[k], hF[k]);
     FL[k] = fma2(hF[k], pk(-2.0f), FR[k]);
   }
-}
-
-// gated van Leer limiter of two lanes, as vanleer
-__device__ __forceinline__ float2 vanleer2(float2 a, float2 b, float eps) {
-  const float2 ab = mul2(a, b);
-  const float2 s = add2(a, b);
-  const float2 D = add2(s, make_float2(copysignf(eps, s.x), copysignf(eps, s.y)));
-  const float2 t = mul2(add2(ab, ab), make_float2(fast_rcp(D.x), fast_rcp(D.y)));
-  return make_float2(ab.x > 0.0f ? t.x : 0.0f, ab.y > 0.0f ? t.y : 0.0f);
 }
 
 // AXIS 1 or 2; n even (8-byte aligned pairs). Thread: lines w, w + 1 (adjacent x columns,
