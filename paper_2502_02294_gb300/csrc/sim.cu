@@ -81,8 +81,9 @@ struct InstConst {
 struct TapeSlot {
   float *U0, *Uk1, *Us1, *Us2, *Us3, *Usg;  // 5 n^3 each
   float *s0, *p0, *g0, *s1, *g1;            // 3 n^3 each
+  float* gd;                                 // n^3: the step's Gumbel difference g0 - g1
 };
-constexpr int kTapeFloatsPerCell = 6 * 5 + 5 * 3;
+constexpr int kTapeFloatsPerCell = 6 * 5 + 5 * 3 + 1;
 
 // Host-side state that a call changes; a replayed graph must start from and end in the
 // same values as the captured call.
@@ -508,7 +509,8 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     float* out = T ? T->Usg : cur;
     zh = T ? nullptr : h->zhat;
     DH_TRY(timed(h, SIM_KT_SUBGRID, [&] {
-      return launch_subgrid(cur, out, sub_at(h, i), zh, T ? nullptr : h->events, h->N3, B, st);
+      return launch_subgrid(cur, out, sub_at(h, i), zh, T ? nullptr : h->events, h->N3, B, st,
+                            T ? T->gd : nullptr);
     }));
     cur = out;
   } else if (T) {
@@ -596,6 +598,7 @@ static TapeSlot tape_slot(sim_t* h, int k) {
   t.g0 = b + 36 * N3;
   t.s1 = b + 39 * N3;
   t.g1 = b + 42 * N3;
+  t.gd = b + 45 * N3;
   return t;
 }
 
@@ -648,7 +651,7 @@ static sim_status reverse_step(sim_t* h, int i, const TapeSlot& T, double* slot,
   if (P.subgrid_on)
     DH_TRY(timed(h, SIM_KT_SUBGRID_ADJOINT, [&] {
       return launch_subgrid_adjoint(T.Us3, h->lam_gas, sub_at(h, i), dpart(h->dglob, NG),
-                                    slot_part(slot, SL_DFB), h->N3, B, st);
+                                    slot_part(slot, SL_DFB), h->N3, B, st, T.gd);
     }));
   // 2. sweeps in reverse
   if (P.hydro_on) {

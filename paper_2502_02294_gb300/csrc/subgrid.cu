@@ -2,7 +2,7 @@
 //
 // Per cell, with e = (eps - |m|^2/(2 rho)) / (a^2 rho), T = t_per_e e, delta = rho/f_b - 1:
 //   ln pi_0 = ln Pi_0 + log sigma((delta - delta_c)/w_delta) + log sigma((T_c - T)/w_T)
-//   l       = ln pi_0 - ln(1 - pi_0) + g_0 - g_1,   g_i = -ln(-ln u_i), u from Philox
+//   l       = ln pi_0 - ln(1 - pi_0) + (g_0 - g_1),  g_i = -ln(-ln u_i), u from Philox
 //   zhat    = sigma(l / tau)                          (Eq. gumbelsoftmax, rewritten stably)
 //   event   = l > 0                                   (hard Gumbel-max draw)
 //   e      <- max(e + E_0 zhat, (T_0/t_per_e) (rho/f_b)^(gamma_uv - 1))   (floor if T_0 > 0)
@@ -54,8 +54,10 @@ struct SgFwd {
   bool floor_on, use_floor;
 };
 
-__device__ __forceinline__ void subgrid_cell(const float u[5], const SubgridConst& c,
-                                             float g0, float g1, SgFwd& r) {
+// gd = g0 - g1, the only way the Gumbel pair enters (the forward and the adjoint use the
+// same float, drawn once or read back from the tape)
+__device__ __forceinline__ void subgrid_cell(const float u[5], const SubgridConst& c, float gd,
+                                             SgFwd& r) {
   const float rho = u[0];
   r.ke = 0.5f * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / rho;
   r.e = (u[4] - r.ke) / (c.a2 * rho);
@@ -65,7 +67,7 @@ __device__ __forceinline__ void subgrid_cell(const float u[5], const SubgridCons
   r.x2 = (c.T_c - r.T) * c.inv_wT;
   r.lnpi = c.lnPi0 + log_sigmoid(r.x1) + log_sigmoid(r.x2);
   r.pi = expf(r.lnpi);
-  r.logit = r.lnpi - log1pf(-r.pi) + g0 - g1;
+  r.logit = (r.lnpi - log1pf(-r.pi)) + gd;
   r.zhat = sigmoidf_(r.logit * c.inv_tau);
   r.e1 = r.e + c.E0 * r.zhat;
   r.floor_on = c.ef0 > 0.0f;
@@ -74,17 +76,19 @@ __device__ __forceinline__ void subgrid_cell(const float u[5], const SubgridCons
   r.e2 = r.use_floor ? r.ef : r.e1;
 }
 
-__device__ __forceinline__ void gumbel_pair(const SubgridConst& c, long long i, float& g0,
-                                            float& g1) {
+__device__ __forceinline__ float gumbel_diff(const SubgridConst& c, long long i) {
   const uint4 w = philox4x32_10(make_uint4((uint32_t)i, c.step, c.instance, TAG_SUBGRID), c.k0, c.k1);
-  g0 = -logf(-logf(uniform_from_word(w.x)));
-  g1 = -logf(-logf(uniform_from_word(w.y)));
+  const float g0 = -logf(-logf(uniform_from_word(w.x)));
+  const float g1 = -logf(-logf(uniform_from_word(w.y)));
+  return g0 - g1;
 }
 
 // grid (cdiv(N3, 256), B); instance b uses constants ca.at(b)
+// gd_out (may be NULL): g0 - g1 of every cell, for the adjoint of the same step
 __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__ out,
                                SubArg ca, float* __restrict__ zhat,
-                               uint32_t* __restrict__ events, long long N3) {
+                               uint32_t* __restrict__ events, float* __restrict__ gd_out,
+                               long long N3) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   in += (size_t)b * 5 * N3;
@@ -97,10 +101,10 @@ __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__
     float u[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) u[k] = in[k * N3 + i];
-    float g0, g1;
-    gumbel_pair(c, i, g0, g1);
+    const float gd = gumbel_diff(c, i);
+    if (gd_out) gd_out[(size_t)b * N3 + i] = gd;
     SgFwd r;
-    subgrid_cell(u, c, g0, g1, r);
+    subgrid_cell(u, c, gd, r);
     ev = r.logit > 0.0f;
     if (out != in) {
 #pragma unroll
@@ -116,8 +120,10 @@ __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__
   }
 }
 
+// gd_in (may be NULL): the g0 - g1 the forward drew (else drawn again from Philox)
 __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restrict__ lam,
-                                   SubArg ca, DPart dpar_b, DPart dfb_b, long long N3) {
+                                   SubArg ca, DPart dpar_b, DPart dfb_b,
+                                   const float* __restrict__ gd_in, long long N3) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   in += (size_t)b * 5 * N3;
@@ -133,10 +139,9 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
       u[k] = in[k * N3 + i];
       l[k] = lam[k * N3 + i];
     }
-    float g0, g1;
-    gumbel_pair(c, i, g0, g1);
+    const float gd = gd_in ? __ldg(gd_in + (size_t)b * N3 + i) : gumbel_diff(c, i);
     SgFwd r;
-    subgrid_cell(u, c, g0, g1, r);
+    subgrid_cell(u, c, gd, r);
     const float rho = u[0];
     // eps' = ke + a^2 rho e2
     const float leps = l[4];
@@ -190,15 +195,15 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
 }
 
 sim_status launch_subgrid(const float* in, float* out, SubArg c, float* zhat,
-                          uint32_t* events, long long N3, int B, cudaStream_t st) {
-  subgrid_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, out, c, zhat, events, N3);
+                          uint32_t* events, long long N3, int B, cudaStream_t st, float* gd) {
+  subgrid_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, out, c, zhat, events, gd, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 sim_status launch_subgrid_adjoint(const float* in, float* lam, SubArg c, DPart dpar, DPart dfb,
-                                  long long N3, int B, cudaStream_t st) {
-  subgrid_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, lam, c, dpar, dfb, N3);
+                                  long long N3, int B, cudaStream_t st, const float* gd) {
+  subgrid_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, lam, c, dpar, dfb, gd, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

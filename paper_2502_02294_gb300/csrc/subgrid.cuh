@@ -32,11 +32,15 @@ double temperature_per_energy(double gamma, double mu);
 
 // B instances one after another (as the PM launchers).
 // out = subgrid(in) (may alias); zhat (n^3) and events (ceil(n^3/32) words) may be NULL
+// gd (may be NULL): receives g0 - g1 of every cell ([B][n^3]) for the adjoint of this step
 sim_status launch_subgrid(const float* in, float* out, SubArg c, float* zhat,
-                          uint32_t* events, long long N3, int B, cudaStream_t st);
-// lam (5 n^3) in/out through the update at `in`; dpar[SIM_P_*] and dfb accumulated
+                          uint32_t* events, long long N3, int B, cudaStream_t st,
+                          float* gd = nullptr);
+// lam (5 n^3) in/out through the update at `in`; dpar[SIM_P_*] and dfb accumulated.
+// gd (may be NULL): the forward's g0 - g1 (else the pair is drawn again from Philox)
 sim_status launch_subgrid_adjoint(const float* in, float* lam, SubArg c, DPart dpar, DPart dfb,
-                                  long long N3, int B, cudaStream_t st);
+                                  long long N3, int B, cudaStream_t st,
+                                  const float* gd = nullptr);
 // max over cells and directions of |v_d| + c_s  (float bits in out_bits[b], atomicMax)
 sim_status launch_signal_speed(const float* gas, float gamma, long long N3,
                                unsigned int* out_bits, int B, cudaStream_t st);
