@@ -65,7 +65,7 @@ def subgrid(U, a, prm, g0, g1):
     zhat = torch.sigmoid(logit / prm["tau"])
     events = logit.detach() > 0
     e1 = e + prm["E0"] * zhat
-    if float(prm["T0_uv"]) > 0:
+    if bool((torch.as_tensor(prm["T0_uv"]) > 0).all()):  # a float, or a tensor (per cell)
         e_floor = (prm["T0_uv"] / tpe) * (rho / prm["f_b"]) ** (prm["gamma_uv"] - 1.0)
         e2 = torch.where(e1 >= e_floor, e1, e_floor)
     else:

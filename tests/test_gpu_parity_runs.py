@@ -43,6 +43,15 @@ def _oracle_grads(o, wo, to):
     return out, g[0], [0.0 if v is None else v.item() for v in g[1:]]
 
 
+def _t0_term_scale(o, wo, to, n):
+    """sum over cells of |contribution| to dL/dT0_uv: T0_uv as a per-cell tensor of equal
+    values, so its gradient splits the partial into the cells' floor terms (Sec. 2.4)."""
+    T0 = torch.full((n, n, n), float(o["T0_uv"]), dtype=DT, requires_grad=True)
+    out = osim.run(wo, dict(o, T0_uv=T0))
+    (g,) = torch.autograd.grad(osim.mse_density(out["U"], to), [T0])
+    return g.abs().sum().item()
+
+
 @pytest.mark.parametrize("n", [16, 32])
 def test_fifty_step_adjoint_matches_oracle_reverse_mode(dh, n):
     p = dh.default_params(n=n, box=float(n), n_steps=50, ckpt_every=10, a_start=0.1,
@@ -146,8 +155,13 @@ def test_batched_instances_match_their_oracle_runs(dh):
             assert rel_l2(st["gas"][b, k], out["U"][k]) < 1e-3, (b, k)
         assert rel_l2(st["s"][b], out["s"]) < 1e-3, b
         assert rel_l2(dnoise[b], gX) < 1e-3, (b, rel_l2(dnoise[b], gX))
+        # dL/dT0_uv sums floor terms of both signs over ~4,000 cells, 15-26 times larger than
+        # the partial itself; besides the 1e-3 relative bar it passes when it agrees to 1e-4
+        # of the summed term magnitudes (float32 per-term accuracy)
+        t0_scale = _t0_term_scale(o, wo, tgs[b][1], n)
         for j, k in enumerate(NAMES):
-            assert abs(dpar[b, j].item() - gp[j]) <= 1e-3 * abs(gp[j]) + 1e-12, (b, k, dpar[b, j].item(), gp[j])
+            bar = 1e-3 * abs(gp[j]) + 1e-12 + (1e-4 * t0_scale if k == "T0_uv" else 0.0)
+            assert abs(dpar[b, j].item() - gp[j]) <= bar, (b, k, dpar[b, j].item(), gp[j], bar)
     sim.close()
 
 
