@@ -12,6 +12,7 @@
 //   full step  (Eq. TVD_fullstep):  U'_i = U_i - nu (F2_{i+1/2} - F2_{i-1/2}),
 //              F2_{i+1/2} = [Fh^R_i + phi(dL, dR)] - [Fh^L_{i+1} - phi(dL', dR')]
 //              with the gated van Leer limiter phi and half differences of Fh^R / Fh^L.
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -37,6 +38,24 @@ struct TileGeom {
   __device__ static __forceinline__ int s_of(int c) { return AXIS == 0 ? c % SP : c / W; }
   __device__ static __forceinline__ int w_of(int c) { return AXIS == 0 ? c / SP : c % W; }
 };
+
+// Line of a thread of the marching and per-cell kernels: blocks of blockDim.x lanes along
+// x (each lane `wmul` adjacent x columns) times blockDim.y rows of the third coordinate, so
+// that grids with n below the block width keep their threads busy (one row per block left
+// 3/4 of them idle at n = 32); blockIdx.y = instance x row blocks. Rows past n are not live.
+struct LineIdx {
+  int w, t, b;
+  bool live;
+};
+__device__ __forceinline__ LineIdx line_index(int n, int wmul) {
+  const int nry = (n + (int)blockDim.y - 1) / (int)blockDim.y;
+  LineIdx r;
+  r.b = blockIdx.y / nry;
+  r.t = (blockIdx.y - r.b * nry) * blockDim.y + threadIdx.y;
+  r.w = wmul * (blockIdx.x * blockDim.x + threadIdx.x);
+  r.live = r.w < n && r.t < n;
+  return r;
+}
 
 // tile shapes (forward / adjoint): x sweep 64 x 4 lines, y/z sweeps 32 x 32 and 16 x 32
 template <int AXIS> struct SweepCfg;
@@ -214,11 +233,10 @@ __global__ void __launch_bounds__(128)
 sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
                    float gam, float eps, int L) {
   constexpr int F = 1 + AXIS;
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;  // line coordinate
-  const int b = blockIdx.y / n;                         // instance
-  const int t = blockIdx.y - b * n;                     // third coordinate
+  const LineIdx li = line_index(n, 1);
+  const int w = li.w, t = li.t, b = li.b;  // line coordinate, third coordinate, instance
   const int s0 = blockIdx.z * L;
-  if (w >= n) return;
+  if (!li.live) return;
   const long long N3 = (long long)n * n * n;
   uin += (size_t)b * 5 * N3;
   uout += (size_t)b * 5 * N3;
@@ -329,11 +347,10 @@ __global__ void __launch_bounds__(128, MINB)
 sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
                     float gam, float eps, int L) {
   constexpr int F = 1 + AXIS;
-  const int w = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int b = blockIdx.y / n;
-  const int t = blockIdx.y - b * n;
+  const LineIdx li = line_index(n, 2);
+  const int w = li.w, t = li.t, b = li.b;
   const int s0 = blockIdx.z * L;
-  if (w >= n) return;
+  if (!li.live) return;
   const long long N3 = (long long)n * n * n;
   uin += (size_t)b * 5 * N3;
   uout += (size_t)b * 5 * N3;
@@ -432,11 +449,11 @@ sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ 
                        float* __restrict__ luh_out, int n, SArg nua, float gam, float eps,
                        DPart dnub, int L) {
   constexpr int F = FC;  // momentum component along the sweep
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y / n;  // instance
-  const int t3 = blockIdx.y - b * n;
+  const LineIdx li = line_index(n, 1);
+  const int w = li.w, b = li.b;  // line coordinate, instance
+  const int t3 = li.t < n ? li.t : 0;  // third coordinate (rows past n load row 0, store nothing)
   const int s0 = blockIdx.z * L;
-  const bool live = w < n;
+  const bool live = li.live;
   const long long N3 = (long long)n * n * n;
   uin += (size_t)b * 5 * N3;
   lout += (size_t)b * 5 * N3;
@@ -618,8 +635,8 @@ sweep_adj_final_kernel(const float* __restrict__ uin, const float* __restrict__ 
   constexpr int F = FC;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.z / n;  // instance
-  const int y = blockIdx.y, z = blockIdx.z - b * n;
-  if (x >= n) return;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z - b * n;
+  if (x >= n || y >= n) return;
   const long long N3 = (long long)n * n * n;
   uin += (size_t)b * 5 * N3;
   lout += (size_t)b * 5 * N3;
@@ -715,7 +732,8 @@ __device__ __forceinline__ void split_flux_vjp2(const float2 u[5], int f, float 
   lu[0] = add2(lu[0], lrho);
 }
 
-// grid (cdiv(n / 2, 128), n, n B); thread: cells x = 2 t, 2 t + 1 of row (y, z)
+// grid (cdiv(n / 2, blockDim.x), cdiv(n, blockDim.y), n B); thread: cells x = 2 t, 2 t + 1
+// of row (y, z)
 template <int AXIS, int FC = 1 + AXIS>
 __global__ void __launch_bounds__(128)
 sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
@@ -724,8 +742,8 @@ sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__
   constexpr int F = FC;
   const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int b = blockIdx.z / n;
-  const int y = blockIdx.y, z = blockIdx.z - b * n;
-  if (x >= n) return;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z - b * n;
+  if (x >= n || y >= n) return;
   const long long N3 = (long long)n * n * n;
   uin += (size_t)b * 5 * N3;
   lout += (size_t)b * 5 * N3;
@@ -945,13 +963,26 @@ static int pick_adj(int axis, int variant) {
   return (variant != SIM_SWEEP_DEFAULT && variant != SIM_SWEEP_PAIR) ? variant : SIM_SWEEP_MARCH_FIT;
 }
 
+// Block of a line kernel (line_index): the x lanes (n, or n / 2 for two columns per lane)
+// in whole warps up to `threads`, and the rest of the block's threads as rows.
+static dim3 line_block(int lanes, int threads) {
+  const int tx = std::min(threads, 32 * cdiv(lanes, 32));
+  return dim3(tx, std::max(1, threads / tx));
+}
+
+// Grid of a line kernel over an n^3 grid of B instances with `segs` segments per line.
+static dim3 line_grid(int lanes, int n, int B, dim3 blk, int segs) {
+  return dim3(cdiv(lanes, blk.x), B * cdiv(n, blk.y), segs);
+}
+
 // Segment length of a marching kernel for an n^3 grid of B instances: the number k of
 // segments per line that minimises waves(k) x (n / k + halo), a wave being the blocks of
-// 128 threads that stay resident on all SMs at the kernel's register use (each thread
+// shape blk that stay resident on all SMs at the kernel's register use (each thread
 // streams its segment plus the halo once).
 template <class Kern>
-static int fit_segment(Kern kernel, int n, int B, int halo, int xthreads = 0, int block = 128) {
-  // blocks of 128 threads resident on the current device, per kernel and device
+static int fit_segment(Kern kernel, int n, int B, int halo, int lanes, dim3 blk) {
+  const int block = (int)(blk.x * blk.y);
+  // resident blocks on the current device, per kernel, block size and device
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, long long> cache;
   int dev = 0;
@@ -975,8 +1006,8 @@ static int fit_segment(Kern kernel, int n, int B, int halo, int xthreads = 0, in
     }
     resident = it->second;
   }
-  // blocks of one segment layer: xthreads threads along x (n: one line per thread)
-  const long long layer = (long long)cdiv(xthreads > 0 ? xthreads : n, block) * n * B;
+  // blocks of one segment layer
+  const long long layer = (long long)cdiv(lanes, blk.x) * cdiv(n, blk.y) * B;
   int best = n, best_cost = 1 << 30;
   for (int k = 1; k <= n; ++k) {
     const int L = cdiv(n, k);
@@ -999,10 +1030,12 @@ static int segment_length(int variant) {
 template <int AXIS>
 static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, float gam,
                                  float eps, int B, int variant, cudaStream_t st) {
-  const int L = variant == SIM_SWEEP_MARCH_FIT ? fit_segment(sweep_march_kernel<AXIS>, n, B, 6)
-                                               : segment_length(variant);
-  dim3 grid(cdiv(n, 128), n * B, cdiv(n, L));
-  sweep_march_kernel<AXIS><<<grid, 128, 0, st>>>(uin, uout, n, nu, gam, eps, L);
+  const dim3 blk = line_block(n, 128);
+  const int L = variant == SIM_SWEEP_MARCH_FIT
+                    ? fit_segment(sweep_march_kernel<AXIS>, n, B, 6, n, blk)
+                    : segment_length(variant);
+  sweep_march_kernel<AXIS><<<line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st>>>(uin, uout, n, nu,
+                                                                                 gam, eps, L);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1010,10 +1043,10 @@ static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, 
 template <int AXIS, int MINB>
 static sim_status launch_march2_mb(const float* uin, float* uout, int n, SArg nu, float gam,
                                    float eps, int B, cudaStream_t st) {
-  const int threads = n / 2 >= 128 ? 128 : (n / 2 >= 64 ? 64 : 32);
-  const int L = fit_segment(sweep_march2_kernel<AXIS, MINB>, n, B, 6, n / 2, threads);
-  dim3 grid(cdiv(n / 2, threads), n * B, cdiv(n, L));
-  sweep_march2_kernel<AXIS, MINB><<<grid, threads, 0, st>>>(uin, uout, n, nu, gam, eps, L);
+  const dim3 blk = line_block(n / 2, 128);
+  const int L = fit_segment(sweep_march2_kernel<AXIS, MINB>, n, B, 6, n / 2, blk);
+  sweep_march2_kernel<AXIS, MINB><<<line_grid(n / 2, n, B, blk, cdiv(n, L)), blk, 0, st>>>(
+      uin, uout, n, nu, gam, eps, L);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1124,11 +1157,13 @@ static sim_status launch_adj_final(const float* uin, const float* lout, const fl
   const uintptr_t al = reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(lout) |
                        reinterpret_cast<uintptr_t>(luh) | reinterpret_cast<uintptr_t>(lin);
   if (AXIS != 0 && n % 2 == 0 && al % 8 == 0) {  // x runs as AXIS 1 on transposed copies
-    dim3 g(cdiv(n / 2, 128), n, n * B);
-    sweep_adj_final2_kernel<AXIS, FC><<<g, 128, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
+    const dim3 blk = line_block(n / 2, 128);
+    const dim3 g(cdiv(n / 2, blk.x), cdiv(n, blk.y), n * B);
+    sweep_adj_final2_kernel<AXIS, FC><<<g, blk, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
   } else {
-    dim3 g(cdiv(n, 256), n, n * B);
-    sweep_adj_final_kernel<AXIS, FC><<<g, 256, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
+    const dim3 blk = line_block(n, 256);
+    const dim3 g(cdiv(n, blk.x), cdiv(n, blk.y), n * B);
+    sweep_adj_final_kernel<AXIS, FC><<<g, blk, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
   }
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -1142,8 +1177,9 @@ static sim_status launch_adj_march_t(const float* uin, const float* lout, float*
     set_error("internal: marching sweep adjoint needs a 5 n^3 scratch buffer per instance");
     return SIM_EINVAL;
   }
-  dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
-  sweep_adj_march_kernel<AXIS><<<g1, 128, 0, st>>>(uin, lout, scratch, n, nu, gam, eps, dnu, L);
+  const dim3 blk = line_block(n, 128);
+  sweep_adj_march_kernel<AXIS><<<line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st>>>(
+      uin, lout, scratch, n, nu, gam, eps, dnu, L);
   DH_LAUNCH_CHECK();
   return launch_adj_final<AXIS, 1 + AXIS>(uin, lout, scratch, lin, n, nu, gam, B, st);
 }
@@ -1156,8 +1192,9 @@ static sim_status launch_adj_x_transposed(const float* uin, const float* lout, f
   const size_t F5 = (size_t)5 * n * n * n * B;
   float *ut = scratch, *lt = scratch + F5, *it = scratch + 2 * F5, *luh = scratch + 3 * F5;
   DH_TRY(launch_transpose_xy(uin, ut, 5 * B, lout, lt, 5 * B, n, st));
-  dim3 g1(cdiv(n, 128), n * B, cdiv(n, L));
-  sweep_adj_march_kernel<1, 1><<<g1, 128, 0, st>>>(ut, lt, luh, n, nu, gam, eps, dnu, L);
+  const dim3 blk = line_block(n, 128);
+  sweep_adj_march_kernel<1, 1><<<line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st>>>(
+      ut, lt, luh, n, nu, gam, eps, dnu, L);
   DH_LAUNCH_CHECK();
   DH_TRY((launch_adj_final<1, 1>(ut, lt, luh, it, n, nu, gam, B, st)));
   return launch_transpose_xy(it, lin, 5 * B, nullptr, nullptr, 0, n, st);
@@ -1171,7 +1208,7 @@ static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float*
   if (variant != SIM_SWEEP_TILE) {
     const int L = variant == SIM_SWEEP_MARCH_FIT
                       ? fit_segment(sweep_adj_march_kernel<AXIS == 0 ? 1 : AXIS, AXIS == 0 ? 1 : 1 + AXIS>,
-                                    n, B, 9)
+                                    n, B, 9, n, line_block(n, 128))
                       : segment_length(variant);
     if (AXIS == 0) {
       if (!scratch) {

@@ -95,9 +95,11 @@ static sim_status fft_exec_c2r(cufftHandle h, cufftComplex* in, float* out) {
 }
 
 // ------------------------------------------------------------------ CIC geometry
-// Particle kernels run on a 3-D grid: x = blockIdx.x * blockDim.x + threadIdx.x (lattice
-// q_x), y = blockIdx.y (q_y), z = blockIdx.z (q_z); no integer division is needed to
-// recover the lattice site. Node and particle indices are 32-bit (n <= 1024).
+// Particle kernels run on a 2-D grid: x over the n^3 particles of an instance in Lagrangian
+// order (lattice x fastest), y = the instance, so every thread of a block has a particle
+// for any n (a grid of one block per lattice row left 3/4 of the threads idle at n = 32) and
+// the blocks of one instance run before the next instance's (its force field stays in L2).
+// Node and particle indices are 32-bit (n <= 1024).
 struct Cic {
   int ix[2], iy[2], iz[2];
   float wx[2], wy[2], wz[2];
@@ -123,20 +125,24 @@ struct PIdx {
   bool ok;
 };
 
-// grid (cdiv(n, threads), n, B n): blockIdx.z carries the instance and the lattice z
+// grid (cdiv(n^3, threads), B); lanes past the last particle get ok = false (and a lattice
+// site past the end, never used)
 __device__ __forceinline__ PIdx particle_index(int n) {
   PIdx r;
-  r.qx = blockIdx.x * blockDim.x + threadIdx.x;
-  r.qy = blockIdx.y;
-  r.b = blockIdx.z / n;
-  r.qz = blockIdx.z - r.b * n;
-  r.ok = r.qx < n;
-  r.p = (r.qz * n + r.qy) * n + r.qx;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nn = (unsigned)n * (unsigned)n;
+  r.b = blockIdx.y;
+  r.p = (int)t;
+  r.ok = t < nn * (unsigned)n;
+  r.qz = (int)(t / nn);
+  const unsigned rem = t - (unsigned)r.qz * nn;
+  r.qy = (int)(rem / (unsigned)n);
+  r.qx = (int)(rem - (unsigned)r.qy * (unsigned)n);
   return r;
 }
 
 static inline dim3 particle_grid(int n, int threads, int B) {
-  return dim3(cdiv(n, threads), n, n * B);
+  return dim3((unsigned)cdiv((long long)n * n * n, threads), B);
 }
 constexpr int kPT = 128;  // threads per particle block
 
@@ -190,7 +196,7 @@ __device__ __forceinline__ XPair xpair(int a0, int a1, bool ok) {
 __global__ void deposit_kernel(const float* __restrict__ s, const float* __restrict__ vals,
                                int n, float inv_dx, unsigned long long* __restrict__ acc) {
   const int N3 = n * n * n;
-  const PIdx q = particle_index(n);  // lanes past the row end stay for the warp exchange
+  const PIdx q = particle_index(n);  // lanes past the last particle stay for the warp exchange
   s += (size_t)q.b * 3 * N3;
   acc += (size_t)q.b * N3;
   Cic c;
@@ -624,7 +630,7 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
         if (!x.given) atomicAdd(lam_g4 + a1, make_float4(w1 * lp[0], w1 * lp[1], w1 * lp[2], 0.0f));
       }
     }
-  // a block never spans two instances (blockIdx.z carries the instance)
+  // a block never spans two instances (blockIdx.y carries the instance)
   if (dK.p) block_sum_atomic(dk, dK.at(q.b));
   if (ddtau.p) block_sum_atomic(dd, ddtau.at(q.b));
 }
