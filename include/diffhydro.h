@@ -267,8 +267,19 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
 
 /* Advance n_steps steps from the initial state (the handle must be fresh from sim_init or
  * sim_reset), storing a checkpoint of the state every ckpt_every steps for
- * sim_run_adjoint (Sec. 2.3.5: checkpoints every 6 steps in the paper). */
+ * sim_run_adjoint (Sec. 2.3.5: checkpoints every 6 steps in the paper). Once the handle
+ * holds the reverse pass's tape (after its first sim_run_adjoint) and tape recording is on
+ * (sim_set_tape_recording), the run also records the checkpoint segment that ends it on the
+ * tape, so that the next sim_run_adjoint does not recompute that segment; the results are
+ * the same either way. */
 sim_status sim_run(sim_t* h, int32_t n_steps);
+
+/* on != 0 (the default): sim_run records its last checkpoint segment on the tape when the
+ * handle holds one (a few extra device copies per recorded step, one segment less to
+ * recompute in the next sim_run_adjoint). on == 0: runs record nothing, for handles that
+ * mostly run forward. sim_fli_step and sim_posterior always record (their reverse pass
+ * follows). SIM_EINVAL on a NULL handle. */
+sim_status sim_set_tape_recording(sim_t* h, int32_t on);
 
 /* Gradient of a scalar loss through the whole run made by sim_run and through the
  * initial conditions. dL_dgas (5 n^3) and dL_dpart (6 n^3: d/ds then d/dp) are the

@@ -91,6 +91,7 @@ SIGNATURES = {
     "sim_group_reset": (ctypes.c_int, [_P]),
     "sim_group_destroy": (None, [_P]),
     "sim_set_graphs": (ctypes.c_int, [_P, _I32]),
+    "sim_set_tape_recording": (ctypes.c_int, [_P, _I32]),
     "sim_kernel_timing": (ctypes.c_int, [_P, _I32]),
     "sim_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
     "sim_step": (ctypes.c_int, [_P]),

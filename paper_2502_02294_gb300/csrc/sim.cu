@@ -88,13 +88,15 @@ constexpr int kTapeFloatsPerCell = 6 * 5 + 5 * 3 + 1;
 // Host-side state that a call changes; a replayed graph must start from and end in the
 // same values as the captured call.
 struct HostState {
-  int step, init_step, prev_step, ckpt_count;
+  int step, init_step, prev_step, ckpt_count, tape_first, tape_end;
   bool ics_valid;
+  bool taped;  // a tape to record on exists (read, not restored: a run records only then)
   float *gas, *gas2, *w_gas, *w_gas2, *lam_gas, *lam_tmp, *lamG0, *lamG1;
   std::vector<int> ckpt_step;
   bool operator==(const HostState& o) const {
     return step == o.step && init_step == o.init_step && prev_step == o.prev_step &&
-           ckpt_count == o.ckpt_count && ics_valid == o.ics_valid && gas == o.gas &&
+           ckpt_count == o.ckpt_count && tape_first == o.tape_first &&
+           tape_end == o.tape_end && ics_valid == o.ics_valid && taped == o.taped && gas == o.gas &&
            gas2 == o.gas2 && w_gas == o.w_gas && w_gas2 == o.w_gas2 && lam_gas == o.lam_gas &&
            lam_tmp == o.lam_tmp && lamG0 == o.lamG0 && lamG1 == o.lamG1 &&
            std::vector<int>(ckpt_step.begin(), ckpt_step.begin() + ckpt_count) ==
@@ -160,6 +162,10 @@ struct sim_s {
   // tape and adjoint scratch (allocated on first use)
   float* tape = nullptr;
   int tape_cap = 0;
+  // steps [tape_first, tape_end) of the last run, recorded on the tape by the run itself
+  // (its last checkpoint segment), or -1: the reverse pass then needs no recompute of it
+  int tape_first = -1, tape_end = -1;
+  bool tape_recording = true;  // sim_set_tape_recording
   float *w_gas = nullptr, *w_gas2 = nullptr, *w_s = nullptr, *w_p = nullptr, *w_g = nullptr;
   float *lam_gas = nullptr, *lam_tmp = nullptr, *lam_s = nullptr, *lam_p = nullptr;
   float *lamG0 = nullptr, *lamG1 = nullptr, *lam_delta = nullptr, *lam4 = nullptr;
@@ -228,7 +234,10 @@ static HostState snapshot(const sim_t* h) {
   s.init_step = h->init_step;
   s.prev_step = h->prev_step;
   s.ckpt_count = h->ckpt_count;
+  s.tape_first = h->tape_first;
+  s.tape_end = h->tape_end;
   s.ics_valid = h->ics_valid;
+  s.taped = h->tape != nullptr;
   s.gas = h->gas;
   s.gas2 = h->gas2;
   s.w_gas = h->w_gas;
@@ -246,6 +255,8 @@ static void restore(sim_t* h, const HostState& s) {
   h->init_step = s.init_step;
   h->prev_step = s.prev_step;
   h->ckpt_count = s.ckpt_count;
+  h->tape_first = s.tape_first;
+  h->tape_end = s.tape_end;
   h->ics_valid = s.ics_valid;
   h->gas = s.gas;
   h->gas2 = s.gas2;
@@ -458,15 +469,20 @@ static sim_status record_diag(sim_t* h, int idx, const float* gas, const float* 
 // merged_in: the step opens with the merged kick K2_{i-1} + K1_i (the previous step ran
 // without its closing kick), which also does the previous step's star readout;
 // kick_out: the step ends with its closing half kick K2_i.
+// T: the step's tape slot (stage inputs recorded, outputs out of place) or NULL. primary:
+// a step of the run itself (star readout, star field, events, diagnostics), as every step
+// without a tape is; a recompute for the reverse pass (T set, primary false) has none of
+// these side effects.
 static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, float* s, float* p,
                                float* g, const TapeSlot* T, bool merged_in = false,
-                               bool kick_out = true) {
+                               bool kick_out = true, bool primary = false) {
   const sim_params& P = h->prm;
   const int B = h->B;
   cudaStream_t st = h->st;
   const size_t gb = 5 * B * h->N3 * sizeof(float), vb = 3 * B * h->N3 * sizeof(float);
   const SArg K1 = sc(h, i, merged_in ? SC_KM : SC_K1), K2 = sc(h, i, SC_K2);
-  float* zh_prev = (merged_in && P.subgrid_on && !T) ? h->zhat : nullptr;
+  const bool fwd = !T || primary;
+  float* zh_prev = (merged_in && P.subgrid_on && fwd) ? h->zhat : nullptr;
   if (T) {
     DH_TRY(dcopy(T->U0, *gas, gb, st));
     DH_TRY(dcopy(T->s0, s, vb, st));
@@ -507,9 +523,9 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   float* zh = nullptr;
   if (P.subgrid_on) {
     float* out = T ? T->Usg : cur;
-    zh = T ? nullptr : h->zhat;
+    zh = fwd ? h->zhat : nullptr;
     DH_TRY(timed(h, SIM_KT_SUBGRID, [&] {
-      return launch_subgrid(cur, out, sub_at(h, i), zh, T ? nullptr : h->events, h->N3, B, st,
+      return launch_subgrid(cur, out, sub_at(h, i), zh, fwd ? h->events : nullptr, h->N3, B, st,
                             T ? T->gd : nullptr);
     }));
     cur = out;
@@ -542,8 +558,8 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, B * h->N3, st));
   // 6. learned correction of the gas fields (solver in the loop, Sec. 4)
   if (h->closure) DH_TRY(closure_apply(h->closure, *gas, h->n, B, st));
-  // 7. diagnostics of the state after the step (eager steps only, not the recompute)
-  if (h->diag_on && !T)
+  // 7. diagnostics of the state after the step (steps of the run, not the recompute)
+  if (h->diag_on && fwd)
     DH_TRY(record_diag(h, i + 1, *gas, p, zh, P.subgrid_on ? h->events : nullptr));
   return SIM_OK;
 }
@@ -577,6 +593,7 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
         if (a == h->tape) a = nullptr;
     }
     h->tape = nullptr;
+    h->tape_first = h->tape_end = -1;
     DH_TRY(dalloc_t(h, &h->tape, (size_t)tape_steps * kTapeFloatsPerCell * N3));
     h->tape_cap = tape_steps;
   }
@@ -902,7 +919,10 @@ static sim_status load_noise(sim_t* h, const float* noise) {
   return SIM_OK;
 }
 
-static void clear_checkpoints(sim_t* h) { h->ckpt_count = 0; }
+static void clear_checkpoints(sim_t* h) {
+  h->ckpt_count = 0;
+  h->tape_first = h->tape_end = -1;
+}
 
 static sim_status ensure_ckpt_pool(sim_t* h, int count) {
   while ((int)h->ckpt_pool.size() < count) {
@@ -1011,12 +1031,19 @@ static sim_status run_prepare(sim_t* h, int n_steps) {
 }
 
 // n_steps forward steps with a checkpoint every ckpt_every steps (Sec. 2.3.5).
-static sim_status run_body(sim_t* h, int n_steps) {
+static sim_status run_body(sim_t* h, int n_steps, bool force_record = false) {
   const int last = h->step + n_steps;
+  const int every = h->prm.ckpt_every;
+  // Once the handle holds a tape (it has run a reverse pass), the run records the checkpoint
+  // segment that ends it as it goes, so the next reverse pass starts without recomputing it.
+  const int seg_first = n_steps > 0 ? h->init_step + (last - 1 - h->init_step) / every * every : 0;
+  const bool record = n_steps > 0 && h->tape && h->tape_cap >= every && !h->closure &&
+                      seg_first >= h->step && (h->tape_recording || force_record);
+  h->tape_first = h->tape_end = -1;
   if (h->diag_on && n_steps > 0)
     DH_TRY(record_diag(h, h->step, h->gas, h->p, nullptr, nullptr));
   for (int k = 0; k < n_steps; ++k) {
-    const int rel = h->step - h->init_step, every = h->prm.ckpt_every;
+    const int rel = h->step - h->init_step;
     if (rel % every == 0) DH_TRY(store_checkpoint(h));
     // kicks merge inside a checkpoint segment (not with a closure, which acts on the state
     // after the closing kick, nor with the CFL watchdog or the diagnostics, which read every
@@ -1024,8 +1051,10 @@ static sim_status run_body(sim_t* h, int n_steps) {
     const bool plain = kicks_apart(h);
     const bool merged_in = !plain && rel % every != 0;
     const bool kick_out = plain || h->step + 1 == last || (rel + 1) % every == 0;
-    DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, nullptr, merged_in,
-                        kick_out));
+    const bool rec = record && h->step >= seg_first;
+    const TapeSlot T = rec ? tape_slot(h, h->step - seg_first) : TapeSlot{};
+    DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, rec ? &T : nullptr,
+                        merged_in, kick_out, true));
     h->step += 1;
     if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
       double c = 0;
@@ -1038,6 +1067,10 @@ static sim_status run_body(sim_t* h, int n_steps) {
     }
   }
   h->prev_step = -1;
+  if (record) {
+    h->tape_first = seg_first;
+    h->tape_end = last;
+  }
   return SIM_OK;
 }
 
@@ -1083,21 +1116,27 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
     DH_TRY(dzero(h->lam_p, 3 * N3 * sizeof(float), st));
   }
   DH_TRY(dzero(h->lamG1, 4 * N3 * sizeof(float), st));
+  // the segment the run recorded on the tape needs no recompute; the recompute of the other
+  // segments overwrites the tape
+  const int taped_first = h->tape_first, taped_end = h->tape_end;
+  h->tape_first = h->tape_end = -1;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int first = h->ckpt_step[seg];
     const int end = seg + 1 < nseg ? h->ckpt_step[seg + 1] : last;
-    const float* c = h->ckpt_pool[seg];
-    DH_TRY(dcopy(h->w_gas, c, 5 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
-    DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
-    DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, first), h->w_g));
     // the same kick merging as the forward run: opening kicks merged after the segment's
     // first step, the closing kick only at the segment's end
     const bool plain = kicks_apart(h);
-    for (int i = first; i < end; ++i) {
-      const TapeSlot T = tape_slot(h, i - first);
-      DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T,
-                          !plain && i != first, plain || i == end - 1));
+    if (!(seg == nseg - 1 && first == taped_first && end == taped_end)) {
+      const float* c = h->ckpt_pool[seg];
+      DH_TRY(dcopy(h->w_gas, c, 5 * N3 * sizeof(float), st));
+      DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
+      DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
+      DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, first), h->w_g));
+      for (int i = first; i < end; ++i) {
+        const TapeSlot T = tape_slot(h, i - first);
+        DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T,
+                            !plain && i != first, plain || i == end - 1));
+      }
     }
     for (int i = end - 1; i >= first; --i)
       DH_TRY(reverse_step(h, i, tape_slot(h, i - first), h->dslots + (size_t)i * B * SL_N,
@@ -1429,6 +1468,7 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
   sim_status r = ensure_adjoint_buffers(h, 1);
   if (r != SIM_OK) return fail(h, r);
   const TapeSlot T = tape_slot(h, 0);
+  h->tape_first = h->tape_end = -1;
   double* slot = h->dslots;
   auto run = [&]() -> sim_status {
     DH_TRY(dzero(h->dslots, 2 * (size_t)B * SL_N * sizeof(double), st));
@@ -1455,13 +1495,20 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
   return fail(h, run());
 }
 
+sim_status sim_set_tape_recording(sim_t* h, int32_t on) {
+  if (!h) return SIM_EINVAL;
+  h->tape_recording = on != 0;
+  return SIM_OK;
+}
+
 sim_status sim_run(sim_t* h, int32_t n_steps) {
   if (!h) return SIM_EINVAL;
   sim_status r = run_prepare(h, n_steps);
   if (r != SIM_OK) return fail(h, r);
   // the CFL watchdog reads back every step: never captured
   if (h->prm.cfl_max > 0) return fail(h, run_body(h, n_steps));
-  return fail(h, run_maybe_graph(h, 1, {(uintptr_t)n_steps}, [&] { return run_body(h, n_steps); }));
+  return fail(h, run_maybe_graph(h, 1, {(uintptr_t)n_steps, (uintptr_t)h->tape_recording},
+                                 [&] { return run_body(h, n_steps); }));
 }
 
 sim_status sim_run_adjoint(sim_t* h, const float* dL_dgas, const float* dL_dpart,
@@ -1538,8 +1585,11 @@ static sim_status posterior_data_term(sim_t* h, int obs, const float* noise, con
   h->ics_valid = true;
   h->init_step = 0;
   DH_TRY(reset_to_init(h));
+  // the reverse-pass buffers first, so that the run records its last segment on the tape
+  DH_TRY(ensure_adjoint_buffers(h, h->prm.ckpt_every));
   DH_TRY(run_prepare(h, h->prm.n_steps));
-  DH_TRY(run_maybe_graph(h, 1, {(uintptr_t)h->prm.n_steps}, [&] { return run_body(h, h->prm.n_steps); }));
+  DH_TRY(run_maybe_graph(h, 1, {(uintptr_t)h->prm.n_steps, (uintptr_t)1},
+                         [&] { return run_body(h, h->prm.n_steps, true); }));
   DH_TRY(field_loss(h, obs, data, 0.5 / (sigma_n * sigma_n), h->fli_dL, loss));
   DH_TRY(run_adjoint_prepare(h, h->fli_g, h->fli_dpar));
   const std::vector<uintptr_t> key = {(uintptr_t)h->fli_dL, (uintptr_t)0, (uintptr_t)h->fli_g,
@@ -1933,7 +1983,10 @@ sim_status sim_group_run(sim_group_t* g) {
     DH_TRY(fail(h, run_prepare(h, h->prm.n_steps - h->step)));
   }
   std::vector<uintptr_t> key;
-  for (sim_t* h : g->m) key.push_back((uintptr_t)(h->prm.n_steps - h->step));
+  for (sim_t* h : g->m) {
+    key.push_back((uintptr_t)(h->prm.n_steps - h->step));
+    key.push_back((uintptr_t)h->tape_recording);
+  }
   return group_graph(g, 1, key, [&](size_t k) {
     sim_t* h = g->m[k];
     return fail(h, run_body(h, h->prm.n_steps - h->step));

@@ -101,6 +101,7 @@ def test_null_arguments_rejected(dh):
     assert L.sim_diagnostics(None, 0, None) == E
     assert L.sim_closure_set_wait_limit(None, 0) == E
     assert L.sim_deposit_cic_static(None, None, 8, 8.0, None, None) == E
+    assert L.sim_set_tape_recording(None, 1) == E
 
 
 def test_no_unresolved_library_symbols(dh):

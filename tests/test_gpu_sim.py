@@ -271,3 +271,47 @@ def test_graph_replay_matches_eager(dh):
         assert torch.equal(gas, ref[2]), (g, rep)
         assert rel_l2(dn, ref[3]) < 1e-5, (g, rep)
         assert rel_l2(dp, ref[4]) < 1e-5, (g, rep)
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_run_records_its_last_segment(dh, graphs):
+    """Once a handle holds a tape (after its first reverse pass), sim_run records its last
+    checkpoint segment as it goes and the next sim_run_adjoint skips that segment's
+    recompute: the run's state, stars, events and diagnostics are those of a run without
+    the tape, the gradients agree (float atomics in the reverse pass: 1e-5), and the reverse
+    pass launches fewer kernels."""
+    n = 16
+    p = dh.default_params(n=n, box=16.0, n_steps=10, ckpt_every=4, a_start=0.1, a_end=0.4,
+                          rms_ref=0.15, **SUB)
+    wg, _ = f32(synth.white_noise(n, 23))
+    tg, _ = f32(0.16 * (1 + 0.2 * synth.field(n, 24)))
+    sim = dh.Simulation(p, wg)
+    sim.set_graphs(bool(graphs))
+    sim.set_diagnostics(True)
+    runs = []
+    for rep in range(3):
+        sim.reset()
+        sim.run()
+        st = {k: v.clone() for k, v in sim.state().items() if torch.is_tensor(v)}
+        diag = [sim.diagnostics(k) for k in range(p.n_steps + 1)]
+        dL, _ = sim.loss_density(tg, 1.0 / n ** 3)
+        torch.cuda.synchronize()
+        l0 = dh.lib.sim_kernel_launches()
+        dnoise, dpar = sim.run_adjoint(dL)
+        torch.cuda.synchronize()
+        runs.append((st, diag, dnoise.clone(), dpar.clone(), dh.lib.sim_kernel_launches() - l0))
+        if rep == 1:
+            sim.set_tape_recording(False)  # the third run records nothing
+    ref = runs[0]
+    for rep, (st, diag, dn, dp, launches) in enumerate(runs[1:], 1):
+        for k in ref[0]:
+            assert torch.equal(st[k], ref[0][k]), k
+        assert diag == ref[1]
+        assert rel_l2(dn, ref[2]) < 1e-5
+        assert rel_l2(dp, ref[3]) < 1e-5
+        # segments [0, 4), [4, 8), [8, 10): the last one is recomputed only without recording
+        if rep == 1:
+            assert launches < ref[4], (launches, ref[4])
+        else:
+            assert launches == ref[4], (launches, ref[4])
+    sim.close()
