@@ -57,8 +57,8 @@ SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, i
 # the ncu captures summarised in profiles/ (128^3, cold cache): forward sweep, the packed x
 # tile (43.8 MB) and the paired y / z forms (44.0, 44.0 MB) averaged; adjoint sweep (x, y, z
 # average of the marching pair with fitted segments, x with its transposes)
-# (423.5 + 259.0 + 259.9) / 3 MB; None where no capture of the current kernel exists
-TRAFFIC_BYTES_PER_CELL = {"sweep": 20.95, "sweep_adjoint": 149.8}
+# (425.1 + 260.2 + 261.1) / 3 MB; None where no capture of the current kernel exists
+TRAFFIC_BYTES_PER_CELL = {"sweep": 20.95, "sweep_adjoint": 150.4}
 # the kernel forms (SWEEP_* per axis x, y, z) those captures measured
 PROFILED_VARIANTS = {"sweep": [1, 5, 5], "sweep_adjoint": [4, 4, 4]}
 # algorithmic bytes per cell of one timed launch group of each class (one particle per cell)
@@ -407,6 +407,10 @@ def main():
                     help="skip the batched parameter-sampling measurement")
     ap.add_argument("--no-closure", action="store_true",
                     help="skip the learned-closure training and 256^3 application")
+    ap.add_argument("--sweep-variants", default=None,
+                    help="x,y,z forward and x,y,z adjoint sweep forms (SWEEP_* codes, six "
+                         "comma-separated) instead of the autotuner's choice, e.g. for a "
+                         "profiler run, under which the autotuner's timings are distorted")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured graphs")
     args = ap.parse_args()
@@ -438,7 +442,14 @@ def main():
     torch.cuda.set_stream(stream)
     sim = dh.Simulation(p, noise)
     # the library's autotuner picks the sweep kernels for this grid (timed on the ICs)
-    variants = sim.autotune(reps=3)
+    if args.sweep_variants:
+        v = [int(t) for t in args.sweep_variants.split(",")]
+        if len(v) != 6:
+            raise SystemExit("--sweep-variants takes six comma-separated codes")
+        sim.set_sweep_variants(v[:3], v[3:])
+        variants = (v[:3], v[3:])
+    else:
+        variants = sim.autotune(reps=3)
     if not args.no_graphs:
         dh._lib.check(dh.lib.sim_set_graphs(sim.h, 1), "sim_set_graphs", sim.h)
     # the field-level-inference mock (Sec. 3.2): the final gas density of the run from the
