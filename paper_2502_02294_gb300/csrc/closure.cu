@@ -20,7 +20,8 @@
 // Backward: the gradient with respect to a layer's input is the same convolution with the
 // taps mirrored and each tap's matrix transposed (same kernel, other weight packing), its
 // epilogue multiplied by GELU' of the previous layer's pre-activation. The weight gradient
-// (a reduction over voxels of 27 rank-1 updates of 16 x 16) runs on the CUDA cores.
+// (a reduction over voxels of 27 rank-1 updates of 16 x 16) is a third tensor-core kernel:
+// M = (tap, input channel), N = output channel, K = voxels.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -610,90 +611,218 @@ static sim_status launch_conv(int mode, ConvArgs a, int B, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ weight gradient
-// dW[tap][ci][co] += sum_v in[v + off(tap)][ci] dz[v][co]; db[co] += sum_v dz[v][co].
-// One CTA per (instance, plane, chunk of L lines); thread (ci, co) keeps 27 sums.
-__global__ void __launch_bounds__(256) conv_dw_kernel(const bf16* __restrict__ in,
-                                                      const bf16* __restrict__ dz, int n, int L,
-                                                      float* __restrict__ dW,
-                                                      float* __restrict__ db) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  const int P = n + 2;
-  const long long N3 = (long long)n * n * n;
-  const int b = blockIdx.z, z = blockIdx.y, y0 = blockIdx.x * L;
-  bf16* si = reinterpret_cast<bf16*>(smem);        // [3][L + 2][P][16]
-  bf16* sd = si + (size_t)3 * (L + 2) * P * CH;     // [L][n][16]
-  in += (size_t)b * N3 * CH;
-  dz += (size_t)b * N3 * CH;
-  const int nreg = 3 * (L + 2) * P;
-  for (int i = threadIdx.x; i < nreg; i += 256) {
-    const int pz = i / ((L + 2) * P);
-    const int rem = i - pz * (L + 2) * P;
-    const int ly = rem / P, px = rem - ly * P;
-    const int gx = wrapi(px - 1, n), gy = wrapi(y0 - 1 + ly, n), gz = wrapi(z - 1 + pz, n);
-    const long long line = (long long)gz * n + gy;
-    uint4* dst = reinterpret_cast<uint4*>(si + (size_t)i * CH);
-    dst[0] = __ldg(reinterpret_cast<const uint4*>(in + act_off(line, n, 0, gx)));
-    dst[1] = __ldg(reinterpret_cast<const uint4*>(in + act_off(line, n, 1, gx)));
-  }
-  for (int i = threadIdx.x; i < L * n; i += 256) {
-    const int ly = i / n, x = i - ly * n;
-    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
-    if (y0 + ly < n) {
-      const long long line = (long long)z * n + y0 + ly;
-      lo = __ldg(reinterpret_cast<const uint4*>(dz + act_off(line, n, 0, x)));
-      hi = __ldg(reinterpret_cast<const uint4*>(dz + act_off(line, n, 1, x)));
-    }
-    uint4* dst = reinterpret_cast<uint4*>(sd + (size_t)i * CH);
-    dst[0] = lo;
-    dst[1] = hi;
-  }
-  __syncthreads();
-  const int ci = threadIdx.x >> 4, co = threadIdx.x & 15;
-  float acc[27];
-#pragma unroll
-  for (int t = 0; t < 27; ++t) acc[t] = 0.0f;
-  float bacc = 0.0f;
-  for (int ly = 0; ly < L; ++ly) {
-    for (int x = 0; x < n; ++x) {
-      const float d = __bfloat162float(sd[((size_t)ly * n + x) * CH + co]);
-      bacc += d;
-#pragma unroll
-      for (int t = 0; t < 27; ++t) {
-        const int kz = t / 9, ky = (t / 3) % 3, kx = t % 3;
-        const float v = __bfloat162float(si[(((size_t)kz * (L + 2) + ly + ky) * P + x + kx) * CH + ci]);
-        acc[t] = fmaf(v, d, acc[t]);
-      }
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < 27; ++t) atomicAdd(dW + (t * CH + ci) * CH + co, acc[t]);
-  if (ci == 0) atomicAdd(db + co, bacc);
+// dW[tap][ci][co] = sum_v in[v + off(tap)][ci] dz[v][co] and db[co] = sum_v dz[v][co], as
+// tensor-core GEMMs with M = (tap, ci), N = co and K = voxels: 16 consecutive x positions of
+// one line per MMA step (a K block). For every K block the producer warps write into a
+// shared-memory stage the block's 27 shifted input tiles (16 channels x 16 voxels each: tap t
+// at rows 16 (t mod 8) .. + 15 of the M = 128 operand of tap group t / 8) and its dz tile
+// (N = 16 rows), every one transposed on the way into the no-swizzle K-major layout (a row is
+// 8 voxels of one channel: stmatrix .trans from the fragment of 4-byte channel pairs). One
+// thread issues the stage's four M128 N16 K16 MMAs (tap groups 0..3) into four 16-column TMEM
+// accumulators that collect all of the CTA's K blocks; the epilogue adds them to dW / db with
+// vector atomics. Row 48 of group 3 (tap slot 3, channel 0) is a constant row of ones, so its
+// accumulator row is db; the other unused rows of group 3 stay zero. Voxels past the end of a
+// line (n not a multiple of 16) have dz = 0.
+constexpr int DW_PRODUCERS = 8;                     // producer warps; one more issues the MMAs
+constexpr int DW_THREADS = 32 * (DW_PRODUCERS + 1);
+constexpr int DW_STAGES = 3;
+constexpr int DW_A_BYTES = 4 * 4096;                // four tap groups x 128 rows x 32 bytes
+constexpr int DW_STAGE_BYTES = DW_A_BYTES + 512;    // + the dz tile: 16 rows x 32 bytes
+constexpr int DW_SMEM = DW_STAGES * DW_STAGE_BYTES + (2 * DW_STAGES + 1) * 8 + 16;
+constexpr int DW_CTAS_PER_SM = 4;
+
+struct DwArgs {
+  const bf16* in;  // layer input [B][n][n][2][n][8]
+  const bf16* dz;  // gradient at the layer's output, same layout
+  int n, nxb;      // grid size, K blocks per line
+  long long kblocks, per_cta;
+  float* dW;  // [27][16][16], accumulated
+  float* db;  // [16], accumulated
+  int* err;
+  unsigned long long wait_ns;
+};
+
+// four 8x8 bfloat16 matrices from the mma fragment (lane 4 r + q: row r, columns 2q, 2q + 1
+// in register j of matrix j) stored transposed: lane l gives the address of row l mod 8 of
+// matrix l / 8
+__device__ __forceinline__ void stmatrix_trans4(uint32_t addr, const uint32_t v[4]) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
 }
 
-static int dw_lines(int n) {
-  for (int L = 8; L > 1; L /= 2) {
-    const size_t sm = ((size_t)3 * (L + 2) * (n + 2) + (size_t)L * n) * CH * 2;
-    if (sm <= 112 * 1024) return L;
+__global__ void __launch_bounds__(DW_THREADS) conv_dw_kernel(DwArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + DW_STAGES * DW_STAGE_BYTES);
+  uint64_t* empty = full + DW_STAGES;
+  uint64_t* done = empty + DW_STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  int* sflag = reinterpret_cast<int*>(tslot + 1);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int n = a.n, nxb = a.nxb;
+  const long long kb0 = (long long)blockIdx.x * a.per_cta;
+  const long long kb1 = kb0 + a.per_cta < a.kblocks ? kb0 + a.per_cta : a.kblocks;
+  const int nkb = (int)(kb1 - kb0);  // >= 1 by the launch
+  const uint32_t s0 = smem_u32(smem);
+  const unsigned long long limit = a.wait_ns;
+
+  for (int i = tid; i < DW_STAGES * DW_STAGE_BYTES / 16; i += DW_THREADS)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  if (tid < 2 * DW_STAGES) {
+    // group 3, M group 6 (tap slot 3, channels 0-7), K chunk tid & 1, row 0: bfloat16 ones
+    const int st = tid >> 1, kc = tid & 1;
+    *reinterpret_cast<uint4*>(smem + st * DW_STAGE_BYTES + 3 * 4096 + 6 * 256 + kc * 128) =
+        make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
   }
-  return 1;
+  if (tid == 0) {
+    for (int st = 0; st < DW_STAGES; ++st) {
+      mbar_init(full + st, DW_PRODUCERS);
+      mbar_init(empty + st, 1);
+    }
+    mbar_init(done, 1);
+    *sflag = 0;
+  }
+  if (w == 0) tmem_alloc_warp(tslot, 64u);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (w < DW_PRODUCERS) {
+    const long long N3 = (long long)n * n * n;
+    const int r = lane >> 2, q = lane & 3;  // fragment row (voxel of an 8-voxel chunk), pair
+    const int mj = lane >> 3, row = lane & 7;
+    // matrix j = 2 h + kc: channel half h, K chunk kc (voxels 8 kc .. 8 kc + 7)
+    const uint32_t row_off = (uint32_t)((mj >> 1) * 256 + (mj & 1) * 128 + row * 16);
+    for (int k = 0; k < nkb; ++k) {
+      const int st = k % DW_STAGES;
+      uint32_t ok = 1;
+      if (k >= DW_STAGES && lane == 0) ok = mbar_wait_ns(empty + st, ((k / DW_STAGES) - 1) & 1, limit);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) *sflag = 1;
+        break;
+      }
+      long long kb = kb0 + k;
+      const int xb = (int)(kb % nxb);
+      kb /= nxb;
+      const int y = (int)(kb % n);
+      kb /= n;
+      const int z = (int)(kb % n);
+      const int b = (int)(kb / n);
+      const int x0 = 16 * xb;
+      const uint32_t stage = s0 + (uint32_t)(st * DW_STAGE_BYTES);
+      const bf16* inb = a.in + (size_t)b * N3 * CH;
+      const bf16* dzb = a.dz + (size_t)b * N3 * CH;
+      for (int j = w; j < 28; j += DW_PRODUCERS) {
+        uint32_t v[4];
+        uint32_t dst;
+        if (j < 27) {
+          const int ddz = j / 9 - 1, ddy = (j / 3) % 3 - 1, ddx = j % 3 - 1;
+          const long long line = (long long)wrapi(z + ddz, n) * n + wrapi(y + ddy, n);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int x = wrapi(x0 + 8 * (m & 1) + r + ddx, n);
+            v[m] = __ldg(reinterpret_cast<const unsigned int*>(inb + act_off(line, n, m >> 1, x) + 2 * q));
+          }
+          dst = stage + (uint32_t)((j >> 3) * 4096 + (j & 7) * 512);
+        } else {
+          const long long line = (long long)z * n + y;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int x = x0 + 8 * (m & 1) + r;
+            v[m] = x < n ? __ldg(reinterpret_cast<const unsigned int*>(dzb + act_off(line, n, m >> 1, x) + 2 * q))
+                         : 0u;
+          }
+          dst = stage + (uint32_t)DW_A_BYTES;
+        }
+        stmatrix_trans4(dst + row_off, v);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        uint64_t state;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+                     : "=l"(state)
+                     : "r"(smem_u32(full + st))
+                     : "memory");
+        (void)state;
+      }
+    }
+  } else if (lane == 0) {
+    // ---- MMA issuer: the stage's four tap groups, then release the stage
+    const uint32_t idesc = umma_idesc_bf16(128, 16);
+    for (int k = 0; k < nkb; ++k) {
+      const int st = k % DW_STAGES;
+      if (!mbar_wait_ns(full + st, (k / DW_STAGES) & 1, limit)) {
+        *sflag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t stage = s0 + (uint32_t)(st * DW_STAGE_BYTES);
+      const uint64_t bdesc = umma_desc(stage + DW_A_BYTES, 128u, 256u);
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+        umma_bf16(tmem + 16u * g, umma_desc(stage + 4096u * g, 128u, 256u), bdesc, idesc, k > 0 ? 1u : 0u);
+      umma_commit(empty + st);
+    }
+    // completes once every MMA issued above has; waited for before TMEM is read or freed
+    umma_commit(done);
+    if (!mbar_wait_ns(done, 0, kDrainNs)) *sflag = 1;
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (w < 4 && *sflag == 0) {
+    // lane 32 w + l of TMEM = row m: tap slot m / 16 of each group, channel m mod 16
+    const int m = 32 * w + lane, slot = m >> 4, ci = m & 15;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      float acc[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * w) << 16) + 16u * g, acc);
+      const int t = 8 * g + slot;
+      float* dst = t < 27 ? a.dW + (size_t)(t * CH + ci) * CH : (t == 27 && ci == 0 ? a.db : nullptr);
+      if (dst)
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4)
+          atomicAdd(reinterpret_cast<float4*>(dst) + c4,
+                    make_float4(acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *sflag) atomicExch(a.err, 1);
+  if (w == 0) tmem_dealloc_warp(tmem, 64u);
 }
 
 static sim_status launch_dw(const bf16* in, const bf16* dz, int n, int B, float* dW, float* db,
-                            cudaStream_t st) {
-  const int L = dw_lines(n);
-  const size_t sm = ((size_t)3 * (L + 2) * (n + 2) + (size_t)L * n) * CH * 2;
-  if (sm > 200 * 1024) {
-    set_error("closure: weight gradient at n = %d needs too much shared memory", n);
-    return SIM_EINVAL;
-  }
+                            int* err, unsigned long long wait_ns, cudaStream_t st) {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
   DH_CUDA_TRY(cudaGetDevice(&dev));
   if (!(done.load() & (1ull << (dev & 63)))) {
-    DH_CUDA_TRY(cudaFuncSetAttribute(conv_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DH_CUDA_TRY(cudaFuncSetAttribute(conv_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM));
     done.fetch_or(1ull << (dev & 63));
   }
-  conv_dw_kernel<<<dim3(cdiv(n, L), n, B), 256, sm, st>>>(in, dz, n, L, dW, db);
+  int sms = 0;
+  DH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DwArgs a;
+  a.in = in;
+  a.dz = dz;
+  a.n = n;
+  a.nxb = cdiv(n, 16);
+  a.kblocks = (long long)B * n * n * a.nxb;
+  const long long ctas = std::max(1, sms * DW_CTAS_PER_SM);
+  a.per_cta = (a.kblocks + ctas - 1) / ctas;
+  a.dW = dW;
+  a.db = db;
+  a.err = err;
+  a.wait_ns = wait_ns;
+  const int grid = (int)((a.kblocks + a.per_cta - 1) / a.per_cta);
+  conv_dw_kernel<<<grid, DW_THREADS, DW_SMEM, st>>>(a);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -915,7 +1044,8 @@ static sim_status closure_backprop(sim_closure_s* c, const float* gas, const flo
   bf16* dcur = c->d1;
   bf16* dnext = c->d2;
   for (int l = 3; l >= 0; --l) {
-    DH_TRY(launch_dw(acts[l], dcur, n, B, c->grad + (size_t)l * WL, c->grad + NL * WL + l * CH, st));
+    DH_TRY(launch_dw(acts[l], dcur, n, B, c->grad + (size_t)l * WL, c->grad + NL * WL + l * CH,
+                     c->err, c->wait_ns, st));
     if (l == 0) break;
     ConvArgs a = conv_args(c, l, true, dcur, n);
     a.out = dnext;

@@ -130,7 +130,7 @@ def test_weights_round_trip(dh):
     c.close()
 
 
-@pytest.mark.parametrize("n", [8, 20])
+@pytest.mark.parametrize("n", [8, 20, 33])
 def test_gradient_matches_oracle(dh, n):
     w = _weights(10)
     c = _closure(dh, w)
