@@ -51,6 +51,8 @@ FLI_TRUTH_SEED = 7
 FLI_NOISE_FRAC = 0.1
 FLI_LR = 0.003
 FLI_ITERS = 200
+TAPE_FLOATS_PER_CELL = 46      # floats per cell of one recorded step (six gas states, s0, p0,
+                               # g0, s1, g1 and the Gumbel difference)
 SWEEP_BYTES_PER_CELL = 40      # sweep: 5 float32 fields read + 5 written
 SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, input adjoint written
 # DRAM bytes per cell of one launch group (dram__bytes_read.sum + dram__bytes_write.sum) from
@@ -411,6 +413,8 @@ def main():
                     help="x,y,z forward and x,y,z adjoint sweep forms (SWEEP_* codes, six "
                          "comma-separated) instead of the autotuner's choice, e.g. for a "
                          "profiler run, under which the autotuner's timings are distorted")
+    ap.add_argument("--no-full-tape", action="store_true",
+                    help="skip the variant that records every segment's tape during the run")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel eagerly instead of replaying captured graphs")
     args = ap.parse_args()
@@ -505,7 +509,7 @@ def main():
     clk = clocks.stop()
     ms = statistics.mean(times)
     # ---- forward-only timing (runs that record no tape for a reverse pass)
-    sim.set_tape_recording(False)
+    sim.set_tape_recording(0)
     sim.reinit(noise)
     sim.run()  # untimed: captures this form's graph
     fwd_times = []
@@ -519,7 +523,7 @@ def main():
         e1.synchronize()
         fwd_times.append(e0.elapsed_time(e1))
     fwd_ms = statistics.mean(fwd_times)
-    sim.set_tape_recording(True)
+    sim.set_tape_recording(1)
     # ---- end to end through host buffers
     host_x = noise.cpu().pin_memory()
     host_out = torch.empty_like(host_x).pin_memory()
@@ -561,6 +565,32 @@ def main():
                         "avg_launch_ms": avg,
                         "achieved_gbs": (bpc * n3 / (avg * 1e-3) / 1e9) if (cnt and bpc) else None}
     dom = max(("sweep", "sweep_adjoint"), key=lambda k: kclass[k]["total_ms"])
+
+    # ---- the same iteration with every checkpoint segment recorded during the run (a tape
+    # of all 100 steps, no recompute in the reverse pass): a variant that spends HBM instead
+    # of recomputation, reported beside the checkpointed headline
+    full_tape = None
+    if not args.no_full_tape:
+        sim.set_tape_recording(-1)
+        for _ in range(2):  # the first one grows the tape
+            x.copy_(noise)
+            hot_path(x)
+        ft = []
+        for _ in range(args.steps):
+            flush.zero_()
+            x.copy_(noise)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hot_path(x)
+            e1.record(stream)
+            e1.synchronize()
+            ft.append(e0.elapsed_time(e1))
+        ft_ms = statistics.mean(ft)
+        full_tape = {"ms_per_step": ft_ms, "value": n3 * p.n_steps / (ft_ms * 1e-3),
+                     "unit": "cell-steps/s",
+                     "tape_gb": TAPE_FLOATS_PER_CELL * 4 * n3 * p.n_steps / 1e9,
+                     "note": "every segment recorded during the run, no recompute"}
+        sim.set_tape_recording(1)
 
     # ---- field-level inference: FLI_ITERS Adam iterations from zero amplitudes
     fli = None
@@ -674,6 +704,8 @@ def main():
                      else "fallback 6.8 TB/s (of fallback)"},
         "clocks": clk,
     }
+    if full_tape is not None:
+        line["fli_full_tape"] = full_tape
     if fli is not None:
         line["fli"] = fli
     if lbfgs_rec is not None:

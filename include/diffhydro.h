@@ -268,18 +268,21 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
 /* Advance n_steps steps from the initial state (the handle must be fresh from sim_init or
  * sim_reset), storing a checkpoint of the state every ckpt_every steps for
  * sim_run_adjoint (Sec. 2.3.5: checkpoints every 6 steps in the paper). Once the handle
- * holds the reverse pass's tape (after its first sim_run_adjoint) and tape recording is on
- * (sim_set_tape_recording), the run also records the checkpoint segment that ends it on the
- * tape, so that the next sim_run_adjoint does not recompute that segment; the results are
- * the same either way. */
+ * holds the reverse pass's tape (after its first sim_run_adjoint), the run also records its
+ * last checkpoint segment(s) on the tape (sim_set_tape_recording), so that the next
+ * sim_run_adjoint does not recompute them; the results are the same either way. */
 sim_status sim_run(sim_t* h, int32_t n_steps);
 
-/* on != 0 (the default): sim_run records its last checkpoint segment on the tape when the
- * handle holds one (a few extra device copies per recorded step, one segment less to
- * recompute in the next sim_run_adjoint). on == 0: runs record nothing, for handles that
- * mostly run forward. sim_fli_step and sim_posterior always record (their reverse pass
- * follows). SIM_EINVAL on a NULL handle. */
-sim_status sim_set_tape_recording(sim_t* h, int32_t on);
+/* Checkpoint segments (ckpt_every steps each) that sim_run records on the tape at the end of
+ * a run once the handle holds one: 1 (the default) records the segment after the last
+ * checkpoint, k > 1 the last k segments, -1 all of them (the reverse pass then recomputes
+ * nothing: at 128^3, 46 floats per cell per step, 3.9 GB per 10-step segment), 0 nothing
+ * (for handles that mostly run forward). Each recorded step costs a few device copies; each
+ * recorded segment is one segment less for the next sim_run_adjoint to recompute. The tape
+ * for k segments is allocated by the next sim_run_adjoint (or sim_fli_step /
+ * sim_posterior, which record at least one segment). Results are the same for every k.
+ * SIM_EINVAL on a NULL handle or segments < -1. */
+sim_status sim_set_tape_recording(sim_t* h, int32_t segments);
 
 /* Gradient of a scalar loss through the whole run made by sim_run and through the
  * initial conditions. dL_dgas (5 n^3) and dL_dpart (6 n^3: d/ds then d/dp) are the

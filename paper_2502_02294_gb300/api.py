@@ -398,10 +398,10 @@ class Simulation:
     def set_graphs(self, on: bool = True):
         self._check(lib.sim_set_graphs(self.h, int(on)), "sim_set_graphs")
 
-    def set_tape_recording(self, on: bool = True):
-        """Whether runs record their last checkpoint segment for the next reverse pass
-        (default on; see sim_set_tape_recording)."""
-        self._check(lib.sim_set_tape_recording(self.h, int(on)), "sim_set_tape_recording")
+    def set_tape_recording(self, segments: int = 1):
+        """Checkpoint segments a run records at its end for the next reverse pass: 1 (the
+        default), k, -1 for all (no recompute), 0 for none; see sim_set_tape_recording."""
+        self._check(lib.sim_set_tape_recording(self.h, int(segments)), "sim_set_tape_recording")
 
     def set_sweep_variants(self, fwd=None, adj=None):
         f = (ctypes.c_int32 * 3)(*fwd) if fwd is not None else None

@@ -165,7 +165,8 @@ struct sim_s {
   // steps [tape_first, tape_end) of the last run, recorded on the tape by the run itself
   // (its last checkpoint segment), or -1: the reverse pass then needs no recompute of it
   int tape_first = -1, tape_end = -1;
-  bool tape_recording = true;  // sim_set_tape_recording
+  // checkpoint segments a run records at its end (sim_set_tape_recording; -1: all of them)
+  int tape_segments = 1;
   float *w_gas = nullptr, *w_gas2 = nullptr, *w_s = nullptr, *w_p = nullptr, *w_g = nullptr;
   float *lam_gas = nullptr, *lam_tmp = nullptr, *lam_s = nullptr, *lam_p = nullptr;
   float *lamG0 = nullptr, *lamG1 = nullptr, *lam_delta = nullptr, *lam4 = nullptr;
@@ -1030,15 +1031,39 @@ static sim_status run_prepare(sim_t* h, int n_steps) {
   return ensure_ckpt_pool(h, (n_steps + h->prm.ckpt_every - 1) / h->prm.ckpt_every);
 }
 
+// Checkpoint segments the handle records at the end of a run, at least min_segments.
+static int recorded_segments(const sim_t* h, int min_segments) {
+  const int all = (h->prm.n_steps + h->prm.ckpt_every - 1) / h->prm.ckpt_every;
+  const int k = h->tape_segments < 0 ? all : h->tape_segments;
+  return std::min(all, std::max(k, min_segments));
+}
+
+// Tape steps the reverse pass of a run needs: one segment to recompute into, or the
+// segments the runs record.
+static int tape_steps_wanted(const sim_t* h) {
+  return h->prm.ckpt_every * std::max(1, recorded_segments(h, 0));
+}
+
 // n_steps forward steps with a checkpoint every ckpt_every steps (Sec. 2.3.5).
-static sim_status run_body(sim_t* h, int n_steps, bool force_record = false) {
+static sim_status run_body(sim_t* h, int n_steps, int min_segments = 0) {
   const int last = h->step + n_steps;
-  const int every = h->prm.ckpt_every;
-  // Once the handle holds a tape (it has run a reverse pass), the run records the checkpoint
-  // segment that ends it as it goes, so the next reverse pass starts without recomputing it.
-  const int seg_first = n_steps > 0 ? h->init_step + (last - 1 - h->init_step) / every * every : 0;
-  const bool record = n_steps > 0 && h->tape && h->tape_cap >= every && !h->closure &&
-                      seg_first >= h->step && (h->tape_recording || force_record);
+  const int every = h->prm.ckpt_every, init = h->init_step;
+  // Once the handle holds a tape (it has run a reverse pass), the run records its last
+  // checkpoint segments as it goes (as many as asked for and as the tape holds, from a
+  // segment start not before this call's first step), so the next reverse pass recomputes
+  // none of them.
+  const int segs = recorded_segments(h, min_segments);
+  int rec_first = 0;
+  bool record = false;
+  if (n_steps > 0 && segs > 0 && h->tape && !h->closure) {
+    const int last_seg = init + (last - 1 - init) / every * every;
+    rec_first = last_seg - (segs - 1) * every;
+    const int fit = last - h->tape_cap;                        // earliest step with a slot
+    if (rec_first < fit) rec_first = init + (fit - init + every - 1) / every * every;
+    const int call_seg = init + (h->step - init + every - 1) / every * every;
+    if (rec_first < call_seg) rec_first = call_seg;
+    record = rec_first <= last_seg;
+  }
   h->tape_first = h->tape_end = -1;
   if (h->diag_on && n_steps > 0)
     DH_TRY(record_diag(h, h->step, h->gas, h->p, nullptr, nullptr));
@@ -1051,8 +1076,8 @@ static sim_status run_body(sim_t* h, int n_steps, bool force_record = false) {
     const bool plain = kicks_apart(h);
     const bool merged_in = !plain && rel % every != 0;
     const bool kick_out = plain || h->step + 1 == last || (rel + 1) % every == 0;
-    const bool rec = record && h->step >= seg_first;
-    const TapeSlot T = rec ? tape_slot(h, h->step - seg_first) : TapeSlot{};
+    const bool rec = record && h->step >= rec_first;
+    const TapeSlot T = rec ? tape_slot(h, h->step - rec_first) : TapeSlot{};
     DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, rec ? &T : nullptr,
                         merged_in, kick_out, true));
     h->step += 1;
@@ -1068,7 +1093,7 @@ static sim_status run_body(sim_t* h, int n_steps, bool force_record = false) {
   }
   h->prev_step = -1;
   if (record) {
-    h->tape_first = seg_first;
+    h->tape_first = rec_first;
     h->tape_end = last;
   }
   return SIM_OK;
@@ -1091,7 +1116,7 @@ static sim_status run_adjoint_prepare(sim_t* h, const float* dL_dnoise, const do
     set_error("sim_run_adjoint: the run did not start from initial conditions");
     return SIM_EINVAL;
   }
-  return ensure_adjoint_buffers(h, h->prm.ckpt_every);
+  return ensure_adjoint_buffers(h, tape_steps_wanted(h));
 }
 
 // Reverse pass over the checkpointed run: every segment recomputed forward with the tape,
@@ -1116,8 +1141,8 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
     DH_TRY(dzero(h->lam_p, 3 * N3 * sizeof(float), st));
   }
   DH_TRY(dzero(h->lamG1, 4 * N3 * sizeof(float), st));
-  // the segment the run recorded on the tape needs no recompute; the recompute of the other
-  // segments overwrites the tape
+  // the segments the run recorded on the tape need no recompute (reversed first, from their
+  // slots); the recompute of the other segments overwrites the tape from slot 0
   const int taped_first = h->tape_first, taped_end = h->tape_end;
   h->tape_first = h->tape_end = -1;
   for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -1126,7 +1151,9 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
     // the same kick merging as the forward run: opening kicks merged after the segment's
     // first step, the closing kick only at the segment's end
     const bool plain = kicks_apart(h);
-    if (!(seg == nseg - 1 && first == taped_first && end == taped_end)) {
+    const bool taped = taped_first >= 0 && first >= taped_first && end <= taped_end;
+    const int base = taped ? taped_first : first;  // step of tape slot 0
+    if (!taped) {
       const float* c = h->ckpt_pool[seg];
       DH_TRY(dcopy(h->w_gas, c, 5 * N3 * sizeof(float), st));
       DH_TRY(dcopy(h->w_s, c + 5 * N3, 3 * N3 * sizeof(float), st));
@@ -1139,7 +1166,7 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
       }
     }
     for (int i = end - 1; i >= first; --i)
-      DH_TRY(reverse_step(h, i, tape_slot(h, i - first), h->dslots + (size_t)i * B * SL_N,
+      DH_TRY(reverse_step(h, i, tape_slot(h, i - base), h->dslots + (size_t)i * B * SL_N,
                           !plain && i != first, plain || i == end - 1));
   }
   // g at the start of the run is a function of the initial state
@@ -1495,9 +1522,12 @@ sim_status sim_step_adjoint(sim_t* h, float* adj_gas, float* adj_part, double* a
   return fail(h, run());
 }
 
-sim_status sim_set_tape_recording(sim_t* h, int32_t on) {
-  if (!h) return SIM_EINVAL;
-  h->tape_recording = on != 0;
+sim_status sim_set_tape_recording(sim_t* h, int32_t segments) {
+  if (!h || segments < -1) {
+    set_error("sim_set_tape_recording: null handle or segments < -1");
+    return fail(h, SIM_EINVAL);
+  }
+  h->tape_segments = segments;
   return SIM_OK;
 }
 
@@ -1507,7 +1537,7 @@ sim_status sim_run(sim_t* h, int32_t n_steps) {
   if (r != SIM_OK) return fail(h, r);
   // the CFL watchdog reads back every step: never captured
   if (h->prm.cfl_max > 0) return fail(h, run_body(h, n_steps));
-  return fail(h, run_maybe_graph(h, 1, {(uintptr_t)n_steps, (uintptr_t)h->tape_recording},
+  return fail(h, run_maybe_graph(h, 1, {(uintptr_t)n_steps, (uintptr_t)recorded_segments(h, 0)},
                                  [&] { return run_body(h, n_steps); }));
 }
 
@@ -1586,10 +1616,10 @@ static sim_status posterior_data_term(sim_t* h, int obs, const float* noise, con
   h->init_step = 0;
   DH_TRY(reset_to_init(h));
   // the reverse-pass buffers first, so that the run records its last segment on the tape
-  DH_TRY(ensure_adjoint_buffers(h, h->prm.ckpt_every));
+  DH_TRY(ensure_adjoint_buffers(h, tape_steps_wanted(h)));
   DH_TRY(run_prepare(h, h->prm.n_steps));
-  DH_TRY(run_maybe_graph(h, 1, {(uintptr_t)h->prm.n_steps, (uintptr_t)1},
-                         [&] { return run_body(h, h->prm.n_steps, true); }));
+  DH_TRY(run_maybe_graph(h, 1, {(uintptr_t)h->prm.n_steps, (uintptr_t)recorded_segments(h, 1)},
+                         [&] { return run_body(h, h->prm.n_steps, 1); }));
   DH_TRY(field_loss(h, obs, data, 0.5 / (sigma_n * sigma_n), h->fli_dL, loss));
   DH_TRY(run_adjoint_prepare(h, h->fli_g, h->fli_dpar));
   const std::vector<uintptr_t> key = {(uintptr_t)h->fli_dL, (uintptr_t)0, (uintptr_t)h->fli_g,
@@ -1985,7 +2015,7 @@ sim_status sim_group_run(sim_group_t* g) {
   std::vector<uintptr_t> key;
   for (sim_t* h : g->m) {
     key.push_back((uintptr_t)(h->prm.n_steps - h->step));
-    key.push_back((uintptr_t)h->tape_recording);
+    key.push_back((uintptr_t)recorded_segments(h, 0));
   }
   return group_graph(g, 1, key, [&](size_t k) {
     sim_t* h = g->m[k];

@@ -274,12 +274,13 @@ def test_graph_replay_matches_eager(dh):
 
 
 @pytest.mark.parametrize("graphs", [0, 1])
-def test_run_records_its_last_segment(dh, graphs):
+def test_runs_record_their_last_segments(dh, graphs):
     """Once a handle holds a tape (after its first reverse pass), sim_run records its last
-    checkpoint segment as it goes and the next sim_run_adjoint skips that segment's
-    recompute: the run's state, stars, events and diagnostics are those of a run without
-    the tape, the gradients agree (float atomics in the reverse pass: 1e-5), and the reverse
-    pass launches fewer kernels."""
+    checkpoint segments as it goes (sim_set_tape_recording: 1 by default, 0 none, -1 all) and
+    the next sim_run_adjoint recomputes none of them: every run's state, stars, events and
+    diagnostics are those of a run without the tape, the gradients agree (float atomics in
+    the reverse pass: 1e-5), and the reverse pass launches fewer kernels. A tape grown for
+    more segments drops what the run before recorded on the old one."""
     n = 16
     p = dh.default_params(n=n, box=16.0, n_steps=10, ckpt_every=4, a_start=0.1, a_end=0.4,
                           rms_ref=0.15, **SUB)
@@ -289,7 +290,9 @@ def test_run_records_its_last_segment(dh, graphs):
     sim.set_graphs(bool(graphs))
     sim.set_diagnostics(True)
     runs = []
-    for rep in range(3):
+    # segments [0, 4), [4, 8), [8, 10); the recording set before each run
+    for segs in (1, 1, 0, -1, -1):
+        sim.set_tape_recording(segs)
         sim.reset()
         sim.run()
         st = {k: v.clone() for k, v in sim.state().items() if torch.is_tensor(v)}
@@ -300,18 +303,15 @@ def test_run_records_its_last_segment(dh, graphs):
         dnoise, dpar = sim.run_adjoint(dL)
         torch.cuda.synchronize()
         runs.append((st, diag, dnoise.clone(), dpar.clone(), dh.lib.sim_kernel_launches() - l0))
-        if rep == 1:
-            sim.set_tape_recording(False)  # the third run records nothing
     ref = runs[0]
-    for rep, (st, diag, dn, dp, launches) in enumerate(runs[1:], 1):
+    for st, diag, dn, dp, _ in runs[1:]:
         for k in ref[0]:
             assert torch.equal(st[k], ref[0][k]), k
         assert diag == ref[1]
         assert rel_l2(dn, ref[2]) < 1e-5
         assert rel_l2(dp, ref[3]) < 1e-5
-        # segments [0, 4), [4, 8), [8, 10): the last one is recomputed only without recording
-        if rep == 1:
-            assert launches < ref[4], (launches, ref[4])
-        else:
-            assert launches == ref[4], (launches, ref[4])
+    L = [r[4] for r in runs]
+    # no tape yet; last segment recorded; nothing recorded; recorded on the old tape, which
+    # the adjoint then grows (recording dropped); all three segments recorded
+    assert L[1] < L[0] and L[2] == L[0] and L[3] == L[0] and L[4] < L[1], L
     sim.close()
