@@ -226,7 +226,11 @@ __global__ void deposit_kernel(const float* __restrict__ s, const float* __restr
 }
 
 // grid (cdiv(N3, 1024), B): four cells per thread, 16-byte vector accesses where N3 and the
-// instance's pointers allow (add may alias out: each cell is read before it is written)
+// instance's pointers allow (add may alias out: each cell is read before it is written).
+// ZERO: the accumulator is cleared behind the read (else the caller clears it before the
+// next deposit with a memset, which streams at the copy rate: the clearing stores here cost
+// more than the conversion itself)
+template <bool ZERO>
 __global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, SArg scale,
                                     const float* add, int add_stride, float offset, float* out,
                                     int N3) {
@@ -243,9 +247,11 @@ __global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, SArg s
     const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(a + i0);
     const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(a + i0 + 2);
     const float4 r = ad ? *reinterpret_cast<const float4*>(ad + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const ulonglong2 z = make_ulonglong2(0ull, 0ull);
-    *reinterpret_cast<ulonglong2*>(a + i0) = z;
-    *reinterpret_cast<ulonglong2*>(a + i0 + 2) = z;
+    if (ZERO) {
+      const ulonglong2 z = make_ulonglong2(0ull, 0ull);
+      *reinterpret_cast<ulonglong2*>(a + i0) = z;
+      *reinterpret_cast<ulonglong2*>(a + i0 + 2) = z;
+    }
     float4 w;
     w.x = sc * from_fix(v0.x) + r.x + offset;
     w.y = sc * from_fix(v0.y) + r.y + offset;
@@ -256,7 +262,7 @@ __global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, SArg s
     const int i1 = i0 + 4 < N3 ? i0 + 4 : N3;
     for (int i = i0; i < i1; ++i) {
       const float cnt = from_fix(a[i]);
-      a[i] = 0ull;
+      if (ZERO) a[i] = 0ull;
       o[i] = sc * cnt + (ad ? ad[i] : 0.0f) + offset;
     }
   }
@@ -271,10 +277,13 @@ sim_status launch_deposit(const float* s, const float* values, int n, float inv_
 
 sim_status launch_fix_to_float(unsigned long long* acc, SArg scale, const float* add,
                                int add_stride, float offset, float* out, int n, int B,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool zero_acc) {
   const int N3 = n * n * n;
-  fix_to_float_kernel<<<dim3(cdiv(N3, 1024), B), 256, 0, st>>>(acc, scale, add, add_stride,
-                                                               offset, out, N3);
+  const dim3 grid(cdiv(N3, 1024), B);
+  if (zero_acc)
+    fix_to_float_kernel<true><<<grid, 256, 0, st>>>(acc, scale, add, add_stride, offset, out, N3);
+  else
+    fix_to_float_kernel<false><<<grid, 256, 0, st>>>(acc, scale, add, add_stride, offset, out, N3);
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

@@ -32,10 +32,10 @@ FFTPlans* shared_plans(int n);
 sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
                           unsigned long long* acc, int B, cudaStream_t st);
 // out = scale * fixed_to_float(acc) + add (add may be NULL; instance stride add_stride)
-// + offset; acc is zeroed
+// + offset; acc is zeroed when zero_acc (else left for the caller to clear)
 sim_status launch_fix_to_float(unsigned long long* acc, SArg scale, const float* add,
                                int add_stride, float offset, float* out, int n, int B,
-                               cudaStream_t st);
+                               cudaStream_t st, bool zero_acc = true);
 // pref / n^3 in float, the normalisation the Green's function kernels take
 float gravity_pref_norm(double pref, int n);
 // g (3 n^3) from delta (n^3): r2c, Green's function * i k * pref / n^3, c2r x3

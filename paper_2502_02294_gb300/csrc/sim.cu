@@ -445,9 +445,11 @@ static sim_status compute_force(sim_t* h, const float* s, const float* gas, SArg
   const int B = h->B;
   if (!h->prm.gravity_on) return dzero(g, 3 * B * h->N3 * sizeof(float), h->st);
   DH_TRY(timed(h, SIM_KT_DEPOSIT, [&] {
+    // the accumulator cleared by a memset ahead of the deposit, not by the conversion
+    DH_TRY(dzero(h->acc, (size_t)B * h->N3 * sizeof(unsigned long long), h->st));
     DH_TRY(launch_deposit(s, nullptr, h->n, (float)h->inv_dx, h->acc, B, h->st));
     return launch_fix_to_float(h->acc, sarg(h->d_cm), gas, (int)(5 * h->N3), -1.0f, h->delta,
-                               h->n, B, h->st);
+                               h->n, B, h->st, false);
   }));
   return timed(h, SIM_KT_POISSON, [&] {
     return launch_gravity(h->delta, g, h->ck, h->ck + B * h->NC, h->n, h->prm.box, pn, B,
