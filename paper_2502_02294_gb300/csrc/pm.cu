@@ -438,7 +438,9 @@ __device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& 
       }
 }
 
-__global__ void kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
+// 40 registers (12 resident blocks per SM instead of 9 at 56): more warps in flight for the
+// CIC gathers (kick class 44.7 -> 43.2 us per launch at 128^3)
+__global__ void __launch_bounds__(128, 12) kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
                                   const float* __restrict__ g, SArg Ka, SArg dtaua,
                                   const float* __restrict__ zhat, float* __restrict__ aux,
                                   int n, float inv_dx) {
