@@ -43,6 +43,34 @@ void count_launch();
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// ------------------------------------------------------------------ dependent launches
+// Kernels of the step follow one another on one stream. Each is launched with programmatic
+// stream serialisation (launch_pdl) and opens with pdl_enter(): it waits there until the
+// grid before it has completed and its writes are visible, then lets the grid after it be
+// scheduled. So the next kernel's blocks are launched while this one's last wave drains,
+// and nothing is read before its producer has finished. (Launched without the attribute,
+// both instructions return at once.)
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Params>(args)...);
+}
+
 // ------------------------------------------------------------------ batched launches
 // Every kernel of the step takes B instances of one grid size stored one after another
 // (instance b of a field with F components of n^3 cells starts at b * F * n^3). A scalar

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256) diag_kernel(const float* __restrict__ gas
                                                    long long N3, float gam, SArg cm,
                                                    double* __restrict__ sums,
                                                    int* __restrict__ mins) {
+  pdl_enter();
   const int b = blockIdx.y;
   gas += (size_t)b * 5 * N3;
   p += (size_t)b * 3 * N3;
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(256) diag_kernel(const float* __restrict__ gas
 }
 
 __global__ void diag_clear_kernel(double* __restrict__ sums, int* __restrict__ mins, int B) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < B * DG_NSUM) sums[i] = 0.0;
   if (i < B * 2) mins[i] = INT_MAX;
@@ -97,12 +99,12 @@ __global__ void diag_clear_kernel(double* __restrict__ sums, int* __restrict__ m
 sim_status launch_diag(const float* gas, const float* p, const float* zhat,
                        const uint32_t* events, long long N3, float gamma, SArg cm, int B,
                        double* sums, int* mins, cudaStream_t st) {
-  diag_clear_kernel<<<cdiv((long long)B * DG_NSUM, 128), 128, 0, st>>>(sums, mins, B);
+  DH_CUDA_TRY((launch_pdl(diag_clear_kernel, cdiv((long long)B * DG_NSUM, 128), 128, 0, st, sums, mins, B)));
   DH_LAUNCH_CHECK();
   int blocks = cdiv(N3, 256);
   const int cap = cdiv(152 * 4, B);
   if (blocks > cap) blocks = cap;
-  diag_kernel<<<dim3(blocks, B), 256, 0, st>>>(gas, p, zhat, events, N3, gamma, cm, sums, mins);
+  DH_CUDA_TRY((launch_pdl(diag_kernel, dim3(blocks, B), 256, 0, st, gas, p, zhat, events, N3, gamma, cm, sums, mins)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) fli_adam_kernel(float* __restrict__ x, co
                                                        long long count, AdamConst c,
                                                        float* __restrict__ grad_out,
                                                        double* __restrict__ prior) {
+  pdl_enter();
   const int b = blockIdx.y;
   const size_t off = (size_t)b * count;
   x += off;
@@ -116,9 +117,9 @@ sim_status launch_fli_adam(float* x, const float* g, float* m, float* v, long lo
   if (blocks > cap) blocks = cap;
   const dim3 grid(blocks, B);
   if (vec)
-    fli_adam_kernel<true><<<grid, 256, 0, st>>>(x, g, m, v, count, c, grad_out, prior);
+    DH_CUDA_TRY((launch_pdl(fli_adam_kernel<true>, grid, 256, 0, st, x, g, m, v, count, c, grad_out, prior)));
   else
-    fli_adam_kernel<false><<<grid, 256, 0, st>>>(x, g, m, v, count, c, grad_out, prior);
+    DH_CUDA_TRY((launch_pdl(fli_adam_kernel<false>, grid, 256, 0, st, x, g, m, v, count, c, grad_out, prior)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(256) prior_grad_kernel(const float* __restrict
                                                          const float* __restrict__ g,
                                                          float* __restrict__ grad, long long count,
                                                          float prior_w, double* __restrict__ prior) {
+  pdl_enter();
   const int b = blockIdx.y;
   const size_t off = (size_t)b * count;
   float acc = 0.0f;
@@ -146,7 +148,7 @@ sim_status launch_prior_grad(const float* x, const float* g, float* grad, long l
   int blocks = cdiv(count, 256);
   const int cap = cdiv(152 * 8, B);
   if (blocks > cap) blocks = cap;
-  prior_grad_kernel<<<dim3(blocks, B), 256, 0, st>>>(x, g, grad, count, (float)prior_w, prior);
+  DH_CUDA_TRY((launch_pdl(prior_grad_kernel, dim3(blocks, B), 256, 0, st, x, g, grad, count, (float)prior_w, prior)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -154,6 +156,7 @@ sim_status launch_prior_grad(const float* x, const float* g, float* grad, long l
 // y = alpha x + beta y over count floats
 __global__ void axpby_kernel(float alpha, const float* __restrict__ x, float beta,
                              float* __restrict__ y, long long count) {
+  pdl_enter();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = alpha * x[i] + beta * y[i];
@@ -164,6 +167,7 @@ __global__ void axpby_kernel(float alpha, const float* __restrict__ x, float bet
 // three weighted powers |X|^2, |Y|^2, Re(X conj Y) (FP64 histograms in shared memory).
 __global__ void xc_bin_kernel(const cufftComplex* __restrict__ a, const cufftComplex* __restrict__ b,
                               int n, int nbins, double* __restrict__ sums) {
+  pdl_enter();
   extern __shared__ double hist[];  // 5 * nbins
   for (int j = threadIdx.x; j < 5 * nbins; j += blockDim.x) hist[j] = 0.0;
   __syncthreads();
@@ -195,6 +199,7 @@ __global__ void xc_bin_kernel(const cufftComplex* __restrict__ a, const cufftCom
 __global__ void xc_finish_kernel(const double* __restrict__ sums, int nbins, double kf,
                                  double* __restrict__ k, double* __restrict__ rc,
                                  double* __restrict__ nm) {
+  pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nbins) return;
   const double w = sums[j], pxx = sums[2 * nbins + j], pyy = sums[3 * nbins + j];
@@ -237,7 +242,7 @@ extern "C" sim_status sim_axpby(double alpha, const float* x, double beta, float
   }
   int blocks = cdiv(count, 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
-  axpby_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((float)alpha, x, (float)beta, y, count);
+  DH_CUDA_TRY((launch_pdl(axpby_kernel, blocks, 256, 0, (cudaStream_t)stream, (float)alpha, x, (float)beta, y, count)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -274,7 +279,7 @@ extern "C" sim_status sim_cross_correlation(const float* a, const float* b, int3
   if (r == SIM_OK) {
     int blocks = cdiv(NC, 256);
     if (blocks > 152 * 4) blocks = 152 * 4;
-    xc_bin_kernel<<<blocks, 256, 5 * nbins * sizeof(double), st>>>(buf, buf + NC, n, nbins, sums);
+    DH_CUDA_TRY((launch_pdl(xc_bin_kernel, blocks, 256, 5 * nbins * sizeof(double), st, buf, buf + NC, n, nbins, sums)));
     count_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("xc_bin_kernel launch failed");
@@ -282,7 +287,7 @@ extern "C" sim_status sim_cross_correlation(const float* a, const float* b, int3
     }
   }
   if (r == SIM_OK) {
-    xc_finish_kernel<<<cdiv(nbins, 128), 128, 0, st>>>(sums, nbins, 2.0 * M_PI / box, k, rc, nmodes);
+    DH_CUDA_TRY((launch_pdl(xc_finish_kernel, cdiv(nbins, 128), 128, 0, st, sums, nbins, 2.0 * M_PI / box, k, rc, nmodes)));
     count_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("xc_finish_kernel launch failed");

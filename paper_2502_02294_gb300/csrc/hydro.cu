@@ -107,6 +107,7 @@ template <int AXIS>
 __global__ void __launch_bounds__(SweepCfg<AXIS>::NT, 2)
 sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
                  float gam, float eps) {
+  pdl_enter();
   constexpr int S = SweepCfg<AXIS>::S, W = SweepCfg<AXIS>::W, NT = SweepCfg<AXIS>::NT;
   using G = TileGeom<AXIS, S, W, 3>;
   constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
@@ -232,6 +233,7 @@ template <int AXIS>
 __global__ void __launch_bounds__(128)
 sweep_march_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
                    float gam, float eps, int L) {
+  pdl_enter();
   constexpr int F = 1 + AXIS;
   const LineIdx li = line_index(n, 1);
   const int w = li.w, t = li.t, b = li.b;  // line coordinate, third coordinate, instance
@@ -346,6 +348,7 @@ template <int AXIS, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
                     float gam, float eps, int L) {
+  pdl_enter();
   constexpr int F = 1 + AXIS;
   const LineIdx li = line_index(n, 2);
   const int w = li.w, t = li.t, b = li.b;
@@ -448,6 +451,7 @@ __global__ void __launch_bounds__(128, 3)
 sweep_adj_march_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                        float* __restrict__ luh_out, int n, SArg nua, float gam, float eps,
                        DPart dnub, int L) {
+  pdl_enter();
   constexpr int F = FC;  // momentum component along the sweep
   const LineIdx li = line_index(n, 1);
   const int w = li.w, b = li.b;  // line coordinate, instance
@@ -632,6 +636,7 @@ __global__ void __launch_bounds__(256)
 sweep_adj_final_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                        const float* __restrict__ luh, float* __restrict__ lin, int n,
                        SArg nua, float gam) {
+  pdl_enter();
   constexpr int F = FC;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.z / n;  // instance
@@ -739,6 +744,7 @@ __global__ void __launch_bounds__(128)
 sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                         const float* __restrict__ luh, float* __restrict__ lin, int n,
                         SArg nua, float gam) {
+  pdl_enter();
   constexpr int F = FC;
   const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int b = blockIdx.z / n;
@@ -787,6 +793,7 @@ template <int AXIS>
 __global__ void __launch_bounds__(SweepCfg<AXIS>::NTA, 2)
 sweep_adj_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
                  float* __restrict__ lin, int n, SArg nua, float gam, float eps, DPart dnub) {
+  pdl_enter();
   constexpr int S = SweepCfg<AXIS>::SA, W = SweepCfg<AXIS>::WA, NT = SweepCfg<AXIS>::NTA;
   using G = TileGeom<AXIS, S, W, 5>;
   constexpr int NC = G::NC, DS = G::DS, SP = G::SP, CPT = (NC + NT - 1) / NT;
@@ -1034,8 +1041,8 @@ static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, 
   const int L = variant == SIM_SWEEP_MARCH_FIT
                     ? fit_segment(sweep_march_kernel<AXIS>, n, B, 6, n, blk)
                     : segment_length(variant);
-  sweep_march_kernel<AXIS><<<line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st>>>(uin, uout, n, nu,
-                                                                                 gam, eps, L);
+  DH_CUDA_TRY((launch_pdl(sweep_march_kernel<AXIS>, line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st, uin, uout, n, nu,
+                                                                                 gam, eps, L)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1045,8 +1052,7 @@ static sim_status launch_march2_mb(const float* uin, float* uout, int n, SArg nu
                                    float eps, int B, cudaStream_t st) {
   const dim3 blk = line_block(n / 2, 128);
   const int L = fit_segment(sweep_march2_kernel<AXIS, MINB>, n, B, 6, n / 2, blk);
-  sweep_march2_kernel<AXIS, MINB><<<line_grid(n / 2, n, B, blk, cdiv(n, L)), blk, 0, st>>>(
-      uin, uout, n, nu, gam, eps, L);
+  DH_CUDA_TRY((launch_pdl(sweep_march2_kernel<AXIS, MINB>, line_grid(n / 2, n, B, blk, cdiv(n, L)), blk, 0, st, uin, uout, n, nu, gam, eps, L)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1073,7 +1079,7 @@ static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, 
   constexpr int NC = (C::S + 6) * C::W;
   const size_t smem = 15 * NC * sizeof(float);
   dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n * B);
-  sweep_fwd_kernel<AXIS><<<grid, C::NT, smem, st>>>(uin, uout, n, nu, gam, eps);
+  DH_CUDA_TRY((launch_pdl(sweep_fwd_kernel<AXIS>, grid, C::NT, smem, st, uin, uout, n, nu, gam, eps)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1093,6 +1099,7 @@ constexpr int TP = 4;
 
 template <bool VEC>
 __global__ void __launch_bounds__(256) transpose_xy_kernel(TPair a, int n) {
+  pdl_enter();
   __shared__ float tile[32][33];
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const int t = threadIdx.x;
@@ -1142,9 +1149,9 @@ static sim_status launch_transpose_xy(const float* in0, float* out0, int nf0, co
   const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(in0) | reinterpret_cast<uintptr_t>(out0) |
                                      reinterpret_cast<uintptr_t>(in1) | reinterpret_cast<uintptr_t>(out1)) % 16 == 0);
   if (vec)
-    transpose_xy_kernel<true><<<grid, 256, 0, st>>>(a, n);
+    DH_CUDA_TRY((launch_pdl(transpose_xy_kernel<true>, grid, 256, 0, st, a, n)));
   else
-    transpose_xy_kernel<false><<<grid, 256, 0, st>>>(a, n);
+    DH_CUDA_TRY((launch_pdl(transpose_xy_kernel<false>, grid, 256, 0, st, a, n)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1159,11 +1166,11 @@ static sim_status launch_adj_final(const float* uin, const float* lout, const fl
   if (AXIS != 0 && n % 2 == 0 && al % 8 == 0) {  // x runs as AXIS 1 on transposed copies
     const dim3 blk = line_block(n / 2, 128);
     const dim3 g(cdiv(n / 2, blk.x), cdiv(n, blk.y), n * B);
-    sweep_adj_final2_kernel<AXIS, FC><<<g, blk, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
+    DH_CUDA_TRY((launch_pdl(sweep_adj_final2_kernel<AXIS, FC>, g, blk, 0, st, uin, lout, luh, lin, n, nu, gam)));
   } else {
     const dim3 blk = line_block(n, 256);
     const dim3 g(cdiv(n, blk.x), cdiv(n, blk.y), n * B);
-    sweep_adj_final_kernel<AXIS, FC><<<g, blk, 0, st>>>(uin, lout, luh, lin, n, nu, gam);
+    DH_CUDA_TRY((launch_pdl(sweep_adj_final_kernel<AXIS, FC>, g, blk, 0, st, uin, lout, luh, lin, n, nu, gam)));
   }
   DH_LAUNCH_CHECK();
   return SIM_OK;
@@ -1178,8 +1185,7 @@ static sim_status launch_adj_march_t(const float* uin, const float* lout, float*
     return SIM_EINVAL;
   }
   const dim3 blk = line_block(n, 128);
-  sweep_adj_march_kernel<AXIS><<<line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st>>>(
-      uin, lout, scratch, n, nu, gam, eps, dnu, L);
+  DH_CUDA_TRY((launch_pdl(sweep_adj_march_kernel<AXIS>, line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st, uin, lout, scratch, n, nu, gam, eps, dnu, L)));
   DH_LAUNCH_CHECK();
   return launch_adj_final<AXIS, 1 + AXIS>(uin, lout, scratch, lin, n, nu, gam, B, st);
 }
@@ -1193,8 +1199,7 @@ static sim_status launch_adj_x_transposed(const float* uin, const float* lout, f
   float *ut = scratch, *lt = scratch + F5, *it = scratch + 2 * F5, *luh = scratch + 3 * F5;
   DH_TRY(launch_transpose_xy(uin, ut, 5 * B, lout, lt, 5 * B, n, st));
   const dim3 blk = line_block(n, 128);
-  sweep_adj_march_kernel<1, 1><<<line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st>>>(
-      ut, lt, luh, n, nu, gam, eps, dnu, L);
+  DH_CUDA_TRY((launch_pdl(sweep_adj_march_kernel<1, 1>, line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st, ut, lt, luh, n, nu, gam, eps, dnu, L)));
   DH_LAUNCH_CHECK();
   DH_TRY((launch_adj_final<1, 1>(ut, lt, luh, it, n, nu, gam, B, st)));
   return launch_transpose_xy(it, lin, 5 * B, nullptr, nullptr, 0, n, st);
@@ -1222,7 +1227,7 @@ static sim_status launch_sweep_adj_t(const float* uin, const float* lout, float*
   constexpr int NC = (C::SA + 10) * C::WA;
   const size_t smem = 20 * NC * sizeof(float);
   dim3 grid(cdiv(n, C::SA), cdiv(n, C::WA), n * B);
-  sweep_adj_kernel<AXIS><<<grid, C::NTA, smem, st>>>(uin, lout, lin, n, nu, gam, eps, dnu);
+  DH_CUDA_TRY((launch_pdl(sweep_adj_kernel<AXIS>, grid, C::NTA, smem, st, uin, lout, lin, n, nu, gam, eps, dnu)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

@@ -10,6 +10,7 @@ namespace dh {
 
 __global__ void noise_kernel(uint32_t k0, uint32_t k1, uint32_t inst, float* __restrict__ w,
                              long long N3) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N3) return;
   const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, inst, TAG_IC_NOISE), k0, k1);
@@ -44,6 +45,7 @@ __device__ __forceinline__ void kvec(long long i, int n, int nh, float kf, float
 // out[0] = Cn sqrtP W ; out[1+j] = i kgrad_j / k^2 * out[0]
 __global__ void shape_kernel(const cufftComplex* __restrict__ W, cufftComplex* __restrict__ out,
                              int n, float kf, float kc, float Cn) {
+  pdl_enter();
   const int nh = n / 2 + 1;
   const long long NC = (long long)n * n * nh;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,6 +63,7 @@ __global__ void shape_kernel(const cufftComplex* __restrict__ W, cufftComplex* _
 // adjoint of shape + c2r: Y = Cn sqrtP (L0 - i sum_j kgrad_j/k^2 L_j)
 __global__ void unshape_kernel(const cufftComplex* __restrict__ L, cufftComplex* __restrict__ Y,
                                int n, float kf, float kc, float Cn) {
+  pdl_enter();
   const int nh = n / 2 + 1;
   const long long NC = (long long)n * n * nh;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,6 +80,7 @@ __global__ void unshape_kernel(const cufftComplex* __restrict__ L, cufftComplex*
 __global__ void place_kernel(const float* __restrict__ f4, float* __restrict__ gas,
                              float* __restrict__ s, float* __restrict__ p, float rp, float fb,
                              float a2e0, long long N3) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N3) return;
   const float delta = f4[i];
@@ -102,6 +106,7 @@ __global__ void unplace_kernel(const float* __restrict__ f4, const float* __rest
                                const float* __restrict__ ls, const float* __restrict__ lp,
                                float* __restrict__ lam4, float rp, float fb, float a2e0,
                                double* __restrict__ drp, double* __restrict__ dfb, long long N3) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float arp = 0.0f, afb = 0.0f;
   if (i < N3) {
@@ -133,8 +138,8 @@ __global__ void unplace_kernel(const float* __restrict__ f4, const float* __rest
 }
 
 sim_status launch_noise(uint64_t seed, int instance, float* w, long long N3, cudaStream_t st) {
-  noise_kernel<<<cdiv(N3, 256), 256, 0, st>>>((uint32_t)(seed & 0xffffffffull),
-                                               (uint32_t)(seed >> 32), (uint32_t)instance, w, N3);
+  DH_CUDA_TRY((launch_pdl(noise_kernel, cdiv(N3, 256), 256, 0, st, (uint32_t)(seed & 0xffffffffull),
+                                               (uint32_t)(seed >> 32), (uint32_t)instance, w, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -151,7 +156,7 @@ sim_status launch_linear_field(const float* w, float* f4, cufftComplex* ck, int 
   const float kf = (float)(2.0 * M_PI / box);
   const float kc = (float)(kc_frac * M_PI * n / box);
   const float Cn = (float)(C / ((double)n * n * n));
-  shape_kernel<<<cdiv(NC, 256), 256, 0, st>>>(ck, ck + NC, n, kf, kc, Cn);
+  DH_CUDA_TRY((launch_pdl(shape_kernel, cdiv(NC, 256), 256, 0, st, ck, ck + NC, n, kf, kc, Cn)));
   DH_LAUNCH_CHECK();
   if (cufftExecC2R(plans.c2r4, ck + NC, f4) != CUFFT_SUCCESS) {
     set_error("cufftExecC2R (ICs) failed");
@@ -162,8 +167,8 @@ sim_status launch_linear_field(const float* w, float* f4, cufftComplex* ck, int 
 
 sim_status launch_place(const float* f4, float* gas, float* s, float* p, double rp, double fb,
                         double a2e0, long long N3, cudaStream_t st) {
-  place_kernel<<<cdiv(N3, 256), 256, 0, st>>>(f4, gas, s, p, (float)rp, (float)fb,
-                                               (float)a2e0, N3);
+  DH_CUDA_TRY((launch_pdl(place_kernel, cdiv(N3, 256), 256, 0, st, f4, gas, s, p, (float)rp, (float)fb,
+                                               (float)a2e0, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -175,8 +180,8 @@ sim_status launch_ic_adjoint(const float* f4, const float* lgas, const float* ls
                              cudaStream_t st) {
   const long long N3 = (long long)n * n * n;
   const long long NC = (long long)n * n * (n / 2 + 1);
-  unplace_kernel<<<cdiv(N3, 256), 256, 0, st>>>(f4, lgas, ls, lp, lam4, (float)rp, (float)fb,
-                                                 (float)a2e0, drp, dfb, N3);
+  DH_CUDA_TRY((launch_pdl(unplace_kernel, cdiv(N3, 256), 256, 0, st, f4, lgas, ls, lp, lam4, (float)rp, (float)fb,
+                                                 (float)a2e0, drp, dfb, N3)));
   DH_LAUNCH_CHECK();
   if (!lam_w) return SIM_OK;
   DH_TRY(plans.set_stream(st));
@@ -187,7 +192,7 @@ sim_status launch_ic_adjoint(const float* f4, const float* lgas, const float* ls
   const float kf = (float)(2.0 * M_PI / box);
   const float kc = (float)(kc_frac * M_PI * n / box);
   const float Cn = (float)(C / ((double)n * n * n));
-  unshape_kernel<<<cdiv(NC, 256), 256, 0, st>>>(ck, ck + 4 * NC, n, kf, kc, Cn);
+  DH_CUDA_TRY((launch_pdl(unshape_kernel, cdiv(NC, 256), 256, 0, st, ck, ck + 4 * NC, n, kf, kc, Cn)));
   DH_LAUNCH_CHECK();
   if (cufftExecC2R(plans.c2r1, ck + 4 * NC, lam_w) != CUFFT_SUCCESS) {
     set_error("cufftExecC2R (IC adjoint) failed");

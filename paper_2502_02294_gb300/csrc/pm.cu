@@ -195,6 +195,7 @@ __device__ __forceinline__ XPair xpair(int a0, int a1, bool ok) {
 
 __global__ void deposit_kernel(const float* __restrict__ s, const float* __restrict__ vals,
                                int n, float inv_dx, unsigned long long* __restrict__ acc) {
+  pdl_enter();
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);  // lanes past the last particle stay for the warp exchange
   s += (size_t)q.b * 3 * N3;
@@ -234,6 +235,7 @@ template <bool ZERO>
 __global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, SArg scale,
                                     const float* add, int add_stride, float offset, float* out,
                                     int N3) {
+  pdl_enter();
   const int b = blockIdx.y;
   const float sc = scale.at(b);
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -270,7 +272,7 @@ __global__ void fix_to_float_kernel(unsigned long long* __restrict__ acc, SArg s
 
 sim_status launch_deposit(const float* s, const float* values, int n, float inv_dx,
                           unsigned long long* acc, int B, cudaStream_t st) {
-  deposit_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, values, n, inv_dx, acc);
+  DH_CUDA_TRY((launch_pdl(deposit_kernel, particle_grid(n, kPT, B), kPT, 0, st, s, values, n, inv_dx, acc)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -281,9 +283,9 @@ sim_status launch_fix_to_float(unsigned long long* acc, SArg scale, const float*
   const int N3 = n * n * n;
   const dim3 grid(cdiv(N3, 1024), B);
   if (zero_acc)
-    fix_to_float_kernel<true><<<grid, 256, 0, st>>>(acc, scale, add, add_stride, offset, out, N3);
+    DH_CUDA_TRY((launch_pdl(fix_to_float_kernel<true>, grid, 256, 0, st, acc, scale, add, add_stride, offset, out, N3)));
   else
-    fix_to_float_kernel<false><<<grid, 256, 0, st>>>(acc, scale, add, add_stride, offset, out, N3);
+    DH_CUDA_TRY((launch_pdl(fix_to_float_kernel<false>, grid, 256, 0, st, acc, scale, add, add_stride, offset, out, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -307,6 +309,7 @@ __device__ __forceinline__ void kindex(int i, int n, int nh, int& kx, int& ky, i
 // gk[j] = i kgrad_j (pref / k^2) dk / n^3   (j = x, y, z); grid (cdiv(NC, 256), B)
 __global__ void green_kernel(const cufftComplex* __restrict__ dk, cufftComplex* __restrict__ gk,
                              int n, float kf, SArg pref_norm) {
+  pdl_enter();
   const int nh = n / 2 + 1;
   const int NC = n * n * nh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -332,6 +335,7 @@ __global__ void green_kernel(const cufftComplex* __restrict__ dk, cufftComplex* 
 // gradient flipped; the Hermitian weights of the half spectrum cancel, see sim_gravity_adjoint)
 __global__ void green_adj_kernel(const cufftComplex* __restrict__ lk, cufftComplex* __restrict__ yk,
                                  int n, float kf, SArg pref_norm) {
+  pdl_enter();
   const int nh = n / 2 + 1;
   const int NC = n * n * nh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -366,7 +370,7 @@ sim_status launch_gravity(const float* delta, float* g, cufftComplex* dk, cufftC
   DH_TRY(plans.set_stream(st));
   DH_TRY(fft_exec_r2c(plans.r2c1, delta, dk));
   const float kf = (float)(2.0 * M_PI / box);
-  green_kernel<<<dim3(cdiv(NC, 256), B), 256, 0, st>>>(dk, gk, n, kf, pref_norm);
+  DH_CUDA_TRY((launch_pdl(green_kernel, dim3(cdiv(NC, 256), B), 256, 0, st, dk, gk, n, kf, pref_norm)));
   DH_LAUNCH_CHECK();
   DH_TRY(fft_exec_c2r(plans.c2r3, gk, g));
   return SIM_OK;
@@ -383,7 +387,7 @@ sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftCom
   DH_TRY(plans.set_stream(st));
   DH_TRY(fft_exec_r2c(plans.r2c3, lam_g, gk));
   const float kf = (float)(2.0 * M_PI / box);
-  green_adj_kernel<<<dim3(cdiv(NC, 256), B), 256, 0, st>>>(gk, dk, n, kf, pref_norm);
+  DH_CUDA_TRY((launch_pdl(green_adj_kernel, dim3(cdiv(NC, 256), B), 256, 0, st, gk, dk, n, kf, pref_norm)));
   DH_LAUNCH_CHECK();
   DH_TRY(fft_exec_c2r(plans.c2r1, dk, lam_delta));
   return SIM_OK;
@@ -392,6 +396,7 @@ sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftCom
 // ------------------------------------------------------------------ readout, kick, drift
 __global__ void interp_kernel(const float* __restrict__ grid, int nf, int n, float inv_dx,
                               const float* __restrict__ s, float* __restrict__ out) {
+  pdl_enter();
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   if (!q.ok) return;
@@ -416,7 +421,7 @@ __global__ void interp_kernel(const float* __restrict__ grid, int nf, int n, flo
 
 sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
                          float* out, int B, cudaStream_t st) {
-  interp_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(grid, nf, n, inv_dx, s, out);
+  DH_CUDA_TRY((launch_pdl(interp_kernel, particle_grid(n, kPT, B), kPT, 0, st, grid, nf, n, inv_dx, s, out)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -444,6 +449,7 @@ __global__ void __launch_bounds__(128, 12) kick_drift_kernel(float* __restrict__
                                   const float* __restrict__ g, SArg Ka, SArg dtaua,
                                   const float* __restrict__ zhat, float* __restrict__ aux,
                                   int n, float inv_dx) {
+  pdl_enter();
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   if (!q.ok) return;
@@ -481,8 +487,8 @@ __global__ void __launch_bounds__(128, 12) kick_drift_kernel(float* __restrict__
 sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
                              const float* zhat, float* aux, int n, float inv_dx, int B,
                              cudaStream_t st) {
-  kick_drift_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, p, g, K, dtau, zhat, aux, n,
-                                                               inv_dx);
+  DH_CUDA_TRY((launch_pdl(kick_drift_kernel, particle_grid(n, kPT, B), kPT, 0, st, s, p, g, K, dtau, zhat, aux, n,
+                                                               inv_dx)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -490,6 +496,7 @@ sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dt
 // grid (cdiv(N3, 256), B)
 __global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__ g, SArg Ka,
                                 int N3) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (i >= N3) return;
@@ -511,7 +518,7 @@ __global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__
 
 sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cudaStream_t st) {
   const int N3 = n * n * n;
-  gas_kick_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(gas, g, K, N3);
+  DH_CUDA_TRY((launch_pdl(gas_kick_kernel, dim3(cdiv(N3, 256), B), 256, 0, st, gas, g, K, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -526,6 +533,7 @@ __global__ void kick_drift_adj_kernel(const float* __restrict__ s0, const float*
                                       float4* __restrict__ lam_g4, DPart dK, DPart ddtau,
                                       const float* __restrict__ gas_u, float* __restrict__ lam_gas,
                                       int n, float inv_dx) {
+  pdl_enter();
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   const size_t o3 = (size_t)q.b * 3 * N3;
@@ -650,8 +658,7 @@ sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const flo
                                      SArg dtau, float* lam_s, float* lam_p, float4* lam_g4,
                                      DPart dK, DPart ddtau, const float* gas_u, float* lam_gas,
                                      int n, float inv_dx, int B, cudaStream_t st) {
-  kick_drift_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(
-      s0, p0, g, K, dtau, lam_s, lam_p, lam_g4, dK, ddtau, gas_u, lam_gas, n, inv_dx);
+  DH_CUDA_TRY((launch_pdl(kick_drift_adj_kernel, particle_grid(n, kPT, B), kPT, 0, st, s0, p0, g, K, dtau, lam_s, lam_p, lam_g4, dK, ddtau, gas_u, lam_gas, n, inv_dx)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -659,6 +666,7 @@ sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const flo
 __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __restrict__ ld,
                                    SArg cma, float* __restrict__ lam_s, DPart dcm, int n,
                                    float inv_dx) {
+  pdl_enter();
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
   s += (size_t)q.b * 3 * N3;
@@ -692,8 +700,8 @@ __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __r
 sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg cm,
                                   float* lam_s, DPart dcm, int n, float inv_dx, int B,
                                   cudaStream_t st) {
-  deposit_adj_kernel<<<particle_grid(n, kPT, B), kPT, 0, st>>>(s, lam_delta, cm, lam_s, dcm, n,
-                                                               inv_dx);
+  DH_CUDA_TRY((launch_pdl(deposit_adj_kernel, particle_grid(n, kPT, B), kPT, 0, st, s, lam_delta, cm, lam_s, dcm, n,
+                                                               inv_dx)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -701,6 +709,7 @@ sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg c
 // grid (blocks, B): lam_g[b][j][i] = lam_g4[b][i].j, out.at(b) += sum lam_g4[b][i].j g[b][j][i]
 __global__ void unpack_dot_kernel(const float4* __restrict__ lam_g4, const float* __restrict__ g,
                                   float* __restrict__ lam_g, DPart out, long long N3) {
+  pdl_enter();
   const int b = blockIdx.y;
   lam_g4 += (size_t)b * N3;
   g += (size_t)b * 3 * N3;
@@ -723,7 +732,7 @@ sim_status launch_unpack_dot(const float4* lam_g4, const float* g, float* lam_g,
   int blocks = cdiv(N3, 256);
   const int cap = cdiv(152 * 16, B);
   if (blocks > cap) blocks = cap;
-  unpack_dot_kernel<<<dim3(blocks, B), 256, 0, st>>>(lam_g4, g, lam_g, out, N3);
+  DH_CUDA_TRY((launch_pdl(unpack_dot_kernel, dim3(blocks, B), 256, 0, st, lam_g4, g, lam_g, out, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -731,6 +740,7 @@ sim_status launch_unpack_dot(const float4* lam_g4, const float* g, float* lam_g,
 // grid (blocks, B): instance b sums a[b count + i] b[b count + i]
 __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ bv,
                            long long count, DPart out) {
+  pdl_enter();
   const int b = blockIdx.y;
   a += (size_t)b * count;
   bv += (size_t)b * count;
@@ -746,19 +756,20 @@ sim_status launch_dot(const float* a, const float* b, long long count, DPart out
   int blocks = cdiv(count, 256);
   const int cap = cdiv(152 * 16, B);
   if (blocks > cap) blocks = cap;
-  dot_kernel<<<dim3(blocks, B), 256, 0, st>>>(a, b, count, out);
+  DH_CUDA_TRY((launch_pdl(dot_kernel, dim3(blocks, B), 256, 0, st, a, b, count, out)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 __global__ void axpy_kernel(float alpha, const float* __restrict__ x, float* __restrict__ y,
                             long long count) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) y[i] += alpha * x[i];
 }
 
 sim_status launch_axpy(float alpha, const float* x, float* y, long long count, cudaStream_t st) {
-  axpy_kernel<<<cdiv(count, 256), 256, 0, st>>>(alpha, x, y, count);
+  DH_CUDA_TRY((launch_pdl(axpy_kernel, cdiv(count, 256), 256, 0, st, alpha, x, y, count)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -766,6 +777,7 @@ sim_status launch_axpy(float alpha, const float* x, float* y, long long count, c
 // y[b][ystride] += x[b][count] over B instances (first `count` floats of each y block)
 __global__ void axpy_strided_kernel(const float* __restrict__ x, float* __restrict__ y,
                                     long long count, long long ystride) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (i < count) y[(size_t)b * ystride + i] += x[(size_t)b * count + i];
@@ -773,7 +785,7 @@ __global__ void axpy_strided_kernel(const float* __restrict__ x, float* __restri
 
 sim_status launch_add_strided(const float* x, float* y, long long count, long long ystride,
                               int B, cudaStream_t st) {
-  axpy_strided_kernel<<<dim3(cdiv(count, 256), B), 256, 0, st>>>(x, y, count, ystride);
+  DH_CUDA_TRY((launch_pdl(axpy_strided_kernel, dim3(cdiv(count, 256), B), 256, 0, st, x, y, count, ystride)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -782,6 +794,7 @@ sim_status launch_add_strided(const float* x, float* y, long long count, long lo
 __global__ void density_loss_kernel(const float* __restrict__ gas, const float* __restrict__ t,
                                     float c, float* __restrict__ grad, double* __restrict__ loss,
                                     long long N3) {
+  pdl_enter();
   const int b = blockIdx.y;
   const float* rho = gas + (size_t)b * 5 * N3;
   t += (size_t)b * N3;
@@ -802,6 +815,7 @@ __global__ void density_loss_kernel(const float* __restrict__ gas, const float* 
 __global__ void thermal_loss_kernel(const float* __restrict__ gas, const float* __restrict__ t,
                                     float c, float* __restrict__ grad, double* __restrict__ loss,
                                     long long N3) {
+  pdl_enter();
   const int b = blockIdx.y;
   const float* g = gas + (size_t)b * 5 * N3;
   t += (size_t)b * N3;
@@ -829,7 +843,7 @@ sim_status launch_thermal_loss(const float* gas, const float* target, float c, f
   int blocks = cdiv(N3, 256);
   const int cap = cdiv(152 * 16, B);
   if (blocks > cap) blocks = cap;
-  thermal_loss_kernel<<<dim3(blocks, B), 256, 0, st>>>(gas, target, c, grad, loss, N3);
+  DH_CUDA_TRY((launch_pdl(thermal_loss_kernel, dim3(blocks, B), 256, 0, st, gas, target, c, grad, loss, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -839,7 +853,7 @@ sim_status launch_density_loss(const float* gas, const float* target, float c, f
   int blocks = cdiv(N3, 256);
   const int cap = cdiv(152 * 16, B);
   if (blocks > cap) blocks = cap;
-  density_loss_kernel<<<dim3(blocks, B), 256, 0, st>>>(gas, target, c, grad, loss, N3);
+  DH_CUDA_TRY((launch_pdl(density_loss_kernel, dim3(blocks, B), 256, 0, st, gas, target, c, grad, loss, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

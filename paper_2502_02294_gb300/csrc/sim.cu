@@ -715,6 +715,7 @@ __global__ void param_chain_kernel(const double* __restrict__ slots,
                                    const double* __restrict__ pch,
                                    const double* __restrict__ glob, int ics, int accumulate,
                                    double* __restrict__ out) {
+  pdl_enter();
   __shared__ double red[256];
   const int b = blockIdx.x;
   double acc = 0.0;
@@ -755,10 +756,10 @@ static sim_status launch_param_chain(sim_t* h, int first, int last, const double
                                      int flush_step, bool ics, bool accumulate, double* out,
                                      const double* slots_first) {
   const int B = h->B;
-  param_chain_kernel<<<B, 256, 0, h->st>>>(slots_first, h->dcoef + (size_t)first * B * SL_N,
+  DH_CUDA_TRY((launch_pdl(param_chain_kernel, B, 256, 0, h->st, slots_first, h->dcoef + (size_t)first * B * SL_N,
                                            last - first, B, flush,
                                            h->d_cpref + (size_t)flush_step * B, h->d_pch,
-                                           h->dglob, ics ? 1 : 0, accumulate ? 1 : 0, out);
+                                           h->dglob, ics ? 1 : 0, accumulate ? 1 : 0, out)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

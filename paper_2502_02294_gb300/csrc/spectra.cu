@@ -8,6 +8,7 @@ namespace dh {
 
 __global__ void pk_bin_kernel(const cufftComplex* __restrict__ a, const cufftComplex* __restrict__ b,
                               int n, int nbins, double* __restrict__ sums) {
+  pdl_enter();
   extern __shared__ double hist[];  // 3 * nbins: weight, weight*|k|, weight*power
   for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x) hist[j] = 0.0;
   __syncthreads();
@@ -38,6 +39,7 @@ __global__ void pk_bin_kernel(const cufftComplex* __restrict__ a, const cufftCom
 __global__ void pk_finish_kernel(const double* __restrict__ sums, int nbins, double kf,
                                  double norm, double* __restrict__ k, double* __restrict__ pk,
                                  double* __restrict__ nm) {
+  pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nbins) return;
   const double w = sums[j];
@@ -54,6 +56,7 @@ __global__ void pk_finish_kernel(const double* __restrict__ sums, int nbins, dou
 __global__ void pk_adj_scale_kernel(cufftComplex* __restrict__ ak, int n, int nbins,
                                     const double* __restrict__ dL_dpk,
                                     const double* __restrict__ sums, double norm) {
+  pdl_enter();
   const int nh = n / 2 + 1;
   const long long NC = (long long)n * n * nh;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < NC;
@@ -107,7 +110,7 @@ extern "C" sim_status sim_power_spectrum_adjoint(const float* a, int32_t n, doub
   int blocks = cdiv(NC, 256);
   if (blocks > 152 * 4) blocks = 152 * 4;
   if (r == SIM_OK) {  // mode weights per bin (the power sums are not needed)
-    pk_bin_kernel<<<blocks, 256, 3 * nbins * sizeof(double), st>>>(ak, ak, n, nbins, sums);
+    DH_CUDA_TRY((launch_pdl(pk_bin_kernel, blocks, 256, 3 * nbins * sizeof(double), st, ak, ak, n, nbins, sums)));
     count_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("pk_bin_kernel launch failed");
@@ -116,7 +119,7 @@ extern "C" sim_status sim_power_spectrum_adjoint(const float* a, int32_t n, doub
   }
   if (r == SIM_OK) {
     const double norm = box * box * box / ((double)n * n * n * (double)n * n * n);
-    pk_adj_scale_kernel<<<blocks, 256, 0, st>>>(ak, n, nbins, dL_dpk, sums, norm);
+    DH_CUDA_TRY((launch_pdl(pk_adj_scale_kernel, blocks, 256, 0, st, ak, n, nbins, dL_dpk, sums, norm)));
     count_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("pk_adj_scale_kernel launch failed");
@@ -170,7 +173,7 @@ extern "C" sim_status sim_power_spectrum(const float* a, const float* b, int32_t
   if (r == SIM_OK) {
     int blocks = cdiv(NC, 256);
     if (blocks > 152 * 4) blocks = 152 * 4;
-    pk_bin_kernel<<<blocks, 256, 3 * nbins * sizeof(double), st>>>(ak, bk, n, nbins, sums);
+    DH_CUDA_TRY((launch_pdl(pk_bin_kernel, blocks, 256, 3 * nbins * sizeof(double), st, ak, bk, n, nbins, sums)));
     count_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("pk_bin_kernel launch failed");
@@ -179,8 +182,8 @@ extern "C" sim_status sim_power_spectrum(const float* a, const float* b, int32_t
   }
   if (r == SIM_OK) {
     const double norm = box * box * box / ((double)n * n * n * (double)n * n * n);
-    pk_finish_kernel<<<cdiv(nbins, 128), 128, 0, st>>>(sums, nbins, 2.0 * M_PI / box, norm, k,
-                                                        pk, nmodes);
+    DH_CUDA_TRY((launch_pdl(pk_finish_kernel, cdiv(nbins, 128), 128, 0, st, sums, nbins, 2.0 * M_PI / box, norm, k,
+                                                        pk, nmodes)));
     count_launch();
     if (cudaGetLastError() != cudaSuccess) {
       set_error("pk_finish_kernel launch failed");

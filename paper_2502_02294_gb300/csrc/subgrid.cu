@@ -89,6 +89,7 @@ __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__
                                SubArg ca, float* __restrict__ zhat,
                                uint32_t* __restrict__ events, float* __restrict__ gd_out,
                                long long N3) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   in += (size_t)b * 5 * N3;
@@ -124,6 +125,7 @@ __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__
 __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restrict__ lam,
                                    SubArg ca, DPart dpar_b, DPart dfb_b,
                                    const float* __restrict__ gd_in, long long N3) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   in += (size_t)b * 5 * N3;
@@ -196,14 +198,14 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
 
 sim_status launch_subgrid(const float* in, float* out, SubArg c, float* zhat,
                           uint32_t* events, long long N3, int B, cudaStream_t st, float* gd) {
-  subgrid_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, out, c, zhat, events, gd, N3);
+  DH_CUDA_TRY((launch_pdl(subgrid_kernel, dim3(cdiv(N3, 256), B), 256, 0, st, in, out, c, zhat, events, gd, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
 
 sim_status launch_subgrid_adjoint(const float* in, float* lam, SubArg c, DPart dpar, DPart dfb,
                                   long long N3, int B, cudaStream_t st, const float* gd) {
-  subgrid_adj_kernel<<<dim3(cdiv(N3, 256), B), 256, 0, st>>>(in, lam, c, dpar, dfb, gd, N3);
+  DH_CUDA_TRY((launch_pdl(subgrid_adj_kernel, dim3(cdiv(N3, 256), B), 256, 0, st, in, lam, c, dpar, dfb, gd, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -216,6 +218,7 @@ __device__ __forceinline__ float max_keep_nan(float a, float b) {
 
 __global__ void signal_speed_kernel(const float* __restrict__ u, float gam, long long N3,
                                     unsigned int* __restrict__ out) {
+  pdl_enter();
   const int b = blockIdx.y;
   u += (size_t)b * 5 * N3;
   out += b;
@@ -245,7 +248,7 @@ sim_status launch_signal_speed(const float* gas, float gamma, long long N3,
   int blocks = cdiv(N3, 256);
   const int cap = cdiv(152 * 8, B);
   if (blocks > cap) blocks = cap;
-  signal_speed_kernel<<<dim3(blocks, B), 256, 0, st>>>(gas, gamma, N3, out_bits);
+  DH_CUDA_TRY((launch_pdl(signal_speed_kernel, dim3(blocks, B), 256, 0, st, gas, gamma, N3, out_bits)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -294,6 +297,7 @@ extern "C" sim_status sim_subgrid_adjoint(const float* gas_in, float* lam, int32
 
 __global__ void philox_kernel(uint32_t k0, uint32_t k1, uint32_t step, uint32_t inst,
                               uint32_t tag, long long count, uint32_t* out) {
+  pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const uint4 w = philox4x32_10(make_uint4((uint32_t)i, step, inst, tag), k0, k1);
@@ -307,8 +311,7 @@ extern "C" sim_status sim_philox(uint64_t seed, uint32_t step, uint32_t instance
     return SIM_EINVAL;
   }
   if (count == 0) return SIM_OK;
-  philox_kernel<<<cdiv(count, 256), 256, 0, (cudaStream_t)stream>>>(
-      (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32), step, instance, tag, count, out);
+  DH_CUDA_TRY((launch_pdl(philox_kernel, cdiv(count, 256), 256, 0, (cudaStream_t)stream, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32), step, instance, tag, count, out)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
