@@ -181,6 +181,74 @@ def bench_batched(dh, synth, torch, steps: int, warmup: int):
                                for n, v in zip(BATCH_SIZES, variants)}}
 
 
+def bench_256(dh, synth, torch, peak_bw: float, steps: int = 2):
+    """The same iteration (ICs, 100-step run, posterior, checkpointed reverse pass, Adam) at
+    256^3 cells + 256^3 particles in a 256 Mpc/h box, where the state (335 MB of gas) no
+    longer fits in L2: forward and forward + adjoint rates, and the sweep classes of one
+    eager pass against the HBM copy peak."""
+    n = 256
+    p = dh.default_params(**dict(WORKLOAD, n=n, box=float(n)))
+    n3 = n ** 3
+    dev = torch.device("cuda", torch.cuda.current_device())
+    noise = torch.from_numpy(synth.white_noise(n, 100).astype("float32")).to(dev)
+    sim = dh.Simulation(p, noise)
+    variants = sim.autotune(reps=2)
+    sim.set_graphs(True)
+    sim.run()
+    data = sim.state()["gas"][0].clone()
+    sigma_n = FLI_NOISE_FRAC * data.std().item()
+    x = noise.clone()
+    mom = torch.zeros_like(x)
+    vel = torch.zeros_like(x)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def it():
+        x.copy_(noise)
+        sim.fli_step(x, mom, vel, data, sigma_n, FLI_LR, 1, loss=loss)
+
+    def timed(fn):
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    it()
+    ms = timed(it)
+    sim.set_tape_recording(0)
+
+    def fwd():
+        sim.reinit(noise)
+        sim.run()
+
+    fwd()
+    fwd_ms = timed(fwd)
+    sim.set_tape_recording(1)
+    sim.kernel_timing(True)
+    sim.kernel_times(reset=True)
+    it()
+    torch.cuda.synchronize()
+    kt = sim.kernel_times(reset=True)
+    sim.kernel_timing(False)
+    sim.close()
+    classes = {}
+    for name in ("sweep", "sweep_adjoint"):
+        tot, cnt = kt[name]
+        avg = tot / max(cnt, 1)
+        gbs = CLASS_BYTES_PER_CELL[name] * n3 / (avg * 1e-3) / 1e9
+        classes[name] = {"launches": cnt, "avg_launch_ms": avg, "achieved_gbs": gbs,
+                         "frac_of_peak": gbs / peak_bw}
+    return {"workload": "as the headline at 256^3 cells + 256^3 particles, box 256 Mpc/h",
+            "value": n3 * p.n_steps / (ms * 1e-3), "ms_per_step": ms,
+            "fwd_value": n3 * p.n_steps / (fwd_ms * 1e-3), "fwd_ms_per_step": fwd_ms,
+            "unit": "cell-steps/s", "sweep_variants": {"fwd": variants[0], "adj": variants[1]},
+            "classes": classes}
+
+
 def bench_lbfgs(dh, synth, torch, sim, truth, p, iters: int):
     """Sec. 3.2 as the paper runs it: subgrid off, the delta_b T probe (internal energy
     density), pixel noise of variance 1x (S/N = 1) and 5x (S/N = 5) the data variance,
@@ -413,6 +481,8 @@ def main():
                     help="x,y,z forward and x,y,z adjoint sweep forms (SWEEP_* codes, six "
                          "comma-separated) instead of the autotuner's choice, e.g. for a "
                          "profiler run, under which the autotuner's timings are distorted")
+    ap.add_argument("--no-256", action="store_true",
+                    help="skip the same iteration at 256^3")
     ap.add_argument("--no-full-tape", action="store_true",
                     help="skip the variant that records every segment's tape during the run")
     ap.add_argument("--no-graphs", action="store_true",
@@ -640,6 +710,14 @@ def main():
         extra["pk_hmc"] = inference.pk_hmc_experiment(dh)
         torch.cuda.set_stream(stream)
 
+    # ---- the same iteration at 256^3 (state beyond L2)
+    run256 = None
+    if not args.no_256 and ws == 1:
+        pk = _peaks()
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        run256 = bench_256(dh, synth, torch, pk["hbm_gbs"] if pk else 6800.0)
+        torch.cuda.set_stream(stream)
+
     # ---- batched parameter-sampling form (96 instances on three grid sizes)
     batched = None
     if not args.no_batched:
@@ -706,6 +784,8 @@ def main():
     }
     if full_tape is not None:
         line["fli_full_tape"] = full_tape
+    if run256 is not None:
+        line["run_256"] = run256
     if fli is not None:
         line["fli"] = fli
     if lbfgs_rec is not None:
