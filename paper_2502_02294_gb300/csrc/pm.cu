@@ -665,7 +665,8 @@ sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const flo
 
 __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __restrict__ ld,
                                    SArg cma, float* __restrict__ lam_s, DPart dcm, int n,
-                                   float inv_dx) {
+                                   float inv_dx, float* __restrict__ lam_rho,
+                                   long long rho_stride) {
   pdl_enter();
   const int N3 = n * n * n;
   const PIdx q = particle_index(n);
@@ -693,15 +694,17 @@ __global__ void deposit_adj_kernel(const float* __restrict__ s, const float* __r
         }
 #pragma unroll
     for (int j = 0; j < 3; ++j) lam_s[j * N3 + i] += cm * gs[j];
+    // the cell of this particle's lattice site: one particle per cell
+    if (lam_rho) lam_rho[(size_t)q.b * rho_stride + i] += __ldg(ld + i);
   }
   if (dcm.p) block_sum_atomic(itp, dcm.at(q.b));
 }
 
 sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg cm,
                                   float* lam_s, DPart dcm, int n, float inv_dx, int B,
-                                  cudaStream_t st) {
-  DH_CUDA_TRY((launch_pdl(deposit_adj_kernel, particle_grid(n, kPT, B), kPT, 0, st, s, lam_delta, cm, lam_s, dcm, n,
-                                                               inv_dx)));
+                                  cudaStream_t st, float* lam_rho, long long rho_stride) {
+  DH_CUDA_TRY((launch_pdl(deposit_adj_kernel, particle_grid(n, kPT, B), kPT, 0, st, s, lam_delta,
+                          cm, lam_s, dcm, n, inv_dx, lam_rho, rho_stride)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

@@ -75,10 +75,12 @@ sim_status launch_kick_drift_adjoint(const float* s0, const float* p0, const flo
                                      DPart dK, DPart ddtau, const float* gas_u, float* lam_gas,
                                      int n, float inv_dx, int B, cudaStream_t st);
 // Deposit adjoint for delta = cm * count + rho_gas - 1:
-//   lam_s += cm grad(interp lam_delta)(s) / dx ; d_cm += sum_p interp(lam_delta)(s_p)
+//   lam_s += cm grad(interp lam_delta)(s) / dx ; d_cm += sum_p interp(lam_delta)(s_p);
+//   lam_rho (may be NULL; instance stride rho_stride) += lam_delta cell by cell
 sim_status launch_deposit_adjoint(const float* s, const float* lam_delta, SArg cm,
                                   float* lam_s, DPart dcm, int n, float inv_dx, int B,
-                                  cudaStream_t st);
+                                  cudaStream_t st, float* lam_rho = nullptr,
+                                  long long rho_stride = 0);
 // lam_g[b][j][i] = lam_g4[b][i].j (j = x, y, z) and out.at(b) += sum_{i,j} lam_g4 g (the
 // force-field dot product), per instance
 sim_status launch_unpack_dot(const float4* lam_g4, const float* g, float* lam_g, DPart out,

@@ -529,7 +529,7 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     zh = fwd ? h->zhat : nullptr;
     DH_TRY(timed(h, SIM_KT_SUBGRID, [&] {
       return launch_subgrid(cur, out, sub_at(h, i), zh, fwd ? h->events : nullptr, h->N3, B, st,
-                            T ? T->gd : nullptr);
+                            T ? T->gd : nullptr, zh ? h->star : nullptr);
     }));
     cur = out;
   } else if (T) {
@@ -558,7 +558,6 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     if (P.gravity_on)
       DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(*gas, g, K2, h->n, B, st); }));
   }
-  if (zh) DH_TRY(launch_axpy(1.0f, zh, h->star, B * h->N3, st));
   // 6. learned correction of the gas fields (solver in the loop, Sec. 4)
   if (h->closure) DH_TRY(closure_apply(h->closure, *gas, h->n, B, st));
   // 7. diagnostics of the state after the step (steps of the run, not the recompute)
@@ -639,9 +638,10 @@ static sim_status force_adjoint(sim_t* h, const float* s, const float* g, SArg p
                                   h->prm.box, pn, B, h->plans, st);
   }));
   return timed(h, SIM_KT_DEPOSIT_ADJOINT, [&] {
-    DH_TRY(launch_add_strided(h->lam_delta, h->lam_gas, h->N3, 5 * h->N3, B, st));
+    // with lam_rho += lam_delta (d delta / d rho_gas = 1) for each particle's own cell
     return launch_deposit_adjoint(s, h->lam_delta, sarg(h->d_cm), h->lam_s,
-                                  slot_part(slot, SL_DCM), h->n, (float)h->inv_dx, B, st);
+                                  slot_part(slot, SL_DCM), h->n, (float)h->inv_dx, B, st,
+                                  h->lam_gas, 5 * h->N3);
   });
 }
 

@@ -84,11 +84,12 @@ __device__ __forceinline__ float gumbel_diff(const SubgridConst& c, long long i)
 }
 
 // grid (cdiv(N3, 256), B); instance b uses constants ca.at(b)
-// gd_out (may be NULL): g0 - g1 of every cell, for the adjoint of the same step
+// gd_out (may be NULL): g0 - g1 of every cell, for the adjoint of the same step; star (may
+// be NULL, used with zhat): the star mesh, += zhat
 __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__ out,
                                SubArg ca, float* __restrict__ zhat,
                                uint32_t* __restrict__ events, float* __restrict__ gd_out,
-                               long long N3) {
+                               float* __restrict__ star, long long N3) {
   pdl_enter();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
@@ -112,7 +113,10 @@ __global__ void subgrid_kernel(const float* __restrict__ in, float* __restrict__
       for (int k = 0; k < 4; ++k) out[k * N3 + i] = u[k];
     }
     out[4 * N3 + i] = r.ke + c.a2 * u[0] * r.e2;
-    if (zhat) zhat[i] = r.zhat;
+    if (zhat) {
+      zhat[i] = r.zhat;
+      if (star) star[(size_t)b * N3 + i] += r.zhat;
+    }
   }
   const unsigned mask = __ballot_sync(0xffffffffu, ev);
   if (events && (threadIdx.x & 31) == 0) {
@@ -197,8 +201,9 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
 }
 
 sim_status launch_subgrid(const float* in, float* out, SubArg c, float* zhat,
-                          uint32_t* events, long long N3, int B, cudaStream_t st, float* gd) {
-  DH_CUDA_TRY((launch_pdl(subgrid_kernel, dim3(cdiv(N3, 256), B), 256, 0, st, in, out, c, zhat, events, gd, N3)));
+                          uint32_t* events, long long N3, int B, cudaStream_t st, float* gd,
+                          float* star) {
+  DH_CUDA_TRY((launch_pdl(subgrid_kernel, dim3(cdiv(N3, 256), B), 256, 0, st, in, out, c, zhat, events, gd, star, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

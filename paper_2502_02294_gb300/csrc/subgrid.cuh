@@ -32,10 +32,11 @@ double temperature_per_energy(double gamma, double mu);
 
 // B instances one after another (as the PM launchers).
 // out = subgrid(in) (may alias); zhat (n^3) and events (ceil(n^3/32) words) may be NULL
-// gd (may be NULL): receives g0 - g1 of every cell ([B][n^3]) for the adjoint of this step
+// gd (may be NULL): receives g0 - g1 of every cell ([B][n^3]) for the adjoint of this step;
+// star (may be NULL, with zhat): the star mesh, += zhat
 sim_status launch_subgrid(const float* in, float* out, SubArg c, float* zhat,
                           uint32_t* events, long long N3, int B, cudaStream_t st,
-                          float* gd = nullptr);
+                          float* gd = nullptr, float* star = nullptr);
 // lam (5 n^3) in/out through the update at `in`; dpar[SIM_P_*] and dfb accumulated.
 // gd (may be NULL): the forward's g0 - g1 (else the pair is drawn again from Philox)
 sim_status launch_subgrid_adjoint(const float* in, float* lam, SubArg c, DPart dpar, DPart dfb,
