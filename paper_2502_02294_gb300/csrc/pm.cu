@@ -494,31 +494,35 @@ sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dt
 }
 
 // grid (cdiv(N3, 256), B)
-__global__ void gas_kick_kernel(float* __restrict__ u, const float* __restrict__ g, SArg Ka,
-                                int N3) {
+// out may be in (in place); out of place the density is copied along
+__global__ void gas_kick_kernel(const float* in, float* out, const float* __restrict__ g,
+                                SArg Ka, int N3) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (i >= N3) return;
-  u += (size_t)b * 5 * N3;
+  in += (size_t)b * 5 * N3;
+  out += (size_t)b * 5 * N3;
   g += (size_t)b * 3 * N3;
   const float K = Ka.at(b);
-  const float rho = u[i];
+  const float rho = in[i];
+  if (out != in) out[i] = rho;
   float mg = 0.0f, g2 = 0.0f;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const float gj = g[j * N3 + i];
-    const float mj = u[(1 + j) * N3 + i];
+    const float mj = in[(1 + j) * N3 + i];
     mg += mj * gj;
     g2 += gj * gj;
-    u[(1 + j) * N3 + i] = mj + rho * gj * K;
+    out[(1 + j) * N3 + i] = mj + rho * gj * K;
   }
-  u[4 * N3 + i] += K * mg + 0.5f * K * K * rho * g2;
+  out[4 * N3 + i] = in[4 * N3 + i] + (K * mg + 0.5f * K * K * rho * g2);
 }
 
-sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cudaStream_t st) {
+sim_status launch_gas_kick(const float* in, float* out, const float* g, SArg K, int n, int B,
+                           cudaStream_t st) {
   const int N3 = n * n * n;
-  DH_CUDA_TRY((launch_pdl(gas_kick_kernel, dim3(cdiv(N3, 256), B), 256, 0, st, gas, g, K, N3)));
+  DH_CUDA_TRY((launch_pdl(gas_kick_kernel, dim3(cdiv(N3, 256), B), 256, 0, st, in, out, g, K, N3)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

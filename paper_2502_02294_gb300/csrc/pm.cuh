@@ -54,8 +54,10 @@ sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const f
 sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
                              const float* zhat, float* aux, int n, float inv_dx, int B,
                              cudaStream_t st);
-// m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2 (gas 5 n^3, g 3 n^3)
-sim_status launch_gas_kick(float* gas, const float* g, SArg K, int n, int B, cudaStream_t st);
+// out = in with m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2 (gas 5 n^3, g 3 n^3; out may
+// be in)
+sim_status launch_gas_kick(const float* in, float* out, const float* g, SArg K, int n, int B,
+                           cudaStream_t st);
 
 // ---- adjoints
 // The adjoint of the force field is accumulated node-interleaved: lam_g4[b][i] = (lam_gx,

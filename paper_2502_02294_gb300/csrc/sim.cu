@@ -486,11 +486,17 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   const SArg K1 = sc(h, i, merged_in ? SC_KM : SC_K1), K2 = sc(h, i, SC_K2);
   const bool fwd = !T || primary;
   float* zh_prev = (merged_in && P.subgrid_on && fwd) ? h->zhat : nullptr;
+  // a step with a merged opening kick records into a chained slot (tape_slot): its input
+  // state, positions and force are already on the tape as the previous step's outputs, and
+  // *gas (not updated by that step) is not read
+  const bool chained = T && merged_in;
   if (T) {
-    DH_TRY(dcopy(T->U0, *gas, gb, st));
-    DH_TRY(dcopy(T->s0, s, vb, st));
+    if (!chained) {
+      DH_TRY(dcopy(T->U0, *gas, gb, st));
+      DH_TRY(dcopy(T->s0, s, vb, st));
+      DH_TRY(dcopy(T->g0, g, vb, st));
+    }
     DH_TRY(dcopy(T->p0, p, vb, st));
-    DH_TRY(dcopy(T->g0, g, vb, st));
   }
   // 1. half kick + drift
   DH_TRY(timed(h, SIM_KT_KICK, [&] {
@@ -499,11 +505,15 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   }));
   float* cur = *gas;
   if (T) {
-    DH_TRY(dcopy(T->Uk1, cur, gb, st));
+    // the gas kick out of place from the recorded input state into the slot's Uk1
+    if (P.gravity_on)
+      DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(T->U0, T->Uk1, g, K1, h->n, B, st); }));
+    else
+      DH_TRY(dcopy(T->Uk1, T->U0, gb, st));
     cur = T->Uk1;
+  } else if (P.gravity_on) {
+    DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(cur, cur, g, K1, h->n, B, st); }));
   }
-  if (P.gravity_on)
-    DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(cur, g, K1, h->n, B, st); }));
   // 2. sweeps
   if (P.hydro_on) {
     const char* order = kOrders[i % 6];
@@ -541,8 +551,12 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   if (T) {
     DH_TRY(dcopy(T->s1, s, vb, st));
     DH_TRY(dcopy(T->g1, g, vb, st));
-    DH_TRY(dcopy(*gas, cur, gb, st));
-    cur = *gas;
+    // *gas takes the state only for the closing kick (the end of a segment, or every step
+    // when kicks are not merged): a chained next step reads it from the tape
+    if (kick_out) {
+      DH_TRY(dcopy(*gas, cur, gb, st));
+      cur = *gas;
+    }
   } else if (cur != *gas) {
     float* t = *gas;
     *gas = *gas_tmp;
@@ -556,7 +570,7 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
                                (float)h->inv_dx, B, st);
     }));
     if (P.gravity_on)
-      DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(*gas, g, K2, h->n, B, st); }));
+      DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(*gas, *gas, g, K2, h->n, B, st); }));
   }
   // 6. learned correction of the gas fields (solver in the loop, Sec. 4)
   if (h->closure) DH_TRY(closure_apply(h->closure, *gas, h->n, B, st));
@@ -602,7 +616,10 @@ static sim_status ensure_adjoint_buffers(sim_t* h, int tape_steps) {
   return SIM_OK;
 }
 
-static TapeSlot tape_slot(sim_t* h, int k) {
+// Slot k of the tape. A chained slot (a step with merged kicks, i.e. not the first of its
+// checkpoint segment, recorded right after the slot before it) takes its input gas state,
+// positions and force from that slot: they are the previous step's Usg, s1 and g1.
+static TapeSlot tape_slot(sim_t* h, int k, bool chained = false) {
   const long long N3 = h->N3 * h->B;
   float* b = h->tape + (size_t)k * kTapeFloatsPerCell * N3;
   TapeSlot t;
@@ -618,6 +635,12 @@ static TapeSlot tape_slot(sim_t* h, int k) {
   t.s1 = b + 39 * N3;
   t.g1 = b + 42 * N3;
   t.gd = b + 45 * N3;
+  if (chained && k > 0) {
+    const float* p = b - (size_t)kTapeFloatsPerCell * N3;
+    t.U0 = const_cast<float*>(p + 25 * N3);  // previous Usg
+    t.s0 = const_cast<float*>(p + 39 * N3);  // previous s1
+    t.g0 = const_cast<float*>(p + 42 * N3);  // previous g1
+  }
   return t;
 }
 
@@ -1080,7 +1103,7 @@ static sim_status run_body(sim_t* h, int n_steps, int min_segments = 0) {
     const bool merged_in = !plain && rel % every != 0;
     const bool kick_out = plain || h->step + 1 == last || (rel + 1) % every == 0;
     const bool rec = record && h->step >= rec_first;
-    const TapeSlot T = rec ? tape_slot(h, h->step - rec_first) : TapeSlot{};
+    const TapeSlot T = rec ? tape_slot(h, h->step - rec_first, merged_in) : TapeSlot{};
     DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, rec ? &T : nullptr,
                         merged_in, kick_out, true));
     h->step += 1;
@@ -1163,13 +1186,14 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
       DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
       DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, first), h->w_g));
       for (int i = first; i < end; ++i) {
-        const TapeSlot T = tape_slot(h, i - first);
+        const TapeSlot T = tape_slot(h, i - first, !plain && i != first);
         DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T,
                             !plain && i != first, plain || i == end - 1));
       }
     }
     for (int i = end - 1; i >= first; --i)
-      DH_TRY(reverse_step(h, i, tape_slot(h, i - base), h->dslots + (size_t)i * B * SL_N,
+      DH_TRY(reverse_step(h, i, tape_slot(h, i - base, !plain && i != first),
+                          h->dslots + (size_t)i * B * SL_N,
                           !plain && i != first, plain || i == end - 1));
   }
   // g at the start of the run is a function of the initial state
