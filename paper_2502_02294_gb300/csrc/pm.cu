@@ -445,7 +445,10 @@ __device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& 
 
 // 40 registers (12 resident blocks per SM instead of 9 at 56): more warps in flight for the
 // CIC gathers (kick class 44.7 -> 43.2 us per launch at 128^3)
-__global__ void __launch_bounds__(128, 12) kick_drift_kernel(float* __restrict__ s, float* __restrict__ p,
+// s_out / p_out may be s / p (in place); out of place the positions are written even when
+// dtau = 0
+__global__ void __launch_bounds__(128, 12) kick_drift_kernel(const float* s, float* s_out,
+                                  const float* p, float* p_out,
                                   const float* __restrict__ g, SArg Ka, SArg dtaua,
                                   const float* __restrict__ zhat, float* __restrict__ aux,
                                   int n, float inv_dx) {
@@ -456,18 +459,21 @@ __global__ void __launch_bounds__(128, 12) kick_drift_kernel(float* __restrict__
   const int i = q.p;
   const size_t o3 = (size_t)q.b * 3 * N3;
   s += o3;
+  s_out += o3;
   p += o3;
+  p_out += o3;
   g += o3;
   const float K = Ka.at(q.b), dtau = dtaua.at(q.b);
   Cic c;
   cic_setup(s, q, N3, n, inv_dx, c);
   float gi[3];
   interp3(g, c, n, N3, gi);
+  const bool moved = s_out != s;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const float pj = p[j * N3 + i] + K * gi[j];
-    p[j * N3 + i] = pj;
-    if (dtau != 0.0f) s[j * N3 + i] += dtau * pj;
+    p_out[j * N3 + i] = pj;
+    if (dtau != 0.0f || moved) s_out[j * N3 + i] = s[j * N3 + i] + dtau * pj;
   }
   // star readout at the position the kick saw (before this launch's drift)
   if (zhat) {
@@ -484,11 +490,11 @@ __global__ void __launch_bounds__(128, 12) kick_drift_kernel(float* __restrict__
   }
 }
 
-sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
-                             const float* zhat, float* aux, int n, float inv_dx, int B,
-                             cudaStream_t st) {
-  DH_CUDA_TRY((launch_pdl(kick_drift_kernel, particle_grid(n, kPT, B), kPT, 0, st, s, p, g, K, dtau, zhat, aux, n,
-                                                               inv_dx)));
+sim_status launch_kick_drift(const float* s, float* s_out, const float* p, float* p_out,
+                             const float* g, SArg K, SArg dtau, const float* zhat, float* aux,
+                             int n, float inv_dx, int B, cudaStream_t st) {
+  DH_CUDA_TRY((launch_pdl(kick_drift_kernel, particle_grid(n, kPT, B), kPT, 0, st, s, s_out, p,
+                          p_out, g, K, dtau, zhat, aux, n, inv_dx)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }

@@ -49,11 +49,12 @@ sim_status launch_gravity_adjoint(const float* lam_g, float* lam_delta, cufftCom
 // out[f][p] = CIC readout of grid f at particle p, nf fields
 sim_status launch_interp(const float* grid, int nf, int n, float inv_dx, const float* s,
                          float* out, int B, cudaStream_t st);
-// p += K interp(g, s); then, if dtau != 0, s += dtau p. If zhat != NULL also
-// aux += interp(zhat, s) at the position before the drift.
-sim_status launch_kick_drift(float* s, float* p, const float* g, SArg K, SArg dtau,
-                             const float* zhat, float* aux, int n, float inv_dx, int B,
-                             cudaStream_t st);
+// p_out = p + K interp(g, s); s_out = s + dtau p_out (s_out / p_out may be s / p: in place,
+// where s is left as it is when dtau = 0). If zhat != NULL also aux += interp(zhat, s) at
+// the position before the drift.
+sim_status launch_kick_drift(const float* s, float* s_out, const float* p, float* p_out,
+                             const float* g, SArg K, SArg dtau, const float* zhat, float* aux,
+                             int n, float inv_dx, int B, cudaStream_t st);
 // out = in with m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2 (gas 5 n^3, g 3 n^3; out may
 // be in)
 sim_status launch_gas_kick(const float* in, float* out, const float* g, SArg K, int n, int B,

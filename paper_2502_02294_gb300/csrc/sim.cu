@@ -476,9 +476,12 @@ static sim_status record_diag(sim_t* h, int idx, const float* gas, const float* 
 // a step of the run itself (star readout, star field, events, diagnostics), as every step
 // without a tape is; a recompute for the reverse pass (T set, primary false) has none of
 // these side effects.
+// Tnext (with T, when the next step records into the chained slot after T): the slot whose
+// p0 takes this step's kicked momenta.
 static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, float* s, float* p,
                                float* g, const TapeSlot* T, bool merged_in = false,
-                               bool kick_out = true, bool primary = false) {
+                               bool kick_out = true, bool primary = false,
+                               const TapeSlot* Tnext = nullptr) {
   const sim_params& P = h->prm;
   const int B = h->B;
   cudaStream_t st = h->st;
@@ -486,28 +489,32 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   const SArg K1 = sc(h, i, merged_in ? SC_KM : SC_K1), K2 = sc(h, i, SC_K2);
   const bool fwd = !T || primary;
   float* zh_prev = (merged_in && P.subgrid_on && fwd) ? h->zhat : nullptr;
-  // a step with a merged opening kick records into a chained slot (tape_slot): its input
-  // state, positions and force are already on the tape as the previous step's outputs, and
-  // *gas (not updated by that step) is not read
+  // With a tape every stage reads and writes the step's slot: the working gas, positions,
+  // momenta and force are read only by the first step of a recorded run of steps and
+  // written back only for the closing kick. A step with a merged opening kick records into
+  // a chained slot (tape_slot): its input state, positions and force are the previous
+  // slot's outputs, and its input momenta were written into its p0 by the previous step.
   const bool chained = T && merged_in;
-  if (T) {
-    if (!chained) {
-      DH_TRY(dcopy(T->U0, *gas, gb, st));
-      DH_TRY(dcopy(T->s0, s, vb, st));
-      DH_TRY(dcopy(T->g0, g, vb, st));
-    }
+  if (T && !chained) {
+    DH_TRY(dcopy(T->U0, *gas, gb, st));
+    DH_TRY(dcopy(T->s0, s, vb, st));
     DH_TRY(dcopy(T->p0, p, vb, st));
+    DH_TRY(dcopy(T->g0, g, vb, st));
   }
-  // 1. half kick + drift
+  // 1. half kick + drift (with a tape: from s0, p0, g0 into s1 and the next slot's p0, or p)
   DH_TRY(timed(h, SIM_KT_KICK, [&] {
-    return launch_kick_drift(s, p, g, K1, sc(h, i, SC_DTAU), zh_prev, zh_prev ? h->aux : nullptr,
-                             h->n, (float)h->inv_dx, B, st);
+    if (T)
+      return launch_kick_drift(T->s0, T->s1, T->p0, Tnext ? Tnext->p0 : p, T->g0, K1,
+                               sc(h, i, SC_DTAU), zh_prev, zh_prev ? h->aux : nullptr, h->n,
+                               (float)h->inv_dx, B, st);
+    return launch_kick_drift(s, s, p, p, g, K1, sc(h, i, SC_DTAU), zh_prev,
+                             zh_prev ? h->aux : nullptr, h->n, (float)h->inv_dx, B, st);
   }));
   float* cur = *gas;
   if (T) {
     // the gas kick out of place from the recorded input state into the slot's Uk1
     if (P.gravity_on)
-      DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(T->U0, T->Uk1, g, K1, h->n, B, st); }));
+      DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(T->U0, T->Uk1, T->g0, K1, h->n, B, st); }));
     else
       DH_TRY(dcopy(T->Uk1, T->U0, gb, st));
     cur = T->Uk1;
@@ -547,14 +554,15 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     cur = T->Usg;
   }
   // 4. force at a_{i+1}
-  DH_TRY(compute_force(h, s, cur, sc(h, i, SC_PN1), g));
+  DH_TRY(compute_force(h, T ? T->s1 : s, cur, sc(h, i, SC_PN1), T ? T->g1 : g));
   if (T) {
-    DH_TRY(dcopy(T->s1, s, vb, st));
-    DH_TRY(dcopy(T->g1, g, vb, st));
-    // *gas takes the state only for the closing kick (the end of a segment, or every step
-    // when kicks are not merged): a chained next step reads it from the tape
+    // the working state takes the step's result only for the closing kick (the end of a
+    // run of recorded steps, or every step when kicks are not merged); the momenta are
+    // already in p then (no next slot)
     if (kick_out) {
       DH_TRY(dcopy(*gas, cur, gb, st));
+      DH_TRY(dcopy(s, T->s1, vb, st));
+      DH_TRY(dcopy(g, T->g1, vb, st));
       cur = *gas;
     }
   } else if (cur != *gas) {
@@ -566,7 +574,7 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
   //    kick when that one is merged
   if (kick_out) {
     DH_TRY(timed(h, SIM_KT_KICK, [&] {
-      return launch_kick_drift(s, p, g, K2, sarg(0.0f), zh, zh ? h->aux : nullptr, h->n,
+      return launch_kick_drift(s, s, p, p, g, K2, sarg(0.0f), zh, zh ? h->aux : nullptr, h->n,
                                (float)h->inv_dx, B, st);
     }));
     if (P.gravity_on)
@@ -1104,8 +1112,10 @@ static sim_status run_body(sim_t* h, int n_steps, int min_segments = 0) {
     const bool kick_out = plain || h->step + 1 == last || (rel + 1) % every == 0;
     const bool rec = record && h->step >= rec_first;
     const TapeSlot T = rec ? tape_slot(h, h->step - rec_first, merged_in) : TapeSlot{};
+    // the next step records into the chained slot after T unless this one closes its kick
+    const TapeSlot Tn = rec && !kick_out ? tape_slot(h, h->step + 1 - rec_first, true) : TapeSlot{};
     DH_TRY(forward_step(h, h->step, &h->gas, &h->gas2, h->s, h->p, h->g, rec ? &T : nullptr,
-                        merged_in, kick_out, true));
+                        merged_in, kick_out, true, rec && !kick_out ? &Tn : nullptr));
     h->step += 1;
     if (h->prm.cfl_max > 0 && h->step < h->prm.n_steps) {
       double c = 0;
@@ -1186,9 +1196,11 @@ static sim_status run_adjoint_body(sim_t* h, const float* dL_dgas, const float* 
       DH_TRY(dcopy(h->w_p, c + 8 * N3, 3 * N3 * sizeof(float), st));
       DH_TRY(compute_force(h, h->w_s, h->w_gas, pn_at(h, first), h->w_g));
       for (int i = first; i < end; ++i) {
+        const bool out = plain || i == end - 1;
         const TapeSlot T = tape_slot(h, i - first, !plain && i != first);
+        const TapeSlot Tn = out ? TapeSlot{} : tape_slot(h, i + 1 - first, true);
         DH_TRY(forward_step(h, i, &h->w_gas, &h->w_gas2, h->w_s, h->w_p, h->w_g, &T,
-                            !plain && i != first, plain || i == end - 1));
+                            !plain && i != first, out, false, out ? nullptr : &Tn));
       }
     }
     for (int i = end - 1; i >= first; --i)
