@@ -117,6 +117,35 @@ def test_sweep_forms_match_oracle(dh, n, variant):
         assert abs(dnu.item() - gnu.item()) < 1e-2 * abs(gnu.item())
 
 
+@pytest.mark.parametrize("variant", [2, 4, 5])
+def test_x_adjoint_marching_forms_128(dh, variant):
+    """The marching x adjoint (on x <-> y transposed copies) at the benchmark's n = 128,
+    where its segments are fitted to whole waves: against the tile form and the oracle with
+    the bars of the forms test."""
+    n, axis = 128, 0
+    Ug, Uo = f32(gas(n, seed=77))
+    lam_g, lam_o = f32(synth.field(n, seed=78, shape=(5, n, n, n)))
+    nu = _nu(Uo)
+    gl, dnu = dh.sweep_adjoint(Ug, lam_g, axis, nu, variant=variant)
+    ref_form, dnu_ref = dh.sweep_adjoint(Ug, lam_g, axis, nu, variant=1)
+    X = Uo.clone().requires_grad_(True)
+    nut = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
+    out = (hydro.sweep(X, "x", nut, GAMMA) * lam_o).sum()
+    gx, gnu = torch.autograd.grad(out, (X, nut))
+    for k in range(5):
+        df = (gl[k] - ref_form[k]).double().cpu().flatten()
+        kf = torch.ones_like(df, dtype=torch.bool)
+        kf[torch.topk(df.abs(), max(1, df.numel() // 1000)).indices] = False
+        assert df[kf].norm().item() < 5e-6 * ref_form[k].double().norm().item(), (k, "forms differ")
+        d = (gl[k].double().cpu() - gx[k]).flatten()
+        keep = torch.ones_like(d, dtype=torch.bool)
+        keep[torch.topk(d.abs(), max(1, d.numel() // 1000)).indices] = False
+        assert d[keep].norm().item() < 1e-4 * gx[k].norm().item(), (k, "outside worst cells")
+        assert rel_l2(gl[k], gx[k]) < 1e-2
+    assert abs(dnu.item() - dnu_ref.item()) < 1e-2 * abs(dnu_ref.item())
+    assert abs(dnu.item() - gnu.item()) < 1e-2 * abs(gnu.item())
+
+
 @pytest.mark.parametrize("n", [8, 20, 48, 64])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_sweep_adjoint(dh, n, axis):
