@@ -134,10 +134,19 @@ __device__ __forceinline__ PIdx particle_index(int n) {
   r.b = blockIdx.y;
   r.p = (int)t;
   r.ok = t < nn * (unsigned)n;
-  r.qz = (int)(t / nn);
-  const unsigned rem = t - (unsigned)r.qz * nn;
-  r.qy = (int)(rem / (unsigned)n);
-  r.qx = (int)(rem - (unsigned)r.qy * (unsigned)n);
+  if ((n & (n - 1)) == 0) {
+    // n a power of two (the usual grid): shifts and masks instead of two divisions
+    const int lg = __ffs(n) - 1;
+    const unsigned m = (unsigned)n - 1u;
+    r.qx = (int)(t & m);
+    r.qy = (int)((t >> lg) & m);
+    r.qz = (int)(t >> (2 * lg));
+  } else {
+    r.qz = (int)(t / nn);
+    const unsigned rem = t - (unsigned)r.qz * nn;
+    r.qy = (int)(rem / (unsigned)n);
+    r.qx = (int)(rem - (unsigned)r.qy * (unsigned)n);
+  }
   return r;
 }
 
