@@ -203,6 +203,25 @@ __device__ __forceinline__ void split_flux_vjp(const float u[5], int f, float ga
   lu[0] += lrho;
 }
 
+// Gravity half kick of one gas cell (Sec. 2.2): m += rho g K, eps += K m.g + K^2 rho |g|^2 / 2,
+// g the three force components at offsets 0, N3, 2 N3 from g. Every product and sum is
+// rounded on its own (no FMA contraction), so that the kick kernel and the sweeps that kick
+// their cells as they load them give the same bits.
+__device__ __forceinline__ void gas_kick_cell(float u[5], const float* g, long long N3, float K) {
+  const float rho = u[0];
+  float mg = 0.0f, g2 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float gj = __ldg(g + j * N3);
+    const float mj = u[1 + j];
+    mg = __fadd_rn(mg, __fmul_rn(mj, gj));
+    g2 = __fadd_rn(g2, __fmul_rn(gj, gj));
+    u[1 + j] = __fadd_rn(mj, __fmul_rn(__fmul_rn(rho, gj), K));
+  }
+  const float de = __fadd_rn(__fmul_rn(K, mg), __fmul_rn(__fmul_rn(__fmul_rn(0.5f, K), K), __fmul_rn(rho, g2)));
+  u[4] = __fadd_rn(u[4], de);
+}
+
 // Gated harmonic-mean (van Leer) limiter 2 max(ab,0) / (a + b + copysign(eps, a+b)).
 __device__ __forceinline__ float vanleer(float a, float b, float eps) {
   const float ab = a * b;

@@ -106,7 +106,7 @@ __device__ __forceinline__ float2 face_flux2(const float2* R, const float2* L, i
 template <int AXIS>
 __global__ void __launch_bounds__(SweepCfg<AXIS>::NT, 2)
 sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
-                 float gam, float eps) {
+                 float gam, float eps, const float* __restrict__ kick_g, SArg kick_K) {
   pdl_enter();
   constexpr int S = SweepCfg<AXIS>::S, W = SweepCfg<AXIS>::W, NT = SweepCfg<AXIS>::NT;
   using G = TileGeom<AXIS, S, W, 3>;
@@ -125,7 +125,8 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
   const int s0 = blockIdx.x * S, w0 = blockIdx.y * W, t = blockIdx.z - b * n;
   uin += (size_t)b * 5 * N3;
   uout += (size_t)b * 5 * N3;
-  const float nu = nua.at(b);
+  if (kick_g) kick_g += (size_t)b * 3 * N3;
+  const float nu = nua.at(b), kK = kick_K.at(b);
   const float2 hnu = pk(0.5f * nu), mnu = pk(-nu);
 
   float ureg[CPT][5];
@@ -140,6 +141,7 @@ sweep_fwd_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n,
         const long long o = goff<AXIS>(sgl, wg, t, n);
 #pragma unroll
         for (int k = 0; k < 5; ++k) u[k] = __ldg(uin + k * N3 + o);
+        if (kick_g) gas_kick_cell(u, kick_g + o, N3, kK);  // the step's opening gas kick
       }
       float FR[5], FL[5];
       split_flux(u, F, gam, FR, FL);
@@ -347,7 +349,7 @@ __device__ __forceinline__ void split_flux2(const float2 u[5], int f, float gam,
 template <int AXIS, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int n, SArg nua,
-                    float gam, float eps, int L) {
+                    float gam, float eps, int L, const float* __restrict__ kick_g, SArg kick_K) {
   pdl_enter();
   constexpr int F = 1 + AXIS;
   const LineIdx li = line_index(n, 2);
@@ -357,7 +359,8 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
   const long long N3 = (long long)n * n * n;
   uin += (size_t)b * 5 * N3;
   uout += (size_t)b * 5 * N3;
-  const float nu = nua.at(b);
+  if (kick_g) kick_g += (size_t)b * 3 * N3;
+  const float nu = nua.at(b), kK = kick_K.at(b);
   const float2 hnu = pk(0.5f * nu), mnu = pk(-nu);
   float2 Ua[5], Ub[5], Uc[5];  // U_{j-3}, U_{j-2}, U_{j-1}
   float2 FRp[5], f1m[5];       // F^R_{j-1}, first-order face j-3/2
@@ -378,6 +381,19 @@ sweep_march2_kernel(const float* __restrict__ uin, float* __restrict__ uout, int
     const long long o = goff<AXIS>(j, w, t, n);
 #pragma unroll
     for (int k = 0; k < 5; ++k) u[k] = __ldg(reinterpret_cast<const float2*>(uin + k * N3 + o));
+    if (kick_g) {
+      // the step's opening gas kick of both columns, as the kick kernel does it
+      float a[5], c[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        a[k] = u[k].x;
+        c[k] = u[k].y;
+      }
+      gas_kick_cell(a, kick_g + o, N3, kK);
+      gas_kick_cell(c, kick_g + o + 1, N3, kK);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) u[k] = make_float2(a[k], c[k]);
+    }
     float2 FR[5], FL[5];
     split_flux2(u, F, gam, FR, FL);
     float2 f1[5], uh[5];
@@ -1049,10 +1065,11 @@ static sim_status launch_march_t(const float* uin, float* uout, int n, SArg nu, 
 
 template <int AXIS, int MINB>
 static sim_status launch_march2_mb(const float* uin, float* uout, int n, SArg nu, float gam,
-                                   float eps, int B, cudaStream_t st) {
+                                   float eps, int B, cudaStream_t st, const float* kick_g,
+                                   SArg kick_K) {
   const dim3 blk = line_block(n / 2, 128);
   const int L = fit_segment(sweep_march2_kernel<AXIS, MINB>, n, B, 6, n / 2, blk);
-  DH_CUDA_TRY((launch_pdl(sweep_march2_kernel<AXIS, MINB>, line_grid(n / 2, n, B, blk, cdiv(n, L)), blk, 0, st, uin, uout, n, nu, gam, eps, L)));
+  DH_CUDA_TRY((launch_pdl(sweep_march2_kernel<AXIS, MINB>, line_grid(n / 2, n, B, blk, cdiv(n, L)), blk, 0, st, uin, uout, n, nu, gam, eps, L, kick_g, kick_K)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1062,24 +1079,36 @@ static sim_status launch_march2_mb(const float* uin, float* uout, int n, SArg nu
 // blocks (206 registers) and 66 / 347 us at four (128 registers, spilling).
 template <int AXIS>
 static sim_status launch_march2_t(const float* uin, float* uout, int n, SArg nu, float gam,
-                                  float eps, int B, cudaStream_t st) {
-  return launch_march2_mb<AXIS, 3>(uin, uout, n, nu, gam, eps, B, st);
+                                  float eps, int B, cudaStream_t st, const float* kick_g,
+                                  SArg kick_K) {
+  return launch_march2_mb<AXIS, 3>(uin, uout, n, nu, gam, eps, B, st, kick_g, kick_K);
+}
+
+// the paired form needs two adjacent x columns per thread: y / z sweeps, n even
+static bool takes_pair(int axis, int n, int variant, const void* uin, const void* uout) {
+  return axis != 0 && variant == SIM_SWEEP_PAIR && n % 2 == 0 &&
+         ((reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(uout)) % 8) == 0;
 }
 
 template <int AXIS>
 static sim_status launch_sweep_t(const float* uin, float* uout, int n, SArg nu, float gam,
-                                 float eps, int B, int variant, cudaStream_t st) {
+                                 float eps, int B, int variant, cudaStream_t st,
+                                 const float* kick_g, SArg kick_K) {
   using C = SweepCfg<AXIS>;
-  // the paired form needs two adjacent x columns per thread: y / z sweeps, n even
-  if (AXIS != 0 && variant == SIM_SWEEP_PAIR && n % 2 == 0 &&
-      ((reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(uout)) % 8) == 0)
-    return launch_march2_t<AXIS>(uin, uout, n, nu, gam, eps, B, st);
-  if (AXIS != 0 && variant != SIM_SWEEP_TILE && variant != SIM_SWEEP_PAIR)
+  if (takes_pair(AXIS, n, variant, uin, uout))
+    return launch_march2_t<AXIS>(uin, uout, n, nu, gam, eps, B, st, kick_g, kick_K);
+  if (AXIS != 0 && variant != SIM_SWEEP_TILE && variant != SIM_SWEEP_PAIR) {
+    if (kick_g) {
+      set_error("internal: the marching forward sweep takes no opening kick");
+      return SIM_EINVAL;
+    }
     return launch_march_t<AXIS>(uin, uout, n, nu, gam, eps, B, variant, st);
+  }
   constexpr int NC = (C::S + 6) * C::W;
   const size_t smem = 15 * NC * sizeof(float);
   dim3 grid(cdiv(n, C::S), cdiv(n, C::W), n * B);
-  DH_CUDA_TRY((launch_pdl(sweep_fwd_kernel<AXIS>, grid, C::NT, smem, st, uin, uout, n, nu, gam, eps)));
+  DH_CUDA_TRY((launch_pdl(sweep_fwd_kernel<AXIS>, grid, C::NT, smem, st, uin, uout, n, nu, gam,
+                          eps, kick_g, kick_K)));
   DH_LAUNCH_CHECK();
   return SIM_OK;
 }
@@ -1260,7 +1289,8 @@ sim_status prepare_sweep_kernels() {
 }
 
 sim_status launch_sweep(int axis, const float* uin, float* uout, int n, SArg nu, double gam,
-                        double eps, int B, int variant, cudaStream_t st) {
+                        double eps, int B, int variant, cudaStream_t st, const float* kick_g,
+                        SArg kick_K) {
   DH_TRY(prepare_sweep_kernels());
   if (axis < 0 || axis > 2) {
     set_error("sweep axis must be 0, 1 or 2 (got %d)", axis);
@@ -1269,10 +1299,16 @@ sim_status launch_sweep(int axis, const float* uin, float* uout, int n, SArg nu,
   const int v = pick_fwd(axis, n, variant);
   const float fg = (float)gam, fe = (float)eps;
   switch (axis) {
-    case 0: return launch_sweep_t<0>(uin, uout, n, nu, fg, fe, B, v, st);
-    case 1: return launch_sweep_t<1>(uin, uout, n, nu, fg, fe, B, v, st);
-    default: return launch_sweep_t<2>(uin, uout, n, nu, fg, fe, B, v, st);
+    case 0: return launch_sweep_t<0>(uin, uout, n, nu, fg, fe, B, v, st, kick_g, kick_K);
+    case 1: return launch_sweep_t<1>(uin, uout, n, nu, fg, fe, B, v, st, kick_g, kick_K);
+    default: return launch_sweep_t<2>(uin, uout, n, nu, fg, fe, B, v, st, kick_g, kick_K);
   }
+}
+
+bool sweep_takes_kick(int axis, int n, int variant, const float* uin, const float* uout) {
+  const int v = pick_fwd(axis, n, variant);
+  return v == SIM_SWEEP_TILE || (axis == 0 && v == SIM_SWEEP_PAIR) ||
+         takes_pair(axis, n, v, uin, uout);
 }
 
 sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
@@ -1303,7 +1339,7 @@ extern "C" sim_status sim_sweep(const float* u_in, float* u_out, int32_t n, int3
     return SIM_EINVAL;
   }
   return dh::launch_sweep(axis, u_in, u_out, n, dh::sarg((float)nu), gamma, limiter_eps, 1,
-                          variant, (cudaStream_t)stream);
+                          variant, (cudaStream_t)stream, nullptr, dh::sarg(0.0f));
 }
 
 extern "C" sim_status sim_sweep_adjoint(const float* u_in, const float* lam_out, float* lam_in,

@@ -520,18 +520,13 @@ __global__ void gas_kick_kernel(const float* in, float* out, const float* __rest
   out += (size_t)b * 5 * N3;
   g += (size_t)b * 3 * N3;
   const float K = Ka.at(b);
-  const float rho = in[i];
-  if (out != in) out[i] = rho;
-  float mg = 0.0f, g2 = 0.0f;
+  float u[5];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const float gj = g[j * N3 + i];
-    const float mj = in[(1 + j) * N3 + i];
-    mg += mj * gj;
-    g2 += gj * gj;
-    out[(1 + j) * N3 + i] = mj + rho * gj * K;
-  }
-  out[4 * N3 + i] = in[4 * N3 + i] + (K * mg + 0.5f * K * K * rho * g2);
+  for (int k = 0; k < 5; ++k) u[k] = in[k * N3 + i];
+  gas_kick_cell(u, g + i, N3, K);
+  if (out != in) out[i] = u[0];
+#pragma unroll
+  for (int k = 1; k < 5; ++k) out[k * N3 + i] = u[k];
 }
 
 sim_status launch_gas_kick(const float* in, float* out, const float* g, SArg K, int n, int B,

@@ -51,8 +51,12 @@ const char* get_error() { return g_err; }
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// kick_g (may be NULL): the sweep first applies the gravity half kick K of force kick_g to
+// every cell it loads (only where sweep_takes_kick says the form can)
 sim_status launch_sweep(int axis, const float* uin, float* uout, int n, SArg nu, double gam,
-                        double eps, int B, int variant, cudaStream_t st);
+                        double eps, int B, int variant, cudaStream_t st,
+                        const float* kick_g = nullptr, SArg kick_K = SArg{0.0f, nullptr});
+bool sweep_takes_kick(int axis, int n, int variant, const float* uin, const float* uout);
 sim_status launch_sweep_adjoint(int axis, const float* uin, const float* lout, float* lin,
                                 int n, SArg nu, double gam, double eps, DPart dnu,
                                 float* scratch, int B, int variant, cudaStream_t st);
@@ -518,9 +522,15 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     else
       DH_TRY(dcopy(T->Uk1, T->U0, gb, st));
     cur = T->Uk1;
-  } else if (P.gravity_on) {
-    DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(cur, cur, g, K1, h->n, B, st); }));
   }
+  // without a tape the gas kick rides in the first sweep, which kicks every cell it loads
+  // (the kicked state is never stored), where that sweep's form can
+  const int first_axis = kOrders[i % 6][0] - 'x';
+  const bool kick_in_sweep = !T && P.gravity_on && P.hydro_on &&
+                             sweep_takes_kick(first_axis, h->n, h->fwd_var[first_axis], cur,
+                                              cur == *gas ? *gas_tmp : *gas);
+  if (!T && P.gravity_on && !kick_in_sweep)
+    DH_TRY(timed(h, SIM_KT_KICK, [&] { return launch_gas_kick(cur, cur, g, K1, h->n, B, st); }));
   // 2. sweeps
   if (P.hydro_on) {
     const char* order = kOrders[i % 6];
@@ -529,9 +539,10 @@ static sim_status forward_step(sim_t* h, int i, float** gas, float** gas_tmp, fl
     for (int k = 0; k < 3; ++k) {
       float* out = T ? outs_tape[k] : (cur == *gas ? *gas_tmp : *gas);
       const int axis = order[k] - 'x';
+      const bool kick = k == 0 && kick_in_sweep;
       DH_TRY(timed(h, SIM_KT_SWEEP, [&] {
         return launch_sweep(axis, cur, out, h->n, nu, P.gamma, P.limiter_eps, B,
-                            h->fwd_var[axis], st);
+                            h->fwd_var[axis], st, kick ? g : nullptr, K1);
       }));
       cur = out;
     }
