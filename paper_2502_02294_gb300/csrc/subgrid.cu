@@ -21,6 +21,7 @@ SubgridConst make_subgrid_const(const sim_params& p, double a, int step) {
   const double fb = p.omega_b / p.omega_m;
   const double tpe = temperature_per_energy(p.gamma, p.mu);
   c.a2 = (float)(a * a);
+  c.inv_a2 = (float)(1.0 / (a * a));
   c.fb = (float)fb;
   c.inv_fb = (float)(1.0 / fb);
   c.tpe = (float)tpe;
@@ -35,6 +36,9 @@ SubgridConst make_subgrid_const(const sim_params& p, double a, int step) {
   c.T0 = (float)p.T0_uv;
   c.ef0 = (float)(p.T0_uv > 0 ? p.T0_uv / tpe : 0.0);
   c.gexp = (float)(p.gamma_uv - 1.0);
+  c.inv_T0 = (float)(p.T0_uv > 0 ? 1.0 / p.T0_uv : 0.0);
+  c.inv_Pi0 = (float)(1.0 / p.Pi0);
+  c.mgexp_fb = (float)(-(p.gamma_uv - 1.0) / fb);
   c.k0 = (uint32_t)(p.seed & 0xffffffffull);
   c.k1 = (uint32_t)(p.seed >> 32);
   c.step = (uint32_t)step;
@@ -47,10 +51,11 @@ __device__ __forceinline__ float log_sigmoid(float x) {
   return -(fmaxf(-x, 0.0f) + log1pf(__expf(-fabsf(x))));
 }
 
-__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
+__device__ __forceinline__ float sigmoidf_(float x) { return __frcp_rn(1.0f + __expf(-x)); }
 
+// One reciprocal of rho serves every division by it (the forward's and the adjoint's).
 struct SgFwd {
-  float ke, e, T, delta, x1, x2, lnpi, pi, logit, zhat, e1, ef, e2;
+  float inv_rho, ke, e, T, delta, x1, x2, lnpi, pi, logit, zhat, e1, lnr, ef, e2;
   bool floor_on, use_floor;
 };
 
@@ -59,8 +64,9 @@ struct SgFwd {
 __device__ __forceinline__ void subgrid_cell(const float u[5], const SubgridConst& c, float gd,
                                              SgFwd& r) {
   const float rho = u[0];
-  r.ke = 0.5f * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / rho;
-  r.e = (u[4] - r.ke) / (c.a2 * rho);
+  r.inv_rho = __frcp_rn(rho);
+  r.ke = 0.5f * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * r.inv_rho;
+  r.e = (u[4] - r.ke) * r.inv_rho * c.inv_a2;
   r.T = c.tpe * r.e;
   r.delta = rho * c.inv_fb - 1.0f;
   r.x1 = (r.delta - c.delta_c) * c.inv_wd;
@@ -71,7 +77,9 @@ __device__ __forceinline__ void subgrid_cell(const float u[5], const SubgridCons
   r.zhat = sigmoidf_(r.logit * c.inv_tau);
   r.e1 = r.e + c.E0 * r.zhat;
   r.floor_on = c.ef0 > 0.0f;
-  r.ef = r.floor_on ? c.ef0 * powf(rho * c.inv_fb, c.gexp) : 0.0f;
+  // (rho / f_b)^(gamma_uv - 1) through its logarithm, which the adjoint reuses
+  r.lnr = r.floor_on ? logf(rho * c.inv_fb) : 0.0f;
+  r.ef = r.floor_on ? c.ef0 * expf(c.gexp * r.lnr) : 0.0f;
   r.use_floor = r.floor_on && !(r.e1 >= r.ef);
   r.e2 = r.use_floor ? r.ef : r.e1;
 }
@@ -155,12 +163,13 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
     float lrho = l[0] + leps * c.a2 * r.e2;
     const float le2 = leps * c.a2 * rho;
     float le1 = 0.0f;
+    const float irho = r.inv_rho;
     if (r.use_floor) {
       const float lef = le2;
-      lrho += lef * r.ef * c.gexp / rho;
-      a_t0 = lef * r.ef / c.T0;
-      a_g = lef * r.ef * logf(rho * c.inv_fb);
-      a_fb += lef * r.ef * (-c.gexp / c.fb);
+      lrho += lef * r.ef * c.gexp * irho;
+      a_t0 = lef * r.ef * c.inv_T0;
+      a_g = lef * r.ef * r.lnr;
+      a_fb += lef * r.ef * c.mgexp_fb;
     } else {
       le1 = le2;
     }
@@ -168,8 +177,8 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
     a_e0 = le1 * r.zhat;
     const float lz = le1 * c.E0;
     const float ll = lz * r.zhat * (1.0f - r.zhat) * c.inv_tau;
-    const float llnpi = ll / (1.0f - r.pi);
-    a_pi = llnpi / c.Pi0;
+    const float llnpi = __fdividef(ll, 1.0f - r.pi);
+    a_pi = llnpi * c.inv_Pi0;
     const float lx1 = llnpi * sigmoidf_(-r.x1);
     const float lx2 = llnpi * sigmoidf_(-r.x2);
     const float ldelta = lx1 * c.inv_wd;
@@ -179,14 +188,14 @@ __global__ void subgrid_adj_kernel(const float* __restrict__ in, float* __restri
     lrho += ldelta * c.inv_fb;
     a_fb += -(ldelta * rho * c.inv_fb * c.inv_fb);
     // e = (eps - ke) / (a^2 rho)
-    const float inv_a2r = 1.0f / (c.a2 * rho);
+    const float inv_a2r = irho * c.inv_a2;
     const float leps_in = le * inv_a2r;
     lke -= le * inv_a2r;
-    lrho -= le * r.e / rho;
+    lrho -= le * r.e * irho;
     // ke = |m|^2 / (2 rho)
 #pragma unroll
-    for (int k = 1; k <= 3; ++k) lam[k * N3 + i] = l[k] + lke * u[k] / rho;
-    lrho -= lke * r.ke / rho;
+    for (int k = 1; k <= 3; ++k) lam[k * N3 + i] = l[k] + lke * u[k] * irho;
+    lrho -= lke * r.ke * irho;
     lam[i] = lrho;
     lam[4 * N3 + i] = leps_in;
   }

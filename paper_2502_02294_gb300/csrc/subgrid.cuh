@@ -8,6 +8,7 @@ namespace dh {
 // Per-run constants of the subgrid step, in float for the kernels.
 struct SubgridConst {
   float a2;        // a^2 at the update
+  float inv_a2;    // 1 / a^2
   float inv_fb;    // 1 / f_b
   float fb;
   float tpe;       // temperature per unit specific energy
@@ -15,6 +16,7 @@ struct SubgridConst {
   float ef0;       // T0_uv / tpe (0: floor off)
   float gexp;      // gamma_uv - 1
   float T0;
+  float inv_T0, inv_Pi0, mgexp_fb;  // 1 / T0_uv (0 when off), 1 / Pi0, -(gamma_uv - 1) / f_b
   uint32_t k0, k1, step, instance;
 };
 
