@@ -452,11 +452,12 @@ __device__ __forceinline__ void interp3(const float* __restrict__ g, const Cic& 
       }
 }
 
-// 40 registers (12 resident blocks per SM instead of 9 at 56): more warps in flight for the
-// CIC gathers (kick class 44.7 -> 43.2 us per launch at 128^3)
+// 32 registers (16 resident blocks per SM instead of 9 at 56, a few words spilled): more
+// warps in flight for the CIC gathers (kick class 44.7 -> 43.2 us per launch at 128^3 with
+// 40 registers, 44.3 -> 43.5 us with 32).
 // s_out / p_out may be s / p (in place); out of place the positions are written even when
 // dtau = 0
-__global__ void __launch_bounds__(128, 12) kick_drift_kernel(const float* s, float* s_out,
+__global__ void __launch_bounds__(128, 16) kick_drift_kernel(const float* s, float* s_out,
                                   const float* p, float* p_out,
                                   const float* __restrict__ g, SArg Ka, SArg dtaua,
                                   const float* __restrict__ zhat, float* __restrict__ aux,
