@@ -54,21 +54,21 @@ constexpr int PACK = 27 * 512 / 2;              // bf16 elements of one packed l
 // contributes to output planes p - 1, p, p + 1 through the taps dz = +1, 0, -1; for one
 // in-plane shift (dy, dx) those three weight blocks sit side by side in one B operand
 // (N = 48), so one MMA adds the shifted input to three output-plane accumulators at once:
-// 9 MMAs per input plane and tile. Inputs are taken in groups of G; the accumulators a
-// group writes (the outputs of its G inputs' planes minus one, i.e. G + 2 planes) occupy
-// G + 2 consecutive plane slots of one of two TMEM buffers ([buffer][tile][slot][16
-// columns]), groups alternating between the buffers. An output plane whose three inputs
-// straddle two groups is the sum of its slots in both buffers. The epilogue drains each
-// output plane once its last input's MMAs are done and, after the last plane that touches
-// a buffer, zeroes that buffer for the group after next. One CTA per SM (all 512 TMEM
-// columns when T = 4); weights, barriers and TMEM are set up once per column of planes.
+// 9 MMAs per input plane and tile. The accumulators form a ring of R = 32 / T plane slots
+// per tile ([tile][slot][16 columns], output plane o in slot o mod R); an input whose
+// output planes wrap around the end of the ring, or lie partly outside the CTA's planes,
+// is issued as runs of N = 16 or 32 on the matching rows of the B operand. The epilogue
+// drains each output plane once its last input's MMAs are done, zeroes its slot and
+// releases it; the MMAs of input i wait for the release of output plane i - R, so they
+// may run up to R - 2 input planes ahead of the epilogue. One CTA per SM (all 512 TMEM
+// columns); weights, barriers and TMEM are set up once per column of planes.
 constexpr int EPI_SETS = 4;                         // epilogue warps per TMEM lane quarter
 constexpr int CONV_THREADS = 128 + 128 * EPI_SETS;  // loaders, MMA issuer, epilogue
 constexpr int ZC_MAX = 128;           // output planes per CTA
 constexpr int NB_MAX = ZC_MAX + 2;    // input planes (and barriers of each kind) per CTA
 
 struct ConvGeom {
-  int n, P, L, T, tpl, contig, Zc, G, ring, slot_pos, ncols;
+  int n, P, L, T, tpl, contig, Zc, R, ring, slot_pos, ncols;
   size_t smem;
 };
 
@@ -106,9 +106,8 @@ static ConvGeom conv_geom(int n, int B) {
     g.L = bestL;
     g.T = cdiv((long long)bestL * g.P, 128);
   }
-  // two buffers of T x (G + 2) accumulator planes in 512 columns
-  g.G = 16 / g.T - 2;
-  if (g.G < 2) g.G = 2;
+  // a ring of R accumulator planes of 16 columns per tile in 512 columns
+  g.R = 32 / g.T;
   g.ncols = 512;
   g.ring = conv_smem(4, g.L, g.P) <= limit ? 4 : 3;
   // output planes per CTA: the split of the planes into chunks that keeps the SMs busiest
@@ -216,7 +215,7 @@ struct ConvArgs {
   const bf16* in;      // activations [B][n][n][2][n][8]
   const bf16* w;       // packed [27][2][16 rows][8]: row = output channel, K = input channel
   const float* bias;   // [16] (forward) or NULL
-  int n, P, L, T, tpl, contig, Zc, G, ring, slot_pos, ncols;
+  int n, P, L, T, tpl, contig, Zc, R, ring, slot_pos, ncols;
   bf16* out;           // HIDDEN / BWD: activations, as in
   float* zout;         // HIDDEN: pre-activation [B][n^3][16] or NULL
   const float* zprev;  // BWD: pre-activation whose GELU' multiplies the result
@@ -281,19 +280,55 @@ __device__ __forceinline__ void tmem_zero(uint32_t tmem, int c0, int c1, int w, 
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// TMEM column of accumulator plane slot s of tile t in buffer beta
-__device__ __forceinline__ uint32_t acc_col(const ConvArgs& a, int beta, int t, int s) {
-  return 16u * (uint32_t)((beta * a.T + t) * (a.G + 2) + s);
+// 16 zero columns at taddr in this warp's 32 lanes (no wait: tcgen05.wait::st follows)
+__device__ __forceinline__ void tmem_zero16_nowait(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
 }
 
-// The 9 x T MMAs of input plane i (ring slot i mod ring): block (dy, dx) of the weights
-// against the input shifted by (dy, dx), into plane slots s, s + 1, s + 2 of buffer beta
-// (output planes i - 2, i - 1, i relative to z0) of every tile.
-__device__ __forceinline__ void conv_issue_input(const ConvArgs& a, int i, int beta, int s,
-                                                 uint32_t tmem, uint64_t a_base, uint64_t b_base,
-                                                 uint32_t slot_units, uint32_t idesc) {
+// 16 columns at t0 and 16 at t1 of this thread's TMEM lane, one wait for both loads (one
+// asm statement, so no use of the outputs can be placed before the wait)
+__device__ __forceinline__ void tmem_ld16x2(uint32_t t0, uint32_t t1, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
+      "%28,%29,%30,%31}, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(t0), "r"(t1)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// TMEM column of accumulator slot s of tile t
+__device__ __forceinline__ uint32_t acc_col(const ConvArgs& a, int t, int s) {
+  return 16u * (uint32_t)(t * a.R + s);
+}
+
+// One run of input plane i (ring slot i mod ring) for every tile: block (dy, dx) of the
+// weights against the input shifted by (dy, dx), into the len consecutive accumulator slots
+// s .. s + len - 1, which hold output planes lo .. lo + len - 1 (relative to z0); output
+// plane i - 2 + k takes rows 16 k .. 16 k + 15 of the B operand (dz = 1 - k).
+__device__ __forceinline__ void conv_issue_run(const ConvArgs& a, int i, int lo, int len, int s,
+                                               uint32_t tmem, uint64_t a_base, uint64_t b_base,
+                                               uint32_t slot_units) {
   const int P = a.P, T = a.T;
   const uint64_t a_slot = a_base + (uint64_t)((i % a.ring) * slot_units);
+  const uint32_t idesc = len == 3 ? umma_idesc_bf16(128, 48)
+                                  : (len == 2 ? umma_idesc_bf16(128, 32) : umma_idesc_bf16(128, 16));
+  // rows 16 k0 .. of each 1536-byte block: 8-row groups 128 bytes apart (16-byte units)
+  const uint64_t b_run = b_base + (uint64_t)(16 * (lo - (i - 2)));
   // tile-major: the 9 MMAs of one tile chain into the same accumulator (switching the
   // accumulator between consecutive MMAs costs several times a chained MMA)
   for (int t = 0; t < T; ++t) {
@@ -304,18 +339,34 @@ __device__ __forceinline__ void conv_issue_input(const ConvArgs& a, int i, int b
       const int ly = t / a.tpl;
       vb = ly * P + 1 + 128 * (t - ly * a.tpl);
     }
-    const uint32_t d = tmem + acc_col(a, beta, t, s);
+    const uint32_t d = tmem + acc_col(a, t, s);
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         const int j = (dy + 1) * 3 + (dx + 1);
-        const uint64_t db = b_base + (uint64_t)(j * 96);  // 1536-byte blocks
+        const uint64_t db = b_run + (uint64_t)(j * 96);  // 1536-byte blocks
         // descriptors are linear in the start address (16-byte units, low 14 bits)
         const uint64_t da = a_slot + (uint64_t)(SLK_BEFORE + (1 + dy) * P + dx + vb);
         umma_bf16(d, da, db, idesc, 1u);
       }
     }
+  }
+}
+
+// The MMAs of input plane i: output planes max(0, i - 2) .. min(i, nz - 1), in one run, or
+// two where their slots wrap around the end of the ring.
+__device__ __forceinline__ void conv_issue_input(const ConvArgs& a, int i, int nz, uint32_t tmem,
+                                                 uint64_t a_base, uint64_t b_base,
+                                                 uint32_t slot_units) {
+  const int lo = max(0, i - 2), hi = min(i, nz - 1);
+  const int len = hi - lo + 1, s0 = lo % a.R;
+  if (s0 + len <= a.R) {
+    conv_issue_run(a, i, lo, len, s0, tmem, a_base, b_base, slot_units);
+  } else {
+    const int first = a.R - s0;
+    conv_issue_run(a, i, lo, first, s0, tmem, a_base, b_base, slot_units);
+    conv_issue_run(a, i, lo + first, len - first, 0, tmem, a_base, b_base, slot_units);
   }
 }
 
@@ -387,11 +438,11 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, const float acc
 
 // Warp roles: warp 0 fetches input planes (bulk copies completing on the plane's mbarrier),
 // warp 2 lane 0 issues the MMAs of each
-// plane once it has landed (and, at the start of a group, once the buffer is free) and
+// plane once it has landed (and once the slot of its newest output plane is released) and
 // commits them to that plane's barrier, warps 4 .. 4 + 4 EPI_SETS - 1 run the epilogue of
 // every output plane once its last input's MMAs are done (warp w reads TMEM lanes
-// 32 (w % 4) .. + 31 of the tiles t = (w - 4) / 4 mod EPI_SETS) and free each buffer
-// after its last plane. Every
+// 32 (w % 4) .. + 31 of the tiles t = (w - 4) / 4 mod EPI_SETS), zero its slot and
+// release it. Every
 // barrier is used once (one per input plane or group), every wait is bounded by a.wait_ns;
 // a wait that gives up sets an error flag and its role stops. Before the CTA frees its TMEM
 // and exits, the loader waits for every bulk copy it issued and the MMA thread for the
@@ -407,8 +458,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
   const int b = blockIdx.z, y0 = blockIdx.x * a.L, z0 = blockIdx.y * a.Zc;
   const int nz = min(a.Zc, n - z0);  // output planes of this CTA
   const int nin = nz + 2;            // input planes z0 - 1 .. z0 + nz
-  const int G = a.G, ring = a.ring;
-  const int ngroups = (nin + G - 1) / G;
+  const int R = a.R, ring = a.ring;
   const int tid = threadIdx.x;
   const int w = tid >> 5, lane = tid & 31;
   const uint32_t slot_bytes = 2u * (uint32_t)a.slot_pos * 16u;
@@ -416,8 +466,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
   uint8_t* sw = smem + ring * slot_bytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(sw + 9 * 1536);  // [NB_MAX]: input landed
   uint64_t* done = full + NB_MAX;                                // [NB_MAX]: its MMAs done
-  uint64_t* freeb = done + NB_MAX;                               // [NB_MAX]: group drained
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(freeb + NB_MAX);
+  uint64_t* drained = done + NB_MAX;                             // [NB_MAX]: output released
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drained + NB_MAX);
   int* sflag = reinterpret_cast<int*>(tslot + 1);
   const bf16* in = a.in + (size_t)b * N3 * CH;
   const uint32_t sa0 = smem_u32(sa);
@@ -438,7 +488,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
       mbar_init(full + i, 1);
       mbar_init(done + i, 1);
     }
-    for (int g = 0; g < ngroups; ++g) mbar_init(freeb + g, 4 * EPI_SETS);
+    for (int o = 0; o < nz; ++o) mbar_init(drained + o, 4 * EPI_SETS);
     *sflag = 0;
   }
   if (w == 0) tmem_alloc_warp(tslot, (uint32_t)a.ncols);
@@ -487,14 +537,13 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
   } else if (w == 2) {
     // ---- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = umma_idesc_bf16(128, 48);
       const uint64_t a_base = umma_desc(sa0, (uint32_t)a.slot_pos * 16u, 128u);
       const uint64_t b_base = umma_desc(smem_u32(sw), 768u, 128u);
       const uint32_t slot_units = slot_bytes >> 4;
       int committed = 0;
       for (int i = 0; i < nin; ++i) {
-        const int g = i / G, s = i - g * G;
-        if (s == 0 && g >= 2 && !mbar_wait_ns(freeb + (g - 2), 0, limit)) {
+        // the slot of output plane i last held output plane i - R
+        if (i < nz && i >= R && !mbar_wait_ns(drained + (i - R), 0, limit)) {
           *sflag = 1;
           break;
         }
@@ -503,7 +552,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
           break;
         }
         tc_fence_after();
-        conv_issue_input(a, i, g & 1, s, tmem, a_base, b_base, slot_units, idesc);
+        conv_issue_input(a, i, nz, tmem, a_base, b_base, slot_units);
         umma_commit(done + i);
         committed = i + 1;
       }
@@ -513,51 +562,62 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv3_kernel(ConvArgs a) {
     __syncwarp();
   } else if (w >= 4) {
     // ---- epilogue: output plane z0 + o is final once input o + 2 is in; its accumulator
-    //      is slot o - ga G + 2 of group ga = o / G, plus slot o - gb G + 2 of group
-    //      gb = (o + 2) / G when its inputs straddle two groups
+    //      is slot o mod R. In columns of 12 planes or more, planes are drained two at a
+    //      time (one wait for their MMAs, one for both TMEM loads, one for the zeroing of
+    //      both slots); short columns take them one by one, so the first starts earlier.
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 of the tiles t = (w - 4) / 4 mod EPI_SETS
     const uint32_t lane_base = (uint32_t)(32 * (w & 3)) << 16;
     const int es = (w - 4) >> 2;
     float bias[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) bias[c] = a.bias ? __ldg(a.bias + c) : 0.0f;
-    for (int o = 0; o < nz; ++o) {
+    const int pstep = nz >= 12 ? 2 : 1;
+    for (int o = 0; o < nz; o += pstep) {
+      const int np = min(pstep, nz - o);  // output planes o .. o + np - 1
       uint32_t ok = 0;
-      if (lane == 0) ok = mbar_wait_ns(done + o + 2, 0, limit);
+      if (lane == 0) ok = mbar_wait_ns(done + o + np + 1, 0, limit);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) {
         if (lane == 0) *sflag = 1;
         break;
       }
       tc_fence_after();
-      const int ga = o / G, gb = (o + 2) / G;
+      const int s0 = o % R, s1 = (o + 1) % R;
       for (int t = es; t < a.T; t += EPI_SETS) {
-        float acc[16];
-        tmem_ld16(tmem + lane_base + acc_col(a, ga & 1, t, o - ga * G + 2), acc);
-        if (gb != ga) {
-          float acc2[16];
-          tmem_ld16(tmem + lane_base + acc_col(a, gb & 1, t, o - gb * G + 2), acc2);
-#pragma unroll
-          for (int c = 0; c < 16; ++c) acc[c] += acc2[c];
+        if (np == 2) {
+          float acc[32];
+          tmem_ld16x2(tmem + lane_base + acc_col(a, t, s0), tmem + lane_base + acc_col(a, t, s1), acc);
+          conv_epilogue<MODE>(a, acc, bias, b, z0 + o, y0, t, 32 * (w & 3) + lane);
+          conv_epilogue<MODE>(a, acc + 16, bias, b, z0 + o + 1, y0, t, 32 * (w & 3) + lane);
+        } else {
+          float acc[16];
+          tmem_ld16(tmem + lane_base + acc_col(a, t, s0), acc);
+          conv_epilogue<MODE>(a, acc, bias, b, z0 + o, y0, t, 32 * (w & 3) + lane);
         }
-        conv_epilogue<MODE>(a, acc, bias, b, z0 + o, y0, t, 32 * (w & 3) + lane);
       }
-      if ((o + 1) % G == 0) {
-        // the last output touching group g = (o + 1) / G - 1: clear its buffer for group g + 2
-        const int g = (o + 1) / G - 1;
-        if (g + 2 < ngroups) {
-          for (int t = es; t < a.T; t += EPI_SETS)
-            tmem_zero(tmem, (int)acc_col(a, g & 1, t, 0), (int)acc_col(a, g & 1, t + 1, 0), w & 3, 1);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            uint64_t state;
+      // clear the slots of planes q + R < nz (reused by output plane q + R) and release them
+      // to the MMA thread
+      const bool rel0 = o + R < nz, rel1 = np == 2 && o + 1 + R < nz;
+      if (rel0) {
+        for (int t = es; t < a.T; t += EPI_SETS) {
+          tmem_zero16_nowait(tmem + lane_base + acc_col(a, t, s0));
+          if (rel1) tmem_zero16_nowait(tmem + lane_base + acc_col(a, t, s1));
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          uint64_t state;
+          asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+                       : "=l"(state)
+                       : "r"(smem_u32(drained + o))
+                       : "memory");
+          if (rel1)
             asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
                          : "=l"(state)
-                         : "r"(smem_u32(freeb + g))
+                         : "r"(smem_u32(drained + o + 1))
                          : "memory");
-            (void)state;
-          }
+          (void)state;
         }
       }
     }
@@ -589,13 +649,19 @@ static sim_status launch_conv(int mode, ConvArgs a, int B, cudaStream_t st) {
     set_error("closure: grid n = %d needs %zu bytes of shared memory per CTA", a.n, g.smem);
     return SIM_EINVAL;
   }
+  // the epilogue drains planes in pairs, waiting for input o + 3 before it releases plane
+  // o, and the MMAs of input i wait for the release of plane i - R: R >= 4 keeps that acyclic
+  if (g.R < 4 || 16 * g.T * g.R > g.ncols) {
+    set_error("closure: grid n = %d needs %d tiles per plane (at most 8)", a.n, g.T);
+    return SIM_EINVAL;
+  }
   a.P = g.P;
   a.L = g.L;
   a.T = g.T;
   a.tpl = g.tpl;
   a.contig = g.contig;
   a.Zc = g.Zc;
-  a.G = g.G;
+  a.R = g.R;
   a.ring = g.ring;
   a.slot_pos = g.slot_pos;
   a.ncols = g.ncols;

@@ -71,7 +71,10 @@ __device__ __forceinline__ uint32_t mbar_test(uint64_t* mbar, uint32_t parity) {
 
 // Wait for phase `parity` of the mbarrier for at most limit_ns nanoseconds of the global
 // timer (and at most 2^26 polls); returns 1 when the phase completed, 0 when the wait gave
-// up. limit_ns = 0: one non-blocking check only.
+// up. limit_ns = 0: one non-blocking check only. Each poll may suspend the thread for up to
+// kSuspendNs until the phase completes, so a waiting warp does not spin on the issue slots
+// the working warps of its scheduler need.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ uint32_t mbar_wait_ns(uint64_t* mbar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_test(mbar, parity)) return 1;
   if (limit_ns == 0) return 0;
@@ -79,10 +82,10 @@ __device__ __forceinline__ uint32_t mbar_wait_ns(uint64_t* mbar, uint32_t parity
   for (int it = 0; it < (1 << 26); ++it) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(parity)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (done) return 1;
     if (global_ns() - t0 >= limit_ns) return 0;
