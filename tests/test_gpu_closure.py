@@ -95,6 +95,34 @@ def test_forward_sampled_voxels_large_grids(dh, n):
     c.close()
 
 
+def test_forward_five_tiles_per_line(dh):
+    """n = 513: five 128-position tiles per line (one line per CTA), the most tiles per plane
+    the grid sizes accepted by the host produce; the accumulator ring then holds six plane
+    slots per tile in 480 of the 512 TMEM columns. The input repeats a 57^3 field nine
+    times per axis, so each sampled voxel's 9^3 window comes from the small field."""
+    n, m = 513, 57
+    w = _weights(12)
+    c = _closure(dh, w)
+    base, base_o = _gas(m, 13)
+    gas = base.repeat(1, n // m, n // m, n // m).contiguous()
+    y = c.forward(gas)
+    c.status()
+    x = _x(base_o)
+    rng = np.random.default_rng(14)
+    # every tile of a line (x = 0, 128, ..., 512), both sides of the CTAs' plane columns
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (102, 5, 127), (103, 6, 128), (205, 500, 255),
+           (206, 1, 256), (308, 2, 383), (309, 3, 384), (411, 4, 511), (412, 7, 512)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(20)]
+    got, want = [], []
+    for z0, y0, x0 in pts:
+        idx = [torch.arange(q - 4, q + 5) % m for q in (z0 % m, y0 % m, x0 % m)]
+        win = x[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+        want.append(oc.network_window(win, w))
+        got.append(y[:, z0, y0, x0].double().cpu())
+    assert rel_l2(torch.stack(got), torch.stack(want)) < 2e-3
+    c.close()
+
+
 def test_batched_forward_and_apply(dh):
     n, B = 16, 3
     w = _weights(6)
