@@ -58,9 +58,10 @@ SWEEP_ADJ_BYTES_PER_CELL = 60  # adjoint sweep: state and output adjoint read, i
 # DRAM bytes per cell of one launch group (dram__bytes_read.sum + dram__bytes_write.sum) from
 # the ncu captures summarised in profiles/ (128^3, cold cache): forward sweep, the packed x
 # tile (43.9 MB) and the paired y / z forms (44.7, 45.1 MB) averaged; adjoint sweep (x, y, z
-# average of the marching pair with fitted segments, x with its transposes)
-# (416.6 + 253.6 + 254.2) / 3 MB; None where no capture of the current kernel exists
-TRAFFIC_BYTES_PER_CELL = {"sweep": 21.26, "sweep_adjoint": 146.9}
+# average of the marching pair with fitted segments, x with its input transposes and the
+# second pass writing the untransposed result) (374.5 + 253.7 + 254.2) / 3 MB; None where no
+# capture of the current kernel exists
+TRAFFIC_BYTES_PER_CELL = {"sweep": 21.26, "sweep_adjoint": 140.25}
 # the kernel forms (SWEEP_* per axis x, y, z) those captures measured
 PROFILED_VARIANTS = {"sweep": [1, 5, 5], "sweep_adjoint": [4, 4, 4]}
 # algorithmic bytes per cell of one timed launch group of each class (one particle per cell)

@@ -753,25 +753,15 @@ __device__ __forceinline__ void split_flux_vjp2(const float2 u[5], int f, float 
   lu[0] = add2(lu[0], lrho);
 }
 
-// grid (cdiv(n / 2, blockDim.x), cdiv(n, blockDim.y), n B); thread: cells x = 2 t, 2 t + 1
-// of row (y, z)
-template <int AXIS, int FC = 1 + AXIS>
-__global__ void __launch_bounds__(128)
-sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
-                        const float* __restrict__ luh, float* __restrict__ lin, int n,
-                        SArg nua, float gam) {
-  pdl_enter();
-  constexpr int F = FC;
-  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int b = blockIdx.z / n;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z - b * n;
-  if (x >= n || y >= n) return;
+// lam_in of cells x, x + 1 of row (y, z) (one instance's arrays): lam_out + lamUh + the
+// flux-split VJP of U with the face adjoints from lamUh of the neighbours along the axis
+template <int AXIS, int F>
+__device__ __forceinline__ void adj_final2_cells(const float* __restrict__ uin,
+                                                 const float* __restrict__ lout,
+                                                 const float* __restrict__ luh, int n, int x,
+                                                 int y, int z, float nu, float gam,
+                                                 float2 lu[5]) {
   const long long N3 = (long long)n * n * n;
-  uin += (size_t)b * 5 * N3;
-  lout += (size_t)b * 5 * N3;
-  luh += (size_t)b * 5 * N3;
-  lin += (size_t)b * 5 * N3;
-  const float nu = nua.at(b);
   const long long o = ((long long)z * n + y) * n + x;
   long long om, op;  // neighbours along the sweep axis (y or z), periodic
   if (AXIS == 1) {
@@ -782,7 +772,7 @@ sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__
     op = o + (long long)((z + 1 == n ? 0 : z + 1) - z) * n * n;
   }
   const float2 hnu = pk(0.5f * nu), mhnu = pk(-0.5f * nu);
-  float2 u[5], lR[5], lL[5], lu[5];
+  float2 u[5], lR[5], lL[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     u[k] = __ldg(reinterpret_cast<const float2*>(uin + k * N3 + o));
@@ -794,6 +784,63 @@ sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__
     lu[k] = add2(__ldg(reinterpret_cast<const float2*>(lout + k * N3 + o)), h0);
   }
   split_flux_vjp2(u, F, gam, lR, lL, lu);
+}
+
+// grid (cdiv(n / 2, blockDim.x), cdiv(n, blockDim.y), n B); thread: cells x = 2 t, 2 t + 1
+// of row (y, z). TOUT (the x axis run on x <-> y transposed copies): blocks of 16 x 32
+// threads cover 32 x 32 cells of a plane, and the result goes out through a shared-memory
+// tile in the untransposed layout, cell (z, y, x) of the copies to (z, x, y) of lin.
+template <int AXIS, int FC = 1 + AXIS, bool TOUT = false>
+__global__ void __launch_bounds__(TOUT ? 512 : 128)
+sweep_adj_final2_kernel(const float* __restrict__ uin, const float* __restrict__ lout,
+                        const float* __restrict__ luh, float* __restrict__ lin, int n,
+                        SArg nua, float gam) {
+  pdl_enter();
+  constexpr int F = FC;
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int b = blockIdx.z / n;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z - b * n;
+  const long long N3 = (long long)n * n * n;
+  if (TOUT) {
+    __shared__ float tile[5][32][33];  // [field][x - x0][y - y0]
+    const int lx = 2 * threadIdx.x, ly = threadIdx.y;
+    if (x < n && y < n) {
+      float2 lu[5];
+      adj_final2_cells<AXIS, F>(uin + (size_t)b * 5 * N3, lout + (size_t)b * 5 * N3,
+                                luh + (size_t)b * 5 * N3, n, x, y, z, nua.at(b), gam, lu);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        tile[k][lx][ly] = lu[k].x;
+        tile[k][lx + 1][ly] = lu[k].y;
+      }
+    }
+    __syncthreads();
+    const int x0 = 2 * blockIdx.x * blockDim.x, y0 = blockIdx.y * blockDim.y;
+    float* out = lin + (size_t)b * 5 * N3;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(lin) & 15) == 0) {
+      // rows of 32 outputs as eight float4 (y0 + c and n are multiples of 4)
+      for (int e = tid; e < 5 * 32 * 8; e += 512) {
+        const int k = e >> 8, r = (e >> 3) & 31, c = (e & 7) << 2;
+        if (x0 + r < n && y0 + c < n)
+          *reinterpret_cast<float4*>(out + k * N3 + ((long long)z * n + x0 + r) * n + y0 + c) =
+              make_float4(tile[k][r][c], tile[k][r][c + 1], tile[k][r][c + 2], tile[k][r][c + 3]);
+      }
+    } else {
+      for (int e = tid; e < 5 * 32 * 32; e += 512) {
+        const int k = e >> 10, r = (e >> 5) & 31, c = e & 31;
+        if (x0 + r < n && y0 + c < n)
+          out[k * N3 + ((long long)z * n + x0 + r) * n + y0 + c] = tile[k][r][c];
+      }
+    }
+    return;
+  }
+  if (x >= n || y >= n) return;
+  float2 lu[5];
+  adj_final2_cells<AXIS, F>(uin + (size_t)b * 5 * N3, lout + (size_t)b * 5 * N3,
+                            luh + (size_t)b * 5 * N3, n, x, y, z, nua.at(b), gam, lu);
+  lin += (size_t)b * 5 * N3;
+  const long long o = ((long long)z * n + y) * n + x;
 #pragma unroll
   for (int k = 0; k < 5; ++k) *reinterpret_cast<float2*>(lin + k * N3 + o) = lu[k];
 }
@@ -1230,6 +1277,16 @@ static sim_status launch_adj_x_transposed(const float* uin, const float* lout, f
   const dim3 blk = line_block(n, 128);
   DH_CUDA_TRY((launch_pdl(sweep_adj_march_kernel<1, 1>, line_grid(n, n, B, blk, cdiv(n, L)), blk, 0, st, ut, lt, luh, n, nu, gam, eps, dnu, L)));
   DH_LAUNCH_CHECK();
+  const uintptr_t al = reinterpret_cast<uintptr_t>(ut) | reinterpret_cast<uintptr_t>(lt) |
+                       reinterpret_cast<uintptr_t>(luh);
+  if (n % 2 == 0 && al % 8 == 0) {
+    // the second pass writes lin in the untransposed layout itself
+    const dim3 blk(16, 32);
+    const dim3 g(cdiv(n / 2, 16), cdiv(n, 32), n * B);
+    DH_CUDA_TRY((launch_pdl(sweep_adj_final2_kernel<1, 1, true>, g, blk, 0, st, ut, lt, luh, lin, n, nu, gam)));
+    DH_LAUNCH_CHECK();
+    return SIM_OK;
+  }
   DH_TRY((launch_adj_final<1, 1>(ut, lt, luh, it, n, nu, gam, B, st)));
   return launch_transpose_xy(it, lin, 5 * B, nullptr, nullptr, 0, n, st);
 }
