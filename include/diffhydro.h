@@ -488,8 +488,9 @@ sim_status sim_closure_train_step(sim_closure_t* c, const float* gas, const floa
 sim_status sim_closure_status(sim_closure_t* c);
 
 /* Time limit of each wait inside the closure's tensor-core kernels (a stage waiting for an
- * input plane, for its MMAs, or for a free accumulator buffer), in nanoseconds of the GPU's
- * global timer; default 1e9 (1 s). A wait that runs out records SIM_ETIMEOUT for
+ * input plane, for its MMAs, or for a free accumulator slot), in nanoseconds of the GPU's
+ * global timer (a wait gives up within 20 us after it); default 1e9 (1 s). A wait that
+ * runs out records SIM_ETIMEOUT for
  * sim_closure_status and its kernel stops early, after waiting (up to 4 s) for the copies
  * and MMAs it has already issued, so the context stays usable. ns = 0 allows a single
  * non-blocking check per wait (which makes the first waits of a launch give up: the way to

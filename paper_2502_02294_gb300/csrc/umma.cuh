@@ -73,7 +73,8 @@ __device__ __forceinline__ uint32_t mbar_test(uint64_t* mbar, uint32_t parity) {
 // timer (and at most 2^26 polls); returns 1 when the phase completed, 0 when the wait gave
 // up. limit_ns = 0: one non-blocking check only. Each poll may suspend the thread for up to
 // kSuspendNs until the phase completes, so a waiting warp does not spin on the issue slots
-// the working warps of its scheduler need.
+// the working warps of its scheduler need; a wait that gives up therefore does so up to
+// kSuspendNs after its limit.
 constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ uint32_t mbar_wait_ns(uint64_t* mbar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_test(mbar, parity)) return 1;
